@@ -1,0 +1,260 @@
+/*
+ * sse.h — C ABI of the B300 sliding super point estimator.
+ *
+ * Method: "Memory efficient distributed sliding super point cardinality estimation by
+ * GPU" (Jie Xu). A host aip is a sliding super point of window W(t,k) (k consecutive
+ * time slices, Section 3.1) when it contacted at least theta distinct opposite hosts bip
+ * in that window (Definitions 1 and 2). Each estimator keeps
+ *   - RSRA, r rows of 2^q sliding rough estimators (SRE) of eta cells (Section 3.3), used
+ *     to find candidate super points through the reversible hash group RHFG (Eq. 6-7);
+ *   - SLEA, r' rows of 2^q' overlapping sliding linear estimators (SLE) of eta' cells,
+ *     adjacent SLEs offset by delta' (Section 4), used to estimate cardinalities.
+ * The paper's cells are 16-bit distances incremented every slice; here every cell is an
+ * 8-bit time stamp 1 + (slice mod 255) (0 = never set), which needs no per-slice pass:
+ * a cell's distance is (current stamp - stamp) mod 255, and a cell is active in the
+ * window when that distance is < k. Both encodings give the same active cells and ages.
+ *
+ * Conventions for every call:
+ *   - Return SSE_OK (0) or a negative SSE_ERR_* code; sse_strerror() names it. Nothing
+ *     aborts, traps or asserts on the device; an invalid argument changes no state.
+ *   - Device pointers ("d_") are caller-owned CUDA global memory, borrowed for the call
+ *     and, for asynchronous calls, until the handle's stream reaches the call. Host
+ *     pointers ("h_") are caller-owned host memory.
+ *   - All device work of a handle is ordered on the CUDA stream given to sse_init().
+ *   - An IP pair is two uint32 in host byte order, {src, dst}: src is aip (the host whose
+ *     cardinality is measured), dst is bip (its opposite host); n pairs are 2n uint32.
+ *   - Handles are not thread-safe; use one handle per thread or serialise calls.
+ */
+#ifndef SSE_H
+#define SSE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SSE_VERSION 1
+
+#if defined(__GNUC__)
+#define SSE_API __attribute__((visibility("default")))
+#else
+#define SSE_API
+#endif
+
+enum sse_status {
+  SSE_OK = 0,
+  SSE_ERR_INVALID_PARAM = -1, /* argument or parameter out of its documented range */
+  SSE_ERR_OOM = -2,           /* device or pinned host allocation failed */
+  SSE_ERR_CAPACITY = -3,      /* a result did not fit its buffer; see the call */
+  SSE_ERR_MISMATCH = -4,      /* estimators differ in parameters, seed or slice */
+  SSE_ERR_CUDA = -5,          /* a CUDA runtime call failed (sticky for the handle) */
+  SSE_ERR_TIMEOUT = -6,       /* a bounded device-side wait gave up */
+  SSE_ERR_STATE = -7          /* call not valid in the handle's current state */
+};
+
+/* Per-host flags of a report or query. */
+enum sse_host_flags {
+  SSE_FLAG_SUPER = 1,    /* corrected weight >= w_theta, i.e. estimate >= theta */
+  SSE_FLAG_SATURATED = 2 /* SLE full or noise correction undefined; estimate capped */
+};
+
+/* Update strategies (sse_set_update_mode). Both give bit-identical estimator state. */
+enum sse_update_mode {
+  SSE_UPDATE_AUTO = 0,   /* choose per call from the batch size and the parameters */
+  SSE_UPDATE_DIRECT = 1, /* every cell write goes straight to the L2-resident estimator */
+  SSE_UPDATE_TILED = 2   /* SLEA writes collect in on-chip bitmaps, then merge into it */
+};
+
+/*
+ * Parameters (symbols of the paper). sse_params_default() fills the values of the
+ * paper's experiment (Section 5): r=r'=5, q=q'=17, delta=5, eta=8, delta'=16,
+ * eta'=2^14, theta=1024, with k=8.
+ *   r      rows of RSRA, 3..16 (candidate tuples start from rows 0, 1, 2: Alg. 4)
+ *   q      log2 of SREs per RSRA row, 5..26
+ *   delta  RHFG shift (Eq. 6); 0 derives ceil((32-q)/(r-2)). Needs delta < q and
+ *          (r-2)*delta + q >= 32 (Section 3.3)
+ *   eta    cells per SRE; must be 8 (the paper's eta, one 64-bit word per SRE)
+ *   r2     rows of SLEA (r'), 1..16
+ *   q2     log2 of SLEs per SLEA row (q'), 0..24
+ *   delta2 offset between adjacent SLEs (delta'), 1..eta2 (Section 4, Eq. 10)
+ *   eta2   cells per SLE (eta'), a power of two, 32..65536
+ *   k      window length in slices, 1..254
+ *   theta  super point threshold (Definition 2), >= 1
+ *   stamp_bits  cell width; must be 8
+ *   max_candidates  capacity for candidate hosts per close, 1..2^22
+ *   seed   every hash key derives from it (SplitMix64)
+ */
+typedef struct sse_params {
+  uint32_t r, q, delta, eta;
+  uint32_t r2, q2, delta2, eta2;
+  uint32_t k, theta;
+  uint32_t stamp_bits;
+  uint32_t max_candidates;
+  uint64_t seed;
+} sse_params;
+
+/* Values derived from sse_params by sse_derive(). */
+typedef struct sse_derived {
+  uint32_t delta;      /* after derivation */
+  uint32_t tau;        /* Eq. 1: smallest tau >= 0 with eta * 2^tau >= theta */
+  uint32_t hot_min;    /* an SRE is hot when >= ceil(eta * rho) cells are active, rho = 0.99(1-e^-1/3) */
+  uint32_t lg_eta2;    /* log2(eta') */
+  uint64_t row_len2;   /* cells of one SLEA row: 2^q' * delta' + eta' - delta' (Section 4) */
+  uint64_t row_pitch2; /* bytes between SLEA rows in device memory (row_len2 rounded up) */
+  uint64_t sre_bytes;  /* r * 2^q * eta */
+  uint64_t sle_bytes;  /* r' * row_pitch2 */
+  double w_theta;      /* eta' * (1 - exp(-theta/eta')): est >= theta <=> w^ >= w_theta (Eq. 8) */
+} sse_derived;
+
+typedef struct sse_handle sse_handle; /* opaque; owns the estimator's device memory */
+
+/*
+ * Result of closing a slice. The caller sets cap and the three array pointers (host
+ * memory, each of cap entries, any may be NULL to skip it); the library fills the rest.
+ * Candidates are all hosts whose r SREs are hot (Section 3.3), ascending; est is the
+ * Algorithm 8 estimate of each (Eq. 8 applied to the corrected weight of Eq. 12), as
+ * float; flags are SSE_FLAG_* bits. Super points are the candidates with
+ * SSE_FLAG_SUPER (the paper drops candidates whose estimate is below theta).
+ */
+typedef struct sse_report {
+  uint64_t slice;        /* index t of the slice that was closed (window ends at t) */
+  uint32_t n_candidates; /* total candidates found (may exceed cap) */
+  uint32_t n_super;      /* candidates flagged SSE_FLAG_SUPER */
+  uint32_t cap;          /* in: capacity of the arrays below */
+  uint32_t truncated;    /* 1 if n_candidates > cap or > max_candidates */
+  uint32_t* hosts;       /* in: [cap] host memory, or NULL */
+  float* est;            /* in: [cap] host memory, or NULL */
+  uint8_t* flags;        /* in: [cap] host memory, or NULL */
+} sse_report;
+
+/* Slice statistics of the most recent close or advance. */
+typedef struct sse_stats {
+  uint64_t slice;          /* index of the slice that was closed */
+  uint32_t hot[16];        /* |HSE(i)|: hot SREs of RSRA row i (Section 3.3) */
+  uint32_t active2[16];    /* active cells of SLEA row i; SF(i,k) = active2[i] / row_len2 (Definition 4) */
+  uint64_t join_pairs;     /* (he_0, he_1) pairs examined to grow candidate tuples */
+  uint32_t n_candidates;
+  uint32_t n_super;
+} sse_stats;
+
+/* Fills *p with the paper's experiment parameters (Section 5) and k = 8. */
+SSE_API void sse_params_default(sse_params* p);
+
+/* Validates *p and computes derived values (d may be NULL). SSE_ERR_INVALID_PARAM if
+ * any field is outside the ranges above. No device work. */
+SSE_API int sse_derive(const sse_params* p, sse_derived* d);
+
+/* Creates an estimator for slice 0 with every cell unset (the paper's initialisation of
+ * every short integer to its largest value, Section 3.2). cuda_stream is a cudaStream_t
+ * (NULL = legacy default stream) on which all of the handle's work is ordered. The device
+ * is the current CUDA device. Errors: INVALID_PARAM, OOM, CUDA. */
+SSE_API int sse_init(const sse_params* p, void* cuda_stream, sse_handle** out);
+
+/* Releases the handle and its device memory after its stream has drained. NULL is a no-op. */
+SSE_API void sse_destroy(sse_handle* h);
+
+/*
+ * Scans n_pairs IP pairs of the current slice (Algorithm 3 for RSRA: the pair updates
+ * the r SREs RSRA[i, RHFG[i](aip)], cell H2(bip), only if LSB(H1(bip)) >= tau;
+ * Algorithm 6 for SLEA: cell H3(bip) of SLE LH_i(aip) in every row i). Every touched cell
+ * is stamped with the current slice; repeated and concurrent writes are idempotent.
+ * d_pairs: device memory, 2*n_pairs uint32 {src, dst, src, dst, ...}, 8-byte aligned.
+ * Asynchronous on the handle's stream. n_pairs == 0 is a no-op.
+ * Errors: INVALID_PARAM (NULL with n_pairs > 0, misaligned), CUDA.
+ */
+SSE_API int sse_update(sse_handle* h, const uint32_t* d_pairs, uint64_t n_pairs);
+
+/*
+ * sse_update() for pairs in host memory: the library copies them to the device in
+ * chunks through its own staging buffers, overlapping copies with the update kernels.
+ * Page-locked host memory is copied directly; pageable memory is staged through pinned
+ * buffers. Returns when h_pairs may be reused (all its bytes have reached the device).
+ * Errors: INVALID_PARAM, OOM, CUDA.
+ */
+SSE_API int sse_update_host(sse_handle* h, const uint32_t* h_pairs, uint64_t n_pairs);
+
+/* Selects how sse_update() writes cells (enum sse_update_mode). Results never depend on
+ * it. Errors: INVALID_PARAM. */
+SSE_API int sse_set_update_mode(sse_handle* h, int mode);
+
+/*
+ * Closes the current slice t: expires cells older than the window W(t,k), finds the
+ * hot SREs of every row, grows candidate tuples and regains candidate hosts (Algorithms
+ * 4-5: every 32-bit aip whose r SREs are all hot), estimates each candidate (Algorithm 8,
+ * Eq. 11-12) and flags those reaching theta; then the handle moves to slice t+1 (the
+ * paper's "slice updating", Section 3.2). Blocks until the report is in host memory.
+ * out may be NULL (statistics are still kept, see sse_get_stats()).
+ * Errors: CAPACITY when candidates exceed max_candidates or out->cap (the report then
+ * holds the first entries, truncated = 1, and the slice still advances); CUDA.
+ */
+SSE_API int sse_close_slice(sse_handle* h, sse_report* out);
+
+/* Moves to the next slice without detection: expires old cells and advances, so a router
+ * whose super points are detected elsewhere (after a merge) keeps a valid window.
+ * Asynchronous. Errors: CUDA. */
+SSE_API int sse_advance(sse_handle* h);
+
+/*
+ * Merges estimators of distributed routers (Algorithm 2 for RSRA, Algorithm 7 for SLEA):
+ * every cell of dst becomes the most recent of dst's and the sources' stamps (the
+ * smallest distance), so dst then describes the union of all their traffic. All handles
+ * need identical parameters and seed and the same current slice, and must live on the
+ * same device; sources are read on dst's stream (the caller orders their own streams
+ * before it, e.g. with sse_sync()). n in 1..64; dst may not be among srcs.
+ * Errors: INVALID_PARAM, MISMATCH, CUDA.
+ */
+SSE_API int sse_merge(sse_handle* dst, const sse_handle* const* srcs, int n);
+
+/*
+ * Estimates the cardinality of n arbitrary hosts in the current window, as if the
+ * current slice were closed now (Algorithm 8 with Eq. 11-12), without changing state.
+ * d_hosts: [n] device uint32; d_est: [n] device float; d_flags: [n] device uint8 or NULL;
+ * d_hist: [n][k] device uint32 or NULL, the number of union-SLE cells whose (largest)
+ * distance is a, for a = 0..k-1. Asynchronous. Errors: INVALID_PARAM, CUDA.
+ */
+SSE_API int sse_query(sse_handle* h, const uint32_t* d_hosts, uint32_t n, float* d_est, uint8_t* d_flags,
+                      uint32_t* d_hist);
+
+/* Statistics of the last close (hot SREs per row, active SLEA cells per row, candidate
+ * and super point counts). Synchronises the stream. Errors: CUDA. */
+SSE_API int sse_get_stats(sse_handle* h, sse_stats* out);
+
+/* Copies the hot-SRE bitmap of the last close into h_bits (r * 2^q bits, row-major,
+ * bit j of row i at bit i*2^q + j, little-endian uint32 words). Synchronous.
+ * Errors: INVALID_PARAM (cap_bytes too small), CUDA. */
+SSE_API int sse_get_hot_bitmap(sse_handle* h, uint32_t* h_bits, size_t cap_bytes);
+
+/*
+ * Checkpoint: writes the estimator (parameters, current slice, RSRA and SLEA stamps) into
+ * h_buf; *used receives the size. With h_buf == NULL only *used is set. Synchronous.
+ * sse_import_state() restores it into a handle with identical parameters; the result is
+ * bit-identical to the exported estimator. Errors: CAPACITY, MISMATCH, INVALID_PARAM, CUDA.
+ */
+SSE_API int sse_export_state(sse_handle* h, void* h_buf, size_t cap, size_t* used);
+SSE_API int sse_import_state(sse_handle* h, const void* h_buf, size_t n);
+
+/* Raw stamp arrays, for inspection: RSRA as [r][2^q][eta] bytes and SLEA as
+ * [r'][row_pitch2] bytes (cells beyond row_len2 are padding). Stamps are 1+(slice mod 255),
+ * 0 = unset. Synchronous. Either pointer may be NULL. Errors: CAPACITY, CUDA. */
+SSE_API int sse_read_stamps(sse_handle* h, uint8_t* h_sre, size_t sre_cap, uint8_t* h_sle, size_t sle_cap);
+
+/* Index t of the slice currently being scanned. */
+SSE_API uint64_t sse_current_slice(const sse_handle* h);
+
+/* Number of CUDA kernels this handle has launched since sse_init (for accounting). */
+SSE_API uint64_t sse_kernel_launches(const sse_handle* h);
+
+/* Waits for the handle's stream and reports deferred errors (CUDA faults, device-side
+ * error flags). Errors: CUDA, TIMEOUT. */
+SSE_API int sse_sync(sse_handle* h);
+
+/* Static string for a status code. */
+SSE_API const char* sse_strerror(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SSE_H */

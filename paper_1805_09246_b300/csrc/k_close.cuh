@@ -1,0 +1,130 @@
+// Slice close, part 1: expire, weigh and count (Sections 3.2-3.3, Definition 4).
+//
+// One pass over the whole estimator. For every cell the current stamp decides whether it
+// is active in the window W(t,k) (distance < k); cells older than the window are reset to
+// unset so that the 255-slice stamp cycle never wraps onto a live cell. RSRA: one thread
+// per SRE (8 cells = one 64-bit word); the SRE is hot when at least hot_min cells are
+// active, and the warp's 32 hot bits form one word of the hot bitmap. SLEA: 16 cells per
+// thread; active cells are summed per row (numerators of the setting factors SF(i,k)).
+#pragma once
+
+#include "sse_internal.cuh"
+
+namespace sse {
+
+constexpr int kCloseThreads = 256;
+constexpr uint32_t kSleBytesPerBlock = kCloseThreads * 16;  // == kPitchAlign
+
+// act[s] = 1 when stamp s is active at current stamp cs for window k.
+__device__ __forceinline__ void build_active_lut(uint8_t* act, uint32_t cs, uint32_t k) {
+  for (uint32_t s = threadIdx.x; s < 256; s += blockDim.x) act[s] = stamp_age(s, cs) < k ? 1 : 0;
+}
+
+// mode bit 0: write back expired cells; bit 1: write the hot bitmap. Blocks
+// [0, sre_blocks) cover RSRA, the rest cover SLEA.
+__global__ void __launch_bounds__(kCloseThreads) k_close(const __grid_constant__ KParams p,
+                                                          uint8_t* __restrict__ sre, uint8_t* __restrict__ sle,
+                                                          uint32_t* __restrict__ hot_bits,
+                                                          uint32_t* __restrict__ active2, uint32_t cs,
+                                                          uint32_t sre_blocks, uint32_t mode) {
+  __shared__ uint8_t act[256];
+  __shared__ uint32_t warp_sum[kCloseThreads / 32];
+  build_active_lut(act, cs, p.k);
+  __syncthreads();
+  const bool expire = (mode & 1u) != 0;
+  if (blockIdx.x < sre_blocks) {
+    // RSRA: SRE index g (row-major over [r][2^q]); r * 2^q is a multiple of 32.
+    const uint64_t n_sre = (uint64_t)p.r << p.q;
+    const uint64_t g = (uint64_t)blockIdx.x * kCloseThreads + threadIdx.x;
+    if (g >= n_sre) return;  // whole warps only
+    uint2* cell = reinterpret_cast<uint2*>(sre) + g;
+    const uint2 v = *cell;
+    uint32_t weight = 0, keep_lo = 0, keep_hi = 0;
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      const uint32_t s0 = (v.x >> (8 * b)) & 0xFFu, s1 = (v.y >> (8 * b)) & 0xFFu;
+      const uint32_t a0 = act[s0], a1 = act[s1];
+      weight += a0 + a1;
+      keep_lo |= (a0 ? 0xFFu : 0u) << (8 * b);
+      keep_hi |= (a1 ? 0xFFu : 0u) << (8 * b);
+    }
+    const unsigned ballot = __ballot_sync(0xFFFFFFFFu, weight >= p.hot_min);
+    if ((mode & 2u) && (threadIdx.x & 31) == 0) hot_bits[g >> 5] = ballot;
+    if (expire && ((v.x & ~keep_lo) | (v.y & ~keep_hi)) != 0) *cell = make_uint2(v.x & keep_lo, v.y & keep_hi);
+    return;
+  }
+  // SLEA: block b covers bytes [b*4096, b*4096 + 4096) of one row.
+  const uint64_t b = blockIdx.x - sre_blocks;
+  const uint64_t blocks_per_row = p.row_pitch2 / kSleBytesPerBlock;
+  const uint32_t row = (uint32_t)(b / blocks_per_row);
+  uint4* cell = reinterpret_cast<uint4*>(sle + b * kSleBytesPerBlock) + threadIdx.x;
+  const uint4 v = *cell;
+  const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+  uint32_t keep[4];
+  uint32_t count = 0;
+#pragma unroll
+  for (int x = 0; x < 4; ++x) {
+    keep[x] = 0;
+#pragma unroll
+    for (int y = 0; y < 4; ++y) {
+      const uint32_t a = act[(w[x] >> (8 * y)) & 0xFFu];
+      count += a;
+      keep[x] |= (a ? 0xFFu : 0u) << (8 * y);
+    }
+  }
+  if (expire && ((w[0] & ~keep[0]) | (w[1] & ~keep[1]) | (w[2] & ~keep[2]) | (w[3] & ~keep[3])) != 0)
+    *cell = make_uint4(w[0] & keep[0], w[1] & keep[1], w[2] & keep[2], w[3] & keep[3]);
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) count += __shfl_xor_sync(0xFFFFFFFFu, count, off);
+  if ((threadIdx.x & 31) == 0) warp_sum[threadIdx.x >> 5] = count;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t total = 0;
+    for (int x = 0; x < kCloseThreads / 32; ++x) total += warp_sum[x];
+    if (total) atomicAdd(&active2[row], total);
+  }
+}
+
+// Hot lists HSE(0) and HSE(1) (column indices, any order) and |HSE(i)| for every row.
+// One thread per bitmap word; warp-aggregated appends.
+__global__ void __launch_bounds__(256) k_hot_lists(const uint32_t* __restrict__ hot_bits, uint32_t r, uint32_t q,
+                                                   uint32_t* __restrict__ hot_count, uint32_t* __restrict__ list0,
+                                                   uint32_t* __restrict__ list1, uint32_t* __restrict__ n_list) {
+  __shared__ uint32_t row_sum[kMaxRows];
+  if (threadIdx.x < kMaxRows) row_sum[threadIdx.x] = 0;
+  __syncthreads();
+  const uint32_t words_per_row = 1u << (q - 5);
+  const uint64_t total = (uint64_t)r * words_per_row;
+  const uint32_t lane = threadIdx.x & 31;
+  for (uint64_t base = (uint64_t)blockIdx.x * blockDim.x; base < total; base += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t wi = base + threadIdx.x;
+    const uint32_t word = wi < total ? hot_bits[wi] : 0u;
+    const uint32_t row = wi < total ? (uint32_t)(wi >> (q - 5)) : 0u;
+    const uint32_t bits = __popc(word);
+    if (bits) atomicAdd(&row_sum[row], bits);
+    // rows 0 and 1: append the column of every hot SRE
+    for (uint32_t rr = 0; rr < 2; ++rr) {
+      const uint32_t mine = (row == rr) ? bits : 0u;
+      uint32_t incl = mine;
+#pragma unroll
+      for (int off = 1; off < 32; off <<= 1) {
+        const uint32_t t = __shfl_up_sync(0xFFFFFFFFu, incl, off);
+        if (lane >= (uint32_t)off) incl += t;
+      }
+      const uint32_t warp_total = __shfl_sync(0xFFFFFFFFu, incl, 31);
+      uint32_t start = 0;
+      if (lane == 31 && warp_total) start = atomicAdd(&n_list[rr], warp_total);
+      start = __shfl_sync(0xFFFFFFFFu, start, 31);
+      if (mine) {
+        uint32_t* list = rr == 0 ? list0 : list1;
+        uint32_t at = start + incl - mine;
+        const uint32_t col0 = (uint32_t)(wi & (words_per_row - 1)) << 5;
+        for (uint32_t m = word; m; m &= m - 1) list[at++] = col0 + (__ffs(m) - 1);
+      }
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x < r && row_sum[threadIdx.x]) atomicAdd(&hot_count[threadIdx.x], row_sum[threadIdx.x]);
+}
+
+}  // namespace sse

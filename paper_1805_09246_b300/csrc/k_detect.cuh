@@ -1,0 +1,254 @@
+// Slice close, part 2: candidate hosts, ordering and estimation.
+//
+// Candidates (Section 3.3, Algorithms 4-5). A host aip is a candidate when all r of its
+// SREs RSRA[i, RHFG[i](aip)] are hot. For hot he_0 in row 0 and he_1 in row 1,
+// B(1) = he_0 XOR he_1 holds aip bits [delta, delta+q) (Eq. 7). Row i >= 2 must hold
+// B(i) = he_0 XOR he_i whose low q-delta bits repeat the top q-delta bits of B(i-1),
+// so only its top delta bits are free: the 2^delta choices are looked up in row i's hot
+// bitmap (the paper's overlap test, applied to all of HSE(i) at once). A complete chain
+// fixes bits [delta, 32); the delta low bits are enumerated and a host is kept when
+// RHFG[0] maps it back to he_0, which makes all of its r SREs exactly the chain's.
+//
+// Estimation (Algorithm 8, Eq. 11-12): one warp per host gathers its r' SLEs; a cell of
+// the union SLE counts when it is active in every row, with the largest distance over the
+// rows; the corrected weight and the estimate are computed in FP64 with explicit
+// round-to-nearest operations in a fixed order, so the super point decision is exact.
+#pragma once
+
+#include "sse_internal.cuh"
+
+namespace sse {
+
+__device__ __forceinline__ bool hot_bit(const uint32_t* hot_bits, uint32_t q, uint32_t row, uint32_t col) {
+  return (hot_bits[((uint64_t)row << (q - 5)) + (col >> 5)] >> (col & 31)) & 1u;
+}
+
+// B(i) = (aip >> i*delta) mod 2^q must have no bits at or above address bit 32.
+__device__ __forceinline__ bool fits32(uint32_t i, uint32_t delta, uint32_t q, uint32_t b) {
+  const uint32_t lo = i * delta;
+  if (lo >= 32) return b == 0;
+  if (lo + q > 32) return (b >> (32 - lo)) == 0;
+  return true;
+}
+
+__device__ __forceinline__ void emit_candidate(uint32_t aip, uint32_t* cand, uint32_t* n_cand, uint32_t cap,
+                                               uint32_t* overflow) {
+  const uint32_t at = atomicAdd(n_cand, 1u);
+  if (at < cap)
+    cand[at] = aip;
+  else
+    atomicOr(overflow, 1u);
+}
+
+// Regain the hosts of a complete chain B[1..r-1] (bits [delta, 32) fixed).
+__device__ __forceinline__ void regain(const KParams& p, uint32_t he0, const uint32_t* B, uint32_t* cand,
+                                       uint32_t* n_cand, uint32_t cap, uint32_t* overflow) {
+  uint64_t high = (uint64_t)B[1] << p.delta;
+  for (uint32_t i = 2; i < p.r; ++i)
+    high |= (uint64_t)(B[i] >> (p.q - p.delta)) << (i * p.delta + p.q - p.delta);
+  for (uint32_t low = 0; low < (1u << p.delta); ++low) {
+    const uint32_t aip = (uint32_t)(high | low);
+    if (mas_top(p.key_a[kR0], p.key_b[kR0], aip, p.q) != he0) continue;
+    emit_candidate(aip, cand, n_cand, cap, overflow);
+  }
+}
+
+// Rows 3..r-1 of a chain whose rows 0..2 are hot (rare: depth-first, explicit stack).
+__device__ __noinline__ void grow_deep(const KParams& p, const uint32_t* hot_bits, uint32_t he0, uint32_t b1,
+                                       uint32_t b2, uint32_t* cand, uint32_t* n_cand, uint32_t cap,
+                                       uint32_t* overflow) {
+  uint32_t B[kMaxRows];
+  uint32_t next[kMaxRows];
+  B[1] = b1;
+  B[2] = b2;
+  const uint32_t fan = 1u << p.delta;
+  const uint32_t shift_hi = p.q - p.delta;
+  int i = 3;
+  if (i < (int)p.r) next[i] = 0;
+  while (i >= 3) {
+    if (i == (int)p.r) {  // chain complete
+      regain(p, he0, B, cand, n_cand, cap, overflow);
+      i -= 1;
+      continue;
+    }
+    if (next[i] == fan) {  // level exhausted
+      i -= 1;
+      continue;
+    }
+    const uint32_t bi = (B[i - 1] >> p.delta) | (next[i] << shift_hi);
+    next[i] += 1;
+    if (!fits32(i, p.delta, p.q, bi) || !hot_bit(hot_bits, p.q, i, he0 ^ bi)) continue;
+    B[i] = bi;
+    i += 1;
+    if (i < (int)p.r) next[i] = 0;
+  }
+}
+
+// Blocks stride over HSE(0), threads over HSE(1).
+__global__ void __launch_bounds__(256) k_join(const __grid_constant__ KParams p, const uint32_t* __restrict__ hot_bits,
+                                              const uint32_t* __restrict__ list0, const uint32_t* __restrict__ list1,
+                                              const uint32_t* __restrict__ n_list, uint32_t* __restrict__ cand,
+                                              uint32_t* __restrict__ n_cand, uint32_t cap,
+                                              uint32_t* __restrict__ overflow) {
+  const uint32_t n0 = n_list[0], n1 = n_list[1];
+  const uint32_t fan = 1u << p.delta;
+  const uint32_t shift_hi = p.q - p.delta;
+  const bool row2_fits_all = 2 * p.delta + p.q <= 32;
+  for (uint32_t a = blockIdx.x; a < n0; a += gridDim.x) {
+    const uint32_t he0 = list0[a];
+    for (uint32_t b = threadIdx.x; b < n1; b += blockDim.x) {
+      const uint32_t b1 = he0 ^ list1[b];
+      if (!fits32(1, p.delta, p.q, b1)) continue;
+      const uint32_t low2 = b1 >> p.delta;
+      for (uint32_t t = 0; t < fan; ++t) {
+        const uint32_t b2 = low2 | (t << shift_hi);
+        if (!row2_fits_all && !fits32(2, p.delta, p.q, b2)) continue;
+        if (!hot_bit(hot_bits, p.q, 2, he0 ^ b2)) continue;
+        grow_deep(p, hot_bits, he0, b1, b2, cand, n_cand, cap, overflow);
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------- ordering
+// Bitonic sort of each kSortChunk-element chunk in shared memory; the tail beyond n is
+// padded with 0xFFFFFFFF (which sorts last, so the first n entries are the real ones).
+__global__ void __launch_bounds__(1024) k_sort_chunks(uint32_t* __restrict__ keys, const uint32_t* __restrict__ n_ptr,
+                                                      uint32_t cap) {
+  __shared__ uint32_t s[kSortChunk];
+  const uint32_t n = min(*n_ptr, cap);
+  const uint32_t start = blockIdx.x * kSortChunk;
+  if (start >= n) return;
+  for (uint32_t x = threadIdx.x; x < kSortChunk; x += blockDim.x)
+    s[x] = (start + x < n) ? keys[start + x] : 0xFFFFFFFFu;
+  __syncthreads();
+  for (uint32_t size = 2; size <= kSortChunk; size <<= 1) {
+    for (uint32_t stride = size >> 1; stride > 0; stride >>= 1) {
+      for (uint32_t x = threadIdx.x; x < kSortChunk / 2; x += blockDim.x) {
+        const uint32_t lo = 2 * x - (x & (stride - 1));
+        const uint32_t hi = lo + stride;
+        const bool up = (lo & size) == 0;
+        const uint32_t a = s[lo], b = s[hi];
+        if ((a > b) == up) {
+          s[lo] = b;
+          s[hi] = a;
+        }
+      }
+      __syncthreads();
+    }
+  }
+  for (uint32_t x = threadIdx.x; x < kSortChunk && start + x < n; x += blockDim.x) keys[start + x] = s[x];
+}
+
+// Merge sorted runs of length `width` pairwise from src into dst (stable; ranks by
+// binary search in the partner run).
+__global__ void __launch_bounds__(256) k_merge_runs(const uint32_t* __restrict__ src, uint32_t* __restrict__ dst,
+                                                    const uint32_t* __restrict__ n_ptr, uint32_t cap,
+                                                    uint32_t width) {
+  const uint32_t n = min(*n_ptr, cap);
+  for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n; x += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t pair_start = (x / (2ull * width)) * (2ull * width);
+    const uint64_t mid = pair_start + width < n ? pair_start + width : n;
+    const uint64_t end = pair_start + 2ull * width < n ? pair_start + 2ull * width : n;
+    const uint32_t v = src[x];
+    uint64_t lo, hi, pos;
+    if (x < mid) {  // left run: count right-run elements < v
+      lo = mid;
+      hi = end;
+      while (lo < hi) {
+        const uint64_t m = (lo + hi) >> 1;
+        if (src[m] < v) lo = m + 1; else hi = m;
+      }
+      pos = pair_start + (x - pair_start) + (lo - mid);
+    } else {  // right run: count left-run elements <= v
+      lo = pair_start;
+      hi = mid;
+      while (lo < hi) {
+        const uint64_t m = (lo + hi) >> 1;
+        if (src[m] <= v) lo = m + 1; else hi = m;
+      }
+      pos = pair_start + (x - mid) + (lo - pair_start);
+    }
+    dst[pos] = v;
+  }
+}
+
+// ---------------------------------------------------------------- estimation
+constexpr int kEstWarps = 8;
+
+// hosts: n_ptr ? min(*n_ptr, n) hosts : n hosts. active2: active cells per SLEA row.
+// Outputs (any may be NULL except est): est, flags, w (FP64 corrected weight), U, hist[n][k].
+__global__ void __launch_bounds__(kEstWarps * 32) k_estimate(
+    const __grid_constant__ KParams p, const uint8_t* __restrict__ sle, const uint32_t* __restrict__ hosts,
+    const uint32_t* __restrict__ n_ptr, uint32_t n, const uint32_t* __restrict__ active2, double w_theta,
+    uint32_t cs, float* __restrict__ est, uint8_t* __restrict__ flags, double* __restrict__ w_out,
+    uint32_t* __restrict__ u_out, uint32_t* __restrict__ hist, uint32_t* __restrict__ n_super) {
+  __shared__ uint8_t age_lut[256];
+  __shared__ uint32_t sh_hist[kEstWarps][256];
+  for (uint32_t s = threadIdx.x; s < 256; s += blockDim.x) {
+    const uint32_t a = stamp_age(s, cs);
+    age_lut[s] = a < p.k ? (uint8_t)a : 255;
+  }
+  __syncthreads();
+  const uint32_t count = n_ptr ? min(*n_ptr, n) : n;
+  const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const double eta2 = (double)p.eta2;
+  for (uint32_t h = blockIdx.x * kEstWarps + warp; h < count; h += gridDim.x * kEstWarps) {
+    const uint32_t aip = hosts[h];
+    if (hist)
+      for (uint32_t a = lane; a < p.k; a += 32) sh_hist[warp][a] = 0;
+    __syncwarp();
+    const uint8_t* row_base[kMaxRows];
+    for (uint32_t i = 0; i < p.r2; ++i) {
+      const uint32_t j = mas_top(p.key_a[kLH + i], p.key_b[kLH + i], aip, p.q2);
+      row_base[i] = sle + i * p.row_pitch2 + (uint64_t)j * p.delta2;
+    }
+    uint32_t u = 0;
+    for (uint32_t z = lane; z < p.eta2; z += 32) {
+      uint32_t m = 0;
+      for (uint32_t i = 0; i < p.r2; ++i) m = max(m, (uint32_t)age_lut[row_base[i][z]]);
+      if (m != 255) {
+        u += 1;
+        if (hist) atomicAdd(&sh_hist[warp][m], 1u);
+      }
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) u += __shfl_xor_sync(0xFFFFFFFFu, u, off);
+    __syncwarp();
+    if (hist)
+      for (uint32_t a = lane; a < p.k; a += 32) hist[(uint64_t)h * p.k + a] = sh_hist[warp][a];
+    if (lane == 0) {
+      // Eq. 12 with SF(i,k) = active2[i] / row_len2 (Definition 4), multiplied in row order.
+      double P = 1.0;
+      for (uint32_t i = 0; i < p.r2; ++i) P = __dmul_rn(P, __ddiv_rn((double)active2[i], (double)p.row_len2));
+      uint8_t f = 0;
+      double w;
+      if (P >= 1.0) {
+        w = eta2 - 1.0;
+        f |= SSE_FLAG_SATURATED;
+      } else {
+        const double num = __dsub_rn((double)u, __dmul_rn(eta2, P));
+        const double den = __dsub_rn(1.0, P);
+        w = __ddiv_rn(num, den);
+        if (w < 0.0) w = 0.0;
+        if (!(w <= eta2 - 1.0)) {
+          w = eta2 - 1.0;
+          f |= SSE_FLAG_SATURATED;
+        }
+      }
+      // Eq. 8 on the corrected weight.
+      const double e = __dmul_rn(-eta2, log(__ddiv_rn(__dsub_rn(eta2, w), eta2)));
+      if (w >= w_theta) {
+        f |= SSE_FLAG_SUPER;
+        if (n_super) atomicAdd(n_super, 1u);
+      }
+      est[h] = (float)e;
+      if (flags) flags[h] = f;
+      if (w_out) w_out[h] = w;
+      if (u_out) u_out[h] = u;
+    }
+    __syncwarp();
+  }
+}
+
+}  // namespace sse

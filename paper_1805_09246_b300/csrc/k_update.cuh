@@ -1,0 +1,105 @@
+// Per-packet update of RSRA (Algorithm 3) and SLEA (Algorithm 6): direct stamping.
+//
+// One thread handles two IP pairs per 128-bit load; the hash functions are evaluated in
+// registers and every touched cell is written with the current stamp. Cells written by
+// several threads in the same slice all receive the same value, so the writes need no
+// atomics and the final state is independent of order and grid shape (Section 3.2:
+// a cell may be set to zero many times, which needs no synchronisation).
+#pragma once
+
+#include "sse_internal.cuh"
+
+namespace sse {
+
+// Streaming 128-bit load of packet data: read once, so keep it out of L1 and mark it
+// first to be evicted from L2, where the estimator should stay resident.
+__device__ __forceinline__ uint4 load_stream(const uint4* ptr) {
+  uint4 v;
+  uint64_t policy;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(policy));
+  asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.v4.u32 {%0,%1,%2,%3}, [%4], %5;"
+               : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+               : "l"(ptr), "l"(policy));
+  return v;
+}
+
+// Algorithm 6 for one pair: in every row i of SLEA, cell H3(bip) of SLE LH_i(aip).
+template <int R2>
+__device__ __forceinline__ void stamp_slea(const KParams& p, uint32_t aip, uint32_t bip, uint8_t* sle,
+                                           uint8_t stamp) {
+  const uint32_t h3 = mas_top(p.key_a[kH3], p.key_b[kH3], bip, p.lg_eta2);
+  const uint32_t rows = R2 > 0 ? (uint32_t)R2 : p.r2;
+#pragma unroll
+  for (uint32_t i = 0; i < (R2 > 0 ? (uint32_t)R2 : (uint32_t)kMaxRows); ++i) {
+    if (R2 == 0 && i >= rows) break;
+    const uint32_t j = mas_top(p.key_a[kLH + i], p.key_b[kLH + i], aip, p.q2);
+    sle[i * p.row_pitch2 + (uint64_t)j * p.delta2 + h3] = stamp;
+  }
+}
+
+// Algorithm 3 for one pair: if LSB(H1(bip)) >= tau, cell H2(bip) of SRE RSRA[i, RHFG[i](aip)]
+// in every row i, with RHFG[i] from Eq. 6.
+__device__ __forceinline__ void stamp_rsra(const KParams& p, uint32_t aip, uint32_t bip, uint8_t* sre,
+                                           uint8_t stamp) {
+  const uint32_t h1 = mas_top(p.key_a[kH1], p.key_b[kH1], bip, 32);
+  if (!p.sre_on || (h1 & p.tau_mask) != 0) return;  // LSB(h1) < tau
+  const uint32_t h2 = mas_top(p.key_a[kH2], p.key_b[kH2], bip, 3);
+  const uint32_t r0 = mas_top(p.key_a[kR0], p.key_b[kR0], aip, p.q);
+  const uint32_t qmask = (1u << p.q) - 1u;
+  sre[((uint64_t)r0 << 3) + h2] = stamp;
+  for (uint32_t i = 1; i < p.r; ++i) {
+    const uint32_t col = (uint32_t)((((uint64_t)aip >> (i * p.delta)) ^ r0) & qmask);
+    sre[((((uint64_t)i << p.q) + col) << 3) + h2] = stamp;
+  }
+}
+
+template <int R2>
+__device__ __forceinline__ void apply_pair(const KParams& p, uint32_t aip, uint32_t bip, uint8_t* sre,
+                                           uint8_t* sle, uint8_t stamp) {
+  stamp_slea<R2>(p, aip, bip, sle, stamp);
+  stamp_rsra(p, aip, bip, sre, stamp);
+}
+
+// pairs: 8-byte aligned {src, dst} pairs. UNROLL 128-bit loads are in flight per thread.
+template <int R2, int UNROLL>
+__global__ void __launch_bounds__(256) k_update_direct(const __grid_constant__ KParams p,
+                                                       const uint2* __restrict__ pairs, uint64_t n,
+                                                       uint8_t* __restrict__ sre, uint8_t* __restrict__ sle,
+                                                       uint8_t stamp) {
+  const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  const uint2* base = pairs;
+  uint64_t cnt = n;
+  if ((reinterpret_cast<uintptr_t>(base) & 15u) != 0 && cnt > 0) {  // peel one pair to reach 16 B
+    if (tid == 0) {
+      uint2 v = base[0];
+      apply_pair<R2>(p, v.x, v.y, sre, sle, stamp);
+    }
+    base += 1;
+    cnt -= 1;
+  }
+  const uint4* vec = reinterpret_cast<const uint4*>(base);
+  const uint64_t nvec = cnt >> 1;
+  for (uint64_t i0 = tid; i0 < nvec; i0 += stride * UNROLL) {
+    uint4 buf[UNROLL];
+#pragma unroll
+    for (int u = 0; u < UNROLL; ++u) {
+      const uint64_t i = i0 + (uint64_t)u * stride;
+      if (i < nvec) buf[u] = load_stream(vec + i);
+    }
+#pragma unroll
+    for (int u = 0; u < UNROLL; ++u) {
+      const uint64_t i = i0 + (uint64_t)u * stride;
+      if (i < nvec) {
+        apply_pair<R2>(p, buf[u].x, buf[u].y, sre, sle, stamp);
+        apply_pair<R2>(p, buf[u].z, buf[u].w, sre, sle, stamp);
+      }
+    }
+  }
+  if ((cnt & 1) && tid == 0) {
+    uint2 v = base[cnt - 1];
+    apply_pair<R2>(p, v.x, v.y, sre, sle, stamp);
+  }
+}
+
+}  // namespace sse

@@ -1,0 +1,616 @@
+// Host runtime of libsse: parameters, handles, launches and the C ABI of sse.h.
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <algorithm>
+#include <cmath>
+#include <new>
+
+#include "k_close.cuh"
+#include "k_detect.cuh"
+#include "k_merge.cuh"
+#include "k_update.cuh"
+#include "sse.h"
+#include "sse_internal.cuh"
+
+namespace sse {
+namespace {
+
+// SplitMix64 (Steele, Lea, Flood 2014): the hash keys are its successive outputs.
+uint64_t splitmix64(uint64_t& state) {
+  state += 0x9E3779B97F4A7C15ULL;
+  uint64_t z = state;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+  return z ^ (z >> 31);
+}
+
+uint32_t ilog2(uint64_t v) {
+  uint32_t m = 0;
+  while ((1ull << m) < v) ++m;
+  return m;
+}
+
+bool is_pow2(uint64_t v) { return v && !(v & (v - 1)); }
+
+int derive_params(const sse_params& in, sse_params& p, sse_derived& d) {
+  p = in;
+  if (p.r < 3 || p.r > (uint32_t)kMaxRows) return SSE_ERR_INVALID_PARAM;
+  if (p.q < 5 || p.q > 26) return SSE_ERR_INVALID_PARAM;
+  if (p.delta == 0) p.delta = (32 - p.q + p.r - 3) / (p.r - 2);  // ceil((32 - q) / (r - 2))
+  if (p.delta == 0 || p.delta >= p.q) return SSE_ERR_INVALID_PARAM;
+  if ((uint64_t)(p.r - 2) * p.delta + p.q < 32) return SSE_ERR_INVALID_PARAM;
+  if ((uint64_t)(p.r - 1) * p.delta + p.q > 64) return SSE_ERR_INVALID_PARAM;
+  if (p.eta != (uint32_t)kEta) return SSE_ERR_INVALID_PARAM;
+  if (p.r2 < 1 || p.r2 > (uint32_t)kMaxRows || p.q2 > 24) return SSE_ERR_INVALID_PARAM;
+  if (!is_pow2(p.eta2) || p.eta2 < 32 || p.eta2 > 65536) return SSE_ERR_INVALID_PARAM;
+  if (p.delta2 < 1 || p.delta2 > p.eta2) return SSE_ERR_INVALID_PARAM;
+  if (p.k < 1 || p.k > 254) return SSE_ERR_INVALID_PARAM;
+  if (p.theta < 1) return SSE_ERR_INVALID_PARAM;
+  if (p.stamp_bits != 8) return SSE_ERR_INVALID_PARAM;
+  if (p.max_candidates < 1 || p.max_candidates > (1u << 22)) return SSE_ERR_INVALID_PARAM;
+  memset(&d, 0, sizeof(d));
+  d.delta = p.delta;
+  uint32_t tau = 0;
+  while (((uint64_t)p.eta << tau) < p.theta) ++tau;  // Eq. 1
+  d.tau = tau;
+  const double rho = 0.99 * (1.0 - std::exp(-1.0 / 3.0));
+  d.hot_min = (uint32_t)std::ceil((double)p.eta * rho);
+  d.lg_eta2 = ilog2(p.eta2);
+  d.row_len2 = ((uint64_t)1 << p.q2) * p.delta2 + p.eta2 - p.delta2;
+  d.row_pitch2 = (d.row_len2 + kPitchAlign - 1) / kPitchAlign * kPitchAlign;
+  d.sre_bytes = (uint64_t)p.r << p.q << 3;
+  d.sle_bytes = (uint64_t)p.r2 * d.row_pitch2;
+  d.w_theta = (double)p.eta2 * (-std::expm1(-(double)p.theta / (double)p.eta2));
+  return SSE_OK;
+}
+
+}  // namespace
+}  // namespace sse
+
+using namespace sse;
+
+struct sse_handle {
+  sse_params p;
+  sse_derived d;
+  KParams kp;
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  uint64_t slice = 0;
+  int sticky = SSE_OK;    // first CUDA error seen; later calls return it
+  uint64_t launches = 0;  // kernels launched by this handle
+  int update_mode = SSE_UPDATE_AUTO;
+  int num_sms = 148;
+  // device memory
+  uint8_t* state = nullptr;  // RSRA then SLEA
+  uint8_t* sre = nullptr;
+  uint8_t* sle = nullptr;
+  uint32_t* hot_bits = nullptr;
+  uint32_t* list0 = nullptr;
+  uint32_t* list1 = nullptr;
+  uint32_t* cand = nullptr;  // two buffers of cand_cap entries
+  uint32_t* cand_alt = nullptr;
+  float* est = nullptr;
+  uint8_t* flags = nullptr;
+  CloseScratch* scratch = nullptr;
+  uint32_t* query_active2 = nullptr;
+  uint32_t cand_cap = 0;  // max_candidates
+  int sort_passes = 0;    // merge passes after the chunk sort
+  CloseScratch* host_scratch = nullptr;  // pinned
+  sse_stats stats;
+  // staging for sse_update_host
+  uint32_t* stage_dev[2] = {nullptr, nullptr};
+  uint32_t* stage_host[2] = {nullptr, nullptr};
+  cudaEvent_t ev_copied[2] = {nullptr, nullptr};
+  cudaEvent_t ev_used[2] = {nullptr, nullptr};
+  cudaStream_t copy_stream = nullptr;
+};
+
+namespace {
+
+int fail(sse_handle* h, cudaError_t e) {
+  if (e == cudaSuccess) return SSE_OK;
+  if (h && h->sticky == SSE_OK) h->sticky = SSE_ERR_CUDA;
+  return SSE_ERR_CUDA;
+}
+
+#define SSE_CUDA(h, call)                        \
+  do {                                           \
+    cudaError_t e_ = (call);                     \
+    if (e_ != cudaSuccess) return fail((h), e_); \
+  } while (0)
+
+#define SSE_LAUNCHED(h)                          \
+  do {                                           \
+    (h)->launches += 1;                          \
+    cudaError_t e_ = cudaGetLastError();         \
+    if (e_ != cudaSuccess) return fail((h), e_); \
+  } while (0)
+
+KParams make_kparams(const sse_params& p, const sse_derived& d) {
+  KParams k;
+  memset(&k, 0, sizeof(k));
+  uint64_t s = p.seed;
+  const uint32_t nkeys = kLH + p.r2;
+  for (uint32_t x = 0; x < nkeys; ++x) {
+    k.key_a[x] = splitmix64(s) | 1ull;
+    k.key_b[x] = splitmix64(s);
+  }
+  k.r = p.r;
+  k.q = p.q;
+  k.delta = p.delta;
+  k.r2 = p.r2;
+  k.q2 = p.q2;
+  k.delta2 = p.delta2;
+  k.lg_eta2 = d.lg_eta2;
+  k.eta2 = p.eta2;
+  k.k = p.k;
+  k.hot_min = d.hot_min;
+  if (d.tau <= 31) {
+    k.sre_on = 1;
+    k.tau_mask = (1u << d.tau) - 1u;
+  } else if (d.tau == 32) {
+    k.sre_on = 1;
+    k.tau_mask = 0xFFFFFFFFu;
+  } else {
+    k.sre_on = 0;  // LSB(H1) <= 32 < tau: no pair is sampled
+    k.tau_mask = 0xFFFFFFFFu;
+  }
+  k.row_pitch2 = d.row_pitch2;
+  k.row_len2 = d.row_len2;
+  return k;
+}
+
+int grid_for(const sse_handle* h, uint64_t work, int block, int per_sm) {
+  uint64_t g = (work + block - 1) / block;
+  uint64_t cap = (uint64_t)h->num_sms * per_sm;
+  if (g > cap) g = cap;
+  if (g < 1) g = 1;
+  return (int)g;
+}
+
+int launch_update_direct(sse_handle* h, const uint32_t* d_pairs, uint64_t n) {
+  const uint8_t stamp = stamp_of(h->slice);
+  const uint64_t work = (n + 1) / 2;
+  constexpr int kUnroll = 4;
+  const int grid = grid_for(h, (work + kUnroll - 1) / kUnroll, 256, 8);
+  const uint2* pairs = reinterpret_cast<const uint2*>(d_pairs);
+  if (h->p.r2 == 5)
+    k_update_direct<5, kUnroll><<<grid, 256, 0, h->stream>>>(h->kp, pairs, n, h->sre, h->sle, stamp);
+  else
+    k_update_direct<0, kUnroll><<<grid, 256, 0, h->stream>>>(h->kp, pairs, n, h->sre, h->sle, stamp);
+  SSE_LAUNCHED(h);
+  return SSE_OK;
+}
+
+int launch_update(sse_handle* h, const uint32_t* d_pairs, uint64_t n) {
+  return launch_update_direct(h, d_pairs, n);
+}
+
+// Expire/weigh/count pass. mode: bit 0 expire, bit 1 write hot bitmap. Without either
+// bit only the SLEA counts are needed and RSRA is skipped.
+int launch_close_pass(sse_handle* h, uint32_t* active2, uint32_t mode) {
+  const uint64_t n_sre = (uint64_t)h->p.r << h->p.q;
+  const uint32_t sre_blocks = mode ? (uint32_t)((n_sre + kCloseThreads - 1) / kCloseThreads) : 0u;
+  const uint64_t sle_blocks = h->d.sle_bytes / kSleBytesPerBlock;
+  const uint64_t blocks = sre_blocks + sle_blocks;
+  k_close<<<(unsigned)blocks, kCloseThreads, 0, h->stream>>>(h->kp, h->sre, h->sle, h->hot_bits, active2,
+                                                               stamp_of(h->slice), sre_blocks, mode);
+  SSE_LAUNCHED(h);
+  return SSE_OK;
+}
+
+// Sorts the first min(n_cand, cap) candidates; returns the buffer that holds them.
+uint32_t* launch_sort(sse_handle* h) {
+  const uint32_t cap = h->cand_cap;
+  const uint32_t* n_ptr = &h->scratch->n_cand;
+  const unsigned chunks = (cap + kSortChunk - 1) / kSortChunk;
+  k_sort_chunks<<<chunks, 1024, 0, h->stream>>>(h->cand, n_ptr, cap);
+  h->launches += 1 + h->sort_passes;
+  uint32_t* src = h->cand;
+  uint32_t* dst = h->cand_alt;
+  uint32_t width = kSortChunk;
+  for (int pass = 0; pass < h->sort_passes; ++pass) {
+    const int grid = grid_for(h, cap, 256, 4);
+    k_merge_runs<<<grid, 256, 0, h->stream>>>(src, dst, n_ptr, cap, width);
+    std::swap(src, dst);
+    width *= 2;
+  }
+  return src;
+}
+
+}  // namespace
+
+extern "C" {
+
+void sse_params_default(sse_params* p) {
+  if (!p) return;
+  memset(p, 0, sizeof(*p));
+  p->r = 5;
+  p->q = 17;
+  p->delta = 5;
+  p->eta = 8;
+  p->r2 = 5;
+  p->q2 = 17;
+  p->delta2 = 16;
+  p->eta2 = 1u << 14;
+  p->k = 8;
+  p->theta = 1024;
+  p->stamp_bits = 8;
+  p->max_candidates = 1u << 16;
+  p->seed = 0;
+}
+
+int sse_derive(const sse_params* p, sse_derived* d) {
+  if (!p) return SSE_ERR_INVALID_PARAM;
+  sse_params q;
+  sse_derived dd;
+  const int rc = derive_params(*p, q, dd);
+  if (rc == SSE_OK && d) *d = dd;
+  return rc;
+}
+
+const char* sse_strerror(int status) {
+  switch (status) {
+    case SSE_OK: return "ok";
+    case SSE_ERR_INVALID_PARAM: return "invalid parameter or argument";
+    case SSE_ERR_OOM: return "out of memory";
+    case SSE_ERR_CAPACITY: return "result exceeds buffer capacity";
+    case SSE_ERR_MISMATCH: return "estimators differ in parameters or slice";
+    case SSE_ERR_CUDA: return "CUDA runtime error";
+    case SSE_ERR_TIMEOUT: return "device-side wait timed out";
+    case SSE_ERR_STATE: return "call not valid in the current state";
+    default: return "unknown status";
+  }
+}
+
+void sse_destroy(sse_handle* h) {
+  if (!h) return;
+  cudaStreamSynchronize(h->stream);
+  if (h->copy_stream) {
+    cudaStreamSynchronize(h->copy_stream);
+    cudaStreamDestroy(h->copy_stream);
+  }
+  for (int b = 0; b < 2; ++b) {
+    if (h->stage_dev[b]) cudaFree(h->stage_dev[b]);
+    if (h->stage_host[b]) cudaFreeHost(h->stage_host[b]);
+    if (h->ev_copied[b]) cudaEventDestroy(h->ev_copied[b]);
+    if (h->ev_used[b]) cudaEventDestroy(h->ev_used[b]);
+  }
+  cudaFree(h->state);
+  cudaFree(h->hot_bits);
+  cudaFree(h->list0);
+  cudaFree(h->list1);
+  cudaFree(h->cand);
+  cudaFree(h->cand_alt);
+  cudaFree(h->est);
+  cudaFree(h->flags);
+  cudaFree(h->scratch);
+  cudaFree(h->query_active2);
+  if (h->host_scratch) cudaFreeHost(h->host_scratch);
+  delete h;
+}
+
+int sse_init(const sse_params* p, void* cuda_stream, sse_handle** out) {
+  if (!p || !out) return SSE_ERR_INVALID_PARAM;
+  *out = nullptr;
+  sse_params q;
+  sse_derived d;
+  int rc = derive_params(*p, q, d);
+  if (rc != SSE_OK) return rc;
+  sse_handle* h = new (std::nothrow) sse_handle();
+  if (!h) return SSE_ERR_OOM;
+  h->p = q;
+  h->d = d;
+  h->kp = make_kparams(q, d);
+  h->stream = (cudaStream_t)cuda_stream;
+  memset(&h->stats, 0, sizeof(h->stats));
+  if (cudaGetDevice(&h->device) != cudaSuccess ||
+      cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device) != cudaSuccess) {
+    cudaGetLastError();
+    delete h;
+    return SSE_ERR_CUDA;
+  }
+  h->cand_cap = q.max_candidates;
+  uint64_t run = kSortChunk;
+  while (run < h->cand_cap) {
+    run *= 2;
+    h->sort_passes += 1;
+  }
+  const uint64_t state_bytes = d.sre_bytes + d.sle_bytes;
+  const uint64_t list_entries = 1ull << q.q;
+  bool ok = cudaMalloc(&h->state, state_bytes) == cudaSuccess &&
+            cudaMalloc(&h->hot_bits, ((uint64_t)q.r << q.q) / 8) == cudaSuccess &&
+            cudaMalloc(&h->list0, list_entries * 4) == cudaSuccess &&
+            cudaMalloc(&h->list1, list_entries * 4) == cudaSuccess &&
+            cudaMalloc(&h->cand, (uint64_t)h->cand_cap * 4) == cudaSuccess &&
+            cudaMalloc(&h->cand_alt, (uint64_t)h->cand_cap * 4) == cudaSuccess &&
+            cudaMalloc(&h->est, (uint64_t)h->cand_cap * 4) == cudaSuccess &&
+            cudaMalloc(&h->flags, (uint64_t)h->cand_cap) == cudaSuccess &&
+            cudaMalloc(&h->scratch, sizeof(CloseScratch)) == cudaSuccess &&
+            cudaMalloc(&h->query_active2, kMaxRows * 4) == cudaSuccess &&
+            cudaMallocHost(&h->host_scratch, sizeof(CloseScratch)) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    sse_destroy(h);
+    return SSE_ERR_OOM;
+  }
+  h->sre = h->state;
+  h->sle = h->state + d.sre_bytes;
+  if (cudaMemsetAsync(h->state, 0, state_bytes, h->stream) != cudaSuccess ||
+      cudaMemsetAsync(h->hot_bits, 0, ((uint64_t)q.r << q.q) / 8, h->stream) != cudaSuccess ||
+      cudaMemsetAsync(h->scratch, 0, sizeof(CloseScratch), h->stream) != cudaSuccess ||
+      cudaStreamSynchronize(h->stream) != cudaSuccess) {
+    cudaGetLastError();
+    sse_destroy(h);
+    return SSE_ERR_CUDA;
+  }
+  *out = h;
+  return SSE_OK;
+}
+
+uint64_t sse_current_slice(const sse_handle* h) { return h ? h->slice : 0; }
+
+uint64_t sse_kernel_launches(const sse_handle* h) { return h ? h->launches : 0; }
+
+int sse_set_update_mode(sse_handle* h, int mode) {
+  if (!h || mode < SSE_UPDATE_AUTO || mode > SSE_UPDATE_DIRECT) return SSE_ERR_INVALID_PARAM;
+  h->update_mode = mode;
+  return SSE_OK;
+}
+
+int sse_update(sse_handle* h, const uint32_t* d_pairs, uint64_t n_pairs) {
+  if (!h) return SSE_ERR_INVALID_PARAM;
+  if (h->sticky) return h->sticky;
+  if (n_pairs == 0) return SSE_OK;
+  if (!d_pairs || (reinterpret_cast<uintptr_t>(d_pairs) & 7u)) return SSE_ERR_INVALID_PARAM;
+  return launch_update(h, d_pairs, n_pairs);
+}
+
+int sse_update_host(sse_handle* h, const uint32_t* h_pairs, uint64_t n_pairs) {
+  if (!h) return SSE_ERR_INVALID_PARAM;
+  if (h->sticky) return h->sticky;
+  if (n_pairs == 0) return SSE_OK;
+  if (!h_pairs) return SSE_ERR_INVALID_PARAM;
+  constexpr uint64_t kChunk = 1ull << 22;  // pairs per staging buffer (32 MiB)
+  if (!h->copy_stream) {
+    bool ok = cudaStreamCreateWithFlags(&h->copy_stream, cudaStreamNonBlocking) == cudaSuccess;
+    for (int b = 0; b < 2 && ok; ++b) {
+      ok = cudaMalloc(&h->stage_dev[b], kChunk * 8) == cudaSuccess &&
+           cudaEventCreateWithFlags(&h->ev_copied[b], cudaEventDisableTiming) == cudaSuccess &&
+           cudaEventCreateWithFlags(&h->ev_used[b], cudaEventDisableTiming) == cudaSuccess;
+    }
+    if (!ok) {
+      cudaGetLastError();
+      return SSE_ERR_OOM;
+    }
+  }
+  cudaPointerAttributes attr;
+  const bool pinned = cudaPointerGetAttributes(&attr, h_pairs) == cudaSuccess && attr.type == cudaMemoryTypeHost;
+  cudaGetLastError();
+  if (!pinned && !h->stage_host[0]) {
+    for (int b = 0; b < 2; ++b)
+      if (cudaMallocHost(&h->stage_host[b], kChunk * 8) != cudaSuccess) {
+        cudaGetLastError();
+        return SSE_ERR_OOM;
+      }
+  }
+  uint64_t done = 0;
+  int b = 0;
+  while (done < n_pairs) {
+    const uint64_t m = std::min<uint64_t>(kChunk, n_pairs - done);
+    SSE_CUDA(h, cudaEventSynchronize(h->ev_used[b]));  // buffer b is free again
+    const void* src = h_pairs + 2 * done;
+    if (!pinned) {
+      memcpy(h->stage_host[b], src, m * 8);
+      src = h->stage_host[b];
+    }
+    SSE_CUDA(h, cudaMemcpyAsync(h->stage_dev[b], src, m * 8, cudaMemcpyHostToDevice, h->copy_stream));
+    SSE_CUDA(h, cudaEventRecord(h->ev_copied[b], h->copy_stream));
+    SSE_CUDA(h, cudaStreamWaitEvent(h->stream, h->ev_copied[b], 0));
+    int rc = launch_update(h, h->stage_dev[b], m);
+    if (rc) return rc;
+    SSE_CUDA(h, cudaEventRecord(h->ev_used[b], h->stream));
+    done += m;
+    b ^= 1;
+  }
+  // the caller's buffer may be reused once every copy out of it has finished
+  SSE_CUDA(h, cudaEventSynchronize(h->ev_copied[0]));
+  SSE_CUDA(h, cudaEventSynchronize(h->ev_copied[1]));
+  return SSE_OK;
+}
+
+int sse_advance(sse_handle* h) {
+  if (!h) return SSE_ERR_INVALID_PARAM;
+  if (h->sticky) return h->sticky;
+  SSE_CUDA(h, cudaMemsetAsync(h->scratch, 0, sizeof(CloseScratch), h->stream));
+  int rc = launch_close_pass(h, h->scratch->active2, 3u);
+  if (rc) return rc;
+  h->stats.slice = h->slice;
+  h->slice += 1;
+  return SSE_OK;
+}
+
+int sse_close_slice(sse_handle* h, sse_report* out) {
+  if (!h) return SSE_ERR_INVALID_PARAM;
+  if (h->sticky) return h->sticky;
+  CloseScratch* sc = h->scratch;
+  SSE_CUDA(h, cudaMemsetAsync(sc, 0, sizeof(CloseScratch), h->stream));
+  int rc = launch_close_pass(h, sc->active2, 3u);
+  if (rc) return rc;
+  {
+    const uint64_t words = ((uint64_t)h->p.r << h->p.q) >> 5;
+    const int grid = grid_for(h, words, 256, 4);
+    k_hot_lists<<<grid, 256, 0, h->stream>>>(h->hot_bits, h->p.r, h->p.q, sc->hot, h->list0, h->list1, sc->n_list);
+    SSE_LAUNCHED(h);
+  }
+  k_join<<<h->num_sms * 8, 256, 0, h->stream>>>(h->kp, h->hot_bits, h->list0, h->list1, sc->n_list, h->cand,
+                                                &sc->n_cand, h->cand_cap, &sc->overflow);
+  SSE_LAUNCHED(h);
+  uint32_t* sorted = launch_sort(h);
+  SSE_CUDA(h, cudaGetLastError());
+  {
+    const int grid = grid_for(h, h->cand_cap, kEstWarps, 8);
+    k_estimate<<<grid, kEstWarps * 32, 0, h->stream>>>(h->kp, h->sle, sorted, &sc->n_cand, h->cand_cap, sc->active2,
+                                                        h->d.w_theta, stamp_of(h->slice), h->est, h->flags, nullptr,
+                                                        nullptr, nullptr, &sc->n_super);
+    SSE_LAUNCHED(h);
+  }
+  SSE_CUDA(h, cudaMemcpyAsync(h->host_scratch, sc, sizeof(CloseScratch), cudaMemcpyDeviceToHost, h->stream));
+  SSE_CUDA(h, cudaStreamSynchronize(h->stream));
+  const CloseScratch& hs = *h->host_scratch;
+  const uint32_t n_found = hs.n_cand;
+  const uint32_t n_kept = std::min(n_found, h->cand_cap);
+  int status = SSE_OK;
+  if (n_found > h->cand_cap) status = SSE_ERR_CAPACITY;
+  h->stats.slice = h->slice;
+  for (int i = 0; i < kMaxRows; ++i) {
+    h->stats.hot[i] = i < (int)h->p.r ? hs.hot[i] : 0;
+    h->stats.active2[i] = i < (int)h->p.r2 ? hs.active2[i] : 0;
+  }
+  h->stats.join_pairs = (uint64_t)hs.n_list[0] * hs.n_list[1];
+  h->stats.n_candidates = n_found;
+  h->stats.n_super = hs.n_super;
+  if (out) {
+    out->slice = h->slice;
+    out->n_candidates = n_found;
+    out->n_super = hs.n_super;
+    const uint32_t n_copy = std::min(n_kept, out->cap);
+    out->truncated = (n_found > n_copy) ? 1u : 0u;
+    if (n_kept > out->cap) status = SSE_ERR_CAPACITY;
+    if (n_copy) {
+      if (out->hosts)
+        SSE_CUDA(h, cudaMemcpyAsync(out->hosts, sorted, (uint64_t)n_copy * 4, cudaMemcpyDeviceToHost, h->stream));
+      if (out->est)
+        SSE_CUDA(h, cudaMemcpyAsync(out->est, h->est, (uint64_t)n_copy * 4, cudaMemcpyDeviceToHost, h->stream));
+      if (out->flags)
+        SSE_CUDA(h, cudaMemcpyAsync(out->flags, h->flags, n_copy, cudaMemcpyDeviceToHost, h->stream));
+      SSE_CUDA(h, cudaStreamSynchronize(h->stream));
+    }
+  }
+  h->slice += 1;
+  return status;
+}
+
+int sse_merge(sse_handle* dst, const sse_handle* const* srcs, int n) {
+  if (!dst || !srcs || n < 1 || n > kMaxMergeSources) return SSE_ERR_INVALID_PARAM;
+  if (dst->sticky) return dst->sticky;
+  MergeSources sre_src, sle_src;
+  memset(&sre_src, 0, sizeof(sre_src));
+  memset(&sle_src, 0, sizeof(sle_src));
+  for (int j = 0; j < n; ++j) {
+    const sse_handle* s = srcs[j];
+    if (!s || s == dst) return SSE_ERR_INVALID_PARAM;
+    if (memcmp(&s->p, &dst->p, sizeof(sse_params)) != 0 || s->slice != dst->slice || s->device != dst->device)
+      return SSE_ERR_MISMATCH;
+    sre_src.ptr[j] = s->sre;
+    sle_src.ptr[j] = s->sle;
+  }
+  const uint32_t cs = stamp_of(dst->slice);
+  const uint64_t n16_sre = dst->d.sre_bytes / 16, n16_sle = dst->d.sle_bytes / 16;
+  k_merge<<<grid_for(dst, n16_sre, 256, 8), 256, 0, dst->stream>>>(dst->sre, sre_src, n, n16_sre, cs);
+  SSE_LAUNCHED(dst);
+  k_merge<<<grid_for(dst, n16_sle, 256, 8), 256, 0, dst->stream>>>(dst->sle, sle_src, n, n16_sle, cs);
+  SSE_LAUNCHED(dst);
+  return SSE_OK;
+}
+
+int sse_query(sse_handle* h, const uint32_t* d_hosts, uint32_t n, float* d_est, uint8_t* d_flags, uint32_t* d_hist) {
+  if (!h) return SSE_ERR_INVALID_PARAM;
+  if (h->sticky) return h->sticky;
+  if (n == 0) return SSE_OK;
+  if (!d_hosts || !d_est) return SSE_ERR_INVALID_PARAM;
+  SSE_CUDA(h, cudaMemsetAsync(h->query_active2, 0, kMaxRows * 4, h->stream));
+  int rc = launch_close_pass(h, h->query_active2, 0u);  // count only
+  if (rc) return rc;
+  const int grid = grid_for(h, n, kEstWarps, 8);
+  k_estimate<<<grid, kEstWarps * 32, 0, h->stream>>>(h->kp, h->sle, d_hosts, nullptr, n, h->query_active2,
+                                                      h->d.w_theta, stamp_of(h->slice), d_est, d_flags, nullptr,
+                                                      nullptr, d_hist, nullptr);
+  SSE_LAUNCHED(h);
+  return SSE_OK;
+}
+
+int sse_get_stats(sse_handle* h, sse_stats* out) {
+  if (!h || !out) return SSE_ERR_INVALID_PARAM;
+  SSE_CUDA(h, cudaStreamSynchronize(h->stream));
+  *out = h->stats;
+  return SSE_OK;
+}
+
+int sse_get_hot_bitmap(sse_handle* h, uint32_t* h_bits, size_t cap_bytes) {
+  if (!h || !h_bits) return SSE_ERR_INVALID_PARAM;
+  const size_t bytes = ((size_t)h->p.r << h->p.q) / 8;
+  if (cap_bytes < bytes) return SSE_ERR_INVALID_PARAM;
+  SSE_CUDA(h, cudaMemcpyAsync(h_bits, h->hot_bits, bytes, cudaMemcpyDeviceToHost, h->stream));
+  SSE_CUDA(h, cudaStreamSynchronize(h->stream));
+  return SSE_OK;
+}
+
+int sse_read_stamps(sse_handle* h, uint8_t* h_sre, size_t sre_cap, uint8_t* h_sle, size_t sle_cap) {
+  if (!h) return SSE_ERR_INVALID_PARAM;
+  if ((h_sre && sre_cap < h->d.sre_bytes) || (h_sle && sle_cap < h->d.sle_bytes)) return SSE_ERR_CAPACITY;
+  if (h_sre) SSE_CUDA(h, cudaMemcpyAsync(h_sre, h->sre, h->d.sre_bytes, cudaMemcpyDeviceToHost, h->stream));
+  if (h_sle) SSE_CUDA(h, cudaMemcpyAsync(h_sle, h->sle, h->d.sle_bytes, cudaMemcpyDeviceToHost, h->stream));
+  SSE_CUDA(h, cudaStreamSynchronize(h->stream));
+  return SSE_OK;
+}
+
+namespace {
+struct StateHeader {
+  uint64_t magic;
+  uint32_t version, pad;
+  sse_params p;
+  uint64_t slice;
+  uint64_t sre_bytes, sle_bytes;
+};
+constexpr uint64_t kMagic = 0x3130455453534553ull;  // "SESSTE01"
+}  // namespace
+
+int sse_export_state(sse_handle* h, void* h_buf, size_t cap, size_t* used) {
+  if (!h || !used) return SSE_ERR_INVALID_PARAM;
+  const size_t total = sizeof(StateHeader) + h->d.sre_bytes + h->d.sle_bytes;
+  *used = total;
+  if (!h_buf) return SSE_OK;
+  if (cap < total) return SSE_ERR_CAPACITY;
+  StateHeader hd;
+  memset(&hd, 0, sizeof(hd));
+  hd.magic = kMagic;
+  hd.version = SSE_VERSION;
+  hd.p = h->p;
+  hd.slice = h->slice;
+  hd.sre_bytes = h->d.sre_bytes;
+  hd.sle_bytes = h->d.sle_bytes;
+  memcpy(h_buf, &hd, sizeof(hd));
+  uint8_t* body = static_cast<uint8_t*>(h_buf) + sizeof(hd);
+  SSE_CUDA(h, cudaMemcpyAsync(body, h->state, h->d.sre_bytes + h->d.sle_bytes, cudaMemcpyDeviceToHost, h->stream));
+  SSE_CUDA(h, cudaStreamSynchronize(h->stream));
+  return SSE_OK;
+}
+
+int sse_import_state(sse_handle* h, const void* h_buf, size_t n) {
+  if (!h || !h_buf || n < sizeof(StateHeader)) return SSE_ERR_INVALID_PARAM;
+  StateHeader hd;
+  memcpy(&hd, h_buf, sizeof(hd));
+  if (hd.magic != kMagic || hd.version != SSE_VERSION) return SSE_ERR_INVALID_PARAM;
+  if (memcmp(&hd.p, &h->p, sizeof(sse_params)) != 0 || hd.sre_bytes != h->d.sre_bytes ||
+      hd.sle_bytes != h->d.sle_bytes)
+    return SSE_ERR_MISMATCH;
+  if (n < sizeof(hd) + hd.sre_bytes + hd.sle_bytes) return SSE_ERR_INVALID_PARAM;
+  const uint8_t* body = static_cast<const uint8_t*>(h_buf) + sizeof(hd);
+  SSE_CUDA(h, cudaMemcpyAsync(h->state, body, hd.sre_bytes + hd.sle_bytes, cudaMemcpyHostToDevice, h->stream));
+  SSE_CUDA(h, cudaStreamSynchronize(h->stream));
+  h->slice = hd.slice;
+  return SSE_OK;
+}
+
+int sse_sync(sse_handle* h) {
+  if (!h) return SSE_ERR_INVALID_PARAM;
+  if (h->sticky) return h->sticky;
+  SSE_CUDA(h, cudaStreamSynchronize(h->stream));
+  SSE_CUDA(h, cudaGetLastError());
+  return SSE_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,58 @@
+// Internal definitions shared by the kernels and the host runtime of libsse.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "sse.h"
+
+namespace sse {
+
+constexpr int kMaxRows = 16;            // r and r' are at most 16
+constexpr int kEta = 8;                 // cells per SRE (one 64-bit word)
+constexpr uint32_t kPitchAlign = 4096;  // SLEA row pitch: whole close-kernel blocks per row
+constexpr int kSortChunk = 4096;        // elements sorted per CTA before merge passes
+constexpr int kMaxMergeSources = 64;
+
+// Key order: 0 = H1, 1 = H2, 2 = H3, 3 = RHFG[0], 4 + i = LH_i.
+enum { kH1 = 0, kH2 = 1, kH3 = 2, kR0 = 3, kLH = 4 };
+
+// Everything a kernel needs to evaluate the method's hash functions and addresses.
+struct KParams {
+  uint64_t key_a[kLH + kMaxRows];
+  uint64_t key_b[kLH + kMaxRows];
+  uint32_t r, q, delta, r2;
+  uint32_t q2, delta2, lg_eta2, eta2;
+  uint32_t k, tau_mask, sre_on, hot_min;
+  uint64_t row_pitch2;  // bytes between SLEA rows
+  uint64_t row_len2;    // cells per SLEA row
+};
+
+// Multiply-add-shift hash: the top m bits (0 <= m <= 32) of (a*x + b) mod 2^64.
+__host__ __device__ __forceinline__ uint32_t mas_top(uint64_t a, uint64_t b, uint32_t x, uint32_t m) {
+  uint64_t v = a * (uint64_t)x + b;
+  return (uint32_t)((v >> 32) >> (32 - m));
+}
+
+// Cyclic stamp arithmetic: slice t has stamp 1 + (t mod 255); 0 marks an unset cell.
+__host__ __device__ __forceinline__ uint8_t stamp_of(uint64_t slice) { return (uint8_t)(1 + slice % 255); }
+
+// Age in slices of stamp s seen from current stamp cs (both 1..255), or 255 when unset.
+__host__ __device__ __forceinline__ uint32_t stamp_age(uint32_t s, uint32_t cs) {
+  if (s == 0) return 255;
+  return (cs + 255 - s) % 255;
+}
+
+// Scratch counters of one close, zeroed before it (one cudaMemsetAsync).
+struct CloseScratch {
+  uint32_t active2[kMaxRows];  // active cells of each SLEA row
+  uint32_t hot[kMaxRows];      // hot SREs of each RSRA row
+  uint32_t n_list[2];          // entries of the hot lists of rows 0 and 1
+  uint32_t n_cand;             // candidate hosts found (may exceed capacity)
+  uint32_t n_super;            // candidates flagged super
+  uint32_t overflow;           // nonzero when a buffer was too small
+  uint32_t error;              // nonzero when a device-side check failed
+  uint32_t pad[2];
+};
+
+}  // namespace sse

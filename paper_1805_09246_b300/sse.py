@@ -1,0 +1,313 @@
+"""Python binding of libsse (include/sse.h): argument marshalling only.
+
+Every computation runs in the CUDA library. PyTorch supplies device memory (tensors
+whose ``data_ptr()`` is passed through) and the CUDA stream. Using this module on a
+machine without the built library or without a CUDA device raises: there is no CPU
+fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libsse.so")
+
+SSE_OK = 0
+FLAG_SUPER = 1
+FLAG_SATURATED = 2
+ERR_CAPACITY = -3
+UPDATE_AUTO, UPDATE_DIRECT, UPDATE_TILED = 0, 1, 2
+
+
+class SSEError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        super().__init__(f"{what}: {_strerror(code)} ({code})")
+        self.code = code
+
+
+class _Params(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_uint32) for n in
+                ("r", "q", "delta", "eta", "r2", "q2", "delta2", "eta2", "k", "theta",
+                 "stamp_bits", "max_candidates")] + [("seed", ctypes.c_uint64)]
+
+
+class _Derived(ctypes.Structure):
+    _fields_ = [("delta", ctypes.c_uint32), ("tau", ctypes.c_uint32), ("hot_min", ctypes.c_uint32),
+                ("lg_eta2", ctypes.c_uint32), ("row_len2", ctypes.c_uint64), ("row_pitch2", ctypes.c_uint64),
+                ("sre_bytes", ctypes.c_uint64), ("sle_bytes", ctypes.c_uint64), ("w_theta", ctypes.c_double)]
+
+
+class _Report(ctypes.Structure):
+    _fields_ = [("slice", ctypes.c_uint64), ("n_candidates", ctypes.c_uint32), ("n_super", ctypes.c_uint32),
+                ("cap", ctypes.c_uint32), ("truncated", ctypes.c_uint32), ("hosts", ctypes.c_void_p),
+                ("est", ctypes.c_void_p), ("flags", ctypes.c_void_p)]
+
+
+class _Stats(ctypes.Structure):
+    _fields_ = [("slice", ctypes.c_uint64), ("hot", ctypes.c_uint32 * 16), ("active2", ctypes.c_uint32 * 16),
+                ("join_pairs", ctypes.c_uint64), ("n_candidates", ctypes.c_uint32), ("n_super", ctypes.c_uint32)]
+
+
+@dataclass
+class Params:
+    """Symbols of the paper; defaults are the 8-slice small trace configuration."""
+    r: int = 5
+    q: int = 14
+    delta: int = 0
+    eta: int = 8
+    r2: int = 5
+    q2: int = 12
+    delta2: int = 16
+    eta2: int = 1024
+    k: int = 4
+    theta: int = 1024
+    stamp_bits: int = 8
+    max_candidates: int = 1 << 16
+    seed: int = 0
+
+    def to_c(self) -> _Params:
+        return _Params(self.r, self.q, self.delta, self.eta, self.r2, self.q2, self.delta2, self.eta2,
+                       self.k, self.theta, self.stamp_bits, self.max_candidates, self.seed)
+
+
+def core_link_params(k: int = 8, seed: int = 0) -> Params:
+    """Core-link scale: SRE rows of 2^20, SLEA 2^16 SLEs of 2^12 cells, window 8."""
+    return Params(q=20, q2=16, eta2=4096, k=k, seed=seed)
+
+
+def paper_params(k: int = 8) -> Params:
+    """The parameter set of the paper's experiments (Section 5)."""
+    p = _Params()
+    lib().sse_params_default(ctypes.byref(p))
+    return Params(r=p.r, q=p.q, delta=p.delta, eta=p.eta, r2=p.r2, q2=p.q2, delta2=p.delta2, eta2=p.eta2,
+                  k=k, theta=p.theta, stamp_bits=p.stamp_bits, max_candidates=p.max_candidates, seed=p.seed)
+
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """The loaded libsse.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"libsse.so is not built ({LIB_PATH}); run paper_1805_09246_b300/build.py")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, u32, u64, i32 = ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int
+        sig = {
+            "sse_params_default": (None, [vp]),
+            "sse_derive": (i32, [vp, vp]),
+            "sse_init": (i32, [vp, vp, ctypes.POINTER(vp)]),
+            "sse_destroy": (None, [vp]),
+            "sse_update": (i32, [vp, vp, u64]),
+            "sse_update_host": (i32, [vp, vp, u64]),
+            "sse_set_update_mode": (i32, [vp, i32]),
+            "sse_close_slice": (i32, [vp, vp]),
+            "sse_advance": (i32, [vp]),
+            "sse_merge": (i32, [vp, ctypes.POINTER(vp), i32]),
+            "sse_query": (i32, [vp, vp, u32, vp, vp, vp]),
+            "sse_get_stats": (i32, [vp, vp]),
+            "sse_get_hot_bitmap": (i32, [vp, vp, ctypes.c_size_t]),
+            "sse_export_state": (i32, [vp, vp, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)]),
+            "sse_import_state": (i32, [vp, vp, ctypes.c_size_t]),
+            "sse_read_stamps": (i32, [vp, vp, ctypes.c_size_t, vp, ctypes.c_size_t]),
+            "sse_current_slice": (u64, [vp]),
+            "sse_kernel_launches": (u64, [vp]),
+            "sse_sync": (i32, [vp]),
+            "sse_strerror": (ctypes.c_char_p, [i32]),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _strerror(code: int) -> str:
+    try:
+        return lib().sse_strerror(code).decode()
+    except Exception:  # library missing: still produce a message
+        return "error"
+
+
+def _check(code: int, what: str) -> int:
+    if code != SSE_OK:
+        raise SSEError(code, what)
+    return code
+
+
+def derive(p: Params) -> dict:
+    d = _Derived()
+    _check(lib().sse_derive(ctypes.byref(p.to_c()), ctypes.byref(d)), "sse_derive")
+    return {name: getattr(d, name) for name, _ in _Derived._fields_}
+
+
+@dataclass
+class Report:
+    slice: int
+    n_candidates: int
+    n_super: int
+    truncated: bool
+    hosts: np.ndarray
+    est: np.ndarray
+    flags: np.ndarray
+    status: int = SSE_OK
+
+    @property
+    def super_points(self) -> np.ndarray:
+        return self.hosts[(self.flags & FLAG_SUPER) != 0]
+
+
+def _torch():
+    import torch
+    if not torch.cuda.is_available():
+        raise RuntimeError("libsse needs a CUDA device; no CPU fallback exists")
+    return torch
+
+
+def _dev_ptr(t, dtype_bytes: int | None = None) -> int:
+    torch = _torch()
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("tensor must be contiguous")
+    if dtype_bytes is not None and t.element_size() != dtype_bytes:
+        raise TypeError(f"expected {dtype_bytes}-byte elements")
+    return t.data_ptr()
+
+
+class Estimator:
+    """One router's estimator (RSRA + SLEA) resident on the current CUDA device."""
+
+    def __init__(self, params: Params | None = None, stream=None):
+        torch = _torch()
+        self.params = params or Params()
+        self._lib = lib()
+        self.derived = derive(self.params)
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self._h = ctypes.c_void_p()
+        _check(self._lib.sse_init(ctypes.byref(self.params.to_c()), ctypes.c_void_p(self.stream.cuda_stream),
+                                  ctypes.byref(self._h)), "sse_init")
+
+    def close(self) -> None:
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._lib.sse_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def handle(self) -> ctypes.c_void_p:
+        return self._h
+
+    @property
+    def slice(self) -> int:
+        return int(self._lib.sse_current_slice(self._h))
+
+    @property
+    def kernel_launches(self) -> int:
+        return int(self._lib.sse_kernel_launches(self._h))
+
+    def set_update_mode(self, mode: int) -> None:
+        _check(self._lib.sse_set_update_mode(self._h, mode), "sse_set_update_mode")
+
+    def update(self, pairs) -> None:
+        """Scan the pairs of a CUDA tensor of shape (n, 2), 32-bit elements {src, dst}."""
+        n = pairs.numel() // 2
+        if n == 0:
+            return
+        _check(self._lib.sse_update(self._h, ctypes.c_void_p(_dev_ptr(pairs, 4)), n), "sse_update")
+
+    def update_host(self, pairs) -> None:
+        """Scan pairs held in host memory (numpy array or CPU tensor, (n, 2) 32-bit)."""
+        if isinstance(pairs, np.ndarray):
+            a = np.ascontiguousarray(pairs).view(np.uint32).reshape(-1)
+            ptr, n = a.ctypes.data, a.size // 2
+        else:
+            if pairs.is_cuda or not pairs.is_contiguous() or pairs.element_size() != 4:
+                raise TypeError("expected a contiguous CPU tensor of 32-bit elements")
+            ptr, n = pairs.data_ptr(), pairs.numel() // 2
+        if n:
+            _check(self._lib.sse_update_host(self._h, ctypes.c_void_p(ptr), n), "sse_update_host")
+
+    def close_slice(self, cap: int | None = None, raise_on_capacity: bool = True) -> Report:
+        """Detect the sliding super points of the window ending at the current slice."""
+        cap = self.params.max_candidates if cap is None else cap
+        hosts = np.zeros(cap, np.uint32)
+        est = np.zeros(cap, np.float32)
+        flags = np.zeros(cap, np.uint8)
+        rep = _Report(0, 0, 0, cap, 0, hosts.ctypes.data, est.ctypes.data, flags.ctypes.data)
+        rc = self._lib.sse_close_slice(self._h, ctypes.byref(rep))
+        if rc != SSE_OK and (rc != ERR_CAPACITY or raise_on_capacity):
+            raise SSEError(rc, "sse_close_slice")
+        m = min(rep.n_candidates, cap, self.params.max_candidates)
+        return Report(slice=rep.slice, n_candidates=rep.n_candidates, n_super=rep.n_super,
+                      truncated=bool(rep.truncated), hosts=hosts[:m].copy(), est=est[:m].copy(),
+                      flags=flags[:m].copy(), status=rc)
+
+    def advance(self) -> None:
+        _check(self._lib.sse_advance(self._h), "sse_advance")
+
+    def merge(self, others: list["Estimator"]) -> None:
+        arr = (ctypes.c_void_p * len(others))(*[o._h.value for o in others])
+        _check(self._lib.sse_merge(self._h, arr, len(others)), "sse_merge")
+
+    def query(self, hosts, hist: bool = False):
+        """Estimates (float32), flags (uint8) and optionally per-distance histograms
+        (32-bit, [n, k]) of the hosts in a CUDA tensor of 32-bit addresses."""
+        torch = _torch()
+        n = hosts.numel()
+        dev = hosts.device
+        est = torch.empty(n, dtype=torch.float32, device=dev)
+        flags = torch.empty(n, dtype=torch.uint8, device=dev)
+        hh = torch.empty((n, self.params.k), dtype=torch.int32, device=dev) if hist else None
+        _check(self._lib.sse_query(self._h, ctypes.c_void_p(_dev_ptr(hosts, 4)), n, ctypes.c_void_p(est.data_ptr()),
+                                   ctypes.c_void_p(flags.data_ptr()),
+                                   ctypes.c_void_p(hh.data_ptr() if hist else 0)), "sse_query")
+        return (est, flags, hh) if hist else (est, flags)
+
+    def stats(self) -> dict:
+        s = _Stats()
+        _check(self._lib.sse_get_stats(self._h, ctypes.byref(s)), "sse_get_stats")
+        return dict(slice=s.slice, hot=list(s.hot)[: self.params.r], active2=list(s.active2)[: self.params.r2],
+                    join_pairs=s.join_pairs, n_candidates=s.n_candidates, n_super=s.n_super)
+
+    def hot_bitmap(self) -> np.ndarray:
+        """Hot flags of the last close as uint8 [r, 2^q]."""
+        p = self.params
+        words = np.zeros(((p.r << p.q) + 31) // 32, np.uint32)
+        _check(self._lib.sse_get_hot_bitmap(self._h, ctypes.c_void_p(words.ctypes.data), words.nbytes),
+               "sse_get_hot_bitmap")
+        bits = np.unpackbits(words.view(np.uint8), bitorder="little")
+        return bits[: p.r << p.q].reshape(p.r, 1 << p.q)
+
+    def read_stamps(self) -> tuple[np.ndarray, np.ndarray]:
+        """Raw stamps: RSRA uint8 [r, 2^q, 8] and SLEA uint8 [r', row_len2]."""
+        p, d = self.params, self.derived
+        sre = np.zeros((p.r, 1 << p.q, p.eta), np.uint8)
+        sle = np.zeros((p.r2, d["row_pitch2"]), np.uint8)
+        _check(self._lib.sse_read_stamps(self._h, ctypes.c_void_p(sre.ctypes.data), sre.nbytes,
+                                         ctypes.c_void_p(sle.ctypes.data), sle.nbytes), "sse_read_stamps")
+        return sre, sle[:, : d["row_len2"]]
+
+    def export_state(self) -> bytes:
+        used = ctypes.c_size_t(0)
+        _check(self._lib.sse_export_state(self._h, None, 0, ctypes.byref(used)), "sse_export_state")
+        buf = ctypes.create_string_buffer(used.value)
+        _check(self._lib.sse_export_state(self._h, buf, used.value, ctypes.byref(used)), "sse_export_state")
+        return buf.raw
+
+    def import_state(self, blob: bytes) -> None:
+        _check(self._lib.sse_import_state(self._h, blob, len(blob)), "sse_import_state")
+
+    def sync(self) -> None:
+        _check(self._lib.sse_sync(self._h), "sse_sync")

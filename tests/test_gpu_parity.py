@@ -1,0 +1,313 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle on the same inputs.
+
+Bar: bit-exact estimator state (canonical ages), hot SREs, active-cell counts, candidate
+and super point sets and flags; estimates (float32) within 1e-6 relative of the oracle's
+FP64 values.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1805_09246_b300 import synth
+from tests import helpers
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+EST_RTOL = 1e-6
+
+
+def sse():
+    from paper_1805_09246_b300 import sse as mod
+    return mod
+
+
+def oracle_params(p):
+    return oracle.Params(r=p.r, q=p.q, delta=p.delta, eta=p.eta, r2=p.r2, q2=p.q2, delta2=p.delta2,
+                         eta2=p.eta2, k=p.k, theta=p.theta, seed=p.seed)
+
+
+def compare_state(est, orc, p, slice_index):
+    sre_s, sle_s = est.read_stamps()
+    o_sre, o_sle = orc.canonical()
+    g_sre = helpers.canonical_from_stamps(sre_s, slice_index, p.k)
+    g_sle = helpers.canonical_from_stamps(sle_s, slice_index, p.k)
+    assert np.array_equal(g_sre, o_sre), "RSRA state differs"
+    assert np.array_equal(g_sle, o_sle), "SLEA state differs"
+
+
+def close_enough(got, ref):
+    got = np.asarray(got, np.float64)
+    return np.all(np.abs(got - ref) <= EST_RTOL * np.maximum(np.abs(ref), 1e-30))
+
+
+def compare_report(rep, det):
+    assert np.array_equal(rep.hosts, det["hosts"]), "candidate sets differ"
+    assert np.array_equal(rep.flags, det["flags"]), "flags differ"
+    assert close_enough(rep.est, det["est"])
+    assert rep.n_super == int((det["flags"] & oracle.SUPER).astype(bool).sum())
+
+
+def run_both(p, slices, mode=None, check_state=True):
+    S = sse()
+    est = S.Estimator(p)
+    if mode is not None:
+        est.set_update_mode(mode)
+    orc = oracle.Oracle(oracle_params(p))
+    reports = []
+    for t, pairs in enumerate(slices):
+        if t:
+            orc.advance()
+        est.update(helpers.to_device(pairs))
+        orc.scan(pairs)
+        rep = est.close_slice()
+        det = orc.detect()
+        if check_state:
+            compare_state(est, orc, p, t)
+            assert np.array_equal(est.hot_bitmap(), orc.hot())
+            st = est.stats()
+            assert st["active2"] == orc.row_counts().tolist()
+        compare_report(rep, det)
+        reports.append(rep)
+    return est, orc, reports
+
+
+def update_modes():
+    S = sse()
+    return [S.UPDATE_DIRECT, S.UPDATE_AUTO]
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_small_trace_end_to_end(mode):
+    """The 8-slice, 2^17-pair trace: every slice's state, hot SREs, counts and report."""
+    S = sse()
+    p = S.Params()
+    tr = synth.Traffic(synth.small_trace())
+    _, _, reports = run_both(p, [tr.slice(0, t) for t in range(8)], mode=mode)
+    assert sum(r.n_super for r in reports) > 100  # the planted super points are found
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 31, 1000, 65537, 300001])
+def test_ragged_sizes_and_tiles(n):
+    S = sse()
+    p = S.Params(q=12, delta=7, q2=8, eta2=256, k=2, theta=16, seed=n)
+    rng = np.random.default_rng(n)
+    src = rng.integers(0, 2**32, 97, dtype=np.uint64).astype(np.uint32)
+    pairs = np.stack([src[rng.integers(0, 97, n)], rng.integers(0, 2**32, n, dtype=np.uint64).astype(np.uint32)], 1)
+    run_both(p, [pairs, pairs[: n // 2 + 1], pairs[::-1].copy()])
+
+
+def test_misaligned_device_pointer():
+    """Pairs starting 8 bytes past a 16-byte boundary (a peeled first pair)."""
+    S = sse()
+    p = S.Params(seed=3)
+    rng = np.random.default_rng(3)
+    pairs = rng.integers(0, 2**32, (10001, 2), dtype=np.uint64).astype(np.uint32)
+    pairs[:, 0] = pairs[:, 0] % 50
+    buf = helpers.to_device(np.concatenate([np.zeros((1, 2), np.uint32), pairs]))
+    est = S.Estimator(p)
+    est.update(buf[1:])
+    orc = oracle.Oracle(oracle_params(p))
+    orc.scan(pairs)
+    compare_state(est, orc, p, 0)
+
+
+def test_window_wraps_stamp_cycle():
+    """More than 255 slices: stamps reuse values, expiry keeps the window exact."""
+    S = sse()
+    p = S.Params(q=10, delta=8, q2=6, eta2=64, delta2=8, k=3, theta=8, seed=9)
+    rng = np.random.default_rng(9)
+    est = S.Estimator(p)
+    orc = oracle.Oracle(oracle_params(p))
+    for t in range(300):
+        if t:
+            orc.advance()
+        pairs = rng.integers(0, 2**32, (200, 2), dtype=np.uint64).astype(np.uint32)
+        pairs[:, 0] %= 7
+        est.update(helpers.to_device(pairs))
+        orc.scan(pairs)
+        if t % 37 == 0 or t >= 297:
+            rep = est.close_slice()
+            compare_state(est, orc, p, t)
+            compare_report(rep, orc.detect())
+        else:
+            est.advance()
+    assert est.slice == 300
+
+
+def test_k1_discrete_window():
+    S = sse()
+    p = S.Params(k=1, theta=256, seed=11)
+    tr = synth.Traffic(synth.small_trace(seed=11))
+    run_both(p, [tr.slice(0, t) for t in range(3)])
+
+
+def test_query_matches_oracle_estimates():
+    S = sse()
+    p = S.Params(k=4, seed=12)
+    tr = synth.Traffic(synth.small_trace(seed=12))
+    est = S.Estimator(p)
+    orc = oracle.Oracle(oracle_params(p))
+    for t in range(3):
+        if t:
+            orc.advance()
+        pairs = tr.slice(0, t)
+        est.update(helpers.to_device(pairs))
+        orc.scan(pairs)
+        if t < 2:
+            est.advance()
+    ip, _ = tr.planted()
+    rng = np.random.default_rng(1)
+    hosts = np.concatenate([ip, tr.slice(0, 0)[:500, 0],
+                            rng.integers(0, 2**32, 300, dtype=np.uint64).astype(np.uint32)])
+    e, f, h = est.query(helpers.to_device(hosts), hist=True)
+    ref = orc.estimate(hosts, hist=True)
+    assert close_enough(e.cpu().numpy(), ref["est"])
+    assert np.array_equal(f.cpu().numpy(), ref["flags"])
+    assert np.array_equal(h.cpu().numpy().view(np.uint32), ref["hist"])
+    compare_state(est, orc, p, 2)  # the query changed nothing
+
+
+def test_merge_of_routers_equals_union():
+    """Three routers' estimators merged on the device equal one estimator of all pairs,
+    and both equal the oracle's merge."""
+    S = sse()
+    p = S.Params(seed=13)
+    tr = synth.Traffic(synth.small_trace(seed=13))
+    rng = np.random.default_rng(13)
+    routers = [S.Estimator(p) for _ in range(3)]
+    whole = S.Estimator(p)
+    orcs = [oracle.Oracle(oracle_params(p)) for _ in range(3)]
+    for t in range(5):
+        pairs = tr.slice(0, t)
+        owner = rng.integers(0, 3, len(pairs))
+        for j in range(3):
+            if t:
+                orcs[j].advance()
+            routers[j].update(helpers.to_device(pairs[owner == j]))
+            orcs[j].scan(pairs[owner == j])
+        whole.update(helpers.to_device(pairs))
+        if t < 4:
+            for e in routers + [whole]:
+                e.advance()
+    glob = S.Estimator(p)
+    for _ in range(4):
+        glob.advance()
+    glob.merge(routers)
+    og = oracle.Oracle(oracle_params(p))
+    for _ in range(4):
+        og.advance()
+    og.merge(orcs)
+    compare_state(glob, og, p, 4)
+    for x, y in zip(glob.read_stamps(), whole.read_stamps()):
+        assert np.array_equal(helpers.canonical_from_stamps(x, 4, p.k), helpers.canonical_from_stamps(y, 4, p.k))
+    compare_report(glob.close_slice(), og.detect())
+    with pytest.raises(S.SSEError):
+        routers[0].merge([glob])  # glob moved past the routers' slice
+
+
+def test_update_host_paths_match_device_path():
+    S = sse()
+    p = S.Params(seed=14)
+    tr = synth.Traffic(synth.small_trace(seed=14))
+    pairs = np.concatenate([tr.slice(0, 0), tr.slice(0, 1)])
+    a, b, c = S.Estimator(p), S.Estimator(p), S.Estimator(p)
+    a.update(helpers.to_device(pairs))
+    b.update_host(pairs)  # pageable
+    pinned = torch.from_numpy(pairs.view(np.int32)).pin_memory()
+    c.update_host(pinned)
+    for x, y, z in zip(a.read_stamps(), b.read_stamps(), c.read_stamps()):
+        assert np.array_equal(x, y) and np.array_equal(x, z)
+
+
+def test_checkpoint_roundtrip():
+    S = sse()
+    p = S.Params(seed=15)
+    tr = synth.Traffic(synth.small_trace(seed=15))
+    a = S.Estimator(p)
+    for t in range(3):
+        a.update(helpers.to_device(tr.slice(0, t)))
+        if t < 2:
+            a.advance()
+    blob = a.export_state()
+    b = S.Estimator(p)
+    b.import_state(blob)
+    assert b.slice == a.slice == 2
+    for x, y in zip(a.read_stamps(), b.read_stamps()):
+        assert np.array_equal(x, y)
+    ra, rb = a.close_slice(), b.close_slice()
+    assert np.array_equal(ra.hosts, rb.hosts) and np.array_equal(ra.est, rb.est)
+    with pytest.raises(S.SSEError):
+        S.Estimator(S.Params(seed=16)).import_state(blob)
+
+
+def _planted_state(p, orc, hosts, rng, noise_cells=20000):
+    sre = np.full((p.r, 1 << p.q, p.eta), helpers.INF, np.uint16)
+    for aip in hosts.tolist():
+        for i in range(p.r):
+            sre[i, orc.rhfg(i, aip), :3] = rng.integers(0, p.k, 3)
+    _, sle = orc.raw()
+    sle[:, rng.integers(0, orc.row_len2, noise_cells)] = 0
+    orc.set_raw(sre, sle)
+    return sre, sle
+
+
+def test_many_candidates_sorted_and_capacity():
+    """Planted hot SREs for thousands of hosts: candidate set = oracle's (brute force),
+    ascending across several sort chunks; a small capacity reports a truncated prefix."""
+    S = sse()
+    p = S.Params(q=20, k=2, theta=64, max_candidates=1 << 14, seed=17)
+    orc = oracle.Oracle(oracle_params(p))
+    rng = np.random.default_rng(17)
+    hosts = np.unique(rng.integers(0, 2**32, 9000, dtype=np.uint64).astype(np.uint32))
+    sre, sle = _planted_state(p, orc, hosts, rng)
+    want = orc.candidates_brute()
+    assert len(want) > 2 * 4096
+    est = S.Estimator(p)
+    blob = helpers.state_blob(est.export_state(), helpers.stamps_from_distances(sre, 0, p.k),
+                              helpers.stamps_from_distances(sle, 0, p.k), est.derived["row_pitch2"])
+    est.import_state(blob)
+    clone = S.Estimator(p)
+    clone.import_state(blob)
+    rep = est.close_slice()
+    assert np.array_equal(rep.hosts, want)
+    ref = orc.estimate(want)
+    assert np.array_equal(rep.flags, ref["flags"])
+    assert close_enough(rep.est, ref["est"])
+    small = clone.close_slice(cap=1000, raise_on_capacity=False)
+    assert small.status == S.ERR_CAPACITY and small.truncated
+    assert small.n_candidates == len(want)
+    assert np.array_equal(small.hosts, want[:1000])
+
+
+def test_candidate_overflow_is_reported():
+    S = sse()
+    p = S.Params(q=14, k=2, theta=64, max_candidates=64, seed=18)
+    orc = oracle.Oracle(oracle_params(p))
+    rng = np.random.default_rng(18)
+    hosts = rng.integers(0, 2**32, 200, dtype=np.uint64).astype(np.uint32)
+    sre, sle = _planted_state(p, orc, hosts, rng, noise_cells=10)
+    est = S.Estimator(p)
+    blob = helpers.state_blob(est.export_state(), helpers.stamps_from_distances(sre, 0, p.k),
+                              helpers.stamps_from_distances(sle, 0, p.k), est.derived["row_pitch2"])
+    est.import_state(blob)
+    rep = est.close_slice(raise_on_capacity=False)
+    assert rep.status == S.ERR_CAPACITY and rep.truncated and rep.n_candidates >= 200
+    assert len(rep.hosts) == 64 and np.all(np.diff(rep.hosts.astype(np.int64)) > 0)
+    est.update(helpers.to_device(np.zeros((4, 2), np.uint32)))  # the handle is still usable
+    est.sync()
+
+
+def test_invalid_arguments():
+    S = sse()
+    with pytest.raises(S.SSEError):
+        S.Estimator(S.Params(k=0))
+    est = S.Estimator(S.Params())
+    est.update(helpers.to_device(np.zeros((0, 2), np.uint32)))  # empty batch is a no-op
+    with pytest.raises(S.SSEError):
+        est.merge([est])
+    lib = S.lib()
+    assert lib.sse_update(est.handle, None, 5) < 0
+    assert lib.sse_query(est.handle, None, 3, None, None, None) < 0
+    assert lib.sse_set_update_mode(est.handle, 7) < 0
+    est.sync()
