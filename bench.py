@@ -1,0 +1,313 @@
+"""Benchmark: SRE+SLE update and slice close on the core-link workload.
+
+One step = one time slice of 2^25 synthetic IP pairs (core-link trace: 16M-host Zipf(1.05)
+population, 200 planted super points): sse_update() of the slice's pairs (already in
+HBM) followed by sse_close_slice() (expire, hot SREs, candidate join, sort, estimation,
+report copied to the host). Estimator: q=20 (RSRA 40 MiB), SLEA 2^16 SLEs x 2^12 cells,
+delta'=16, window k=8, theta=1024, 8-bit stamps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line. Under torchrun (N > 1) every rank runs its own router's trace
+(independent estimators: weak scaling, no data-path collective); the time is the max
+over ranks. --impl reference times the CPU oracle (tests' checker) on a bounded sample.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Gpackets/s SRE+SLE update at 1 B300 (% of L2/HBM roofline); slice-close p50/p99 ms"
+UNIT = "Gpkt/s"
+PAIRS_PER_SLICE = 1 << 25
+PREFILL = 8          # slices scanned before warm-up so that the window is full
+DISTINCT = 16        # device-resident slices the warm-up and timed steps cycle through
+PAIR_BYTES = 8
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--mode", type=int, default=0, help="update mode: 0 auto, 1 direct, 2 tiled")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6400.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.gpu = gpu
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.out = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.out, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.out.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    mx.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for name, val in zip(names, parts[5:9]):
+                    if val.lower() == "active":
+                        reasons.add(name)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def make_traffic(rank: int):
+    from paper_1805_09246_b300 import synth
+    return synth.Traffic(synth.core_link(seed=rank))
+
+
+def run_reference(args, rank, world):
+    """The CPU oracle as it stands, single-threaded, on a bounded sample of each slice."""
+    if rank != 0:
+        return
+    import oracle
+    tr = make_traffic(0)
+    sample = 1 << 21
+    o = oracle.Oracle(oracle.Params(q=20, q2=16, eta2=4096, k=8, theta=1024, seed=0))
+    data = [tr.slice(0, t)[:sample].copy() for t in range(min(args.warmup + args.steps, 16))]
+    for w in range(args.warmup):
+        o.scan(data[w % len(data)])
+        o.advance()
+    t0 = time.perf_counter()
+    for s in range(args.steps):
+        o.scan(data[(args.warmup + s) % len(data)])
+        o.advance()
+    dt = time.perf_counter() - t0
+    value = args.steps * sample / dt / 1e9
+    desc = (f"oracle scan (Alg. 3 + Alg. 6) of the first {sample} pairs of each core-link slice plus the "
+            "per-slice distance increment; detection is not timed: the oracle's tuple growth is "
+            "O(|HSE|^3) at this size")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": round(value, 6), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt / args.steps * 1e3, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+        "config": {"workload": "core_link: 2^25 pairs/slice, q=20, SLEA 2^16x2^12, k=8, theta=1024",
+                   "sample_pairs_per_step": sample},
+        "cpu_baseline": {"value": round(value, 6), "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc},
+        "e2e": {"value": round(value, 6), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def cpu_baseline(tr_slices):
+    """The oracle's update loop, single-threaded, on the first slices of the workload."""
+    import oracle
+    o = oracle.Oracle(oracle.Params(q=20, q2=16, eta2=4096, k=8, theta=1024, seed=0))
+    n = 0
+    t0 = time.perf_counter()
+    for t, s in enumerate(tr_slices):
+        if t:
+            o.advance()
+        o.scan(s)
+        n += len(s)
+    dt = time.perf_counter() - t0
+    return {"value": round(n / dt / 1e9, 6), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"oracle scan + slice increment over {len(tr_slices)} full core-link slices "
+                      f"({n} pairs, {dt:.1f} s); detection excluded (tuple growth is O(|HSE|^3) here)"}
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    import torch
+    from paper_1805_09246_b300 import sse
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+        pg = dist
+
+    tr = make_traffic(rank)
+    params = sse.core_link_params(k=8, seed=0)
+    est = sse.Estimator(params)
+    if args.mode:
+        est.set_update_mode(args.mode)
+    stream = torch.cuda.current_stream()
+
+    # inputs: PREFILL slices for the window, then DISTINCT slices the steps cycle through
+    host = [tr.slice(0, t) for t in range(PREFILL + DISTINCT)]
+    dev_slices = [torch.from_numpy(h.view(np.int32)).to(dev) for h in host]
+    torch.cuda.synchronize()
+    for t in range(PREFILL):
+        est.update(dev_slices[t])
+        est.close_slice()
+
+    def step_input(s):
+        return dev_slices[PREFILL + s % DISTINCT]
+
+    for w in range(args.warmup):
+        est.update(step_input(w))
+        est.close_slice()
+
+    # ---- timed region: K steps, inputs resident in HBM
+    ev_start, ev_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    upd_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    close_ms = []
+    launches0 = est.kernel_launches
+    n_super = n_cand = 0
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    if pg:
+        pg.barrier()
+    torch.cuda.synchronize()
+    ev_start.record(stream)
+    for s in range(args.steps):
+        a, b = upd_ev[s]
+        a.record(stream)
+        est.update(step_input(args.warmup + s))
+        b.record(stream)
+        stream.synchronize()  # slice boundary: all of this slice's pairs are applied
+        t0 = time.perf_counter()
+        rep = est.close_slice()
+        close_ms.append((time.perf_counter() - t0) * 1e3)
+        n_super += rep.n_super
+        n_cand += rep.n_candidates
+    ev_end.record(stream)
+    torch.cuda.synchronize()
+    if pg:
+        pg.barrier()
+    clk = clocks.stop()
+    launches = est.kernel_launches - launches0
+    elapsed_s = ev_start.elapsed_time(ev_end) / 1e3
+    upd_ms = sum(a.elapsed_time(b) for a, b in upd_ev) / args.steps
+    if pg:
+        t = torch.tensor([elapsed_s], device=dev)
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        elapsed_s = float(t.item())
+    total_pairs = args.steps * PAIRS_PER_SLICE * world
+    value = total_pairs / elapsed_s / 1e9
+
+    # ---- end to end through the public API: pinned host slices -> report on the host
+    e2e = None
+    if not args.no_e2e:
+        k_e2e = min(args.steps, 40)
+        pinned = [torch.from_numpy(host[PREFILL + s % DISTINCT].view(np.int32)).pin_memory()
+                  for s in range(min(k_e2e, DISTINCT))]
+        e2e_est = sse.Estimator(params)
+        if args.mode:
+            e2e_est.set_update_mode(args.mode)
+        for t in range(PREFILL):
+            e2e_est.update(dev_slices[t])
+            e2e_est.close_slice()
+        e2e_est.update_host(pinned[0])
+        e2e_est.close_slice()
+        d2h = 0
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for s in range(k_e2e):
+            e2e_est.update_host(pinned[s % len(pinned)])
+            r = e2e_est.close_slice()
+            d2h += 64 + r.n_candidates * 9  # report header + hosts/est/flags
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        e2e = {"value": round(k_e2e * PAIRS_PER_SLICE * world / dt / 1e9, 4), "unit": UNIT,
+               "h2d_bytes_per_step": PAIRS_PER_SLICE * PAIR_BYTES, "d2h_bytes_per_step": int(d2h / k_e2e),
+               "steps": k_e2e}
+        del e2e_est, pinned
+
+    hbm_peak, peak_kind = peaks()
+    achieved = PAIRS_PER_SLICE * PAIR_BYTES / (upd_ms / 1e3) / 1e9
+    roofline = {"bound": "hbm", "kernel": "sse update", "achieved": round(achieved, 2), "peak": hbm_peak,
+                "unit": "GB/s", "frac": round(achieved / hbm_peak, 4), "traffic": None,
+                "peak_source": f"{peak_kind} hbm_gbs",
+                "algorithmic_bytes_per_launch": PAIRS_PER_SLICE * PAIR_BYTES}
+
+    if rank != 0:
+        return
+    cpu = None if args.no_cpu else cpu_baseline([host[t] for t in range(8)])
+    close_sorted = sorted(close_ms)
+    out = {
+        "metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(elapsed_s / args.steps * 1e3, 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+        "config": {"workload": "core_link: 2^25 pairs/slice, 16M-host Zipf(1.05), 200 planted super points; "
+                               "q=20, r=5, SLEA r'=5 x (2^16 SLEs, eta'=4096, delta'=16), k=8, theta=1024",
+                   "pairs_per_step": PAIRS_PER_SLICE, "l2": "inputs larger than L2 (256 MiB per step)",
+                   "update_mode": args.mode},
+        "update_gpkts": round(PAIRS_PER_SLICE / (upd_ms / 1e3) / 1e9, 3),
+        "update_ms": round(upd_ms, 4),
+        "close_ms_p50": round(close_sorted[len(close_sorted) // 2], 4),
+        "close_ms_p99": round(close_sorted[min(len(close_sorted) - 1, int(0.99 * len(close_sorted)))], 4),
+        "candidates_per_slice": round(n_cand / args.steps, 1), "super_per_slice": round(n_super / args.steps, 1),
+        "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
+        "clocks": clk,
+    }
+    print(json.dumps(out), flush=True)
+    if pg:
+        pg.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()
