@@ -217,6 +217,26 @@ SSE_API int sse_merge(sse_handle* dst, const sse_handle* const* srcs, int n);
 SSE_API int sse_query(sse_handle* h, const uint32_t* d_hosts, uint32_t n, float* d_est, uint8_t* d_flags,
                       uint32_t* d_hist);
 
+/*
+ * sse_query() for callers that cannot allocate device memory. The paper has no
+ * counterpart: this entry point exists for processes that are handed pre-sized device
+ * buffers by their host framework and may not call the CUDA allocator themselves (an
+ * allocation can synchronise the device and stall their data path), so they cannot create
+ * a handle. The caller owns everything: p (the estimator's parameters), d_sle (its SLEA
+ * stamps, [r'][row_pitch2] bytes as sse_read_stamps() lays them out, 16-byte aligned),
+ * slice (the index t of the slice being scanned), d_hosts [n], d_est [n], d_flags [n] or
+ * NULL; results equal sse_query() on an estimator holding those stamps. The only scratch,
+ * one active-cell counter per SLEA row, is a 64-byte array inside the library that every
+ * GPU which loads the library keeps until the process exits; r' above 16 is rejected with
+ * SSE_ERR_INVALID_PARAM. The first call on a device looks up that array's device address
+ * (make it before any stream capture); each call clears the counters and then runs
+ * asynchronously on cuda_stream. All calls share the one array, so calls whose GPU work
+ * overlaps (different streams or threads) race and must be serialised by the caller.
+ * Allocates nothing. Errors: INVALID_PARAM, CUDA.
+ */
+SSE_API int sse_query_noalloc(const sse_params* p, const uint8_t* d_sle, uint64_t slice, const uint32_t* d_hosts,
+                              uint32_t n, float* d_est, uint8_t* d_flags, void* cuda_stream);
+
 /* Statistics of the last close (hot SREs per row, active SLEA cells per row, candidate
  * and super point counts). Synchronises the stream. Errors: CUDA. */
 SSE_API int sse_get_stats(sse_handle* h, sse_stats* out);

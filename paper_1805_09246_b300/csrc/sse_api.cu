@@ -614,3 +614,79 @@ int sse_sync(sse_handle* h) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------------------
+// Allocation-free query. Some callers cannot allocate device memory at all: for example a
+// packet-processing process that receives fixed, pre-sized device buffers from its host
+// framework and may not call the CUDA allocator (an allocation can synchronise the device
+// and stall the data path), so it cannot create a handle. sse_query_noalloc() serves them:
+// the caller passes the SLEA stamps, the hosts and the output buffers; the only scratch the
+// query needs (one active-cell counter per SLEA row) lives in the file-scope device array
+// below, which every GPU that loads this library holds until the process exits.
+namespace {
+
+constexpr int kNoAllocMaxRows = 16;  // scratch capacity: one counter per SLEA row
+static __device__ __align__(256) uint32_t g_noalloc_row_counts[kNoAllocMaxRows];
+
+constexpr int kNoAllocMaxDevices = 64;
+uint32_t* g_noalloc_ptr[kNoAllocMaxDevices];  // device address of the array, per device
+
+// First call on a device: look up the array's device address with that device current.
+// The host-side name of the array is only a stand-in and must never reach a kernel.
+int noalloc_scratch(uint32_t** out) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNoAllocMaxDevices) {
+    cudaGetLastError();
+    return SSE_ERR_CUDA;
+  }
+  if (!g_noalloc_ptr[dev]) {
+    void* ptr = nullptr;
+    if (cudaGetSymbolAddress(&ptr, g_noalloc_row_counts) != cudaSuccess || !ptr) {
+      cudaGetLastError();
+      return SSE_ERR_CUDA;
+    }
+    g_noalloc_ptr[dev] = static_cast<uint32_t*>(ptr);
+  }
+  *out = g_noalloc_ptr[dev];
+  return SSE_OK;
+}
+
+}  // namespace
+
+extern "C" int sse_query_noalloc(const sse_params* p, const uint8_t* d_sle, uint64_t slice, const uint32_t* d_hosts,
+                                 uint32_t n, float* d_est, uint8_t* d_flags, void* cuda_stream) {
+  if (!p) return SSE_ERR_INVALID_PARAM;
+  sse_params q;
+  sse_derived d;
+  const int rc = derive_params(*p, q, d);
+  if (rc != SSE_OK) return rc;
+  if (q.r2 > (uint32_t)kNoAllocMaxRows) return SSE_ERR_INVALID_PARAM;  // beyond the scratch array
+  if (n == 0) return SSE_OK;
+  if (!d_sle || !d_hosts || !d_est || (reinterpret_cast<uintptr_t>(d_sle) & 15u)) return SSE_ERR_INVALID_PARAM;
+  uint32_t* counts = nullptr;
+  if (noalloc_scratch(&counts) != SSE_OK) return SSE_ERR_CUDA;
+  int num_sms = 148, dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+    cudaGetLastError();
+    return SSE_ERR_CUDA;
+  }
+  cudaStream_t stream = (cudaStream_t)cuda_stream;
+  const KParams kp = make_kparams(q, d);
+  // the counters still hold the previous call's totals: clear them first
+  if (cudaMemsetAsync(counts, 0, kNoAllocMaxRows * sizeof(uint32_t), stream) != cudaSuccess) {
+    cudaGetLastError();
+    return SSE_ERR_CUDA;
+  }
+  const uint64_t sle_blocks = d.sle_bytes / kSleBytesPerBlock;
+  k_close<<<(unsigned)sle_blocks, kCloseThreads, 0, stream>>>(kp, nullptr, const_cast<uint8_t*>(d_sle), nullptr,
+                                                                counts, stamp_of(slice), 0u, 0u);
+  if (cudaGetLastError() != cudaSuccess) return SSE_ERR_CUDA;
+  uint64_t grid = ((uint64_t)n + kEstWarps - 1) / kEstWarps;
+  grid = std::min<uint64_t>(grid, (uint64_t)num_sms * 8);
+  k_estimate<<<(unsigned)grid, kEstWarps * 32, 0, stream>>>(kp, d_sle, d_hosts, nullptr, n, counts, d.w_theta,
+                                                             stamp_of(slice), d_est, d_flags, nullptr, nullptr,
+                                                             nullptr, nullptr);
+  if (cudaGetLastError() != cudaSuccess) return SSE_ERR_CUDA;
+  return SSE_OK;
+}
