@@ -1,0 +1,126 @@
+// Per-packet update, tiled strategy: SLEA writes are collected on chip.
+//
+// Within one slice every write stores the same stamp, so a slice's SLEA update is fully
+// described by the set of cells touched (Algorithm 6 writes are idempotent). Each CTA owns
+// one tile: a piece of one SLEA row, kept as a bitmap in shared memory (one bit per cell).
+// The CTAs of a group together own every tile and share one contiguous range of the pairs:
+// each CTA hashes each pair for its own row (LH_row and H3), and sets the bit when the cell
+// falls in its piece — an on-chip atomic OR instead of a scattered one-byte L2 write. At the
+// end every CTA ORs its non-zero bitmap words into a global bitmap of the SLEA, and
+// k_apply_bits turns each set bit into the stamp (and clears the bitmap for the next call).
+// RSRA writes (Algorithm 3, only a 2^-tau fraction of pairs) stay direct global stores;
+// each pair's RSRA work is done by exactly one CTA of its group (chosen by the low bits of
+// the pair index).
+#pragma once
+
+#include "k_update.cuh"
+#include "sse_internal.cuh"
+
+namespace sse {
+
+constexpr int kTiledThreads = 1024;
+
+struct TileGeometry {
+  uint32_t tiles;         // tiles per group (r' * pieces)
+  uint32_t pieces;        // pieces per SLEA row
+  uint32_t piece_bytes;   // cells per piece (multiple of 1024)
+  uint32_t groups;        // groups of CTAs; the pairs are split evenly between groups
+  uint32_t sre_span;      // power of two <= tiles: pair j's RSRA work goes to tile j mod sre_span
+};
+
+// grid = groups * tiles CTAs; dynamic shared memory = piece_bytes / 8.
+template <int UNROLL>
+__global__ void __launch_bounds__(kTiledThreads, 1) k_update_tiled(const __grid_constant__ KParams p, TileGeometry g,
+                                                                   const uint2* __restrict__ pairs, uint64_t n,
+                                                                   uint8_t* __restrict__ sre,
+                                                                   uint32_t* __restrict__ gbits, uint8_t stamp) {
+  extern __shared__ uint32_t bm[];
+  const uint32_t tile = blockIdx.x % g.tiles;
+  const uint32_t group = blockIdx.x / g.tiles;
+  const uint32_t row = tile / g.pieces;
+  const uint32_t piece = tile % g.pieces;
+  const uint32_t lo = piece * g.piece_bytes;  // cell range [lo, lo + piece_bytes) of the row
+  const uint32_t words = g.piece_bytes >> 5;
+  for (uint32_t w = threadIdx.x; w < words; w += blockDim.x) bm[w] = 0;
+  __syncthreads();
+
+  // this group's pairs: [begin, end)
+  const uint64_t begin = n * group / g.groups, end = n * (group + 1) / g.groups;
+  const uint64_t akey = p.key_a[kLH + row], bkey = p.key_b[kLH + row];
+  auto touch = [&](uint64_t j, uint32_t aip, uint32_t bip) {
+    const uint32_t h3 = mas_top(p.key_a[kH3], p.key_b[kH3], bip, p.lg_eta2);
+    const uint32_t lh = mas_top(akey, bkey, aip, p.q2);
+    const uint32_t cell = lh * p.delta2 + h3 - lo;  // wraps to a large value below lo
+    if (cell < g.piece_bytes) atomicOr(&bm[cell >> 5], 1u << (cell & 31));
+    if (((uint32_t)j & (g.sre_span - 1)) == tile) stamp_rsra(p, aip, bip, sre, stamp);
+  };
+  // peel to a 16-byte boundary, then two pairs per 128-bit load
+  uint64_t j0 = begin;
+  if (j0 < end && (reinterpret_cast<uintptr_t>(pairs + j0) & 15u)) {
+    if (threadIdx.x == 0) {
+      const uint2 v = pairs[j0];
+      touch(j0, v.x, v.y);
+    }
+    j0 += 1;
+  }
+  const uint4* vec = reinterpret_cast<const uint4*>(pairs + j0);
+  const uint64_t nvec = (end - j0) >> 1;
+  for (uint64_t i0 = threadIdx.x; i0 < nvec; i0 += (uint64_t)blockDim.x * UNROLL) {
+    uint4 buf[UNROLL];
+#pragma unroll
+    for (int u = 0; u < UNROLL; ++u) {
+      const uint64_t i = i0 + (uint64_t)u * blockDim.x;
+      if (i < nvec) buf[u] = vec[i];
+    }
+#pragma unroll
+    for (int u = 0; u < UNROLL; ++u) {
+      const uint64_t i = i0 + (uint64_t)u * blockDim.x;
+      if (i < nvec) {
+        touch(j0 + 2 * i, buf[u].x, buf[u].y);
+        touch(j0 + 2 * i + 1, buf[u].z, buf[u].w);
+      }
+    }
+  }
+  if (((end - j0) & 1) && threadIdx.x == 0) {
+    const uint2 v = pairs[end - 1];
+    touch(end - 1, v.x, v.y);
+  }
+  __syncthreads();
+  // flush: OR the piece's non-zero words into the global SLEA bitmap
+  uint32_t* dst = gbits + (((uint64_t)row * p.row_pitch2 + lo) >> 5);
+  for (uint32_t w = threadIdx.x; w < words; w += blockDim.x) {
+    const uint32_t v = bm[w];
+    if (v) atomicOr(&dst[w], v);
+  }
+}
+
+// Stamp every SLEA cell whose bit is set and clear the bitmap. One thread per bitmap word
+// (32 cells = two 16-byte vectors of the state); each word has a single owner.
+__global__ void __launch_bounds__(256) k_apply_bits(uint32_t* __restrict__ gbits, uint8_t* __restrict__ sle,
+                                                    uint64_t n_words, uint8_t stamp) {
+  for (uint64_t w = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; w < n_words;
+       w += (uint64_t)gridDim.x * blockDim.x) {
+    const uint32_t bits = gbits[w];
+    if (!bits) continue;
+    uint4* cells = reinterpret_cast<uint4*>(sle + (w << 5));
+#pragma unroll
+    for (int half = 0; half < 2; ++half) {
+      const uint32_t hb = (bits >> (16 * half)) & 0xFFFFu;
+      if (!hb) continue;
+      uint4 v = cells[half];
+      uint32_t x[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const uint32_t nib = (hb >> (4 * q)) & 0xFu;
+        // byte mask: 0xFF in byte b where bit b of nib is set
+        const uint32_t mask = ((nib & 1u) ? 0x000000FFu : 0u) | ((nib & 2u) ? 0x0000FF00u : 0u) |
+                              ((nib & 4u) ? 0x00FF0000u : 0u) | ((nib & 8u) ? 0xFF000000u : 0u);
+        x[q] = (x[q] & ~mask) | (stamp * 0x01010101u & mask);
+      }
+      cells[half] = make_uint4(x[0], x[1], x[2], x[3]);
+    }
+    gbits[w] = 0;
+  }
+}
+
+}  // namespace sse

@@ -11,6 +11,7 @@
 #include "k_detect.cuh"
 #include "k_merge.cuh"
 #include "k_update.cuh"
+#include "k_update_tiled.cuh"
 #include "sse.h"
 #include "sse_internal.cuh"
 
@@ -59,6 +60,7 @@ int derive_params(const sse_params& in, sse_params& p, sse_derived& d) {
   d.hot_min = (uint32_t)std::ceil((double)p.eta * rho);
   d.lg_eta2 = ilog2(p.eta2);
   d.row_len2 = ((uint64_t)1 << p.q2) * p.delta2 + p.eta2 - p.delta2;
+  if (d.row_len2 > (1ull << 31)) return SSE_ERR_INVALID_PARAM;
   d.row_pitch2 = (d.row_len2 + kPitchAlign - 1) / kPitchAlign * kPitchAlign;
   d.sre_bytes = (uint64_t)p.r << p.q << 3;
   d.sle_bytes = (uint64_t)p.r2 * d.row_pitch2;
@@ -87,6 +89,8 @@ struct sse_handle {
   uint8_t* sre = nullptr;
   uint8_t* sle = nullptr;
   uint32_t* hot_bits = nullptr;
+  uint32_t* sle_bits = nullptr;  // touched-cell bitmap of SLEA for the tiled update (kept zero)
+  TileGeometry tiles;
   uint32_t* list0 = nullptr;
   uint32_t* list1 = nullptr;
   uint32_t* cand = nullptr;  // two buffers of cand_cap entries
@@ -184,8 +188,43 @@ int launch_update_direct(sse_handle* h, const uint32_t* d_pairs, uint64_t n) {
   return SSE_OK;
 }
 
+// Tiles: each SLEA row is cut into pieces whose bitmap fits one CTA's shared memory.
+constexpr uint64_t kTileMaxCells = 1600u * 1024u;  // 200 KiB of bitmap
+
+TileGeometry make_tiles(const sse_params& p, const sse_derived& d, int num_sms) {
+  TileGeometry g;
+  g.pieces = (uint32_t)((d.row_pitch2 + kTileMaxCells - 1) / kTileMaxCells);
+  uint64_t piece = (d.row_pitch2 + g.pieces - 1) / g.pieces;
+  g.piece_bytes = (uint32_t)((piece + 1023) / 1024 * 1024);
+  g.tiles = p.r2 * g.pieces;
+  g.groups = std::max<uint32_t>(1u, (uint32_t)num_sms / g.tiles);
+  g.sre_span = 1;
+  while (g.sre_span * 2 <= g.tiles) g.sre_span *= 2;
+  return g;
+}
+
+int launch_update_tiled(sse_handle* h, const uint32_t* d_pairs, uint64_t n) {
+  const uint8_t stamp = stamp_of(h->slice);
+  const TileGeometry& g = h->tiles;
+  const size_t smem = g.piece_bytes / 8;
+  k_update_tiled<4><<<g.groups * g.tiles, kTiledThreads, smem, h->stream>>>(
+      h->kp, g, reinterpret_cast<const uint2*>(d_pairs), n, h->sre, h->sle_bits, stamp);
+  SSE_LAUNCHED(h);
+  const uint64_t words = h->d.sle_bytes / 32;
+  k_apply_bits<<<grid_for(h, words, 256, 8), 256, 0, h->stream>>>(h->sle_bits, h->sle, words, stamp);
+  SSE_LAUNCHED(h);
+  return SSE_OK;
+}
+
+// Batches of at least this many pairs use the tiled update in SSE_UPDATE_AUTO mode: the
+// flush of one bitmap per CTA (about r' * row length bits per group) must be small against
+// the pairs' own work.
+constexpr uint64_t kTiledMinPairs = 1ull << 20;
+
 int launch_update(sse_handle* h, const uint32_t* d_pairs, uint64_t n) {
-  return launch_update_direct(h, d_pairs, n);
+  const bool tiled = h->update_mode == SSE_UPDATE_TILED ||
+                     (h->update_mode == SSE_UPDATE_AUTO && n >= kTiledMinPairs);
+  return tiled ? launch_update_tiled(h, d_pairs, n) : launch_update_direct(h, d_pairs, n);
 }
 
 // Expire/weigh/count pass. mode: bit 0 expire, bit 1 write hot bitmap. Without either
@@ -280,6 +319,7 @@ void sse_destroy(sse_handle* h) {
   }
   cudaFree(h->state);
   cudaFree(h->hot_bits);
+  cudaFree(h->sle_bits);
   cudaFree(h->list0);
   cudaFree(h->list1);
   cudaFree(h->cand);
@@ -322,6 +362,7 @@ int sse_init(const sse_params* p, void* cuda_stream, sse_handle** out) {
   const uint64_t list_entries = 1ull << q.q;
   bool ok = cudaMalloc(&h->state, state_bytes) == cudaSuccess &&
             cudaMalloc(&h->hot_bits, ((uint64_t)q.r << q.q) / 8) == cudaSuccess &&
+            cudaMalloc(&h->sle_bits, d.sle_bytes / 8) == cudaSuccess &&
             cudaMalloc(&h->list0, list_entries * 4) == cudaSuccess &&
             cudaMalloc(&h->list1, list_entries * 4) == cudaSuccess &&
             cudaMalloc(&h->cand, (uint64_t)h->cand_cap * 4) == cudaSuccess &&
@@ -338,8 +379,16 @@ int sse_init(const sse_params* p, void* cuda_stream, sse_handle** out) {
   }
   h->sre = h->state;
   h->sle = h->state + d.sre_bytes;
+  h->tiles = make_tiles(q, d, h->num_sms);
+  if (cudaFuncSetAttribute(k_update_tiled<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)(h->tiles.piece_bytes / 8)) != cudaSuccess) {
+    cudaGetLastError();
+    sse_destroy(h);
+    return SSE_ERR_CUDA;
+  }
   if (cudaMemsetAsync(h->state, 0, state_bytes, h->stream) != cudaSuccess ||
       cudaMemsetAsync(h->hot_bits, 0, ((uint64_t)q.r << q.q) / 8, h->stream) != cudaSuccess ||
+      cudaMemsetAsync(h->sle_bits, 0, d.sle_bytes / 8, h->stream) != cudaSuccess ||
       cudaMemsetAsync(h->scratch, 0, sizeof(CloseScratch), h->stream) != cudaSuccess ||
       cudaStreamSynchronize(h->stream) != cudaSuccess) {
     cudaGetLastError();
@@ -355,7 +404,7 @@ uint64_t sse_current_slice(const sse_handle* h) { return h ? h->slice : 0; }
 uint64_t sse_kernel_launches(const sse_handle* h) { return h ? h->launches : 0; }
 
 int sse_set_update_mode(sse_handle* h, int mode) {
-  if (!h || mode < SSE_UPDATE_AUTO || mode > SSE_UPDATE_DIRECT) return SSE_ERR_INVALID_PARAM;
+  if (!h || mode < SSE_UPDATE_AUTO || mode > SSE_UPDATE_TILED) return SSE_ERR_INVALID_PARAM;
   h->update_mode = mode;
   return SSE_OK;
 }

@@ -72,12 +72,10 @@ def run_both(p, slices, mode=None, check_state=True):
     return est, orc, reports
 
 
-def update_modes():
-    S = sse()
-    return [S.UPDATE_DIRECT, S.UPDATE_AUTO]
+DIRECT, TILED = 1, 2
 
 
-@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("mode", [DIRECT, TILED])
 def test_small_trace_end_to_end(mode):
     """The 8-slice, 2^17-pair trace: every slice's state, hot SREs, counts and report."""
     S = sse()
@@ -87,14 +85,40 @@ def test_small_trace_end_to_end(mode):
     assert sum(r.n_super for r in reports) > 100  # the planted super points are found
 
 
+@pytest.mark.parametrize("mode", [DIRECT, TILED])
 @pytest.mark.parametrize("n", [1, 2, 3, 31, 1000, 65537, 300001])
-def test_ragged_sizes_and_tiles(n):
+def test_ragged_sizes_and_tiles(n, mode):
     S = sse()
     p = S.Params(q=12, delta=7, q2=8, eta2=256, k=2, theta=16, seed=n)
     rng = np.random.default_rng(n)
     src = rng.integers(0, 2**32, 97, dtype=np.uint64).astype(np.uint32)
     pairs = np.stack([src[rng.integers(0, 97, n)], rng.integers(0, 2**32, n, dtype=np.uint64).astype(np.uint32)], 1)
-    run_both(p, [pairs, pairs[: n // 2 + 1], pairs[::-1].copy()])
+    run_both(p, [pairs, pairs[: n // 2 + 1], pairs[::-1].copy()], mode=mode)
+
+
+@pytest.mark.parametrize("params", ["paper", "core_link", "many_rows"])
+def test_update_strategies_agree(params):
+    """Direct and tiled updates leave bit-identical stamps, including rows split into
+    several shared-memory pieces (the paper's q'=17 rows) and misaligned group starts."""
+    S = sse()
+    p = {"paper": S.paper_params(k=8), "core_link": S.core_link_params(),
+         "many_rows": S.Params(r2=16, q2=14, eta2=2048, seed=4)}[params]
+    rng = np.random.default_rng(7)
+    n = (1 << 22) + 3
+    src = rng.integers(0, 2**32, 1 << 20, dtype=np.uint64).astype(np.uint32)
+    pairs = np.stack([src[rng.integers(0, 1 << 20, n)], rng.integers(0, 2**32, n, dtype=np.uint64).astype(np.uint32)], 1)
+    a, b = S.Estimator(p), S.Estimator(p)
+    a.set_update_mode(DIRECT)
+    b.set_update_mode(TILED)
+    for t in range(2):
+        buf = helpers.to_device(np.concatenate([np.zeros((1, 2), np.uint32), pairs]))
+        a.update(buf[1:])
+        b.update(buf[1:])
+        for x, y in zip(a.read_stamps(), b.read_stamps()):
+            assert np.array_equal(x, y)
+        a.advance()
+        b.advance()
+        pairs = pairs[::-1].copy()
 
 
 def test_misaligned_device_pointer():
@@ -133,6 +157,34 @@ def test_window_wraps_stamp_cycle():
         else:
             est.advance()
     assert est.slice == 300
+
+
+def test_core_link_full_size_parity():
+    """Three 2^25-pair slices of the core-link trace in the benchmark's configuration
+    (automatic update strategy): state, hot SREs, row counts, candidates (against the
+    definitional brute force over all 2^32 addresses) and estimates."""
+    S = sse()
+    p = S.core_link_params()
+    tr = synth.Traffic(synth.core_link())
+    est = S.Estimator(p)
+    orc = oracle.Oracle(oracle_params(p))
+    for t in range(3):
+        pairs = tr.slice(0, t)
+        if t:
+            orc.advance()
+        est.update(helpers.to_device(pairs))
+        orc.scan(pairs)
+        rep = est.close_slice()
+    compare_state(est, orc, p, 2)
+    assert np.array_equal(est.hot_bitmap(), orc.hot())
+    assert est.stats()["active2"] == orc.row_counts().tolist()
+    want = orc.candidates_brute()
+    assert np.array_equal(rep.hosts, want)
+    ref = orc.estimate(want)
+    assert np.array_equal(rep.flags, ref["flags"])
+    assert close_enough(rep.est, ref["est"])
+    ip, _ = tr.planted()
+    assert len(np.intersect1d(ip, rep.super_points)) > 20
 
 
 def test_k1_discrete_window():
