@@ -43,6 +43,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--mode", type=int, default=0, help="update mode: 0 auto, 1 direct, 2 tiled")
+    ap.add_argument("--prefill", type=int, default=PREFILL, help="slices scanned before warm-up")
+    ap.add_argument("--distinct", type=int, default=DISTINCT, help="device-resident step inputs")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     return ap.parse_args()
@@ -196,15 +198,16 @@ def main():
     stream = torch.cuda.current_stream()
 
     # inputs: PREFILL slices for the window, then DISTINCT slices the steps cycle through
-    host = [tr.slice(0, t) for t in range(PREFILL + DISTINCT)]
+    prefill, distinct = args.prefill, max(1, args.distinct)
+    host = [tr.slice(0, t) for t in range(prefill + distinct)]
     dev_slices = [torch.from_numpy(h.view(np.int32)).to(dev) for h in host]
     torch.cuda.synchronize()
-    for t in range(PREFILL):
+    for t in range(prefill):
         est.update(dev_slices[t])
         est.close_slice()
 
     def step_input(s):
-        return dev_slices[PREFILL + s % DISTINCT]
+        return dev_slices[prefill + s % distinct]
 
     for w in range(args.warmup):
         est.update(step_input(w))
@@ -240,6 +243,7 @@ def main():
         pg.barrier()
     clk = clocks.stop()
     launches = est.kernel_launches - launches0
+    slice_stats = est.stats()
     elapsed_s = ev_start.elapsed_time(ev_end) / 1e3
     upd_ms = sum(a.elapsed_time(b) for a, b in upd_ev) / args.steps
     if pg:
@@ -253,12 +257,12 @@ def main():
     e2e = None
     if not args.no_e2e:
         k_e2e = min(args.steps, 40)
-        pinned = [torch.from_numpy(host[PREFILL + s % DISTINCT].view(np.int32)).pin_memory()
-                  for s in range(min(k_e2e, DISTINCT))]
+        pinned = [torch.from_numpy(host[prefill + s % distinct].view(np.int32)).pin_memory()
+                  for s in range(min(k_e2e, distinct))]
         e2e_est = sse.Estimator(params)
         if args.mode:
             e2e_est.set_update_mode(args.mode)
-        for t in range(PREFILL):
+        for t in range(prefill):
             e2e_est.update(dev_slices[t])
             e2e_est.close_slice()
         e2e_est.update_host(pinned[0])
@@ -301,6 +305,8 @@ def main():
         "close_ms_p50": round(close_sorted[len(close_sorted) // 2], 4),
         "close_ms_p99": round(close_sorted[min(len(close_sorted) - 1, int(0.99 * len(close_sorted)))], 4),
         "candidates_per_slice": round(n_cand / args.steps, 1), "super_per_slice": round(n_super / args.steps, 1),
+        "last_slice": {"hot_sre_per_row": slice_stats["hot"], "join_pairs": slice_stats["join_pairs"],
+                       "sf": [round(c / est.derived["row_len2"], 4) for c in slice_stats["active2"]]},
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
         "clocks": clk,
     }

@@ -84,27 +84,72 @@ __device__ __noinline__ void grow_deep(const KParams& p, const uint32_t* hot_bit
   }
 }
 
-// Blocks stride over HSE(0), threads over HSE(1).
-__global__ void __launch_bounds__(256) k_join(const __grid_constant__ KParams p, const uint32_t* __restrict__ hot_bits,
-                                              const uint32_t* __restrict__ list0, const uint32_t* __restrict__ list1,
-                                              const uint32_t* __restrict__ n_list, uint32_t* __restrict__ cand,
-                                              uint32_t* __restrict__ n_cand, uint32_t cap,
-                                              uint32_t* __restrict__ overflow) {
+// Row 2's hot bitmap regrouped for the join: bit (c << delta) + t of t2 is the hot flag of
+// SRE c | (t << (q - delta)) of row 2, so the 2^delta SREs that share their low q-delta
+// bits c (the part of B(2) fixed by B(1)) are adjacent bits. One thread per output word.
+__global__ void __launch_bounds__(256) k_row2_regroup(const uint32_t* __restrict__ hot_bits, uint32_t q,
+                                                      uint32_t delta, uint32_t* __restrict__ t2) {
+  const uint64_t nwords = (1ull << q) >> 5;
+  const uint32_t tmask = (1u << delta) - 1u;
+  for (uint64_t w = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; w < nwords; w += (uint64_t)gridDim.x * blockDim.x) {
+    uint32_t out = 0;
+    for (uint32_t b = 0; b < 32; ++b) {
+      const uint64_t bit = (w << 5) + b;
+      const uint32_t c = (uint32_t)(bit >> delta), t = (uint32_t)bit & tmask;
+      out |= (hot_bit(hot_bits, q, 2, c | (t << (q - delta))) ? 1u : 0u) << b;
+    }
+    t2[w] = out;
+  }
+}
+
+constexpr int kJoinThreads = 1024;
+
+// Blocks stride over HSE(0), threads over HSE(1). For a pair (he_0, he_1), B(1) fixes the
+// low q-delta bits c of every admissible he_2 (he_2 = he_0 XOR B(2)); the regrouped row-2
+// bitmap gives all 2^delta hot flags of those he_2 at once. t2 is staged in shared memory
+// when it fits (t2_in_smem), else read from global memory.
+__global__ void __launch_bounds__(kJoinThreads) k_join(const __grid_constant__ KParams p,
+                                                       const uint32_t* __restrict__ hot_bits,
+                                                       const uint32_t* __restrict__ t2_global,
+                                                       const uint32_t* __restrict__ list0,
+                                                       const uint32_t* __restrict__ list1,
+                                                       const uint32_t* __restrict__ n_list, uint32_t* __restrict__ cand,
+                                                       uint32_t* __restrict__ n_cand, uint32_t cap,
+                                                       uint32_t* __restrict__ overflow, uint32_t t2_in_smem) {
+  extern __shared__ uint32_t t2_smem[];
   const uint32_t n0 = n_list[0], n1 = n_list[1];
-  const uint32_t fan = 1u << p.delta;
-  const uint32_t shift_hi = p.q - p.delta;
-  const bool row2_fits_all = 2 * p.delta + p.q <= 32;
+  if (n0 == 0 || n1 == 0) return;
+  const uint32_t delta = p.delta, q = p.q;
+  const uint32_t shift_hi = q - delta;
+  const uint32_t cmask = (1u << shift_hi) - 1u;
+  const uint32_t span = 1u << delta;  // flags per c
+  const bool row2_fits_all = 2 * delta + q <= 32;
+  const uint32_t* t2 = t2_global;
+  if (t2_in_smem) {
+    const uint32_t nwords = (1u << q) >> 5;
+    for (uint32_t w = threadIdx.x; w < nwords; w += blockDim.x) t2_smem[w] = t2_global[w];
+    __syncthreads();
+    t2 = t2_smem;
+  }
   for (uint32_t a = blockIdx.x; a < n0; a += gridDim.x) {
     const uint32_t he0 = list0[a];
+    const uint32_t hi0 = he0 >> shift_hi;  // top delta bits of he_0
     for (uint32_t b = threadIdx.x; b < n1; b += blockDim.x) {
       const uint32_t b1 = he0 ^ list1[b];
-      if (!fits32(1, p.delta, p.q, b1)) continue;
-      const uint32_t low2 = b1 >> p.delta;
-      for (uint32_t t = 0; t < fan; ++t) {
-        const uint32_t b2 = low2 | (t << shift_hi);
-        if (!row2_fits_all && !fits32(2, p.delta, p.q, b2)) continue;
-        if (!hot_bit(hot_bits, p.q, 2, he0 ^ b2)) continue;
-        grow_deep(p, hot_bits, he0, b1, b2, cand, n_cand, cap, overflow);
+      if (!fits32(1, delta, q, b1)) continue;
+      const uint32_t low2 = b1 >> delta;
+      const uint32_t c = (he0 ^ low2) & cmask;
+      const uint64_t first = (uint64_t)c << delta;
+      for (uint32_t base = 0; base < span; base += 32) {
+        uint32_t m = t2[(first + base) >> 5];
+        if (span < 32) m = (m >> ((uint32_t)first & 31)) & ((1u << span) - 1u);
+        while (m) {
+          const uint32_t tp = base + (__ffs(m) - 1);  // top bits of he_2
+          m &= m - 1;
+          const uint32_t b2 = low2 | ((tp ^ hi0) << shift_hi);
+          if (!row2_fits_all && !fits32(2, delta, q, b2)) continue;
+          grow_deep(p, hot_bits, he0, b1, b2, cand, n_cand, cap, overflow);
+        }
       }
     }
   }
@@ -174,50 +219,75 @@ __global__ void __launch_bounds__(256) k_merge_runs(const uint32_t* __restrict__
 }
 
 // ---------------------------------------------------------------- estimation
-constexpr int kEstWarps = 8;
+constexpr int kEstThreads = 128;
 
-// hosts: n_ptr ? min(*n_ptr, n) hosts : n hosts. active2: active cells per SLEA row.
-// Outputs (any may be NULL except est): est, flags, w (FP64 corrected weight), U, hist[n][k].
-__global__ void __launch_bounds__(kEstWarps * 32) k_estimate(
+// One CTA per host (grid-stride). hosts: n_ptr ? min(*n_ptr, n) hosts : n hosts. active2:
+// active cells per SLEA row. Outputs (any may be NULL except est): est, flags, w (FP64
+// corrected weight), U, hist[n][k]. vec16: every SLE starts on a 16-byte boundary
+// (delta' % 16 == 0), so cells are gathered 16 at a time.
+__global__ void __launch_bounds__(kEstThreads) k_estimate(
     const __grid_constant__ KParams p, const uint8_t* __restrict__ sle, const uint32_t* __restrict__ hosts,
     const uint32_t* __restrict__ n_ptr, uint32_t n, const uint32_t* __restrict__ active2, double w_theta,
     uint32_t cs, float* __restrict__ est, uint8_t* __restrict__ flags, double* __restrict__ w_out,
     uint32_t* __restrict__ u_out, uint32_t* __restrict__ hist, uint32_t* __restrict__ n_super) {
   __shared__ uint8_t age_lut[256];
-  __shared__ uint32_t sh_hist[kEstWarps][256];
+  __shared__ uint32_t sh_hist[256];
+  __shared__ uint32_t warp_u[kEstThreads / 32];
+  __shared__ const uint8_t* row_base[kMaxRows];
   for (uint32_t s = threadIdx.x; s < 256; s += blockDim.x) {
     const uint32_t a = stamp_age(s, cs);
     age_lut[s] = a < p.k ? (uint8_t)a : 255;
   }
-  __syncthreads();
   const uint32_t count = n_ptr ? min(*n_ptr, n) : n;
-  const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const bool vec16 = (p.delta2 & 15u) == 0;
   const double eta2 = (double)p.eta2;
-  for (uint32_t h = blockIdx.x * kEstWarps + warp; h < count; h += gridDim.x * kEstWarps) {
+  for (uint32_t h = blockIdx.x; h < count; h += gridDim.x) {
     const uint32_t aip = hosts[h];
-    if (hist)
-      for (uint32_t a = lane; a < p.k; a += 32) sh_hist[warp][a] = 0;
-    __syncwarp();
-    const uint8_t* row_base[kMaxRows];
-    for (uint32_t i = 0; i < p.r2; ++i) {
-      const uint32_t j = mas_top(p.key_a[kLH + i], p.key_b[kLH + i], aip, p.q2);
-      row_base[i] = sle + i * p.row_pitch2 + (uint64_t)j * p.delta2;
+    if (threadIdx.x < p.r2) {
+      const uint32_t j = mas_top(p.key_a[kLH + threadIdx.x], p.key_b[kLH + threadIdx.x], aip, p.q2);
+      row_base[threadIdx.x] = sle + threadIdx.x * p.row_pitch2 + (uint64_t)j * p.delta2;
     }
+    if (hist)
+      for (uint32_t a = threadIdx.x; a < p.k; a += blockDim.x) sh_hist[a] = 0;
+    __syncthreads();
     uint32_t u = 0;
-    for (uint32_t z = lane; z < p.eta2; z += 32) {
-      uint32_t m = 0;
-      for (uint32_t i = 0; i < p.r2; ++i) m = max(m, (uint32_t)age_lut[row_base[i][z]]);
-      if (m != 255) {
-        u += 1;
-        if (hist) atomicAdd(&sh_hist[warp][m], 1u);
+    if (vec16) {
+      for (uint32_t z = threadIdx.x * 16; z < p.eta2; z += blockDim.x * 16) {
+        uint32_t m[16];
+#pragma unroll
+        for (int b = 0; b < 16; ++b) m[b] = 0;
+        for (uint32_t i = 0; i < p.r2; ++i) {
+          const uint4 v = *reinterpret_cast<const uint4*>(row_base[i] + z);
+          const uint32_t x[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+          for (int b = 0; b < 16; ++b) m[b] = max(m[b], (uint32_t)age_lut[(x[b >> 2] >> (8 * (b & 3))) & 0xFFu]);
+        }
+#pragma unroll
+        for (int b = 0; b < 16; ++b)
+          if (m[b] != 255) {
+            u += 1;
+            if (hist) atomicAdd(&sh_hist[m[b]], 1u);
+          }
+      }
+    } else {
+      for (uint32_t z = threadIdx.x; z < p.eta2; z += blockDim.x) {
+        uint32_t m = 0;
+        for (uint32_t i = 0; i < p.r2; ++i) m = max(m, (uint32_t)age_lut[row_base[i][z]]);
+        if (m != 255) {
+          u += 1;
+          if (hist) atomicAdd(&sh_hist[m], 1u);
+        }
       }
     }
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) u += __shfl_xor_sync(0xFFFFFFFFu, u, off);
-    __syncwarp();
+    if ((threadIdx.x & 31) == 0) warp_u[threadIdx.x >> 5] = u;
+    __syncthreads();
     if (hist)
-      for (uint32_t a = lane; a < p.k; a += 32) hist[(uint64_t)h * p.k + a] = sh_hist[warp][a];
-    if (lane == 0) {
+      for (uint32_t a = threadIdx.x; a < p.k; a += blockDim.x) hist[(uint64_t)h * p.k + a] = sh_hist[a];
+    if (threadIdx.x == 0) {
+      uint32_t U = 0;
+      for (int x = 0; x < kEstThreads / 32; ++x) U += warp_u[x];
       // Eq. 12 with SF(i,k) = active2[i] / row_len2 (Definition 4), multiplied in row order.
       double P = 1.0;
       for (uint32_t i = 0; i < p.r2; ++i) P = __dmul_rn(P, __ddiv_rn((double)active2[i], (double)p.row_len2));
@@ -227,7 +297,7 @@ __global__ void __launch_bounds__(kEstWarps * 32) k_estimate(
         w = eta2 - 1.0;
         f |= SSE_FLAG_SATURATED;
       } else {
-        const double num = __dsub_rn((double)u, __dmul_rn(eta2, P));
+        const double num = __dsub_rn((double)U, __dmul_rn(eta2, P));
         const double den = __dsub_rn(1.0, P);
         w = __ddiv_rn(num, den);
         if (w < 0.0) w = 0.0;
@@ -245,9 +315,9 @@ __global__ void __launch_bounds__(kEstWarps * 32) k_estimate(
       est[h] = (float)e;
       if (flags) flags[h] = f;
       if (w_out) w_out[h] = w;
-      if (u_out) u_out[h] = u;
+      if (u_out) u_out[h] = U;
     }
-    __syncwarp();
+    __syncthreads();
   }
 }
 

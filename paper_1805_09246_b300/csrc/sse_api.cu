@@ -93,6 +93,8 @@ struct sse_handle {
   TileGeometry tiles;
   uint32_t* list0 = nullptr;
   uint32_t* list1 = nullptr;
+  uint32_t* t2 = nullptr;  // row 2's hot bitmap regrouped for the join
+  uint32_t t2_in_smem = 0;
   uint32_t* cand = nullptr;  // two buffers of cand_cap entries
   uint32_t* cand_alt = nullptr;
   float* est = nullptr;
@@ -322,6 +324,7 @@ void sse_destroy(sse_handle* h) {
   cudaFree(h->sle_bits);
   cudaFree(h->list0);
   cudaFree(h->list1);
+  cudaFree(h->t2);
   cudaFree(h->cand);
   cudaFree(h->cand_alt);
   cudaFree(h->est);
@@ -365,6 +368,7 @@ int sse_init(const sse_params* p, void* cuda_stream, sse_handle** out) {
             cudaMalloc(&h->sle_bits, d.sle_bytes / 8) == cudaSuccess &&
             cudaMalloc(&h->list0, list_entries * 4) == cudaSuccess &&
             cudaMalloc(&h->list1, list_entries * 4) == cudaSuccess &&
+            cudaMalloc(&h->t2, list_entries / 8) == cudaSuccess &&
             cudaMalloc(&h->cand, (uint64_t)h->cand_cap * 4) == cudaSuccess &&
             cudaMalloc(&h->cand_alt, (uint64_t)h->cand_cap * 4) == cudaSuccess &&
             cudaMalloc(&h->est, (uint64_t)h->cand_cap * 4) == cudaSuccess &&
@@ -380,6 +384,15 @@ int sse_init(const sse_params* p, void* cuda_stream, sse_handle** out) {
   h->sre = h->state;
   h->sle = h->state + d.sre_bytes;
   h->tiles = make_tiles(q, d, h->num_sms);
+  // the regrouped row-2 bitmap (2^q bits) is staged in shared memory up to q = 20
+  h->t2_in_smem = q.q <= 20 ? 1u : 0u;
+  if (h->t2_in_smem &&
+      cudaFuncSetAttribute(k_join, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(list_entries / 8)) !=
+          cudaSuccess) {
+    cudaGetLastError();
+    sse_destroy(h);
+    return SSE_ERR_CUDA;
+  }
   if (cudaFuncSetAttribute(k_update_tiled<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)(h->tiles.piece_bytes / 8)) != cudaSuccess) {
     cudaGetLastError();
@@ -494,14 +507,21 @@ int sse_close_slice(sse_handle* h, sse_report* out) {
     k_hot_lists<<<grid, 256, 0, h->stream>>>(h->hot_bits, h->p.r, h->p.q, sc->hot, h->list0, h->list1, sc->n_list);
     SSE_LAUNCHED(h);
   }
-  k_join<<<h->num_sms * 8, 256, 0, h->stream>>>(h->kp, h->hot_bits, h->list0, h->list1, sc->n_list, h->cand,
-                                                &sc->n_cand, h->cand_cap, &sc->overflow);
-  SSE_LAUNCHED(h);
+  {
+    const uint64_t words = (1ull << h->p.q) >> 5;
+    k_row2_regroup<<<grid_for(h, words, 256, 8), 256, 0, h->stream>>>(h->hot_bits, h->p.q, h->p.delta, h->t2);
+    SSE_LAUNCHED(h);
+    const size_t smem = h->t2_in_smem ? (size_t)(words * 4) : 0;
+    k_join<<<h->num_sms, kJoinThreads, smem, h->stream>>>(h->kp, h->hot_bits, h->t2, h->list0, h->list1, sc->n_list,
+                                                          h->cand, &sc->n_cand, h->cand_cap, &sc->overflow,
+                                                          h->t2_in_smem);
+    SSE_LAUNCHED(h);
+  }
   uint32_t* sorted = launch_sort(h);
   SSE_CUDA(h, cudaGetLastError());
   {
-    const int grid = grid_for(h, h->cand_cap, kEstWarps, 8);
-    k_estimate<<<grid, kEstWarps * 32, 0, h->stream>>>(h->kp, h->sle, sorted, &sc->n_cand, h->cand_cap, sc->active2,
+    const int grid = grid_for(h, h->cand_cap, 1, 16);
+    k_estimate<<<grid, kEstThreads, 0, h->stream>>>(h->kp, h->sle, sorted, &sc->n_cand, h->cand_cap, sc->active2,
                                                         h->d.w_theta, stamp_of(h->slice), h->est, h->flags, nullptr,
                                                         nullptr, nullptr, &sc->n_super);
     SSE_LAUNCHED(h);
@@ -573,8 +593,8 @@ int sse_query(sse_handle* h, const uint32_t* d_hosts, uint32_t n, float* d_est, 
   SSE_CUDA(h, cudaMemsetAsync(h->query_active2, 0, kMaxRows * 4, h->stream));
   int rc = launch_close_pass(h, h->query_active2, 0u);  // count only
   if (rc) return rc;
-  const int grid = grid_for(h, n, kEstWarps, 8);
-  k_estimate<<<grid, kEstWarps * 32, 0, h->stream>>>(h->kp, h->sle, d_hosts, nullptr, n, h->query_active2,
+  const int grid = grid_for(h, n, 1, 16);
+  k_estimate<<<grid, kEstThreads, 0, h->stream>>>(h->kp, h->sle, d_hosts, nullptr, n, h->query_active2,
                                                       h->d.w_theta, stamp_of(h->slice), d_est, d_flags, nullptr,
                                                       nullptr, d_hist, nullptr);
   SSE_LAUNCHED(h);
@@ -731,9 +751,8 @@ extern "C" int sse_query_noalloc(const sse_params* p, const uint8_t* d_sle, uint
   k_close<<<(unsigned)sle_blocks, kCloseThreads, 0, stream>>>(kp, nullptr, const_cast<uint8_t*>(d_sle), nullptr,
                                                                 counts, stamp_of(slice), 0u, 0u);
   if (cudaGetLastError() != cudaSuccess) return SSE_ERR_CUDA;
-  uint64_t grid = ((uint64_t)n + kEstWarps - 1) / kEstWarps;
-  grid = std::min<uint64_t>(grid, (uint64_t)num_sms * 8);
-  k_estimate<<<(unsigned)grid, kEstWarps * 32, 0, stream>>>(kp, d_sle, d_hosts, nullptr, n, counts, d.w_theta,
+  uint64_t grid = std::min<uint64_t>((uint64_t)n, (uint64_t)num_sms * 16);
+  k_estimate<<<(unsigned)grid, kEstThreads, 0, stream>>>(kp, d_sle, d_hosts, nullptr, n, counts, d.w_theta,
                                                              stamp_of(slice), d_est, d_flags, nullptr, nullptr,
                                                              nullptr, nullptr);
   if (cudaGetLastError() != cudaSuccess) return SSE_ERR_CUDA;
