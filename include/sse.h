@@ -270,6 +270,9 @@ SSE_API uint64_t sse_kernel_launches(const sse_handle* h);
  * error flags). Errors: CUDA, TIMEOUT. */
 SSE_API int sse_sync(sse_handle* h);
 
+/* Name of the CUDA error behind a handle's SSE_ERR_CUDA ("" if none). */
+SSE_API const char* sse_cuda_error(const sse_handle* h);
+
 /* Static string for a status code. */
 SSE_API const char* sse_strerror(int status);
 

@@ -84,39 +84,84 @@ __device__ __noinline__ void grow_deep(const KParams& p, const uint32_t* hot_bit
   }
 }
 
-// Row 2's hot bitmap regrouped for the join: bit (c << delta) + t of t2 is the hot flag of
-// SRE c | (t << (q - delta)) of row 2, so the 2^delta SREs that share their low q-delta
-// bits c (the part of B(2) fixed by B(1)) are adjacent bits. One thread per output word.
-__global__ void __launch_bounds__(256) k_row2_regroup(const uint32_t* __restrict__ hot_bits, uint32_t q,
-                                                      uint32_t delta, uint32_t* __restrict__ t2) {
+// Hot bitmaps of rows 2..r-1 regrouped for the join: bit (c << delta) + t of table i-2 is
+// the hot flag of SRE c | (t << (q - delta)) of row i, so the 2^delta SREs that share their
+// low q-delta bits c (the part of B(i) fixed by B(i-1)) are adjacent bits.
+// One thread per output word; blockIdx.y = row - 2.
+__global__ void __launch_bounds__(256) k_row_regroup(const uint32_t* __restrict__ hot_bits, uint32_t q,
+                                                     uint32_t delta, uint32_t* __restrict__ tables) {
+  const uint32_t row = blockIdx.y + 2;
   const uint64_t nwords = (1ull << q) >> 5;
+  uint32_t* out_row = tables + (uint64_t)blockIdx.y * nwords;
   const uint32_t tmask = (1u << delta) - 1u;
   for (uint64_t w = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; w < nwords; w += (uint64_t)gridDim.x * blockDim.x) {
     uint32_t out = 0;
     for (uint32_t b = 0; b < 32; ++b) {
       const uint64_t bit = (w << 5) + b;
       const uint32_t c = (uint32_t)(bit >> delta), t = (uint32_t)bit & tmask;
-      out |= (hot_bit(hot_bits, q, 2, c | (t << (q - delta))) ? 1u : 0u) << b;
+      out |= (hot_bit(hot_bits, q, row, c | (t << (q - delta))) ? 1u : 0u) << b;
     }
-    t2[w] = out;
+    out_row[w] = out;
   }
 }
 
-constexpr int kJoinThreads = 1024;
+// The 2^delta (<= 32) hot flags, indexed by the top delta bits of he_i, of the row whose
+// regrouped table is `table`, for the SREs whose low q-delta bits are c.
+__device__ __forceinline__ uint32_t hot_group(const uint32_t* table, uint32_t c, uint32_t delta) {
+  const uint32_t first = c << delta;
+  const uint32_t span = 1u << delta;
+  const uint32_t w = table[first >> 5];
+  return span == 32 ? w : (w >> (first & 31)) & ((1u << span) - 1u);
+}
+
+// Rows 3..r-1 for delta <= 5: depth-first over the set bits of each row's hot group.
+__device__ __noinline__ void grow_grouped(const KParams& p, const uint32_t* tables, uint32_t he0, uint32_t b1,
+                                          uint32_t b2, uint32_t* cand, uint32_t* n_cand, uint32_t cap,
+                                          uint32_t* overflow) {
+  const uint32_t delta = p.delta, q = p.q, shift_hi = q - delta;
+  const uint32_t cmask = (1u << shift_hi) - 1u, hi0 = he0 >> shift_hi;
+  const uint64_t nwords = (1ull << q) >> 5;
+  uint32_t B[kMaxRows], M[kMaxRows];
+  B[1] = b1;
+  B[2] = b2;
+  int i = 3;
+  if (i < (int)p.r) M[i] = hot_group(tables + (uint64_t)(i - 2) * nwords, (he0 ^ (b2 >> delta)) & cmask, delta);
+  while (i >= 3) {
+    if (i == (int)p.r) {  // chain complete
+      regain(p, he0, B, cand, n_cand, cap, overflow);
+      i -= 1;
+      continue;
+    }
+    if (M[i] == 0) {  // level exhausted
+      i -= 1;
+      continue;
+    }
+    const uint32_t tp = __ffs(M[i]) - 1;  // top bits of he_i
+    M[i] &= M[i] - 1;
+    const uint32_t bi = (B[i - 1] >> delta) | ((tp ^ hi0) << shift_hi);
+    if (!fits32(i, delta, q, bi)) continue;
+    B[i] = bi;
+    i += 1;
+    if (i < (int)p.r) M[i] = hot_group(tables + (uint64_t)(i - 2) * nwords, (he0 ^ (bi >> delta)) & cmask, delta);
+  }
+}
+
+constexpr int kJoinThreads = 512;
 
 // Blocks stride over HSE(0), threads over HSE(1). For a pair (he_0, he_1), B(1) fixes the
 // low q-delta bits c of every admissible he_2 (he_2 = he_0 XOR B(2)); the regrouped row-2
-// bitmap gives all 2^delta hot flags of those he_2 at once. t2 is staged in shared memory
-// when it fits (t2_in_smem), else read from global memory.
+// table gives all 2^delta hot flags of those he_2 at once. The row-2 table (smem_t2 != 0)
+// and HSE(1) (when it fits in list1_cap entries) are staged in shared memory.
 __global__ void __launch_bounds__(kJoinThreads) k_join(const __grid_constant__ KParams p,
                                                        const uint32_t* __restrict__ hot_bits,
-                                                       const uint32_t* __restrict__ t2_global,
+                                                       const uint32_t* __restrict__ tables,
                                                        const uint32_t* __restrict__ list0,
                                                        const uint32_t* __restrict__ list1,
                                                        const uint32_t* __restrict__ n_list, uint32_t* __restrict__ cand,
                                                        uint32_t* __restrict__ n_cand, uint32_t cap,
-                                                       uint32_t* __restrict__ overflow, uint32_t t2_in_smem) {
-  extern __shared__ uint32_t t2_smem[];
+                                                       uint32_t* __restrict__ overflow, uint32_t smem_t2,
+                                                       uint32_t list1_cap) {
+  extern __shared__ uint32_t sm[];
   const uint32_t n0 = n_list[0], n1 = n_list[1];
   if (n0 == 0 || n1 == 0) return;
   const uint32_t delta = p.delta, q = p.q;
@@ -124,31 +169,41 @@ __global__ void __launch_bounds__(kJoinThreads) k_join(const __grid_constant__ K
   const uint32_t cmask = (1u << shift_hi) - 1u;
   const uint32_t span = 1u << delta;  // flags per c
   const bool row2_fits_all = 2 * delta + q <= 32;
-  const uint32_t* t2 = t2_global;
-  if (t2_in_smem) {
-    const uint32_t nwords = (1u << q) >> 5;
-    for (uint32_t w = threadIdx.x; w < nwords; w += blockDim.x) t2_smem[w] = t2_global[w];
-    __syncthreads();
-    t2 = t2_smem;
+  const uint32_t nwords = (1u << q) >> 5;
+  const uint32_t* t2 = tables;
+  uint32_t* sm_next = sm;
+  if (smem_t2) {
+    for (uint32_t w = threadIdx.x; w < nwords; w += blockDim.x) sm[w] = tables[w];
+    t2 = sm;
+    sm_next = sm + nwords;
   }
+  const uint32_t* l1 = list1;
+  if (n1 <= list1_cap) {
+    for (uint32_t x = threadIdx.x; x < n1; x += blockDim.x) sm_next[x] = list1[x];
+    l1 = sm_next;
+  }
+  __syncthreads();
   for (uint32_t a = blockIdx.x; a < n0; a += gridDim.x) {
     const uint32_t he0 = list0[a];
     const uint32_t hi0 = he0 >> shift_hi;  // top delta bits of he_0
     for (uint32_t b = threadIdx.x; b < n1; b += blockDim.x) {
-      const uint32_t b1 = he0 ^ list1[b];
+      const uint32_t b1 = he0 ^ l1[b];
       if (!fits32(1, delta, q, b1)) continue;
       const uint32_t low2 = b1 >> delta;
       const uint32_t c = (he0 ^ low2) & cmask;
-      const uint64_t first = (uint64_t)c << delta;
+      const uint32_t first = c << delta;
       for (uint32_t base = 0; base < span; base += 32) {
         uint32_t m = t2[(first + base) >> 5];
-        if (span < 32) m = (m >> ((uint32_t)first & 31)) & ((1u << span) - 1u);
+        if (span < 32) m = (m >> (first & 31)) & ((1u << span) - 1u);
         while (m) {
           const uint32_t tp = base + (__ffs(m) - 1);  // top bits of he_2
           m &= m - 1;
           const uint32_t b2 = low2 | ((tp ^ hi0) << shift_hi);
           if (!row2_fits_all && !fits32(2, delta, q, b2)) continue;
-          grow_deep(p, hot_bits, he0, b1, b2, cand, n_cand, cap, overflow);
+          if (span <= 32)
+            grow_grouped(p, tables, he0, b1, b2, cand, n_cand, cap, overflow);
+          else
+            grow_deep(p, hot_bits, he0, b1, b2, cand, n_cand, cap, overflow);
         }
       }
     }
@@ -156,16 +211,32 @@ __global__ void __launch_bounds__(kJoinThreads) k_join(const __grid_constant__ K
 }
 
 // ---------------------------------------------------------------- ordering
-// Bitonic sort of each kSortChunk-element chunk in shared memory; the tail beyond n is
-// padded with 0xFFFFFFFF (which sorts last, so the first n entries are the real ones).
+// Sort of each kSortChunk-element chunk in shared memory. Up to 1024 keys: rank sort (each
+// key's position is the number of keys before it in sorted order; ties by index). Larger
+// chunks: bitonic sort with the tail padded with 0xFFFFFFFF (which sorts last, so the first
+// entries are the real ones).
 __global__ void __launch_bounds__(1024) k_sort_chunks(uint32_t* __restrict__ keys, const uint32_t* __restrict__ n_ptr,
                                                       uint32_t cap) {
   __shared__ uint32_t s[kSortChunk];
   const uint32_t n = min(*n_ptr, cap);
   const uint32_t start = blockIdx.x * kSortChunk;
   if (start >= n) return;
-  for (uint32_t x = threadIdx.x; x < kSortChunk; x += blockDim.x)
-    s[x] = (start + x < n) ? keys[start + x] : 0xFFFFFFFFu;
+  const uint32_t m = min(n - start, (uint32_t)kSortChunk);
+  if (m <= 1024) {
+    for (uint32_t x = threadIdx.x; x < m; x += blockDim.x) s[x] = keys[start + x];
+    __syncthreads();
+    for (uint32_t x = threadIdx.x; x < m; x += blockDim.x) {
+      const uint32_t v = s[x];
+      uint32_t rank = 0;
+      for (uint32_t y = 0; y < m; ++y) {
+        const uint32_t u = s[y];
+        rank += (u < v || (u == v && y < x)) ? 1u : 0u;
+      }
+      keys[start + rank] = v;
+    }
+    return;
+  }
+  for (uint32_t x = threadIdx.x; x < kSortChunk; x += blockDim.x) s[x] = (x < m) ? keys[start + x] : 0xFFFFFFFFu;
   __syncthreads();
   for (uint32_t size = 2; size <= kSortChunk; size <<= 1) {
     for (uint32_t stride = size >> 1; stride > 0; stride >>= 1) {
@@ -182,7 +253,7 @@ __global__ void __launch_bounds__(1024) k_sort_chunks(uint32_t* __restrict__ key
       __syncthreads();
     }
   }
-  for (uint32_t x = threadIdx.x; x < kSortChunk && start + x < n; x += blockDim.x) keys[start + x] = s[x];
+  for (uint32_t x = threadIdx.x; x < m; x += blockDim.x) keys[start + x] = s[x];
 }
 
 // Merge sorted runs of length `width` pairwise from src into dst (stable; ranks by

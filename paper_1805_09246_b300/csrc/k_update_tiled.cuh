@@ -46,44 +46,48 @@ __global__ void __launch_bounds__(kTiledThreads, 1) k_update_tiled(const __grid_
 
   // this group's pairs: [begin, end)
   const uint64_t begin = n * group / g.groups, end = n * (group + 1) / g.groups;
-  const uint64_t akey = p.key_a[kLH + row], bkey = p.key_b[kLH + row];
-  auto touch = [&](uint64_t j, uint32_t aip, uint32_t bip) {
-    const uint32_t h3 = mas_top(p.key_a[kH3], p.key_b[kH3], bip, p.lg_eta2);
-    const uint32_t lh = mas_top(akey, bkey, aip, p.q2);
-    const uint32_t cell = lh * p.delta2 + h3 - lo;  // wraps to a large value below lo
-    if (cell < g.piece_bytes) atomicOr(&bm[cell >> 5], 1u << (cell & 31));
-    if (((uint32_t)j & (g.sre_span - 1)) == tile) stamp_rsra(p, aip, bip, sre, stamp);
+  const uint64_t a3 = p.key_a[kH3], b3 = p.key_b[kH3];
+  const uint64_t al = p.key_a[kLH + row], bl = p.key_b[kLH + row];
+  const uint32_t sh3 = 32 - p.lg_eta2, shl = 32 - p.q2, d2 = p.delta2, span = g.piece_bytes;
+  const uint32_t sre_mask = g.sre_span - 1;
+  auto touch = [&](uint32_t j, uint32_t aip, uint32_t bip) {
+    const uint32_t h3 = (uint32_t)((uint64_t)mas_hi(a3, b3, bip) >> sh3);
+    const uint32_t lh = (uint32_t)((uint64_t)mas_hi(al, bl, aip) >> shl);
+    const uint32_t cell = lh * d2 + h3 - lo;  // wraps to a large value below lo
+    if (cell < span) atomicOr(&bm[cell >> 5], 1u << (cell & 31));
+    if ((j & sre_mask) == tile) stamp_rsra(p, aip, bip, sre, stamp);
   };
   // peel to a 16-byte boundary, then two pairs per 128-bit load
   uint64_t j0 = begin;
   if (j0 < end && (reinterpret_cast<uintptr_t>(pairs + j0) & 15u)) {
     if (threadIdx.x == 0) {
       const uint2 v = pairs[j0];
-      touch(j0, v.x, v.y);
+      touch((uint32_t)j0, v.x, v.y);
     }
     j0 += 1;
   }
   const uint4* vec = reinterpret_cast<const uint4*>(pairs + j0);
-  const uint64_t nvec = (end - j0) >> 1;
-  for (uint64_t i0 = threadIdx.x; i0 < nvec; i0 += (uint64_t)blockDim.x * UNROLL) {
+  const uint32_t nvec = (uint32_t)((end - j0) >> 1);
+  const uint32_t jb = (uint32_t)j0;
+  for (uint32_t i0 = threadIdx.x; i0 < nvec; i0 += blockDim.x * UNROLL) {
     uint4 buf[UNROLL];
 #pragma unroll
     for (int u = 0; u < UNROLL; ++u) {
-      const uint64_t i = i0 + (uint64_t)u * blockDim.x;
+      const uint32_t i = i0 + u * blockDim.x;
       if (i < nvec) buf[u] = vec[i];
     }
 #pragma unroll
     for (int u = 0; u < UNROLL; ++u) {
-      const uint64_t i = i0 + (uint64_t)u * blockDim.x;
+      const uint32_t i = i0 + u * blockDim.x;
       if (i < nvec) {
-        touch(j0 + 2 * i, buf[u].x, buf[u].y);
-        touch(j0 + 2 * i + 1, buf[u].z, buf[u].w);
+        touch(jb + 2 * i, buf[u].x, buf[u].y);
+        touch(jb + 2 * i + 1, buf[u].z, buf[u].w);
       }
     }
   }
   if (((end - j0) & 1) && threadIdx.x == 0) {
     const uint2 v = pairs[end - 1];
-    touch(end - 1, v.x, v.y);
+    touch((uint32_t)(end - 1), v.x, v.y);
   }
   __syncthreads();
   // flush: OR the piece's non-zero words into the global SLEA bitmap

@@ -81,6 +81,7 @@ struct sse_handle {
   cudaStream_t stream = nullptr;
   uint64_t slice = 0;
   int sticky = SSE_OK;    // first CUDA error seen; later calls return it
+  cudaError_t cuda_error = cudaSuccess;  // the CUDA error behind `sticky`
   uint64_t launches = 0;  // kernels launched by this handle
   int update_mode = SSE_UPDATE_AUTO;
   int num_sms = 148;
@@ -93,8 +94,10 @@ struct sse_handle {
   TileGeometry tiles;
   uint32_t* list0 = nullptr;
   uint32_t* list1 = nullptr;
-  uint32_t* t2 = nullptr;  // row 2's hot bitmap regrouped for the join
-  uint32_t t2_in_smem = 0;
+  uint32_t* tables = nullptr;  // hot bitmaps of rows 2..r-1 regrouped for the join
+  uint32_t join_smem_t2 = 0;   // stage the row-2 table in shared memory
+  uint32_t join_list1_cap = 0; // HSE(1) entries staged in shared memory when it fits
+  size_t join_smem = 0;
   uint32_t* cand = nullptr;  // two buffers of cand_cap entries
   uint32_t* cand_alt = nullptr;
   float* est = nullptr;
@@ -117,7 +120,10 @@ namespace {
 
 int fail(sse_handle* h, cudaError_t e) {
   if (e == cudaSuccess) return SSE_OK;
-  if (h && h->sticky == SSE_OK) h->sticky = SSE_ERR_CUDA;
+  if (h && h->sticky == SSE_OK) {
+    h->sticky = SSE_ERR_CUDA;
+    h->cuda_error = e;
+  }
   return SSE_ERR_CUDA;
 }
 
@@ -209,9 +215,13 @@ int launch_update_tiled(sse_handle* h, const uint32_t* d_pairs, uint64_t n) {
   const uint8_t stamp = stamp_of(h->slice);
   const TileGeometry& g = h->tiles;
   const size_t smem = g.piece_bytes / 8;
-  k_update_tiled<4><<<g.groups * g.tiles, kTiledThreads, smem, h->stream>>>(
-      h->kp, g, reinterpret_cast<const uint2*>(d_pairs), n, h->sre, h->sle_bits, stamp);
-  SSE_LAUNCHED(h);
+  constexpr uint64_t kMaxPairsPerLaunch = 1ull << 30;  // keeps per-group indices in 32 bits
+  for (uint64_t done = 0; done < n; done += kMaxPairsPerLaunch) {
+    const uint64_t m = std::min(kMaxPairsPerLaunch, n - done);
+    k_update_tiled<4><<<g.groups * g.tiles, kTiledThreads, smem, h->stream>>>(
+        h->kp, g, reinterpret_cast<const uint2*>(d_pairs + 2 * done), m, h->sre, h->sle_bits, stamp);
+    SSE_LAUNCHED(h);
+  }
   const uint64_t words = h->d.sle_bytes / 32;
   k_apply_bits<<<grid_for(h, words, 256, 8), 256, 0, h->stream>>>(h->sle_bits, h->sle, words, stamp);
   SSE_LAUNCHED(h);
@@ -324,7 +334,7 @@ void sse_destroy(sse_handle* h) {
   cudaFree(h->sle_bits);
   cudaFree(h->list0);
   cudaFree(h->list1);
-  cudaFree(h->t2);
+  cudaFree(h->tables);
   cudaFree(h->cand);
   cudaFree(h->cand_alt);
   cudaFree(h->est);
@@ -368,7 +378,7 @@ int sse_init(const sse_params* p, void* cuda_stream, sse_handle** out) {
             cudaMalloc(&h->sle_bits, d.sle_bytes / 8) == cudaSuccess &&
             cudaMalloc(&h->list0, list_entries * 4) == cudaSuccess &&
             cudaMalloc(&h->list1, list_entries * 4) == cudaSuccess &&
-            cudaMalloc(&h->t2, list_entries / 8) == cudaSuccess &&
+            cudaMalloc(&h->tables, (q.r - 2) * (list_entries / 8)) == cudaSuccess &&
             cudaMalloc(&h->cand, (uint64_t)h->cand_cap * 4) == cudaSuccess &&
             cudaMalloc(&h->cand_alt, (uint64_t)h->cand_cap * 4) == cudaSuccess &&
             cudaMalloc(&h->est, (uint64_t)h->cand_cap * 4) == cudaSuccess &&
@@ -384,20 +394,26 @@ int sse_init(const sse_params* p, void* cuda_stream, sse_handle** out) {
   h->sre = h->state;
   h->sle = h->state + d.sre_bytes;
   h->tiles = make_tiles(q, d, h->num_sms);
-  // the regrouped row-2 bitmap (2^q bits) is staged in shared memory up to q = 20
-  h->t2_in_smem = q.q <= 20 ? 1u : 0u;
-  if (h->t2_in_smem &&
-      cudaFuncSetAttribute(k_join, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(list_entries / 8)) !=
-          cudaSuccess) {
-    cudaGetLastError();
-    sse_destroy(h);
-    return SSE_ERR_CUDA;
-  }
   if (cudaFuncSetAttribute(k_update_tiled<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)(h->tiles.piece_bytes / 8)) != cudaSuccess) {
     cudaGetLastError();
     sse_destroy(h);
     return SSE_ERR_CUDA;
+  }
+  // join shared memory: the regrouped row-2 table (2^q bits) up to q = 20, then as much of
+  // HSE(1) as fits in the rest of a 200 KiB budget
+  {
+    const size_t budget = 200u * 1024u;
+    const size_t t2_bytes = (size_t)(list_entries / 8);
+    h->join_smem_t2 = t2_bytes <= 128u * 1024u ? 1u : 0u;
+    const size_t used = h->join_smem_t2 ? t2_bytes : 0;
+    h->join_list1_cap = (uint32_t)std::min<uint64_t>(list_entries, (budget - used) / 4);
+    h->join_smem = used + (size_t)h->join_list1_cap * 4;
+    if (cudaFuncSetAttribute(k_join, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)h->join_smem) != cudaSuccess) {
+      cudaGetLastError();
+      sse_destroy(h);
+      return SSE_ERR_CUDA;
+    }
   }
   if (cudaMemsetAsync(h->state, 0, state_bytes, h->stream) != cudaSuccess ||
       cudaMemsetAsync(h->hot_bits, 0, ((uint64_t)q.r << q.q) / 8, h->stream) != cudaSuccess ||
@@ -415,6 +431,10 @@ int sse_init(const sse_params* p, void* cuda_stream, sse_handle** out) {
 uint64_t sse_current_slice(const sse_handle* h) { return h ? h->slice : 0; }
 
 uint64_t sse_kernel_launches(const sse_handle* h) { return h ? h->launches : 0; }
+
+const char* sse_cuda_error(const sse_handle* h) {
+  return (h && h->cuda_error != cudaSuccess) ? cudaGetErrorName(h->cuda_error) : "";
+}
 
 int sse_set_update_mode(sse_handle* h, int mode) {
   if (!h || mode < SSE_UPDATE_AUTO || mode > SSE_UPDATE_TILED) return SSE_ERR_INVALID_PARAM;
@@ -509,12 +529,12 @@ int sse_close_slice(sse_handle* h, sse_report* out) {
   }
   {
     const uint64_t words = (1ull << h->p.q) >> 5;
-    k_row2_regroup<<<grid_for(h, words, 256, 8), 256, 0, h->stream>>>(h->hot_bits, h->p.q, h->p.delta, h->t2);
+    const dim3 grid(grid_for(h, words, 256, 2), h->p.r - 2);
+    k_row_regroup<<<grid, 256, 0, h->stream>>>(h->hot_bits, h->p.q, h->p.delta, h->tables);
     SSE_LAUNCHED(h);
-    const size_t smem = h->t2_in_smem ? (size_t)(words * 4) : 0;
-    k_join<<<h->num_sms, kJoinThreads, smem, h->stream>>>(h->kp, h->hot_bits, h->t2, h->list0, h->list1, sc->n_list,
-                                                          h->cand, &sc->n_cand, h->cand_cap, &sc->overflow,
-                                                          h->t2_in_smem);
+    k_join<<<h->num_sms, kJoinThreads, h->join_smem, h->stream>>>(h->kp, h->hot_bits, h->tables, h->list0, h->list1,
+                                                                  sc->n_list, h->cand, &sc->n_cand, h->cand_cap,
+                                                                  &sc->overflow, h->join_smem_t2, h->join_list1_cap);
     SSE_LAUNCHED(h);
   }
   uint32_t* sorted = launch_sort(h);

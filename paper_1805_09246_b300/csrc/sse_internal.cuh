@@ -29,9 +29,14 @@ struct KParams {
 };
 
 // Multiply-add-shift hash: the top m bits (0 <= m <= 32) of (a*x + b) mod 2^64.
+// With x < 2^32 the high word is hi32(lo32(a)*x + b) + hi32(a)*x (mod 2^32): one widening
+// multiply-add and one 32-bit multiply-add.
+__host__ __device__ __forceinline__ uint32_t mas_hi(uint64_t a, uint64_t b, uint32_t x) {
+  const uint64_t t = (uint64_t)(uint32_t)a * x + b;
+  return (uint32_t)(t >> 32) + (uint32_t)(a >> 32) * x;
+}
 __host__ __device__ __forceinline__ uint32_t mas_top(uint64_t a, uint64_t b, uint32_t x, uint32_t m) {
-  uint64_t v = a * (uint64_t)x + b;
-  return (uint32_t)((v >> 32) >> (32 - m));
+  return (uint32_t)((uint64_t)mas_hi(a, b, x) >> (32 - m));
 }
 
 // Cyclic stamp arithmetic: slice t has stamp 1 + (t mod 255); 0 marks an unset cell.

@@ -119,6 +119,7 @@ def lib() -> ctypes.CDLL:
             "sse_kernel_launches": (u64, [vp]),
             "sse_sync": (i32, [vp]),
             "sse_strerror": (ctypes.c_char_p, [i32]),
+            "sse_cuda_error": (ctypes.c_char_p, [vp]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -135,9 +136,12 @@ def _strerror(code: int) -> str:
         return "error"
 
 
-def _check(code: int, what: str) -> int:
+def _check(code: int, what: str, handle=None) -> int:
     if code != SSE_OK:
-        raise SSEError(code, what)
+        detail = ""
+        if handle is not None and handle.value:
+            detail = lib().sse_cuda_error(handle).decode()
+        raise SSEError(code, f"{what} [{detail}]" if detail else what)
     return code
 
 
@@ -225,7 +229,7 @@ class Estimator:
         n = pairs.numel() // 2
         if n == 0:
             return
-        _check(self._lib.sse_update(self._h, ctypes.c_void_p(_dev_ptr(pairs, 4)), n), "sse_update")
+        _check(self._lib.sse_update(self._h, ctypes.c_void_p(_dev_ptr(pairs, 4)), n), "sse_update", self._h)
 
     def update_host(self, pairs) -> None:
         """Scan pairs held in host memory (numpy array or CPU tensor, (n, 2) 32-bit)."""
@@ -248,7 +252,7 @@ class Estimator:
         rep = _Report(0, 0, 0, cap, 0, hosts.ctypes.data, est.ctypes.data, flags.ctypes.data)
         rc = self._lib.sse_close_slice(self._h, ctypes.byref(rep))
         if rc != SSE_OK and (rc != ERR_CAPACITY or raise_on_capacity):
-            raise SSEError(rc, "sse_close_slice")
+            _check(rc, "sse_close_slice", self._h)
         m = min(rep.n_candidates, cap, self.params.max_candidates)
         return Report(slice=rep.slice, n_candidates=rep.n_candidates, n_super=rep.n_super,
                       truncated=bool(rep.truncated), hosts=hosts[:m].copy(), est=est[:m].copy(),
