@@ -9,8 +9,7 @@
 // end every CTA ORs its non-zero bitmap words into a global bitmap of the SLEA, and
 // k_apply_bits turns each set bit into the stamp (and clears the bitmap for the next call).
 // RSRA writes (Algorithm 3, only a 2^-tau fraction of pairs) stay direct global stores;
-// each pair's RSRA work is done by exactly one CTA of its group (chosen by the low bits of
-// the pair index).
+// each pair's RSRA work is done by exactly one CTA of its group.
 #pragma once
 
 #include "k_update.cuh"
@@ -25,7 +24,6 @@ struct TileGeometry {
   uint32_t pieces;        // pieces per SLEA row
   uint32_t piece_bytes;   // cells per piece (multiple of 1024)
   uint32_t groups;        // groups of CTAs; the pairs are split evenly between groups
-  uint32_t sre_span;      // power of two <= tiles: pair j's RSRA work goes to tile j mod sre_span
 };
 
 // grid = groups * tiles CTAs; dynamic shared memory = piece_bytes / 8.
@@ -49,45 +47,64 @@ __global__ void __launch_bounds__(kTiledThreads, 1) k_update_tiled(const __grid_
   const uint64_t a3 = p.key_a[kH3], b3 = p.key_b[kH3];
   const uint64_t al = p.key_a[kLH + row], bl = p.key_b[kLH + row];
   const uint32_t sh3 = 32 - p.lg_eta2, shl = 32 - p.q2, d2 = p.delta2, span = g.piece_bytes;
-  const uint32_t sre_mask = g.sre_span - 1;
-  auto touch = [&](uint32_t j, uint32_t aip, uint32_t bip) {
+  auto touch = [&](uint32_t aip, uint32_t bip) {
     const uint32_t h3 = (uint32_t)((uint64_t)mas_hi(a3, b3, bip) >> sh3);
     const uint32_t lh = (uint32_t)((uint64_t)mas_hi(al, bl, aip) >> shl);
     const uint32_t cell = lh * d2 + h3 - lo;  // wraps to a large value below lo
     if (cell < span) atomicOr(&bm[cell >> 5], 1u << (cell & 31));
-    if ((j & sre_mask) == tile) stamp_rsra(p, aip, bip, sre, stamp);
   };
-  // peel to a 16-byte boundary, then two pairs per 128-bit load
+  // peel to a 16-byte boundary, then two pairs per 128-bit load; the peeled and the odd
+  // last pair's RSRA work belongs to tile 0
   uint64_t j0 = begin;
   if (j0 < end && (reinterpret_cast<uintptr_t>(pairs + j0) & 15u)) {
     if (threadIdx.x == 0) {
       const uint2 v = pairs[j0];
-      touch((uint32_t)j0, v.x, v.y);
+      touch(v.x, v.y);
+      if (tile == 0) stamp_rsra(p, v.x, v.y, sre, stamp);
     }
     j0 += 1;
   }
   const uint4* vec = reinterpret_cast<const uint4*>(pairs + j0);
   const uint32_t nvec = (uint32_t)((end - j0) >> 1);
-  const uint32_t jb = (uint32_t)j0;
-  for (uint32_t i0 = threadIdx.x; i0 < nvec; i0 += blockDim.x * UNROLL) {
+  const uint32_t stride = blockDim.x;
+  // Block iteration k covers vectors [k*stride*UNROLL, (k+1)*stride*UNROLL); sub-step u of
+  // it is owned, for RSRA, by tile (k*UNROLL + u) mod tiles — uniform across the block, so
+  // the RSRA branch never diverges inside a warp.
+  const uint32_t full = nvec / (stride * UNROLL);
+  uint32_t owner = 0;
+  for (uint32_t k = 0; k < full; ++k) {
+    const uint32_t base = k * stride * UNROLL + threadIdx.x;
     uint4 buf[UNROLL];
 #pragma unroll
-    for (int u = 0; u < UNROLL; ++u) {
-      const uint32_t i = i0 + u * blockDim.x;
-      if (i < nvec) buf[u] = vec[i];
-    }
+    for (int u = 0; u < UNROLL; ++u) buf[u] = vec[base + u * stride];
 #pragma unroll
     for (int u = 0; u < UNROLL; ++u) {
-      const uint32_t i = i0 + u * blockDim.x;
-      if (i < nvec) {
-        touch(jb + 2 * i, buf[u].x, buf[u].y);
-        touch(jb + 2 * i + 1, buf[u].z, buf[u].w);
+      touch(buf[u].x, buf[u].y);
+      touch(buf[u].z, buf[u].w);
+      if (owner == tile) {
+        stamp_rsra(p, buf[u].x, buf[u].y, sre, stamp);
+        stamp_rsra(p, buf[u].z, buf[u].w, sre, stamp);
+      }
+      owner = owner + 1 == g.tiles ? 0 : owner + 1;
+    }
+  }
+  for (uint32_t u = 0; u < UNROLL; ++u) {  // remainder: the last, partial iteration
+    const uint32_t i = full * stride * UNROLL + u * stride + threadIdx.x;
+    if (i < nvec) {
+      const uint4 v = vec[i];
+      touch(v.x, v.y);
+      touch(v.z, v.w);
+      if (owner == tile) {
+        stamp_rsra(p, v.x, v.y, sre, stamp);
+        stamp_rsra(p, v.z, v.w, sre, stamp);
       }
     }
+    owner = owner + 1 == g.tiles ? 0 : owner + 1;
   }
   if (((end - j0) & 1) && threadIdx.x == 0) {
     const uint2 v = pairs[end - 1];
-    touch((uint32_t)(end - 1), v.x, v.y);
+    touch(v.x, v.y);
+    if (tile == 0) stamp_rsra(p, v.x, v.y, sre, stamp);
   }
   __syncthreads();
   // flush: OR the piece's non-zero words into the global SLEA bitmap

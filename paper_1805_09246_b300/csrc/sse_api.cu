@@ -206,8 +206,6 @@ TileGeometry make_tiles(const sse_params& p, const sse_derived& d, int num_sms) 
   g.piece_bytes = (uint32_t)((piece + 1023) / 1024 * 1024);
   g.tiles = p.r2 * g.pieces;
   g.groups = std::max<uint32_t>(1u, (uint32_t)num_sms / g.tiles);
-  g.sre_span = 1;
-  while (g.sre_span * 2 <= g.tiles) g.sre_span *= 2;
   return g;
 }
 
