@@ -209,6 +209,9 @@ def main():
     def step_input(s):
         return dev_slices[prefill + s % distinct]
 
+    # autotune the update on the next slice's pairs (idempotent within the slice), untimed
+    tuned, tune_ms = est.autotune_update(step_input(0), reps=3)
+
     for w in range(args.warmup):
         est.update(step_input(w))
         est.close_slice()
@@ -262,6 +265,7 @@ def main():
         e2e_est = sse.Estimator(params)
         if args.mode:
             e2e_est.set_update_mode(args.mode)
+        e2e_est.set_update_variant(tuned)
         for t in range(prefill):
             e2e_est.update(dev_slices[t])
             e2e_est.close_slice()
@@ -299,7 +303,8 @@ def main():
         "config": {"workload": "core_link: 2^25 pairs/slice, 16M-host Zipf(1.05), 200 planted super points; "
                                "q=20, r=5, SLEA r'=5 x (2^16 SLEs, eta'=4096, delta'=16), k=8, theta=1024",
                    "pairs_per_step": PAIRS_PER_SLICE, "l2": "inputs larger than L2 (256 MiB per step)",
-                   "update_mode": args.mode},
+                   "update_mode": args.mode, "update_variant": tuned,
+                   "variant_ms": [round(t, 4) for t in tune_ms]},
         "update_gpkts": round(PAIRS_PER_SLICE / (upd_ms / 1e3) / 1e9, 3),
         "update_ms": round(upd_ms, 4),
         "close_ms_p50": round(close_sorted[len(close_sorted) // 2], 4),

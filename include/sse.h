@@ -179,6 +179,25 @@ SSE_API int sse_update_host(sse_handle* h, const uint32_t* h_pairs, uint64_t n_p
  * it. Errors: INVALID_PARAM. */
 SSE_API int sse_set_update_mode(sse_handle* h, int mode);
 
+/* Number of update variants the autotuner chooses from (variant 0 is the direct update,
+ * the others are tiled updates with different loads in flight and atomic policies). */
+SSE_API int sse_update_variant_count(void);
+
+/* Fixes the update variant used by SSE_UPDATE_AUTO for large batches (and, if tiled, by
+ * SSE_UPDATE_TILED); -1 restores the built-in rule. Errors: INVALID_PARAM. */
+SSE_API int sse_set_update_variant(sse_handle* h, int variant);
+
+/*
+ * Autotuner: times every update variant on d_pairs (device pairs of the current slice;
+ * rescanning them changes nothing, since a slice's writes are idempotent), reps timed
+ * launches each after one warm-up, on the handle's stream, and keeps the fastest for
+ * batches of this size in SSE_UPDATE_AUTO mode (and the fastest tiled one for
+ * SSE_UPDATE_TILED). times_ms: NULL or sse_update_variant_count() floats (mean ms per
+ * update); *chosen: the chosen variant. Synchronous. Errors: INVALID_PARAM, CUDA.
+ */
+SSE_API int sse_autotune_update(sse_handle* h, const uint32_t* d_pairs, uint64_t n_pairs, int reps,
+                                float* times_ms, int* chosen);
+
 /*
  * Closes the current slice t: expires cells older than the window W(t,k), finds the
  * hot SREs of every row, grows candidate tuples and regains candidate hosts (Algorithms

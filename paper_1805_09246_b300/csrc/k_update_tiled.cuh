@@ -26,8 +26,10 @@ struct TileGeometry {
   uint32_t groups;        // groups of CTAs; the pairs are split evenly between groups
 };
 
-// grid = groups * tiles CTAs; dynamic shared memory = piece_bytes / 8.
-template <int UNROLL>
+// grid = groups * tiles CTAs; dynamic shared memory = piece_bytes / 8. UNROLL 128-bit loads
+// are in flight per thread; CHECK reads the bitmap word first and skips the atomic when the
+// bit is already set (repeated pairs are common in real traffic).
+template <int UNROLL, bool CHECK>
 __global__ void __launch_bounds__(kTiledThreads, 1) k_update_tiled(const __grid_constant__ KParams p, TileGeometry g,
                                                                    const uint2* __restrict__ pairs, uint64_t n,
                                                                    uint8_t* __restrict__ sre,
@@ -51,7 +53,10 @@ __global__ void __launch_bounds__(kTiledThreads, 1) k_update_tiled(const __grid_
     const uint32_t h3 = (uint32_t)((uint64_t)mas_hi(a3, b3, bip) >> sh3);
     const uint32_t lh = (uint32_t)((uint64_t)mas_hi(al, bl, aip) >> shl);
     const uint32_t cell = lh * d2 + h3 - lo;  // wraps to a large value below lo
-    if (cell < span) atomicOr(&bm[cell >> 5], 1u << (cell & 31));
+    if (cell < span) {
+      const uint32_t bit = 1u << (cell & 31);
+      if (!CHECK || !(bm[cell >> 5] & bit)) atomicOr(&bm[cell >> 5], bit);
+    }
   };
   // peel to a 16-byte boundary, then two pairs per 128-bit load; the peeled and the odd
   // last pair's RSRA work belongs to tile 0

@@ -84,6 +84,7 @@ struct sse_handle {
   cudaError_t cuda_error = cudaSuccess;  // the CUDA error behind `sticky`
   uint64_t launches = 0;  // kernels launched by this handle
   int update_mode = SSE_UPDATE_AUTO;
+  int tuned_variant = -1;  // update variant chosen by sse_autotune_update (-1: none yet)
   int num_sms = 148;
   // device memory
   uint8_t* state = nullptr;  // RSRA then SLEA
@@ -209,14 +210,30 @@ TileGeometry make_tiles(const sse_params& p, const sse_derived& d, int num_sms) 
   return g;
 }
 
-int launch_update_tiled(sse_handle* h, const uint32_t* d_pairs, uint64_t n) {
+// Tiled update variants: loads in flight per thread and test-before-set atomics.
+using TiledKernel = void (*)(KParams, TileGeometry, const uint2*, uint64_t, uint8_t*, uint32_t*, uint8_t);
+struct TiledVariant {
+  TiledKernel fn;
+  int unroll;
+  bool check;
+};
+const TiledVariant kTiledVariants[] = {
+    {k_update_tiled<4, false>, 4, false}, {k_update_tiled<2, false>, 2, false}, {k_update_tiled<8, false>, 8, false},
+    {k_update_tiled<4, true>, 4, true},   {k_update_tiled<2, true>, 2, true},   {k_update_tiled<8, true>, 8, true},
+};
+constexpr int kNumTiledVariants = sizeof(kTiledVariants) / sizeof(kTiledVariants[0]);
+// Update variants seen by the autotuner: 0 = direct, 1 + v = tiled variant v.
+constexpr int kNumUpdateVariants = 1 + kNumTiledVariants;
+
+int launch_update_tiled(sse_handle* h, const uint32_t* d_pairs, uint64_t n, int variant) {
   const uint8_t stamp = stamp_of(h->slice);
   const TileGeometry& g = h->tiles;
   const size_t smem = g.piece_bytes / 8;
+  const TiledKernel fn = kTiledVariants[variant].fn;
   constexpr uint64_t kMaxPairsPerLaunch = 1ull << 30;  // keeps per-group indices in 32 bits
   for (uint64_t done = 0; done < n; done += kMaxPairsPerLaunch) {
     const uint64_t m = std::min(kMaxPairsPerLaunch, n - done);
-    k_update_tiled<4><<<g.groups * g.tiles, kTiledThreads, smem, h->stream>>>(
+    fn<<<g.groups * g.tiles, kTiledThreads, smem, h->stream>>>(
         h->kp, g, reinterpret_cast<const uint2*>(d_pairs + 2 * done), m, h->sre, h->sle_bits, stamp);
     SSE_LAUNCHED(h);
   }
@@ -226,15 +243,21 @@ int launch_update_tiled(sse_handle* h, const uint32_t* d_pairs, uint64_t n) {
   return SSE_OK;
 }
 
-// Batches of at least this many pairs use the tiled update in SSE_UPDATE_AUTO mode: the
-// flush of one bitmap per CTA (about r' * row length bits per group) must be small against
-// the pairs' own work.
+// Batches of at least this many pairs use the tiled update in SSE_UPDATE_AUTO mode unless
+// the autotuner chose otherwise: the flush of one bitmap per CTA (about r' * row length
+// bits per group) must be small against the pairs' own work.
 constexpr uint64_t kTiledMinPairs = 1ull << 20;
 
+int launch_variant(sse_handle* h, const uint32_t* d_pairs, uint64_t n, int variant) {
+  return variant == 0 ? launch_update_direct(h, d_pairs, n) : launch_update_tiled(h, d_pairs, n, variant - 1);
+}
+
 int launch_update(sse_handle* h, const uint32_t* d_pairs, uint64_t n) {
-  const bool tiled = h->update_mode == SSE_UPDATE_TILED ||
-                     (h->update_mode == SSE_UPDATE_AUTO && n >= kTiledMinPairs);
-  return tiled ? launch_update_tiled(h, d_pairs, n) : launch_update_direct(h, d_pairs, n);
+  const int tiled_variant = h->tuned_variant > 0 ? h->tuned_variant : 1;
+  if (h->update_mode == SSE_UPDATE_DIRECT) return launch_variant(h, d_pairs, n, 0);
+  if (h->update_mode == SSE_UPDATE_TILED) return launch_variant(h, d_pairs, n, tiled_variant);
+  if (n < kTiledMinPairs) return launch_variant(h, d_pairs, n, 0);
+  return launch_variant(h, d_pairs, n, h->tuned_variant >= 0 ? h->tuned_variant : tiled_variant);
 }
 
 // Expire/weigh/count pass. mode: bit 0 expire, bit 1 write hot bitmap. Without either
@@ -392,11 +415,13 @@ int sse_init(const sse_params* p, void* cuda_stream, sse_handle** out) {
   h->sre = h->state;
   h->sle = h->state + d.sre_bytes;
   h->tiles = make_tiles(q, d, h->num_sms);
-  if (cudaFuncSetAttribute(k_update_tiled<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)(h->tiles.piece_bytes / 8)) != cudaSuccess) {
-    cudaGetLastError();
-    sse_destroy(h);
-    return SSE_ERR_CUDA;
+  for (int v = 0; v < kNumTiledVariants; ++v) {
+    if (cudaFuncSetAttribute(kTiledVariants[v].fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(h->tiles.piece_bytes / 8)) != cudaSuccess) {
+      cudaGetLastError();
+      sse_destroy(h);
+      return SSE_ERR_CUDA;
+    }
   }
   // join shared memory: the regrouped row-2 table (2^q bits) up to q = 20, then as much of
   // HSE(1) as fits in the rest of a 200 KiB budget
@@ -437,6 +462,52 @@ const char* sse_cuda_error(const sse_handle* h) {
 int sse_set_update_mode(sse_handle* h, int mode) {
   if (!h || mode < SSE_UPDATE_AUTO || mode > SSE_UPDATE_TILED) return SSE_ERR_INVALID_PARAM;
   h->update_mode = mode;
+  return SSE_OK;
+}
+
+int sse_update_variant_count(void) { return kNumUpdateVariants; }
+
+int sse_set_update_variant(sse_handle* h, int variant) {
+  if (!h || variant < -1 || variant >= kNumUpdateVariants) return SSE_ERR_INVALID_PARAM;
+  h->tuned_variant = variant;
+  return SSE_OK;
+}
+
+int sse_autotune_update(sse_handle* h, const uint32_t* d_pairs, uint64_t n_pairs, int reps, float* times_ms,
+                        int* chosen) {
+  if (!h || !d_pairs || n_pairs == 0 || reps < 1 || (reinterpret_cast<uintptr_t>(d_pairs) & 7u))
+    return SSE_ERR_INVALID_PARAM;
+  if (h->sticky) return h->sticky;
+  cudaEvent_t e0, e1;
+  SSE_CUDA(h, cudaEventCreate(&e0));
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return fail(h, cudaGetLastError());
+  }
+  int best = -1, rc = SSE_OK;
+  float best_ms = 0.f;
+  for (int v = 0; v < kNumUpdateVariants && rc == SSE_OK; ++v) {
+    // the pairs belong to the current slice, so repeating their update changes nothing
+    rc = launch_variant(h, d_pairs, n_pairs, v);
+    if (rc == SSE_OK && cudaEventRecord(e0, h->stream) != cudaSuccess) rc = fail(h, cudaGetLastError());
+    for (int r = 0; r < reps && rc == SSE_OK; ++r) rc = launch_variant(h, d_pairs, n_pairs, v);
+    if (rc == SSE_OK && (cudaEventRecord(e1, h->stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess))
+      rc = fail(h, cudaGetLastError());
+    if (rc != SSE_OK) break;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    ms /= reps;
+    if (times_ms) times_ms[v] = ms;
+    if (best < 0 || ms < best_ms) {
+      best = v;
+      best_ms = ms;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc != SSE_OK) return rc;
+  h->tuned_variant = best;
+  if (chosen) *chosen = best;
   return SSE_OK;
 }
 

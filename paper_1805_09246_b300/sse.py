@@ -106,6 +106,9 @@ def lib() -> ctypes.CDLL:
             "sse_update": (i32, [vp, vp, u64]),
             "sse_update_host": (i32, [vp, vp, u64]),
             "sse_set_update_mode": (i32, [vp, i32]),
+            "sse_set_update_variant": (i32, [vp, i32]),
+            "sse_update_variant_count": (i32, []),
+            "sse_autotune_update": (i32, [vp, vp, u64, i32, vp, ctypes.POINTER(i32)]),
             "sse_close_slice": (i32, [vp, vp]),
             "sse_advance": (i32, [vp]),
             "sse_merge": (i32, [vp, ctypes.POINTER(vp), i32]),
@@ -127,6 +130,10 @@ def lib() -> ctypes.CDLL:
             fn.argtypes = args
         _lib = L
     return _lib
+
+
+def update_variant_count() -> int:
+    return int(lib().sse_update_variant_count())
 
 
 def _strerror(code: int) -> str:
@@ -223,6 +230,18 @@ class Estimator:
 
     def set_update_mode(self, mode: int) -> None:
         _check(self._lib.sse_set_update_mode(self._h, mode), "sse_set_update_mode")
+
+    def set_update_variant(self, variant: int) -> None:
+        _check(self._lib.sse_set_update_variant(self._h, variant), "sse_set_update_variant")
+
+    def autotune_update(self, pairs, reps: int = 3) -> tuple[int, list[float]]:
+        """Time every update variant on these (current-slice) pairs and keep the fastest."""
+        nv = int(self._lib.sse_update_variant_count())
+        times = (ctypes.c_float * nv)()
+        chosen = ctypes.c_int(-1)
+        _check(self._lib.sse_autotune_update(self._h, ctypes.c_void_p(_dev_ptr(pairs, 4)), pairs.numel() // 2,
+                                             reps, times, ctypes.byref(chosen)), "sse_autotune_update", self._h)
+        return chosen.value, [float(t) for t in times]
 
     def update(self, pairs) -> None:
         """Scan the pairs of a CUDA tensor of shape (n, 2), 32-bit elements {src, dst}."""

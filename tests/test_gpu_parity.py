@@ -96,6 +96,40 @@ def test_ragged_sizes_and_tiles(n, mode):
     run_both(p, [pairs, pairs[: n // 2 + 1], pairs[::-1].copy()], mode=mode)
 
 
+def test_every_update_variant_matches_oracle():
+    """Each autotuner variant (direct and every tiled form) gives the oracle's state."""
+    S = sse()
+    p = S.Params(seed=19)
+    tr = synth.Traffic(synth.small_trace(seed=19))
+    slices = [tr.slice(0, t) for t in range(2)]
+    for v in range(S.update_variant_count()):
+        est = S.Estimator(p)
+        est.set_update_mode(TILED if v else DIRECT)
+        est.set_update_variant(v)
+        orc = oracle.Oracle(oracle_params(p))
+        for t, pairs in enumerate(slices):
+            if t:
+                orc.advance()
+                est.advance()
+            est.update(helpers.to_device(pairs))
+            orc.scan(pairs)
+        compare_state(est, orc, p, 1)
+
+
+def test_autotune_keeps_state_and_picks_a_variant():
+    S = sse()
+    p = S.Params(seed=20)
+    tr = synth.Traffic(synth.small_trace(seed=20))
+    pairs = helpers.to_device(tr.slice(0, 0))
+    a, b = S.Estimator(p), S.Estimator(p)
+    a.update(pairs)
+    chosen, times = b.autotune_update(pairs, reps=2)
+    assert 0 <= chosen < S.update_variant_count() and len(times) == S.update_variant_count()
+    assert all(t > 0 for t in times) and times[chosen] == min(times)
+    for x, y in zip(a.read_stamps(), b.read_stamps()):
+        assert np.array_equal(x, y)
+
+
 @pytest.mark.parametrize("params", ["paper", "core_link", "many_rows"])
 def test_update_strategies_agree(params):
     """Direct and tiled updates leave bit-identical stamps, including rows split into
