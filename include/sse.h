@@ -289,6 +289,58 @@ SSE_API uint64_t sse_kernel_launches(const sse_handle* h);
  * error flags). Errors: CUDA, TIMEOUT. */
 SSE_API int sse_sync(sse_handle* h);
 
+/*
+ * Batches: R edge routers (1..64) whose estimators advance slice by slice together, plus a
+ * global estimator that merges them (the distributed setting of Section 3.3 and Alg. 7,
+ * with all routers' estimators on one device). Each step scans every router's pairs of
+ * the current slice in ONE persistent kernel launch (work items = (router, chunk), taken
+ * from per-tile counters, so uneven router loads balance), merges the routers into the
+ * global estimator (expiring the routers' old cells on the way), closes the slice on the
+ * global estimator (candidates, estimates, flags, as sse_close_slice) and advances every
+ * estimator. The step's device work is captured once into a CUDA graph and replayed.
+ * The batch owns a non-blocking CUDA stream (sse_batch_stream) and its estimators; the
+ * handles from sse_batch_router / sse_batch_global stay owned by the batch (do not
+ * destroy them, and call only read-only functions on them between steps).
+ */
+typedef struct sse_batch sse_batch;
+
+/* capacity_pairs: size of each router's input buffer. Errors: INVALID_PARAM, OOM, CUDA. */
+SSE_API int sse_batch_create(const sse_params* p, int n_routers, uint64_t capacity_pairs, sse_batch** out);
+SSE_API void sse_batch_destroy(sse_batch* b);
+
+/* Device input buffer of a router (capacity_pairs pairs {src, dst}); fill it, on the
+ * batch's stream or before the step, with the router's pairs of the current slice. */
+SSE_API uint32_t* sse_batch_input(sse_batch* b, int router);
+SSE_API void* sse_batch_stream(sse_batch* b);
+
+/* Copies n_pairs pairs (device memory, or host memory when from_host) into a router's
+ * input buffer and returns when the copy is done (device sources must be ready: the copy
+ * runs on the batch's own stream). Errors: INVALID_PARAM, CAPACITY, CUDA. */
+SSE_API int sse_batch_load(sse_batch* b, int router, const uint32_t* pairs, uint64_t n_pairs, int from_host);
+SSE_API int sse_batch_router(sse_batch* b, int router, sse_handle** out);
+SSE_API int sse_batch_global(sse_batch* b, sse_handle** out);
+
+/* 1 (default): capture the step into a CUDA graph on first use and replay it; 0: launch
+ * the same kernels directly each step. Results are identical. */
+SSE_API int sse_batch_use_graph(sse_batch* b, int enable);
+
+/* Work-item size (pairs, >= 1024) and loads in flight per thread (2, 4 or 8) of the
+ * persistent update. Errors: INVALID_PARAM. */
+SSE_API int sse_batch_configure(sse_batch* b, uint32_t item_pairs, int unroll);
+
+/* Autotuner for the persistent update: times 9 configurations (item 2^18, 2^20, 2^22 x
+ * loads 2, 4, 8) on the routers' current inputs (idempotent within the slice) and keeps
+ * the fastest. times_ms: NULL or 9 floats; *chosen: index item*3 + load. Synchronous. */
+SSE_API int sse_batch_tune(sse_batch* b, const uint64_t* h_counts, int reps, float* times_ms, int* chosen);
+
+/* One slice (see above). h_counts[r] pairs of router r's input buffer are scanned; out
+ * receives the global estimator's report (may be NULL). Blocks until the report is on the
+ * host. Errors: CAPACITY (a count above capacity_pairs, or report truncated), CUDA. */
+SSE_API int sse_batch_step(sse_batch* b, const uint64_t* h_counts, sse_report* out);
+
+/* Kernels executed by the batch's steps so far. */
+SSE_API uint64_t sse_batch_kernel_launches(const sse_batch* b);
+
 /* Name of the CUDA error behind a handle's SSE_ERR_CUDA ("" if none). */
 SSE_API const char* sse_cuda_error(const sse_handle* h);
 

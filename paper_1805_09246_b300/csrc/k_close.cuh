@@ -25,8 +25,10 @@ __device__ __forceinline__ void build_active_lut(uint8_t* act, uint32_t cs, uint
 __global__ void __launch_bounds__(kCloseThreads) k_close(const __grid_constant__ KParams p,
                                                           uint8_t* __restrict__ sre, uint8_t* __restrict__ sle,
                                                           uint32_t* __restrict__ hot_bits,
-                                                          uint32_t* __restrict__ active2, uint32_t cs,
-                                                          uint32_t sre_blocks, uint32_t mode) {
+                                                          uint32_t* __restrict__ active2, uint32_t cs_value,
+                                                          const uint32_t* __restrict__ clock, uint32_t sre_blocks,
+                                                          uint32_t mode) {
+  const uint32_t cs = clock ? *clock : cs_value;
   __shared__ uint8_t act[256];
   __shared__ uint32_t warp_sum[kCloseThreads / 32];
   build_active_lut(act, cs, p.k);

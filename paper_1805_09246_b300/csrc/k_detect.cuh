@@ -299,12 +299,14 @@ constexpr int kEstThreads = 128;
 __global__ void __launch_bounds__(kEstThreads) k_estimate(
     const __grid_constant__ KParams p, const uint8_t* __restrict__ sle, const uint32_t* __restrict__ hosts,
     const uint32_t* __restrict__ n_ptr, uint32_t n, const uint32_t* __restrict__ active2, double w_theta,
-    uint32_t cs, float* __restrict__ est, uint8_t* __restrict__ flags, double* __restrict__ w_out,
+    uint32_t cs_value, const uint32_t* __restrict__ clock, float* __restrict__ est, uint8_t* __restrict__ flags,
+    double* __restrict__ w_out,
     uint32_t* __restrict__ u_out, uint32_t* __restrict__ hist, uint32_t* __restrict__ n_super) {
   __shared__ uint8_t age_lut[256];
   __shared__ uint32_t sh_hist[256];
   __shared__ uint32_t warp_u[kEstThreads / 32];
   __shared__ const uint8_t* row_base[kMaxRows];
+  const uint32_t cs = clock ? *clock : cs_value;
   for (uint32_t s = threadIdx.x; s < 256; s += blockDim.x) {
     const uint32_t a = stamp_age(s, cs);
     age_lut[s] = a < p.k ? (uint8_t)a : 255;

@@ -13,8 +13,10 @@ struct MergeSources {
 };
 
 __global__ void __launch_bounds__(256) k_merge(uint8_t* __restrict__ dst, const __grid_constant__ MergeSources src,
-                                               int nsrc, uint64_t n16, uint32_t cs) {
+                                               int nsrc, uint64_t n16, uint32_t cs_value,
+                                               const uint32_t* __restrict__ clock) {
   __shared__ uint8_t age_lut[256];
+  const uint32_t cs = clock ? *clock : cs_value;
   for (uint32_t s = threadIdx.x; s < 256; s += blockDim.x) age_lut[s] = (uint8_t)stamp_age(s, cs);
   __syncthreads();
   for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n16; x += (uint64_t)gridDim.x * blockDim.x) {

@@ -61,11 +61,14 @@ __device__ __forceinline__ void apply_pair(const KParams& p, uint32_t aip, uint3
 }
 
 // pairs: 8-byte aligned {src, dst} pairs. UNROLL 128-bit loads are in flight per thread.
+// The stamp is read from the estimator's device clock when `clock` is set, so a captured
+// CUDA graph replays correctly in later slices.
 template <int R2, int UNROLL>
 __global__ void __launch_bounds__(256) k_update_direct(const __grid_constant__ KParams p,
                                                        const uint2* __restrict__ pairs, uint64_t n,
                                                        uint8_t* __restrict__ sre, uint8_t* __restrict__ sle,
-                                                       uint8_t stamp) {
+                                                       uint32_t stamp_value, const uint32_t* __restrict__ clock) {
+  const uint8_t stamp = (uint8_t)(clock ? *clock : stamp_value);
   const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   const uint2* base = pairs;

@@ -33,7 +33,9 @@ template <int UNROLL, bool CHECK>
 __global__ void __launch_bounds__(kTiledThreads, 1) k_update_tiled(const __grid_constant__ KParams p, TileGeometry g,
                                                                    const uint2* __restrict__ pairs, uint64_t n,
                                                                    uint8_t* __restrict__ sre,
-                                                                   uint32_t* __restrict__ gbits, uint8_t stamp) {
+                                                                   uint32_t* __restrict__ gbits, uint32_t stamp_value,
+                                                                   const uint32_t* __restrict__ clock) {
+  const uint8_t stamp = (uint8_t)(clock ? *clock : stamp_value);
   extern __shared__ uint32_t bm[];
   const uint32_t tile = blockIdx.x % g.tiles;
   const uint32_t group = blockIdx.x / g.tiles;
@@ -123,7 +125,9 @@ __global__ void __launch_bounds__(kTiledThreads, 1) k_update_tiled(const __grid_
 // Stamp every SLEA cell whose bit is set and clear the bitmap. One thread per bitmap word
 // (32 cells = two 16-byte vectors of the state); each word has a single owner.
 __global__ void __launch_bounds__(256) k_apply_bits(uint32_t* __restrict__ gbits, uint8_t* __restrict__ sle,
-                                                    uint64_t n_words, uint8_t stamp) {
+                                                    uint64_t n_words, uint32_t stamp_value,
+                                                    const uint32_t* __restrict__ clock) {
+  const uint32_t stamp = clock ? *clock : stamp_value;
   for (uint64_t w = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; w < n_words;
        w += (uint64_t)gridDim.x * blockDim.x) {
     const uint32_t bits = gbits[w];

@@ -7,6 +7,7 @@
 #include <cmath>
 #include <new>
 
+#include "k_batch.cuh"
 #include "k_close.cuh"
 #include "k_detect.cuh"
 #include "k_merge.cuh"
@@ -88,6 +89,7 @@ struct sse_handle {
   int num_sms = 148;
   // device memory
   uint8_t* state = nullptr;  // RSRA then SLEA
+  uint32_t* clock = nullptr; // device copy of the current stamp, 1 + (slice mod 255)
   uint8_t* sre = nullptr;
   uint8_t* sle = nullptr;
   uint32_t* hot_bits = nullptr;
@@ -190,9 +192,9 @@ int launch_update_direct(sse_handle* h, const uint32_t* d_pairs, uint64_t n) {
   const int grid = grid_for(h, (work + kUnroll - 1) / kUnroll, 256, 8);
   const uint2* pairs = reinterpret_cast<const uint2*>(d_pairs);
   if (h->p.r2 == 5)
-    k_update_direct<5, kUnroll><<<grid, 256, 0, h->stream>>>(h->kp, pairs, n, h->sre, h->sle, stamp);
+    k_update_direct<5, kUnroll><<<grid, 256, 0, h->stream>>>(h->kp, pairs, n, h->sre, h->sle, stamp, h->clock);
   else
-    k_update_direct<0, kUnroll><<<grid, 256, 0, h->stream>>>(h->kp, pairs, n, h->sre, h->sle, stamp);
+    k_update_direct<0, kUnroll><<<grid, 256, 0, h->stream>>>(h->kp, pairs, n, h->sre, h->sle, stamp, h->clock);
   SSE_LAUNCHED(h);
   return SSE_OK;
 }
@@ -211,7 +213,8 @@ TileGeometry make_tiles(const sse_params& p, const sse_derived& d, int num_sms) 
 }
 
 // Tiled update variants: loads in flight per thread and test-before-set atomics.
-using TiledKernel = void (*)(KParams, TileGeometry, const uint2*, uint64_t, uint8_t*, uint32_t*, uint8_t);
+using TiledKernel = void (*)(KParams, TileGeometry, const uint2*, uint64_t, uint8_t*, uint32_t*, uint32_t,
+                            const uint32_t*);
 struct TiledVariant {
   TiledKernel fn;
   int unroll;
@@ -234,11 +237,11 @@ int launch_update_tiled(sse_handle* h, const uint32_t* d_pairs, uint64_t n, int 
   for (uint64_t done = 0; done < n; done += kMaxPairsPerLaunch) {
     const uint64_t m = std::min(kMaxPairsPerLaunch, n - done);
     fn<<<g.groups * g.tiles, kTiledThreads, smem, h->stream>>>(
-        h->kp, g, reinterpret_cast<const uint2*>(d_pairs + 2 * done), m, h->sre, h->sle_bits, stamp);
+        h->kp, g, reinterpret_cast<const uint2*>(d_pairs + 2 * done), m, h->sre, h->sle_bits, stamp, h->clock);
     SSE_LAUNCHED(h);
   }
   const uint64_t words = h->d.sle_bytes / 32;
-  k_apply_bits<<<grid_for(h, words, 256, 8), 256, 0, h->stream>>>(h->sle_bits, h->sle, words, stamp);
+  k_apply_bits<<<grid_for(h, words, 256, 8), 256, 0, h->stream>>>(h->sle_bits, h->sle, words, stamp, h->clock);
   SSE_LAUNCHED(h);
   return SSE_OK;
 }
@@ -268,8 +271,16 @@ int launch_close_pass(sse_handle* h, uint32_t* active2, uint32_t mode) {
   const uint64_t sle_blocks = h->d.sle_bytes / kSleBytesPerBlock;
   const uint64_t blocks = sre_blocks + sle_blocks;
   k_close<<<(unsigned)blocks, kCloseThreads, 0, h->stream>>>(h->kp, h->sre, h->sle, h->hot_bits, active2,
-                                                               stamp_of(h->slice), sre_blocks, mode);
+                                                               stamp_of(h->slice), h->clock, sre_blocks, mode);
   SSE_LAUNCHED(h);
+  return SSE_OK;
+}
+
+// Moves the handle to the next slice: the device clock on the stream, the host copy now.
+int advance_clock(sse_handle* h) {
+  k_tick<<<1, 32, 0, h->stream>>>(h->clock, 1);
+  SSE_LAUNCHED(h);
+  h->slice += 1;
   return SSE_OK;
 }
 
@@ -351,6 +362,7 @@ void sse_destroy(sse_handle* h) {
     if (h->ev_used[b]) cudaEventDestroy(h->ev_used[b]);
   }
   cudaFree(h->state);
+  cudaFree(h->clock);
   cudaFree(h->hot_bits);
   cudaFree(h->sle_bits);
   cudaFree(h->list0);
@@ -394,7 +406,7 @@ int sse_init(const sse_params* p, void* cuda_stream, sse_handle** out) {
   }
   const uint64_t state_bytes = d.sre_bytes + d.sle_bytes;
   const uint64_t list_entries = 1ull << q.q;
-  bool ok = cudaMalloc(&h->state, state_bytes) == cudaSuccess &&
+  bool ok = cudaMalloc(&h->state, state_bytes) == cudaSuccess && cudaMalloc(&h->clock, 256) == cudaSuccess &&
             cudaMalloc(&h->hot_bits, ((uint64_t)q.r << q.q) / 8) == cudaSuccess &&
             cudaMalloc(&h->sle_bits, d.sle_bytes / 8) == cudaSuccess &&
             cudaMalloc(&h->list0, list_entries * 4) == cudaSuccess &&
@@ -438,7 +450,9 @@ int sse_init(const sse_params* p, void* cuda_stream, sse_handle** out) {
       return SSE_ERR_CUDA;
     }
   }
-  if (cudaMemsetAsync(h->state, 0, state_bytes, h->stream) != cudaSuccess ||
+  const uint32_t first_stamp = stamp_of(0);
+  if (cudaMemcpyAsync(h->clock, &first_stamp, sizeof(first_stamp), cudaMemcpyHostToDevice, h->stream) != cudaSuccess ||
+      cudaMemsetAsync(h->state, 0, state_bytes, h->stream) != cudaSuccess ||
       cudaMemsetAsync(h->hot_bits, 0, ((uint64_t)q.r << q.q) / 8, h->stream) != cudaSuccess ||
       cudaMemsetAsync(h->sle_bits, 0, d.sle_bytes / 8, h->stream) != cudaSuccess ||
       cudaMemsetAsync(h->scratch, 0, sizeof(CloseScratch), h->stream) != cudaSuccess ||
@@ -579,13 +593,17 @@ int sse_advance(sse_handle* h) {
   int rc = launch_close_pass(h, h->scratch->active2, 3u);
   if (rc) return rc;
   h->stats.slice = h->slice;
-  h->slice += 1;
-  return SSE_OK;
+  return advance_clock(h);
 }
 
-int sse_close_slice(sse_handle* h, sse_report* out) {
-  if (!h) return SSE_ERR_INVALID_PARAM;
-  if (h->sticky) return h->sticky;
+}  // extern "C"
+
+namespace {
+
+// Detection kernels of a close (no host synchronisation, so a CUDA graph can hold them):
+// the sorted candidates end in *sorted, estimates and flags in h->est / h->flags, and the
+// counters are copied to the pinned h->host_scratch.
+int close_enqueue(sse_handle* h, uint32_t** sorted) {
   CloseScratch* sc = h->scratch;
   SSE_CUDA(h, cudaMemsetAsync(sc, 0, sizeof(CloseScratch), h->stream));
   int rc = launch_close_pass(h, sc->active2, 3u);
@@ -606,16 +624,21 @@ int sse_close_slice(sse_handle* h, sse_report* out) {
                                                                   &sc->overflow, h->join_smem_t2, h->join_list1_cap);
     SSE_LAUNCHED(h);
   }
-  uint32_t* sorted = launch_sort(h);
+  *sorted = launch_sort(h);
   SSE_CUDA(h, cudaGetLastError());
   {
     const int grid = grid_for(h, h->cand_cap, 1, 16);
-    k_estimate<<<grid, kEstThreads, 0, h->stream>>>(h->kp, h->sle, sorted, &sc->n_cand, h->cand_cap, sc->active2,
-                                                        h->d.w_theta, stamp_of(h->slice), h->est, h->flags, nullptr,
-                                                        nullptr, nullptr, &sc->n_super);
+    k_estimate<<<grid, kEstThreads, 0, h->stream>>>(h->kp, h->sle, *sorted, &sc->n_cand, h->cand_cap, sc->active2,
+                                                    h->d.w_theta, stamp_of(h->slice), h->clock, h->est, h->flags,
+                                                    nullptr, nullptr, nullptr, &sc->n_super);
     SSE_LAUNCHED(h);
   }
   SSE_CUDA(h, cudaMemcpyAsync(h->host_scratch, sc, sizeof(CloseScratch), cudaMemcpyDeviceToHost, h->stream));
+  return SSE_OK;
+}
+
+// Waits for an enqueued close and copies its report to the host.
+int close_collect(sse_handle* h, const uint32_t* sorted, sse_report* out) {
   SSE_CUDA(h, cudaStreamSynchronize(h->stream));
   const CloseScratch& hs = *h->host_scratch;
   const uint32_t n_found = hs.n_cand;
@@ -647,8 +670,23 @@ int sse_close_slice(sse_handle* h, sse_report* out) {
       SSE_CUDA(h, cudaStreamSynchronize(h->stream));
     }
   }
-  h->slice += 1;
   return status;
+}
+
+}  // namespace
+
+extern "C" {
+
+int sse_close_slice(sse_handle* h, sse_report* out) {
+  if (!h) return SSE_ERR_INVALID_PARAM;
+  if (h->sticky) return h->sticky;
+  uint32_t* sorted = nullptr;
+  int rc = close_enqueue(h, &sorted);
+  if (rc) return rc;
+  const int status = close_collect(h, sorted, out);
+  if (status != SSE_OK && status != SSE_ERR_CAPACITY) return status;
+  const int rc_tick = advance_clock(h);
+  return rc_tick ? rc_tick : status;
 }
 
 int sse_merge(sse_handle* dst, const sse_handle* const* srcs, int n) {
@@ -667,9 +705,9 @@ int sse_merge(sse_handle* dst, const sse_handle* const* srcs, int n) {
   }
   const uint32_t cs = stamp_of(dst->slice);
   const uint64_t n16_sre = dst->d.sre_bytes / 16, n16_sle = dst->d.sle_bytes / 16;
-  k_merge<<<grid_for(dst, n16_sre, 256, 8), 256, 0, dst->stream>>>(dst->sre, sre_src, n, n16_sre, cs);
+  k_merge<<<grid_for(dst, n16_sre, 256, 8), 256, 0, dst->stream>>>(dst->sre, sre_src, n, n16_sre, cs, dst->clock);
   SSE_LAUNCHED(dst);
-  k_merge<<<grid_for(dst, n16_sle, 256, 8), 256, 0, dst->stream>>>(dst->sle, sle_src, n, n16_sle, cs);
+  k_merge<<<grid_for(dst, n16_sle, 256, 8), 256, 0, dst->stream>>>(dst->sle, sle_src, n, n16_sle, cs, dst->clock);
   SSE_LAUNCHED(dst);
   return SSE_OK;
 }
@@ -684,7 +722,7 @@ int sse_query(sse_handle* h, const uint32_t* d_hosts, uint32_t n, float* d_est, 
   if (rc) return rc;
   const int grid = grid_for(h, n, 1, 16);
   k_estimate<<<grid, kEstThreads, 0, h->stream>>>(h->kp, h->sle, d_hosts, nullptr, n, h->query_active2,
-                                                      h->d.w_theta, stamp_of(h->slice), d_est, d_flags, nullptr,
+                                                      h->d.w_theta, stamp_of(h->slice), h->clock, d_est, d_flags, nullptr,
                                                       nullptr, d_hist, nullptr);
   SSE_LAUNCHED(h);
   return SSE_OK;
@@ -757,7 +795,9 @@ int sse_import_state(sse_handle* h, const void* h_buf, size_t n) {
     return SSE_ERR_MISMATCH;
   if (n < sizeof(hd) + hd.sre_bytes + hd.sle_bytes) return SSE_ERR_INVALID_PARAM;
   const uint8_t* body = static_cast<const uint8_t*>(h_buf) + sizeof(hd);
+  const uint32_t stamp = stamp_of(hd.slice);
   SSE_CUDA(h, cudaMemcpyAsync(h->state, body, hd.sre_bytes + hd.sle_bytes, cudaMemcpyHostToDevice, h->stream));
+  SSE_CUDA(h, cudaMemcpyAsync(h->clock, &stamp, sizeof(stamp), cudaMemcpyHostToDevice, h->stream));
   SSE_CUDA(h, cudaStreamSynchronize(h->stream));
   h->slice = hd.slice;
   return SSE_OK;
@@ -838,12 +878,284 @@ extern "C" int sse_query_noalloc(const sse_params* p, const uint8_t* d_sle, uint
   }
   const uint64_t sle_blocks = d.sle_bytes / kSleBytesPerBlock;
   k_close<<<(unsigned)sle_blocks, kCloseThreads, 0, stream>>>(kp, nullptr, const_cast<uint8_t*>(d_sle), nullptr,
-                                                                counts, stamp_of(slice), 0u, 0u);
+                                                                counts, stamp_of(slice), nullptr, 0u, 0u);
   if (cudaGetLastError() != cudaSuccess) return SSE_ERR_CUDA;
   uint64_t grid = std::min<uint64_t>((uint64_t)n, (uint64_t)num_sms * 16);
   k_estimate<<<(unsigned)grid, kEstThreads, 0, stream>>>(kp, d_sle, d_hosts, nullptr, n, counts, d.w_theta,
-                                                             stamp_of(slice), d_est, d_flags, nullptr, nullptr,
+                                                             stamp_of(slice), nullptr, d_est, d_flags, nullptr, nullptr,
                                                              nullptr, nullptr);
   if (cudaGetLastError() != cudaSuccess) return SSE_ERR_CUDA;
   return SSE_OK;
 }
+
+// ---------------------------------------------------------------------------------------
+// Multi-router batches: R router estimators and one global estimator advanced together.
+struct sse_batch {
+  int n = 0;
+  sse_params p;
+  sse_derived d;
+  cudaStream_t stream = nullptr;  // owned; graphs are captured on it
+  sse_handle* router[kMaxRouters] = {};
+  sse_handle* global = nullptr;
+  uint64_t capacity = 0;      // pairs per router input buffer
+  uint32_t* inputs = nullptr; // n * capacity pairs
+  uint64_t* d_counts = nullptr;
+  uint64_t* h_counts = nullptr;  // pinned, read by the graph's copy node
+  uint32_t* tile_next = nullptr;
+  uint32_t item_pairs = 1u << 20;
+  int unroll = 4;
+  RouterTable rt;
+  int use_graph = 1;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  uint32_t* sorted = nullptr;     // global's sorted candidates (fixed per configuration)
+  uint64_t kernels_per_step = 0;
+  uint64_t launches = 0;
+};
+
+namespace {
+
+using RoutersKernel = void (*)(KParams, TileGeometry, RouterTable, int, uint64_t, const uint64_t*, uint32_t, uint32_t*,
+                               const uint32_t*);
+
+RoutersKernel routers_kernel(int unroll) {
+  return unroll == 2 ? k_update_routers<2> : unroll == 8 ? k_update_routers<8> : k_update_routers<4>;
+}
+
+// Update of every router (one persistent launch) and the bitmap apply, on b->stream.
+int batch_enqueue_update(sse_batch* b) {
+  sse_handle* g = b->global;
+  SSE_CUDA(g, cudaMemcpyAsync(b->d_counts, b->h_counts, b->n * sizeof(uint64_t), cudaMemcpyHostToDevice, b->stream));
+  const TileGeometry& tg = g->tiles;
+  SSE_CUDA(g, cudaMemsetAsync(b->tile_next, 0, tg.tiles * sizeof(uint32_t), b->stream));
+  const uint32_t per_tile = std::max<uint32_t>(1u, (uint32_t)g->num_sms / tg.tiles);
+  routers_kernel(b->unroll)<<<tg.tiles * per_tile, kTiledThreads, tg.piece_bytes / 8, b->stream>>>(
+      g->kp, tg, b->rt, b->n, g->d.sre_bytes, b->d_counts, b->item_pairs, b->tile_next, g->clock);
+  SSE_LAUNCHED(g);
+  const uint64_t words = g->d.sle_bytes / 32;
+  const dim3 grid(grid_for(g, words, 256, 2), b->n);
+  k_apply_routers<<<grid, 256, 0, b->stream>>>(b->rt, g->d.sre_bytes, words, g->clock);
+  SSE_LAUNCHED(g);
+  return SSE_OK;
+}
+
+// One slice: update all routers, merge them (with their expiry) into the global estimator,
+// detect on it, and advance every clock.
+int batch_enqueue_step(sse_batch* b) {
+  sse_handle* g = b->global;
+  int rc = batch_enqueue_update(b);
+  if (rc) return rc;
+  const uint64_t n16 = (g->d.sre_bytes + g->d.sle_bytes) / 16;
+  k_merge_routers<<<grid_for(g, n16, 256, 8), 256, 0, b->stream>>>(g->state, b->rt, b->n, n16, g->p.k, g->clock);
+  SSE_LAUNCHED(g);
+  rc = close_enqueue(g, &b->sorted);
+  if (rc) return rc;
+  ClockList cl;
+  for (int r = 0; r < b->n; ++r) cl.c[r] = b->router[r]->clock;
+  cl.c[b->n] = g->clock;
+  k_tick_list<<<1, 128, 0, b->stream>>>(cl, b->n + 1);
+  SSE_LAUNCHED(g);
+  return SSE_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void sse_batch_destroy(sse_batch* b) {
+  if (!b) return;
+  if (b->stream) cudaStreamSynchronize(b->stream);
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  for (int r = 0; r < b->n; ++r) sse_destroy(b->router[r]);
+  sse_destroy(b->global);
+  cudaFree(b->inputs);
+  cudaFree(b->d_counts);
+  cudaFree(b->tile_next);
+  if (b->h_counts) cudaFreeHost(b->h_counts);
+  if (b->stream) cudaStreamDestroy(b->stream);
+  delete b;
+}
+
+int sse_batch_create(const sse_params* p, int n_routers, uint64_t capacity_pairs, sse_batch** out) {
+  if (!p || !out || n_routers < 1 || n_routers > kMaxRouters || capacity_pairs == 0) return SSE_ERR_INVALID_PARAM;
+  *out = nullptr;
+  sse_params q;
+  sse_derived d;
+  int rc = derive_params(*p, q, d);
+  if (rc) return rc;
+  sse_batch* b = new (std::nothrow) sse_batch();
+  if (!b) return SSE_ERR_OOM;
+  b->n = n_routers;
+  b->p = q;
+  b->d = d;
+  b->capacity = capacity_pairs;
+  if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    delete b;
+    return SSE_ERR_CUDA;
+  }
+  for (int r = 0; r < n_routers && rc == SSE_OK; ++r) rc = sse_init(p, b->stream, &b->router[r]);
+  if (rc == SSE_OK) rc = sse_init(p, b->stream, &b->global);
+  if (rc == SSE_OK) {
+    const bool ok = cudaMalloc(&b->inputs, (uint64_t)n_routers * capacity_pairs * 8) == cudaSuccess &&
+                    cudaMalloc(&b->d_counts, kMaxRouters * sizeof(uint64_t)) == cudaSuccess &&
+                    cudaMalloc(&b->tile_next, b->global->tiles.tiles * sizeof(uint32_t)) == cudaSuccess &&
+                    cudaMallocHost(&b->h_counts, kMaxRouters * sizeof(uint64_t)) == cudaSuccess;
+    if (!ok) {
+      cudaGetLastError();
+      rc = SSE_ERR_OOM;
+    }
+  }
+  if (rc == SSE_OK) {
+    for (int v = 2; v <= 8; v *= 2)
+      if (cudaFuncSetAttribute(routers_kernel(v), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)(b->global->tiles.piece_bytes / 8)) != cudaSuccess) {
+        cudaGetLastError();
+        rc = SSE_ERR_CUDA;
+      }
+  }
+  if (rc != SSE_OK) {
+    sse_batch_destroy(b);
+    return rc;
+  }
+  memset(&b->rt, 0, sizeof(b->rt));
+  for (int r = 0; r < n_routers; ++r) {
+    b->rt.pairs[r] = reinterpret_cast<const uint2*>(b->inputs + 2 * (uint64_t)r * capacity_pairs);
+    b->rt.state[r] = b->router[r]->state;
+    b->rt.gbits[r] = b->router[r]->sle_bits;
+  }
+  memset(b->h_counts, 0, kMaxRouters * sizeof(uint64_t));
+  *out = b;
+  return SSE_OK;
+}
+
+uint32_t* sse_batch_input(sse_batch* b, int router) {
+  if (!b || router < 0 || router >= b->n) return nullptr;
+  return b->inputs + 2 * (uint64_t)router * b->capacity;
+}
+
+void* sse_batch_stream(sse_batch* b) { return b ? (void*)b->stream : nullptr; }
+
+int sse_batch_load(sse_batch* b, int router, const uint32_t* pairs, uint64_t n_pairs, int from_host) {
+  if (!b || router < 0 || router >= b->n || (!pairs && n_pairs)) return SSE_ERR_INVALID_PARAM;
+  if (n_pairs > b->capacity) return SSE_ERR_CAPACITY;
+  if (!n_pairs) return SSE_OK;
+  SSE_CUDA(b->global, cudaMemcpyAsync(sse_batch_input(b, router), pairs, n_pairs * 8,
+                                      from_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, b->stream));
+  SSE_CUDA(b->global, cudaStreamSynchronize(b->stream));
+  return SSE_OK;
+}
+
+int sse_batch_router(sse_batch* b, int router, sse_handle** out) {
+  if (!b || !out || router < 0 || router >= b->n) return SSE_ERR_INVALID_PARAM;
+  *out = b->router[router];
+  return SSE_OK;
+}
+
+int sse_batch_global(sse_batch* b, sse_handle** out) {
+  if (!b || !out) return SSE_ERR_INVALID_PARAM;
+  *out = b->global;
+  return SSE_OK;
+}
+
+int sse_batch_use_graph(sse_batch* b, int enable) {
+  if (!b) return SSE_ERR_INVALID_PARAM;
+  b->use_graph = enable ? 1 : 0;
+  return SSE_OK;
+}
+
+int sse_batch_configure(sse_batch* b, uint32_t item_pairs, int unroll) {
+  if (!b || item_pairs < 1024 || item_pairs > (1u << 30) || (unroll != 2 && unroll != 4 && unroll != 8))
+    return SSE_ERR_INVALID_PARAM;
+  b->item_pairs = item_pairs;
+  b->unroll = unroll;
+  if (b->exec) {  // the captured graph holds the old launch configuration
+    cudaGraphExecDestroy(b->exec);
+    cudaGraphDestroy(b->graph);
+    b->exec = nullptr;
+    b->graph = nullptr;
+  }
+  return SSE_OK;
+}
+
+int sse_batch_step(sse_batch* b, const uint64_t* h_counts, sse_report* out) {
+  if (!b || !h_counts) return SSE_ERR_INVALID_PARAM;
+  sse_handle* g = b->global;
+  if (g->sticky) return g->sticky;
+  for (int r = 0; r < b->n; ++r) {
+    if (h_counts[r] > b->capacity) return SSE_ERR_CAPACITY;
+    if (b->router[r]->sticky) return b->router[r]->sticky;
+  }
+  memcpy(b->h_counts, h_counts, b->n * sizeof(uint64_t));  // the copy node reads this pinned array
+  const uint64_t launches0 = g->launches;
+  if (b->use_graph) {
+    if (!b->exec) {
+      SSE_CUDA(g, cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+      const int rc = batch_enqueue_step(b);
+      cudaGraph_t graph = nullptr;
+      const cudaError_t e = cudaStreamEndCapture(b->stream, &graph);
+      if (rc) {
+        if (graph) cudaGraphDestroy(graph);
+        return rc;
+      }
+      SSE_CUDA(g, e);
+      b->graph = graph;
+      SSE_CUDA(g, cudaGraphInstantiate(&b->exec, b->graph, 0));
+      b->kernels_per_step = g->launches - launches0;
+      g->launches = launches0;
+    }
+    SSE_CUDA(g, cudaGraphLaunch(b->exec, b->stream));
+  } else {
+    const int rc = batch_enqueue_step(b);
+    if (rc) return rc;
+    b->kernels_per_step = g->launches - launches0;
+    g->launches = launches0;
+  }
+  b->launches += b->kernels_per_step;
+  const int status = close_collect(g, b->sorted, out);
+  if (status != SSE_OK && status != SSE_ERR_CAPACITY) return status;
+  for (int r = 0; r < b->n; ++r) b->router[r]->slice += 1;
+  g->slice += 1;
+  return status;
+}
+
+int sse_batch_tune(sse_batch* b, const uint64_t* h_counts, int reps, float* times_ms, int* chosen) {
+  if (!b || !h_counts || reps < 1) return SSE_ERR_INVALID_PARAM;
+  sse_handle* g = b->global;
+  memcpy(b->h_counts, h_counts, b->n * sizeof(uint64_t));
+  const uint32_t items[3] = {1u << 18, 1u << 20, 1u << 22};
+  const int unrolls[3] = {2, 4, 8};
+  cudaEvent_t e0, e1;
+  SSE_CUDA(g, cudaEventCreate(&e0));
+  SSE_CUDA(g, cudaEventCreate(&e1));
+  int best = -1, rc = SSE_OK;
+  float best_ms = 0.f;
+  for (int c = 0; c < 9 && rc == SSE_OK; ++c) {
+    b->item_pairs = items[c / 3];
+    b->unroll = unrolls[c % 3];
+    rc = batch_enqueue_update(b);  // the routers' pairs belong to the current slice: idempotent
+    if (rc == SSE_OK && cudaEventRecord(e0, b->stream) != cudaSuccess) rc = fail(g, cudaGetLastError());
+    for (int r = 0; r < reps && rc == SSE_OK; ++r) rc = batch_enqueue_update(b);
+    if (rc == SSE_OK && (cudaEventRecord(e1, b->stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess))
+      rc = fail(g, cudaGetLastError());
+    if (rc) break;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    ms /= reps;
+    if (times_ms) times_ms[c] = ms;
+    if (best < 0 || ms < best_ms) {
+      best = c;
+      best_ms = ms;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc) return rc;
+  if (chosen) *chosen = best;
+  return sse_batch_configure(b, items[best / 3], unrolls[best % 3]);
+}
+
+uint64_t sse_batch_kernel_launches(const sse_batch* b) { return b ? b->launches : 0; }
+
+}  // extern "C"

@@ -48,6 +48,13 @@ __host__ __device__ __forceinline__ uint32_t stamp_age(uint32_t s, uint32_t cs) 
   return (cs + 255 - s) % 255;
 }
 
+// The estimator's device clock holds the current stamp; advancing a slice moves it along the
+// 1..255 cycle on the device, so launches read the right stamp even when replayed.
+__global__ void k_tick(uint32_t* clock, uint32_t n) {
+  if (threadIdx.x == 0 && blockIdx.x == 0)
+    for (uint32_t i = 0; i < n; ++i) clock[i] = clock[i] % 255u + 1u;
+}
+
 // Scratch counters of one close, zeroed before it (one cudaMemsetAsync).
 struct CloseScratch {
   uint32_t active2[kMaxRows];  // active cells of each SLEA row

@@ -122,6 +122,18 @@ def lib() -> ctypes.CDLL:
             "sse_kernel_launches": (u64, [vp]),
             "sse_sync": (i32, [vp]),
             "sse_strerror": (ctypes.c_char_p, [i32]),
+            "sse_batch_create": (i32, [vp, i32, u64, ctypes.POINTER(vp)]),
+            "sse_batch_destroy": (None, [vp]),
+            "sse_batch_input": (vp, [vp, i32]),
+            "sse_batch_stream": (vp, [vp]),
+            "sse_batch_load": (i32, [vp, i32, vp, u64, i32]),
+            "sse_batch_router": (i32, [vp, i32, ctypes.POINTER(vp)]),
+            "sse_batch_global": (i32, [vp, ctypes.POINTER(vp)]),
+            "sse_batch_use_graph": (i32, [vp, i32]),
+            "sse_batch_configure": (i32, [vp, u32, i32]),
+            "sse_batch_tune": (i32, [vp, vp, i32, vp, ctypes.POINTER(i32)]),
+            "sse_batch_step": (i32, [vp, vp, vp]),
+            "sse_batch_kernel_launches": (u64, [vp]),
             "sse_cuda_error": (ctypes.c_char_p, [vp]),
         }
         for name, (res, args) in sig.items():
@@ -195,6 +207,18 @@ def _dev_ptr(t, dtype_bytes: int | None = None) -> int:
 class Estimator:
     """One router's estimator (RSRA + SLEA) resident on the current CUDA device."""
 
+    @classmethod
+    def _borrowed(cls, params: Params, handle: ctypes.c_void_p) -> "Estimator":
+        """A view of an estimator owned elsewhere (a batch's router or global estimator)."""
+        e = cls.__new__(cls)
+        e.params = params
+        e._lib = lib()
+        e.derived = derive(params)
+        e.stream = None
+        e._h = handle
+        e._borrowed_handle = True
+        return e
+
     def __init__(self, params: Params | None = None, stream=None):
         torch = _torch()
         self.params = params or Params()
@@ -206,6 +230,9 @@ class Estimator:
                                   ctypes.byref(self._h)), "sse_init")
 
     def close(self) -> None:
+        if getattr(self, "_borrowed_handle", False):
+            self._h = None
+            return
         if getattr(self, "_h", None) is not None and self._h.value:
             self._lib.sse_destroy(self._h)
             self._h = None
@@ -334,3 +361,95 @@ class Estimator:
 
     def sync(self) -> None:
         _check(self._lib.sse_sync(self._h), "sse_sync")
+
+
+class Batch:
+    """R routers' estimators plus their merged global estimator, advanced slice by slice
+    with one persistent update launch per slice and a CUDA-graph-captured step."""
+
+    def __init__(self, params: Params, n_routers: int, capacity_pairs: int, use_graph: bool = True):
+        _torch()
+        self.params = params
+        self.n = n_routers
+        self.capacity = capacity_pairs
+        self._lib = lib()
+        self._b = ctypes.c_void_p()
+        _check(self._lib.sse_batch_create(ctypes.byref(params.to_c()), n_routers, capacity_pairs,
+                                          ctypes.byref(self._b)), "sse_batch_create")
+        self._lib.sse_batch_use_graph(self._b, 1 if use_graph else 0)
+        self._views = {}
+
+    def close(self) -> None:
+        if getattr(self, "_b", None) is not None and self._b.value:
+            for v in self._views.values():
+                v.close()
+            self._lib.sse_batch_destroy(self._b)
+            self._b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def stream_ptr(self) -> int:
+        return int(self._lib.sse_batch_stream(self._b) or 0)
+
+    def load(self, router: int, pairs) -> int:
+        """Copy a router's pairs (CUDA tensor, numpy array or CPU tensor) into its input."""
+        if isinstance(pairs, np.ndarray):
+            a = np.ascontiguousarray(pairs).view(np.uint32).reshape(-1)
+            ptr, n, host = a.ctypes.data, a.size // 2, 1
+            self._keep = a
+        elif pairs.is_cuda:
+            _torch().cuda.current_stream().synchronize()  # the batch copies on its own stream
+            ptr, n, host = _dev_ptr(pairs, 4), pairs.numel() // 2, 0
+        else:
+            ptr, n, host = pairs.data_ptr(), pairs.numel() // 2, 1
+        _check(self._lib.sse_batch_load(self._b, router, ctypes.c_void_p(ptr), n, host), "sse_batch_load")
+        return n
+
+    def configure(self, item_pairs: int, unroll: int) -> None:
+        _check(self._lib.sse_batch_configure(self._b, item_pairs, unroll), "sse_batch_configure")
+
+    def tune(self, counts, reps: int = 2) -> tuple[int, list[float]]:
+        c = np.ascontiguousarray(counts, dtype=np.uint64)
+        times = (ctypes.c_float * 9)()
+        chosen = ctypes.c_int(-1)
+        _check(self._lib.sse_batch_tune(self._b, ctypes.c_void_p(c.ctypes.data), reps, times, ctypes.byref(chosen)),
+               "sse_batch_tune")
+        return chosen.value, [float(t) for t in times]
+
+    def step(self, counts, cap: int | None = None) -> Report:
+        c = np.ascontiguousarray(counts, dtype=np.uint64)
+        cap = self.params.max_candidates if cap is None else cap
+        hosts = np.zeros(cap, np.uint32)
+        est = np.zeros(cap, np.float32)
+        flags = np.zeros(cap, np.uint8)
+        rep = _Report(0, 0, 0, cap, 0, hosts.ctypes.data, est.ctypes.data, flags.ctypes.data)
+        rc = self._lib.sse_batch_step(self._b, ctypes.c_void_p(c.ctypes.data), ctypes.byref(rep))
+        if rc != SSE_OK and rc != ERR_CAPACITY:
+            _check(rc, "sse_batch_step")
+        m = min(rep.n_candidates, cap, self.params.max_candidates)
+        return Report(slice=rep.slice, n_candidates=rep.n_candidates, n_super=rep.n_super,
+                      truncated=bool(rep.truncated), hosts=hosts[:m].copy(), est=est[:m].copy(),
+                      flags=flags[:m].copy(), status=rc)
+
+    def router(self, r: int) -> Estimator:
+        if r not in self._views:
+            h = ctypes.c_void_p()
+            _check(self._lib.sse_batch_router(self._b, r, ctypes.byref(h)), "sse_batch_router")
+            self._views[r] = Estimator._borrowed(self.params, h)
+        return self._views[r]
+
+    def global_estimator(self) -> Estimator:
+        if "global" not in self._views:
+            h = ctypes.c_void_p()
+            _check(self._lib.sse_batch_global(self._b, ctypes.byref(h)), "sse_batch_global")
+            self._views["global"] = Estimator._borrowed(self.params, h)
+        return self._views["global"]
+
+    @property
+    def kernel_launches(self) -> int:
+        return int(self._lib.sse_batch_kernel_launches(self._b))

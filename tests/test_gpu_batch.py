@@ -1,0 +1,113 @@
+"""Multi-router batches: one persistent update launch per slice, merge into the global
+estimator, detection, CUDA-graph replay — checked against separate estimators driven
+through the single-router API and against the oracle's routers and merge."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1805_09246_b300 import synth
+from tests import helpers
+from tests.test_gpu_parity import compare_report, compare_state, oracle_params
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def sse():
+    from paper_1805_09246_b300 import sse as mod
+    return mod
+
+
+def router_traffic(n_routers, n_slices, seed):
+    cfg = synth.TrafficConfig(seed=seed, n_slices=n_slices, n_routers=n_routers, load_min=1 << 12,
+                              load_max=1 << 17, n_sources=20_000, n_planted=12, planted_min=1500,
+                              planted_max=6000, group_min=1, group_max=min(3, n_routers))
+    tr = synth.Traffic(cfg)
+    return [[tr.slice(r, t) for r in range(n_routers)] for t in range(n_slices)]
+
+
+def run_reference(p, slices):
+    """The same work through the single-router API: routers, global merge, global close."""
+    S = sse()
+    routers = [S.Estimator(p) for _ in slices[0]]
+    glob = S.Estimator(p)
+    reports = []
+    for t, per_router in enumerate(slices):
+        for e, pairs in zip(routers, per_router):
+            if len(pairs):
+                e.update(helpers.to_device(pairs))
+        glob.merge(routers)
+        reports.append(glob.close_slice())
+        for e in routers:
+            e.advance()
+    return routers, glob, reports
+
+
+@pytest.mark.parametrize("graph", [True, False])
+def test_batch_matches_single_router_api_and_oracle(graph):
+    S = sse()
+    p = S.Params(seed=31)
+    R, T = 5, 6
+    slices = router_traffic(R, T, seed=31)
+    cap = max(len(x) for s in slices for x in s)
+    batch = S.Batch(p, R, cap, use_graph=graph)
+    _, ref_glob, ref_reports = run_reference(p, slices)
+    orcs = [oracle.Oracle(oracle_params(p)) for _ in range(R)]
+    og = oracle.Oracle(oracle_params(p))
+    for t, per_router in enumerate(slices):
+        for r, pairs in enumerate(per_router):
+            batch.load(r, helpers.to_device(pairs) if len(pairs) else pairs)
+        rep = batch.step([len(x) for x in per_router])
+        ref = ref_reports[t]
+        assert np.array_equal(rep.hosts, ref.hosts) and np.array_equal(rep.flags, ref.flags)
+        assert np.array_equal(rep.est, ref.est)
+        # oracle: routers scan, the global estimator merges them and detects
+        for o, pairs in zip(orcs, per_router):
+            if t:
+                o.advance()
+            o.scan(pairs)
+        if t:
+            og.advance()
+        og.merge(orcs)
+        compare_report(rep, og.detect())
+    compare_state(batch.global_estimator(), og, p, T - 1)
+    for r in range(R):
+        compare_state(batch.router(r), orcs[r], p, T - 1)
+    assert batch.router(0).slice == T and batch.global_estimator().slice == T
+    assert batch.kernel_launches > 0
+
+
+def test_batch_graph_replay_equals_direct_launches_and_tuning_keeps_results():
+    S = sse()
+    p = S.Params(seed=32)
+    R, T = 4, 5
+    slices = router_traffic(R, T, seed=32)
+    cap = max(len(x) for s in slices for x in s)
+    a = S.Batch(p, R, cap, use_graph=True)
+    b = S.Batch(p, R, cap, use_graph=False)
+    for t, per_router in enumerate(slices):
+        counts = [len(x) for x in per_router]
+        for r, pairs in enumerate(per_router):
+            a.load(r, pairs)
+            b.load(r, pairs)
+        if t == 1:
+            chosen, times = b.tune(counts)
+            assert 0 <= chosen < 9 and all(x > 0 for x in times)
+        ra, rb = a.step(counts), b.step(counts)
+        assert np.array_equal(ra.hosts, rb.hosts) and np.array_equal(ra.est, rb.est)
+        assert np.array_equal(ra.flags, rb.flags)
+    for x, y in zip(a.global_estimator().read_stamps(), b.global_estimator().read_stamps()):
+        assert np.array_equal(x, y)
+
+
+def test_batch_rejects_counts_above_capacity_and_handles_empty_routers():
+    S = sse()
+    p = S.Params(seed=33)
+    batch = S.Batch(p, 3, 1000)
+    with pytest.raises(S.SSEError):
+        batch.load(0, np.zeros((1001, 2), np.uint32))
+    assert batch.step([0, 0, 0]).n_candidates == 0
+    from paper_1805_09246_b300.sse import lib
+    import ctypes
+    counts = np.array([5, 2000, 0], np.uint64)
+    assert lib().sse_batch_step(batch._b, ctypes.c_void_p(counts.ctypes.data), None) == S.ERR_CAPACITY
