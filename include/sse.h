@@ -330,13 +330,21 @@ SSE_API int sse_batch_configure(sse_batch* b, uint32_t item_pairs, int unroll);
 
 /* Autotuner for the persistent update: times 9 configurations (item 2^18, 2^20, 2^22 x
  * loads 2, 4, 8) on the routers' current inputs (idempotent within the slice) and keeps
- * the fastest. times_ms: NULL or 9 floats; *chosen: index item*3 + load. Synchronous. */
-SSE_API int sse_batch_tune(sse_batch* b, const uint64_t* h_counts, int reps, float* times_ms, int* chosen);
+ * the fastest. d_pairs: NULL (the routers' input buffers) or one device pointer per router;
+ * times_ms: NULL or 9 floats; *chosen: index item*3 + load. Synchronous. */
+SSE_API int sse_batch_tune(sse_batch* b, const uint32_t* const* d_pairs, const uint64_t* h_counts, int reps,
+                           float* times_ms, int* chosen);
 
 /* One slice (see above). h_counts[r] pairs of router r's input buffer are scanned; out
  * receives the global estimator's report (may be NULL). Blocks until the report is on the
  * host. Errors: CAPACITY (a count above capacity_pairs, or report truncated), CUDA. */
 SSE_API int sse_batch_step(sse_batch* b, const uint64_t* h_counts, sse_report* out);
+
+/* sse_batch_step() reading router r's h_counts[r] pairs from the caller's device buffer
+ * d_pairs[r] (8-byte aligned; written before the call, since the batch runs on its own
+ * stream) instead of the batch's input buffers. Errors: INVALID_PARAM, CAPACITY, CUDA. */
+SSE_API int sse_batch_step_from(sse_batch* b, const uint32_t* const* d_pairs, const uint64_t* h_counts,
+                                sse_report* out);
 
 /* Kernels executed by the batch's steps so far. */
 SSE_API uint64_t sse_batch_kernel_launches(const sse_batch* b);

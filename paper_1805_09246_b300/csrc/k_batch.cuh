@@ -18,16 +18,23 @@ namespace sse {
 constexpr int kMaxRouters = 64;
 
 struct RouterTable {
-  const uint2* pairs[kMaxRouters];  // each router's input pairs
-  uint8_t* state[kMaxRouters];      // RSRA then SLEA of each router
-  uint32_t* gbits[kMaxRouters];     // each router's SLEA touched-cell bitmap
+  uint8_t* state[kMaxRouters];   // RSRA then SLEA of each router
+  uint32_t* gbits[kMaxRouters];  // each router's SLEA touched-cell bitmap
+};
+
+// Per-step inputs in device memory (refreshed by a copy before every step, so a captured
+// graph reads the current pointers and counts).
+struct RouterInputs {
+  const uint2* pairs[kMaxRouters];
+  uint64_t counts[kMaxRouters];
 };
 
 template <int UNROLL>
 __global__ void __launch_bounds__(kTiledThreads, 1)
     k_update_routers(const __grid_constant__ KParams p, TileGeometry g, const __grid_constant__ RouterTable rt,
-                     int n_routers, uint64_t sre_bytes, const uint64_t* __restrict__ counts, uint32_t item_pairs,
+                     int n_routers, uint64_t sre_bytes, const RouterInputs* __restrict__ in, uint32_t item_pairs,
                      uint32_t* __restrict__ tile_next, const uint32_t* __restrict__ clock) {
+  const uint64_t* counts = in->counts;
   extern __shared__ uint32_t bm[];
   __shared__ uint64_t first_item[kMaxRouters + 1];
   __shared__ uint32_t sh_item;
@@ -83,7 +90,7 @@ __global__ void __launch_bounds__(kTiledThreads, 1)
     const uint64_t begin = chunk * item_pairs;
     const uint64_t end = min(begin + item_pairs, counts[r]);
     const bool rsra = (uint32_t)(chunk % g.tiles) == tile;
-    const uint2* pairs = rt.pairs[r];
+    const uint2* pairs = in->pairs[r];
     uint8_t* sre = rt.state[r];
     uint64_t j0 = begin;
     if (j0 < end && (reinterpret_cast<uintptr_t>(pairs + j0) & 15u)) {

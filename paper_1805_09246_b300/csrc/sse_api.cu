@@ -899,8 +899,8 @@ struct sse_batch {
   sse_handle* global = nullptr;
   uint64_t capacity = 0;      // pairs per router input buffer
   uint32_t* inputs = nullptr; // n * capacity pairs
-  uint64_t* d_counts = nullptr;
-  uint64_t* h_counts = nullptr;  // pinned, read by the graph's copy node
+  RouterInputs* d_in = nullptr;  // per-step input pointers and counts (device)
+  RouterInputs* h_in = nullptr;  // pinned copy, read by the step's copy node
   uint32_t* tile_next = nullptr;
   uint32_t item_pairs = 1u << 20;
   int unroll = 4;
@@ -915,8 +915,8 @@ struct sse_batch {
 
 namespace {
 
-using RoutersKernel = void (*)(KParams, TileGeometry, RouterTable, int, uint64_t, const uint64_t*, uint32_t, uint32_t*,
-                               const uint32_t*);
+using RoutersKernel = void (*)(KParams, TileGeometry, RouterTable, int, uint64_t, const RouterInputs*, uint32_t,
+                               uint32_t*, const uint32_t*);
 
 RoutersKernel routers_kernel(int unroll) {
   return unroll == 2 ? k_update_routers<2> : unroll == 8 ? k_update_routers<8> : k_update_routers<4>;
@@ -925,12 +925,12 @@ RoutersKernel routers_kernel(int unroll) {
 // Update of every router (one persistent launch) and the bitmap apply, on b->stream.
 int batch_enqueue_update(sse_batch* b) {
   sse_handle* g = b->global;
-  SSE_CUDA(g, cudaMemcpyAsync(b->d_counts, b->h_counts, b->n * sizeof(uint64_t), cudaMemcpyHostToDevice, b->stream));
+  SSE_CUDA(g, cudaMemcpyAsync(b->d_in, b->h_in, sizeof(RouterInputs), cudaMemcpyHostToDevice, b->stream));
   const TileGeometry& tg = g->tiles;
   SSE_CUDA(g, cudaMemsetAsync(b->tile_next, 0, tg.tiles * sizeof(uint32_t), b->stream));
   const uint32_t per_tile = std::max<uint32_t>(1u, (uint32_t)g->num_sms / tg.tiles);
   routers_kernel(b->unroll)<<<tg.tiles * per_tile, kTiledThreads, tg.piece_bytes / 8, b->stream>>>(
-      g->kp, tg, b->rt, b->n, g->d.sre_bytes, b->d_counts, b->item_pairs, b->tile_next, g->clock);
+      g->kp, tg, b->rt, b->n, g->d.sre_bytes, b->d_in, b->item_pairs, b->tile_next, g->clock);
   SSE_LAUNCHED(g);
   const uint64_t words = g->d.sle_bytes / 32;
   const dim3 grid(grid_for(g, words, 256, 2), b->n);
@@ -970,9 +970,9 @@ void sse_batch_destroy(sse_batch* b) {
   for (int r = 0; r < b->n; ++r) sse_destroy(b->router[r]);
   sse_destroy(b->global);
   cudaFree(b->inputs);
-  cudaFree(b->d_counts);
+  cudaFree(b->d_in);
   cudaFree(b->tile_next);
-  if (b->h_counts) cudaFreeHost(b->h_counts);
+  if (b->h_in) cudaFreeHost(b->h_in);
   if (b->stream) cudaStreamDestroy(b->stream);
   delete b;
 }
@@ -999,9 +999,9 @@ int sse_batch_create(const sse_params* p, int n_routers, uint64_t capacity_pairs
   if (rc == SSE_OK) rc = sse_init(p, b->stream, &b->global);
   if (rc == SSE_OK) {
     const bool ok = cudaMalloc(&b->inputs, (uint64_t)n_routers * capacity_pairs * 8) == cudaSuccess &&
-                    cudaMalloc(&b->d_counts, kMaxRouters * sizeof(uint64_t)) == cudaSuccess &&
+                    cudaMalloc(&b->d_in, sizeof(RouterInputs)) == cudaSuccess &&
                     cudaMalloc(&b->tile_next, b->global->tiles.tiles * sizeof(uint32_t)) == cudaSuccess &&
-                    cudaMallocHost(&b->h_counts, kMaxRouters * sizeof(uint64_t)) == cudaSuccess;
+                    cudaMallocHost(&b->h_in, sizeof(RouterInputs)) == cudaSuccess;
     if (!ok) {
       cudaGetLastError();
       rc = SSE_ERR_OOM;
@@ -1021,11 +1021,10 @@ int sse_batch_create(const sse_params* p, int n_routers, uint64_t capacity_pairs
   }
   memset(&b->rt, 0, sizeof(b->rt));
   for (int r = 0; r < n_routers; ++r) {
-    b->rt.pairs[r] = reinterpret_cast<const uint2*>(b->inputs + 2 * (uint64_t)r * capacity_pairs);
     b->rt.state[r] = b->router[r]->state;
     b->rt.gbits[r] = b->router[r]->sle_bits;
   }
-  memset(b->h_counts, 0, kMaxRouters * sizeof(uint64_t));
+  memset(b->h_in, 0, sizeof(RouterInputs));
   *out = b;
   return SSE_OK;
 }
@@ -1079,15 +1078,21 @@ int sse_batch_configure(sse_batch* b, uint32_t item_pairs, int unroll) {
   return SSE_OK;
 }
 
-int sse_batch_step(sse_batch* b, const uint64_t* h_counts, sse_report* out) {
-  if (!b || !h_counts) return SSE_ERR_INVALID_PARAM;
+}  // extern "C"
+
+namespace {
+
+int batch_step(sse_batch* b, const uint32_t* const* d_pairs, const uint64_t* h_counts, sse_report* out) {
   sse_handle* g = b->global;
   if (g->sticky) return g->sticky;
   for (int r = 0; r < b->n; ++r) {
-    if (h_counts[r] > b->capacity) return SSE_ERR_CAPACITY;
     if (b->router[r]->sticky) return b->router[r]->sticky;
+    if (h_counts[r] && (!d_pairs[r] || (reinterpret_cast<uintptr_t>(d_pairs[r]) & 7u))) return SSE_ERR_INVALID_PARAM;
   }
-  memcpy(b->h_counts, h_counts, b->n * sizeof(uint64_t));  // the copy node reads this pinned array
+  for (int r = 0; r < b->n; ++r) {  // the step's copy node reads this pinned table
+    b->h_in->pairs[r] = reinterpret_cast<const uint2*>(d_pairs[r]);
+    b->h_in->counts[r] = h_counts[r];
+  }
   const uint64_t launches0 = g->launches;
   if (b->use_graph) {
     if (!b->exec) {
@@ -1120,10 +1125,34 @@ int sse_batch_step(sse_batch* b, const uint64_t* h_counts, sse_report* out) {
   return status;
 }
 
-int sse_batch_tune(sse_batch* b, const uint64_t* h_counts, int reps, float* times_ms, int* chosen) {
+}  // namespace
+
+extern "C" {
+
+int sse_batch_step(sse_batch* b, const uint64_t* h_counts, sse_report* out) {
+  if (!b || !h_counts) return SSE_ERR_INVALID_PARAM;
+  const uint32_t* ptrs[kMaxRouters];
+  for (int r = 0; r < b->n; ++r) {
+    if (h_counts[r] > b->capacity) return SSE_ERR_CAPACITY;
+    ptrs[r] = sse_batch_input(b, r);
+  }
+  return batch_step(b, ptrs, h_counts, out);
+}
+
+int sse_batch_step_from(sse_batch* b, const uint32_t* const* d_pairs, const uint64_t* h_counts, sse_report* out) {
+  if (!b || !d_pairs || !h_counts) return SSE_ERR_INVALID_PARAM;
+  return batch_step(b, d_pairs, h_counts, out);
+}
+
+int sse_batch_tune(sse_batch* b, const uint32_t* const* d_pairs, const uint64_t* h_counts, int reps, float* times_ms,
+                   int* chosen) {
   if (!b || !h_counts || reps < 1) return SSE_ERR_INVALID_PARAM;
   sse_handle* g = b->global;
-  memcpy(b->h_counts, h_counts, b->n * sizeof(uint64_t));
+  for (int r = 0; r < b->n; ++r) {
+    if (!d_pairs && h_counts[r] > b->capacity) return SSE_ERR_CAPACITY;
+    b->h_in->pairs[r] = reinterpret_cast<const uint2*>(d_pairs ? d_pairs[r] : sse_batch_input(b, r));
+    b->h_in->counts[r] = h_counts[r];
+  }
   const uint32_t items[3] = {1u << 18, 1u << 20, 1u << 22};
   const int unrolls[3] = {2, 4, 8};
   cudaEvent_t e0, e1;

@@ -131,8 +131,9 @@ def lib() -> ctypes.CDLL:
             "sse_batch_global": (i32, [vp, ctypes.POINTER(vp)]),
             "sse_batch_use_graph": (i32, [vp, i32]),
             "sse_batch_configure": (i32, [vp, u32, i32]),
-            "sse_batch_tune": (i32, [vp, vp, i32, vp, ctypes.POINTER(i32)]),
+            "sse_batch_tune": (i32, [vp, vp, vp, i32, vp, ctypes.POINTER(i32)]),
             "sse_batch_step": (i32, [vp, vp, vp]),
+            "sse_batch_step_from": (i32, [vp, vp, vp, vp]),
             "sse_batch_kernel_launches": (u64, [vp]),
             "sse_cuda_error": (ctypes.c_char_p, [vp]),
         }
@@ -413,22 +414,43 @@ class Batch:
     def configure(self, item_pairs: int, unroll: int) -> None:
         _check(self._lib.sse_batch_configure(self._b, item_pairs, unroll), "sse_batch_configure")
 
-    def tune(self, counts, reps: int = 2) -> tuple[int, list[float]]:
+    @staticmethod
+    def _ptrs(tensors):
+        if tensors is None:
+            return None
+        arr = (ctypes.c_void_p * len(tensors))(*[_dev_ptr(t, 4) if t.numel() else 0 for t in tensors])
+        return arr
+
+    def tune(self, counts, reps: int = 2, inputs=None) -> tuple[int, list[float]]:
+        """Tune the persistent update on the loaded inputs, or on `inputs` (CUDA tensors)."""
+        if inputs is not None:
+            counts = [t.numel() // 2 for t in inputs]
+            _torch().cuda.current_stream().synchronize()
         c = np.ascontiguousarray(counts, dtype=np.uint64)
         times = (ctypes.c_float * 9)()
         chosen = ctypes.c_int(-1)
-        _check(self._lib.sse_batch_tune(self._b, ctypes.c_void_p(c.ctypes.data), reps, times, ctypes.byref(chosen)),
-               "sse_batch_tune")
+        _check(self._lib.sse_batch_tune(self._b, self._ptrs(inputs), ctypes.c_void_p(c.ctypes.data), reps, times,
+                                        ctypes.byref(chosen)), "sse_batch_tune")
         return chosen.value, [float(t) for t in times]
 
-    def step(self, counts, cap: int | None = None) -> Report:
+    def step(self, counts=None, cap: int | None = None, inputs=None) -> Report:
+        """One slice. Without `inputs`, router r scans counts[r] pairs of its loaded input
+        buffer; with `inputs` (one CUDA tensor (n_r, 2) per router, already written), it scans
+        those tensors in place."""
+        if inputs is not None:
+            counts = [t.numel() // 2 for t in inputs]
+            _torch().cuda.current_stream().synchronize()  # producers finish before the batch stream reads
         c = np.ascontiguousarray(counts, dtype=np.uint64)
         cap = self.params.max_candidates if cap is None else cap
         hosts = np.zeros(cap, np.uint32)
         est = np.zeros(cap, np.float32)
         flags = np.zeros(cap, np.uint8)
         rep = _Report(0, 0, 0, cap, 0, hosts.ctypes.data, est.ctypes.data, flags.ctypes.data)
-        rc = self._lib.sse_batch_step(self._b, ctypes.c_void_p(c.ctypes.data), ctypes.byref(rep))
+        if inputs is not None:
+            rc = self._lib.sse_batch_step_from(self._b, self._ptrs(inputs), ctypes.c_void_p(c.ctypes.data),
+                                               ctypes.byref(rep))
+        else:
+            rc = self._lib.sse_batch_step(self._b, ctypes.c_void_p(c.ctypes.data), ctypes.byref(rep))
         if rc != SSE_OK and rc != ERR_CAPACITY:
             _check(rc, "sse_batch_step")
         m = min(rep.n_candidates, cap, self.params.max_candidates)

@@ -87,13 +87,15 @@ def test_batch_graph_replay_equals_direct_launches_and_tuning_keeps_results():
     b = S.Batch(p, R, cap, use_graph=False)
     for t, per_router in enumerate(slices):
         counts = [len(x) for x in per_router]
+        dev = [helpers.to_device(x) for x in per_router]
+        torch.cuda.synchronize()
         for r, pairs in enumerate(per_router):
-            a.load(r, pairs)
             b.load(r, pairs)
         if t == 1:
             chosen, times = b.tune(counts)
             assert 0 <= chosen < 9 and all(x > 0 for x in times)
-        ra, rb = a.step(counts), b.step(counts)
+            chosen, times = a.tune(counts, inputs=dev)
+        ra, rb = a.step(inputs=dev), b.step(counts)  # caller buffers in place vs loaded inputs
         assert np.array_equal(ra.hosts, rb.hosts) and np.array_equal(ra.est, rb.est)
         assert np.array_equal(ra.flags, rb.flags)
     for x, y in zip(a.global_estimator().read_stamps(), b.global_estimator().read_stamps()):
