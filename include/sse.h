@@ -349,6 +349,64 @@ SSE_API int sse_batch_step_from(sse_batch* b, const uint32_t* const* d_pairs, co
 /* Kernels executed by the batch's steps so far. */
 SSE_API uint64_t sse_batch_kernel_launches(const sse_batch* b);
 
+/*
+ * Serving: a request loop over many routers with all estimator state on the device (the
+ * paper's deployment: edge routers stream IP pairs, the detector reports sliding super
+ * points at every slice end, Sections 3.1 and 3.3). Requests are batches of one router's
+ * pairs with a virtual arrival time; the slice of a request is floor(t / slice_seconds),
+ * fixed at admission, so results never depend on GPU timing. Each router has its own
+ * estimator and stream: requests of different routers run concurrently, those of one router
+ * in order. A request is copied into one of `slots` pinned staging buffers and scanned from
+ * its device twin; when every slot is busy, admission waits for the oldest one (the only
+ * backpressure). A request in a later slice first closes the current slice: the routers are
+ * merged into the global estimator (Algorithm 7; routers' old cells expire on the way),
+ * detection runs on the global estimator while the next slice's requests proceed, and a
+ * reporter thread collects the report; its latency runs from the slice boundary to the
+ * report being on the host. Arrival times must not decrease. One thread submits.
+ */
+typedef struct sse_server sse_server;
+
+typedef struct sse_server_config {
+  uint32_t n_routers;      /* routers served, 1..64 */
+  uint32_t slots;          /* staging buffers (batches in flight) */
+  uint64_t slot_pairs;     /* capacity of one staging buffer; larger requests are split */
+  uint64_t memory_budget;  /* device bytes the server may use: (routers + 1) estimators + staging */
+  double slice_seconds;    /* virtual-time length of one slice */
+} sse_server_config;
+
+typedef struct sse_server_stats {
+  uint64_t requests, pairs, slices_closed, slot_waits, current_slice;
+  double latency_p50_ms, latency_p99_ms; /* slice boundary to report on the host */
+} sse_server_stats;
+
+/* Defaults: 32 routers, 16 slots of 2^22 pairs, a 40 GiB budget, slices of 2^26 packets at
+ * an aggregate 2e9 packets/s (33.6 ms). */
+SSE_API void sse_server_config_default(sse_server_config* c);
+
+/* Errors: INVALID_PARAM; OOM when the estimators and staging exceed memory_budget (nothing
+ * is allocated then) or an allocation fails; CUDA. */
+SSE_API int sse_server_create(const sse_params* p, const sse_server_config* cfg, sse_server** out);
+SSE_API void sse_server_destroy(sse_server* s);
+
+/* Admits n_pairs host pairs of `router` arriving at virtual time t_arrival (seconds);
+ * returns once they are copied to staging (h_pairs may then be reused). Errors:
+ * INVALID_PARAM, STATE (t_arrival in an already closed slice), CUDA. */
+SSE_API int sse_server_submit(sse_server* s, uint32_t router, double t_arrival, const uint32_t* h_pairs,
+                              uint64_t n_pairs);
+
+/* Closes the current slice and waits until every report is ready. */
+SSE_API int sse_server_flush(sse_server* s);
+
+/* Takes the oldest ready report (out may be NULL; out->cap and arrays as for
+ * sse_close_slice) and its latency. Returns SSE_ERR_STATE when no report is ready. */
+SSE_API int sse_server_poll(sse_server* s, sse_report* out, double* latency_ms);
+
+SSE_API int sse_server_get_stats(sse_server* s, sse_server_stats* out);
+
+/* The estimators (owned by the server; read-only use after sse_server_flush). */
+SSE_API int sse_server_router(sse_server* s, uint32_t router, sse_handle** out);
+SSE_API int sse_server_global(sse_server* s, sse_handle** out);
+
 /* Name of the CUDA error behind a handle's SSE_ERR_CUDA ("" if none). */
 SSE_API const char* sse_cuda_error(const sse_handle* h);
 

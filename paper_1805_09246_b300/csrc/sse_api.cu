@@ -1188,3 +1188,357 @@ int sse_batch_tune(sse_batch* b, const uint32_t* const* d_pairs, const uint64_t*
 uint64_t sse_batch_kernel_launches(const sse_batch* b) { return b ? b->launches : 0; }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------------------
+// Serving: a request loop over many routers with state resident on the device.
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <mutex>
+#include <thread>
+#include <vector>
+
+namespace {
+
+uint64_t estimator_bytes(const sse_params& p, const sse_derived& d) {
+  const uint64_t cols = 1ull << p.q;
+  return d.sre_bytes + d.sle_bytes + 256 + ((uint64_t)p.r << p.q) / 8 + d.sle_bytes / 8 + 2 * cols * 4 +
+         (p.r - 2) * cols / 8 + (uint64_t)p.max_candidates * 13 + sizeof(CloseScratch) + kMaxRows * 4;
+}
+
+struct ServerSlot {
+  uint32_t* h_pin = nullptr;  // pinned staging
+  uint32_t* d_buf = nullptr;  // device staging
+  cudaEvent_t done = nullptr; // the update that read d_buf has finished
+  bool used = false;
+};
+
+struct PendingClose {
+  uint64_t slice;
+  std::chrono::steady_clock::time_point boundary;
+  uint32_t* sorted;
+};
+
+struct ReadyReport {
+  uint64_t slice;
+  uint32_t n_candidates, n_super, truncated;
+  int status;
+  double latency_ms;
+  std::vector<uint32_t> hosts;
+  std::vector<float> est;
+  std::vector<uint8_t> flags;
+};
+
+}  // namespace
+
+struct sse_server {
+  sse_params p;
+  sse_derived d;
+  sse_server_config cfg;
+  int n = 0;
+  sse_handle* router[kMaxRouters] = {};
+  cudaStream_t rstream[kMaxRouters] = {};
+  cudaEvent_t ev_router[kMaxRouters] = {};
+  sse_handle* global = nullptr;
+  cudaStream_t gstream = nullptr;
+  cudaEvent_t ev_merged = nullptr;
+  RouterTable rt;
+  std::vector<ServerSlot> slots;
+  size_t next_slot = 0;
+  uint64_t cur_slice = 0;
+  bool started = false;
+  double first_time = 0.0;
+  // reporting thread
+  std::thread reporter;
+  std::mutex mu;
+  std::condition_variable cv;
+  std::deque<PendingClose> pending;
+  std::deque<ReadyReport> ready;
+  std::vector<double> latencies;
+  bool stop = false;
+  int error = SSE_OK;
+  std::vector<uint32_t> rep_hosts;
+  std::vector<float> rep_est;
+  std::vector<uint8_t> rep_flags;
+  // counters
+  uint64_t requests = 0, pairs = 0, slot_waits = 0, slices_closed = 0;
+};
+
+namespace {
+
+void reporter_loop(sse_server* s) {
+  std::unique_lock<std::mutex> lk(s->mu);
+  while (true) {
+    s->cv.wait(lk, [s] { return s->stop || !s->pending.empty(); });
+    if (s->pending.empty()) return;  // stop requested and nothing left
+    const PendingClose pc = s->pending.front();
+    lk.unlock();
+    sse_report rep;
+    memset(&rep, 0, sizeof(rep));
+    rep.cap = (uint32_t)s->rep_hosts.size();
+    rep.hosts = s->rep_hosts.data();
+    rep.est = s->rep_est.data();
+    rep.flags = s->rep_flags.data();
+    const int status = close_collect(s->global, pc.sorted, &rep);
+    const double ms =
+        std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - pc.boundary).count();
+    ReadyReport rr;
+    rr.slice = pc.slice;
+    rr.n_candidates = rep.n_candidates;
+    rr.n_super = rep.n_super;
+    rr.truncated = rep.truncated;
+    rr.status = status;
+    rr.latency_ms = ms;
+    const uint32_t m = std::min(rep.n_candidates, rep.cap);
+    rr.hosts.assign(rep.hosts, rep.hosts + m);
+    rr.est.assign(rep.est, rep.est + m);
+    rr.flags.assign(rep.flags, rep.flags + m);
+    lk.lock();
+    if (status != SSE_OK && status != SSE_ERR_CAPACITY && s->error == SSE_OK) s->error = status;
+    s->global->slice += 1;
+    s->latencies.push_back(ms);
+    s->ready.push_back(std::move(rr));
+    s->pending.pop_front();
+    s->slices_closed += 1;
+    s->cv.notify_all();
+  }
+}
+
+// Closes the current slice: routers -> global merge (expiring the routers' old cells),
+// detection on the global stream, router clocks advance; the report is collected by the
+// reporter thread. At most one close is in flight.
+int server_close_slice(sse_server* s) {
+  {
+    std::unique_lock<std::mutex> lk(s->mu);
+    s->cv.wait(lk, [s] { return s->pending.empty(); });
+    if (s->error) return s->error;
+  }
+  sse_handle* g = s->global;
+  const auto boundary = std::chrono::steady_clock::now();
+  for (int r = 0; r < s->n; ++r) {
+    SSE_CUDA(g, cudaEventRecord(s->ev_router[r], s->rstream[r]));
+    SSE_CUDA(g, cudaStreamWaitEvent(s->gstream, s->ev_router[r], 0));
+  }
+  const uint64_t n16 = (g->d.sre_bytes + g->d.sle_bytes) / 16;
+  k_merge_routers<<<grid_for(g, n16, 256, 8), 256, 0, s->gstream>>>(g->state, s->rt, s->n, n16, g->p.k, g->clock);
+  SSE_LAUNCHED(g);
+  SSE_CUDA(g, cudaEventRecord(s->ev_merged, s->gstream));
+  for (int r = 0; r < s->n; ++r) {
+    sse_handle* h = s->router[r];
+    SSE_CUDA(h, cudaStreamWaitEvent(s->rstream[r], s->ev_merged, 0));
+    k_tick<<<1, 32, 0, s->rstream[r]>>>(h->clock, 1);
+    SSE_LAUNCHED(h);
+    h->slice += 1;
+  }
+  uint32_t* sorted = nullptr;
+  int rc = close_enqueue(g, &sorted);
+  if (rc) return rc;
+  k_tick<<<1, 32, 0, s->gstream>>>(g->clock, 1);
+  SSE_LAUNCHED(g);
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->pending.push_back(PendingClose{s->cur_slice, boundary, sorted});
+  }
+  s->cv.notify_all();
+  s->cur_slice += 1;
+  return SSE_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void sse_server_config_default(sse_server_config* c) {
+  if (!c) return;
+  memset(c, 0, sizeof(*c));
+  c->n_routers = 32;
+  c->slots = 16;
+  c->slot_pairs = 1u << 22;
+  c->memory_budget = 40ull << 30;
+  c->slice_seconds = (double)(1u << 26) / 2e9;
+}
+
+void sse_server_destroy(sse_server* s) {
+  if (!s) return;
+  if (s->reporter.joinable()) {
+    {
+      std::lock_guard<std::mutex> lk(s->mu);
+      s->stop = true;
+    }
+    s->cv.notify_all();
+    s->reporter.join();
+  }
+  for (int r = 0; r < s->n; ++r) {
+    if (s->rstream[r]) cudaStreamSynchronize(s->rstream[r]);
+    sse_destroy(s->router[r]);
+    if (s->ev_router[r]) cudaEventDestroy(s->ev_router[r]);
+  }
+  if (s->gstream) cudaStreamSynchronize(s->gstream);
+  sse_destroy(s->global);
+  for (ServerSlot& sl : s->slots) {
+    if (sl.done) cudaEventDestroy(sl.done);
+    cudaFree(sl.d_buf);
+    if (sl.h_pin) cudaFreeHost(sl.h_pin);
+  }
+  if (s->ev_merged) cudaEventDestroy(s->ev_merged);
+  for (int r = 0; r < s->n; ++r)
+    if (s->rstream[r]) cudaStreamDestroy(s->rstream[r]);
+  if (s->gstream) cudaStreamDestroy(s->gstream);
+  delete s;
+}
+
+int sse_server_create(const sse_params* p, const sse_server_config* cfg, sse_server** out) {
+  if (!p || !cfg || !out || cfg->n_routers < 1 || cfg->n_routers > (uint32_t)kMaxRouters || cfg->slots < 1 ||
+      cfg->slot_pairs < 1024 || !(cfg->slice_seconds > 0.0))
+    return SSE_ERR_INVALID_PARAM;
+  *out = nullptr;
+  sse_params q;
+  sse_derived d;
+  int rc = derive_params(*p, q, d);
+  if (rc) return rc;
+  // admission by memory budget: every router's estimator, the global one and the staging
+  const uint64_t need = (cfg->n_routers + 1) * estimator_bytes(q, d) + (uint64_t)cfg->slots * cfg->slot_pairs * 8;
+  if (need > cfg->memory_budget) return SSE_ERR_OOM;
+  sse_server* s = new (std::nothrow) sse_server();
+  if (!s) return SSE_ERR_OOM;
+  s->p = q;
+  s->d = d;
+  s->cfg = *cfg;
+  s->n = (int)cfg->n_routers;
+  bool ok = cudaStreamCreateWithFlags(&s->gstream, cudaStreamNonBlocking) == cudaSuccess &&
+            cudaEventCreateWithFlags(&s->ev_merged, cudaEventDisableTiming) == cudaSuccess;
+  for (int r = 0; r < s->n && ok; ++r)
+    ok = cudaStreamCreateWithFlags(&s->rstream[r], cudaStreamNonBlocking) == cudaSuccess &&
+         cudaEventCreateWithFlags(&s->ev_router[r], cudaEventDisableTiming) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    sse_server_destroy(s);
+    return SSE_ERR_CUDA;
+  }
+  for (int r = 0; r < s->n && rc == SSE_OK; ++r) rc = sse_init(p, s->rstream[r], &s->router[r]);
+  if (rc == SSE_OK) rc = sse_init(p, s->gstream, &s->global);
+  if (rc == SSE_OK) {
+    s->slots.resize(cfg->slots);
+    for (ServerSlot& sl : s->slots) {
+      if (cudaMallocHost(&sl.h_pin, cfg->slot_pairs * 8) != cudaSuccess ||
+          cudaMalloc(&sl.d_buf, cfg->slot_pairs * 8) != cudaSuccess ||
+          cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        rc = SSE_ERR_OOM;
+        break;
+      }
+    }
+  }
+  if (rc != SSE_OK) {
+    sse_server_destroy(s);
+    return rc;
+  }
+  memset(&s->rt, 0, sizeof(s->rt));
+  for (int r = 0; r < s->n; ++r) {
+    s->rt.state[r] = s->router[r]->state;
+    s->rt.gbits[r] = s->router[r]->sle_bits;
+  }
+  s->rep_hosts.resize(q.max_candidates);
+  s->rep_est.resize(q.max_candidates);
+  s->rep_flags.resize(q.max_candidates);
+  s->reporter = std::thread(reporter_loop, s);
+  *out = s;
+  return SSE_OK;
+}
+
+int sse_server_submit(sse_server* s, uint32_t router, double t_arrival, const uint32_t* h_pairs, uint64_t n_pairs) {
+  if (!s || router >= (uint32_t)s->n || (!h_pairs && n_pairs) || !(t_arrival >= 0.0)) return SSE_ERR_INVALID_PARAM;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (s->error) return s->error;
+  }
+  const uint64_t slice = (uint64_t)(t_arrival / s->cfg.slice_seconds);
+  if (slice < s->cur_slice) return SSE_ERR_STATE;  // arrivals must not go back in time
+  while (s->cur_slice < slice) {
+    const int rc = server_close_slice(s);
+    if (rc) return rc;
+  }
+  sse_handle* h = s->router[router];
+  uint64_t done = 0;
+  while (done < n_pairs) {
+    const uint64_t m = std::min<uint64_t>(s->cfg.slot_pairs, n_pairs - done);
+    ServerSlot& sl = s->slots[s->next_slot];
+    s->next_slot = (s->next_slot + 1) % s->slots.size();
+    if (sl.used) {  // admission: wait until this slot's previous batch has been scanned
+      if (cudaEventQuery(sl.done) == cudaErrorNotReady) s->slot_waits += 1;
+      SSE_CUDA(h, cudaEventSynchronize(sl.done));
+    }
+    memcpy(sl.h_pin, h_pairs + 2 * done, m * 8);
+    SSE_CUDA(h, cudaMemcpyAsync(sl.d_buf, sl.h_pin, m * 8, cudaMemcpyHostToDevice, s->rstream[router]));
+    int rc = sse_update(h, sl.d_buf, m);
+    if (rc) return rc;
+    SSE_CUDA(h, cudaEventRecord(sl.done, s->rstream[router]));
+    sl.used = true;
+    done += m;
+  }
+  s->requests += 1;
+  s->pairs += n_pairs;
+  return SSE_OK;
+}
+
+int sse_server_flush(sse_server* s) {
+  if (!s) return SSE_ERR_INVALID_PARAM;
+  int rc = server_close_slice(s);
+  if (rc) return rc;
+  std::unique_lock<std::mutex> lk(s->mu);
+  s->cv.wait(lk, [s] { return s->pending.empty(); });
+  return s->error;
+}
+
+int sse_server_poll(sse_server* s, sse_report* out, double* latency_ms) {
+  if (!s) return SSE_ERR_INVALID_PARAM;
+  std::lock_guard<std::mutex> lk(s->mu);
+  if (s->ready.empty()) return SSE_ERR_STATE;
+  ReadyReport& rr = s->ready.front();
+  if (out) {
+    out->slice = rr.slice;
+    out->n_candidates = rr.n_candidates;
+    out->n_super = rr.n_super;
+    const uint32_t m = std::min<uint32_t>((uint32_t)rr.hosts.size(), out->cap);
+    out->truncated = rr.truncated || m < rr.hosts.size();
+    if (out->hosts) memcpy(out->hosts, rr.hosts.data(), m * 4);
+    if (out->est) memcpy(out->est, rr.est.data(), m * 4);
+    if (out->flags) memcpy(out->flags, rr.flags.data(), m);
+  }
+  if (latency_ms) *latency_ms = rr.latency_ms;
+  const int status = rr.status;
+  s->ready.pop_front();
+  return status;
+}
+
+int sse_server_get_stats(sse_server* s, sse_server_stats* out) {
+  if (!s || !out) return SSE_ERR_INVALID_PARAM;
+  std::lock_guard<std::mutex> lk(s->mu);
+  memset(out, 0, sizeof(*out));
+  out->requests = s->requests;
+  out->pairs = s->pairs;
+  out->slices_closed = s->slices_closed;
+  out->slot_waits = s->slot_waits;
+  out->current_slice = s->cur_slice;
+  std::vector<double> l = s->latencies;
+  std::sort(l.begin(), l.end());
+  if (!l.empty()) {
+    out->latency_p50_ms = l[l.size() / 2];
+    out->latency_p99_ms = l[std::min(l.size() - 1, (size_t)(0.99 * l.size()))];
+  }
+  return SSE_OK;
+}
+
+int sse_server_router(sse_server* s, uint32_t router, sse_handle** out) {
+  if (!s || !out || router >= (uint32_t)s->n) return SSE_ERR_INVALID_PARAM;
+  *out = s->router[router];
+  return SSE_OK;
+}
+
+int sse_server_global(sse_server* s, sse_handle** out) {
+  if (!s || !out) return SSE_ERR_INVALID_PARAM;
+  *out = s->global;
+  return SSE_OK;
+}
+
+}  // extern "C"

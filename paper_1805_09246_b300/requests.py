@@ -1,0 +1,50 @@
+"""Seeded request streams for the serving loop (inputs only).
+
+Each router's pairs come from the synthetic trace generator; they are cut into batches of
+log-uniform size and given Poisson arrival times so that the routers together offer a
+fixed aggregate packet rate. A request is (time, router, start, size): the batch is pairs
+start .. start+size-1 of the router's pool, wrapping around.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import synth
+
+
+@dataclass
+class RequestStream:
+    pools: list  # per router: uint32 array (pool_pairs, 2)
+    requests: list  # (time, router, start, size), by time
+
+    def pairs(self, router: int, start: int, size: int) -> np.ndarray:
+        pool = self.pools[router]
+        if start + size <= len(pool):
+            return pool[start:start + size]
+        return np.take(pool, np.arange(start, start + size), axis=0, mode="wrap")
+
+
+def poisson_requests(n_routers: int, duration_s: float, offered_pps: float, batch_min: int, batch_max: int,
+                     pool_pairs: int, seed: int = 0) -> RequestStream:
+    rng = np.random.default_rng(seed)
+    cfg = synth.TrafficConfig(seed=seed, n_slices=1, n_routers=n_routers, load_min=pool_pairs,
+                              load_max=pool_pairs, n_sources=200_000, zipf_s=1.05, n_planted=4 * n_routers,
+                              planted_min=2000, planted_max=20000, group_min=1, group_max=min(8, n_routers))
+    tr = synth.Traffic(cfg)
+    pools = [tr.slice(r, 0) for r in range(n_routers)]
+    mean_batch = (batch_max - batch_min) / np.log(batch_max / batch_min)
+    rate = offered_pps / n_routers / mean_batch  # batches per second per router
+    reqs = []
+    for r in range(n_routers):
+        t, pos = 0.0, 0
+        while True:
+            t += rng.exponential(1.0 / rate)
+            if t >= duration_s:
+                break
+            size = int(np.exp(rng.uniform(np.log(batch_min), np.log(batch_max))))
+            reqs.append((t, r, pos, size))
+            pos = (pos + size) % pool_pairs
+    reqs.sort(key=lambda x: (x[0], x[1]))
+    return RequestStream(pools, reqs)

@@ -52,6 +52,17 @@ class _Stats(ctypes.Structure):
                 ("join_pairs", ctypes.c_uint64), ("n_candidates", ctypes.c_uint32), ("n_super", ctypes.c_uint32)]
 
 
+class _ServerConfig(ctypes.Structure):
+    _fields_ = [("n_routers", ctypes.c_uint32), ("slots", ctypes.c_uint32), ("slot_pairs", ctypes.c_uint64),
+                ("memory_budget", ctypes.c_uint64), ("slice_seconds", ctypes.c_double)]
+
+
+class _ServerStats(ctypes.Structure):
+    _fields_ = [("requests", ctypes.c_uint64), ("pairs", ctypes.c_uint64), ("slices_closed", ctypes.c_uint64),
+                ("slot_waits", ctypes.c_uint64), ("current_slice", ctypes.c_uint64),
+                ("latency_p50_ms", ctypes.c_double), ("latency_p99_ms", ctypes.c_double)]
+
+
 @dataclass
 class Params:
     """Symbols of the paper; defaults are the 8-slice small trace configuration."""
@@ -135,6 +146,15 @@ def lib() -> ctypes.CDLL:
             "sse_batch_step": (i32, [vp, vp, vp]),
             "sse_batch_step_from": (i32, [vp, vp, vp, vp]),
             "sse_batch_kernel_launches": (u64, [vp]),
+            "sse_server_config_default": (None, [vp]),
+            "sse_server_create": (i32, [vp, vp, ctypes.POINTER(vp)]),
+            "sse_server_destroy": (None, [vp]),
+            "sse_server_submit": (i32, [vp, u32, ctypes.c_double, vp, u64]),
+            "sse_server_flush": (i32, [vp]),
+            "sse_server_poll": (i32, [vp, vp, ctypes.POINTER(ctypes.c_double)]),
+            "sse_server_get_stats": (i32, [vp, vp]),
+            "sse_server_router": (i32, [vp, u32, ctypes.POINTER(vp)]),
+            "sse_server_global": (i32, [vp, ctypes.POINTER(vp)]),
             "sse_cuda_error": (ctypes.c_char_p, [vp]),
         }
         for name, (res, args) in sig.items():
@@ -475,3 +495,83 @@ class Batch:
     @property
     def kernel_launches(self) -> int:
         return int(self._lib.sse_batch_kernel_launches(self._b))
+
+
+class Server:
+    """Request loop over many routers (see sse_server_* in include/sse.h)."""
+
+    def __init__(self, params: Params, n_routers: int = 32, slots: int = 16, slot_pairs: int = 1 << 22,
+                 memory_budget: int = 40 << 30, slice_seconds: float | None = None):
+        _torch()
+        self.params = params
+        self._lib = lib()
+        cfg = _ServerConfig()
+        self._lib.sse_server_config_default(ctypes.byref(cfg))
+        cfg.n_routers, cfg.slots, cfg.slot_pairs, cfg.memory_budget = n_routers, slots, slot_pairs, memory_budget
+        if slice_seconds is not None:
+            cfg.slice_seconds = slice_seconds
+        self.slice_seconds = cfg.slice_seconds
+        self._s = ctypes.c_void_p()
+        _check(self._lib.sse_server_create(ctypes.byref(params.to_c()), ctypes.byref(cfg), ctypes.byref(self._s)),
+               "sse_server_create")
+        self._views = {}
+
+    def close(self) -> None:
+        if getattr(self, "_s", None) is not None and self._s.value:
+            for v in self._views.values():
+                v.close()
+            self._lib.sse_server_destroy(self._s)
+            self._s = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def submit(self, router: int, t_arrival: float, pairs: np.ndarray) -> None:
+        a = np.ascontiguousarray(pairs, dtype=np.uint32).reshape(-1)
+        _check(self._lib.sse_server_submit(self._s, router, float(t_arrival), ctypes.c_void_p(a.ctypes.data),
+                                           a.size // 2), "sse_server_submit")
+
+    def flush(self) -> None:
+        _check(self._lib.sse_server_flush(self._s), "sse_server_flush")
+
+    def poll(self, cap: int | None = None):
+        """All ready reports as (Report, latency_ms)."""
+        cap = self.params.max_candidates if cap is None else cap
+        out = []
+        while True:
+            hosts = np.zeros(cap, np.uint32)
+            est = np.zeros(cap, np.float32)
+            flags = np.zeros(cap, np.uint8)
+            rep = _Report(0, 0, 0, cap, 0, hosts.ctypes.data, est.ctypes.data, flags.ctypes.data)
+            lat = ctypes.c_double(0)
+            rc = self._lib.sse_server_poll(self._s, ctypes.byref(rep), ctypes.byref(lat))
+            if rc == -7:  # nothing ready
+                return out
+            if rc != SSE_OK and rc != ERR_CAPACITY:
+                _check(rc, "sse_server_poll")
+            m = min(rep.n_candidates, cap)
+            out.append((Report(slice=rep.slice, n_candidates=rep.n_candidates, n_super=rep.n_super,
+                               truncated=bool(rep.truncated), hosts=hosts[:m].copy(), est=est[:m].copy(),
+                               flags=flags[:m].copy(), status=rc), lat.value))
+
+    def stats(self) -> dict:
+        st = _ServerStats()
+        _check(self._lib.sse_server_get_stats(self._s, ctypes.byref(st)), "sse_server_get_stats")
+        return {name: getattr(st, name) for name, _ in _ServerStats._fields_}
+
+    def router(self, r: int) -> Estimator:
+        if r not in self._views:
+            h = ctypes.c_void_p()
+            _check(self._lib.sse_server_router(self._s, r, ctypes.byref(h)), "sse_server_router")
+            self._views[r] = Estimator._borrowed(self.params, h)
+        return self._views[r]
+
+    def global_estimator(self) -> Estimator:
+        if "global" not in self._views:
+            h = ctypes.c_void_p()
+            _check(self._lib.sse_server_global(self._s, ctypes.byref(h)), "sse_server_global")
+            self._views["global"] = Estimator._borrowed(self.params, h)
+        return self._views["global"]
