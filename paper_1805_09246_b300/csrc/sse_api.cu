@@ -1210,6 +1210,7 @@ struct ServerSlot {
   uint32_t* h_pin = nullptr;  // pinned staging
   uint32_t* d_buf = nullptr;  // device staging
   cudaEvent_t done = nullptr; // the update that read d_buf has finished
+  cudaEvent_t copied = nullptr;  // the host-to-device copy into d_buf has finished
   bool used = false;
 };
 
@@ -1377,6 +1378,7 @@ void sse_server_destroy(sse_server* s) {
   sse_destroy(s->global);
   for (ServerSlot& sl : s->slots) {
     if (sl.done) cudaEventDestroy(sl.done);
+    if (sl.copied) cudaEventDestroy(sl.copied);
     cudaFree(sl.d_buf);
     if (sl.h_pin) cudaFreeHost(sl.h_pin);
   }
@@ -1422,7 +1424,8 @@ int sse_server_create(const sse_params* p, const sse_server_config* cfg, sse_ser
     for (ServerSlot& sl : s->slots) {
       if (cudaMallocHost(&sl.h_pin, cfg->slot_pairs * 8) != cudaSuccess ||
           cudaMalloc(&sl.d_buf, cfg->slot_pairs * 8) != cudaSuccess ||
-          cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming) != cudaSuccess) {
+          cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming) != cudaSuccess ||
+          cudaEventCreateWithFlags(&sl.copied, cudaEventDisableTiming) != cudaSuccess) {
         cudaGetLastError();
         rc = SSE_ERR_OOM;
         break;
@@ -1459,6 +1462,12 @@ int sse_server_submit(sse_server* s, uint32_t router, double t_arrival, const ui
     if (rc) return rc;
   }
   sse_handle* h = s->router[router];
+  // page-locked caller memory is copied by DMA straight from where it is; the request
+  // returns once those copies are done, so the caller may reuse the buffer
+  cudaPointerAttributes attr;
+  const bool pinned =
+      n_pairs && cudaPointerGetAttributes(&attr, h_pairs) == cudaSuccess && attr.type == cudaMemoryTypeHost;
+  cudaGetLastError();
   uint64_t done = 0;
   while (done < n_pairs) {
     const uint64_t m = std::min<uint64_t>(s->cfg.slot_pairs, n_pairs - done);
@@ -1468,14 +1477,21 @@ int sse_server_submit(sse_server* s, uint32_t router, double t_arrival, const ui
       if (cudaEventQuery(sl.done) == cudaErrorNotReady) s->slot_waits += 1;
       SSE_CUDA(h, cudaEventSynchronize(sl.done));
     }
-    memcpy(sl.h_pin, h_pairs + 2 * done, m * 8);
-    SSE_CUDA(h, cudaMemcpyAsync(sl.d_buf, sl.h_pin, m * 8, cudaMemcpyHostToDevice, s->rstream[router]));
+    const void* src = h_pairs + 2 * done;
+    if (!pinned) {
+      memcpy(sl.h_pin, src, m * 8);
+      src = sl.h_pin;
+    }
+    SSE_CUDA(h, cudaMemcpyAsync(sl.d_buf, src, m * 8, cudaMemcpyHostToDevice, s->rstream[router]));
+    SSE_CUDA(h, cudaEventRecord(sl.copied, s->rstream[router]));
     int rc = sse_update(h, sl.d_buf, m);
     if (rc) return rc;
     SSE_CUDA(h, cudaEventRecord(sl.done, s->rstream[router]));
     sl.used = true;
     done += m;
   }
+  if (pinned && n_pairs)  // copies on one stream finish in order: the last one covers all
+    SSE_CUDA(h, cudaEventSynchronize(s->slots[(s->next_slot + s->slots.size() - 1) % s->slots.size()].copied));
   s->requests += 1;
   s->pairs += n_pairs;
   return SSE_OK;

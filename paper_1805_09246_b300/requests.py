@@ -27,24 +27,32 @@ class RequestStream:
 
 
 def poisson_requests(n_routers: int, duration_s: float, offered_pps: float, batch_min: int, batch_max: int,
-                     pool_pairs: int, seed: int = 0) -> RequestStream:
+                     pool_pairs: int | None = None, seed: int = 0) -> RequestStream:
+    """pool_pairs=None sizes every router's pool to its whole request stream, so no batch
+    wraps around and every batch is a contiguous view of the pool."""
     rng = np.random.default_rng(seed)
-    cfg = synth.TrafficConfig(seed=seed, n_slices=1, n_routers=n_routers, load_min=pool_pairs,
-                              load_max=pool_pairs, n_sources=200_000, zipf_s=1.05, n_planted=4 * n_routers,
-                              planted_min=2000, planted_max=20000, group_min=1, group_max=min(8, n_routers))
-    tr = synth.Traffic(cfg)
-    pools = [tr.slice(r, 0) for r in range(n_routers)]
     mean_batch = (batch_max - batch_min) / np.log(batch_max / batch_min)
     rate = offered_pps / n_routers / mean_batch  # batches per second per router
-    reqs = []
+    plan = []
     for r in range(n_routers):
-        t, pos = 0.0, 0
+        t = 0.0
         while True:
             t += rng.exponential(1.0 / rate)
             if t >= duration_s:
                 break
-            size = int(np.exp(rng.uniform(np.log(batch_min), np.log(batch_max))))
-            reqs.append((t, r, pos, size))
-            pos = (pos + size) % pool_pairs
+            plan.append((t, r, int(np.exp(rng.uniform(np.log(batch_min), np.log(batch_max))))))
+    per_router = np.zeros(n_routers, np.int64)
+    for _, r, size in plan:
+        per_router[r] += size
+    pool = int(pool_pairs or max(1, per_router.max()))
+    cfg = synth.TrafficConfig(seed=seed, n_slices=1, n_routers=n_routers, load_min=pool, load_max=pool,
+                              n_sources=200_000, zipf_s=1.05, n_planted=4 * n_routers, planted_min=2000,
+                              planted_max=20000, group_min=1, group_max=min(8, n_routers))
+    tr = synth.Traffic(cfg)
+    pools = [tr.slice(r, 0) for r in range(n_routers)]
+    reqs, pos = [], np.zeros(n_routers, np.int64)
+    for t, r, size in plan:
+        reqs.append((t, r, int(pos[r]), size))
+        pos[r] = (pos[r] + size) % pool
     reqs.sort(key=lambda x: (x[0], x[1]))
     return RequestStream(pools, reqs)
