@@ -112,6 +112,7 @@ def _load():
         lib.orc_estimate.argtypes = [vp, vp, u64, vp, vp, vp, vp, vp]
         lib.orc_detect.argtypes = [vp, vp, vp, vp, vp, u64]
         lib.orc_detect.restype = ctypes.c_int64
+        lib.orc_sre_weights.argtypes = [vp, vp, u64, vp]
         lib.orc_merge.argtypes = [vp, ctypes.POINTER(vp), ctypes.c_int]
         lib.orc_merge.restype = ctypes.c_int
         lib.orc_exact_counts.argtypes = [vp, vp, u64, vp]
@@ -272,6 +273,22 @@ class Oracle:
             self._lib.orc_detect(self._h, hosts.ctypes.data, w.ctypes.data, est.ctypes.data,
                                  flags.ctypes.data, n)
         return dict(hosts=hosts, w=w, est=est, flags=flags)
+
+    def sre_weights(self, hosts) -> np.ndarray:
+        """|SRE_i|^k of each host's r rough estimators, shape [n, r]."""
+        h = np.ascontiguousarray(hosts, dtype=np.uint32).reshape(-1)
+        out = np.zeros((h.size, self.p.r), np.uint32)
+        if h.size:
+            self._lib.orc_sre_weights(self._h, h.ctypes.data, h.size, out.ctypes.data)
+        return out
+
+    def features(self, hosts) -> np.ndarray:
+        """Learned-correction inputs (FP64): log1p of the union SLE's active cells per
+        distance 0..k-1, then log1p of the sum and of the minimum of the SRE weights."""
+        e = self.estimate(hosts, hist=True)
+        w = self.sre_weights(hosts).astype(np.float64)
+        return np.log1p(np.concatenate([e["hist"].astype(np.float64), w.sum(1, keepdims=True),
+                                        w.min(1, keepdims=True)], axis=1))
 
     def merge(self, others: list["Oracle"]) -> None:
         arr = (ctypes.c_void_p * len(others))(*[o._h.value for o in others])

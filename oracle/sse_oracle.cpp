@@ -511,6 +511,13 @@ int64_t orc_detect(void* h, uint32_t* hosts, double* w, double* est, uint8_t* fl
   return n;
 }
 
+// Weights |SRE_i|^k of each host's r estimators RSRA[i, RHFG[i](aip)]: out[n][r].
+void orc_sre_weights(void* h, const uint32_t* hosts, uint64_t n, uint32_t* out) {
+  const Oracle& o = *(Oracle*)h;
+  for (uint64_t x = 0; x < n; ++x)
+    for (uint32_t i = 0; i < o.p.r; ++i) out[x * o.p.r + i] = o.sre_weight(i, o.rhfg(i, hosts[x]));
+}
+
 // Merge (Algorithms 2 and 7, read as keeping the smaller distance): dst absorbs srcs.
 int orc_merge(void* dst, void* const* srcs, int n) {
   Oracle& o = *(Oracle*)dst;

@@ -519,3 +519,66 @@ def test_detection_on_small_trace():
         # every exact super point well above theta is found
         assert set(exact[card >= 2 * p.theta].tolist()) <= found
     assert tp >= 120 and fp <= 5 and fn <= 10
+
+
+# ---------------------------------------------------------------- learned correction (FP64 reference)
+
+def test_mlp_gradient_matches_central_differences():
+    from oracle import mlp
+    rng = np.random.default_rng(50)
+    D, H, n = 6, 8, 13
+    theta = rng.normal(0, 0.5, mlp.param_count(D, H))
+    x = rng.normal(0, 1, (n, D))
+    t = rng.normal(0, 1, n)
+    _, g = mlp.gradient(theta, x, t, D, H)
+    eps = 1e-6
+    num = np.zeros_like(theta)
+    for k in range(theta.size):
+        e = np.zeros_like(theta)
+        e[k] = eps
+        num[k] = (mlp.loss(theta + e, x, t, D, H) - mlp.loss(theta - e, x, t, D, H)) / (2 * eps)
+    assert np.allclose(g, num, rtol=1e-5, atol=1e-8)
+
+
+def test_mlp_forward_closed_form():
+    """With identity-like weights the network is a hand-computable function."""
+    from oracle import mlp
+    D, H = 2, 2
+    W1 = np.array([[1.0, 0.0], [0.0, -1.0]])
+    b1 = np.array([0.5, 0.0])
+    W2 = np.eye(2)
+    b2 = np.zeros(2)
+    W3 = np.array([2.0, 3.0])
+    b3 = 1.0
+    theta = np.concatenate([W1.ravel(), b1, W2.ravel(), b2, W3, [b3]])
+    x = np.array([[1.0, -2.0], [-3.0, 4.0]])
+    # sample 0: h1 = relu([1.5, 2]) = [1.5, 2] -> y = 1 + 2*1.5 + 3*2 = 10
+    # sample 1: h1 = relu([-2.5, -4]) = [0, 0] -> y = 1
+    assert np.allclose(mlp.forward(theta, x, D, H), [10.0, 1.0])
+
+
+def test_bf16_rounding():
+    from oracle import mlp
+    vals = np.array([1.0, 1.0 + 2**-8, 1.0 + 2**-7, 1.0 + 3 * 2**-8, -2.5, 3.1415927], np.float32)
+    got = mlp.bf16(vals)
+    # 1+2^-8 is the tie between 1 and 1+2^-7: rounds to even (1); 1+3*2^-8 rounds up to 1+2^-6
+    assert got.tolist()[:5] == [1.0, 1.0, 1.0 + 2**-7, 1.0 + 2**-6, -2.5]
+    assert abs(got[5] - 3.140625) < 1e-12
+
+
+def test_sre_weights_and_features():
+    p = small_params(seed=51, k=3)
+    o = Oracle(p)
+    rng = np.random.default_rng(51)
+    o.scan(random_pairs(rng, 20000, n_src=50))
+    hosts = np.unique(random_pairs(rng, 200, n_src=50)[:, 0])
+    sre, _ = o.raw()
+    w = o.sre_weights(hosts)
+    for j, aip in enumerate(hosts.tolist()):
+        for i in range(p.r):
+            assert w[j, i] == (sre[i, o.rhfg(i, aip)] < p.k).sum()
+    f = o.features(hosts)
+    e = o.estimate(hosts, hist=True)
+    assert f.shape == (len(hosts), p.k + 2)
+    assert np.allclose(np.expm1(f[:, : p.k]).round(), e["hist"])
+    assert np.allclose(np.expm1(f[:, p.k]).round(), w.sum(1))
