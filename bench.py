@@ -39,20 +39,25 @@ PAIR_BYTES = 8
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--steps", type=int, default=None, help="timed steps (default 200; 27 epochs for learned)")
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--mode", type=int, default=0, help="update mode: 0 auto, 1 direct, 2 tiled")
     ap.add_argument("--prefill", type=int, default=PREFILL, help="slices scanned before warm-up")
     ap.add_argument("--distinct", type=int, default=DISTINCT, help="device-resident step inputs")
-    ap.add_argument("--workload", default="core_link", choices=["core_link", "edge_routers", "serving"])
+    ap.add_argument("--workload", default="core_link", choices=["core_link", "edge_routers", "serving", "learned"])
+    ap.add_argument("--learn-train", type=int, default=1_000_000, help="training hosts (learned workload)")
+    ap.add_argument("--learn-test", type=int, default=100_000, help="held-out hosts (learned workload)")
     ap.add_argument("--serve-seconds", type=float, default=0.5, help="virtual seconds of serving traffic")
     ap.add_argument("--routers", type=int, default=16)
     ap.add_argument("--edge-q", type=int, default=22, help="RSRA size (log2 SREs per row) for edge_routers")
     ap.add_argument("--no-graph", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    return ap.parse_args()
+    args = ap.parse_args()
+    if args.steps is None:
+        args.steps = 27 if args.workload == "learned" else 200
+    return args
 
 
 def dist_env():
@@ -315,6 +320,94 @@ def main_serving(args, rank, world, local):
     }), flush=True)
 
 
+def main_learned(args, rank, world, local):
+    """Learned correction, MLP 18->64->64->1 (BF16 weights, FP32 sums): 1e6 training hosts
+    from GPU episodes (k = 16, core-link estimator shapes, exact window cardinality
+    log-uniform in [1e2, 1e6]), trained with the library's forward/backward/Adam kernels;
+    1e5 held-out hosts scored through sse_query_learned against linear counting. One step =
+    one training epoch over the hosts whose union SLE is at least 90% full; the warm-up
+    epochs are the first epochs of the same training run."""
+    import torch
+    from paper_1805_09246_b300 import learn, sse
+    from paper_1805_09246_b300.synth import episodes as ep
+
+    torch.cuda.set_device(local)
+    cfg = ep.EpisodeConfig()
+    params = learn.learned_params(cfg.k, seed=rank)
+    t0 = time.perf_counter()
+    tr = learn.episodes(params, cfg, args.learn_train, routers=64, seed=rank)
+    torch.cuda.synchronize()
+    gen_s = time.perf_counter() - t0
+    tt = learn.targets(tr)
+    act = learn.active_cells(tr.x, params.k)
+    rows = np.nonzero(act >= 0.9 * params.eta2)[0]
+    mlp = sse.MLP(params.k + 2, hidden=64, max_batch=1 << 16, seed=rank + 1)
+    rng = np.random.default_rng(rank + 2)
+    batch, lr = 512, 1e-3
+    learn.train(mlp, tr.x, tt, epochs=args.warmup, batch=batch, lr=lr, rows=rows, rng=rng)
+    launches0 = mlp.kernel_launches
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    torch.cuda.synchronize()
+    w0 = time.perf_counter()
+    e0.record(stream)
+    losses = learn.train(mlp, tr.x, tt, epochs=args.steps, batch=batch, lr=lr, rows=rows, rng=rng,
+                         first_epoch=args.warmup)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - w0
+    clk = clocks.stop()
+    launches = mlp.kernel_launches - launches0
+    elapsed = e0.elapsed_time(e1) / 1e3
+    y = mlp.forward(tr.x).cpu().numpy()
+    gate = learn.choose_gate(tr.lc.cpu().numpy(), y, tr.exact, act, params.eta2)
+    mlp.set_gate(gate)
+    mlp.set_feature_max(learn.feature_max(tr.x))
+    te = learn.episodes(params, cfg, args.learn_test, routers=64, seed=rank + 1000, mlp=mlp)
+    lc = te.lc.cpu().numpy().astype(np.float64)
+    le = te.learned.cpu().numpy().astype(np.float64)
+    ex = te.exact
+    gated = learn.active_cells(te.x, params.k) >= gate
+    rel = lambda e, m: float(np.median(np.abs(e[m] - ex[m]) / ex[m])) if m.any() else None
+    every = np.ones(len(ex), bool)
+    if rank != 0:
+        return
+    samples = len(rows) * args.steps
+    flops_per_sample = 3 * 2 * (18 * 64 + 64 * 64 + 64)  # forward, input-side backward, weight gradients
+    print(json.dumps({
+        "metric": "learned correction: training samples/s (own forward/backward/Adam kernels); median relative "
+                  "error learned vs linear counting on held-out hosts",
+        "value": round(samples * world / elapsed, 1), "unit": "samples/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(elapsed / args.steps * 1e3, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "bf16 weights, f32 accumulate", "data": "synthetic",
+        "config": {"workload": f"learned: MLP 18->64->64->1, {args.learn_train} training hosts from GPU episodes "
+                               f"({cfg.hosts} hosts + {cfg.noise_pairs} noise pairs/slice per episode, 64 episodes per "
+                               f"batch, slices 0..{cfg.query_slice}, k={cfg.k}), q=20, SLEA 5 x 2^16 x 4096; "
+                               f"{args.learn_test} held-out hosts", "train_rows": int(len(rows)),
+                   "minibatch": batch, "step": "one training epoch", "gate_min_active": int(gate)},
+        "median_rel_err_learned": round(rel(le, every), 5), "median_rel_err_lc": round(rel(lc, every), 5),
+        "median_rel_err_learned_above_gate": rel(le, gated), "median_rel_err_lc_above_gate": rel(lc, gated),
+        "hosts_above_gate": round(float(gated.mean()), 4),
+        "p90_rel_err_learned": round(float(np.quantile(np.abs(le - ex) / ex, 0.9)), 4),
+        "p90_rel_err_lc": round(float(np.quantile(np.abs(lc - ex) / ex, 0.9)), 4),
+        "final_loss": round(losses[-1], 5),
+        "episodes": {"train_s": round(gen_s, 2), "scan_s": round(tr.seconds["scan"], 2),
+                     "query_s": round(tr.seconds["query"], 3),
+                     "learned_query_hosts_per_s": round(args.learn_test / te.seconds["query"], 1)},
+        "roofline": {"bound": "alu", "kernel": "MLP training (backward + weight gradients)",
+                     "achieved": round(samples * flops_per_sample / elapsed / 1e12, 4),
+                     "peak": round(148 * 128 * 2 * 2.032e9 / 1e12, 1), "unit": "TFLOP/s",
+                     "frac": round(samples * flops_per_sample / elapsed / (148 * 128 * 2 * 2.032e9), 6),
+                     "traffic": None, "peak_source": "FP32 FMA: 148 SMs x 128 lanes x 2 x 2.032 GHz (nominal)"},
+        "e2e": {"value": round(samples * world / wall, 1), "unit": "samples/s",
+                "h2d_bytes_per_step": int(4 * len(rows)), "d2h_bytes_per_step": 4},
+        "gpu_launches": int(launches), "clocks": clk,
+    }), flush=True)
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
@@ -326,6 +419,9 @@ def main():
         return
     if args.workload == "serving":
         main_serving(args, rank, world, local)
+        return
+    if args.workload == "learned":
+        main_learned(args, rank, world, local)
         return
     import torch
     from paper_1805_09246_b300 import sse

@@ -349,6 +349,18 @@ SSE_API int sse_batch_step_from(sse_batch* b, const uint32_t* const* d_pairs, co
 /* Kernels executed by the batch's steps so far. */
 SSE_API uint64_t sse_batch_kernel_launches(const sse_batch* b);
 
+/* What a step does. SSE_BATCH_DETECT (default): as described above. SSE_BATCH_ROUTERS: the
+ * routers scan their pairs and close the slice (their old cells expire, every clock
+ * advances); the global estimator is not merged into and the report is empty
+ * (n_candidates = 0): for independent routers, e.g. training episodes queried one by one.
+ * SSE_BATCH_SCAN: the routers scan their pairs and the slice stays open (sse_query on a
+ * router then sees it); a later step continues the same slice. Errors: INVALID_PARAM. */
+enum { SSE_BATCH_DETECT = 0, SSE_BATCH_ROUTERS = 1, SSE_BATCH_SCAN = 2 };
+SSE_API int sse_batch_set_mode(sse_batch* b, int mode);
+
+/* Resets every router and the global estimator to slice 0 (sse_reset). Synchronous. */
+SSE_API int sse_batch_reset(sse_batch* b);
+
 /*
  * Serving: a request loop over many routers with all estimator state on the device (the
  * paper's deployment: edge routers stream IP pairs, the detector reports sliding super
@@ -406,6 +418,69 @@ SSE_API int sse_server_get_stats(sse_server* s, sse_server_stats* out);
 /* The estimators (owned by the server; read-only use after sse_server_flush). */
 SSE_API int sse_server_router(sse_server* s, uint32_t router, sse_handle** out);
 SSE_API int sse_server_global(sse_server* s, sse_handle** out);
+
+/* Clears the estimator to its initial state at slice 0 (as sse_init). Synchronous. */
+SSE_API int sse_reset(sse_handle* h);
+
+/*
+ * Learned cardinality correction (an extension beside the paper's method; Algorithm 8's
+ * linear-counting estimate stays the fallback). Features of a host, as in Algorithm 8 at
+ * the current slice: the union SLE's active cells per distance a = 0..k-1 (the largest
+ * distance over the host's r' SLEs), then the sum and the minimum over rows of the host's
+ * SRE weights |SRE_i|^k; each value v is given as log(1 + v). d_x: [n][k + 2] device floats.
+ * Asynchronous on the handle's stream. Errors: INVALID_PARAM, CUDA.
+ */
+SSE_API int sse_features(sse_handle* h, const uint32_t* d_hosts, uint32_t n, float* d_x);
+
+/*
+ * A multilayer perceptron n_in -> hidden -> hidden -> 1 with ReLU, mapping a host's features
+ * to a correction in log space: the learned estimate is max(LC, 1) * exp(output), LC being
+ * linear counting's estimate (Algorithm 8), so the training target is log(cardinality) -
+ * log(max(LC, 1)). Parameters are kept in FP32 for the optimiser and in BF16 for the
+ * arithmetic; all sums accumulate in FP32. Flat parameter layout: W1[hidden][n_in],
+ * b1[hidden], W2[hidden][hidden], b2[hidden], W3[hidden], b3. Weights start uniform in
+ * +-sqrt(6 / fan_in) from SplitMix64(seed), biases at 0. max_batch bounds the samples of one
+ * gradient call and of one chunk of sse_query_learned. Calls run on the given stream (NULL:
+ * legacy default); functions that return host values synchronise it.
+ */
+typedef struct sse_mlp sse_mlp;
+SSE_API int sse_mlp_create(uint32_t n_in, uint32_t hidden, uint32_t max_batch, uint64_t seed, sse_mlp** out);
+SSE_API void sse_mlp_destroy(sse_mlp* m);
+SSE_API uint32_t sse_mlp_param_count(const sse_mlp* m);
+/* Kernels launched by the MLP's forward, gradient and Adam calls so far. */
+SSE_API uint64_t sse_mlp_kernel_launches(const sse_mlp* m);
+/* Replaces the FP32 parameters (and their BF16 copy) and resets the optimiser. */
+SSE_API int sse_mlp_set_params(sse_mlp* m, const float* h_params);
+/* Host copies of the FP32 parameters, the BF16 parameters (raw bits) and the last
+ * gradients; any pointer may be NULL. */
+SSE_API int sse_mlp_get_params(sse_mlp* m, float* h_fp32, uint16_t* h_bf16, float* h_grads);
+/* Per-feature upper bounds of the training data: inputs beyond them fall back to linear
+ * counting in sse_query_learned. */
+SSE_API int sse_mlp_set_feature_max(sse_mlp* m, const float* h_xmax);
+/* Gate of sse_query_learned: the network's estimate is used only for hosts whose union SLE
+ * has at least min_active active cells; below, linear counting is kept (default 0: all). */
+SSE_API int sse_mlp_set_gate(sse_mlp* m, uint32_t min_active);
+/* d_y[b] = network output for d_x[b] ([n][n_in]). */
+SSE_API int sse_mlp_forward(sse_mlp* m, const float* d_x, uint32_t n, float* d_y, void* stream);
+/* Gradients of the mean squared error between the output and d_t over the n samples
+ * d_rows[0..n) of d_x / d_t (d_rows NULL: rows 0..n-1), n <= max_batch; *h_loss (may be
+ * NULL) receives the loss. The gradients stay in the MLP for sse_mlp_adam. */
+SSE_API int sse_mlp_gradients(sse_mlp* m, const float* d_x, const float* d_t, const uint32_t* d_rows, uint32_t n,
+                              float* h_loss, void* stream);
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8) with learning rate lr. */
+SSE_API int sse_mlp_adam(sse_mlp* m, float lr, void* stream);
+/* One epoch: minibatches of `batch` consecutive entries of d_perm (a permutation of the n
+ * training rows), each a gradient call and an Adam step; *h_loss: the last minibatch's loss. */
+SSE_API int sse_mlp_train_epoch(sse_mlp* m, const float* d_x, const float* d_t, const uint32_t* d_perm, uint32_t n,
+                                uint32_t batch, float lr, float* h_loss, void* stream);
+
+/* Estimates n hosts with the network: d_est[b] = max(LC, 1) * exp(output) for the host's
+ * features, or LC itself when the host is below the gate (sse_mlp_set_gate), a feature
+ * exceeds the training range or the result is not finite; d_est_lc and d_flags receive sse_query's estimate and flags. The network must
+ * take k + 2 inputs. Asynchronous on the handle's stream. Errors: INVALID_PARAM, MISMATCH,
+ * CUDA. */
+SSE_API int sse_query_learned(sse_handle* h, sse_mlp* m, const uint32_t* d_hosts, uint32_t n, float* d_est,
+                              float* d_est_lc, uint8_t* d_flags);
 
 /* Name of the CUDA error behind a handle's SSE_ERR_CUDA ("" if none). */
 SSE_API const char* sse_cuda_error(const sse_handle* h);

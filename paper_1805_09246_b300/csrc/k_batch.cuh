@@ -165,7 +165,8 @@ __global__ void __launch_bounds__(256) k_apply_routers(const __grid_constant__ R
 
 // Merge of every router into the global estimator (Algorithms 2 and 7: most recent stamp
 // per cell) fused with the routers' own expiry: router cells that left the window W(t,k)
-// are reset to unset while they are read anyway. 16 cells per thread.
+// are reset to unset while they are read anyway. 16 cells per thread. With dst == NULL the
+// routers are only expired.
 __global__ void __launch_bounds__(256) k_merge_routers(uint8_t* __restrict__ dst, const __grid_constant__ RouterTable rt,
                                                        int n_routers, uint64_t n16, uint32_t k,
                                                        const uint32_t* __restrict__ clock) {
@@ -174,7 +175,7 @@ __global__ void __launch_bounds__(256) k_merge_routers(uint8_t* __restrict__ dst
   for (uint32_t s = threadIdx.x; s < 256; s += blockDim.x) age_lut[s] = (uint8_t)stamp_age(s, cs);
   __syncthreads();
   for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n16; x += (uint64_t)gridDim.x * blockDim.x) {
-    const uint4 d = reinterpret_cast<const uint4*>(dst)[x];
+    const uint4 d = dst ? reinterpret_cast<const uint4*>(dst)[x] : make_uint4(0, 0, 0, 0);
     uint32_t w[4] = {d.x, d.y, d.z, d.w};
     for (int r = 0; r < n_routers; ++r) {
       uint4* src = reinterpret_cast<uint4*>(rt.state[r]) + x;
@@ -197,7 +198,7 @@ __global__ void __launch_bounds__(256) k_merge_routers(uint8_t* __restrict__ dst
       }
       if (expired) *src = make_uint4(o[0] & keep[0], o[1] & keep[1], o[2] & keep[2], o[3] & keep[3]);
     }
-    reinterpret_cast<uint4*>(dst)[x] = make_uint4(w[0], w[1], w[2], w[3]);
+    if (dst) reinterpret_cast<uint4*>(dst)[x] = make_uint4(w[0], w[1], w[2], w[3]);
   }
 }
 

@@ -10,6 +10,7 @@
 #include "k_batch.cuh"
 #include "k_close.cuh"
 #include "k_detect.cuh"
+#include "k_learn.cuh"
 #include "k_merge.cuh"
 #include "k_update.cuh"
 #include "k_update_tiled.cuh"
@@ -906,10 +907,11 @@ struct sse_batch {
   int unroll = 4;
   RouterTable rt;
   int use_graph = 1;
-  cudaGraph_t graph = nullptr;
-  cudaGraphExec_t exec = nullptr;
+  int mode = SSE_BATCH_DETECT;
+  cudaGraph_t graph[3] = {};     // one captured step per mode
+  cudaGraphExec_t exec[3] = {};
   uint32_t* sorted = nullptr;     // global's sorted candidates (fixed per configuration)
-  uint64_t kernels_per_step = 0;
+  uint64_t kernels_per_step[3] = {};
   uint64_t launches = 0;
 };
 
@@ -917,6 +919,15 @@ namespace {
 
 using RoutersKernel = void (*)(KParams, TileGeometry, RouterTable, int, uint64_t, const RouterInputs*, uint32_t,
                                uint32_t*, const uint32_t*);
+
+void drop_graphs(sse_batch* b) {
+  for (int m = 0; m < 3; ++m) {
+    if (b->exec[m]) cudaGraphExecDestroy(b->exec[m]);
+    if (b->graph[m]) cudaGraphDestroy(b->graph[m]);
+    b->exec[m] = nullptr;
+    b->graph[m] = nullptr;
+  }
+}
 
 RoutersKernel routers_kernel(int unroll) {
   return unroll == 2 ? k_update_routers<2> : unroll == 8 ? k_update_routers<8> : k_update_routers<4>;
@@ -940,19 +951,24 @@ int batch_enqueue_update(sse_batch* b) {
 }
 
 // One slice: update all routers, merge them (with their expiry) into the global estimator,
-// detect on it, and advance every clock.
+// detect on it, and advance every clock (SSE_BATCH_DETECT); see sse_batch_set_mode for the
+// other modes.
 int batch_enqueue_step(sse_batch* b) {
   sse_handle* g = b->global;
   int rc = batch_enqueue_update(b);
-  if (rc) return rc;
+  if (rc || b->mode == SSE_BATCH_SCAN) return rc;
+  const bool detect = b->mode == SSE_BATCH_DETECT;
   const uint64_t n16 = (g->d.sre_bytes + g->d.sle_bytes) / 16;
-  k_merge_routers<<<grid_for(g, n16, 256, 8), 256, 0, b->stream>>>(g->state, b->rt, b->n, n16, g->p.k, g->clock);
+  k_merge_routers<<<grid_for(g, n16, 256, 8), 256, 0, b->stream>>>(detect ? g->state : nullptr, b->rt, b->n, n16,
+                                                                    g->p.k, g->clock);
   SSE_LAUNCHED(g);
-  rc = close_enqueue(g, &b->sorted);
-  if (rc) return rc;
+  if (detect) {
+    rc = close_enqueue(g, &b->sorted);
+    if (rc) return rc;
+  }
   ClockList cl;
   for (int r = 0; r < b->n; ++r) cl.c[r] = b->router[r]->clock;
-  cl.c[b->n] = g->clock;
+  cl.c[b->n] = g->clock;  // the global clock advances in either mode (the routers read it)
   k_tick_list<<<1, 128, 0, b->stream>>>(cl, b->n + 1);
   SSE_LAUNCHED(g);
   return SSE_OK;
@@ -965,8 +981,7 @@ extern "C" {
 void sse_batch_destroy(sse_batch* b) {
   if (!b) return;
   if (b->stream) cudaStreamSynchronize(b->stream);
-  if (b->exec) cudaGraphExecDestroy(b->exec);
-  if (b->graph) cudaGraphDestroy(b->graph);
+  drop_graphs(b);
   for (int r = 0; r < b->n; ++r) sse_destroy(b->router[r]);
   sse_destroy(b->global);
   cudaFree(b->inputs);
@@ -1064,17 +1079,27 @@ int sse_batch_use_graph(sse_batch* b, int enable) {
   return SSE_OK;
 }
 
+int sse_batch_set_mode(sse_batch* b, int mode) {
+  if (!b || mode < SSE_BATCH_DETECT || mode > SSE_BATCH_SCAN) return SSE_ERR_INVALID_PARAM;
+  b->mode = mode;
+  return SSE_OK;
+}
+
+int sse_batch_reset(sse_batch* b) {
+  if (!b) return SSE_ERR_INVALID_PARAM;
+  for (int r = 0; r < b->n; ++r) {
+    const int rc = sse_reset(b->router[r]);
+    if (rc) return rc;
+  }
+  return sse_reset(b->global);
+}
+
 int sse_batch_configure(sse_batch* b, uint32_t item_pairs, int unroll) {
   if (!b || item_pairs < 1024 || item_pairs > (1u << 30) || (unroll != 2 && unroll != 4 && unroll != 8))
     return SSE_ERR_INVALID_PARAM;
   b->item_pairs = item_pairs;
   b->unroll = unroll;
-  if (b->exec) {  // the captured graph holds the old launch configuration
-    cudaGraphExecDestroy(b->exec);
-    cudaGraphDestroy(b->graph);
-    b->exec = nullptr;
-    b->graph = nullptr;
-  }
+  drop_graphs(b);  // the captured graphs hold the old launch configuration
   return SSE_OK;
 }
 
@@ -1095,7 +1120,8 @@ int batch_step(sse_batch* b, const uint32_t* const* d_pairs, const uint64_t* h_c
   }
   const uint64_t launches0 = g->launches;
   if (b->use_graph) {
-    if (!b->exec) {
+    const int m = b->mode;
+    if (!b->exec[m]) {
       SSE_CUDA(g, cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
       const int rc = batch_enqueue_step(b);
       cudaGraph_t graph = nullptr;
@@ -1105,20 +1131,30 @@ int batch_step(sse_batch* b, const uint32_t* const* d_pairs, const uint64_t* h_c
         return rc;
       }
       SSE_CUDA(g, e);
-      b->graph = graph;
-      SSE_CUDA(g, cudaGraphInstantiate(&b->exec, b->graph, 0));
-      b->kernels_per_step = g->launches - launches0;
+      b->graph[m] = graph;
+      SSE_CUDA(g, cudaGraphInstantiate(&b->exec[m], b->graph[m], 0));
+      b->kernels_per_step[m] = g->launches - launches0;
       g->launches = launches0;
     }
-    SSE_CUDA(g, cudaGraphLaunch(b->exec, b->stream));
+    SSE_CUDA(g, cudaGraphLaunch(b->exec[m], b->stream));
   } else {
     const int rc = batch_enqueue_step(b);
     if (rc) return rc;
-    b->kernels_per_step = g->launches - launches0;
+    b->kernels_per_step[b->mode] = g->launches - launches0;
     g->launches = launches0;
   }
-  b->launches += b->kernels_per_step;
-  const int status = close_collect(g, b->sorted, out);
+  b->launches += b->kernels_per_step[b->mode];
+  int status = SSE_OK;
+  if (b->mode == SSE_BATCH_DETECT) {
+    status = close_collect(g, b->sorted, out);
+  } else {
+    SSE_CUDA(g, cudaStreamSynchronize(b->stream));
+    if (out) {
+      out->slice = g->slice;
+      out->n_candidates = out->n_super = out->truncated = 0;
+    }
+    if (b->mode == SSE_BATCH_SCAN) return SSE_OK;  // the slice stays open
+  }
   if (status != SSE_OK && status != SSE_ERR_CAPACITY) return status;
   for (int r = 0; r < b->n; ++r) b->router[r]->slice += 1;
   g->slice += 1;
@@ -1554,6 +1590,227 @@ int sse_server_router(sse_server* s, uint32_t router, sse_handle** out) {
 int sse_server_global(sse_server* s, sse_handle** out) {
   if (!s || !out) return SSE_ERR_INVALID_PARAM;
   *out = s->global;
+  return SSE_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------------------
+// Learned correction: features, MLP training and inference.
+struct sse_mlp {
+  MlpShape s;
+  uint32_t max_batch = 0;
+  float* wf = nullptr;           // FP32 parameters (optimiser)
+  __nv_bfloat16* wb = nullptr;   // BF16 parameters (arithmetic)
+  float* g = nullptr;            // gradients
+  float* m = nullptr;            // Adam moments
+  float* v = nullptr;
+  float* act = nullptr;          // per-sample activations and deltas [max_batch][4H+1]
+  float* loss = nullptr;         // device loss accumulator
+  float* x_max = nullptr;        // per-feature upper bound of the training data
+  float* scratch_x = nullptr;    // query features [max_batch][n_in]
+  float* scratch_y = nullptr;    // query outputs [max_batch]
+  uint32_t min_active = 0;       // gate of sse_query_learned
+  uint64_t step = 0;
+  uint64_t launches = 0;         // kernels launched by forward / gradients / Adam
+};
+
+extern "C" {
+
+void sse_mlp_destroy(sse_mlp* m) {
+  if (!m) return;
+  cudaDeviceSynchronize();
+  cudaFree(m->wf);
+  cudaFree(m->wb);
+  cudaFree(m->g);
+  cudaFree(m->m);
+  cudaFree(m->v);
+  cudaFree(m->act);
+  cudaFree(m->loss);
+  cudaFree(m->x_max);
+  cudaFree(m->scratch_x);
+  cudaFree(m->scratch_y);
+  delete m;
+}
+
+int sse_mlp_create(uint32_t n_in, uint32_t hidden, uint32_t max_batch, uint64_t seed, sse_mlp** out) {
+  if (!out || n_in < 1 || n_in > (uint32_t)kMaxIn || hidden < 1 || hidden > (uint32_t)kMaxHidden || max_batch < 1)
+    return SSE_ERR_INVALID_PARAM;
+  *out = nullptr;
+  sse_mlp* m = new (std::nothrow) sse_mlp();
+  if (!m) return SSE_ERR_OOM;
+  m->s = mlp_shape(n_in, hidden);
+  m->max_batch = max_batch;
+  const uint32_t T = m->s.total;
+  const bool ok = cudaMalloc(&m->wf, T * 4) == cudaSuccess && cudaMalloc(&m->wb, T * 2) == cudaSuccess &&
+                  cudaMalloc(&m->g, T * 4) == cudaSuccess && cudaMalloc(&m->m, T * 4) == cudaSuccess &&
+                  cudaMalloc(&m->v, T * 4) == cudaSuccess &&
+                  cudaMalloc(&m->act, (uint64_t)max_batch * (4 * hidden + 1) * 4) == cudaSuccess &&
+                  cudaMalloc(&m->loss, 4) == cudaSuccess && cudaMalloc(&m->x_max, n_in * 4) == cudaSuccess &&
+                  cudaMalloc(&m->scratch_x, (uint64_t)max_batch * n_in * 4) == cudaSuccess &&
+                  cudaMalloc(&m->scratch_y, (uint64_t)max_batch * 4) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    sse_mlp_destroy(m);
+    return SSE_ERR_OOM;
+  }
+  // uniform initialisation in +-sqrt(6 / fan_in) (He et al. 2015), zero biases, from SplitMix64(seed)
+  std::vector<float> w(T, 0.f);
+  uint64_t st = seed;
+  auto uni = [&st]() { return (double)(splitmix64(st) >> 11) * (1.0 / 9007199254740992.0); };
+  const double a1 = std::sqrt(6.0 / n_in), a2 = std::sqrt(6.0 / hidden);
+  for (uint32_t k = m->s.off_w1; k < m->s.off_b1; ++k) w[k] = (float)((2 * uni() - 1) * a1);
+  for (uint32_t k = m->s.off_w2; k < m->s.off_b2; ++k) w[k] = (float)((2 * uni() - 1) * a2);
+  for (uint32_t k = m->s.off_w3; k < m->s.off_b3; ++k) w[k] = (float)((2 * uni() - 1) * a2);
+  std::vector<float> big(n_in, 3.0e38f);
+  if (cudaMemcpy(m->wf, w.data(), T * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemset(m->m, 0, T * 4) != cudaSuccess || cudaMemset(m->v, 0, T * 4) != cudaSuccess ||
+      cudaMemcpy(m->x_max, big.data(), n_in * 4, cudaMemcpyHostToDevice) != cudaSuccess) {
+    cudaGetLastError();
+    sse_mlp_destroy(m);
+    return SSE_ERR_CUDA;
+  }
+  k_mlp_to_bf16<<<(T + 255) / 256, 256>>>(T, m->wf, m->wb);
+  if (cudaDeviceSynchronize() != cudaSuccess) {
+    cudaGetLastError();
+    sse_mlp_destroy(m);
+    return SSE_ERR_CUDA;
+  }
+  *out = m;
+  return SSE_OK;
+}
+
+uint32_t sse_mlp_param_count(const sse_mlp* m) { return m ? m->s.total : 0; }
+
+uint64_t sse_mlp_kernel_launches(const sse_mlp* m) { return m ? m->launches : 0; }
+
+int sse_mlp_set_params(sse_mlp* m, const float* h_params) {
+  if (!m || !h_params) return SSE_ERR_INVALID_PARAM;
+  if (cudaMemcpy(m->wf, h_params, m->s.total * 4, cudaMemcpyHostToDevice) != cudaSuccess) return SSE_ERR_CUDA;
+  k_mlp_to_bf16<<<(m->s.total + 255) / 256, 256>>>(m->s.total, m->wf, m->wb);
+  m->step = 0;
+  if (cudaMemset(m->m, 0, m->s.total * 4) != cudaSuccess || cudaMemset(m->v, 0, m->s.total * 4) != cudaSuccess ||
+      cudaDeviceSynchronize() != cudaSuccess)
+    return SSE_ERR_CUDA;
+  return SSE_OK;
+}
+
+int sse_mlp_get_params(sse_mlp* m, float* h_fp32, uint16_t* h_bf16, float* h_grads) {
+  if (!m) return SSE_ERR_INVALID_PARAM;
+  if (cudaDeviceSynchronize() != cudaSuccess) return SSE_ERR_CUDA;
+  if (h_fp32 && cudaMemcpy(h_fp32, m->wf, m->s.total * 4, cudaMemcpyDeviceToHost) != cudaSuccess) return SSE_ERR_CUDA;
+  if (h_bf16 && cudaMemcpy(h_bf16, m->wb, m->s.total * 2, cudaMemcpyDeviceToHost) != cudaSuccess) return SSE_ERR_CUDA;
+  if (h_grads && cudaMemcpy(h_grads, m->g, m->s.total * 4, cudaMemcpyDeviceToHost) != cudaSuccess) return SSE_ERR_CUDA;
+  return SSE_OK;
+}
+
+int sse_mlp_set_feature_max(sse_mlp* m, const float* h_xmax) {
+  if (!m || !h_xmax) return SSE_ERR_INVALID_PARAM;
+  return cudaMemcpy(m->x_max, h_xmax, m->s.n_in * 4, cudaMemcpyHostToDevice) == cudaSuccess ? SSE_OK : SSE_ERR_CUDA;
+}
+
+int sse_mlp_set_gate(sse_mlp* m, uint32_t min_active) {
+  if (!m) return SSE_ERR_INVALID_PARAM;
+  m->min_active = min_active;
+  return SSE_OK;
+}
+
+int sse_mlp_forward(sse_mlp* m, const float* d_x, uint32_t n, float* d_y, void* stream) {
+  if (!m || (!d_x && n) || (!d_y && n)) return SSE_ERR_INVALID_PARAM;
+  if (!n) return SSE_OK;
+  const unsigned grid = std::min<uint64_t>((n + 127) / 128, 148 * 8);
+  k_mlp_forward<<<grid, 128, m->s.total * 4, (cudaStream_t)stream>>>(m->s, m->wb, d_x, nullptr, n, d_y);
+  m->launches += 1;
+  return cudaGetLastError() == cudaSuccess ? SSE_OK : SSE_ERR_CUDA;
+}
+
+int sse_mlp_gradients(sse_mlp* m, const float* d_x, const float* d_t, const uint32_t* d_rows, uint32_t n,
+                      float* h_loss, void* stream) {
+  if (!m || !d_x || !d_t || n < 1 || n > m->max_batch) return SSE_ERR_INVALID_PARAM;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (cudaMemsetAsync(m->loss, 0, 4, st) != cudaSuccess) return SSE_ERR_CUDA;
+  const unsigned grid = std::min<uint64_t>((n + 127) / 128, 148 * 8);
+  k_mlp_backward<<<grid, 128, m->s.total * 4, st>>>(m->s, m->wb, d_x, d_t, d_rows, n, m->act, m->loss);
+  k_mlp_weight_grads<<<(m->s.total + 255) / 256, 256, 0, st>>>(m->s, d_x, d_rows, n, m->act, m->g);
+  m->launches += 2;
+  if (cudaGetLastError() != cudaSuccess) return SSE_ERR_CUDA;
+  if (h_loss) {
+    if (cudaMemcpyAsync(h_loss, m->loss, 4, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+      return SSE_ERR_CUDA;
+  }
+  return SSE_OK;
+}
+
+int sse_mlp_adam(sse_mlp* m, float lr, void* stream) {
+  if (!m || !(lr > 0.f)) return SSE_ERR_INVALID_PARAM;
+  const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
+  m->step += 1;
+  const float bc1 = 1.f - std::pow(b1, (float)m->step), bc2 = 1.f - std::pow(b2, (float)m->step);
+  k_mlp_adam<<<(m->s.total + 255) / 256, 256, 0, (cudaStream_t)stream>>>(m->s.total, m->wf, m->wb, m->g, m->m, m->v,
+                                                                        lr, b1, b2, eps, bc1, bc2);
+  m->launches += 1;
+  return cudaGetLastError() == cudaSuccess ? SSE_OK : SSE_ERR_CUDA;
+}
+
+// One epoch over d_perm (n indices into d_x / d_t), minibatches of `batch`; returns the
+// last minibatch's loss.
+int sse_mlp_train_epoch(sse_mlp* m, const float* d_x, const float* d_t, const uint32_t* d_perm, uint32_t n,
+                        uint32_t batch, float lr, float* h_loss, void* stream) {
+  if (!m || !d_x || !d_t || !d_perm || n < 1 || batch < 1 || batch > m->max_batch) return SSE_ERR_INVALID_PARAM;
+  cudaStream_t st = (cudaStream_t)stream;
+  float last = 0.f;
+  for (uint32_t b0 = 0; b0 < n; b0 += batch) {
+    const uint32_t nb = std::min(batch, n - b0);
+    int rc = sse_mlp_gradients(m, d_x, d_t, d_perm + b0, nb, (b0 + batch >= n) ? &last : nullptr, st);
+    if (rc) return rc;
+    rc = sse_mlp_adam(m, lr, st);
+    if (rc) return rc;
+  }
+  if (h_loss) *h_loss = last;
+  return cudaStreamSynchronize(st) == cudaSuccess ? SSE_OK : SSE_ERR_CUDA;
+}
+
+int sse_features(sse_handle* h, const uint32_t* d_hosts, uint32_t n, float* d_x) {
+  if (!h || (!d_hosts && n) || (!d_x && n)) return SSE_ERR_INVALID_PARAM;
+  if (h->sticky) return h->sticky;
+  if (!n) return SSE_OK;
+  k_features<<<grid_for(h, n, 1, 16), kFeatThreads, 0, h->stream>>>(h->kp, h->sre, h->sle, d_hosts, n, h->clock, d_x);
+  SSE_LAUNCHED(h);
+  return SSE_OK;
+}
+
+int sse_query_learned(sse_handle* h, sse_mlp* m, const uint32_t* d_hosts, uint32_t n, float* d_est,
+                      float* d_est_lc, uint8_t* d_flags) {
+  if (!h || !m || (!d_hosts && n) || (!d_est && n) || (!d_est_lc && n)) return SSE_ERR_INVALID_PARAM;
+  if (m->s.n_in != h->p.k + 2) return SSE_ERR_MISMATCH;
+  for (uint32_t b0 = 0; b0 < n; b0 += m->max_batch) {
+    const uint32_t nb = std::min(m->max_batch, n - b0);
+    int rc = sse_query(h, d_hosts + b0, nb, d_est_lc + b0, d_flags ? d_flags + b0 : nullptr, nullptr);
+    if (rc) return rc;
+    rc = sse_features(h, d_hosts + b0, nb, m->scratch_x);
+    if (rc) return rc;
+    rc = sse_mlp_forward(m, m->scratch_x, nb, m->scratch_y, h->stream);
+    if (rc) return fail(h, cudaGetLastError());
+    k_learned_select<<<(nb + 255) / 256, 256, 0, h->stream>>>(nb, m->s.n_in, m->scratch_x, m->scratch_y,
+                                                             d_est_lc + b0, m->x_max, m->min_active, d_est + b0);
+    SSE_LAUNCHED(h);
+  }
+  return SSE_OK;
+}
+
+int sse_reset(sse_handle* h) {
+  if (!h) return SSE_ERR_INVALID_PARAM;
+  if (h->sticky) return h->sticky;
+  const uint32_t first = stamp_of(0);
+  SSE_CUDA(h, cudaMemsetAsync(h->state, 0, h->d.sre_bytes + h->d.sle_bytes, h->stream));
+  SSE_CUDA(h, cudaMemsetAsync(h->sle_bits, 0, h->d.sle_bytes / 8, h->stream));
+  SSE_CUDA(h, cudaMemsetAsync(h->hot_bits, 0, ((uint64_t)h->p.r << h->p.q) / 8, h->stream));
+  SSE_CUDA(h, cudaMemsetAsync(h->scratch, 0, sizeof(CloseScratch), h->stream));
+  SSE_CUDA(h, cudaMemcpyAsync(h->clock, &first, 4, cudaMemcpyHostToDevice, h->stream));
+  SSE_CUDA(h, cudaStreamSynchronize(h->stream));
+  h->slice = 0;
+  memset(&h->stats, 0, sizeof(h->stats));
   return SSE_OK;
 }
 

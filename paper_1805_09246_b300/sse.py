@@ -21,6 +21,7 @@ FLAG_SUPER = 1
 FLAG_SATURATED = 2
 ERR_CAPACITY = -3
 UPDATE_AUTO, UPDATE_DIRECT, UPDATE_TILED = 0, 1, 2
+BATCH_DETECT, BATCH_ROUTERS, BATCH_SCAN = 0, 1, 2
 
 
 class SSEError(RuntimeError):
@@ -156,6 +157,23 @@ def lib() -> ctypes.CDLL:
             "sse_server_router": (i32, [vp, u32, ctypes.POINTER(vp)]),
             "sse_server_global": (i32, [vp, ctypes.POINTER(vp)]),
             "sse_cuda_error": (ctypes.c_char_p, [vp]),
+            "sse_reset": (i32, [vp]),
+            "sse_batch_set_mode": (i32, [vp, i32]),
+            "sse_batch_reset": (i32, [vp]),
+            "sse_features": (i32, [vp, vp, u32, vp]),
+            "sse_mlp_create": (i32, [u32, u32, u32, u64, ctypes.POINTER(vp)]),
+            "sse_mlp_destroy": (None, [vp]),
+            "sse_mlp_param_count": (u32, [vp]),
+            "sse_mlp_kernel_launches": (u64, [vp]),
+            "sse_mlp_set_params": (i32, [vp, vp]),
+            "sse_mlp_get_params": (i32, [vp, vp, vp, vp]),
+            "sse_mlp_set_feature_max": (i32, [vp, vp]),
+            "sse_mlp_set_gate": (i32, [vp, u32]),
+            "sse_mlp_forward": (i32, [vp, vp, u32, vp, vp]),
+            "sse_mlp_gradients": (i32, [vp, vp, vp, vp, u32, vp, vp]),
+            "sse_mlp_adam": (i32, [vp, ctypes.c_float, vp]),
+            "sse_mlp_train_epoch": (i32, [vp, vp, vp, vp, u32, u32, ctypes.c_float, vp, vp]),
+            "sse_query_learned": (i32, [vp, vp, vp, u32, vp, vp, vp]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -383,6 +401,33 @@ class Estimator:
     def sync(self) -> None:
         _check(self._lib.sse_sync(self._h), "sse_sync")
 
+    def reset(self) -> None:
+        """Back to the initial state at slice 0."""
+        _check(self._lib.sse_reset(self._h), "sse_reset", self._h)
+
+    def features(self, hosts, out=None):
+        """Learned-correction features of the hosts (CUDA tensor of 32-bit addresses):
+        float32 [n, k + 2], log(1 + v) of the union SLE's per-distance active cells and of the
+        sum and minimum of the host's SRE weights. Asynchronous on the estimator's stream."""
+        torch = _torch()
+        n = hosts.numel()
+        x = torch.empty((n, self.params.k + 2), dtype=torch.float32, device=hosts.device) if out is None else out
+        _check(self._lib.sse_features(self._h, ctypes.c_void_p(_dev_ptr(hosts, 4)), n,
+                                      ctypes.c_void_p(_dev_ptr(x, 4))), "sse_features", self._h)
+        return x
+
+    def query_learned(self, mlp: "MLP", hosts):
+        """(learned estimate, linear-counting estimate, flags) of the hosts."""
+        torch = _torch()
+        n = hosts.numel()
+        est = torch.empty(n, dtype=torch.float32, device=hosts.device)
+        lc = torch.empty(n, dtype=torch.float32, device=hosts.device)
+        flags = torch.empty(n, dtype=torch.uint8, device=hosts.device)
+        _check(self._lib.sse_query_learned(self._h, mlp._m, ctypes.c_void_p(_dev_ptr(hosts, 4)), n,
+                                           ctypes.c_void_p(est.data_ptr()), ctypes.c_void_p(lc.data_ptr()),
+                                           ctypes.c_void_p(flags.data_ptr())), "sse_query_learned", self._h)
+        return est, lc, flags
+
 
 class Batch:
     """R routers' estimators plus their merged global estimator, advanced slice by slice
@@ -495,6 +540,99 @@ class Batch:
     @property
     def kernel_launches(self) -> int:
         return int(self._lib.sse_batch_kernel_launches(self._b))
+
+    def set_mode(self, mode: int) -> None:
+        """BATCH_DETECT (default), BATCH_ROUTERS or BATCH_SCAN (see sse_batch_set_mode)."""
+        _check(self._lib.sse_batch_set_mode(self._b, mode), "sse_batch_set_mode")
+
+    def reset(self) -> None:
+        """Every estimator back to slice 0."""
+        _check(self._lib.sse_batch_reset(self._b), "sse_batch_reset")
+
+
+class MLP:
+    """The learned correction's network (sse_mlp_*): n_in -> hidden -> hidden -> 1, BF16
+    weights, FP32 sums, trained with the library's own kernels."""
+
+    def __init__(self, n_in: int, hidden: int = 64, max_batch: int = 1 << 16, seed: int = 0):
+        _torch()
+        self._lib = lib()
+        self._m = ctypes.c_void_p()
+        _check(self._lib.sse_mlp_create(n_in, hidden, max_batch, seed, ctypes.byref(self._m)), "sse_mlp_create")
+        self.n_in, self.hidden, self.max_batch = n_in, hidden, max_batch
+        self.n_params = int(self._lib.sse_mlp_param_count(self._m))
+
+    def close(self) -> None:
+        if getattr(self, "_m", None) is not None and self._m.value:
+            self._lib.sse_mlp_destroy(self._m)
+            self._m = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @staticmethod
+    def _stream():
+        return ctypes.c_void_p(_torch().cuda.current_stream().cuda_stream)
+
+    def set_params(self, w: np.ndarray) -> None:
+        a = np.ascontiguousarray(w, dtype=np.float32)
+        assert a.size == self.n_params
+        _check(self._lib.sse_mlp_set_params(self._m, ctypes.c_void_p(a.ctypes.data)), "sse_mlp_set_params")
+
+    def params(self) -> tuple[np.ndarray, np.ndarray, np.ndarray]:
+        """(FP32 parameters, BF16 parameters as uint16 bits, last gradients)."""
+        _torch().cuda.current_stream().synchronize()
+        f = np.zeros(self.n_params, np.float32)
+        b = np.zeros(self.n_params, np.uint16)
+        g = np.zeros(self.n_params, np.float32)
+        _check(self._lib.sse_mlp_get_params(self._m, ctypes.c_void_p(f.ctypes.data), ctypes.c_void_p(b.ctypes.data),
+                                            ctypes.c_void_p(g.ctypes.data)), "sse_mlp_get_params")
+        return f, b, g
+
+    def set_feature_max(self, xmax) -> None:
+        a = np.ascontiguousarray(xmax, dtype=np.float32)
+        assert a.size == self.n_in
+        _check(self._lib.sse_mlp_set_feature_max(self._m, ctypes.c_void_p(a.ctypes.data)),
+               "sse_mlp_set_feature_max")
+
+    @property
+    def kernel_launches(self) -> int:
+        return int(self._lib.sse_mlp_kernel_launches(self._m))
+
+    def set_gate(self, min_active: int) -> None:
+        """Use the network only for hosts with at least min_active active union-SLE cells."""
+        _check(self._lib.sse_mlp_set_gate(self._m, int(min_active)), "sse_mlp_set_gate")
+
+    def forward(self, x):
+        torch = _torch()
+        n = x.shape[0]
+        y = torch.empty(n, dtype=torch.float32, device=x.device)
+        _check(self._lib.sse_mlp_forward(self._m, ctypes.c_void_p(_dev_ptr(x, 4)), n,
+                                         ctypes.c_void_p(y.data_ptr()), self._stream()), "sse_mlp_forward")
+        return y
+
+    def gradients(self, x, t, rows=None) -> float:
+        """Gradients of the mean squared error over `rows` (or all rows); returns the loss."""
+        n = rows.numel() if rows is not None else x.shape[0]
+        loss = ctypes.c_float(0)
+        _check(self._lib.sse_mlp_gradients(self._m, ctypes.c_void_p(_dev_ptr(x, 4)), ctypes.c_void_p(_dev_ptr(t, 4)),
+                                           ctypes.c_void_p(_dev_ptr(rows, 4) if rows is not None else 0), n,
+                                           ctypes.byref(loss), self._stream()), "sse_mlp_gradients")
+        return float(loss.value)
+
+    def adam(self, lr: float) -> None:
+        _check(self._lib.sse_mlp_adam(self._m, ctypes.c_float(lr), self._stream()), "sse_mlp_adam")
+
+    def train_epoch(self, x, t, perm, batch: int, lr: float) -> float:
+        loss = ctypes.c_float(0)
+        _check(self._lib.sse_mlp_train_epoch(self._m, ctypes.c_void_p(_dev_ptr(x, 4)), ctypes.c_void_p(_dev_ptr(t, 4)),
+                                             ctypes.c_void_p(_dev_ptr(perm, 4)), perm.numel(), batch,
+                                             ctypes.c_float(lr), ctypes.byref(loss), self._stream()),
+               "sse_mlp_train_epoch")
+        return float(loss.value)
 
 
 class Server:
