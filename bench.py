@@ -51,6 +51,7 @@ def parse():
     ap.add_argument("--serve-seconds", type=float, default=0.5, help="virtual seconds of serving traffic")
     ap.add_argument("--routers", type=int, default=16)
     ap.add_argument("--edge-q", type=int, default=22, help="RSRA size (log2 SREs per row) for edge_routers")
+    ap.add_argument("--update-variant", type=int, default=None, help="fixed update variant (no autotuning)")
     ap.add_argument("--no-graph", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
@@ -453,8 +454,14 @@ def main():
     def step_input(s):
         return dev_slices[prefill + s % distinct]
 
-    # autotune the update on the next slice's pairs (idempotent within the slice), untimed
-    tuned, tune_ms = est.autotune_update(step_input(0), reps=3)
+    # autotune the update on the next slice's pairs (idempotent within the slice), untimed;
+    # --update-variant fixes the variant instead (profiler runs, where event timing of the
+    # candidates is distorted)
+    if args.update_variant is None:
+        tuned, tune_ms = est.autotune_update(step_input(0), reps=3)
+    else:
+        tuned, tune_ms = args.update_variant, []
+        est.set_update_variant(tuned)
 
     for w in range(args.warmup):
         est.update(step_input(w))
@@ -464,6 +471,7 @@ def main():
     ev_start, ev_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     upd_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     close_ms = []
+    close_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     launches0 = est.kernel_launches
     n_super = n_cand = 0
     clocks = ClockSampler(local)
@@ -480,7 +488,9 @@ def main():
         b.record(stream)
         stream.synchronize()  # slice boundary: all of this slice's pairs are applied
         t0 = time.perf_counter()
+        close_ev[s][0].record(stream)
         rep = est.close_slice()
+        close_ev[s][1].record(stream)
         close_ms.append((time.perf_counter() - t0) * 1e3)
         n_super += rep.n_super
         n_cand += rep.n_candidates
@@ -553,6 +563,7 @@ def main():
         "update_ms": round(upd_ms, 4),
         "close_ms_p50": round(close_sorted[len(close_sorted) // 2], 4),
         "close_ms_p99": round(close_sorted[min(len(close_sorted) - 1, int(0.99 * len(close_sorted)))], 4),
+        "close_device_ms_p50": round(sorted(a.elapsed_time(b) for a, b in close_ev)[len(close_ev) // 2], 4),
         "candidates_per_slice": round(n_cand / args.steps, 1), "super_per_slice": round(n_super / args.steps, 1),
         "last_slice": {"hot_sre_per_row": slice_stats["hot"], "join_pairs": slice_stats["join_pairs"],
                        "sf": [round(c / est.derived["row_len2"], 4) for c in slice_stats["active2"]]},

@@ -210,6 +210,11 @@ SSE_API int sse_autotune_update(sse_handle* h, const uint32_t* d_pairs, uint64_t
  */
 SSE_API int sse_close_slice(sse_handle* h, sse_report* out);
 
+/* 1 (default): sse_close_slice replays its device work (close kernels, counter and report
+ * copies, clock tick) from a CUDA graph captured at the first call; 0: launches the same
+ * kernels one by one. Results are identical. Errors: INVALID_PARAM. */
+SSE_API int sse_close_use_graph(sse_handle* h, int enable);
+
 /* Moves to the next slice without detection: expires old cells and advances, so a router
  * whose super points are detected elsewhere (after a merge) keeps a valid window.
  * Asynchronous. Errors: CUDA. */

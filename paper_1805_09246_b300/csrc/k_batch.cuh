@@ -9,6 +9,8 @@
 // single tile with index chunk mod tiles.
 #pragma once
 
+#include <type_traits>
+
 #include "k_update.cuh"
 #include "k_update_tiled.cuh"
 #include "sse_internal.cuh"
@@ -29,7 +31,7 @@ struct RouterInputs {
   uint64_t counts[kMaxRouters];
 };
 
-template <int UNROLL>
+template <int UNROLL, bool WHOLE>
 __global__ void __launch_bounds__(kTiledThreads, 1)
     k_update_routers(const __grid_constant__ KParams p, TileGeometry g, const __grid_constant__ RouterTable rt,
                      int n_routers, uint64_t sre_bytes, const RouterInputs* __restrict__ in, uint32_t item_pairs,
@@ -52,15 +54,8 @@ __global__ void __launch_bounds__(kTiledThreads, 1)
   }
   __syncthreads();
   const uint64_t total = first_item[n_routers];
-  const uint64_t a3 = p.key_a[kH3], b3 = p.key_b[kH3];
-  const uint64_t al = p.key_a[kLH + row], bl = p.key_b[kLH + row];
-  const uint32_t sh3 = 32 - p.lg_eta2, shl = 32 - p.q2, d2 = p.delta2, span = g.piece_bytes;
-  auto touch = [&](uint32_t aip, uint32_t bip) {
-    const uint32_t h3 = (uint32_t)((uint64_t)mas_hi(a3, b3, bip) >> sh3);
-    const uint32_t lh = (uint32_t)((uint64_t)mas_hi(al, bl, aip) >> shl);
-    const uint32_t cell = lh * d2 + h3 - lo;
-    if (cell < span) atomicOr(&bm[cell >> 5], 1u << (cell & 31));
-  };
+  const SleTile st(p, row, lo, g.piece_bytes);
+  auto touch = [&](uint32_t aip, uint32_t bip) { st.touch<WHOLE, false>(bm, aip, bip); };
   auto flush = [&](int r) {
     uint32_t* dst = rt.gbits[r] + (((uint64_t)row * p.row_pitch2 + lo) >> 5);
     for (uint32_t w = threadIdx.x; w < words; w += blockDim.x) {
@@ -72,6 +67,7 @@ __global__ void __launch_bounds__(kTiledThreads, 1)
     }
   };
   for (uint32_t w = threadIdx.x; w < words; w += blockDim.x) bm[w] = 0;
+  RsraQueue rq{reinterpret_cast<uint2*>(bm + words) + (threadIdx.x >> 5) * kRsraQueueEntries, 0u, threadIdx.x & 31u};
   int cur = -1;
   while (true) {
     __syncthreads();  // previous item done; sh_item free
@@ -103,26 +99,55 @@ __global__ void __launch_bounds__(kTiledThreads, 1)
     }
     const uint4* vec = reinterpret_cast<const uint4*>(pairs + j0);
     const uint32_t nvec = (uint32_t)((end - j0) >> 1);
-    for (uint32_t i0 = threadIdx.x; i0 < nvec; i0 += blockDim.x * UNROLL) {
-      uint4 buf[UNROLL];
+    // the item's RSRA owner runs a separate copy of the loop, so the other tiles execute
+    // none of its sampling; iterations are uniform per warp (RsraQueue needs every lane)
+    const uint32_t lane = threadIdx.x & 31u;
+    auto scan = [&](auto with_rsra) {
+      constexpr bool kRsra = decltype(with_rsra)::value;
+      for (uint32_t b0 = threadIdx.x - lane; b0 < nvec; b0 += blockDim.x * UNROLL) {
+        const uint32_t i0 = b0 + lane;
+        uint4 buf[UNROLL];
+        if (b0 + (UNROLL - 1) * blockDim.x + 31 < nvec) {  // every load of the warp in range
 #pragma unroll
-      for (int u = 0; u < UNROLL; ++u) {
-        const uint32_t i = i0 + u * blockDim.x;
-        if (i < nvec) buf[u] = vec[i];
-      }
+          for (int u = 0; u < UNROLL; ++u) buf[u] = vec[i0 + u * blockDim.x];
 #pragma unroll
-      for (int u = 0; u < UNROLL; ++u) {
-        const uint32_t i = i0 + u * blockDim.x;
-        if (i < nvec) {
-          touch(buf[u].x, buf[u].y);
-          touch(buf[u].z, buf[u].w);
-          if (rsra) {
-            stamp_rsra(p, buf[u].x, buf[u].y, sre, stamp);
-            stamp_rsra(p, buf[u].z, buf[u].w, sre, stamp);
+          for (int u = 0; u < UNROLL; ++u) {
+            touch(buf[u].x, buf[u].y);
+            touch(buf[u].z, buf[u].w);
+          }
+          if (kRsra && p.sre_on) {
+#pragma unroll
+            for (int u = 0; u < UNROLL; ++u) {
+              rq.push(p, true, buf[u].x, buf[u].y, sre, stamp);
+              rq.push(p, true, buf[u].z, buf[u].w, sre, stamp);
+            }
+          }
+          continue;
+        }
+#pragma unroll
+        for (int u = 0; u < UNROLL; ++u) {
+          const uint32_t i = i0 + u * blockDim.x;
+          buf[u] = i < nvec ? vec[i] : make_uint4(0, 0, 0, 0);
+        }
+#pragma unroll
+        for (int u = 0; u < UNROLL; ++u) {
+          const bool ok = i0 + u * blockDim.x < nvec;
+          if (ok) {
+            touch(buf[u].x, buf[u].y);
+            touch(buf[u].z, buf[u].w);
+          }
+          if (kRsra && p.sre_on) {
+            rq.push(p, ok, buf[u].x, buf[u].y, sre, stamp);
+            rq.push(p, ok, buf[u].z, buf[u].w, sre, stamp);
           }
         }
       }
-    }
+      if (kRsra && p.sre_on) rq.drain(p, sre, stamp);
+    };
+    if (rsra)
+      scan(std::true_type{});
+    else
+      scan(std::false_type{});
     if (((end - j0) & 1) && threadIdx.x == 0) {
       const uint2 v = pairs[end - 1];
       touch(v.x, v.y);

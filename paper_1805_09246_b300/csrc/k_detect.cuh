@@ -146,15 +146,31 @@ __device__ __noinline__ void grow_grouped(const KParams& p, const uint32_t* tabl
   }
 }
 
-constexpr int kJoinThreads = 512;
+constexpr int kJoinThreads = 1024;
+
+// "Any hot" bitmap of a regrouped table: bit c is set when some of the 2^delta (<= 32) SREs
+// with low bits c is hot, i.e. when hot_group(table, c) != 0. One thread per output word.
+__global__ void __launch_bounds__(256) k_row_any(const uint32_t* __restrict__ table, uint32_t q, uint32_t delta,
+                                                 uint32_t* __restrict__ any) {
+  const uint32_t n_words = (1u << (q - delta)) >> 5;
+  for (uint32_t w = blockIdx.x * blockDim.x + threadIdx.x; w < n_words; w += gridDim.x * blockDim.x) {
+    uint32_t out = 0;
+    for (uint32_t b = 0; b < 32; ++b) out |= (hot_group(table, (w << 5) + b, delta) != 0 ? 1u : 0u) << b;
+    any[w] = out;
+  }
+}
 
 // Blocks stride over HSE(0), threads over HSE(1). For a pair (he_0, he_1), B(1) fixes the
 // low q-delta bits c of every admissible he_2 (he_2 = he_0 XOR B(2)); the regrouped row-2
-// table gives all 2^delta hot flags of those he_2 at once. The row-2 table (smem_t2 != 0)
-// and HSE(1) (when it fits in list1_cap entries) are staged in shared memory.
+// table gives all 2^delta hot flags of those he_2 at once. A chain through rows 0-2 then
+// needs some hot SRE in row 3 among the 2^delta its B(2) admits: that is one bit of row 3's
+// "any hot" bitmap (any3, when given), checked in shared memory before the chain is grown
+// from the global tables. Shared memory holds, when they fit: the row-2 table (smem_t2),
+// any3, and HSE(1) (up to list1_cap entries).
 __global__ void __launch_bounds__(kJoinThreads) k_join(const __grid_constant__ KParams p,
                                                        const uint32_t* __restrict__ hot_bits,
                                                        const uint32_t* __restrict__ tables,
+                                                       const uint32_t* __restrict__ any3,
                                                        const uint32_t* __restrict__ list0,
                                                        const uint32_t* __restrict__ list1,
                                                        const uint32_t* __restrict__ n_list, uint32_t* __restrict__ cand,
@@ -168,6 +184,7 @@ __global__ void __launch_bounds__(kJoinThreads) k_join(const __grid_constant__ K
   const uint32_t shift_hi = q - delta;
   const uint32_t cmask = (1u << shift_hi) - 1u;
   const uint32_t span = 1u << delta;  // flags per c
+  const bool grouped = span <= 32;
   const bool row2_fits_all = 2 * delta + q <= 32;
   const uint32_t nwords = (1u << q) >> 5;
   const uint32_t* t2 = tables;
@@ -176,6 +193,13 @@ __global__ void __launch_bounds__(kJoinThreads) k_join(const __grid_constant__ K
     for (uint32_t w = threadIdx.x; w < nwords; w += blockDim.x) sm[w] = tables[w];
     t2 = sm;
     sm_next = sm + nwords;
+  }
+  const uint32_t* a3 = nullptr;
+  if (any3) {
+    const uint32_t any_words = (1u << shift_hi) >> 5;
+    for (uint32_t w = threadIdx.x; w < any_words; w += blockDim.x) sm_next[w] = any3[w];
+    a3 = sm_next;
+    sm_next += any_words;
   }
   const uint32_t* l1 = list1;
   if (n1 <= list1_cap) {
@@ -190,8 +214,7 @@ __global__ void __launch_bounds__(kJoinThreads) k_join(const __grid_constant__ K
       const uint32_t b1 = he0 ^ l1[b];
       if (!fits32(1, delta, q, b1)) continue;
       const uint32_t low2 = b1 >> delta;
-      const uint32_t c = (he0 ^ low2) & cmask;
-      const uint32_t first = c << delta;
+      const uint32_t first = ((he0 ^ low2) & cmask) << delta;
       for (uint32_t base = 0; base < span; base += 32) {
         uint32_t m = t2[(first + base) >> 5];
         if (span < 32) m = (m >> (first & 31)) & ((1u << span) - 1u);
@@ -200,13 +223,161 @@ __global__ void __launch_bounds__(kJoinThreads) k_join(const __grid_constant__ K
           m &= m - 1;
           const uint32_t b2 = low2 | ((tp ^ hi0) << shift_hi);
           if (!row2_fits_all && !fits32(2, delta, q, b2)) continue;
-          if (span <= 32)
+          if (a3) {
+            const uint32_t c3 = (he0 ^ (b2 >> delta)) & cmask;
+            if (!((a3[c3 >> 5] >> (c3 & 31)) & 1u)) continue;
+          }
+          if (grouped)
             grow_grouped(p, tables, he0, b1, b2, cand, n_cand, cap, overflow);
           else
             grow_deep(p, hot_bits, he0, b1, b2, cand, n_cand, cap, overflow);
         }
       }
     }
+  }
+}
+
+// The close's report written straight into page-locked, device-mapped host memory (one
+// kernel instead of copy-engine transfers): the counters, then the first min(n_cand, cap,
+// n_stage) hosts, estimates and flags. Layout: CloseScratch | hosts[n_stage] |
+// est[n_stage] | flags[n_stage].
+__global__ void __launch_bounds__(256) k_report(const CloseScratch* __restrict__ sc,
+                                                const uint32_t* __restrict__ hosts, const float* __restrict__ est,
+                                                const uint8_t* __restrict__ flags, uint32_t cap, uint32_t n_stage,
+                                                uint8_t* __restrict__ out) {
+  const uint32_t n = min(min(sc->n_cand, cap), n_stage);
+  const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x, stride = gridDim.x * blockDim.x;
+  constexpr uint32_t kWords = sizeof(CloseScratch) / 4;
+  for (uint32_t i = tid; i < kWords; i += stride)
+    reinterpret_cast<uint32_t*>(out)[i] = reinterpret_cast<const uint32_t*>(sc)[i];
+  uint32_t* oh = reinterpret_cast<uint32_t*>(out + sizeof(CloseScratch));
+  float* oe = reinterpret_cast<float*>(oh + n_stage);
+  uint8_t* of = reinterpret_cast<uint8_t*>(oe + n_stage);
+  for (uint32_t i = tid; i < n; i += stride) {
+    oh[i] = hosts[i];
+    oe[i] = est[i];
+    of[i] = flags[i];
+  }
+}
+
+// Join for delta <= 5, tiled over (HSE(1) x HSE(0)): each thread keeps one he_1 in registers
+// and probes it against a chunk of HSE(0) staged in shared memory. With
+// g_1 = (he_1 >> delta) mod 2^(q-delta) and K(he_0) = (he_0 XOR (he_0 >> delta)) mod 2^(q-delta),
+// the low bits c of every admissible B(2) XOR he_0 are K(he_0) XOR g_1 (Eq. 7 and the overlap
+// of B(1) and B(2)), so a probe is one XOR and one lookup of the regrouped row-2 table. A
+// thread first collects, for 32 he_0 at a time, which probes found a hot row-2 group, then
+// expands only those (batched, so a warp's lanes diverge once per 32 probes, not per probe).
+// Chains that pass row 3's "any hot" test are queued in shared memory and grown by the whole
+// block at the end of the work unit; a full queue makes the thread grow the chain itself.
+constexpr int kJoinTiledThreads = 1024;
+constexpr uint32_t kJoinQueueCap = 2048;   // chains per block queue
+constexpr uint32_t kJoinChunkMax = 1024;   // he_0 per work unit
+
+__global__ void __launch_bounds__(kJoinTiledThreads) k_join_tiled(
+    const __grid_constant__ KParams p, const uint32_t* __restrict__ tables, const uint32_t* __restrict__ any3,
+    const uint32_t* __restrict__ list0, const uint32_t* __restrict__ list1, const uint32_t* __restrict__ n_list,
+    uint32_t* __restrict__ cand, uint32_t* __restrict__ n_cand, uint32_t cap, uint32_t* __restrict__ overflow,
+    uint32_t smem_t2) {
+  extern __shared__ uint32_t sm[];
+  __shared__ uint32_t s_qn;
+  const uint32_t n0 = n_list[0], n1 = n_list[1];
+  if (n0 == 0 || n1 == 0) return;
+  const uint32_t delta = p.delta, q = p.q;
+  const uint32_t shift_hi = q - delta;
+  const uint32_t cmask = (1u << shift_hi) - 1u;
+  const uint32_t span_mask = delta == 5 ? 0xFFFFFFFFu : (1u << (1u << delta)) - 1u;
+  const bool row2_fits_all = 2 * delta + q <= 32;
+  const uint32_t nwords = (1u << q) >> 5;
+  // shared memory: [row-2 table] [any3] [queue: he0 | b1 | b2] [he_0 chunk]
+  const uint32_t* t2 = tables;
+  uint32_t* next = sm;
+  if (smem_t2) {
+    for (uint32_t w = threadIdx.x; w < nwords; w += blockDim.x) sm[w] = tables[w];
+    t2 = sm;
+    next += nwords;
+  }
+  const uint32_t* a3 = nullptr;
+  if (any3) {
+    const uint32_t any_words = (1u << shift_hi) >> 5;
+    for (uint32_t w = threadIdx.x; w < any_words; w += blockDim.x) next[w] = any3[w];
+    a3 = next;
+    next += any_words;
+  }
+  uint32_t* qh = next;
+  uint32_t* qb1 = qh + kJoinQueueCap;
+  uint32_t* qb2 = qb1 + kJoinQueueCap;
+  uint32_t* s_he0 = qb2 + kJoinQueueCap;
+  if (threadIdx.x == 0) s_qn = 0;
+
+  const uint32_t tiles1 = (n1 + blockDim.x - 1) / blockDim.x;
+  const uint32_t width1 = (n1 + tiles1 - 1) / tiles1;
+  uint32_t chunk = (uint32_t)(((uint64_t)n0 * tiles1 + gridDim.x - 1) / gridDim.x);
+  chunk = max(1u, min(chunk, kJoinChunkMax));
+  const uint32_t chunks0 = (n0 + chunk - 1) / chunk;
+
+  auto lookup = [&](uint32_t c) -> uint32_t {  // hot flags of row 2's group c
+    const uint32_t first = c << delta;
+    return (t2[first >> 5] >> (first & 31)) & span_mask;
+  };
+  auto emit = [&](uint32_t he0, uint32_t b1, uint32_t b2) {
+    const uint32_t at = atomicAdd(&s_qn, 1u);
+    if (at < kJoinQueueCap) {
+      qh[at] = he0;
+      qb1[at] = b1;
+      qb2[at] = b2;
+    } else {
+      grow_grouped(p, tables, he0, b1, b2, cand, n_cand, cap, overflow);
+    }
+  };
+
+  for (uint32_t u = blockIdx.x; u < tiles1 * chunks0; u += gridDim.x) {
+    const uint32_t tile = u % tiles1, c0 = (u / tiles1) * chunk;
+    const uint32_t m0 = min(chunk, n0 - c0);
+    __syncthreads();  // previous unit's chunk and queue are done with
+    for (uint32_t j = threadIdx.x; j < m0; j += blockDim.x) s_he0[j] = list0[c0 + j];
+    __syncthreads();
+    const uint32_t b = tile * width1 + threadIdx.x;
+    const bool valid = threadIdx.x < width1 && b < n1;
+    const uint32_t he1 = valid ? list1[b] : 0u;
+    const uint32_t g1 = (he1 >> delta) & cmask;
+    if (valid) {
+      for (uint32_t j0 = 0; j0 < m0; j0 += 32) {
+        const uint32_t jn = min(32u, m0 - j0);
+        uint32_t hits = 0;
+        for (uint32_t j = 0; j < jn; ++j) {
+          const uint32_t he0 = s_he0[j0 + j];
+          const uint32_t c = ((he0 ^ (he0 >> delta)) & cmask) ^ g1;
+          hits |= (lookup(c) != 0 ? 1u : 0u) << j;
+        }
+        while (hits) {
+          const uint32_t j = __ffs(hits) - 1;
+          hits &= hits - 1;
+          const uint32_t he0 = s_he0[j0 + j];
+          const uint32_t b1 = he0 ^ he1;
+          if (!fits32(1, delta, q, b1)) continue;
+          const uint32_t low2 = b1 >> delta;
+          const uint32_t hi0 = he0 >> shift_hi;
+          uint32_t m = lookup((he0 ^ low2) & cmask);
+          while (m) {
+            const uint32_t tp = __ffs(m) - 1;  // top bits of he_2
+            m &= m - 1;
+            const uint32_t b2 = low2 | ((tp ^ hi0) << shift_hi);
+            if (!row2_fits_all && !fits32(2, delta, q, b2)) continue;
+            if (a3) {
+              const uint32_t c3 = (he0 ^ (b2 >> delta)) & cmask;
+              if (!((a3[c3 >> 5] >> (c3 & 31)) & 1u)) continue;
+            }
+            emit(he0, b1, b2);
+          }
+        }
+      }
+    }
+    __syncthreads();  // the queue is complete
+    const uint32_t qn = min(s_qn, kJoinQueueCap);
+    for (uint32_t i = threadIdx.x; i < qn; i += blockDim.x)
+      grow_grouped(p, tables, qh[i], qb1[i], qb2[i], cand, n_cand, cap, overflow);
+    __syncthreads();
+    if (threadIdx.x == 0) s_qn = 0;
   }
 }
 

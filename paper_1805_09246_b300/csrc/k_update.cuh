@@ -37,12 +37,15 @@ __device__ __forceinline__ void stamp_slea(const KParams& p, uint32_t aip, uint3
   }
 }
 
-// Algorithm 3 for one pair: if LSB(H1(bip)) >= tau, cell H2(bip) of SRE RSRA[i, RHFG[i](aip)]
-// in every row i, with RHFG[i] from Eq. 6.
-__device__ __forceinline__ void stamp_rsra(const KParams& p, uint32_t aip, uint32_t bip, uint8_t* sre,
+// Algorithm 3, sampling test: LSB(H1(bip)) >= tau (the low tau bits of H1 are zero).
+__device__ __forceinline__ bool rsra_sampled(const KParams& p, uint32_t bip) {
+  return (mas_hi(p.key_a[kH1], p.key_b[kH1], bip) & p.tau_mask) == 0;
+}
+
+// Algorithm 3's writes for a sampled pair: cell H2(bip) of SRE RSRA[i, RHFG[i](aip)] in every
+// row i, with RHFG[i] from Eq. 6.
+__device__ __forceinline__ void rsra_write(const KParams& p, uint32_t aip, uint32_t bip, uint8_t* sre,
                                            uint8_t stamp) {
-  const uint32_t h1 = mas_top(p.key_a[kH1], p.key_b[kH1], bip, 32);
-  if (!p.sre_on || (h1 & p.tau_mask) != 0) return;  // LSB(h1) < tau
   const uint32_t h2 = mas_top(p.key_a[kH2], p.key_b[kH2], bip, 3);
   const uint32_t r0 = mas_top(p.key_a[kR0], p.key_b[kR0], aip, p.q);
   const uint32_t qmask = (1u << p.q) - 1u;
@@ -52,6 +55,53 @@ __device__ __forceinline__ void stamp_rsra(const KParams& p, uint32_t aip, uint3
     sre[((((uint64_t)i << p.q) + col) << 3) + h2] = stamp;
   }
 }
+
+// Algorithm 3 for one pair.
+__device__ __forceinline__ void stamp_rsra(const KParams& p, uint32_t aip, uint32_t bip, uint8_t* sre,
+                                           uint8_t stamp) {
+  if (p.sre_on && rsra_sampled(p, bip)) rsra_write(p, aip, bip, sre, stamp);
+}
+
+// Warp-cooperative Algorithm 3 for the streaming kernels. Only 2^-tau of the pairs are
+// sampled, so a per-pair branch into the write path would be taken by some lane of most
+// warps; instead every lane tests its pairs, the sampled ones are appended to the warp's
+// queue in shared memory (ballot + prefix count), and each time 32 are queued the whole
+// warp writes them, one pair per lane. All 32 lanes must call push() and drain() together.
+constexpr uint32_t kRsraQueueEntries = 64;  // per warp: < 32 waiting + up to 32 pushed at once
+
+struct RsraQueue {
+  uint2* q;      // this warp's kRsraQueueEntries entries
+  uint32_t n;    // entries waiting (the same in every lane)
+  uint32_t lane;
+
+  __device__ __forceinline__ void push(const KParams& p, bool valid, uint32_t aip, uint32_t bip, uint8_t* sre,
+                                       uint8_t stamp) {
+    const bool s = valid && rsra_sampled(p, bip);
+    const uint32_t b = __ballot_sync(0xFFFFFFFFu, s);
+    if (b == 0) return;
+    if (s) q[n + __popc(b & ((1u << lane) - 1u))] = make_uint2(aip, bip);
+    n += __popc(b);
+    if (n >= 32) {
+      __syncwarp();
+      const uint2 e = q[lane];
+      __syncwarp();
+      if (lane + 32 < n) q[lane] = q[lane + 32];
+      __syncwarp();
+      n -= 32;
+      rsra_write(p, e.x, e.y, sre, stamp);
+    }
+  }
+
+  __device__ __forceinline__ void drain(const KParams& p, uint8_t* sre, uint8_t stamp) {
+    __syncwarp();
+    if (lane < n) {
+      const uint2 e = q[lane];
+      rsra_write(p, e.x, e.y, sre, stamp);
+    }
+    __syncwarp();
+    n = 0;
+  }
+};
 
 template <int R2>
 __device__ __forceinline__ void apply_pair(const KParams& p, uint32_t aip, uint32_t bip, uint8_t* sre,

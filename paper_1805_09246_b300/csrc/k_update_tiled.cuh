@@ -18,6 +18,44 @@
 namespace sse {
 
 constexpr int kTiledThreads = 1024;
+// Shared memory behind the tile's bitmap: one RSRA queue per warp.
+constexpr uint32_t kRsraQueueBytes = (kTiledThreads / 32) * kRsraQueueEntries * sizeof(uint2);
+
+// Hashing and marking for one tile: cell H3(bip) of SLE LH_row(aip) (Algorithm 6) as a bit
+// of the tile's shared-memory bitmap. Keys are split into 32-bit halves once, so each hash
+// is one widening multiply-add and one multiply-add. WHOLE: the tile is the whole row
+// (lo = 0, every cell of the row is inside the bitmap), so no range test is needed.
+struct SleTile {
+  uint32_t a3lo, a3hi, alo, ahi;
+  uint64_t b3, bl;
+  uint32_t sh3, shl, d2, lo, span;
+
+  __device__ __forceinline__ SleTile(const KParams& p, uint32_t row, uint32_t lo_, uint32_t span_)
+      : a3lo((uint32_t)p.key_a[kH3]), a3hi((uint32_t)(p.key_a[kH3] >> 32)), alo((uint32_t)p.key_a[kLH + row]),
+        ahi((uint32_t)(p.key_a[kLH + row] >> 32)), b3(p.key_b[kH3]), bl(p.key_b[kLH + row]),
+        sh3(32 - p.lg_eta2), shl(32 - p.q2), d2(p.delta2), lo(lo_), span(span_) {}
+
+  static __device__ __forceinline__ uint32_t hash_hi(uint32_t alo_, uint32_t ahi_, uint64_t b, uint32_t x) {
+    const uint64_t t = (uint64_t)alo_ * x + b;
+    return (uint32_t)(t >> 32) + ahi_ * x;
+  }
+
+  template <bool WHOLE, bool CHECK>
+  __device__ __forceinline__ void touch(uint32_t* bm, uint32_t aip, uint32_t bip) const {
+    const uint32_t h3 = hash_hi(a3lo, a3hi, b3, bip) >> sh3;  // sh3, shl <= 31: eta', 2^q' >= 2
+    const uint32_t lh = hash_hi(alo, ahi, bl, aip) >> shl;
+    uint32_t cell = lh * d2 + h3;
+    if (!WHOLE) {
+      cell -= lo;  // wraps to a large value below lo
+      if (cell >= span) return;
+    }
+    uint32_t bit;  // 1 << (cell mod 32): funnel shift of {1:0}
+    asm("shf.l.wrap.b32 %0, %1, %2, %3;" : "=r"(bit) : "r"(0u), "r"(1u), "r"(cell));
+    uint32_t* w = bm + (cell >> 5);
+    if (CHECK && (*w & bit)) return;
+    atomicOr(w, bit);
+  }
+};
 
 struct TileGeometry {
   uint32_t tiles;         // tiles per group (r' * pieces)
@@ -26,10 +64,10 @@ struct TileGeometry {
   uint32_t groups;        // groups of CTAs; the pairs are split evenly between groups
 };
 
-// grid = groups * tiles CTAs; dynamic shared memory = piece_bytes / 8. UNROLL 128-bit loads
+// grid = groups * tiles CTAs; dynamic shared memory = piece_bytes / 8 + kRsraQueueBytes. UNROLL 128-bit loads
 // are in flight per thread; CHECK reads the bitmap word first and skips the atomic when the
 // bit is already set (repeated pairs are common in real traffic).
-template <int UNROLL, bool CHECK>
+template <int UNROLL, bool CHECK, bool WHOLE>
 __global__ void __launch_bounds__(kTiledThreads, 1) k_update_tiled(const __grid_constant__ KParams p, TileGeometry g,
                                                                    const uint2* __restrict__ pairs, uint64_t n,
                                                                    uint8_t* __restrict__ sre,
@@ -44,22 +82,13 @@ __global__ void __launch_bounds__(kTiledThreads, 1) k_update_tiled(const __grid_
   const uint32_t lo = piece * g.piece_bytes;  // cell range [lo, lo + piece_bytes) of the row
   const uint32_t words = g.piece_bytes >> 5;
   for (uint32_t w = threadIdx.x; w < words; w += blockDim.x) bm[w] = 0;
+  RsraQueue rq{reinterpret_cast<uint2*>(bm + words) + (threadIdx.x >> 5) * kRsraQueueEntries, 0u, threadIdx.x & 31u};
   __syncthreads();
 
   // this group's pairs: [begin, end)
   const uint64_t begin = n * group / g.groups, end = n * (group + 1) / g.groups;
-  const uint64_t a3 = p.key_a[kH3], b3 = p.key_b[kH3];
-  const uint64_t al = p.key_a[kLH + row], bl = p.key_b[kLH + row];
-  const uint32_t sh3 = 32 - p.lg_eta2, shl = 32 - p.q2, d2 = p.delta2, span = g.piece_bytes;
-  auto touch = [&](uint32_t aip, uint32_t bip) {
-    const uint32_t h3 = (uint32_t)((uint64_t)mas_hi(a3, b3, bip) >> sh3);
-    const uint32_t lh = (uint32_t)((uint64_t)mas_hi(al, bl, aip) >> shl);
-    const uint32_t cell = lh * d2 + h3 - lo;  // wraps to a large value below lo
-    if (cell < span) {
-      const uint32_t bit = 1u << (cell & 31);
-      if (!CHECK || !(bm[cell >> 5] & bit)) atomicOr(&bm[cell >> 5], bit);
-    }
-  };
+  const SleTile st(p, row, lo, g.piece_bytes);
+  auto touch = [&](uint32_t aip, uint32_t bip) { st.touch<WHOLE, CHECK>(bm, aip, bip); };
   // peel to a 16-byte boundary, then two pairs per 128-bit load; the peeled and the odd
   // last pair's RSRA work belongs to tile 0
   uint64_t j0 = begin;
@@ -74,9 +103,10 @@ __global__ void __launch_bounds__(kTiledThreads, 1) k_update_tiled(const __grid_
   const uint4* vec = reinterpret_cast<const uint4*>(pairs + j0);
   const uint32_t nvec = (uint32_t)((end - j0) >> 1);
   const uint32_t stride = blockDim.x;
-  // Block iteration k covers vectors [k*stride*UNROLL, (k+1)*stride*UNROLL); sub-step u of
-  // it is owned, for RSRA, by tile (k*UNROLL + u) mod tiles — uniform across the block, so
-  // the RSRA branch never diverges inside a warp.
+  // Block iteration k covers vectors [k*stride*UNROLL, (k+1)*stride*UNROLL); its RSRA work
+  // belongs to tile k mod tiles. The test is uniform across the block and taken once per
+  // 2*UNROLL pairs, so the RSRA code is a real branch, skipped by the other tiles (per-pair
+  // ownership let the compiler predicate the hashing of H1 into every tile).
   const uint32_t full = nvec / (stride * UNROLL);
   uint32_t owner = 0;
   for (uint32_t k = 0; k < full; ++k) {
@@ -88,26 +118,31 @@ __global__ void __launch_bounds__(kTiledThreads, 1) k_update_tiled(const __grid_
     for (int u = 0; u < UNROLL; ++u) {
       touch(buf[u].x, buf[u].y);
       touch(buf[u].z, buf[u].w);
-      if (owner == tile) {
-        stamp_rsra(p, buf[u].x, buf[u].y, sre, stamp);
-        stamp_rsra(p, buf[u].z, buf[u].w, sre, stamp);
-      }
-      owner = owner + 1 == g.tiles ? 0 : owner + 1;
     }
-  }
-  for (uint32_t u = 0; u < UNROLL; ++u) {  // remainder: the last, partial iteration
-    const uint32_t i = full * stride * UNROLL + u * stride + threadIdx.x;
-    if (i < nvec) {
-      const uint4 v = vec[i];
-      touch(v.x, v.y);
-      touch(v.z, v.w);
-      if (owner == tile) {
-        stamp_rsra(p, v.x, v.y, sre, stamp);
-        stamp_rsra(p, v.z, v.w, sre, stamp);
+    if (owner == tile && p.sre_on) {
+#pragma unroll
+      for (int u = 0; u < UNROLL; ++u) {
+        rq.push(p, true, buf[u].x, buf[u].y, sre, stamp);
+        rq.push(p, true, buf[u].z, buf[u].w, sre, stamp);
       }
     }
     owner = owner + 1 == g.tiles ? 0 : owner + 1;
   }
+  const bool mine = owner == tile && p.sre_on;  // remainder: the last, partial iteration
+  for (uint32_t u = 0; u < UNROLL; ++u) {
+    const uint32_t i = full * stride * UNROLL + u * stride + threadIdx.x;
+    const bool ok = i < nvec;
+    const uint4 v = ok ? vec[i] : make_uint4(0, 0, 0, 0);
+    if (ok) {
+      touch(v.x, v.y);
+      touch(v.z, v.w);
+    }
+    if (mine) {
+      rq.push(p, ok, v.x, v.y, sre, stamp);
+      rq.push(p, ok, v.z, v.w, sre, stamp);
+    }
+  }
+  if (p.sre_on) rq.drain(p, sre, stamp);
   if (((end - j0) & 1) && threadIdx.x == 0) {
     const uint2 v = pairs[end - 1];
     touch(v.x, v.y);

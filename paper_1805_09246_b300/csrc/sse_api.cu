@@ -99,9 +99,11 @@ struct sse_handle {
   uint32_t* list0 = nullptr;
   uint32_t* list1 = nullptr;
   uint32_t* tables = nullptr;  // hot bitmaps of rows 2..r-1 regrouped for the join
+  uint32_t* any3 = nullptr;    // row 3's "any hot" bitmap over c (r > 3, delta <= 5)
   uint32_t join_smem_t2 = 0;   // stage the row-2 table in shared memory
   uint32_t join_list1_cap = 0; // HSE(1) entries staged in shared memory when it fits
   size_t join_smem = 0;
+  size_t join_tiled_smem = 0;  // k_join_tiled (delta <= 5)
   uint32_t* cand = nullptr;  // two buffers of cand_cap entries
   uint32_t* cand_alt = nullptr;
   float* est = nullptr;
@@ -118,6 +120,16 @@ struct sse_handle {
   cudaEvent_t ev_copied[2] = {nullptr, nullptr};
   cudaEvent_t ev_used[2] = {nullptr, nullptr};
   cudaStream_t copy_stream = nullptr;
+  // sse_close_slice as one CUDA graph (captured on a private stream, replayed on `stream`)
+  int close_graph = 1;
+  cudaStream_t capture_stream = nullptr;
+  cudaGraph_t close_g = nullptr;
+  cudaGraphExec_t close_exec = nullptr;
+  uint32_t* close_sorted = nullptr;  // the candidate buffer the captured sort ends in
+  uint64_t close_kernels = 0;        // kernels per replay
+  uint32_t report_stage_n = 0;       // report entries the graph writes to report_stage
+  uint8_t* report_stage = nullptr;   // page-locked, mapped: CloseScratch | hosts | est | flags
+  uint8_t* report_stage_dev = nullptr;  // its device address
 };
 
 namespace {
@@ -217,14 +229,17 @@ TileGeometry make_tiles(const sse_params& p, const sse_derived& d, int num_sms) 
 using TiledKernel = void (*)(KParams, TileGeometry, const uint2*, uint64_t, uint8_t*, uint32_t*, uint32_t,
                             const uint32_t*);
 struct TiledVariant {
-  TiledKernel fn;
+  TiledKernel fn;        // tiles smaller than a row
+  TiledKernel fn_whole;  // one tile per row (no range test)
   int unroll;
   bool check;
 };
+#define SSE_TILED(U, C) {k_update_tiled<U, C, false>, k_update_tiled<U, C, true>, U, C}
 const TiledVariant kTiledVariants[] = {
-    {k_update_tiled<4, false>, 4, false}, {k_update_tiled<2, false>, 2, false}, {k_update_tiled<8, false>, 8, false},
-    {k_update_tiled<4, true>, 4, true},   {k_update_tiled<2, true>, 2, true},   {k_update_tiled<8, true>, 8, true},
+    SSE_TILED(4, false), SSE_TILED(2, false), SSE_TILED(8, false),
+    SSE_TILED(4, true),  SSE_TILED(2, true),  SSE_TILED(8, true),
 };
+#undef SSE_TILED
 constexpr int kNumTiledVariants = sizeof(kTiledVariants) / sizeof(kTiledVariants[0]);
 // Update variants seen by the autotuner: 0 = direct, 1 + v = tiled variant v.
 constexpr int kNumUpdateVariants = 1 + kNumTiledVariants;
@@ -232,8 +247,8 @@ constexpr int kNumUpdateVariants = 1 + kNumTiledVariants;
 int launch_update_tiled(sse_handle* h, const uint32_t* d_pairs, uint64_t n, int variant) {
   const uint8_t stamp = stamp_of(h->slice);
   const TileGeometry& g = h->tiles;
-  const size_t smem = g.piece_bytes / 8;
-  const TiledKernel fn = kTiledVariants[variant].fn;
+  const size_t smem = g.piece_bytes / 8 + kRsraQueueBytes;
+  const TiledKernel fn = g.pieces == 1 ? kTiledVariants[variant].fn_whole : kTiledVariants[variant].fn;
   constexpr uint64_t kMaxPairsPerLaunch = 1ull << 30;  // keeps per-group indices in 32 bits
   for (uint64_t done = 0; done < n; done += kMaxPairsPerLaunch) {
     const uint64_t m = std::min(kMaxPairsPerLaunch, n - done);
@@ -375,7 +390,12 @@ void sse_destroy(sse_handle* h) {
   cudaFree(h->flags);
   cudaFree(h->scratch);
   cudaFree(h->query_active2);
+  cudaFree(h->any3);
   if (h->host_scratch) cudaFreeHost(h->host_scratch);
+  if (h->close_exec) cudaGraphExecDestroy(h->close_exec);
+  if (h->close_g) cudaGraphDestroy(h->close_g);
+  if (h->capture_stream) cudaStreamDestroy(h->capture_stream);
+  if (h->report_stage) cudaFreeHost(h->report_stage);
   delete h;
 }
 
@@ -428,23 +448,42 @@ int sse_init(const sse_params* p, void* cuda_stream, sse_handle** out) {
   h->sre = h->state;
   h->sle = h->state + d.sre_bytes;
   h->tiles = make_tiles(q, d, h->num_sms);
-  for (int v = 0; v < kNumTiledVariants; ++v) {
-    if (cudaFuncSetAttribute(kTiledVariants[v].fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)(h->tiles.piece_bytes / 8)) != cudaSuccess) {
+  for (int v = 0; v < 2 * kNumTiledVariants; ++v) {
+    const TiledKernel fn = (v & 1) ? kTiledVariants[v / 2].fn_whole : kTiledVariants[v / 2].fn;
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(h->tiles.piece_bytes / 8 + kRsraQueueBytes)) !=
+        cudaSuccess) {
       cudaGetLastError();
       sse_destroy(h);
       return SSE_ERR_CUDA;
     }
   }
-  // join shared memory: the regrouped row-2 table (2^q bits) up to q = 20, then as much of
-  // HSE(1) as fits in the rest of a 200 KiB budget
+  // join shared memory: the regrouped row-2 table (2^q bits) up to q = 20, row 3's "any hot"
+  // bitmap (2^(q-delta) bits) when it fits, then as much of HSE(1) as fits in the rest of a
+  // 216 KiB budget
   {
-    const size_t budget = 200u * 1024u;
+    const size_t budget = 216u * 1024u;
     const size_t t2_bytes = (size_t)(list_entries / 8);
     h->join_smem_t2 = t2_bytes <= 128u * 1024u ? 1u : 0u;
-    const size_t used = h->join_smem_t2 ? t2_bytes : 0;
+    size_t used = h->join_smem_t2 ? t2_bytes : 0;
+    const size_t any_bytes = ((size_t)1 << (q.q - d.delta)) / 8;
+    if (q.r > 3 && d.delta <= 5 && used + any_bytes <= 160u * 1024u) {
+      if (cudaMalloc(&h->any3, any_bytes) != cudaSuccess) {
+        cudaGetLastError();
+        sse_destroy(h);
+        return SSE_ERR_OOM;
+      }
+      used += any_bytes;
+    }
     h->join_list1_cap = (uint32_t)std::min<uint64_t>(list_entries, (budget - used) / 4);
     h->join_smem = used + (size_t)h->join_list1_cap * 4;
+    h->join_tiled_smem = used + (3 * (size_t)kJoinQueueCap + kJoinChunkMax) * 4;
+    if (d.delta <= 5 && cudaFuncSetAttribute(k_join_tiled, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)h->join_tiled_smem) != cudaSuccess) {
+      cudaGetLastError();
+      sse_destroy(h);
+      return SSE_ERR_CUDA;
+    }
     if (cudaFuncSetAttribute(k_join, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)h->join_smem) != cudaSuccess) {
       cudaGetLastError();
       sse_destroy(h);
@@ -604,7 +643,7 @@ namespace {
 // Detection kernels of a close (no host synchronisation, so a CUDA graph can hold them):
 // the sorted candidates end in *sorted, estimates and flags in h->est / h->flags, and the
 // counters are copied to the pinned h->host_scratch.
-int close_enqueue(sse_handle* h, uint32_t** sorted) {
+int close_enqueue(sse_handle* h, uint32_t** sorted, bool copy_counters = true) {
   CloseScratch* sc = h->scratch;
   SSE_CUDA(h, cudaMemsetAsync(sc, 0, sizeof(CloseScratch), h->stream));
   int rc = launch_close_pass(h, sc->active2, 3u);
@@ -620,9 +659,20 @@ int close_enqueue(sse_handle* h, uint32_t** sorted) {
     const dim3 grid(grid_for(h, words, 256, 2), h->p.r - 2);
     k_row_regroup<<<grid, 256, 0, h->stream>>>(h->hot_bits, h->p.q, h->p.delta, h->tables);
     SSE_LAUNCHED(h);
-    k_join<<<h->num_sms, kJoinThreads, h->join_smem, h->stream>>>(h->kp, h->hot_bits, h->tables, h->list0, h->list1,
-                                                                  sc->n_list, h->cand, &sc->n_cand, h->cand_cap,
-                                                                  &sc->overflow, h->join_smem_t2, h->join_list1_cap);
+    if (h->any3) {
+      const uint32_t any_words = (1u << (h->p.q - h->kp.delta)) >> 5;
+      k_row_any<<<(any_words + 255) / 256, 256, 0, h->stream>>>(h->tables + words, h->p.q, h->kp.delta, h->any3);
+      SSE_LAUNCHED(h);
+    }
+    if (h->kp.delta <= 5)
+      k_join_tiled<<<h->num_sms, kJoinTiledThreads, h->join_tiled_smem, h->stream>>>(
+          h->kp, h->tables, h->any3, h->list0, h->list1, sc->n_list, h->cand, &sc->n_cand, h->cand_cap, &sc->overflow,
+          h->join_smem_t2);
+    else
+      k_join<<<h->num_sms, kJoinThreads, h->join_smem, h->stream>>>(h->kp, h->hot_bits, h->tables, h->any3, h->list0,
+                                                                    h->list1, sc->n_list, h->cand, &sc->n_cand,
+                                                                    h->cand_cap, &sc->overflow, h->join_smem_t2,
+                                                                    h->join_list1_cap);
     SSE_LAUNCHED(h);
   }
   *sorted = launch_sort(h);
@@ -634,7 +684,8 @@ int close_enqueue(sse_handle* h, uint32_t** sorted) {
                                                     nullptr, nullptr, nullptr, &sc->n_super);
     SSE_LAUNCHED(h);
   }
-  SSE_CUDA(h, cudaMemcpyAsync(h->host_scratch, sc, sizeof(CloseScratch), cudaMemcpyDeviceToHost, h->stream));
+  if (copy_counters)
+    SSE_CUDA(h, cudaMemcpyAsync(h->host_scratch, sc, sizeof(CloseScratch), cudaMemcpyDeviceToHost, h->stream));
   return SSE_OK;
 }
 
@@ -674,6 +725,95 @@ int close_collect(sse_handle* h, const uint32_t* sorted, sse_report* out) {
   return status;
 }
 
+// sse_close_slice replayed from a CUDA graph: the close kernels (which read the stamp from
+// the device clock), the copy of the counters and of the first report_stage_n report
+// entries into pinned memory, and the clock tick. One launch and one synchronisation per
+// slice; reports longer than report_stage_n are completed with direct copies.
+int close_slice_graph(sse_handle* h, sse_report* out) {
+  if (!h->close_exec) {
+    if (!h->capture_stream) SSE_CUDA(h, cudaStreamCreateWithFlags(&h->capture_stream, cudaStreamNonBlocking));
+    if (!h->report_stage) {
+      h->report_stage_n = std::min<uint32_t>(h->cand_cap, 8192u);
+      SSE_CUDA(h, cudaHostAlloc(&h->report_stage, sizeof(CloseScratch) + (size_t)h->report_stage_n * 9,
+                                cudaHostAllocMapped));
+      SSE_CUDA(h, cudaHostGetDevicePointer(reinterpret_cast<void**>(&h->report_stage_dev), h->report_stage, 0));
+    }
+    const cudaStream_t user = h->stream;
+    const uint64_t launches0 = h->launches;
+    h->stream = h->capture_stream;
+    cudaError_t e = cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal);
+    int rc = SSE_OK;
+    if (e == cudaSuccess) {
+      rc = close_enqueue(h, &h->close_sorted, false);
+      if (rc == SSE_OK) {
+        k_report<<<8, 256, 0, h->stream>>>(h->scratch, h->close_sorted, h->est, h->flags, h->cand_cap,
+                                           h->report_stage_n, h->report_stage_dev);
+        SSE_LAUNCHED(h);
+        k_tick<<<1, 32, 0, h->stream>>>(h->clock, 1);
+        SSE_LAUNCHED(h);
+      }
+      cudaGraph_t g = nullptr;
+      const cudaError_t e2 = cudaStreamEndCapture(h->stream, &g);
+      if (e2 == cudaSuccess && rc == SSE_OK) {
+        h->close_g = g;
+        e = cudaGraphInstantiate(&h->close_exec, g, 0);
+      } else {
+        if (g) cudaGraphDestroy(g);
+        if (e == cudaSuccess) e = e2;
+      }
+    }
+    h->stream = user;
+    h->close_kernels = h->launches - launches0;
+    h->launches = launches0;
+    if (rc) return rc;
+    SSE_CUDA(h, e);
+  }
+  SSE_CUDA(h, cudaGraphLaunch(h->close_exec, h->stream));
+  h->launches += h->close_kernels;
+  SSE_CUDA(h, cudaStreamSynchronize(h->stream));
+  CloseScratch hs;
+  memcpy(&hs, h->report_stage, sizeof(hs));  // written by k_report before the synchronisation
+  const uint32_t n_found = hs.n_cand;
+  const uint32_t n_kept = std::min(n_found, h->cand_cap);
+  int status = n_found > h->cand_cap ? SSE_ERR_CAPACITY : SSE_OK;
+  h->stats.slice = h->slice;
+  for (int i = 0; i < kMaxRows; ++i) {
+    h->stats.hot[i] = i < (int)h->p.r ? hs.hot[i] : 0;
+    h->stats.active2[i] = i < (int)h->p.r2 ? hs.active2[i] : 0;
+  }
+  h->stats.join_pairs = (uint64_t)hs.n_list[0] * hs.n_list[1];
+  h->stats.n_candidates = n_found;
+  h->stats.n_super = hs.n_super;
+  if (out) {
+    out->slice = h->slice;
+    out->n_candidates = n_found;
+    out->n_super = hs.n_super;
+    const uint32_t n_copy = std::min(n_kept, out->cap);
+    out->truncated = (n_found > n_copy) ? 1u : 0u;
+    if (n_kept > out->cap) status = SSE_ERR_CAPACITY;
+    const uint32_t staged = std::min(n_copy, h->report_stage_n);
+    const size_t n = h->report_stage_n;
+    const uint8_t* st = h->report_stage + sizeof(CloseScratch);
+    if (out->hosts) memcpy(out->hosts, st, (size_t)staged * 4);
+    if (out->est) memcpy(out->est, st + n * 4, (size_t)staged * 4);
+    if (out->flags) memcpy(out->flags, st + n * 8, staged);
+    if (n_copy > staged) {  // the rest, straight from the device
+      const uint32_t m = n_copy - staged;
+      if (out->hosts)
+        SSE_CUDA(h, cudaMemcpyAsync(out->hosts + staged, h->close_sorted + staged, (size_t)m * 4,
+                                    cudaMemcpyDeviceToHost, h->stream));
+      if (out->est)
+        SSE_CUDA(h, cudaMemcpyAsync(out->est + staged, h->est + staged, (size_t)m * 4, cudaMemcpyDeviceToHost,
+                                    h->stream));
+      if (out->flags)
+        SSE_CUDA(h, cudaMemcpyAsync(out->flags + staged, h->flags + staged, m, cudaMemcpyDeviceToHost, h->stream));
+      SSE_CUDA(h, cudaStreamSynchronize(h->stream));
+    }
+  }
+  h->slice += 1;
+  return status;
+}
+
 }  // namespace
 
 extern "C" {
@@ -681,6 +821,7 @@ extern "C" {
 int sse_close_slice(sse_handle* h, sse_report* out) {
   if (!h) return SSE_ERR_INVALID_PARAM;
   if (h->sticky) return h->sticky;
+  if (h->close_graph) return close_slice_graph(h, out);
   uint32_t* sorted = nullptr;
   int rc = close_enqueue(h, &sorted);
   if (rc) return rc;
@@ -688,6 +829,12 @@ int sse_close_slice(sse_handle* h, sse_report* out) {
   if (status != SSE_OK && status != SSE_ERR_CAPACITY) return status;
   const int rc_tick = advance_clock(h);
   return rc_tick ? rc_tick : status;
+}
+
+int sse_close_use_graph(sse_handle* h, int enable) {
+  if (!h) return SSE_ERR_INVALID_PARAM;
+  h->close_graph = enable ? 1 : 0;
+  return SSE_OK;
 }
 
 int sse_merge(sse_handle* dst, const sse_handle* const* srcs, int n) {
@@ -929,8 +1076,9 @@ void drop_graphs(sse_batch* b) {
   }
 }
 
-RoutersKernel routers_kernel(int unroll) {
-  return unroll == 2 ? k_update_routers<2> : unroll == 8 ? k_update_routers<8> : k_update_routers<4>;
+RoutersKernel routers_kernel(int unroll, bool whole) {
+  if (whole) return unroll == 2 ? k_update_routers<2, true> : unroll == 8 ? k_update_routers<8, true> : k_update_routers<4, true>;
+  return unroll == 2 ? k_update_routers<2, false> : unroll == 8 ? k_update_routers<8, false> : k_update_routers<4, false>;
 }
 
 // Update of every router (one persistent launch) and the bitmap apply, on b->stream.
@@ -940,7 +1088,8 @@ int batch_enqueue_update(sse_batch* b) {
   const TileGeometry& tg = g->tiles;
   SSE_CUDA(g, cudaMemsetAsync(b->tile_next, 0, tg.tiles * sizeof(uint32_t), b->stream));
   const uint32_t per_tile = std::max<uint32_t>(1u, (uint32_t)g->num_sms / tg.tiles);
-  routers_kernel(b->unroll)<<<tg.tiles * per_tile, kTiledThreads, tg.piece_bytes / 8, b->stream>>>(
+  routers_kernel(b->unroll, tg.pieces == 1)<<<tg.tiles * per_tile, kTiledThreads, tg.piece_bytes / 8 + kRsraQueueBytes,
+                                               b->stream>>>(
       g->kp, tg, b->rt, b->n, g->d.sre_bytes, b->d_in, b->item_pairs, b->tile_next, g->clock);
   SSE_LAUNCHED(g);
   const uint64_t words = g->d.sle_bytes / 32;
@@ -1023,9 +1172,9 @@ int sse_batch_create(const sse_params* p, int n_routers, uint64_t capacity_pairs
     }
   }
   if (rc == SSE_OK) {
-    for (int v = 2; v <= 8; v *= 2)
-      if (cudaFuncSetAttribute(routers_kernel(v), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)(b->global->tiles.piece_bytes / 8)) != cudaSuccess) {
+    for (int v = 0; v < 6; ++v)  // loads in flight 2, 4, 8 x (part of a row, whole row)
+      if (cudaFuncSetAttribute(routers_kernel(2 << (v >> 1), v & 1), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)(b->global->tiles.piece_bytes / 8 + kRsraQueueBytes)) != cudaSuccess) {
         cudaGetLastError();
         rc = SSE_ERR_CUDA;
       }

@@ -158,6 +158,7 @@ def lib() -> ctypes.CDLL:
             "sse_server_global": (i32, [vp, ctypes.POINTER(vp)]),
             "sse_cuda_error": (ctypes.c_char_p, [vp]),
             "sse_reset": (i32, [vp]),
+            "sse_close_use_graph": (i32, [vp, i32]),
             "sse_batch_set_mode": (i32, [vp, i32]),
             "sse_batch_reset": (i32, [vp]),
             "sse_features": (i32, [vp, vp, u32, vp]),
@@ -331,9 +332,10 @@ class Estimator:
     def close_slice(self, cap: int | None = None, raise_on_capacity: bool = True) -> Report:
         """Detect the sliding super points of the window ending at the current slice."""
         cap = self.params.max_candidates if cap is None else cap
-        hosts = np.zeros(cap, np.uint32)
-        est = np.zeros(cap, np.float32)
-        flags = np.zeros(cap, np.uint8)
+        bufs = getattr(self, "_report_bufs", None)
+        if bufs is None or len(bufs[0]) != cap:  # reused across slices (allocating them costs more than the copy)
+            bufs = self._report_bufs = (np.empty(cap, np.uint32), np.empty(cap, np.float32), np.empty(cap, np.uint8))
+        hosts, est, flags = bufs
         rep = _Report(0, 0, 0, cap, 0, hosts.ctypes.data, est.ctypes.data, flags.ctypes.data)
         rc = self._lib.sse_close_slice(self._h, ctypes.byref(rep))
         if rc != SSE_OK and (rc != ERR_CAPACITY or raise_on_capacity):
@@ -400,6 +402,10 @@ class Estimator:
 
     def sync(self) -> None:
         _check(self._lib.sse_sync(self._h), "sse_sync")
+
+    def close_use_graph(self, enable: bool) -> None:
+        """Replay sse_close_slice from a CUDA graph (default) or launch its kernels one by one."""
+        _check(self._lib.sse_close_use_graph(self._h, 1 if enable else 0), "sse_close_use_graph")
 
     def reset(self) -> None:
         """Back to the initial state at slice 0."""

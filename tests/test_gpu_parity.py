@@ -397,3 +397,27 @@ def test_invalid_arguments():
     assert lib.sse_query(est.handle, None, 3, None, None, None) < 0
     assert lib.sse_set_update_mode(est.handle, 7) < 0
     est.sync()
+
+
+def test_close_graph_equals_direct_launches():
+    """sse_close_slice replayed from its CUDA graph gives the same reports, statistics and
+    state as the kernels launched one by one, also when a handle switches between them."""
+    S = sse()
+    p = S.Params(seed=41)
+    tr = synth.Traffic(synth.small_trace(seed=41))
+    a, b = S.Estimator(p), S.Estimator(p)
+    b.close_use_graph(False)
+    for t in range(6):
+        pairs = helpers.to_device(tr.slice(0, t))
+        a.update(pairs)
+        b.update(pairs)
+        if t == 3:
+            a.close_use_graph(False)
+            b.close_use_graph(True)
+        ra, rb = a.close_slice(), b.close_slice()
+        assert np.array_equal(ra.hosts, rb.hosts) and np.array_equal(ra.est, rb.est)
+        assert np.array_equal(ra.flags, rb.flags) and ra.n_super == rb.n_super and ra.slice == rb.slice == t
+        assert a.stats() == b.stats()
+    for x, y in zip(a.read_stamps(), b.read_stamps()):
+        assert np.array_equal(x, y)
+    assert a.slice == b.slice == 6
