@@ -215,6 +215,15 @@ SSE_API int sse_close_slice(sse_handle* h, sse_report* out);
  * kernels one by one. Results are identical. Errors: INVALID_PARAM. */
 SSE_API int sse_close_use_graph(sse_handle* h, int enable);
 
+/* sse_close_slice in two halves, so that the next slice's updates can be enqueued while the
+ * report is produced: _async enqueues the close (graph mode only) and moves the handle to
+ * the next slice; _wait blocks until that close's report is in host memory and fills out
+ * (as sse_close_slice). One close may be pending; sse_close_slice, a second _async and
+ * sse_close_use_graph are refused meanwhile. Errors: STATE (no graph mode, a close already
+ * pending, or none pending for _wait), CAPACITY, CUDA. */
+SSE_API int sse_close_slice_async(sse_handle* h);
+SSE_API int sse_close_slice_wait(sse_handle* h, sse_report* out);
+
 /* Moves to the next slice without detection: expires old cells and advances, so a router
  * whose super points are detected elsewhere (after a merge) keeps a valid window.
  * Asynchronous. Errors: CUDA. */

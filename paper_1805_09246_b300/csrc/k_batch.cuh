@@ -102,6 +102,7 @@ __global__ void __launch_bounds__(kTiledThreads, 1)
     // the item's RSRA owner runs a separate copy of the loop, so the other tiles execute
     // none of its sampling; iterations are uniform per warp (RsraQueue needs every lane)
     const uint32_t lane = threadIdx.x & 31u;
+    const uint64_t policy = stream_policy();
     auto scan = [&](auto with_rsra) {
       constexpr bool kRsra = decltype(with_rsra)::value;
       for (uint32_t b0 = threadIdx.x - lane; b0 < nvec; b0 += blockDim.x * UNROLL) {
@@ -109,7 +110,7 @@ __global__ void __launch_bounds__(kTiledThreads, 1)
         uint4 buf[UNROLL];
         if (b0 + (UNROLL - 1) * blockDim.x + 31 < nvec) {  // every load of the warp in range
 #pragma unroll
-          for (int u = 0; u < UNROLL; ++u) buf[u] = vec[i0 + u * blockDim.x];
+          for (int u = 0; u < UNROLL; ++u) buf[u] = load_stream(vec + i0 + u * blockDim.x, policy);
 #pragma unroll
           for (int u = 0; u < UNROLL; ++u) {
             touch(buf[u].x, buf[u].y);
@@ -127,7 +128,7 @@ __global__ void __launch_bounds__(kTiledThreads, 1)
 #pragma unroll
         for (int u = 0; u < UNROLL; ++u) {
           const uint32_t i = i0 + u * blockDim.x;
-          buf[u] = i < nvec ? vec[i] : make_uint4(0, 0, 0, 0);
+          buf[u] = i < nvec ? load_stream(vec + i, policy) : make_uint4(0, 0, 0, 0);
         }
 #pragma unroll
         for (int u = 0; u < UNROLL; ++u) {

@@ -20,71 +20,76 @@ __device__ __forceinline__ void build_active_lut(uint8_t* act, uint32_t cs, uint
   for (uint32_t s = threadIdx.x; s < 256; s += blockDim.x) act[s] = stamp_age(s, cs) < k ? 1 : 0;
 }
 
-// mode bit 0: write back expired cells; bit 1: write the hot bitmap. Blocks
-// [0, sre_blocks) cover RSRA, the rest cover SLEA.
+// mode bit 0: write back expired cells; bit 1: write the hot bitmap. do_sre != 0: the
+// RSRA is processed as well as the SLEA. Grid-stride over both arrays (any grid size); the
+// active-stamp table is built once per block.
 __global__ void __launch_bounds__(kCloseThreads) k_close(const __grid_constant__ KParams p,
                                                           uint8_t* __restrict__ sre, uint8_t* __restrict__ sle,
                                                           uint32_t* __restrict__ hot_bits,
                                                           uint32_t* __restrict__ active2, uint32_t cs_value,
-                                                          const uint32_t* __restrict__ clock, uint32_t sre_blocks,
+                                                          const uint32_t* __restrict__ clock, uint32_t do_sre,
                                                           uint32_t mode) {
   const uint32_t cs = clock ? *clock : cs_value;
   __shared__ uint8_t act[256];
-  __shared__ uint32_t warp_sum[kCloseThreads / 32];
+  __shared__ uint32_t row_sum[kMaxRows];
   build_active_lut(act, cs, p.k);
+  if (threadIdx.x < kMaxRows) row_sum[threadIdx.x] = 0;
   __syncthreads();
   const bool expire = (mode & 1u) != 0;
-  if (blockIdx.x < sre_blocks) {
-    // RSRA: SRE index g (row-major over [r][2^q]); r * 2^q is a multiple of 32.
+  const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const uint64_t nthreads = (uint64_t)gridDim.x * blockDim.x;  // a multiple of 32
+  if (do_sre) {
+    // RSRA: SRE index g (row-major over [r][2^q]); r * 2^q is a multiple of 32, so every
+    // iteration covers whole warps.
     const uint64_t n_sre = (uint64_t)p.r << p.q;
-    const uint64_t g = (uint64_t)blockIdx.x * kCloseThreads + threadIdx.x;
-    if (g >= n_sre) return;  // whole warps only
-    uint2* cell = reinterpret_cast<uint2*>(sre) + g;
-    const uint2 v = *cell;
-    uint32_t weight = 0, keep_lo = 0, keep_hi = 0;
+    for (uint64_t g = tid; g < n_sre; g += nthreads) {
+      uint2* cell = reinterpret_cast<uint2*>(sre) + g;
+      const uint2 v = *cell;
+      uint32_t weight = 0, keep_lo = 0, keep_hi = 0;
 #pragma unroll
-    for (int b = 0; b < 4; ++b) {
-      const uint32_t s0 = (v.x >> (8 * b)) & 0xFFu, s1 = (v.y >> (8 * b)) & 0xFFu;
-      const uint32_t a0 = act[s0], a1 = act[s1];
-      weight += a0 + a1;
-      keep_lo |= (a0 ? 0xFFu : 0u) << (8 * b);
-      keep_hi |= (a1 ? 0xFFu : 0u) << (8 * b);
-    }
-    const unsigned ballot = __ballot_sync(0xFFFFFFFFu, weight >= p.hot_min);
-    if ((mode & 2u) && (threadIdx.x & 31) == 0) hot_bits[g >> 5] = ballot;
-    if (expire && ((v.x & ~keep_lo) | (v.y & ~keep_hi)) != 0) *cell = make_uint2(v.x & keep_lo, v.y & keep_hi);
-    return;
-  }
-  // SLEA: block b covers bytes [b*4096, b*4096 + 4096) of one row.
-  const uint64_t b = blockIdx.x - sre_blocks;
-  const uint64_t blocks_per_row = p.row_pitch2 / kSleBytesPerBlock;
-  const uint32_t row = (uint32_t)(b / blocks_per_row);
-  uint4* cell = reinterpret_cast<uint4*>(sle + b * kSleBytesPerBlock) + threadIdx.x;
-  const uint4 v = *cell;
-  const uint32_t w[4] = {v.x, v.y, v.z, v.w};
-  uint32_t keep[4];
-  uint32_t count = 0;
-#pragma unroll
-  for (int x = 0; x < 4; ++x) {
-    keep[x] = 0;
-#pragma unroll
-    for (int y = 0; y < 4; ++y) {
-      const uint32_t a = act[(w[x] >> (8 * y)) & 0xFFu];
-      count += a;
-      keep[x] |= (a ? 0xFFu : 0u) << (8 * y);
+      for (int b = 0; b < 4; ++b) {
+        const uint32_t s0 = (v.x >> (8 * b)) & 0xFFu, s1 = (v.y >> (8 * b)) & 0xFFu;
+        const uint32_t a0 = act[s0], a1 = act[s1];
+        weight += a0 + a1;
+        keep_lo |= (a0 ? 0xFFu : 0u) << (8 * b);
+        keep_hi |= (a1 ? 0xFFu : 0u) << (8 * b);
+      }
+      const unsigned ballot = __ballot_sync(0xFFFFFFFFu, weight >= p.hot_min);
+      if ((mode & 2u) && (threadIdx.x & 31) == 0) hot_bits[g >> 5] = ballot;
+      if (expire && ((v.x & ~keep_lo) | (v.y & ~keep_hi)) != 0) *cell = make_uint2(v.x & keep_lo, v.y & keep_hi);
     }
   }
-  if (expire && ((w[0] & ~keep[0]) | (w[1] & ~keep[1]) | (w[2] & ~keep[2]) | (w[3] & ~keep[3])) != 0)
-    *cell = make_uint4(w[0] & keep[0], w[1] & keep[1], w[2] & keep[2], w[3] & keep[3]);
+  // SLEA: 16 cells per thread; rows are multiples of 4096 bytes, so a warp's 512 bytes lie
+  // in one row
+  const uint64_t n_vec = (uint64_t)p.r2 * p.row_pitch2 / 16;
+  const uint64_t vec_per_row = p.row_pitch2 / 16;
+  for (uint64_t x0 = tid - (threadIdx.x & 31); x0 < n_vec; x0 += nthreads) {
+    const uint64_t x = x0 + (threadIdx.x & 31);
+    uint32_t count = 0;
+    if (x < n_vec) {
+      uint4* cell = reinterpret_cast<uint4*>(sle) + x;
+      const uint4 v = *cell;
+      const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+      uint32_t keep[4];
 #pragma unroll
-  for (int off = 16; off > 0; off >>= 1) count += __shfl_xor_sync(0xFFFFFFFFu, count, off);
-  if ((threadIdx.x & 31) == 0) warp_sum[threadIdx.x >> 5] = count;
+      for (int i = 0; i < 4; ++i) {
+        keep[i] = 0;
+#pragma unroll
+        for (int y = 0; y < 4; ++y) {
+          const uint32_t a = act[(w[i] >> (8 * y)) & 0xFFu];
+          count += a;
+          keep[i] |= (a ? 0xFFu : 0u) << (8 * y);
+        }
+      }
+      if (expire && ((w[0] & ~keep[0]) | (w[1] & ~keep[1]) | (w[2] & ~keep[2]) | (w[3] & ~keep[3])) != 0)
+        *cell = make_uint4(w[0] & keep[0], w[1] & keep[1], w[2] & keep[2], w[3] & keep[3]);
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) count += __shfl_xor_sync(0xFFFFFFFFu, count, off);
+    if ((threadIdx.x & 31) == 0 && count) atomicAdd(&row_sum[(uint32_t)(x0 / vec_per_row)], count);
+  }
   __syncthreads();
-  if (threadIdx.x == 0) {
-    uint32_t total = 0;
-    for (int x = 0; x < kCloseThreads / 32; ++x) total += warp_sum[x];
-    if (total) atomicAdd(&active2[row], total);
-  }
+  if (threadIdx.x < p.r2 && row_sum[threadIdx.x]) atomicAdd(&active2[threadIdx.x], row_sum[threadIdx.x]);
 }
 
 // Hot lists HSE(0) and HSE(1) (column indices, any order) and |HSE(i)| for every row.

@@ -264,14 +264,19 @@ __global__ void __launch_bounds__(256) k_report(const CloseScratch* __restrict__
 // and probes it against a chunk of HSE(0) staged in shared memory. With
 // g_1 = (he_1 >> delta) mod 2^(q-delta) and K(he_0) = (he_0 XOR (he_0 >> delta)) mod 2^(q-delta),
 // the low bits c of every admissible B(2) XOR he_0 are K(he_0) XOR g_1 (Eq. 7 and the overlap
-// of B(1) and B(2)), so a probe is one XOR and one lookup of the regrouped row-2 table. A
-// thread first collects, for 32 he_0 at a time, which probes found a hot row-2 group, then
-// expands only those (batched, so a warp's lanes diverge once per 32 probes, not per probe).
+// of B(1) and B(2)), so a probe is one XOR and one lookup of the regrouped row-2 table.
+// Probes run 16 he_0 at a time; the (lane, he_0) pairs that found a hot row-2 group are
+// compacted into a per-warp list (warp prefix sum) and expanded by all 32 lanes together.
 // Chains that pass row 3's "any hot" test are queued in shared memory and grown by the whole
 // block at the end of the work unit; a full queue makes the thread grow the chain itself.
 constexpr int kJoinTiledThreads = 1024;
 constexpr uint32_t kJoinQueueCap = 2048;   // chains per block queue
 constexpr uint32_t kJoinChunkMax = 1024;   // he_0 per work unit
+constexpr uint32_t kJoinProbeBlock = 16;   // he_0 probed before a compaction
+constexpr uint32_t kJoinListWords = 32 * kJoinProbeBlock / 2;  // per warp: 16-bit entries
+// dynamic shared memory after the optional tables: queue, he_0 chunk, K chunk, he_1, lists
+constexpr size_t kJoinTiledFixedBytes =
+    (3 * (size_t)kJoinQueueCap + 2 * kJoinChunkMax + kJoinTiledThreads + (kJoinTiledThreads / 32) * kJoinListWords) * 4;
 
 __global__ void __launch_bounds__(kJoinTiledThreads) k_join_tiled(
     const __grid_constant__ KParams p, const uint32_t* __restrict__ tables, const uint32_t* __restrict__ any3,
@@ -288,7 +293,8 @@ __global__ void __launch_bounds__(kJoinTiledThreads) k_join_tiled(
   const uint32_t span_mask = delta == 5 ? 0xFFFFFFFFu : (1u << (1u << delta)) - 1u;
   const bool row2_fits_all = 2 * delta + q <= 32;
   const uint32_t nwords = (1u << q) >> 5;
-  // shared memory: [row-2 table] [any3] [queue: he0 | b1 | b2] [he_0 chunk]
+  const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+  // shared memory: [row-2 table] [any3] [queue: he0 | b1 | b2] [he_0 chunk] [K chunk] [he_1] [lists]
   const uint32_t* t2 = tables;
   uint32_t* next = sm;
   if (smem_t2) {
@@ -307,13 +313,17 @@ __global__ void __launch_bounds__(kJoinTiledThreads) k_join_tiled(
   uint32_t* qb1 = qh + kJoinQueueCap;
   uint32_t* qb2 = qb1 + kJoinQueueCap;
   uint32_t* s_he0 = qb2 + kJoinQueueCap;
+  uint32_t* s_k = s_he0 + kJoinChunkMax;
+  uint32_t* s_he1 = s_k + kJoinChunkMax;
+  uint16_t* my_list = reinterpret_cast<uint16_t*>(s_he1 + kJoinTiledThreads) + warp * (2 * kJoinListWords);
   if (threadIdx.x == 0) s_qn = 0;
 
+  // Work rows (tile of HSE(1), he_0), tile-major, split evenly over the blocks; a block's
+  // range is cut into units of at most kJoinChunkMax he_0 of one tile.
   const uint32_t tiles1 = (n1 + blockDim.x - 1) / blockDim.x;
   const uint32_t width1 = (n1 + tiles1 - 1) / tiles1;
-  uint32_t chunk = (uint32_t)(((uint64_t)n0 * tiles1 + gridDim.x - 1) / gridDim.x);
-  chunk = max(1u, min(chunk, kJoinChunkMax));
-  const uint32_t chunks0 = (n0 + chunk - 1) / chunk;
+  const uint64_t rows = (uint64_t)tiles1 * n0;
+  const uint64_t r_begin = rows * blockIdx.x / gridDim.x, r_end = rows * (blockIdx.x + 1) / gridDim.x;
 
   auto lookup = [&](uint32_t c) -> uint32_t {  // hot flags of row 2's group c
     const uint32_t first = c << delta;
@@ -330,47 +340,67 @@ __global__ void __launch_bounds__(kJoinTiledThreads) k_join_tiled(
     }
   };
 
-  for (uint32_t u = blockIdx.x; u < tiles1 * chunks0; u += gridDim.x) {
-    const uint32_t tile = u % tiles1, c0 = (u / tiles1) * chunk;
-    const uint32_t m0 = min(chunk, n0 - c0);
+  for (uint64_t r0 = r_begin; r0 < r_end;) {
+    const uint32_t tile = (uint32_t)(r0 / n0), c0 = (uint32_t)(r0 % n0);
+    uint64_t mm = n0 - c0;  // he_0 left in this tile
+    if (mm > kJoinChunkMax) mm = kJoinChunkMax;
+    if (mm > r_end - r0) mm = r_end - r0;
+    const uint32_t m0 = (uint32_t)mm;
+    r0 += m0;
     __syncthreads();  // previous unit's chunk and queue are done with
-    for (uint32_t j = threadIdx.x; j < m0; j += blockDim.x) s_he0[j] = list0[c0 + j];
-    __syncthreads();
+    for (uint32_t j = threadIdx.x; j < m0; j += blockDim.x) {
+      const uint32_t he0 = list0[c0 + j];
+      s_he0[j] = he0;
+      s_k[j] = (he0 ^ (he0 >> delta)) & cmask;
+    }
     const uint32_t b = tile * width1 + threadIdx.x;
     const bool valid = threadIdx.x < width1 && b < n1;
     const uint32_t he1 = valid ? list1[b] : 0u;
     const uint32_t g1 = (he1 >> delta) & cmask;
-    if (valid) {
-      for (uint32_t j0 = 0; j0 < m0; j0 += 32) {
-        const uint32_t jn = min(32u, m0 - j0);
-        uint32_t hits = 0;
-        for (uint32_t j = 0; j < jn; ++j) {
-          const uint32_t he0 = s_he0[j0 + j];
-          const uint32_t c = ((he0 ^ (he0 >> delta)) & cmask) ^ g1;
-          hits |= (lookup(c) != 0 ? 1u : 0u) << j;
-        }
-        while (hits) {
-          const uint32_t j = __ffs(hits) - 1;
-          hits &= hits - 1;
-          const uint32_t he0 = s_he0[j0 + j];
-          const uint32_t b1 = he0 ^ he1;
-          if (!fits32(1, delta, q, b1)) continue;
-          const uint32_t low2 = b1 >> delta;
-          const uint32_t hi0 = he0 >> shift_hi;
-          uint32_t m = lookup((he0 ^ low2) & cmask);
-          while (m) {
-            const uint32_t tp = __ffs(m) - 1;  // top bits of he_2
-            m &= m - 1;
-            const uint32_t b2 = low2 | ((tp ^ hi0) << shift_hi);
-            if (!row2_fits_all && !fits32(2, delta, q, b2)) continue;
-            if (a3) {
-              const uint32_t c3 = (he0 ^ (b2 >> delta)) & cmask;
-              if (!((a3[c3 >> 5] >> (c3 & 31)) & 1u)) continue;
-            }
-            emit(he0, b1, b2);
+    s_he1[threadIdx.x] = he1;
+    __syncthreads();
+    for (uint32_t j0 = 0; j0 < m0; j0 += kJoinProbeBlock) {  // uniform over the block
+      const uint32_t jn = min(kJoinProbeBlock, m0 - j0);
+      uint32_t hits = 0;
+      if (valid)
+        for (uint32_t j = 0; j < jn; ++j) hits |= (lookup(s_k[j0 + j] ^ g1) != 0 ? 1u : 0u) << j;
+      // compact this warp's hits: exclusive prefix sum of the per-lane counts
+      const uint32_t cnt = __popc(hits);
+      uint32_t incl = cnt;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t v = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+        if (lane >= (uint32_t)o) incl += v;
+      }
+      const uint32_t total = __shfl_sync(0xFFFFFFFFu, incl, 31);
+      uint32_t at = incl - cnt;
+      while (hits) {
+        const uint32_t j = __ffs(hits) - 1;
+        hits &= hits - 1;
+        my_list[at++] = (uint16_t)((lane << 4) | j);
+      }
+      __syncwarp();
+      for (uint32_t i = lane; i < total; i += 32) {
+        const uint32_t e = my_list[i];
+        const uint32_t he0 = s_he0[j0 + (e & 15u)];
+        const uint32_t b1 = he0 ^ s_he1[warp * 32 + (e >> 4)];
+        if (!fits32(1, delta, q, b1)) continue;
+        const uint32_t low2 = b1 >> delta;
+        const uint32_t hi0 = he0 >> shift_hi;
+        uint32_t m = lookup((he0 ^ low2) & cmask);
+        while (m) {
+          const uint32_t tp = __ffs(m) - 1;  // top bits of he_2
+          m &= m - 1;
+          const uint32_t b2 = low2 | ((tp ^ hi0) << shift_hi);
+          if (!row2_fits_all && !fits32(2, delta, q, b2)) continue;
+          if (a3) {
+            const uint32_t c3 = (he0 ^ (b2 >> delta)) & cmask;
+            if (!((a3[c3 >> 5] >> (c3 & 31)) & 1u)) continue;
           }
+          emit(he0, b1, b2);
         }
       }
+      __syncwarp();  // the list is rewritten by the next probe block
     }
     __syncthreads();  // the queue is complete
     const uint32_t qn = min(s_qn, kJoinQueueCap);

@@ -11,17 +11,21 @@
 
 namespace sse {
 
-// Streaming 128-bit load of packet data: read once, so keep it out of L1 and mark it
+// Streaming 128-bit load of packet data: read once per SM, so keep it out of L1 and mark it
 // first to be evicted from L2, where the estimator should stay resident.
-__device__ __forceinline__ uint4 load_stream(const uint4* ptr) {
-  uint4 v;
+__device__ __forceinline__ uint64_t stream_policy() {
   uint64_t policy;
-  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(policy));
+  asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(policy));
+  return policy;
+}
+__device__ __forceinline__ uint4 load_stream(const uint4* ptr, uint64_t policy) {
+  uint4 v;
   asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.v4.u32 {%0,%1,%2,%3}, [%4], %5;"
                : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
                : "l"(ptr), "l"(policy));
   return v;
 }
+__device__ __forceinline__ uint4 load_stream(const uint4* ptr) { return load_stream(ptr, stream_policy()); }
 
 // Algorithm 6 for one pair: in every row i of SLEA, cell H3(bip) of SLE LH_i(aip).
 template <int R2>

@@ -103,6 +103,7 @@ __global__ void __launch_bounds__(kTiledThreads, 1) k_update_tiled(const __grid_
   const uint4* vec = reinterpret_cast<const uint4*>(pairs + j0);
   const uint32_t nvec = (uint32_t)((end - j0) >> 1);
   const uint32_t stride = blockDim.x;
+  const uint64_t policy = stream_policy();
   // Block iteration k covers vectors [k*stride*UNROLL, (k+1)*stride*UNROLL); its RSRA work
   // belongs to tile k mod tiles. The test is uniform across the block and taken once per
   // 2*UNROLL pairs, so the RSRA code is a real branch, skipped by the other tiles (per-pair
@@ -113,7 +114,7 @@ __global__ void __launch_bounds__(kTiledThreads, 1) k_update_tiled(const __grid_
     const uint32_t base = k * stride * UNROLL + threadIdx.x;
     uint4 buf[UNROLL];
 #pragma unroll
-    for (int u = 0; u < UNROLL; ++u) buf[u] = vec[base + u * stride];
+    for (int u = 0; u < UNROLL; ++u) buf[u] = load_stream(vec + base + u * stride, policy);
 #pragma unroll
     for (int u = 0; u < UNROLL; ++u) {
       touch(buf[u].x, buf[u].y);
@@ -132,7 +133,7 @@ __global__ void __launch_bounds__(kTiledThreads, 1) k_update_tiled(const __grid_
   for (uint32_t u = 0; u < UNROLL; ++u) {
     const uint32_t i = full * stride * UNROLL + u * stride + threadIdx.x;
     const bool ok = i < nvec;
-    const uint4 v = ok ? vec[i] : make_uint4(0, 0, 0, 0);
+    const uint4 v = ok ? load_stream(vec + i, policy) : make_uint4(0, 0, 0, 0);
     if (ok) {
       touch(v.x, v.y);
       touch(v.z, v.w);

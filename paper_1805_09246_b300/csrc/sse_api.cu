@@ -130,6 +130,9 @@ struct sse_handle {
   uint32_t report_stage_n = 0;       // report entries the graph writes to report_stage
   uint8_t* report_stage = nullptr;   // page-locked, mapped: CloseScratch | hosts | est | flags
   uint8_t* report_stage_dev = nullptr;  // its device address
+  cudaEvent_t close_done = nullptr;  // recorded after each graph replay
+  int close_pending = 0;             // a replay whose report has not been collected
+  uint64_t close_pending_slice = 0;
 };
 
 namespace {
@@ -282,12 +285,9 @@ int launch_update(sse_handle* h, const uint32_t* d_pairs, uint64_t n) {
 // Expire/weigh/count pass. mode: bit 0 expire, bit 1 write hot bitmap. Without either
 // bit only the SLEA counts are needed and RSRA is skipped.
 int launch_close_pass(sse_handle* h, uint32_t* active2, uint32_t mode) {
-  const uint64_t n_sre = (uint64_t)h->p.r << h->p.q;
-  const uint32_t sre_blocks = mode ? (uint32_t)((n_sre + kCloseThreads - 1) / kCloseThreads) : 0u;
-  const uint64_t sle_blocks = h->d.sle_bytes / kSleBytesPerBlock;
-  const uint64_t blocks = sre_blocks + sle_blocks;
-  k_close<<<(unsigned)blocks, kCloseThreads, 0, h->stream>>>(h->kp, h->sre, h->sle, h->hot_bits, active2,
-                                                               stamp_of(h->slice), h->clock, sre_blocks, mode);
+  k_close<<<(unsigned)(h->num_sms * 8), kCloseThreads, 0, h->stream>>>(h->kp, h->sre, h->sle, h->hot_bits, active2,
+                                                                       stamp_of(h->slice), h->clock, mode ? 1u : 0u,
+                                                                       mode);
   SSE_LAUNCHED(h);
   return SSE_OK;
 }
@@ -396,6 +396,7 @@ void sse_destroy(sse_handle* h) {
   if (h->close_g) cudaGraphDestroy(h->close_g);
   if (h->capture_stream) cudaStreamDestroy(h->capture_stream);
   if (h->report_stage) cudaFreeHost(h->report_stage);
+  if (h->close_done) cudaEventDestroy(h->close_done);
   delete h;
 }
 
@@ -477,7 +478,7 @@ int sse_init(const sse_params* p, void* cuda_stream, sse_handle** out) {
     }
     h->join_list1_cap = (uint32_t)std::min<uint64_t>(list_entries, (budget - used) / 4);
     h->join_smem = used + (size_t)h->join_list1_cap * 4;
-    h->join_tiled_smem = used + (3 * (size_t)kJoinQueueCap + kJoinChunkMax) * 4;
+    h->join_tiled_smem = used + kJoinTiledFixedBytes;
     if (d.delta <= 5 && cudaFuncSetAttribute(k_join_tiled, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)h->join_tiled_smem) != cudaSuccess) {
       cudaGetLastError();
@@ -729,7 +730,7 @@ int close_collect(sse_handle* h, const uint32_t* sorted, sse_report* out) {
 // the device clock), the copy of the counters and of the first report_stage_n report
 // entries into pinned memory, and the clock tick. One launch and one synchronisation per
 // slice; reports longer than report_stage_n are completed with direct copies.
-int close_slice_graph(sse_handle* h, sse_report* out) {
+int close_graph_launch(sse_handle* h) {
   if (!h->close_exec) {
     if (!h->capture_stream) SSE_CUDA(h, cudaStreamCreateWithFlags(&h->capture_stream, cudaStreamNonBlocking));
     if (!h->report_stage) {
@@ -768,15 +769,26 @@ int close_slice_graph(sse_handle* h, sse_report* out) {
     if (rc) return rc;
     SSE_CUDA(h, e);
   }
+  if (!h->close_done) SSE_CUDA(h, cudaEventCreateWithFlags(&h->close_done, cudaEventDisableTiming));
   SSE_CUDA(h, cudaGraphLaunch(h->close_exec, h->stream));
+  SSE_CUDA(h, cudaEventRecord(h->close_done, h->stream));
   h->launches += h->close_kernels;
-  SSE_CUDA(h, cudaStreamSynchronize(h->stream));
+  h->close_pending = 1;
+  h->close_pending_slice = h->slice;
+  h->slice += 1;  // the replay ends with the clock tick
+  return SSE_OK;
+}
+
+// Waits for the pending replay and fills `out` from the page-locked stage.
+int close_graph_collect(sse_handle* h, sse_report* out) {
+  h->close_pending = 0;
+  SSE_CUDA(h, cudaEventSynchronize(h->close_done));
   CloseScratch hs;
   memcpy(&hs, h->report_stage, sizeof(hs));  // written by k_report before the synchronisation
   const uint32_t n_found = hs.n_cand;
   const uint32_t n_kept = std::min(n_found, h->cand_cap);
   int status = n_found > h->cand_cap ? SSE_ERR_CAPACITY : SSE_OK;
-  h->stats.slice = h->slice;
+  h->stats.slice = h->close_pending_slice;
   for (int i = 0; i < kMaxRows; ++i) {
     h->stats.hot[i] = i < (int)h->p.r ? hs.hot[i] : 0;
     h->stats.active2[i] = i < (int)h->p.r2 ? hs.active2[i] : 0;
@@ -785,7 +797,7 @@ int close_slice_graph(sse_handle* h, sse_report* out) {
   h->stats.n_candidates = n_found;
   h->stats.n_super = hs.n_super;
   if (out) {
-    out->slice = h->slice;
+    out->slice = h->close_pending_slice;
     out->n_candidates = n_found;
     out->n_super = hs.n_super;
     const uint32_t n_copy = std::min(n_kept, out->cap);
@@ -810,8 +822,12 @@ int close_slice_graph(sse_handle* h, sse_report* out) {
       SSE_CUDA(h, cudaStreamSynchronize(h->stream));
     }
   }
-  h->slice += 1;
   return status;
+}
+
+int close_slice_graph(sse_handle* h, sse_report* out) {
+  const int rc = close_graph_launch(h);
+  return rc ? rc : close_graph_collect(h, out);
 }
 
 }  // namespace
@@ -821,6 +837,7 @@ extern "C" {
 int sse_close_slice(sse_handle* h, sse_report* out) {
   if (!h) return SSE_ERR_INVALID_PARAM;
   if (h->sticky) return h->sticky;
+  if (h->close_pending) return SSE_ERR_STATE;
   if (h->close_graph) return close_slice_graph(h, out);
   uint32_t* sorted = nullptr;
   int rc = close_enqueue(h, &sorted);
@@ -832,9 +849,23 @@ int sse_close_slice(sse_handle* h, sse_report* out) {
 }
 
 int sse_close_use_graph(sse_handle* h, int enable) {
-  if (!h) return SSE_ERR_INVALID_PARAM;
+  if (!h || h->close_pending) return SSE_ERR_INVALID_PARAM;
   h->close_graph = enable ? 1 : 0;
   return SSE_OK;
+}
+
+int sse_close_slice_async(sse_handle* h) {
+  if (!h) return SSE_ERR_INVALID_PARAM;
+  if (h->sticky) return h->sticky;
+  if (!h->close_graph || h->close_pending) return SSE_ERR_STATE;
+  return close_graph_launch(h);
+}
+
+int sse_close_slice_wait(sse_handle* h, sse_report* out) {
+  if (!h) return SSE_ERR_INVALID_PARAM;
+  if (h->sticky) return h->sticky;
+  if (!h->close_pending) return SSE_ERR_STATE;
+  return close_graph_collect(h, out);
 }
 
 int sse_merge(sse_handle* dst, const sse_handle* const* srcs, int n) {
@@ -1024,9 +1055,8 @@ extern "C" int sse_query_noalloc(const sse_params* p, const uint8_t* d_sle, uint
     cudaGetLastError();
     return SSE_ERR_CUDA;
   }
-  const uint64_t sle_blocks = d.sle_bytes / kSleBytesPerBlock;
-  k_close<<<(unsigned)sle_blocks, kCloseThreads, 0, stream>>>(kp, nullptr, const_cast<uint8_t*>(d_sle), nullptr,
-                                                                counts, stamp_of(slice), nullptr, 0u, 0u);
+  k_close<<<(unsigned)(num_sms * 8), kCloseThreads, 0, stream>>>(kp, nullptr, const_cast<uint8_t*>(d_sle), nullptr,
+                                                                   counts, stamp_of(slice), nullptr, 0u, 0u);
   if (cudaGetLastError() != cudaSuccess) return SSE_ERR_CUDA;
   uint64_t grid = std::min<uint64_t>((uint64_t)n, (uint64_t)num_sms * 16);
   k_estimate<<<(unsigned)grid, kEstThreads, 0, stream>>>(kp, d_sle, d_hosts, nullptr, n, counts, d.w_theta,
@@ -1959,6 +1989,7 @@ int sse_reset(sse_handle* h) {
   SSE_CUDA(h, cudaMemcpyAsync(h->clock, &first, 4, cudaMemcpyHostToDevice, h->stream));
   SSE_CUDA(h, cudaStreamSynchronize(h->stream));
   h->slice = 0;
+  h->close_pending = 0;  // a pending report is dropped
   memset(&h->stats, 0, sizeof(h->stats));
   return SSE_OK;
 }

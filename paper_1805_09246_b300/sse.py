@@ -159,6 +159,8 @@ def lib() -> ctypes.CDLL:
             "sse_cuda_error": (ctypes.c_char_p, [vp]),
             "sse_reset": (i32, [vp]),
             "sse_close_use_graph": (i32, [vp, i32]),
+            "sse_close_slice_async": (i32, [vp]),
+            "sse_close_slice_wait": (i32, [vp, vp]),
             "sse_batch_set_mode": (i32, [vp, i32]),
             "sse_batch_reset": (i32, [vp]),
             "sse_features": (i32, [vp, vp, u32, vp]),
@@ -331,19 +333,30 @@ class Estimator:
 
     def close_slice(self, cap: int | None = None, raise_on_capacity: bool = True) -> Report:
         """Detect the sliding super points of the window ending at the current slice."""
+        return self._collect(self._lib.sse_close_slice, "sse_close_slice", cap, raise_on_capacity)
+
+    def _collect(self, fn, what: str, cap: int | None, raise_on_capacity: bool) -> Report:
         cap = self.params.max_candidates if cap is None else cap
         bufs = getattr(self, "_report_bufs", None)
         if bufs is None or len(bufs[0]) != cap:  # reused across slices (allocating them costs more than the copy)
             bufs = self._report_bufs = (np.empty(cap, np.uint32), np.empty(cap, np.float32), np.empty(cap, np.uint8))
         hosts, est, flags = bufs
         rep = _Report(0, 0, 0, cap, 0, hosts.ctypes.data, est.ctypes.data, flags.ctypes.data)
-        rc = self._lib.sse_close_slice(self._h, ctypes.byref(rep))
+        rc = fn(self._h, ctypes.byref(rep))
         if rc != SSE_OK and (rc != ERR_CAPACITY or raise_on_capacity):
-            _check(rc, "sse_close_slice", self._h)
+            _check(rc, what, self._h)
         m = min(rep.n_candidates, cap, self.params.max_candidates)
         return Report(slice=rep.slice, n_candidates=rep.n_candidates, n_super=rep.n_super,
                       truncated=bool(rep.truncated), hosts=hosts[:m].copy(), est=est[:m].copy(),
                       flags=flags[:m].copy(), status=rc)
+
+    def close_slice_async(self) -> None:
+        """Enqueue the close of the current slice (see sse_close_slice_async); the report is
+        collected by close_slice_wait()."""
+        _check(self._lib.sse_close_slice_async(self._h), "sse_close_slice_async", self._h)
+
+    def close_slice_wait(self, cap: int | None = None, raise_on_capacity: bool = True) -> Report:
+        return self._collect(self._lib.sse_close_slice_wait, "sse_close_slice_wait", cap, raise_on_capacity)
 
     def advance(self) -> None:
         _check(self._lib.sse_advance(self._h), "sse_advance")

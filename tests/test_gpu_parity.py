@@ -421,3 +421,36 @@ def test_close_graph_equals_direct_launches():
     for x, y in zip(a.read_stamps(), b.read_stamps()):
         assert np.array_equal(x, y)
     assert a.slice == b.slice == 6
+
+
+def test_async_close_pipelined_with_next_update():
+    """close_slice_async + the next slice's update + close_slice_wait gives the reports and
+    state of the synchronous close; misuse is refused with STATE."""
+    S = sse()
+    p = S.Params(seed=42)
+    tr = synth.Traffic(synth.small_trace(seed=42))
+    slices = [helpers.to_device(tr.slice(0, t)) for t in range(6)]
+    a, b = S.Estimator(p), S.Estimator(p)
+    ref = []
+    for x in slices:
+        a.update(x)
+        ref.append(a.close_slice())
+    got = []
+    b.update(slices[0])
+    for t in range(6):
+        b.close_slice_async()
+        with pytest.raises(S.SSEError):
+            b.close_slice_async()  # one close at a time
+        with pytest.raises(S.SSEError):
+            b.close_slice()
+        if t + 1 < 6:
+            b.update(slices[t + 1])  # scanned into the next slice while the report is produced
+        got.append(b.close_slice_wait())
+    with pytest.raises(S.SSEError):
+        b.close_slice_wait()  # nothing pending
+    for ra, rb in zip(ref, got):
+        assert ra.slice == rb.slice
+        assert np.array_equal(ra.hosts, rb.hosts) and np.array_equal(ra.est, rb.est)
+        assert np.array_equal(ra.flags, rb.flags)
+    for x, y in zip(a.read_stamps(), b.read_stamps()):
+        assert np.array_equal(x, y)
