@@ -42,21 +42,32 @@ __global__ void __launch_bounds__(kCloseThreads) k_close(const __grid_constant__
     // RSRA: SRE index g (row-major over [r][2^q]); r * 2^q is a multiple of 32, so every
     // iteration covers whole warps.
     const uint64_t n_sre = (uint64_t)p.r << p.q;
-    for (uint64_t g = tid; g < n_sre; g += nthreads) {
-      uint2* cell = reinterpret_cast<uint2*>(sre) + g;
-      const uint2 v = *cell;
-      uint32_t weight = 0, keep_lo = 0, keep_hi = 0;
+    constexpr int kLoads = 4;  // SREs in flight per thread
+    for (uint64_t g0 = tid; g0 < n_sre; g0 += kLoads * nthreads) {
+      uint2 v[kLoads];
 #pragma unroll
-      for (int b = 0; b < 4; ++b) {
-        const uint32_t s0 = (v.x >> (8 * b)) & 0xFFu, s1 = (v.y >> (8 * b)) & 0xFFu;
-        const uint32_t a0 = act[s0], a1 = act[s1];
-        weight += a0 + a1;
-        keep_lo |= (a0 ? 0xFFu : 0u) << (8 * b);
-        keep_hi |= (a1 ? 0xFFu : 0u) << (8 * b);
+      for (int u = 0; u < kLoads; ++u) {
+        const uint64_t g = g0 + u * nthreads;
+        v[u] = g < n_sre ? reinterpret_cast<const uint2*>(sre)[g] : make_uint2(0, 0);
       }
-      const unsigned ballot = __ballot_sync(0xFFFFFFFFu, weight >= p.hot_min);
-      if ((mode & 2u) && (threadIdx.x & 31) == 0) hot_bits[g >> 5] = ballot;
-      if (expire && ((v.x & ~keep_lo) | (v.y & ~keep_hi)) != 0) *cell = make_uint2(v.x & keep_lo, v.y & keep_hi);
+#pragma unroll
+      for (int u = 0; u < kLoads; ++u) {
+        const uint64_t g = g0 + u * nthreads;
+        if (g >= n_sre) break;  // whole warps (g0 and nthreads are multiples of 32 apart)
+        uint32_t weight = 0, keep_lo = 0, keep_hi = 0;
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+          const uint32_t s0 = (v[u].x >> (8 * b)) & 0xFFu, s1 = (v[u].y >> (8 * b)) & 0xFFu;
+          const uint32_t a0 = act[s0], a1 = act[s1];
+          weight += a0 + a1;
+          keep_lo |= (a0 ? 0xFFu : 0u) << (8 * b);
+          keep_hi |= (a1 ? 0xFFu : 0u) << (8 * b);
+        }
+        const unsigned ballot = __ballot_sync(0xFFFFFFFFu, weight >= p.hot_min);
+        if ((mode & 2u) && (threadIdx.x & 31) == 0) hot_bits[g >> 5] = ballot;
+        if (expire && ((v[u].x & ~keep_lo) | (v[u].y & ~keep_hi)) != 0)
+          reinterpret_cast<uint2*>(sre)[g] = make_uint2(v[u].x & keep_lo, v[u].y & keep_hi);
+      }
     }
   }
   // SLEA: 16 cells per thread; rows are multiples of 4096 bytes, so a warp's 512 bytes lie

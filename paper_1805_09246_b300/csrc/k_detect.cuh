@@ -412,7 +412,36 @@ __global__ void __launch_bounds__(kJoinTiledThreads) k_join_tiled(
 }
 
 // ---------------------------------------------------------------- ordering
-// Sort of each kSortChunk-element chunk in shared memory. Up to 1024 keys: rank sort (each
+// Ascending order of up to kSortChunk distinct keys (the usual report): each key is placed
+// at its rank, the number of smaller keys (ties, which a candidate set does not have, are
+// broken by index). kRankSplit neighbouring threads count one key's rank over interleaved
+// parts of the keys and add their counts with shuffles. Blocks split the keys; every block
+// reads them all into shared memory. Larger counts are left to k_sort_chunks and
+// k_merge_runs.
+constexpr int kRankThreads = 256;
+constexpr uint32_t kRankSplit = 8;
+__global__ void __launch_bounds__(kRankThreads) k_rank_sort(const uint32_t* __restrict__ keys,
+                                                            const uint32_t* __restrict__ n_ptr, uint32_t cap,
+                                                            uint32_t* __restrict__ out) {
+  __shared__ uint32_t s[kSortChunk];
+  const uint32_t n = min(*n_ptr, cap);
+  const uint32_t per_block = kRankThreads / kRankSplit;
+  if (n > kSortChunk || blockIdx.x * per_block >= n) return;
+  for (uint32_t x = threadIdx.x; x < n; x += blockDim.x) s[x] = keys[x];
+  __syncthreads();
+  const uint32_t i = blockIdx.x * per_block + threadIdx.x / kRankSplit;
+  const uint32_t part = threadIdx.x % kRankSplit;
+  const uint32_t v = i < n ? s[i] : 0u;
+  uint32_t rank = 0;
+  if (i < n)
+    for (uint32_t y = part; y < n; y += kRankSplit) rank += (s[y] < v || (s[y] == v && y < i)) ? 1u : 0u;
+#pragma unroll
+  for (uint32_t o = kRankSplit / 2; o > 0; o >>= 1) rank += __shfl_xor_sync(0xFFFFFFFFu, rank, o);
+  if (i < n && part == 0) out[rank] = v;
+}
+
+// Sort of each kSortChunk-element chunk in shared memory, when there are more than
+// kSortChunk keys (fewer are sorted by k_rank_sort). Up to 1024 keys: rank sort (each
 // key's position is the number of keys before it in sorted order; ties by index). Larger
 // chunks: bitonic sort with the tail padded with 0xFFFFFFFF (which sorts last, so the first
 // entries are the real ones).
@@ -420,6 +449,7 @@ __global__ void __launch_bounds__(1024) k_sort_chunks(uint32_t* __restrict__ key
                                                       uint32_t cap) {
   __shared__ uint32_t s[kSortChunk];
   const uint32_t n = min(*n_ptr, cap);
+  if (n <= kSortChunk) return;
   const uint32_t start = blockIdx.x * kSortChunk;
   if (start >= n) return;
   const uint32_t m = min(n - start, (uint32_t)kSortChunk);
@@ -463,6 +493,7 @@ __global__ void __launch_bounds__(256) k_merge_runs(const uint32_t* __restrict__
                                                     const uint32_t* __restrict__ n_ptr, uint32_t cap,
                                                     uint32_t width) {
   const uint32_t n = min(*n_ptr, cap);
+  if (n <= kSortChunk) return;  // k_rank_sort has sorted them
   for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n; x += (uint64_t)gridDim.x * blockDim.x) {
     const uint64_t pair_start = (x / (2ull * width)) * (2ull * width);
     const uint64_t mid = pair_start + width < n ? pair_start + width : n;

@@ -106,6 +106,7 @@ struct sse_handle {
   size_t join_tiled_smem = 0;  // k_join_tiled (delta <= 5)
   uint32_t* cand = nullptr;  // two buffers of cand_cap entries
   uint32_t* cand_alt = nullptr;
+  uint32_t* cand_out = nullptr;  // the sorted candidates
   float* est = nullptr;
   uint8_t* flags = nullptr;
   CloseScratch* scratch = nullptr;
@@ -300,10 +301,17 @@ int advance_clock(sse_handle* h) {
   return SSE_OK;
 }
 
-// Sorts the first min(n_cand, cap) candidates; returns the buffer that holds them.
+// Sorts the first min(n_cand, cap) candidates into cand_out and returns it. Up to
+// kSortChunk keys (decided on the device): k_rank_sort; more: chunk sorts in place, then
+// merge passes alternating between cand and cand_alt, the last one into cand_out.
 uint32_t* launch_sort(sse_handle* h) {
   const uint32_t cap = h->cand_cap;
   const uint32_t* n_ptr = &h->scratch->n_cand;
+  const uint32_t small = std::min<uint32_t>(cap, kSortChunk);
+  const uint32_t per_block = kRankThreads / kRankSplit;
+  k_rank_sort<<<(small + per_block - 1) / per_block, kRankThreads, 0, h->stream>>>(h->cand, n_ptr, cap, h->cand_out);
+  h->launches += 1;
+  if (h->sort_passes == 0) return h->cand_out;
   const unsigned chunks = (cap + kSortChunk - 1) / kSortChunk;
   k_sort_chunks<<<chunks, 1024, 0, h->stream>>>(h->cand, n_ptr, cap);
   h->launches += 1 + h->sort_passes;
@@ -311,12 +319,13 @@ uint32_t* launch_sort(sse_handle* h) {
   uint32_t* dst = h->cand_alt;
   uint32_t width = kSortChunk;
   for (int pass = 0; pass < h->sort_passes; ++pass) {
+    if (pass + 1 == h->sort_passes) dst = h->cand_out;
     const int grid = grid_for(h, cap, 256, 4);
     k_merge_runs<<<grid, 256, 0, h->stream>>>(src, dst, n_ptr, cap, width);
     std::swap(src, dst);
     width *= 2;
   }
-  return src;
+  return h->cand_out;
 }
 
 }  // namespace
@@ -386,6 +395,7 @@ void sse_destroy(sse_handle* h) {
   cudaFree(h->tables);
   cudaFree(h->cand);
   cudaFree(h->cand_alt);
+  cudaFree(h->cand_out);
   cudaFree(h->est);
   cudaFree(h->flags);
   cudaFree(h->scratch);
@@ -436,6 +446,7 @@ int sse_init(const sse_params* p, void* cuda_stream, sse_handle** out) {
             cudaMalloc(&h->tables, (q.r - 2) * (list_entries / 8)) == cudaSuccess &&
             cudaMalloc(&h->cand, (uint64_t)h->cand_cap * 4) == cudaSuccess &&
             cudaMalloc(&h->cand_alt, (uint64_t)h->cand_cap * 4) == cudaSuccess &&
+            cudaMalloc(&h->cand_out, (uint64_t)h->cand_cap * 4) == cudaSuccess &&
             cudaMalloc(&h->est, (uint64_t)h->cand_cap * 4) == cudaSuccess &&
             cudaMalloc(&h->flags, (uint64_t)h->cand_cap) == cudaSuccess &&
             cudaMalloc(&h->scratch, sizeof(CloseScratch)) == cudaSuccess &&
