@@ -125,95 +125,207 @@ __global__ void __launch_bounds__(128) k_mlp_forward(MlpShape s, const __nv_bflo
   }
 }
 
-// Training, per sample: forward, squared-error loss on the target t (mean over the n
-// samples) and back-propagation to the pre-activations. Stores per sample: h1 = relu(z1)
-// [H], h2 = relu(z2) [H], dz1 [H], dz2 [H], dy; loss partial sums go to loss_acc.
-__global__ void __launch_bounds__(128) k_mlp_backward(MlpShape s, const __nv_bfloat16* __restrict__ wb,
-                                                      const float* __restrict__ x, const float* __restrict__ t,
-                                                      const uint32_t* __restrict__ rows, uint32_t n,
-                                                      float* __restrict__ act, float* __restrict__ loss_acc) {
-  extern __shared__ float w[];
-  for (uint32_t i = threadIdx.x; i < s.total; i += blockDim.x) w[i] = __bfloat162float(wb[i]);
-  __syncthreads();
-  const uint32_t H = s.hidden, D = s.n_in;
+// Training step, part 1: one CTA per kTrainSamples samples of the minibatch. The BF16
+// weights (as FP32), the samples' inputs, activations and deltas live in shared memory:
+// forward (h1 = relu(W1 x + b1), h2 = relu(W2 h1 + b2), y = W3 . h2 + b3), the squared error
+// against t (mean over the n samples of the minibatch), back-propagation to the
+// pre-activations (dz2 = dy W3 relu'(z2), dz1 = (W2^T dz2) relu'(z1)), and this CTA's share
+// of every weight gradient, summed over its samples in a fixed order into partial[cta][k].
+// loss_partial[cta] = sum over its samples of (y - t)^2 / n.
+constexpr uint32_t kTrainSamples = 4;
+constexpr int kTrainThreads = 256;
+
+__host__ __device__ inline uint32_t train_smem_floats(const MlpShape& s) {
+  const uint32_t wpad = (s.total + 3) & ~3u;
+  return wpad + kTrainSamples * (s.n_in + 4 * s.hidden) + 2 * kTrainSamples;
+}
+
+// HC, DC: the hidden width and input count when known at compile time (loops unroll), else 0.
+template <int HC, int DC>
+__global__ void __launch_bounds__(kTrainThreads) k_mlp_grad_partial(MlpShape s, const __nv_bfloat16* __restrict__ wb,
+                                                                     const float* __restrict__ x,
+                                                                     const float* __restrict__ t,
+                                                                     const uint32_t* __restrict__ rows, uint32_t n,
+                                                                     float* __restrict__ partial,
+                                                                     float* __restrict__ loss_partial) {
+  extern __shared__ __align__(16) float train_sm[];
+  const uint32_t H = HC ? (uint32_t)HC : s.hidden, D = DC ? (uint32_t)DC : s.n_in;
+  constexpr uint32_t S = kTrainSamples;
+  float* w = train_sm;
+  float* xs = w + ((s.total + 3) & ~3u);  // [S][D]
+  float* h1 = xs + S * D;                  // [S][H]
+  float* h2 = h1 + S * H;
+  float* d2 = h2 + S * H;                  // dz2
+  float* d1 = d2 + S * H;                  // dz1
+  float* dy = d1 + S * H;                  // [S]
+  float* se = dy + S;                      // squared errors [S]
+  const float* W1 = w + s.off_w1;
+  const float* B1 = w + s.off_b1;
+  const float* W2 = w + s.off_w2;
+  const float* B2 = w + s.off_b2;
+  const float* W3 = w + s.off_w3;
+  const uint32_t b0 = blockIdx.x * S;
+  const uint32_t ns = min(S, n - b0);
   const float inv_n = 1.f / (float)n;
-  float local_loss = 0.f;
-  for (uint32_t b = blockIdx.x * blockDim.x + threadIdx.x; b < n; b += gridDim.x * blockDim.x) {
-    const uint32_t row = rows ? rows[b] : b;
-    const float* xb = x + (uint64_t)row * D;
-    float* a = act + (uint64_t)b * (4 * H + 1);  // h1 | h2 | dz1 | dz2 | dy
-    float xi[kMaxIn];
-    for (uint32_t i = 0; i < D; ++i) xi[i] = xb[i];
-    float h1[kMaxHidden];
-    for (uint32_t o = 0; o < H; ++o) {
-      float acc = w[s.off_b1 + o];
-      for (uint32_t i = 0; i < D; ++i) acc = fmaf(w[s.off_w1 + o * D + i], xi[i], acc);
-      h1[o] = fmaxf(acc, 0.f);
-      a[o] = h1[o];
-    }
-    float yv = w[s.off_b3];
-    for (uint32_t o = 0; o < H; ++o) {
-      float acc = w[s.off_b2 + o];
-      for (uint32_t i = 0; i < H; ++i) acc = fmaf(w[s.off_w2 + o * H + i], h1[i], acc);
-      const float h2 = fmaxf(acc, 0.f);
-      a[H + o] = h2;
-      yv = fmaf(w[s.off_w3 + o], h2, yv);
-    }
-    const float err = yv - t[row];
-    local_loss = fmaf(err, err, local_loss);
-    const float dy = 2.f * err * inv_n;  // d(mean squared error)/dy
-    a[4 * H] = dy;
-    // dz2 = dy * W3 * relu'(z2); dz1 = (W2^T dz2) * relu'(z1)
-    for (uint32_t o = 0; o < H; ++o) a[3 * H + o] = a[H + o] > 0.f ? dy * w[s.off_w3 + o] : 0.f;
-    for (uint32_t i = 0; i < H; ++i) {
-      float acc = 0.f;
-      if (h1[i] > 0.f)
-        for (uint32_t o = 0; o < H; ++o) acc = fmaf(w[s.off_w2 + o * H + i], a[3 * H + o], acc);
-      a[2 * H + i] = acc;
+  {  // weights: 8 BF16 per 16-byte load (the BF16 array is padded to a multiple of 8)
+    const uint32_t nvec = (s.total + 7) / 8;
+    const uint4* wv = reinterpret_cast<const uint4*>(wb);
+#pragma unroll 4
+    for (uint32_t c = threadIdx.x; c < nvec; c += blockDim.x) {
+      const uint4 v = __ldg(wv + c);
+      const uint32_t u[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const uint32_t idx = c * 8 + 2 * j;
+        if (idx < s.total) w[idx] = __uint_as_float(u[j] << 16);
+        if (idx + 1 < s.total) w[idx + 1] = __uint_as_float(u[j] & 0xFFFF0000u);
+      }
     }
   }
-  for (int off = 16; off > 0; off >>= 1) local_loss += __shfl_xor_sync(0xFFFFFFFFu, local_loss, off);
-  if ((threadIdx.x & 31) == 0 && local_loss != 0.f) atomicAdd(loss_acc, local_loss * inv_n);
+  for (uint32_t i = threadIdx.x; i < S * D; i += blockDim.x) {
+    const uint32_t q = i / D, d = i - q * D;
+    xs[i] = q < ns ? x[(uint64_t)(rows ? rows[b0 + q] : b0 + q) * D + d] : 0.f;
+  }
+  __syncthreads();
+  for (uint32_t i = threadIdx.x; i < S * H; i += blockDim.x) {  // layer 1
+    const uint32_t q = i / H, o = i - q * H;
+    float acc = B1[o];
+#pragma unroll
+    for (uint32_t d = 0; d < D; ++d) acc = fmaf(W1[o * D + d], xs[q * D + d], acc);
+    h1[i] = fmaxf(acc, 0.f);
+  }
+  __syncthreads();
+  for (uint32_t i = threadIdx.x; i < S * H; i += blockDim.x) {  // layer 2
+    const uint32_t q = i / H, o = i - q * H;
+    float acc = B2[o];
+#pragma unroll 16
+    for (uint32_t k = 0; k < H; ++k) acc = fmaf(W2[o * H + k], h1[q * H + k], acc);
+    h2[i] = fmaxf(acc, 0.f);
+  }
+  __syncthreads();
+  const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  for (uint32_t q = warp; q < S; q += nwarps) {  // output, error and dy: one warp per sample
+    float acc = 0.f;
+    for (uint32_t o = lane; o < H; o += 32) acc = fmaf(W3[o], h2[q * H + o], acc);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xFFFFFFFFu, acc, off);
+    if (lane == 0) {
+      const float y = acc + w[s.off_b3];
+      const float err = q < ns ? y - t[rows ? rows[b0 + q] : b0 + q] : 0.f;
+      dy[q] = 2.f * err * inv_n;
+      se[q] = err * err;
+    }
+  }
+  __syncthreads();
+  for (uint32_t i = threadIdx.x; i < S * H; i += blockDim.x) {  // dz2
+    const uint32_t q = i / H, o = i - q * H;
+    d2[i] = h2[i] > 0.f ? dy[q] * W3[o] : 0.f;
+  }
+  __syncthreads();
+  for (uint32_t i = threadIdx.x; i < S * H; i += blockDim.x) {  // dz1
+    const uint32_t q = i / H, k = i - q * H;
+    float acc = 0.f;
+    if (h1[i] > 0.f) {
+#pragma unroll 16
+      for (uint32_t o = 0; o < H; ++o) acc = fmaf(W2[o * H + k], d2[q * H + o], acc);
+    }
+    d1[i] = acc;
+  }
+  __syncthreads();
+  float* out = partial + (uint64_t)blockIdx.x * s.total;
+  // this CTA's gradient share, region by region (2-D indices without a division per entry)
+  for (uint32_t k = threadIdx.x; k < H * D; k += blockDim.x) {  // W1[o][d]: dz1[o] * x[d]
+    const uint32_t o = k / D, d = k - o * D;
+    float acc = 0.f;
+#pragma unroll
+    for (uint32_t q = 0; q < S; ++q) acc = fmaf(d1[q * H + o], xs[q * D + d], acc);
+    out[s.off_w1 + k] = acc;
+  }
+  for (uint32_t k = threadIdx.x; k < H * H; k += blockDim.x) {  // W2[o][i]: dz2[o] * h1[i]
+    const uint32_t o = k / H, i = k - o * H;
+    float acc = 0.f;
+#pragma unroll
+    for (uint32_t q = 0; q < S; ++q) acc = fmaf(d2[q * H + o], h1[q * H + i], acc);
+    out[s.off_w2 + k] = acc;
+  }
+  for (uint32_t o = threadIdx.x; o < H; o += blockDim.x) {  // b1, b2, W3
+    float a1 = 0.f, a2 = 0.f, a3 = 0.f;
+#pragma unroll
+    for (uint32_t q = 0; q < S; ++q) {
+      a1 += d1[q * H + o];
+      a2 += d2[q * H + o];
+      a3 = fmaf(dy[q], h2[q * H + o], a3);
+    }
+    out[s.off_b1 + o] = a1;
+    out[s.off_b2 + o] = a2;
+    out[s.off_w3 + o] = a3;
+  }
+  if (threadIdx.x == 0) {
+    float b3 = 0.f, l = 0.f;
+    for (uint32_t q = 0; q < S; ++q) {
+      b3 += dy[q];
+      l += se[q];
+    }
+    out[s.off_b3] = b3;
+    loss_partial[blockIdx.x] = l * inv_n;
+  }
 }
 
-// Weight gradients, one thread per parameter: sums over the batch in FP32.
-__global__ void __launch_bounds__(256) k_mlp_weight_grads(MlpShape s, const float* __restrict__ x,
-                                                          const uint32_t* __restrict__ rows, uint32_t n,
-                                                          const float* __restrict__ act, float* __restrict__ g) {
-  const uint32_t H = s.hidden, D = s.n_in, stride = 4 * H + 1;
+// Sum over the CTAs' shares of parameter k: eight running sums over c = j mod 8, added
+// pairwise at the end (a fixed order, and eight loads in flight).
+__device__ __forceinline__ float sum_parts(const float* __restrict__ partial, uint32_t n_parts, uint32_t total,
+                                           uint32_t k) {
+  float a[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  uint32_t c = 0;
+  for (; c + 8 <= n_parts; c += 8)
+#pragma unroll
+    for (int j = 0; j < 8; ++j) a[j] += partial[(uint64_t)(c + j) * total + k];
+  for (; c < n_parts; ++c) a[c & 7] += partial[(uint64_t)c * total + k];
+  return ((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7]));
+}
+
+// Training step, part 2 (gradient only): g[k] = sum_parts; *loss = sum of loss_partial
+// (thread 0 of block 0).
+__global__ void k_mlp_reduce_grads(uint32_t total, uint32_t n_parts, const float* __restrict__ partial,
+                                   const float* __restrict__ loss_partial, float* __restrict__ g,
+                                   float* __restrict__ loss) {
   const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= s.total) return;
-  float acc = 0.f;
-  if (k < s.off_b1) {  // W1[o][i]: dz1[o] * x[i]
-    const uint32_t o = k / D, i = k % D;
-    for (uint32_t b = 0; b < n; ++b)
-      acc = fmaf(act[(uint64_t)b * stride + 2 * H + o], x[(uint64_t)(rows ? rows[b] : b) * D + i], acc);
-  } else if (k < s.off_w2) {  // b1[o]
-    const uint32_t o = k - s.off_b1;
-    for (uint32_t b = 0; b < n; ++b) acc += act[(uint64_t)b * stride + 2 * H + o];
-  } else if (k < s.off_b2) {  // W2[o][i]: dz2[o] * h1[i]
-    const uint32_t o = (k - s.off_w2) / H, i = (k - s.off_w2) % H;
-    for (uint32_t b = 0; b < n; ++b)
-      acc = fmaf(act[(uint64_t)b * stride + 3 * H + o], act[(uint64_t)b * stride + i], acc);
-  } else if (k < s.off_w3) {  // b2[o]
-    const uint32_t o = k - s.off_b2;
-    for (uint32_t b = 0; b < n; ++b) acc += act[(uint64_t)b * stride + 3 * H + o];
-  } else if (k < s.off_b3) {  // W3[o]: dy * h2[o]
-    const uint32_t o = k - s.off_w3;
-    for (uint32_t b = 0; b < n; ++b) acc = fmaf(act[(uint64_t)b * stride + 4 * H], act[(uint64_t)b * stride + H + o], acc);
-  } else {  // b3
-    for (uint32_t b = 0; b < n; ++b) acc += act[(uint64_t)b * stride + 4 * H];
+  if (k < total) g[k] = sum_parts(partial, n_parts, total, k);
+  if (k == 0) {
+    float l = 0.f;
+    for (uint32_t c = 0; c < n_parts; ++c) l += loss_partial[c];
+    *loss = l;
   }
-  g[k] = acc;
 }
 
-// Adam (Kingma and Ba 2015) on the FP32 parameters; the BF16 copy is refreshed.
+// Adam (Kingma and Ba 2015) on the FP32 parameters; the BF16 copy is refreshed. The step
+// number is *step_base + step_off (the base lives on the device so that a captured epoch
+// replays correctly; k_mlp_step_add advances it), the learning rate *lr_dev when given,
+// else lr. With partial != NULL the gradient is first summed from the CTAs' shares
+// (sum_parts, as k_mlp_reduce_grads) and stored in g.
 __global__ void k_mlp_adam(uint32_t total, float* __restrict__ wf, __nv_bfloat16* __restrict__ wb,
-                           const float* __restrict__ g, float* __restrict__ m, float* __restrict__ v, float lr,
-                           float beta1, float beta2, float eps, float bc1, float bc2) {
+                           float* __restrict__ g, float* __restrict__ m, float* __restrict__ v,
+                           const float* __restrict__ lr_dev, float lr_val, const uint32_t* __restrict__ step_base,
+                           uint32_t step_off, float beta1, float beta2, float eps,
+                           const float* __restrict__ partial, uint32_t n_parts,
+                           const float* __restrict__ loss_partial, float* __restrict__ loss) {
   const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+  const float lr = lr_dev ? *lr_dev : lr_val;
+  const float step = (float)(*step_base + step_off);
+  const float bc1 = 1.f - powf(beta1, step), bc2 = 1.f - powf(beta2, step);
+  if (partial && k == 0 && loss) {
+    float l = 0.f;
+    for (uint32_t c = 0; c < n_parts; ++c) l += loss_partial[c];
+    *loss = l;
+  }
   if (k >= total) return;
-  const float gk = g[k];
+  float gk;
+  if (partial) {
+    gk = sum_parts(partial, n_parts, total, k);
+    g[k] = gk;
+  } else {
+    gk = g[k];
+  }
   const float mk = beta1 * m[k] + (1.f - beta1) * gk;
   const float vk = beta2 * v[k] + (1.f - beta2) * gk * gk;
   m[k] = mk;
@@ -222,6 +334,8 @@ __global__ void k_mlp_adam(uint32_t total, float* __restrict__ wf, __nv_bfloat16
   wf[k] = w;
   wb[k] = __float2bfloat16_rn(w);
 }
+
+__global__ void k_mlp_step_add(uint32_t* step_base, uint32_t n) { *step_base += n; }
 
 __global__ void k_mlp_to_bf16(uint32_t total, const float* __restrict__ wf, __nv_bfloat16* __restrict__ wb) {
   const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;

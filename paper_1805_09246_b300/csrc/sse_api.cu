@@ -1795,14 +1795,26 @@ struct sse_mlp {
   float* g = nullptr;            // gradients
   float* m = nullptr;            // Adam moments
   float* v = nullptr;
-  float* act = nullptr;          // per-sample activations and deltas [max_batch][4H+1]
+  float* partial = nullptr;      // per-CTA gradient shares [max_batch / kTrainSamples][total]
+  float* loss_partial = nullptr; // per-CTA loss shares
   float* loss = nullptr;         // device loss accumulator
   float* x_max = nullptr;        // per-feature upper bound of the training data
   float* scratch_x = nullptr;    // query features [max_batch][n_in]
   float* scratch_y = nullptr;    // query outputs [max_batch]
   uint32_t min_active = 0;       // gate of sse_query_learned
-  uint64_t step = 0;
+  uint32_t* d_step = nullptr;    // Adam steps taken (device)
+  float* d_lr = nullptr;         // learning rate of the captured epoch (device)
   uint64_t launches = 0;         // kernels launched by forward / gradients / Adam
+  // sse_mlp_train_epoch as one CUDA graph, for a fixed (x, t, n, batch)
+  uint32_t* perm = nullptr;      // the epoch's row order, copied from the caller
+  uint64_t perm_cap = 0;
+  cudaStream_t capture_stream = nullptr;
+  cudaGraph_t epoch_g = nullptr;
+  cudaGraphExec_t epoch_exec = nullptr;
+  const float* key_x = nullptr;
+  const float* key_t = nullptr;
+  uint32_t key_n = 0, key_batch = 0;
+  uint64_t epoch_kernels = 0;
 };
 
 extern "C" {
@@ -1815,7 +1827,14 @@ void sse_mlp_destroy(sse_mlp* m) {
   cudaFree(m->g);
   cudaFree(m->m);
   cudaFree(m->v);
-  cudaFree(m->act);
+  cudaFree(m->partial);
+  cudaFree(m->loss_partial);
+  cudaFree(m->d_step);
+  cudaFree(m->d_lr);
+  cudaFree(m->perm);
+  if (m->epoch_exec) cudaGraphExecDestroy(m->epoch_exec);
+  if (m->epoch_g) cudaGraphDestroy(m->epoch_g);
+  if (m->capture_stream) cudaStreamDestroy(m->capture_stream);
   cudaFree(m->loss);
   cudaFree(m->x_max);
   cudaFree(m->scratch_x);
@@ -1831,11 +1850,23 @@ int sse_mlp_create(uint32_t n_in, uint32_t hidden, uint32_t max_batch, uint64_t 
   if (!m) return SSE_ERR_OOM;
   m->s = mlp_shape(n_in, hidden);
   m->max_batch = max_batch;
+  if (cudaFuncSetAttribute(k_mlp_grad_partial<64, 18>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)(train_smem_floats(m->s) * 4)) != cudaSuccess ||
+      cudaFuncSetAttribute(k_mlp_grad_partial<0, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)(train_smem_floats(m->s) * 4)) != cudaSuccess) {
+    cudaGetLastError();
+    delete m;
+    return SSE_ERR_CUDA;
+  }
   const uint32_t T = m->s.total;
-  const bool ok = cudaMalloc(&m->wf, T * 4) == cudaSuccess && cudaMalloc(&m->wb, T * 2) == cudaSuccess &&
+  const bool ok = cudaMalloc(&m->wf, T * 4) == cudaSuccess && cudaMalloc(&m->wb, (T + 7) / 8 * 16) == cudaSuccess &&
                   cudaMalloc(&m->g, T * 4) == cudaSuccess && cudaMalloc(&m->m, T * 4) == cudaSuccess &&
                   cudaMalloc(&m->v, T * 4) == cudaSuccess &&
-                  cudaMalloc(&m->act, (uint64_t)max_batch * (4 * hidden + 1) * 4) == cudaSuccess &&
+                  cudaMalloc(&m->partial, (uint64_t)((max_batch + kTrainSamples - 1) / kTrainSamples) *
+                                              m->s.total * 4) == cudaSuccess &&
+                  cudaMalloc(&m->loss_partial, (uint64_t)((max_batch + kTrainSamples - 1) / kTrainSamples) * 4) ==
+                      cudaSuccess &&
+                  cudaMalloc(&m->d_step, 4) == cudaSuccess && cudaMalloc(&m->d_lr, 4) == cudaSuccess &&
                   cudaMalloc(&m->loss, 4) == cudaSuccess && cudaMalloc(&m->x_max, n_in * 4) == cudaSuccess &&
                   cudaMalloc(&m->scratch_x, (uint64_t)max_batch * n_in * 4) == cudaSuccess &&
                   cudaMalloc(&m->scratch_y, (uint64_t)max_batch * 4) == cudaSuccess;
@@ -1855,6 +1886,7 @@ int sse_mlp_create(uint32_t n_in, uint32_t hidden, uint32_t max_batch, uint64_t 
   std::vector<float> big(n_in, 3.0e38f);
   if (cudaMemcpy(m->wf, w.data(), T * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaMemset(m->m, 0, T * 4) != cudaSuccess || cudaMemset(m->v, 0, T * 4) != cudaSuccess ||
+      cudaMemset(m->d_step, 0, 4) != cudaSuccess ||
       cudaMemcpy(m->x_max, big.data(), n_in * 4, cudaMemcpyHostToDevice) != cudaSuccess) {
     cudaGetLastError();
     sse_mlp_destroy(m);
@@ -1878,8 +1910,8 @@ int sse_mlp_set_params(sse_mlp* m, const float* h_params) {
   if (!m || !h_params) return SSE_ERR_INVALID_PARAM;
   if (cudaMemcpy(m->wf, h_params, m->s.total * 4, cudaMemcpyHostToDevice) != cudaSuccess) return SSE_ERR_CUDA;
   k_mlp_to_bf16<<<(m->s.total + 255) / 256, 256>>>(m->s.total, m->wf, m->wb);
-  m->step = 0;
   if (cudaMemset(m->m, 0, m->s.total * 4) != cudaSuccess || cudaMemset(m->v, 0, m->s.total * 4) != cudaSuccess ||
+      cudaMemset(m->d_step, 0, 4) != cudaSuccess ||
       cudaDeviceSynchronize() != cudaSuccess)
     return SSE_ERR_CUDA;
   return SSE_OK;
@@ -1914,15 +1946,52 @@ int sse_mlp_forward(sse_mlp* m, const float* d_x, uint32_t n, float* d_y, void* 
   return cudaGetLastError() == cudaSuccess ? SSE_OK : SSE_ERR_CUDA;
 }
 
+}  // extern "C"
+
+namespace {
+
+// Part 1 of a training step: every CTA's gradient share for the n samples d_rows[0..n).
+int mlp_grad_partial(sse_mlp* m, const float* d_x, const float* d_t, const uint32_t* d_rows, uint32_t n,
+                     cudaStream_t st, uint32_t* parts) {
+  *parts = (n + kTrainSamples - 1) / kTrainSamples;
+  const auto fn = (m->s.hidden == 64 && m->s.n_in == 18) ? k_mlp_grad_partial<64, 18> : k_mlp_grad_partial<0, 0>;
+  fn<<<*parts, kTrainThreads, train_smem_floats(m->s) * 4, st>>>(m->s, m->wb, d_x, d_t, d_rows, n, m->partial,
+                                                                  m->loss_partial);
+  m->launches += 1;
+  return cudaGetLastError() == cudaSuccess ? SSE_OK : SSE_ERR_CUDA;
+}
+
+// Part 2: Adam step number *d_step + step_off on the summed shares (parts > 0) or on m->g
+// (parts == 0); the learning rate from *lr_dev when given, else lr.
+int mlp_adam(sse_mlp* m, const float* lr_dev, float lr, uint32_t step_off, cudaStream_t st, uint32_t parts,
+             float* d_loss) {
+  k_mlp_adam<<<(m->s.total + 255) / 256, 256, 0, st>>>(m->s.total, m->wf, m->wb, m->g, m->m, m->v, lr_dev, lr,
+                                                       m->d_step, step_off, 0.9f, 0.999f, 1e-8f,
+                                                       parts ? m->partial : nullptr, parts, m->loss_partial, d_loss);
+  m->launches += 1;
+  return cudaGetLastError() == cudaSuccess ? SSE_OK : SSE_ERR_CUDA;
+}
+
+int mlp_step_add(sse_mlp* m, uint32_t n, cudaStream_t st) {
+  k_mlp_step_add<<<1, 1, 0, st>>>(m->d_step, n);
+  m->launches += 1;
+  return cudaGetLastError() == cudaSuccess ? SSE_OK : SSE_ERR_CUDA;
+}
+
+}  // namespace
+
+extern "C" {
+
 int sse_mlp_gradients(sse_mlp* m, const float* d_x, const float* d_t, const uint32_t* d_rows, uint32_t n,
                       float* h_loss, void* stream) {
   if (!m || !d_x || !d_t || n < 1 || n > m->max_batch) return SSE_ERR_INVALID_PARAM;
   cudaStream_t st = (cudaStream_t)stream;
-  if (cudaMemsetAsync(m->loss, 0, 4, st) != cudaSuccess) return SSE_ERR_CUDA;
-  const unsigned grid = std::min<uint64_t>((n + 127) / 128, 148 * 8);
-  k_mlp_backward<<<grid, 128, m->s.total * 4, st>>>(m->s, m->wb, d_x, d_t, d_rows, n, m->act, m->loss);
-  k_mlp_weight_grads<<<(m->s.total + 255) / 256, 256, 0, st>>>(m->s, d_x, d_rows, n, m->act, m->g);
-  m->launches += 2;
+  uint32_t parts = 0;
+  int rc = mlp_grad_partial(m, d_x, d_t, d_rows, n, st, &parts);
+  if (rc) return rc;
+  k_mlp_reduce_grads<<<(m->s.total + 255) / 256, 256, 0, st>>>(m->s.total, parts, m->partial, m->loss_partial, m->g,
+                                                               m->loss);
+  m->launches += 1;
   if (cudaGetLastError() != cudaSuccess) return SSE_ERR_CUDA;
   if (h_loss) {
     if (cudaMemcpyAsync(h_loss, m->loss, 4, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
@@ -1934,30 +2003,80 @@ int sse_mlp_gradients(sse_mlp* m, const float* d_x, const float* d_t, const uint
 
 int sse_mlp_adam(sse_mlp* m, float lr, void* stream) {
   if (!m || !(lr > 0.f)) return SSE_ERR_INVALID_PARAM;
-  const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
-  m->step += 1;
-  const float bc1 = 1.f - std::pow(b1, (float)m->step), bc2 = 1.f - std::pow(b2, (float)m->step);
-  k_mlp_adam<<<(m->s.total + 255) / 256, 256, 0, (cudaStream_t)stream>>>(m->s.total, m->wf, m->wb, m->g, m->m, m->v,
-                                                                        lr, b1, b2, eps, bc1, bc2);
-  m->launches += 1;
-  return cudaGetLastError() == cudaSuccess ? SSE_OK : SSE_ERR_CUDA;
+  const int rc = mlp_adam(m, nullptr, lr, 1, (cudaStream_t)stream, 0, nullptr);
+  return rc ? rc : mlp_step_add(m, 1, (cudaStream_t)stream);
 }
 
-// One epoch over d_perm (n indices into d_x / d_t), minibatches of `batch`; returns the
-// last minibatch's loss.
+// One epoch over d_perm (n indices into d_x / d_t), minibatches of `batch`, each one
+// gradient-share kernel and one Adam kernel (which sums the shares); returns the last
+// minibatch's loss. The minibatch kernels of an epoch are captured once into a CUDA graph
+// for a given (d_x, d_t, n, batch) and replayed: the row order is first copied into the
+// MLP's own buffer and the learning rate into device memory, and the Adam steps count
+// from a device counter, so every replay is a fresh epoch.
 int sse_mlp_train_epoch(sse_mlp* m, const float* d_x, const float* d_t, const uint32_t* d_perm, uint32_t n,
                         uint32_t batch, float lr, float* h_loss, void* stream) {
-  if (!m || !d_x || !d_t || !d_perm || n < 1 || batch < 1 || batch > m->max_batch) return SSE_ERR_INVALID_PARAM;
+  if (!m || !d_x || !d_t || !d_perm || n < 1 || batch < 1 || batch > m->max_batch || !(lr > 0.f))
+    return SSE_ERR_INVALID_PARAM;
   cudaStream_t st = (cudaStream_t)stream;
-  float last = 0.f;
-  for (uint32_t b0 = 0; b0 < n; b0 += batch) {
-    const uint32_t nb = std::min(batch, n - b0);
-    int rc = sse_mlp_gradients(m, d_x, d_t, d_perm + b0, nb, (b0 + batch >= n) ? &last : nullptr, st);
-    if (rc) return rc;
-    rc = sse_mlp_adam(m, lr, st);
-    if (rc) return rc;
+  if (n > m->perm_cap) {
+    cudaFree(m->perm);
+    m->perm = nullptr;
+    m->perm_cap = 0;
+    if (cudaMalloc(&m->perm, (uint64_t)n * 4) != cudaSuccess) {
+      cudaGetLastError();
+      return SSE_ERR_OOM;
+    }
+    m->perm_cap = n;
+    if (m->epoch_exec) {  // the graph reads the old buffer
+      cudaGraphExecDestroy(m->epoch_exec);
+      cudaGraphDestroy(m->epoch_g);
+      m->epoch_exec = nullptr;
+      m->epoch_g = nullptr;
+    }
   }
-  if (h_loss) *h_loss = last;
+  if (m->epoch_exec && (m->key_x != d_x || m->key_t != d_t || m->key_n != n || m->key_batch != batch)) {
+    cudaGraphExecDestroy(m->epoch_exec);
+    cudaGraphDestroy(m->epoch_g);
+    m->epoch_exec = nullptr;
+    m->epoch_g = nullptr;
+  }
+  if (!m->epoch_exec) {
+    if (!m->capture_stream && cudaStreamCreateWithFlags(&m->capture_stream, cudaStreamNonBlocking) != cudaSuccess)
+      return SSE_ERR_CUDA;
+    const uint64_t launches0 = m->launches;
+    cudaStream_t cs = m->capture_stream;
+    if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return SSE_ERR_CUDA;
+    int rc = SSE_OK;
+    uint32_t steps = 0;
+    for (uint32_t b0 = 0; b0 < n && rc == SSE_OK; b0 += batch, ++steps) {
+      const uint32_t nb = std::min(batch, n - b0);
+      uint32_t parts = 0;
+      rc = mlp_grad_partial(m, d_x, d_t, m->perm + b0, nb, cs, &parts);
+      if (rc == SSE_OK) rc = mlp_adam(m, m->d_lr, 0.f, steps + 1, cs, parts, b0 + batch >= n ? m->loss : nullptr);
+    }
+    if (rc == SSE_OK) rc = mlp_step_add(m, steps, cs);
+    cudaGraph_t g = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(cs, &g);
+    m->epoch_kernels = m->launches - launches0;
+    m->launches = launches0;
+    if (rc != SSE_OK || e != cudaSuccess || cudaGraphInstantiate(&m->epoch_exec, g, 0) != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      m->epoch_exec = nullptr;
+      cudaGetLastError();
+      return rc ? rc : SSE_ERR_CUDA;
+    }
+    m->epoch_g = g;
+    m->key_x = d_x;
+    m->key_t = d_t;
+    m->key_n = n;
+    m->key_batch = batch;
+  }
+  if (cudaMemcpyAsync(m->perm, d_perm, (uint64_t)n * 4, cudaMemcpyDeviceToDevice, st) != cudaSuccess ||
+      cudaMemcpyAsync(m->d_lr, &lr, 4, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+      cudaGraphLaunch(m->epoch_exec, st) != cudaSuccess)
+    return SSE_ERR_CUDA;
+  m->launches += m->epoch_kernels;
+  if (h_loss && cudaMemcpyAsync(h_loss, m->loss, 4, cudaMemcpyDeviceToHost, st) != cudaSuccess) return SSE_ERR_CUDA;
   return cudaStreamSynchronize(st) == cudaSuccess ? SSE_OK : SSE_ERR_CUDA;
 }
 
