@@ -80,9 +80,12 @@ enum sse_update_mode {
  *   q2     log2 of SLEs per SLEA row (q'), 0..24
  *   delta2 offset between adjacent SLEs (delta'), 1..eta2 (Section 4, Eq. 10)
  *   eta2   cells per SLE (eta'), a power of two, 32..65536
- *   k      window length in slices, 1..254
+ *   k      window length in slices, 1..254 (8-bit stamps) or 1..65534 (16-bit stamps)
  *   theta  super point threshold (Definition 2), >= 1
- *   stamp_bits  cell width; must be 8
+ *   stamp_bits  cell width, 8 or 16: a cell holds the stamp 1 + (t mod (2^w - 1)) of the last
+ *          slice t that touched it (0: never), so the window k must be < 2^w - 1. 16-bit cells
+ *          double the state; batches, the server, sse_features and sse_query_learned take
+ *          8-bit cells only
  *   max_candidates  capacity for candidate hosts per close, 1..2^22
  *   seed   every hash key derives from it (SplitMix64)
  */
@@ -139,7 +142,9 @@ typedef struct sse_stats {
   uint32_t n_super;
 } sse_stats;
 
-/* Fills *p with the paper's experiment parameters (Section 5) and k = 8. */
+/* Fills *p with the paper's experiment parameters (Section 5: q = q' = 17, delta = 5,
+ * delta' = 16, eta' = 2^14, r = r' = 5) and its sliding-window length k = 300, which needs
+ * 16-bit stamps. */
 SSE_API void sse_params_default(sse_params* p);
 
 /* Validates *p and computes derived values (d may be NULL). SSE_ERR_INVALID_PARAM if

@@ -8,6 +8,8 @@
 // thread; active cells are summed per row (numerators of the setting factors SF(i,k)).
 #pragma once
 
+#include <type_traits>
+
 #include "sse_internal.cuh"
 
 namespace sse {
@@ -20,19 +22,51 @@ __device__ __forceinline__ void build_active_lut(uint8_t* act, uint32_t cs, uint
   for (uint32_t s = threadIdx.x; s < 256; s += blockDim.x) act[s] = stamp_age(s, cs) < k ? 1 : 0;
 }
 
+// Activity of one cell: set and younger than the window. 8-bit stamps use the 256-entry
+// table act[] built per block; 16-bit stamps compute the cyclic age (mod 65535).
+template <typename St>
+__device__ __forceinline__ uint32_t cell_active(uint32_t s, const uint8_t* act, uint32_t cs, uint32_t k) {
+  if constexpr (sizeof(St) == 1) {
+    return act[s];
+  } else {
+    const uint32_t age = cs >= s ? cs - s : cs + 65535u - s;
+    return (s != 0 && age < k) ? 1u : 0u;
+  }
+}
+
+// One 32-bit word of cells: adds its active cells to `count` and returns the mask that
+// keeps them (all ones over active cells, zero over the rest).
+template <typename St>
+__device__ __forceinline__ uint32_t word_keep(uint32_t w, const uint8_t* act, uint32_t cs, uint32_t k,
+                                              uint32_t& count) {
+  constexpr int kBits = 8 * sizeof(St);
+  constexpr uint32_t kMask = sizeof(St) == 1 ? 0xFFu : 0xFFFFu;
+  uint32_t keep = 0;
+#pragma unroll
+  for (int b = 0; b < 32 / kBits; ++b) {
+    const uint32_t a = cell_active<St>((w >> (kBits * b)) & kMask, act, cs, k);
+    count += a;
+    keep |= (a ? kMask : 0u) << (kBits * b);
+  }
+  return keep;
+}
+
 // mode bit 0: write back expired cells; bit 1: write the hot bitmap. do_sre != 0: the
-// RSRA is processed as well as the SLEA. Grid-stride over both arrays (any grid size); the
-// active-stamp table is built once per block.
+// RSRA is processed as well as the SLEA. Grid-stride over both arrays (any grid size).
+// Cells are St (8 or 16 bits); one SRE is 8 cells (a 64- or 128-bit word).
+template <typename St>
 __global__ void __launch_bounds__(kCloseThreads) k_close(const __grid_constant__ KParams p,
                                                           uint8_t* __restrict__ sre, uint8_t* __restrict__ sle,
                                                           uint32_t* __restrict__ hot_bits,
                                                           uint32_t* __restrict__ active2, uint32_t cs_value,
                                                           const uint32_t* __restrict__ clock, uint32_t do_sre,
                                                           uint32_t mode) {
+  using SreWord = typename std::conditional<sizeof(St) == 1, uint2, uint4>::type;
+  constexpr int kSreInts = sizeof(SreWord) / 4;
   const uint32_t cs = clock ? *clock : cs_value;
   __shared__ uint8_t act[256];
   __shared__ uint32_t row_sum[kMaxRows];
-  build_active_lut(act, cs, p.k);
+  if (sizeof(St) == 1) build_active_lut(act, cs, p.k);
   if (threadIdx.x < kMaxRows) row_sum[threadIdx.x] = 0;
   __syncthreads();
   const bool expire = (mode & 1u) != 0;
@@ -42,58 +76,55 @@ __global__ void __launch_bounds__(kCloseThreads) k_close(const __grid_constant__
     // RSRA: SRE index g (row-major over [r][2^q]); r * 2^q is a multiple of 32, so every
     // iteration covers whole warps.
     const uint64_t n_sre = (uint64_t)p.r << p.q;
+    SreWord* words = reinterpret_cast<SreWord*>(sre);
     constexpr int kLoads = 4;  // SREs in flight per thread
     for (uint64_t g0 = tid; g0 < n_sre; g0 += kLoads * nthreads) {
-      uint2 v[kLoads];
+      SreWord v[kLoads];
 #pragma unroll
       for (int u = 0; u < kLoads; ++u) {
         const uint64_t g = g0 + u * nthreads;
-        v[u] = g < n_sre ? reinterpret_cast<const uint2*>(sre)[g] : make_uint2(0, 0);
+        if (g < n_sre) v[u] = words[g];
       }
 #pragma unroll
       for (int u = 0; u < kLoads; ++u) {
         const uint64_t g = g0 + u * nthreads;
         if (g >= n_sre) break;  // whole warps (g0 and nthreads are multiples of 32 apart)
-        uint32_t weight = 0, keep_lo = 0, keep_hi = 0;
+        uint32_t x[kSreInts], keep[kSreInts], weight = 0, expired = 0;
+        memcpy(x, &v[u], sizeof(SreWord));
 #pragma unroll
-        for (int b = 0; b < 4; ++b) {
-          const uint32_t s0 = (v[u].x >> (8 * b)) & 0xFFu, s1 = (v[u].y >> (8 * b)) & 0xFFu;
-          const uint32_t a0 = act[s0], a1 = act[s1];
-          weight += a0 + a1;
-          keep_lo |= (a0 ? 0xFFu : 0u) << (8 * b);
-          keep_hi |= (a1 ? 0xFFu : 0u) << (8 * b);
+        for (int i = 0; i < kSreInts; ++i) {
+          keep[i] = word_keep<St>(x[i], act, cs, p.k, weight);
+          expired |= x[i] & ~keep[i];
         }
         const unsigned ballot = __ballot_sync(0xFFFFFFFFu, weight >= p.hot_min);
         if ((mode & 2u) && (threadIdx.x & 31) == 0) hot_bits[g >> 5] = ballot;
-        if (expire && ((v[u].x & ~keep_lo) | (v[u].y & ~keep_hi)) != 0)
-          reinterpret_cast<uint2*>(sre)[g] = make_uint2(v[u].x & keep_lo, v[u].y & keep_hi);
+        if (expire && expired) {
+#pragma unroll
+          for (int i = 0; i < kSreInts; ++i) x[i] &= keep[i];
+          memcpy(&v[u], x, sizeof(SreWord));
+          words[g] = v[u];
+        }
       }
     }
   }
-  // SLEA: 16 cells per thread; rows are multiples of 4096 bytes, so a warp's 512 bytes lie
-  // in one row
-  const uint64_t n_vec = (uint64_t)p.r2 * p.row_pitch2 / 16;
-  const uint64_t vec_per_row = p.row_pitch2 / 16;
+  // SLEA: 16 bytes per thread; a row pitch is a multiple of 4096 cells, so a warp's
+  // 512 bytes lie in one row
+  const uint64_t n_vec = (uint64_t)p.r2 * p.row_pitch2 * sizeof(St) / 16;
+  const uint64_t vec_per_row = p.row_pitch2 * sizeof(St) / 16;
   for (uint64_t x0 = tid - (threadIdx.x & 31); x0 < n_vec; x0 += nthreads) {
     const uint64_t x = x0 + (threadIdx.x & 31);
     uint32_t count = 0;
     if (x < n_vec) {
       uint4* cell = reinterpret_cast<uint4*>(sle) + x;
       const uint4 v = *cell;
-      const uint32_t w[4] = {v.x, v.y, v.z, v.w};
-      uint32_t keep[4];
+      uint32_t w[4] = {v.x, v.y, v.z, v.w};
+      uint32_t keep[4], expired = 0;
 #pragma unroll
       for (int i = 0; i < 4; ++i) {
-        keep[i] = 0;
-#pragma unroll
-        for (int y = 0; y < 4; ++y) {
-          const uint32_t a = act[(w[i] >> (8 * y)) & 0xFFu];
-          count += a;
-          keep[i] |= (a ? 0xFFu : 0u) << (8 * y);
-        }
+        keep[i] = word_keep<St>(w[i], act, cs, p.k, count);
+        expired |= w[i] & ~keep[i];
       }
-      if (expire && ((w[0] & ~keep[0]) | (w[1] & ~keep[1]) | (w[2] & ~keep[2]) | (w[3] & ~keep[3])) != 0)
-        *cell = make_uint4(w[0] & keep[0], w[1] & keep[1], w[2] & keep[2], w[3] & keep[3]);
+      if (expire && expired) *cell = make_uint4(w[0] & keep[0], w[1] & keep[1], w[2] & keep[2], w[3] & keep[3]);
     }
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) count += __shfl_xor_sync(0xFFFFFFFFu, count, off);

@@ -528,8 +528,26 @@ constexpr int kEstThreads = 128;
 // active cells per SLEA row. Outputs (any may be NULL except est): est, flags, w (FP64
 // corrected weight), U, hist[n][k]. vec16: every SLE starts on a 16-byte boundary
 // (delta' % 16 == 0), so cells are gathered 16 at a time.
+// Distance of a stamp from the current stamp cs, or kInactive<St> when unset or outside the
+// window (8-bit stamps: a 256-entry table with 255 for inactive, windows being at most 254
+// slices; 16-bit stamps: computed, mod 65535). The sentinel exceeds every active distance,
+// so the largest distance over a host's rows is inactive as soon as one row is.
+template <typename St>
+constexpr uint32_t kInactive = sizeof(St) == 1 ? 255u : 0xFFFFFFFFu;
+
+template <typename St>
+__device__ __forceinline__ uint32_t cell_age(uint32_t s, const uint8_t* age_lut, uint32_t cs, uint32_t k) {
+  if constexpr (sizeof(St) == 1) {
+    return age_lut[s];
+  } else {
+    const uint32_t age = cs >= s ? cs - s : cs + 65535u - s;
+    return (s != 0 && age < k) ? age : kInactive<St>;
+  }
+}
+
+template <typename St>
 __global__ void __launch_bounds__(kEstThreads) k_estimate(
-    const __grid_constant__ KParams p, const uint8_t* __restrict__ sle, const uint32_t* __restrict__ hosts,
+    const __grid_constant__ KParams p, const uint8_t* __restrict__ sle_bytes, const uint32_t* __restrict__ hosts,
     const uint32_t* __restrict__ n_ptr, uint32_t n, const uint32_t* __restrict__ active2, double w_theta,
     uint32_t cs_value, const uint32_t* __restrict__ clock, float* __restrict__ est, uint8_t* __restrict__ flags,
     double* __restrict__ w_out,
@@ -537,12 +555,14 @@ __global__ void __launch_bounds__(kEstThreads) k_estimate(
   __shared__ uint8_t age_lut[256];
   __shared__ uint32_t sh_hist[256];
   __shared__ uint32_t warp_u[kEstThreads / 32];
-  __shared__ const uint8_t* row_base[kMaxRows];
+  __shared__ const St* row_base[kMaxRows];
+  const St* sle = reinterpret_cast<const St*>(sle_bytes);
   const uint32_t cs = clock ? *clock : cs_value;
-  for (uint32_t s = threadIdx.x; s < 256; s += blockDim.x) {
-    const uint32_t a = stamp_age(s, cs);
-    age_lut[s] = a < p.k ? (uint8_t)a : 255;
-  }
+  if (sizeof(St) == 1)
+    for (uint32_t s = threadIdx.x; s < 256; s += blockDim.x) {
+      const uint32_t a = stamp_age(s, cs);
+      age_lut[s] = a < p.k ? (uint8_t)a : 255;
+    }
   const uint32_t count = n_ptr ? min(*n_ptr, n) : n;
   const bool vec16 = (p.delta2 & 15u) == 0;
   const double eta2 = (double)p.eta2;
@@ -552,35 +572,49 @@ __global__ void __launch_bounds__(kEstThreads) k_estimate(
       const uint32_t j = mas_top(p.key_a[kLH + threadIdx.x], p.key_b[kLH + threadIdx.x], aip, p.q2);
       row_base[threadIdx.x] = sle + threadIdx.x * p.row_pitch2 + (uint64_t)j * p.delta2;
     }
+    // per-distance counts: in shared memory for windows up to 256 slices, else straight
+    // into this host's output row (zeroed first)
+    const bool hist_smem = p.k <= 256;
+    uint32_t* hist_row = hist ? hist + (uint64_t)h * p.k : nullptr;
     if (hist)
-      for (uint32_t a = threadIdx.x; a < p.k; a += blockDim.x) sh_hist[a] = 0;
+      for (uint32_t a = threadIdx.x; a < p.k; a += blockDim.x) {
+        if (hist_smem)
+          sh_hist[a] = 0;
+        else
+          hist_row[a] = 0;
+      }
     __syncthreads();
     uint32_t u = 0;
+    constexpr int kVecCells = 16 / sizeof(St);  // cells per 16-byte load
+    constexpr int kIntCells = 4 / sizeof(St);
+    constexpr uint32_t kMask = sizeof(St) == 1 ? 0xFFu : 0xFFFFu;
     if (vec16) {
-      for (uint32_t z = threadIdx.x * 16; z < p.eta2; z += blockDim.x * 16) {
-        uint32_t m[16];
+      for (uint32_t z = threadIdx.x * kVecCells; z < p.eta2; z += blockDim.x * kVecCells) {
+        uint32_t m[kVecCells];
 #pragma unroll
-        for (int b = 0; b < 16; ++b) m[b] = 0;
+        for (int b = 0; b < kVecCells; ++b) m[b] = 0;
         for (uint32_t i = 0; i < p.r2; ++i) {
           const uint4 v = *reinterpret_cast<const uint4*>(row_base[i] + z);
           const uint32_t x[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
-          for (int b = 0; b < 16; ++b) m[b] = max(m[b], (uint32_t)age_lut[(x[b >> 2] >> (8 * (b & 3))) & 0xFFu]);
+          for (int b = 0; b < kVecCells; ++b)
+            m[b] = max(m[b], cell_age<St>((x[b / kIntCells] >> (8 * sizeof(St) * (b % kIntCells))) & kMask, age_lut,
+                                          cs, p.k));
         }
 #pragma unroll
-        for (int b = 0; b < 16; ++b)
-          if (m[b] != 255) {
+        for (int b = 0; b < kVecCells; ++b)
+          if (m[b] != kInactive<St>) {
             u += 1;
-            if (hist) atomicAdd(&sh_hist[m[b]], 1u);
+            if (hist) atomicAdd(hist_smem ? &sh_hist[m[b]] : &hist_row[m[b]], 1u);
           }
       }
     } else {
       for (uint32_t z = threadIdx.x; z < p.eta2; z += blockDim.x) {
         uint32_t m = 0;
-        for (uint32_t i = 0; i < p.r2; ++i) m = max(m, (uint32_t)age_lut[row_base[i][z]]);
-        if (m != 255) {
+        for (uint32_t i = 0; i < p.r2; ++i) m = max(m, cell_age<St>(row_base[i][z], age_lut, cs, p.k));
+        if (m != kInactive<St>) {
           u += 1;
-          if (hist) atomicAdd(&sh_hist[m], 1u);
+          if (hist) atomicAdd(hist_smem ? &sh_hist[m] : &hist_row[m], 1u);
         }
       }
     }
@@ -588,8 +622,8 @@ __global__ void __launch_bounds__(kEstThreads) k_estimate(
     for (int off = 16; off > 0; off >>= 1) u += __shfl_xor_sync(0xFFFFFFFFu, u, off);
     if ((threadIdx.x & 31) == 0) warp_u[threadIdx.x >> 5] = u;
     __syncthreads();
-    if (hist)
-      for (uint32_t a = threadIdx.x; a < p.k; a += blockDim.x) hist[(uint64_t)h * p.k + a] = sh_hist[a];
+    if (hist && hist_smem)
+      for (uint32_t a = threadIdx.x; a < p.k; a += blockDim.x) hist_row[a] = sh_hist[a];
     if (threadIdx.x == 0) {
       uint32_t U = 0;
       for (int x = 0; x < kEstThreads / 32; ++x) U += warp_u[x];

@@ -27,10 +27,12 @@ __device__ __forceinline__ uint4 load_stream(const uint4* ptr, uint64_t policy) 
 }
 __device__ __forceinline__ uint4 load_stream(const uint4* ptr) { return load_stream(ptr, stream_policy()); }
 
+// Stamps are cells of type St (uint8_t or uint16_t); kernels take byte pointers to the
+// estimator and address it in cells.
+
 // Algorithm 6 for one pair: in every row i of SLEA, cell H3(bip) of SLE LH_i(aip).
-template <int R2>
-__device__ __forceinline__ void stamp_slea(const KParams& p, uint32_t aip, uint32_t bip, uint8_t* sle,
-                                           uint8_t stamp) {
+template <typename St, int R2>
+__device__ __forceinline__ void stamp_slea(const KParams& p, uint32_t aip, uint32_t bip, St* sle, St stamp) {
   const uint32_t h3 = mas_top(p.key_a[kH3], p.key_b[kH3], bip, p.lg_eta2);
   const uint32_t rows = R2 > 0 ? (uint32_t)R2 : p.r2;
 #pragma unroll
@@ -48,8 +50,8 @@ __device__ __forceinline__ bool rsra_sampled(const KParams& p, uint32_t bip) {
 
 // Algorithm 3's writes for a sampled pair: cell H2(bip) of SRE RSRA[i, RHFG[i](aip)] in every
 // row i, with RHFG[i] from Eq. 6.
-__device__ __forceinline__ void rsra_write(const KParams& p, uint32_t aip, uint32_t bip, uint8_t* sre,
-                                           uint8_t stamp) {
+template <typename St>
+__device__ __forceinline__ void rsra_write(const KParams& p, uint32_t aip, uint32_t bip, St* sre, St stamp) {
   const uint32_t h2 = mas_top(p.key_a[kH2], p.key_b[kH2], bip, 3);
   const uint32_t r0 = mas_top(p.key_a[kR0], p.key_b[kR0], aip, p.q);
   const uint32_t qmask = (1u << p.q) - 1u;
@@ -61,8 +63,8 @@ __device__ __forceinline__ void rsra_write(const KParams& p, uint32_t aip, uint3
 }
 
 // Algorithm 3 for one pair.
-__device__ __forceinline__ void stamp_rsra(const KParams& p, uint32_t aip, uint32_t bip, uint8_t* sre,
-                                           uint8_t stamp) {
+template <typename St>
+__device__ __forceinline__ void stamp_rsra(const KParams& p, uint32_t aip, uint32_t bip, St* sre, St stamp) {
   if (p.sre_on && rsra_sampled(p, bip)) rsra_write(p, aip, bip, sre, stamp);
 }
 
@@ -78,8 +80,9 @@ struct RsraQueue {
   uint32_t n;    // entries waiting (the same in every lane)
   uint32_t lane;
 
-  __device__ __forceinline__ void push(const KParams& p, bool valid, uint32_t aip, uint32_t bip, uint8_t* sre,
-                                       uint8_t stamp) {
+  template <typename St>
+  __device__ __forceinline__ void push(const KParams& p, bool valid, uint32_t aip, uint32_t bip, St* sre,
+                                       St stamp) {
     const bool s = valid && rsra_sampled(p, bip);
     const uint32_t b = __ballot_sync(0xFFFFFFFFu, s);
     if (b == 0) return;
@@ -96,7 +99,8 @@ struct RsraQueue {
     }
   }
 
-  __device__ __forceinline__ void drain(const KParams& p, uint8_t* sre, uint8_t stamp) {
+  template <typename St>
+  __device__ __forceinline__ void drain(const KParams& p, St* sre, St stamp) {
     __syncwarp();
     if (lane < n) {
       const uint2 e = q[lane];
@@ -107,22 +111,24 @@ struct RsraQueue {
   }
 };
 
-template <int R2>
-__device__ __forceinline__ void apply_pair(const KParams& p, uint32_t aip, uint32_t bip, uint8_t* sre,
-                                           uint8_t* sle, uint8_t stamp) {
-  stamp_slea<R2>(p, aip, bip, sle, stamp);
+template <typename St, int R2>
+__device__ __forceinline__ void apply_pair(const KParams& p, uint32_t aip, uint32_t bip, St* sre, St* sle,
+                                           St stamp) {
+  stamp_slea<St, R2>(p, aip, bip, sle, stamp);
   stamp_rsra(p, aip, bip, sre, stamp);
 }
 
 // pairs: 8-byte aligned {src, dst} pairs. UNROLL 128-bit loads are in flight per thread.
 // The stamp is read from the estimator's device clock when `clock` is set, so a captured
 // CUDA graph replays correctly in later slices.
-template <int R2, int UNROLL>
+template <typename St, int R2, int UNROLL>
 __global__ void __launch_bounds__(256) k_update_direct(const __grid_constant__ KParams p,
                                                        const uint2* __restrict__ pairs, uint64_t n,
-                                                       uint8_t* __restrict__ sre, uint8_t* __restrict__ sle,
+                                                       uint8_t* __restrict__ sre_bytes, uint8_t* __restrict__ sle_bytes,
                                                        uint32_t stamp_value, const uint32_t* __restrict__ clock) {
-  const uint8_t stamp = (uint8_t)(clock ? *clock : stamp_value);
+  const St stamp = (St)(clock ? *clock : stamp_value);
+  St* sre = reinterpret_cast<St*>(sre_bytes);
+  St* sle = reinterpret_cast<St*>(sle_bytes);
   const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   const uint2* base = pairs;
@@ -130,7 +136,7 @@ __global__ void __launch_bounds__(256) k_update_direct(const __grid_constant__ K
   if ((reinterpret_cast<uintptr_t>(base) & 15u) != 0 && cnt > 0) {  // peel one pair to reach 16 B
     if (tid == 0) {
       uint2 v = base[0];
-      apply_pair<R2>(p, v.x, v.y, sre, sle, stamp);
+      apply_pair<St, R2>(p, v.x, v.y, sre, sle, stamp);
     }
     base += 1;
     cnt -= 1;
@@ -148,14 +154,14 @@ __global__ void __launch_bounds__(256) k_update_direct(const __grid_constant__ K
     for (int u = 0; u < UNROLL; ++u) {
       const uint64_t i = i0 + (uint64_t)u * stride;
       if (i < nvec) {
-        apply_pair<R2>(p, buf[u].x, buf[u].y, sre, sle, stamp);
-        apply_pair<R2>(p, buf[u].z, buf[u].w, sre, sle, stamp);
+        apply_pair<St, R2>(p, buf[u].x, buf[u].y, sre, sle, stamp);
+        apply_pair<St, R2>(p, buf[u].z, buf[u].w, sre, sle, stamp);
       }
     }
   }
   if ((cnt & 1) && tid == 0) {
     uint2 v = base[cnt - 1];
-    apply_pair<R2>(p, v.x, v.y, sre, sle, stamp);
+    apply_pair<St, R2>(p, v.x, v.y, sre, sle, stamp);
   }
 }
 

@@ -67,13 +67,14 @@ struct TileGeometry {
 // grid = groups * tiles CTAs; dynamic shared memory = piece_bytes / 8 + kRsraQueueBytes. UNROLL 128-bit loads
 // are in flight per thread; CHECK reads the bitmap word first and skips the atomic when the
 // bit is already set (repeated pairs are common in real traffic).
-template <int UNROLL, bool CHECK, bool WHOLE>
+template <typename St, int UNROLL, bool CHECK, bool WHOLE>
 __global__ void __launch_bounds__(kTiledThreads, 1) k_update_tiled(const __grid_constant__ KParams p, TileGeometry g,
                                                                    const uint2* __restrict__ pairs, uint64_t n,
-                                                                   uint8_t* __restrict__ sre,
+                                                                   uint8_t* __restrict__ sre_bytes,
                                                                    uint32_t* __restrict__ gbits, uint32_t stamp_value,
                                                                    const uint32_t* __restrict__ clock) {
-  const uint8_t stamp = (uint8_t)(clock ? *clock : stamp_value);
+  const St stamp = (St)(clock ? *clock : stamp_value);
+  St* sre = reinterpret_cast<St*>(sre_bytes);
   extern __shared__ uint32_t bm[];
   const uint32_t tile = blockIdx.x % g.tiles;
   const uint32_t group = blockIdx.x / g.tiles;
@@ -159,31 +160,38 @@ __global__ void __launch_bounds__(kTiledThreads, 1) k_update_tiled(const __grid_
 }
 
 // Stamp every SLEA cell whose bit is set and clear the bitmap. One thread per bitmap word
-// (32 cells = two 16-byte vectors of the state); each word has a single owner.
+// (32 cells: two 16-byte vectors of 8-bit stamps or four of 16-bit stamps); each word has a
+// single owner.
+template <typename St>
 __global__ void __launch_bounds__(256) k_apply_bits(uint32_t* __restrict__ gbits, uint8_t* __restrict__ sle,
                                                     uint64_t n_words, uint32_t stamp_value,
                                                     const uint32_t* __restrict__ clock) {
+  constexpr int kCellsPerVec = 16 / sizeof(St);  // 16 or 8
+  constexpr int kVecs = 32 / kCellsPerVec;       // 2 or 4
+  constexpr int kCellsPerInt = 4 / sizeof(St);   // 4 or 2
+  constexpr uint32_t kCellMask = sizeof(St) == 1 ? 0xFFu : 0xFFFFu;
   const uint32_t stamp = clock ? *clock : stamp_value;
+  const uint32_t fill = sizeof(St) == 1 ? stamp * 0x01010101u : stamp * 0x00010001u;
   for (uint64_t w = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; w < n_words;
        w += (uint64_t)gridDim.x * blockDim.x) {
     const uint32_t bits = gbits[w];
     if (!bits) continue;
-    uint4* cells = reinterpret_cast<uint4*>(sle + (w << 5));
+    uint4* cells = reinterpret_cast<uint4*>(sle + (w << 5) * sizeof(St));
 #pragma unroll
-    for (int half = 0; half < 2; ++half) {
-      const uint32_t hb = (bits >> (16 * half)) & 0xFFFFu;
+    for (int h = 0; h < kVecs; ++h) {
+      const uint32_t hb = (bits >> (kCellsPerVec * h)) & ((1u << kCellsPerVec) - 1u);
       if (!hb) continue;
-      uint4 v = cells[half];
+      uint4 v = cells[h];
       uint32_t x[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
-        const uint32_t nib = (hb >> (4 * q)) & 0xFu;
-        // byte mask: 0xFF in byte b where bit b of nib is set
-        const uint32_t mask = ((nib & 1u) ? 0x000000FFu : 0u) | ((nib & 2u) ? 0x0000FF00u : 0u) |
-                              ((nib & 4u) ? 0x00FF0000u : 0u) | ((nib & 8u) ? 0xFF000000u : 0u);
-        x[q] = (x[q] & ~mask) | (stamp * 0x01010101u & mask);
+        const uint32_t nib = (hb >> (kCellsPerInt * q)) & ((1u << kCellsPerInt) - 1u);
+        uint32_t mask = 0;  // all ones in the cells whose bit is set
+#pragma unroll
+        for (int b = 0; b < kCellsPerInt; ++b) mask |= ((nib >> b) & 1u) ? kCellMask << (8 * sizeof(St) * b) : 0u;
+        x[q] = (x[q] & ~mask) | (fill & mask);
       }
-      cells[half] = make_uint4(x[0], x[1], x[2], x[3]);
+      cells[h] = make_uint4(x[0], x[1], x[2], x[3]);
     }
     gbits[w] = 0;
   }

@@ -49,9 +49,9 @@ int derive_params(const sse_params& in, sse_params& p, sse_derived& d) {
   if (p.r2 < 1 || p.r2 > (uint32_t)kMaxRows || p.q2 > 24) return SSE_ERR_INVALID_PARAM;
   if (!is_pow2(p.eta2) || p.eta2 < 32 || p.eta2 > 65536) return SSE_ERR_INVALID_PARAM;
   if (p.delta2 < 1 || p.delta2 > p.eta2) return SSE_ERR_INVALID_PARAM;
-  if (p.k < 1 || p.k > 254) return SSE_ERR_INVALID_PARAM;
+  if (p.stamp_bits != 8 && p.stamp_bits != 16) return SSE_ERR_INVALID_PARAM;
+  if (p.k < 1 || p.k > stamp_mod(p.stamp_bits) - 1) return SSE_ERR_INVALID_PARAM;  // k <= 254 or 65534
   if (p.theta < 1) return SSE_ERR_INVALID_PARAM;
-  if (p.stamp_bits != 8) return SSE_ERR_INVALID_PARAM;
   if (p.max_candidates < 1 || p.max_candidates > (1u << 22)) return SSE_ERR_INVALID_PARAM;
   memset(&d, 0, sizeof(d));
   d.delta = p.delta;
@@ -64,8 +64,8 @@ int derive_params(const sse_params& in, sse_params& p, sse_derived& d) {
   d.row_len2 = ((uint64_t)1 << p.q2) * p.delta2 + p.eta2 - p.delta2;
   if (d.row_len2 > (1ull << 31)) return SSE_ERR_INVALID_PARAM;
   d.row_pitch2 = (d.row_len2 + kPitchAlign - 1) / kPitchAlign * kPitchAlign;
-  d.sre_bytes = (uint64_t)p.r << p.q << 3;
-  d.sle_bytes = (uint64_t)p.r2 * d.row_pitch2;
+  d.sre_bytes = ((uint64_t)p.r << p.q << 3) * (p.stamp_bits / 8);
+  d.sle_bytes = (uint64_t)p.r2 * d.row_pitch2 * (p.stamp_bits / 8);
   d.w_theta = (double)p.eta2 * (-std::expm1(-(double)p.theta / (double)p.eta2));
   return SSE_OK;
 }
@@ -82,6 +82,9 @@ struct sse_handle {
   int device = 0;
   cudaStream_t stream = nullptr;
   uint64_t slice = 0;
+  uint32_t smod = 255;    // stamp cycle: 255 (8-bit cells) or 65535 (16-bit cells)
+  bool wide = false;      // 16-bit cells
+  uint64_t sle_cells = 0; // r' * row pitch
   int sticky = SSE_OK;    // first CUDA error seen; later calls return it
   cudaError_t cuda_error = cudaSuccess;  // the CUDA error behind `sticky`
   uint64_t launches = 0;  // kernels launched by this handle
@@ -203,15 +206,14 @@ int grid_for(const sse_handle* h, uint64_t work, int block, int per_sm) {
 }
 
 int launch_update_direct(sse_handle* h, const uint32_t* d_pairs, uint64_t n) {
-  const uint8_t stamp = stamp_of(h->slice);
+  const uint32_t stamp = stamp_of(h->slice, h->smod);
   const uint64_t work = (n + 1) / 2;
   constexpr int kUnroll = 4;
   const int grid = grid_for(h, (work + kUnroll - 1) / kUnroll, 256, 8);
   const uint2* pairs = reinterpret_cast<const uint2*>(d_pairs);
-  if (h->p.r2 == 5)
-    k_update_direct<5, kUnroll><<<grid, 256, 0, h->stream>>>(h->kp, pairs, n, h->sre, h->sle, stamp, h->clock);
-  else
-    k_update_direct<0, kUnroll><<<grid, 256, 0, h->stream>>>(h->kp, pairs, n, h->sre, h->sle, stamp, h->clock);
+  const auto fn = h->wide ? (h->p.r2 == 5 ? k_update_direct<uint16_t, 5, kUnroll> : k_update_direct<uint16_t, 0, kUnroll>)
+                          : (h->p.r2 == 5 ? k_update_direct<uint8_t, 5, kUnroll> : k_update_direct<uint8_t, 0, kUnroll>);
+  fn<<<grid, 256, 0, h->stream>>>(h->kp, pairs, n, h->sre, h->sle, stamp, h->clock);
   SSE_LAUNCHED(h);
   return SSE_OK;
 }
@@ -233,12 +235,14 @@ TileGeometry make_tiles(const sse_params& p, const sse_derived& d, int num_sms) 
 using TiledKernel = void (*)(KParams, TileGeometry, const uint2*, uint64_t, uint8_t*, uint32_t*, uint32_t,
                             const uint32_t*);
 struct TiledVariant {
-  TiledKernel fn;        // tiles smaller than a row
-  TiledKernel fn_whole;  // one tile per row (no range test)
+  TiledKernel fn[2][2];  // [16-bit cells][one tile per row (no range test)]
   int unroll;
   bool check;
 };
-#define SSE_TILED(U, C) {k_update_tiled<U, C, false>, k_update_tiled<U, C, true>, U, C}
+#define SSE_TILED(U, C)                                                           \
+  {{{k_update_tiled<uint8_t, U, C, false>, k_update_tiled<uint8_t, U, C, true>},   \
+    {k_update_tiled<uint16_t, U, C, false>, k_update_tiled<uint16_t, U, C, true>}}, \
+   U, C}
 const TiledVariant kTiledVariants[] = {
     SSE_TILED(4, false), SSE_TILED(2, false), SSE_TILED(8, false),
     SSE_TILED(4, true),  SSE_TILED(2, true),  SSE_TILED(8, true),
@@ -249,10 +253,10 @@ constexpr int kNumTiledVariants = sizeof(kTiledVariants) / sizeof(kTiledVariants
 constexpr int kNumUpdateVariants = 1 + kNumTiledVariants;
 
 int launch_update_tiled(sse_handle* h, const uint32_t* d_pairs, uint64_t n, int variant) {
-  const uint8_t stamp = stamp_of(h->slice);
+  const uint32_t stamp = stamp_of(h->slice, h->smod);
   const TileGeometry& g = h->tiles;
   const size_t smem = g.piece_bytes / 8 + kRsraQueueBytes;
-  const TiledKernel fn = g.pieces == 1 ? kTiledVariants[variant].fn_whole : kTiledVariants[variant].fn;
+  const TiledKernel fn = kTiledVariants[variant].fn[h->wide][g.pieces == 1];
   constexpr uint64_t kMaxPairsPerLaunch = 1ull << 30;  // keeps per-group indices in 32 bits
   for (uint64_t done = 0; done < n; done += kMaxPairsPerLaunch) {
     const uint64_t m = std::min(kMaxPairsPerLaunch, n - done);
@@ -260,8 +264,9 @@ int launch_update_tiled(sse_handle* h, const uint32_t* d_pairs, uint64_t n, int 
         h->kp, g, reinterpret_cast<const uint2*>(d_pairs + 2 * done), m, h->sre, h->sle_bits, stamp, h->clock);
     SSE_LAUNCHED(h);
   }
-  const uint64_t words = h->d.sle_bytes / 32;
-  k_apply_bits<<<grid_for(h, words, 256, 8), 256, 0, h->stream>>>(h->sle_bits, h->sle, words, stamp, h->clock);
+  const uint64_t words = h->sle_cells / 32;
+  const auto apply = h->wide ? k_apply_bits<uint16_t> : k_apply_bits<uint8_t>;
+  apply<<<grid_for(h, words, 256, 8), 256, 0, h->stream>>>(h->sle_bits, h->sle, words, stamp, h->clock);
   SSE_LAUNCHED(h);
   return SSE_OK;
 }
@@ -286,16 +291,17 @@ int launch_update(sse_handle* h, const uint32_t* d_pairs, uint64_t n) {
 // Expire/weigh/count pass. mode: bit 0 expire, bit 1 write hot bitmap. Without either
 // bit only the SLEA counts are needed and RSRA is skipped.
 int launch_close_pass(sse_handle* h, uint32_t* active2, uint32_t mode) {
-  k_close<<<(unsigned)(h->num_sms * 8), kCloseThreads, 0, h->stream>>>(h->kp, h->sre, h->sle, h->hot_bits, active2,
-                                                                       stamp_of(h->slice), h->clock, mode ? 1u : 0u,
-                                                                       mode);
+  const auto fn = h->wide ? k_close<uint16_t> : k_close<uint8_t>;
+  fn<<<(unsigned)(h->num_sms * 8), kCloseThreads, 0, h->stream>>>(h->kp, h->sre, h->sle, h->hot_bits, active2,
+                                                                  stamp_of(h->slice, h->smod), h->clock,
+                                                                  mode ? 1u : 0u, mode);
   SSE_LAUNCHED(h);
   return SSE_OK;
 }
 
 // Moves the handle to the next slice: the device clock on the stream, the host copy now.
 int advance_clock(sse_handle* h) {
-  k_tick<<<1, 32, 0, h->stream>>>(h->clock, 1);
+  k_tick<<<1, 32, 0, h->stream>>>(h->clock, 1, h->smod);
   SSE_LAUNCHED(h);
   h->slice += 1;
   return SSE_OK;
@@ -343,9 +349,9 @@ void sse_params_default(sse_params* p) {
   p->q2 = 17;
   p->delta2 = 16;
   p->eta2 = 1u << 14;
-  p->k = 8;
+  p->k = 300;
   p->theta = 1024;
-  p->stamp_bits = 8;
+  p->stamp_bits = 16;
   p->max_candidates = 1u << 16;
   p->seed = 0;
 }
@@ -422,6 +428,9 @@ int sse_init(const sse_params* p, void* cuda_stream, sse_handle** out) {
   h->p = q;
   h->d = d;
   h->kp = make_kparams(q, d);
+  h->smod = stamp_mod(q.stamp_bits);
+  h->wide = q.stamp_bits == 16;
+  h->sle_cells = (uint64_t)q.r2 * d.row_pitch2;
   h->stream = (cudaStream_t)cuda_stream;
   memset(&h->stats, 0, sizeof(h->stats));
   if (cudaGetDevice(&h->device) != cudaSuccess ||
@@ -440,7 +449,7 @@ int sse_init(const sse_params* p, void* cuda_stream, sse_handle** out) {
   const uint64_t list_entries = 1ull << q.q;
   bool ok = cudaMalloc(&h->state, state_bytes) == cudaSuccess && cudaMalloc(&h->clock, 256) == cudaSuccess &&
             cudaMalloc(&h->hot_bits, ((uint64_t)q.r << q.q) / 8) == cudaSuccess &&
-            cudaMalloc(&h->sle_bits, d.sle_bytes / 8) == cudaSuccess &&
+            cudaMalloc(&h->sle_bits, h->sle_cells / 8) == cudaSuccess &&
             cudaMalloc(&h->list0, list_entries * 4) == cudaSuccess &&
             cudaMalloc(&h->list1, list_entries * 4) == cudaSuccess &&
             cudaMalloc(&h->tables, (q.r - 2) * (list_entries / 8)) == cudaSuccess &&
@@ -460,8 +469,8 @@ int sse_init(const sse_params* p, void* cuda_stream, sse_handle** out) {
   h->sre = h->state;
   h->sle = h->state + d.sre_bytes;
   h->tiles = make_tiles(q, d, h->num_sms);
-  for (int v = 0; v < 2 * kNumTiledVariants; ++v) {
-    const TiledKernel fn = (v & 1) ? kTiledVariants[v / 2].fn_whole : kTiledVariants[v / 2].fn;
+  for (int v = 0; v < 4 * kNumTiledVariants; ++v) {
+    const TiledKernel fn = kTiledVariants[v / 4].fn[(v >> 1) & 1][v & 1];
     if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)(h->tiles.piece_bytes / 8 + kRsraQueueBytes)) !=
         cudaSuccess) {
@@ -502,11 +511,11 @@ int sse_init(const sse_params* p, void* cuda_stream, sse_handle** out) {
       return SSE_ERR_CUDA;
     }
   }
-  const uint32_t first_stamp = stamp_of(0);
+  const uint32_t first_stamp = stamp_of(0, h->smod);
   if (cudaMemcpyAsync(h->clock, &first_stamp, sizeof(first_stamp), cudaMemcpyHostToDevice, h->stream) != cudaSuccess ||
       cudaMemsetAsync(h->state, 0, state_bytes, h->stream) != cudaSuccess ||
       cudaMemsetAsync(h->hot_bits, 0, ((uint64_t)q.r << q.q) / 8, h->stream) != cudaSuccess ||
-      cudaMemsetAsync(h->sle_bits, 0, d.sle_bytes / 8, h->stream) != cudaSuccess ||
+      cudaMemsetAsync(h->sle_bits, 0, h->sle_cells / 8, h->stream) != cudaSuccess ||
       cudaMemsetAsync(h->scratch, 0, sizeof(CloseScratch), h->stream) != cudaSuccess ||
       cudaStreamSynchronize(h->stream) != cudaSuccess) {
     cudaGetLastError();
@@ -691,8 +700,9 @@ int close_enqueue(sse_handle* h, uint32_t** sorted, bool copy_counters = true) {
   SSE_CUDA(h, cudaGetLastError());
   {
     const int grid = grid_for(h, h->cand_cap, 1, 16);
-    k_estimate<<<grid, kEstThreads, 0, h->stream>>>(h->kp, h->sle, *sorted, &sc->n_cand, h->cand_cap, sc->active2,
-                                                    h->d.w_theta, stamp_of(h->slice), h->clock, h->est, h->flags,
+    const auto est_fn = h->wide ? k_estimate<uint16_t> : k_estimate<uint8_t>;
+    est_fn<<<grid, kEstThreads, 0, h->stream>>>(h->kp, h->sle, *sorted, &sc->n_cand, h->cand_cap, sc->active2,
+                                                h->d.w_theta, stamp_of(h->slice, h->smod), h->clock, h->est, h->flags,
                                                     nullptr, nullptr, nullptr, &sc->n_super);
     SSE_LAUNCHED(h);
   }
@@ -761,7 +771,7 @@ int close_graph_launch(sse_handle* h) {
         k_report<<<8, 256, 0, h->stream>>>(h->scratch, h->close_sorted, h->est, h->flags, h->cand_cap,
                                            h->report_stage_n, h->report_stage_dev);
         SSE_LAUNCHED(h);
-        k_tick<<<1, 32, 0, h->stream>>>(h->clock, 1);
+        k_tick<<<1, 32, 0, h->stream>>>(h->clock, 1, h->smod);
         SSE_LAUNCHED(h);
       }
       cudaGraph_t g = nullptr;
@@ -893,11 +903,12 @@ int sse_merge(sse_handle* dst, const sse_handle* const* srcs, int n) {
     sre_src.ptr[j] = s->sre;
     sle_src.ptr[j] = s->sle;
   }
-  const uint32_t cs = stamp_of(dst->slice);
+  const uint32_t cs = stamp_of(dst->slice, dst->smod);
+  const auto merge_fn = dst->wide ? k_merge<uint16_t> : k_merge<uint8_t>;
   const uint64_t n16_sre = dst->d.sre_bytes / 16, n16_sle = dst->d.sle_bytes / 16;
-  k_merge<<<grid_for(dst, n16_sre, 256, 8), 256, 0, dst->stream>>>(dst->sre, sre_src, n, n16_sre, cs, dst->clock);
+  merge_fn<<<grid_for(dst, n16_sre, 256, 8), 256, 0, dst->stream>>>(dst->sre, sre_src, n, n16_sre, cs, dst->clock);
   SSE_LAUNCHED(dst);
-  k_merge<<<grid_for(dst, n16_sle, 256, 8), 256, 0, dst->stream>>>(dst->sle, sle_src, n, n16_sle, cs, dst->clock);
+  merge_fn<<<grid_for(dst, n16_sle, 256, 8), 256, 0, dst->stream>>>(dst->sle, sle_src, n, n16_sle, cs, dst->clock);
   SSE_LAUNCHED(dst);
   return SSE_OK;
 }
@@ -911,8 +922,9 @@ int sse_query(sse_handle* h, const uint32_t* d_hosts, uint32_t n, float* d_est, 
   int rc = launch_close_pass(h, h->query_active2, 0u);  // count only
   if (rc) return rc;
   const int grid = grid_for(h, n, 1, 16);
-  k_estimate<<<grid, kEstThreads, 0, h->stream>>>(h->kp, h->sle, d_hosts, nullptr, n, h->query_active2,
-                                                      h->d.w_theta, stamp_of(h->slice), h->clock, d_est, d_flags, nullptr,
+  const auto est_fn = h->wide ? k_estimate<uint16_t> : k_estimate<uint8_t>;
+  est_fn<<<grid, kEstThreads, 0, h->stream>>>(h->kp, h->sle, d_hosts, nullptr, n, h->query_active2,
+                                                      h->d.w_theta, stamp_of(h->slice, h->smod), h->clock, d_est, d_flags, nullptr,
                                                       nullptr, d_hist, nullptr);
   SSE_LAUNCHED(h);
   return SSE_OK;
@@ -985,7 +997,7 @@ int sse_import_state(sse_handle* h, const void* h_buf, size_t n) {
     return SSE_ERR_MISMATCH;
   if (n < sizeof(hd) + hd.sre_bytes + hd.sle_bytes) return SSE_ERR_INVALID_PARAM;
   const uint8_t* body = static_cast<const uint8_t*>(h_buf) + sizeof(hd);
-  const uint32_t stamp = stamp_of(hd.slice);
+  const uint32_t stamp = stamp_of(hd.slice, h->smod);
   SSE_CUDA(h, cudaMemcpyAsync(h->state, body, hd.sre_bytes + hd.sle_bytes, cudaMemcpyHostToDevice, h->stream));
   SSE_CUDA(h, cudaMemcpyAsync(h->clock, &stamp, sizeof(stamp), cudaMemcpyHostToDevice, h->stream));
   SSE_CUDA(h, cudaStreamSynchronize(h->stream));
@@ -1049,6 +1061,7 @@ extern "C" int sse_query_noalloc(const sse_params* p, const uint8_t* d_sle, uint
   const int rc = derive_params(*p, q, d);
   if (rc != SSE_OK) return rc;
   if (q.r2 > (uint32_t)kNoAllocMaxRows) return SSE_ERR_INVALID_PARAM;  // beyond the scratch array
+  if (q.stamp_bits != 8) return SSE_ERR_INVALID_PARAM;                // 8-bit stamps only
   if (n == 0) return SSE_OK;
   if (!d_sle || !d_hosts || !d_est || (reinterpret_cast<uintptr_t>(d_sle) & 15u)) return SSE_ERR_INVALID_PARAM;
   uint32_t* counts = nullptr;
@@ -1066,11 +1079,11 @@ extern "C" int sse_query_noalloc(const sse_params* p, const uint8_t* d_sle, uint
     cudaGetLastError();
     return SSE_ERR_CUDA;
   }
-  k_close<<<(unsigned)(num_sms * 8), kCloseThreads, 0, stream>>>(kp, nullptr, const_cast<uint8_t*>(d_sle), nullptr,
-                                                                   counts, stamp_of(slice), nullptr, 0u, 0u);
+  k_close<uint8_t><<<(unsigned)(num_sms * 8), kCloseThreads, 0, stream>>>(
+      kp, nullptr, const_cast<uint8_t*>(d_sle), nullptr, counts, stamp_of(slice), nullptr, 0u, 0u);
   if (cudaGetLastError() != cudaSuccess) return SSE_ERR_CUDA;
   uint64_t grid = std::min<uint64_t>((uint64_t)n, (uint64_t)num_sms * 16);
-  k_estimate<<<(unsigned)grid, kEstThreads, 0, stream>>>(kp, d_sle, d_hosts, nullptr, n, counts, d.w_theta,
+  k_estimate<uint8_t><<<(unsigned)grid, kEstThreads, 0, stream>>>(kp, d_sle, d_hosts, nullptr, n, counts, d.w_theta,
                                                              stamp_of(slice), nullptr, d_est, d_flags, nullptr, nullptr,
                                                              nullptr, nullptr);
   if (cudaGetLastError() != cudaSuccess) return SSE_ERR_CUDA;
@@ -1189,6 +1202,7 @@ int sse_batch_create(const sse_params* p, int n_routers, uint64_t capacity_pairs
   sse_derived d;
   int rc = derive_params(*p, q, d);
   if (rc) return rc;
+  if (q.stamp_bits != 8) return SSE_ERR_INVALID_PARAM;  // batches use 8-bit stamps
   sse_batch* b = new (std::nothrow) sse_batch();
   if (!b) return SSE_ERR_OOM;
   b->n = n_routers;
@@ -1624,6 +1638,7 @@ int sse_server_create(const sse_params* p, const sse_server_config* cfg, sse_ser
   sse_derived d;
   int rc = derive_params(*p, q, d);
   if (rc) return rc;
+  if (q.stamp_bits != 8) return SSE_ERR_INVALID_PARAM;  // the server uses 8-bit stamps
   // admission by memory budget: every router's estimator, the global one and the staging
   const uint64_t need = (cfg->n_routers + 1) * estimator_bytes(q, d) + (uint64_t)cfg->slots * cfg->slot_pairs * 8;
   if (need > cfg->memory_budget) return SSE_ERR_OOM;
@@ -2081,7 +2096,7 @@ int sse_mlp_train_epoch(sse_mlp* m, const float* d_x, const float* d_t, const ui
 }
 
 int sse_features(sse_handle* h, const uint32_t* d_hosts, uint32_t n, float* d_x) {
-  if (!h || (!d_hosts && n) || (!d_x && n)) return SSE_ERR_INVALID_PARAM;
+  if (!h || (!d_hosts && n) || (!d_x && n) || h->wide) return SSE_ERR_INVALID_PARAM;
   if (h->sticky) return h->sticky;
   if (!n) return SSE_OK;
   k_features<<<grid_for(h, n, 1, 16), kFeatThreads, 0, h->stream>>>(h->kp, h->sre, h->sle, d_hosts, n, h->clock, d_x);
@@ -2091,7 +2106,7 @@ int sse_features(sse_handle* h, const uint32_t* d_hosts, uint32_t n, float* d_x)
 
 int sse_query_learned(sse_handle* h, sse_mlp* m, const uint32_t* d_hosts, uint32_t n, float* d_est,
                       float* d_est_lc, uint8_t* d_flags) {
-  if (!h || !m || (!d_hosts && n) || (!d_est && n) || (!d_est_lc && n)) return SSE_ERR_INVALID_PARAM;
+  if (!h || !m || (!d_hosts && n) || (!d_est && n) || (!d_est_lc && n) || h->wide) return SSE_ERR_INVALID_PARAM;
   if (m->s.n_in != h->p.k + 2) return SSE_ERR_MISMATCH;
   for (uint32_t b0 = 0; b0 < n; b0 += m->max_batch) {
     const uint32_t nb = std::min(m->max_batch, n - b0);
@@ -2111,9 +2126,9 @@ int sse_query_learned(sse_handle* h, sse_mlp* m, const uint32_t* d_hosts, uint32
 int sse_reset(sse_handle* h) {
   if (!h) return SSE_ERR_INVALID_PARAM;
   if (h->sticky) return h->sticky;
-  const uint32_t first = stamp_of(0);
+  const uint32_t first = stamp_of(0, h->smod);
   SSE_CUDA(h, cudaMemsetAsync(h->state, 0, h->d.sre_bytes + h->d.sle_bytes, h->stream));
-  SSE_CUDA(h, cudaMemsetAsync(h->sle_bits, 0, h->d.sle_bytes / 8, h->stream));
+  SSE_CUDA(h, cudaMemsetAsync(h->sle_bits, 0, h->sle_cells / 8, h->stream));
   SSE_CUDA(h, cudaMemsetAsync(h->hot_bits, 0, ((uint64_t)h->p.r << h->p.q) / 8, h->stream));
   SSE_CUDA(h, cudaMemsetAsync(h->scratch, 0, sizeof(CloseScratch), h->stream));
   SSE_CUDA(h, cudaMemcpyAsync(h->clock, &first, 4, cudaMemcpyHostToDevice, h->stream));

@@ -48,11 +48,17 @@ __host__ __device__ __forceinline__ uint32_t stamp_age(uint32_t s, uint32_t cs) 
   return (cs + 255 - s) % 255;
 }
 
+// Stamps of w-bit cells cycle through 1..2^w - 1 (slice t: 1 + t mod (2^w - 1)); 0 is unset.
+__host__ __device__ __forceinline__ uint32_t stamp_mod(uint32_t stamp_bits) { return (1u << stamp_bits) - 1u; }
+__host__ __device__ __forceinline__ uint32_t stamp_of(uint64_t slice, uint32_t mod) {
+  return (uint32_t)(1 + slice % mod);
+}
+
 // The estimator's device clock holds the current stamp; advancing a slice moves it along the
-// 1..255 cycle on the device, so launches read the right stamp even when replayed.
-__global__ void k_tick(uint32_t* clock, uint32_t n) {
+// 1..mod cycle on the device, so launches read the right stamp even when replayed.
+__global__ void k_tick(uint32_t* clock, uint32_t n, uint32_t mod = 255u) {
   if (threadIdx.x == 0 && blockIdx.x == 0)
-    for (uint32_t i = 0; i < n; ++i) clock[i] = clock[i] % 255u + 1u;
+    for (uint32_t i = 0; i < n; ++i) clock[i] = clock[i] % mod + 1u;
 }
 
 // Scratch counters of one close, zeroed before it (one cudaMemsetAsync).

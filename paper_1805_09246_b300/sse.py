@@ -91,8 +91,9 @@ def core_link_params(k: int = 8, seed: int = 0) -> Params:
     return Params(q=20, q2=16, eta2=4096, k=k, seed=seed)
 
 
-def paper_params(k: int = 8) -> Params:
-    """The parameter set of the paper's experiments (Section 5)."""
+def paper_params(k: int = 300) -> Params:
+    """The parameter set of the paper's experiments (Section 5), 16-bit stamps; k defaults to
+    the paper's sliding-window length."""
     p = _Params()
     lib().sse_params_default(ctypes.byref(p))
     return Params(r=p.r, q=p.q, delta=p.delta, eta=p.eta, r2=p.r2, q2=p.q2, delta2=p.delta2, eta2=p.eta2,
@@ -395,10 +396,11 @@ class Estimator:
         return bits[: p.r << p.q].reshape(p.r, 1 << p.q)
 
     def read_stamps(self) -> tuple[np.ndarray, np.ndarray]:
-        """Raw stamps: RSRA uint8 [r, 2^q, 8] and SLEA uint8 [r', row_len2]."""
+        """Raw stamps: RSRA [r, 2^q, 8] and SLEA [r', row_len2], uint8 or uint16 cells."""
         p, d = self.params, self.derived
-        sre = np.zeros((p.r, 1 << p.q, p.eta), np.uint8)
-        sle = np.zeros((p.r2, d["row_pitch2"]), np.uint8)
+        dt = np.uint8 if p.stamp_bits == 8 else np.uint16
+        sre = np.zeros((p.r, 1 << p.q, p.eta), dt)
+        sle = np.zeros((p.r2, d["row_pitch2"]), dt)
         _check(self._lib.sse_read_stamps(self._h, ctypes.c_void_p(sre.ctypes.data), sre.nbytes,
                                          ctypes.c_void_p(sle.ctypes.data), sle.nbytes), "sse_read_stamps")
         return sre, sle[:, : d["row_len2"]]

@@ -58,7 +58,8 @@ def test_derivation_matches_oracle(libsse):
 def test_invalid_parameters_rejected(libsse):
     from paper_1805_09246_b300 import sse
     bad = [dict(r=2), dict(q=4), dict(q=14, delta=5), dict(eta=16), dict(eta2=1000), dict(k=0), dict(k=255),
-           dict(theta=0), dict(stamp_bits=16), dict(max_candidates=0), dict(r2=17), dict(delta2=0)]
+           dict(theta=0), dict(stamp_bits=12), dict(stamp_bits=16, k=65535), dict(max_candidates=0), dict(r2=17),
+           dict(delta2=0)]
     for kw in bad:
         with pytest.raises(sse.SSEError):
             sse.derive(_params(**kw))
@@ -68,3 +69,6 @@ def test_paper_defaults(libsse):
     from paper_1805_09246_b300 import sse
     p = sse.paper_params()
     assert (p.r, p.q, p.delta, p.eta, p.r2, p.q2, p.delta2, p.eta2, p.theta) == (5, 17, 5, 8, 5, 17, 16, 1 << 14, 1024)
+    assert (p.k, p.stamp_bits) == (300, 16)  # the sliding-window experiment (Section 5)
+    d = sse.derive(p)
+    assert d["sre_bytes"] == 5 * (1 << 17) * 8 * 2 and d["sle_bytes"] == 5 * d["row_pitch2"] * 2

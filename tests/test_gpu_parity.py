@@ -29,9 +29,9 @@ def oracle_params(p):
 
 def compare_state(est, orc, p, slice_index):
     sre_s, sle_s = est.read_stamps()
-    o_sre, o_sle = orc.canonical()
-    g_sre = helpers.canonical_from_stamps(sre_s, slice_index, p.k)
-    g_sle = helpers.canonical_from_stamps(sle_s, slice_index, p.k)
+    o_sre, o_sle = helpers.oracle_canonical(orc, p.k)
+    g_sre = helpers.canonical_from_stamps(sre_s, slice_index, p.k, p.stamp_bits)
+    g_sle = helpers.canonical_from_stamps(sle_s, slice_index, p.k, p.stamp_bits)
     assert np.array_equal(g_sre, o_sre), "RSRA state differs"
     assert np.array_equal(g_sle, o_sle), "SLEA state differs"
 
