@@ -544,9 +544,13 @@ def main():
         d2h = 0
         torch.cuda.synchronize()
         t0 = time.perf_counter()
+        # each slice's host-to-device copies run while the previous slice's close is on the GPU
+        e2e_est.update_host(pinned[0])
         for s in range(k_e2e):
-            e2e_est.update_host(pinned[s % len(pinned)])
-            r = e2e_est.close_slice()
+            e2e_est.close_slice_async()
+            if s + 1 < k_e2e:
+                e2e_est.update_host(pinned[(s + 1) % len(pinned)])
+            r = e2e_est.close_slice_wait()
             d2h += 64 + r.n_candidates * 9  # report header + hosts/est/flags
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0

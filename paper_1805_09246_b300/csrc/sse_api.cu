@@ -123,7 +123,7 @@ struct sse_handle {
   uint32_t* stage_host[2] = {nullptr, nullptr};
   cudaEvent_t ev_copied[2] = {nullptr, nullptr};
   cudaEvent_t ev_used[2] = {nullptr, nullptr};
-  cudaStream_t copy_stream = nullptr;
+  cudaStream_t copy_stream[2] = {nullptr, nullptr};  // one per staging buffer (two copy engines)
   // sse_close_slice as one CUDA graph (captured on a private stream, replayed on `stream`)
   int close_graph = 1;
   cudaStream_t capture_stream = nullptr;
@@ -382,10 +382,11 @@ const char* sse_strerror(int status) {
 void sse_destroy(sse_handle* h) {
   if (!h) return;
   cudaStreamSynchronize(h->stream);
-  if (h->copy_stream) {
-    cudaStreamSynchronize(h->copy_stream);
-    cudaStreamDestroy(h->copy_stream);
-  }
+  for (int b = 0; b < 2; ++b)
+    if (h->copy_stream[b]) {
+      cudaStreamSynchronize(h->copy_stream[b]);
+      cudaStreamDestroy(h->copy_stream[b]);
+    }
   for (int b = 0; b < 2; ++b) {
     if (h->stage_dev[b]) cudaFree(h->stage_dev[b]);
     if (h->stage_host[b]) cudaFreeHost(h->stage_host[b]);
@@ -600,10 +601,11 @@ int sse_update_host(sse_handle* h, const uint32_t* h_pairs, uint64_t n_pairs) {
   if (n_pairs == 0) return SSE_OK;
   if (!h_pairs) return SSE_ERR_INVALID_PARAM;
   constexpr uint64_t kChunk = 1ull << 22;  // pairs per staging buffer (32 MiB)
-  if (!h->copy_stream) {
-    bool ok = cudaStreamCreateWithFlags(&h->copy_stream, cudaStreamNonBlocking) == cudaSuccess;
+  if (!h->copy_stream[0]) {
+    bool ok = true;
     for (int b = 0; b < 2 && ok; ++b) {
-      ok = cudaMalloc(&h->stage_dev[b], kChunk * 8) == cudaSuccess &&
+      ok = cudaStreamCreateWithFlags(&h->copy_stream[b], cudaStreamNonBlocking) == cudaSuccess &&
+           cudaMalloc(&h->stage_dev[b], kChunk * 8) == cudaSuccess &&
            cudaEventCreateWithFlags(&h->ev_copied[b], cudaEventDisableTiming) == cudaSuccess &&
            cudaEventCreateWithFlags(&h->ev_used[b], cudaEventDisableTiming) == cudaSuccess;
     }
@@ -632,8 +634,8 @@ int sse_update_host(sse_handle* h, const uint32_t* h_pairs, uint64_t n_pairs) {
       memcpy(h->stage_host[b], src, m * 8);
       src = h->stage_host[b];
     }
-    SSE_CUDA(h, cudaMemcpyAsync(h->stage_dev[b], src, m * 8, cudaMemcpyHostToDevice, h->copy_stream));
-    SSE_CUDA(h, cudaEventRecord(h->ev_copied[b], h->copy_stream));
+    SSE_CUDA(h, cudaMemcpyAsync(h->stage_dev[b], src, m * 8, cudaMemcpyHostToDevice, h->copy_stream[b]));
+    SSE_CUDA(h, cudaEventRecord(h->ev_copied[b], h->copy_stream[b]));
     SSE_CUDA(h, cudaStreamWaitEvent(h->stream, h->ev_copied[b], 0));
     int rc = launch_update(h, h->stage_dev[b], m);
     if (rc) return rc;
