@@ -35,7 +35,7 @@
 extern "C" {
 #endif
 
-#define SSE_VERSION 1
+#define SSE_VERSION 2
 
 #if defined(__GNUC__)
 #define SSE_API __attribute__((visibility("default")))
@@ -87,6 +87,11 @@ enum sse_update_mode {
  *          double the state; batches, the server, sse_features and sse_query_learned take
  *          8-bit cells only
  *   max_candidates  capacity for candidate hosts per close, 1..2^22
+ *   rhfg_hash  hash of RHFG[0] (Eq. 6): 0 = multiply-add-shift like the other functions,
+ *          1 = simple tabulation (the family the paper cites for RHFG[0]): four tables of 256
+ *          32-bit entries indexed by the address bytes and XORed, entries drawn from
+ *          SplitMix64(seed) after the other keys; the top q bits are used
+ *   reserved  must be 0
  *   seed   every hash key derives from it (SplitMix64)
  */
 typedef struct sse_params {
@@ -95,6 +100,8 @@ typedef struct sse_params {
   uint32_t k, theta;
   uint32_t stamp_bits;
   uint32_t max_candidates;
+  uint32_t rhfg_hash;
+  uint32_t reserved;
   uint64_t seed;
 } sse_params;
 
@@ -182,6 +189,16 @@ SSE_API int sse_update_host(sse_handle* h, const uint32_t* h_pairs, uint64_t n_p
 
 /* Selects how sse_update() writes cells (enum sse_update_mode). Results never depend on
  * it. Errors: INVALID_PARAM. */
+/*
+ * Which end of a pair is the host aip whose opposite hosts are counted (Definition 1 lets a
+ * host be either end): SSE_DIR_SRC (default) scans (src, dst) as (aip, bip), SSE_DIR_DST as
+ * (bip, aip), SSE_DIR_BOTH scans every pair both ways (a host's opposite hosts in either
+ * direction). DST and BOTH exchange the ends into a 128 MiB device buffer owned by the
+ * handle, allocated at first use. Errors: INVALID_PARAM.
+ */
+enum { SSE_DIR_SRC = 0, SSE_DIR_DST = 1, SSE_DIR_BOTH = 2 };
+SSE_API int sse_set_direction(sse_handle* h, int direction);
+
 SSE_API int sse_set_update_mode(sse_handle* h, int mode);
 
 /* Number of update variants the autotuner chooses from (variant 0 is the direct update,

@@ -43,7 +43,7 @@ def build(force: bool = False) -> str:
 
 class _Params(ctypes.Structure):
     _fields_ = [(n, ctypes.c_uint32) for n in
-                ("r", "q", "delta", "eta", "r2", "q2", "delta2", "eta2", "k", "theta")] + \
+                ("r", "q", "delta", "eta", "r2", "q2", "delta2", "eta2", "k", "theta", "rhfg_hash", "pad")] + \
                [("seed", ctypes.c_uint64)]
 
 
@@ -68,10 +68,11 @@ class Params:
     k: int = 4
     theta: int = 1024
     seed: int = 0
+    rhfg_hash: int = 0  # RHFG[0]: 0 multiply-add-shift, 1 simple tabulation (Section 3.3)
 
     def to_c(self) -> _Params:
         return _Params(self.r, self.q, self.delta, self.eta, self.r2, self.q2, self.delta2,
-                       self.eta2, self.k, self.theta, self.seed)
+                       self.eta2, self.k, self.theta, self.rhfg_hash, 0, self.seed)
 
 
 _lib = None

@@ -22,7 +22,10 @@
 //    compares B(i-1) >> delta with the low q-delta bits of B(i);
 //  * the delta low bits of aip that no B(i) carries are enumerated, and a host is kept
 //    only if its r estimators are exactly the tuple's;
-//  * hash functions: multiply-add-shift with keys drawn from SplitMix64(seed);
+//  * hash functions: multiply-add-shift with keys drawn from SplitMix64(seed); RHFG[0]
+//    may instead be simple tabulation (the family Section 3.3 cites for it): four tables of
+//    256 32-bit entries, one per address byte, XORed, entries drawn from SplitMix64 after
+//    the keys (top 32 bits of each output);
 //  * LSB(0) = 32;
 //  * a host is reported when its corrected weight w^ reaches
 //    w_theta = eta' * (1 - exp(-theta/eta')), which is est >= theta in exact arithmetic;
@@ -88,6 +91,8 @@ struct orc_params {
   uint32_t r, q, delta, eta;        // RSRA: r rows of 2^q SREs, RHFG shift delta, eta cells per SRE
   uint32_t r2, q2, delta2, eta2;    // SLEA: r' rows of 2^q' SLEs, offset delta', eta' cells per SLE
   uint32_t k, theta;                // window length in slices, super point threshold
+  uint32_t rhfg_hash;               // RHFG[0]: 0 multiply-add-shift, 1 simple tabulation
+  uint32_t pad;
   uint64_t seed;                    // all hash keys derive from it
 };
 
@@ -114,6 +119,7 @@ struct Oracle {
   unsigned lg_eta, lg_eta2;
   Key H1, H2, H3, R0;
   std::vector<Key> LH;
+  uint32_t tab[4][256];  // RHFG[0] tabulation tables (rhfg_hash = 1)
   std::vector<uint16_t> rsra;  // [r][2^q][eta]
   std::vector<uint16_t> slea;  // [r'][row_len2]
   uint64_t slice = 0;          // index t of the slice being scanned
@@ -127,7 +133,12 @@ struct Oracle {
   size_t sle_cell(uint32_t row, uint64_t pos) const { return (size_t)row * d.row_len2 + pos; }
 
   // RHFG[0]: a random hash of aip onto [0, 2^q) (Section 3.3).
-  uint32_t rhfg0(uint32_t aip) const { return hash_top(R0, aip, p.q); }
+  uint32_t rhfg0(uint32_t aip) const {
+    if (p.rhfg_hash == 0) return hash_top(R0, aip, p.q);
+    uint32_t v = 0;
+    for (int j = 0; j < 4; ++j) v ^= tab[j][(aip >> (8 * j)) & 0xFFu];
+    return p.q == 0 ? 0u : v >> (32 - p.q);
+  }
   // RHFG[i] for 1 <= i <= r-1, Eq. 6: ((aip >> i*delta) XOR RHFG[0](aip)) mod 2^q.
   uint32_t rhfg(uint32_t i, uint32_t aip) const {
     if (i == 0) return rhfg0(aip);
@@ -193,6 +204,7 @@ int derive(const orc_params& in, orc_params& p, orc_derived& d) {
   if (p.delta2 < 1 || p.delta2 > p.eta2) return ORC_ERR_PARAM;
   if (p.k < 1 || p.k >= kInf) return ORC_ERR_PARAM;
   if (p.theta < 1) return ORC_ERR_PARAM;
+  if (p.rhfg_hash > 1) return ORC_ERR_PARAM;
   d = orc_derived{};
   d.delta = p.delta;
   // Eq. 1: tau = ceil(log2(theta/eta)), taken as the smallest tau >= 0 with eta*2^tau >= theta.
@@ -297,6 +309,8 @@ int orc_create(const orc_params* in, int track_exact, void** out) {
   o->H3 = next_key();
   o->R0 = next_key();
   for (uint32_t i = 0; i < o->p.r2; ++i) o->LH.push_back(next_key());
+  for (int j = 0; j < 4; ++j)
+    for (int v = 0; v < 256; ++v) o->tab[j][v] = (uint32_t)(splitmix64_next(s) >> 32);
   o->rsra.assign((size_t)o->p.r * ((size_t)1 << o->p.q) * o->p.eta, kInf);
   o->slea.assign((size_t)o->p.r2 * o->d.row_len2, kInf);
   o->slice = 0;

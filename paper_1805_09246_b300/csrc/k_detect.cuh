@@ -48,7 +48,7 @@ __device__ __forceinline__ void regain(const KParams& p, uint32_t he0, const uin
     high |= (uint64_t)(B[i] >> (p.q - p.delta)) << (i * p.delta + p.q - p.delta);
   for (uint32_t low = 0; low < (1u << p.delta); ++low) {
     const uint32_t aip = (uint32_t)(high | low);
-    if (mas_top(p.key_a[kR0], p.key_b[kR0], aip, p.q) != he0) continue;
+    if (rhfg0(p, aip) != he0) continue;
     emit_candidate(aip, cand, n_cand, cap, overflow);
   }
 }

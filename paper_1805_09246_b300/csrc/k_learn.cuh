@@ -47,7 +47,7 @@ __global__ void __launch_bounds__(kFeatThreads) k_features(const __grid_constant
     // SRE weights of the host's r estimators (RHFG[i], Eq. 6), one thread per row
     if (threadIdx.x < p.r) {
       const uint32_t i = threadIdx.x;
-      const uint32_t r0 = mas_top(p.key_a[kR0], p.key_b[kR0], aip, p.q);
+      const uint32_t r0 = rhfg0(p, aip);
       const uint32_t col =
           i == 0 ? r0 : (uint32_t)((((uint64_t)aip >> (i * p.delta)) ^ r0) & ((1u << p.q) - 1u));
       const uint8_t* cells = sre + (((uint64_t)i << p.q) + col) * 8;

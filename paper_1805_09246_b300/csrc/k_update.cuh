@@ -27,6 +27,14 @@ __device__ __forceinline__ uint4 load_stream(const uint4* ptr, uint64_t policy) 
 }
 __device__ __forceinline__ uint4 load_stream(const uint4* ptr) { return load_stream(ptr, stream_policy()); }
 
+// Exchanges the two ends of n pairs (src <-> dst), for hosts counted as destinations.
+__global__ void k_swap_pairs(const uint2* __restrict__ in, uint2* __restrict__ out, uint64_t n) {
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
+    const uint2 v = in[i];
+    out[i] = make_uint2(v.y, v.x);
+  }
+}
+
 // Stamps are cells of type St (uint8_t or uint16_t); kernels take byte pointers to the
 // estimator and address it in cells.
 
@@ -53,7 +61,7 @@ __device__ __forceinline__ bool rsra_sampled(const KParams& p, uint32_t bip) {
 template <typename St>
 __device__ __forceinline__ void rsra_write(const KParams& p, uint32_t aip, uint32_t bip, St* sre, St stamp) {
   const uint32_t h2 = mas_top(p.key_a[kH2], p.key_b[kH2], bip, 3);
-  const uint32_t r0 = mas_top(p.key_a[kR0], p.key_b[kR0], aip, p.q);
+  const uint32_t r0 = rhfg0(p, aip);
   const uint32_t qmask = (1u << p.q) - 1u;
   sre[((uint64_t)r0 << 3) + h2] = stamp;
   for (uint32_t i = 1; i < p.r; ++i) {

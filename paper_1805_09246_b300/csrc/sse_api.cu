@@ -50,6 +50,7 @@ int derive_params(const sse_params& in, sse_params& p, sse_derived& d) {
   if (!is_pow2(p.eta2) || p.eta2 < 32 || p.eta2 > 65536) return SSE_ERR_INVALID_PARAM;
   if (p.delta2 < 1 || p.delta2 > p.eta2) return SSE_ERR_INVALID_PARAM;
   if (p.stamp_bits != 8 && p.stamp_bits != 16) return SSE_ERR_INVALID_PARAM;
+  if (p.rhfg_hash > 1 || p.reserved != 0) return SSE_ERR_INVALID_PARAM;
   if (p.k < 1 || p.k > stamp_mod(p.stamp_bits) - 1) return SSE_ERR_INVALID_PARAM;  // k <= 254 or 65534
   if (p.theta < 1) return SSE_ERR_INVALID_PARAM;
   if (p.max_candidates < 1 || p.max_candidates > (1u << 22)) return SSE_ERR_INVALID_PARAM;
@@ -89,6 +90,8 @@ struct sse_handle {
   cudaError_t cuda_error = cudaSuccess;  // the CUDA error behind `sticky`
   uint64_t launches = 0;  // kernels launched by this handle
   int update_mode = SSE_UPDATE_AUTO;
+  int direction = SSE_DIR_SRC;   // which end of a pair is the host aip (Definition 1)
+  uint32_t* swap_buf = nullptr;  // pairs with their ends exchanged (SSE_DIR_DST / BOTH)
   int tuned_variant = -1;  // update variant chosen by sse_autotune_update (-1: none yet)
   int num_sms = 148;
   // device memory
@@ -103,6 +106,7 @@ struct sse_handle {
   uint32_t* list1 = nullptr;
   uint32_t* tables = nullptr;  // hot bitmaps of rows 2..r-1 regrouped for the join
   uint32_t* any3 = nullptr;    // row 3's "any hot" bitmap over c (r > 3, delta <= 5)
+  uint32_t* rhfg_tab = nullptr;  // RHFG[0] tabulation tables (rhfg_hash = 1)
   uint32_t join_smem_t2 = 0;   // stage the row-2 table in shared memory
   uint32_t join_list1_cap = 0; // HSE(1) entries staged in shared memory when it fits
   size_t join_smem = 0;
@@ -162,6 +166,15 @@ int fail(sse_handle* h, cudaError_t e) {
     cudaError_t e_ = cudaGetLastError();         \
     if (e_ != cudaSuccess) return fail((h), e_); \
   } while (0)
+
+// The simple-tabulation tables of RHFG[0]: 1024 32-bit entries (table j, byte value v at
+// j * 256 + v), the top halves of the SplitMix64(seed) outputs that follow the keys of
+// H1, H2, H3, RHFG[0] and LH_0..LH_{r'-1}.
+void make_rhfg_tables(const sse_params& p, uint32_t* tab) {
+  uint64_t s = p.seed;
+  for (uint32_t x = 0; x < 2 * (kLH + p.r2); ++x) splitmix64(s);
+  for (int i = 0; i < 1024; ++i) tab[i] = (uint32_t)(splitmix64(s) >> 32);
+}
 
 KParams make_kparams(const sse_params& p, const sse_derived& d) {
   KParams k;
@@ -280,12 +293,37 @@ int launch_variant(sse_handle* h, const uint32_t* d_pairs, uint64_t n, int varia
   return variant == 0 ? launch_update_direct(h, d_pairs, n) : launch_update_tiled(h, d_pairs, n, variant - 1);
 }
 
-int launch_update(sse_handle* h, const uint32_t* d_pairs, uint64_t n) {
+int launch_update_one_way(sse_handle* h, const uint32_t* d_pairs, uint64_t n) {
   const int tiled_variant = h->tuned_variant > 0 ? h->tuned_variant : 1;
   if (h->update_mode == SSE_UPDATE_DIRECT) return launch_variant(h, d_pairs, n, 0);
   if (h->update_mode == SSE_UPDATE_TILED) return launch_variant(h, d_pairs, n, tiled_variant);
   if (n < kTiledMinPairs) return launch_variant(h, d_pairs, n, 0);
   return launch_variant(h, d_pairs, n, h->tuned_variant >= 0 ? h->tuned_variant : tiled_variant);
+}
+
+constexpr uint64_t kSwapChunk = 1ull << 24;  // pairs per exchanged chunk (128 MiB)
+
+// Definition 1 counts a host's opposite hosts; SSE_DIR_SRC takes aip = src (the default),
+// SSE_DIR_DST aip = dst, SSE_DIR_BOTH both (each pair is scanned in both directions).
+int launch_update(sse_handle* h, const uint32_t* d_pairs, uint64_t n) {
+  if (h->direction == SSE_DIR_SRC) return launch_update_one_way(h, d_pairs, n);
+  if (h->direction == SSE_DIR_BOTH) {
+    const int rc = launch_update_one_way(h, d_pairs, n);
+    if (rc) return rc;
+  }
+  if (!h->swap_buf && cudaMalloc(&h->swap_buf, kSwapChunk * 8) != cudaSuccess) {
+    cudaGetLastError();
+    return SSE_ERR_OOM;
+  }
+  for (uint64_t done = 0; done < n; done += kSwapChunk) {
+    const uint64_t m = std::min(kSwapChunk, n - done);
+    k_swap_pairs<<<grid_for(h, m, 256, 8), 256, 0, h->stream>>>(reinterpret_cast<const uint2*>(d_pairs + 2 * done),
+                                                                 reinterpret_cast<uint2*>(h->swap_buf), m);
+    SSE_LAUNCHED(h);
+    const int rc = launch_update_one_way(h, h->swap_buf, m);
+    if (rc) return rc;
+  }
+  return SSE_OK;
 }
 
 // Expire/weigh/count pass. mode: bit 0 expire, bit 1 write hot bitmap. Without either
@@ -408,6 +446,8 @@ void sse_destroy(sse_handle* h) {
   cudaFree(h->scratch);
   cudaFree(h->query_active2);
   cudaFree(h->any3);
+  cudaFree(h->rhfg_tab);
+  cudaFree(h->swap_buf);
   if (h->host_scratch) cudaFreeHost(h->host_scratch);
   if (h->close_exec) cudaGraphExecDestroy(h->close_exec);
   if (h->close_g) cudaGraphDestroy(h->close_g);
@@ -469,6 +509,17 @@ int sse_init(const sse_params* p, void* cuda_stream, sse_handle** out) {
   }
   h->sre = h->state;
   h->sle = h->state + d.sre_bytes;
+  if (q.rhfg_hash == 1) {
+    uint32_t tab[1024];
+    make_rhfg_tables(q, tab);
+    if (cudaMalloc(&h->rhfg_tab, sizeof(tab)) != cudaSuccess ||
+        cudaMemcpy(h->rhfg_tab, tab, sizeof(tab), cudaMemcpyHostToDevice) != cudaSuccess) {
+      cudaGetLastError();
+      sse_destroy(h);
+      return SSE_ERR_OOM;
+    }
+    h->kp.tab = h->rhfg_tab;
+  }
   h->tiles = make_tiles(q, d, h->num_sms);
   for (int v = 0; v < 4 * kNumTiledVariants; ++v) {
     const TiledKernel fn = kTiledVariants[v / 4].fn[(v >> 1) & 1][v & 1];
@@ -533,6 +584,12 @@ uint64_t sse_kernel_launches(const sse_handle* h) { return h ? h->launches : 0; 
 
 const char* sse_cuda_error(const sse_handle* h) {
   return (h && h->cuda_error != cudaSuccess) ? cudaGetErrorName(h->cuda_error) : "";
+}
+
+int sse_set_direction(sse_handle* h, int direction) {
+  if (!h || direction < SSE_DIR_SRC || direction > SSE_DIR_BOTH) return SSE_ERR_INVALID_PARAM;
+  h->direction = direction;
+  return SSE_OK;
 }
 
 int sse_set_update_mode(sse_handle* h, int mode) {

@@ -24,8 +24,9 @@ struct KParams {
   uint32_t r, q, delta, r2;
   uint32_t q2, delta2, lg_eta2, eta2;
   uint32_t k, tau_mask, sre_on, hot_min;
-  uint64_t row_pitch2;  // bytes between SLEA rows
+  uint64_t row_pitch2;  // cells between SLEA rows
   uint64_t row_len2;    // cells per SLEA row
+  const uint32_t* tab;  // RHFG[0] tabulation tables [4][256] (device), or NULL: multiply-add-shift
 };
 
 // Multiply-add-shift hash: the top m bits (0 <= m <= 32) of (a*x + b) mod 2^64.
@@ -37,6 +38,15 @@ __host__ __device__ __forceinline__ uint32_t mas_hi(uint64_t a, uint64_t b, uint
 }
 __host__ __device__ __forceinline__ uint32_t mas_top(uint64_t a, uint64_t b, uint32_t x, uint32_t m) {
   return (uint32_t)((uint64_t)mas_hi(a, b, x) >> (32 - m));
+}
+
+// RHFG[0](aip) (Eq. 6): simple tabulation over the four address bytes when the tables are
+// set, else multiply-add-shift; the top q bits.
+__device__ __forceinline__ uint32_t rhfg0(const KParams& p, uint32_t aip) {
+  if (p.tab)
+    return (p.tab[aip & 255u] ^ p.tab[256 + ((aip >> 8) & 255u)] ^ p.tab[512 + ((aip >> 16) & 255u)] ^
+            p.tab[768 + (aip >> 24)]) >> (32 - p.q);
+  return mas_top(p.key_a[kR0], p.key_b[kR0], aip, p.q);
 }
 
 // Cyclic stamp arithmetic: slice t has stamp 1 + (t mod 255); 0 marks an unset cell.

@@ -22,6 +22,7 @@ FLAG_SATURATED = 2
 ERR_CAPACITY = -3
 UPDATE_AUTO, UPDATE_DIRECT, UPDATE_TILED = 0, 1, 2
 BATCH_DETECT, BATCH_ROUTERS, BATCH_SCAN = 0, 1, 2
+DIR_SRC, DIR_DST, DIR_BOTH = 0, 1, 2
 
 
 class SSEError(RuntimeError):
@@ -33,7 +34,7 @@ class SSEError(RuntimeError):
 class _Params(ctypes.Structure):
     _fields_ = [(n, ctypes.c_uint32) for n in
                 ("r", "q", "delta", "eta", "r2", "q2", "delta2", "eta2", "k", "theta",
-                 "stamp_bits", "max_candidates")] + [("seed", ctypes.c_uint64)]
+                 "stamp_bits", "max_candidates", "rhfg_hash", "reserved")] + [("seed", ctypes.c_uint64)]
 
 
 class _Derived(ctypes.Structure):
@@ -80,10 +81,11 @@ class Params:
     stamp_bits: int = 8
     max_candidates: int = 1 << 16
     seed: int = 0
+    rhfg_hash: int = 0  # 0: multiply-add-shift, 1: simple tabulation (RHFG[0])
 
     def to_c(self) -> _Params:
         return _Params(self.r, self.q, self.delta, self.eta, self.r2, self.q2, self.delta2, self.eta2,
-                       self.k, self.theta, self.stamp_bits, self.max_candidates, self.seed)
+                       self.k, self.theta, self.stamp_bits, self.max_candidates, self.rhfg_hash, 0, self.seed)
 
 
 def core_link_params(k: int = 8, seed: int = 0) -> Params:
@@ -97,7 +99,8 @@ def paper_params(k: int = 300) -> Params:
     p = _Params()
     lib().sse_params_default(ctypes.byref(p))
     return Params(r=p.r, q=p.q, delta=p.delta, eta=p.eta, r2=p.r2, q2=p.q2, delta2=p.delta2, eta2=p.eta2,
-                  k=k, theta=p.theta, stamp_bits=p.stamp_bits, max_candidates=p.max_candidates, seed=p.seed)
+                  k=k, theta=p.theta, stamp_bits=p.stamp_bits, max_candidates=p.max_candidates, seed=p.seed,
+                  rhfg_hash=p.rhfg_hash)
 
 
 _lib = None
@@ -119,6 +122,7 @@ def lib() -> ctypes.CDLL:
             "sse_update": (i32, [vp, vp, u64]),
             "sse_update_host": (i32, [vp, vp, u64]),
             "sse_set_update_mode": (i32, [vp, i32]),
+            "sse_set_direction": (i32, [vp, i32]),
             "sse_set_update_variant": (i32, [vp, i32]),
             "sse_update_variant_count": (i32, []),
             "sse_autotune_update": (i32, [vp, vp, u64, i32, vp, ctypes.POINTER(i32)]),
@@ -300,6 +304,10 @@ class Estimator:
 
     def set_update_mode(self, mode: int) -> None:
         _check(self._lib.sse_set_update_mode(self._h, mode), "sse_set_update_mode")
+
+    def set_direction(self, direction: int) -> None:
+        """DIR_SRC (aip = source, default), DIR_DST (aip = destination) or DIR_BOTH (Definition 1)."""
+        _check(self._lib.sse_set_direction(self._h, direction), "sse_set_direction")
 
     def set_update_variant(self, variant: int) -> None:
         _check(self._lib.sse_set_update_variant(self._h, variant), "sse_set_update_variant")

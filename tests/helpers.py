@@ -9,7 +9,7 @@ import numpy as np
 
 INF = 65535
 INACTIVE = 65535
-HEADER_BYTES = 96  # size of the checkpoint header written by sse_export_state
+HEADER_BYTES = 104  # size of the checkpoint header written by sse_export_state
 
 
 def modulus(stamp_bits: int = 8) -> int:

@@ -24,7 +24,7 @@ def sse():
 
 def oracle_params(p):
     return oracle.Params(r=p.r, q=p.q, delta=p.delta, eta=p.eta, r2=p.r2, q2=p.q2, delta2=p.delta2,
-                         eta2=p.eta2, k=p.k, theta=p.theta, seed=p.seed)
+                         eta2=p.eta2, k=p.k, theta=p.theta, seed=p.seed, rhfg_hash=p.rhfg_hash)
 
 
 def compare_state(est, orc, p, slice_index):
@@ -454,3 +454,37 @@ def test_async_close_pipelined_with_next_update():
         assert np.array_equal(ra.flags, rb.flags)
     for x, y in zip(a.read_stamps(), b.read_stamps()):
         assert np.array_equal(x, y)
+
+
+@pytest.mark.parametrize("rhfg_hash", [0, 1])
+def test_directions_and_tabulation_rhfg0(rhfg_hash):
+    """Definition 1 either way: SSE_DIR_DST equals scanning the exchanged pairs, SSE_DIR_BOTH
+    equals scanning both; with RHFG[0] by simple tabulation as well (states and reports
+    against the oracle, candidates against the definitional brute force)."""
+    S = sse()
+    p = S.Params(seed=61, rhfg_hash=rhfg_hash)
+    tr = synth.Traffic(synth.small_trace(seed=61))
+    slices = [tr.slice(0, t) for t in range(3)]
+    swapped = [x[:, ::-1].copy() for x in slices]
+    both = [np.concatenate([x, y]) for x, y in zip(slices, swapped)]
+    ref_dst = S.Estimator(p)
+    dst = S.Estimator(p)
+    dst.set_direction(S.DIR_DST)
+    two = S.Estimator(p)
+    two.set_direction(S.DIR_BOTH)
+    orc = oracle.Oracle(oracle_params(p))
+    for t in range(3):
+        if t:
+            orc.advance()
+        ref_dst.update(helpers.to_device(swapped[t]))
+        dst.update(helpers.to_device(slices[t]))
+        two.update(helpers.to_device(slices[t]))
+        orc.scan(both[t])
+        ra, rb, rc = ref_dst.close_slice(), dst.close_slice(), two.close_slice()
+        assert np.array_equal(ra.hosts, rb.hosts) and np.array_equal(ra.est, rb.est)
+        compare_report(rc, orc.detect())
+        compare_state(two, orc, p, t)
+    for x, y in zip(ref_dst.read_stamps(), dst.read_stamps()):
+        assert np.array_equal(x, y)
+    if rhfg_hash:
+        assert np.array_equal(rc.hosts, orc.candidates_brute())

@@ -582,3 +582,31 @@ def test_sre_weights_and_features():
     assert f.shape == (len(hosts), p.k + 2)
     assert np.allclose(np.expm1(f[:, : p.k]).round(), e["hist"])
     assert np.allclose(np.expm1(f[:, p.k]).round(), w.sum(1))
+
+
+def test_tabulation_rhfg0_structure_and_tables():
+    """RHFG[0] by simple tabulation (the family Section 3.3 cites): the value is the XOR of
+    four byte-indexed table entries drawn from SplitMix64 after the keys, so (i) changing
+    one byte of the address changes the hash by an amount that does not depend on the other
+    bytes, and (ii) RHFG[0](0) is the XOR of the first entry of each table."""
+    p = oracle.Params(q=14, r2=5, seed=77, rhfg_hash=1)
+    o = oracle.Oracle(p)
+    rng = np.random.default_rng(77)
+    for j in range(4):
+        a, b = rng.integers(0, 256, 2)
+        diffs = set()
+        for x in rng.integers(0, 2**32, 20, dtype=np.uint64).astype(np.uint32):
+            x = int(x) & ~(0xFF << (8 * j))
+            diffs.add(o.rhfg0(x | (int(a) << (8 * j))) ^ o.rhfg0(x | (int(b) << (8 * j))))
+        assert len(diffs) == 1
+    draws = oracle.splitmix64(77, 2 * (4 + p.r2) + 1024)[2 * (4 + p.r2):]
+    tab = [[d >> 32 for d in draws[256 * j:256 * (j + 1)]] for j in range(4)]
+    assert o.rhfg0(0) == (tab[0][0] ^ tab[1][0] ^ tab[2][0] ^ tab[3][0]) >> (32 - p.q)
+    x = 0x12345678
+    want = tab[0][0x78] ^ tab[1][0x56] ^ tab[2][0x34] ^ tab[3][0x12]
+    assert o.rhfg0(x) == want >> (32 - p.q)
+    # the RHFG chain of Eq. 6 and its inversion (Eq. 7) hold for any RHFG[0]
+    for x in rng.integers(0, 2**32, 200, dtype=np.uint64).astype(np.uint32):
+        he0 = o.rhfg0(int(x))
+        for i in range(1, p.r):
+            assert o.rhfg(i, int(x)) ^ he0 == (int(x) >> (i * o.delta)) & ((1 << p.q) - 1)
