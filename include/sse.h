@@ -330,10 +330,13 @@ SSE_API int sse_sync(sse_handle* h);
  * global estimator that merges them (the distributed setting of Section 3.3 and Alg. 7,
  * with all routers' estimators on one device). Each step scans every router's pairs of
  * the current slice in ONE persistent kernel launch (work items = (router, chunk), taken
- * from per-tile counters, so uneven router loads balance), merges the routers into the
- * global estimator (expiring the routers' old cells on the way), closes the slice on the
- * global estimator (candidates, estimates, flags, as sse_close_slice) and advances every
- * estimator. The step's device work is captured once into a CUDA graph and replayed.
+ * from per-tile counters, so uneven router loads balance) whose cell writes go both to the
+ * router and to the global estimator, so the global estimator always equals the merge of
+ * the routers (Algorithms 2 and 7: merge(A, B) is the estimator of A's and B's pairs) without
+ * a pass over the routers' state; it closes the slice on the global estimator (candidates,
+ * estimates, flags, as sse_close_slice) and advances every estimator. The routers' cells
+ * that left the window are reset every 254 - k slices (before their stamp comes round).
+ * The step's device work is captured once into a CUDA graph and replayed.
  * The batch owns a non-blocking CUDA stream (sse_batch_stream) and its estimators; the
  * handles from sse_batch_router / sse_batch_global stay owned by the batch (do not
  * destroy them, and call only read-only functions on them between steps).

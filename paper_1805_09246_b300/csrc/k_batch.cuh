@@ -35,7 +35,8 @@ template <int UNROLL, bool WHOLE>
 __global__ void __launch_bounds__(kTiledThreads, 1)
     k_update_routers(const __grid_constant__ KParams p, TileGeometry g, const __grid_constant__ RouterTable rt,
                      int n_routers, uint64_t sre_bytes, const RouterInputs* __restrict__ in, uint32_t item_pairs,
-                     uint32_t* __restrict__ tile_next, const uint32_t* __restrict__ clock) {
+                     uint32_t* __restrict__ tile_next, const uint32_t* __restrict__ clock,
+                     uint8_t* __restrict__ g_sre) {
   const uint64_t* counts = in->counts;
   extern __shared__ uint32_t bm[];
   __shared__ uint64_t first_item[kMaxRouters + 1];
@@ -93,7 +94,7 @@ __global__ void __launch_bounds__(kTiledThreads, 1)
       if (threadIdx.x == 0) {
         const uint2 v = pairs[j0];
         touch(v.x, v.y);
-        if (rsra) stamp_rsra(p, v.x, v.y, sre, stamp);
+        if (rsra) stamp_rsra(p, v.x, v.y, sre, stamp, g_sre);
       }
       j0 += 1;
     }
@@ -119,8 +120,8 @@ __global__ void __launch_bounds__(kTiledThreads, 1)
           if (kRsra && p.sre_on) {
 #pragma unroll
             for (int u = 0; u < UNROLL; ++u) {
-              rq.push(p, true, buf[u].x, buf[u].y, sre, stamp);
-              rq.push(p, true, buf[u].z, buf[u].w, sre, stamp);
+              rq.push(p, true, buf[u].x, buf[u].y, sre, stamp, g_sre);
+              rq.push(p, true, buf[u].z, buf[u].w, sre, stamp, g_sre);
             }
           }
           continue;
@@ -138,12 +139,12 @@ __global__ void __launch_bounds__(kTiledThreads, 1)
             touch(buf[u].z, buf[u].w);
           }
           if (kRsra && p.sre_on) {
-            rq.push(p, ok, buf[u].x, buf[u].y, sre, stamp);
-            rq.push(p, ok, buf[u].z, buf[u].w, sre, stamp);
+            rq.push(p, ok, buf[u].x, buf[u].y, sre, stamp, g_sre);
+            rq.push(p, ok, buf[u].z, buf[u].w, sre, stamp, g_sre);
           }
         }
       }
-      if (kRsra && p.sre_on) rq.drain(p, sre, stamp);
+      if (kRsra && p.sre_on) rq.drain(p, sre, stamp, g_sre);
     };
     if (rsra)
       scan(std::true_type{});
@@ -152,16 +153,18 @@ __global__ void __launch_bounds__(kTiledThreads, 1)
     if (((end - j0) & 1) && threadIdx.x == 0) {
       const uint2 v = pairs[end - 1];
       touch(v.x, v.y);
-      if (rsra) stamp_rsra(p, v.x, v.y, sre, stamp);
+      if (rsra) stamp_rsra(p, v.x, v.y, sre, stamp, g_sre);
     }
   }
   if (cur >= 0) flush(cur);
   (void)sre_bytes;
 }
 
-// k_apply_bits over every router: blockIdx.y is the router.
+// k_apply_bits over every router: blockIdx.y is the router. With g_gbits set, every
+// router's touched cells are also ORed into the global estimator's bitmap (applied after).
 __global__ void __launch_bounds__(256) k_apply_routers(const __grid_constant__ RouterTable rt, uint64_t sre_bytes,
-                                                       uint64_t n_words, const uint32_t* __restrict__ clock) {
+                                                       uint64_t n_words, const uint32_t* __restrict__ clock,
+                                                       uint32_t* __restrict__ g_gbits) {
   const uint32_t stamp = *clock;
   uint32_t* gbits = rt.gbits[blockIdx.y];
   uint8_t* sle = rt.state[blockIdx.y] + sre_bytes;
@@ -169,6 +172,7 @@ __global__ void __launch_bounds__(256) k_apply_routers(const __grid_constant__ R
        w += (uint64_t)gridDim.x * blockDim.x) {
     const uint32_t bits = gbits[w];
     if (!bits) continue;
+    if (g_gbits) atomicOr(&g_gbits[w], bits);
     uint4* cells = reinterpret_cast<uint4*>(sle + (w << 5));
 #pragma unroll
     for (int half = 0; half < 2; ++half) {
@@ -203,26 +207,38 @@ __global__ void __launch_bounds__(256) k_merge_routers(uint8_t* __restrict__ dst
   for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n16; x += (uint64_t)gridDim.x * blockDim.x) {
     const uint4 d = dst ? reinterpret_cast<const uint4*>(dst)[x] : make_uint4(0, 0, 0, 0);
     uint32_t w[4] = {d.x, d.y, d.z, d.w};
-    for (int r = 0; r < n_routers; ++r) {
-      uint4* src = reinterpret_cast<uint4*>(rt.state[r]) + x;
-      const uint4 v = *src;
-      const uint32_t o[4] = {v.x, v.y, v.z, v.w};
-      uint32_t keep[4];
-      bool expired = false;
+    constexpr int kLoads = 4;  // routers' vectors in flight
+    for (int r0 = 0; r0 < n_routers; r0 += kLoads) {
+      uint4 v[kLoads];
 #pragma unroll
-      for (int a = 0; a < 4; ++a) {
-        uint32_t out = 0, kp = 0;
+      for (int u = 0; u < kLoads; ++u)
+        if (r0 + u < n_routers) v[u] = reinterpret_cast<const uint4*>(rt.state[r0 + u])[x];
 #pragma unroll
-        for (int b = 0; b < 4; ++b) {
-          const uint32_t s0 = (w[a] >> (8 * b)) & 0xFFu, s1 = (o[a] >> (8 * b)) & 0xFFu;
-          out |= (age_lut[s1] < age_lut[s0] ? s1 : s0) << (8 * b);
-          kp |= (age_lut[s1] < k ? 0xFFu : 0u) << (8 * b);
+      for (int u = 0; u < kLoads; ++u) {
+        if (r0 + u >= n_routers) break;
+        const uint32_t o[4] = {v[u].x, v[u].y, v[u].z, v[u].w};
+        if ((o[0] | o[1] | o[2] | o[3]) == 0) continue;  // nothing set: no merge, no expiry
+        uint32_t keep[4];
+        bool expired = false;
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+          keep[a] = 0;
+          if (o[a] == 0) continue;
+          uint32_t out = 0, kp = 0;
+#pragma unroll
+          for (int b = 0; b < 4; ++b) {
+            const uint32_t s0 = (w[a] >> (8 * b)) & 0xFFu, s1 = (o[a] >> (8 * b)) & 0xFFu;
+            out |= (age_lut[s1] < age_lut[s0] ? s1 : s0) << (8 * b);
+            kp |= (age_lut[s1] < k ? 0xFFu : 0u) << (8 * b);
+          }
+          w[a] = out;
+          keep[a] = kp;
+          expired |= (o[a] & ~kp) != 0;
         }
-        w[a] = out;
-        keep[a] = kp;
-        expired |= (o[a] & ~kp) != 0;
+        if (expired)
+          reinterpret_cast<uint4*>(rt.state[r0 + u])[x] =
+              make_uint4(o[0] & keep[0], o[1] & keep[1], o[2] & keep[2], o[3] & keep[3]);
       }
-      if (expired) *src = make_uint4(o[0] & keep[0], o[1] & keep[1], o[2] & keep[2], o[3] & keep[3]);
     }
     if (dst) reinterpret_cast<uint4*>(dst)[x] = make_uint4(w[0], w[1], w[2], w[3]);
   }

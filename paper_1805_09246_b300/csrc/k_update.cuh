@@ -57,23 +57,30 @@ __device__ __forceinline__ bool rsra_sampled(const KParams& p, uint32_t bip) {
 }
 
 // Algorithm 3's writes for a sampled pair: cell H2(bip) of SRE RSRA[i, RHFG[i](aip)] in every
-// row i, with RHFG[i] from Eq. 6.
+// row i, with RHFG[i] from Eq. 6; into a second RSRA as well when sre2 is set (a batch's
+// global estimator, which so receives the union of its routers' writes).
 template <typename St>
-__device__ __forceinline__ void rsra_write(const KParams& p, uint32_t aip, uint32_t bip, St* sre, St stamp) {
+__device__ __forceinline__ void rsra_write(const KParams& p, uint32_t aip, uint32_t bip, St* sre, St stamp,
+                                           St* sre2 = nullptr) {
   const uint32_t h2 = mas_top(p.key_a[kH2], p.key_b[kH2], bip, 3);
   const uint32_t r0 = rhfg0(p, aip);
   const uint32_t qmask = (1u << p.q) - 1u;
-  sre[((uint64_t)r0 << 3) + h2] = stamp;
+  uint64_t at = ((uint64_t)r0 << 3) + h2;
+  sre[at] = stamp;
+  if (sre2) sre2[at] = stamp;
   for (uint32_t i = 1; i < p.r; ++i) {
     const uint32_t col = (uint32_t)((((uint64_t)aip >> (i * p.delta)) ^ r0) & qmask);
-    sre[((((uint64_t)i << p.q) + col) << 3) + h2] = stamp;
+    at = ((((uint64_t)i << p.q) + col) << 3) + h2;
+    sre[at] = stamp;
+    if (sre2) sre2[at] = stamp;
   }
 }
 
 // Algorithm 3 for one pair.
 template <typename St>
-__device__ __forceinline__ void stamp_rsra(const KParams& p, uint32_t aip, uint32_t bip, St* sre, St stamp) {
-  if (p.sre_on && rsra_sampled(p, bip)) rsra_write(p, aip, bip, sre, stamp);
+__device__ __forceinline__ void stamp_rsra(const KParams& p, uint32_t aip, uint32_t bip, St* sre, St stamp,
+                                           St* sre2 = nullptr) {
+  if (p.sre_on && rsra_sampled(p, bip)) rsra_write(p, aip, bip, sre, stamp, sre2);
 }
 
 // Warp-cooperative Algorithm 3 for the streaming kernels. Only 2^-tau of the pairs are
@@ -90,7 +97,7 @@ struct RsraQueue {
 
   template <typename St>
   __device__ __forceinline__ void push(const KParams& p, bool valid, uint32_t aip, uint32_t bip, St* sre,
-                                       St stamp) {
+                                       St stamp, St* sre2 = nullptr) {
     const bool s = valid && rsra_sampled(p, bip);
     const uint32_t b = __ballot_sync(0xFFFFFFFFu, s);
     if (b == 0) return;
@@ -103,16 +110,16 @@ struct RsraQueue {
       if (lane + 32 < n) q[lane] = q[lane + 32];
       __syncwarp();
       n -= 32;
-      rsra_write(p, e.x, e.y, sre, stamp);
+      rsra_write(p, e.x, e.y, sre, stamp, sre2);
     }
   }
 
   template <typename St>
-  __device__ __forceinline__ void drain(const KParams& p, St* sre, St stamp) {
+  __device__ __forceinline__ void drain(const KParams& p, St* sre, St stamp, St* sre2 = nullptr) {
     __syncwarp();
     if (lane < n) {
       const uint2 e = q[lane];
-      rsra_write(p, e.x, e.y, sre, stamp);
+      rsra_write(p, e.x, e.y, sre, stamp, sre2);
     }
     __syncwarp();
     n = 0;

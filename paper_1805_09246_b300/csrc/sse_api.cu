@@ -1168,20 +1168,22 @@ struct sse_batch {
   RouterTable rt;
   int use_graph = 1;
   int mode = SSE_BATCH_DETECT;
-  cudaGraph_t graph[3] = {};     // one captured step per mode
-  cudaGraphExec_t exec[3] = {};
+  cudaGraph_t graph[6] = {};     // one captured step per (mode, routers expire)
+  cudaGraphExec_t exec[6] = {};
+  bool expire_now = false;       // this step expires the routers' old cells
+  uint32_t since_expire = 0;     // steps since the routers were last expired
   uint32_t* sorted = nullptr;     // global's sorted candidates (fixed per configuration)
-  uint64_t kernels_per_step[3] = {};
+  uint64_t kernels_per_step[6] = {};
   uint64_t launches = 0;
 };
 
 namespace {
 
 using RoutersKernel = void (*)(KParams, TileGeometry, RouterTable, int, uint64_t, const RouterInputs*, uint32_t,
-                               uint32_t*, const uint32_t*);
+                               uint32_t*, const uint32_t*, uint8_t*);
 
 void drop_graphs(sse_batch* b) {
-  for (int m = 0; m < 3; ++m) {
+  for (int m = 0; m < 6; ++m) {
     if (b->exec[m]) cudaGraphExecDestroy(b->exec[m]);
     if (b->graph[m]) cudaGraphDestroy(b->graph[m]);
     b->exec[m] = nullptr;
@@ -1194,7 +1196,10 @@ RoutersKernel routers_kernel(int unroll, bool whole) {
   return unroll == 2 ? k_update_routers<2, false> : unroll == 8 ? k_update_routers<8, false> : k_update_routers<4, false>;
 }
 
-// Update of every router (one persistent launch) and the bitmap apply, on b->stream.
+// Update of every router (one persistent launch) and the bitmap apply, on b->stream. In
+// detect mode the same writes go to the global estimator too (RSRA stamps directly, SLEA
+// through its bitmap), so the global holds the union of the routers' pairs — what merging
+// the routers (Algorithms 2 and 7) gives — without reading every router's state.
 int batch_enqueue_update(sse_batch* b) {
   sse_handle* g = b->global;
   SSE_CUDA(g, cudaMemcpyAsync(b->d_in, b->h_in, sizeof(RouterInputs), cudaMemcpyHostToDevice, b->stream));
@@ -1203,12 +1208,18 @@ int batch_enqueue_update(sse_batch* b) {
   const uint32_t per_tile = std::max<uint32_t>(1u, (uint32_t)g->num_sms / tg.tiles);
   routers_kernel(b->unroll, tg.pieces == 1)<<<tg.tiles * per_tile, kTiledThreads, tg.piece_bytes / 8 + kRsraQueueBytes,
                                                b->stream>>>(
-      g->kp, tg, b->rt, b->n, g->d.sre_bytes, b->d_in, b->item_pairs, b->tile_next, g->clock);
+      g->kp, tg, b->rt, b->n, g->d.sre_bytes, b->d_in, b->item_pairs, b->tile_next, g->clock,
+      b->mode == SSE_BATCH_DETECT ? g->sre : nullptr);
   SSE_LAUNCHED(g);
   const uint64_t words = g->d.sle_bytes / 32;
   const dim3 grid(grid_for(g, words, 256, 2), b->n);
-  k_apply_routers<<<grid, 256, 0, b->stream>>>(b->rt, g->d.sre_bytes, words, g->clock);
+  const bool global = b->mode == SSE_BATCH_DETECT;
+  k_apply_routers<<<grid, 256, 0, b->stream>>>(b->rt, g->d.sre_bytes, words, g->clock, global ? g->sle_bits : nullptr);
   SSE_LAUNCHED(g);
+  if (global) {
+    k_apply_bits<uint8_t><<<grid_for(g, words, 256, 8), 256, 0, b->stream>>>(g->sle_bits, g->sle, words, 0u, g->clock);
+    SSE_LAUNCHED(g);
+  }
   return SSE_OK;
 }
 
@@ -1220,10 +1231,11 @@ int batch_enqueue_step(sse_batch* b) {
   int rc = batch_enqueue_update(b);
   if (rc || b->mode == SSE_BATCH_SCAN) return rc;
   const bool detect = b->mode == SSE_BATCH_DETECT;
-  const uint64_t n16 = (g->d.sre_bytes + g->d.sle_bytes) / 16;
-  k_merge_routers<<<grid_for(g, n16, 256, 8), 256, 0, b->stream>>>(detect ? g->state : nullptr, b->rt, b->n, n16,
-                                                                    g->p.k, g->clock);
-  SSE_LAUNCHED(g);
+  if (b->expire_now) {  // reset the routers' cells that left the window (no merge: see above)
+    const uint64_t n16 = (g->d.sre_bytes + g->d.sle_bytes) / 16;
+    k_merge_routers<<<grid_for(g, n16, 256, 8), 256, 0, b->stream>>>(nullptr, b->rt, b->n, n16, g->p.k, g->clock);
+    SSE_LAUNCHED(g);
+  }
   if (detect) {
     rc = close_enqueue(g, &b->sorted);
     if (rc) return rc;
@@ -1350,6 +1362,7 @@ int sse_batch_set_mode(sse_batch* b, int mode) {
 
 int sse_batch_reset(sse_batch* b) {
   if (!b) return SSE_ERR_INVALID_PARAM;
+  b->since_expire = 0;
   for (int r = 0; r < b->n; ++r) {
     const int rc = sse_reset(b->router[r]);
     if (rc) return rc;
@@ -1381,9 +1394,14 @@ int batch_step(sse_batch* b, const uint32_t* const* d_pairs, const uint64_t* h_c
     b->h_in->pairs[r] = reinterpret_cast<const uint2*>(d_pairs[r]);
     b->h_in->counts[r] = h_counts[r];
   }
+  // A router cell stamped at slice t leaves the window at t + k and would look active again
+  // when its stamp comes round at t + 255; expiring the routers every 254 - k slices clears
+  // every such cell in between (the global estimator expires its own cells at every close).
+  const uint32_t every = g->p.k < 253 ? 254u - g->p.k : 1u;
+  b->expire_now = b->mode != SSE_BATCH_SCAN && b->since_expire + 1 >= every;
   const uint64_t launches0 = g->launches;
   if (b->use_graph) {
-    const int m = b->mode;
+    const int m = b->mode * 2 + (b->expire_now ? 1 : 0);
     if (!b->exec[m]) {
       SSE_CUDA(g, cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
       const int rc = batch_enqueue_step(b);
@@ -1403,10 +1421,10 @@ int batch_step(sse_batch* b, const uint32_t* const* d_pairs, const uint64_t* h_c
   } else {
     const int rc = batch_enqueue_step(b);
     if (rc) return rc;
-    b->kernels_per_step[b->mode] = g->launches - launches0;
+    b->kernels_per_step[b->mode * 2 + (b->expire_now ? 1 : 0)] = g->launches - launches0;
     g->launches = launches0;
   }
-  b->launches += b->kernels_per_step[b->mode];
+  b->launches += b->kernels_per_step[b->mode * 2 + (b->expire_now ? 1 : 0)];
   int status = SSE_OK;
   if (b->mode == SSE_BATCH_DETECT) {
     status = close_collect(g, b->sorted, out);
@@ -1419,6 +1437,7 @@ int batch_step(sse_batch* b, const uint32_t* const* d_pairs, const uint64_t* h_c
     if (b->mode == SSE_BATCH_SCAN) return SSE_OK;  // the slice stays open
   }
   if (status != SSE_OK && status != SSE_ERR_CAPACITY) return status;
+  b->since_expire = b->expire_now ? 0 : b->since_expire + 1;
   for (int r = 0; r < b->n; ++r) b->router[r]->slice += 1;
   g->slice += 1;
   return status;

@@ -113,3 +113,35 @@ def test_batch_rejects_counts_above_capacity_and_handles_empty_routers():
     import ctypes
     counts = np.array([5, 2000, 0], np.uint64)
     assert lib().sse_batch_step(batch._b, ctypes.c_void_p(counts.ctypes.data), None) == S.ERR_CAPACITY
+
+
+def test_batch_router_expiry_across_stamp_cycle():
+    """Over 300 slices (more than one 8-bit stamp cycle) with k = 3: routers expire their old
+    cells every 251 slices, the global estimator receives the routers' writes directly; both
+    keep the oracle's state and reports (routers scanned alone, global = their merge)."""
+    S = sse()
+    p = S.Params(q=10, delta=8, q2=6, eta2=64, delta2=8, k=3, theta=8, seed=34)
+    rng = np.random.default_rng(34)
+    R = 2
+    batch = S.Batch(p, R, 1024)
+    orcs = [oracle.Oracle(oracle_params(p)) for _ in range(R)]
+    og = oracle.Oracle(oracle_params(p))
+    for t in range(300):
+        per_router = []
+        for r in range(R):
+            pairs = rng.integers(0, 2**32, (150, 2), dtype=np.uint64).astype(np.uint32)
+            pairs[:, 0] %= 11
+            per_router.append(pairs)
+        rep = batch.step(inputs=[helpers.to_device(x) for x in per_router])
+        for o, pairs in zip(orcs, per_router):
+            if t:
+                o.advance()
+            o.scan(pairs)
+        if t:
+            og.advance()
+        og.scan(np.concatenate(per_router))
+        if t % 50 == 0 or t >= 295:
+            compare_report(rep, og.detect())
+            compare_state(batch.global_estimator(), og, p, t)
+            for r in range(R):
+                compare_state(batch.router(r), orcs[r], p, t)
