@@ -53,6 +53,8 @@ def parse():
     ap.add_argument("--routers", type=int, default=16)
     ap.add_argument("--edge-q", type=int, default=22, help="RSRA size (log2 SREs per row) for edge_routers")
     ap.add_argument("--update-variant", type=int, default=None, help="fixed update variant (no autotuning)")
+    ap.add_argument("--batch-config", type=int, default=None,
+                    help="fixed batch configuration item*3 + loads (no autotuning), edge_routers")
     ap.add_argument("--no-graph", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
@@ -211,7 +213,11 @@ def main_edge_routers(args, rank, world, local):
     def step_inputs(s):
         return slices[prefill + s % distinct]
 
-    tuned, tune_ms = batch.tune(None, inputs=step_inputs(0))
+    if args.batch_config is None:
+        tuned, tune_ms = batch.tune(None, inputs=step_inputs(0))
+    else:  # fixed configuration (profiler runs, where event timing of the candidates is distorted)
+        tuned, tune_ms = args.batch_config, []
+        batch.configure([1 << 18, 1 << 20, 1 << 22][tuned // 3], [2, 4, 8][tuned % 3])
     for w in range(args.warmup):
         batch.step(inputs=step_inputs(w))
     pairs_per_step = [sum(x.numel() // 2 for x in step_inputs(args.warmup + s)) for s in range(args.steps)]

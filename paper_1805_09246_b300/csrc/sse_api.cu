@@ -810,15 +810,25 @@ int close_collect(sse_handle* h, const uint32_t* sorted, sse_report* out) {
 // the device clock), the copy of the counters and of the first report_stage_n report
 // entries into pinned memory, and the clock tick. One launch and one synchronisation per
 // slice; reports longer than report_stage_n are completed with direct copies.
+// The page-locked, device-mapped report stage written by k_report (allocated once).
+int ensure_report_stage(sse_handle* h) {
+  if (h->report_stage) return SSE_OK;
+  h->report_stage_n = std::min<uint32_t>(h->cand_cap, 8192u);
+  SSE_CUDA(h, cudaHostAlloc(&h->report_stage, sizeof(CloseScratch) + (size_t)h->report_stage_n * 9,
+                            cudaHostAllocMapped));
+  SSE_CUDA(h, cudaHostGetDevicePointer(reinterpret_cast<void**>(&h->report_stage_dev), h->report_stage, 0));
+  return SSE_OK;
+}
+
+// Report of a finished close from the stage (and, beyond report_stage_n entries, from the
+// device buffers): counters into the statistics, entries into out.
+int collect_staged(sse_handle* h, const uint32_t* sorted, uint64_t slice, sse_report* out);
+
 int close_graph_launch(sse_handle* h) {
   if (!h->close_exec) {
     if (!h->capture_stream) SSE_CUDA(h, cudaStreamCreateWithFlags(&h->capture_stream, cudaStreamNonBlocking));
-    if (!h->report_stage) {
-      h->report_stage_n = std::min<uint32_t>(h->cand_cap, 8192u);
-      SSE_CUDA(h, cudaHostAlloc(&h->report_stage, sizeof(CloseScratch) + (size_t)h->report_stage_n * 9,
-                                cudaHostAllocMapped));
-      SSE_CUDA(h, cudaHostGetDevicePointer(reinterpret_cast<void**>(&h->report_stage_dev), h->report_stage, 0));
-    }
+    const int rc_stage = ensure_report_stage(h);
+    if (rc_stage) return rc_stage;
     const cudaStream_t user = h->stream;
     const uint64_t launches0 = h->launches;
     h->stream = h->capture_stream;
@@ -863,12 +873,16 @@ int close_graph_launch(sse_handle* h) {
 int close_graph_collect(sse_handle* h, sse_report* out) {
   h->close_pending = 0;
   SSE_CUDA(h, cudaEventSynchronize(h->close_done));
+  return collect_staged(h, h->close_sorted, h->close_pending_slice, out);
+}
+
+int collect_staged(sse_handle* h, const uint32_t* sorted, uint64_t slice, sse_report* out) {
   CloseScratch hs;
   memcpy(&hs, h->report_stage, sizeof(hs));  // written by k_report before the synchronisation
   const uint32_t n_found = hs.n_cand;
   const uint32_t n_kept = std::min(n_found, h->cand_cap);
   int status = n_found > h->cand_cap ? SSE_ERR_CAPACITY : SSE_OK;
-  h->stats.slice = h->close_pending_slice;
+  h->stats.slice = slice;
   for (int i = 0; i < kMaxRows; ++i) {
     h->stats.hot[i] = i < (int)h->p.r ? hs.hot[i] : 0;
     h->stats.active2[i] = i < (int)h->p.r2 ? hs.active2[i] : 0;
@@ -877,7 +891,7 @@ int close_graph_collect(sse_handle* h, sse_report* out) {
   h->stats.n_candidates = n_found;
   h->stats.n_super = hs.n_super;
   if (out) {
-    out->slice = h->close_pending_slice;
+    out->slice = slice;
     out->n_candidates = n_found;
     out->n_super = hs.n_super;
     const uint32_t n_copy = std::min(n_kept, out->cap);
@@ -892,8 +906,8 @@ int close_graph_collect(sse_handle* h, sse_report* out) {
     if (n_copy > staged) {  // the rest, straight from the device
       const uint32_t m = n_copy - staged;
       if (out->hosts)
-        SSE_CUDA(h, cudaMemcpyAsync(out->hosts + staged, h->close_sorted + staged, (size_t)m * 4,
-                                    cudaMemcpyDeviceToHost, h->stream));
+        SSE_CUDA(h, cudaMemcpyAsync(out->hosts + staged, sorted + staged, (size_t)m * 4, cudaMemcpyDeviceToHost,
+                                    h->stream));
       if (out->est)
         SSE_CUDA(h, cudaMemcpyAsync(out->est + staged, h->est + staged, (size_t)m * 4, cudaMemcpyDeviceToHost,
                                     h->stream));
@@ -1237,8 +1251,11 @@ int batch_enqueue_step(sse_batch* b) {
     SSE_LAUNCHED(g);
   }
   if (detect) {
-    rc = close_enqueue(g, &b->sorted);
+    rc = close_enqueue(g, &b->sorted, false);
     if (rc) return rc;
+    k_report<<<8, 256, 0, b->stream>>>(g->scratch, b->sorted, g->est, g->flags, g->cand_cap, g->report_stage_n,
+                                       g->report_stage_dev);
+    SSE_LAUNCHED(g);
   }
   ClockList cl;
   for (int r = 0; r < b->n; ++r) cl.c[r] = b->router[r]->clock;
@@ -1315,6 +1332,11 @@ int sse_batch_create(const sse_params* p, int n_routers, uint64_t capacity_pairs
     b->rt.gbits[r] = b->router[r]->sle_bits;
   }
   memset(b->h_in, 0, sizeof(RouterInputs));
+  rc = ensure_report_stage(b->global);  // the step's report kernel writes here
+  if (rc != SSE_OK) {
+    sse_batch_destroy(b);
+    return rc;
+  }
   *out = b;
   return SSE_OK;
 }
@@ -1427,7 +1449,8 @@ int batch_step(sse_batch* b, const uint32_t* const* d_pairs, const uint64_t* h_c
   b->launches += b->kernels_per_step[b->mode * 2 + (b->expire_now ? 1 : 0)];
   int status = SSE_OK;
   if (b->mode == SSE_BATCH_DETECT) {
-    status = close_collect(g, b->sorted, out);
+    SSE_CUDA(g, cudaStreamSynchronize(b->stream));
+    status = collect_staged(g, b->sorted, g->slice, out);
   } else {
     SSE_CUDA(g, cudaStreamSynchronize(b->stream));
     if (out) {

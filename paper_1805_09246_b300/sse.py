@@ -536,9 +536,10 @@ class Batch:
             _torch().cuda.current_stream().synchronize()  # producers finish before the batch stream reads
         c = np.ascontiguousarray(counts, dtype=np.uint64)
         cap = self.params.max_candidates if cap is None else cap
-        hosts = np.zeros(cap, np.uint32)
-        est = np.zeros(cap, np.float32)
-        flags = np.zeros(cap, np.uint8)
+        bufs = getattr(self, "_report_bufs", None)
+        if bufs is None or len(bufs[0]) != cap:  # reused across steps
+            bufs = self._report_bufs = (np.empty(cap, np.uint32), np.empty(cap, np.float32), np.empty(cap, np.uint8))
+        hosts, est, flags = bufs
         rep = _Report(0, 0, 0, cap, 0, hosts.ctypes.data, est.ctypes.data, flags.ctypes.data)
         if inputs is not None:
             rc = self._lib.sse_batch_step_from(self._b, self._ptrs(inputs), ctypes.c_void_p(c.ctypes.data),
