@@ -448,6 +448,8 @@ def main():
     est = sse.Estimator(params, stream=stream)
     if args.mode:
         est.set_update_mode(args.mode)
+    if args.no_graph:  # the close's kernels launched one by one (per-kernel profiles)
+        est.close_use_graph(False)
 
     # inputs: PREFILL slices for the window, then DISTINCT slices the steps cycle through
     prefill, distinct = args.prefill, max(1, args.distinct)
@@ -492,13 +494,17 @@ def main():
     est.update(step_input(args.warmup))
     upd_ev[0][1].record(stream)
     for s in range(args.steps):
-        est.close_slice_async()
+        if args.no_graph:  # kernels launched one by one: the close is synchronous
+            rep = est.close_slice()
+        else:
+            est.close_slice_async()
         if s + 1 < args.steps:
             a, b = upd_ev[s + 1]
             a.record(stream)
             est.update(step_input(args.warmup + s + 1))
             b.record(stream)
-        rep = est.close_slice_wait()
+        if not args.no_graph:
+            rep = est.close_slice_wait()
         n_super += rep.n_super
         n_cand += rep.n_candidates
     ev_end.record(stream)

@@ -17,38 +17,26 @@ namespace sse {
 constexpr int kCloseThreads = 256;
 constexpr uint32_t kSleBytesPerBlock = kCloseThreads * 16;  // == kPitchAlign
 
-// act[s] = 1 when stamp s is active at current stamp cs for window k.
-__device__ __forceinline__ void build_active_lut(uint8_t* act, uint32_t cs, uint32_t k) {
-  for (uint32_t s = threadIdx.x; s < 256; s += blockDim.x) act[s] = stamp_age(s, cs) < k ? 1 : 0;
-}
-
-// Activity of one cell: set and younger than the window. 8-bit stamps use the 256-entry
-// table act[] built per block; 16-bit stamps compute the cyclic age (mod 65535).
-template <typename St>
-__device__ __forceinline__ uint32_t cell_active(uint32_t s, const uint8_t* act, uint32_t cs, uint32_t k) {
-  if constexpr (sizeof(St) == 1) {
-    return act[s];
-  } else {
-    const uint32_t age = cs >= s ? cs - s : cs + 65535u - s;
-    return (s != 0 && age < k) ? 1u : 0u;
-  }
+// Activity of one 16-bit cell: set and younger than the window (cyclic age mod 65535).
+__device__ __forceinline__ uint32_t cell_active16(uint32_t s, uint32_t cs, uint32_t k) {
+  const uint32_t age = cs >= s ? cs - s : cs + 65535u - s;
+  return (s != 0 && age < k) ? 1u : 0u;
 }
 
 // One 32-bit word of cells: adds its active cells to `count` and returns the mask that
-// keeps them (all ones over active cells, zero over the rest).
+// keeps them (all ones over active cells, zero over the rest). 8-bit cells are tested four
+// at a time (active_hi8); 16-bit cells one by one.
 template <typename St>
-__device__ __forceinline__ uint32_t word_keep(uint32_t w, const uint8_t* act, uint32_t cs, uint32_t k,
-                                              uint32_t& count) {
-  constexpr int kBits = 8 * sizeof(St);
-  constexpr uint32_t kMask = sizeof(St) == 1 ? 0xFFu : 0xFFFFu;
-  uint32_t keep = 0;
-#pragma unroll
-  for (int b = 0; b < 32 / kBits; ++b) {
-    const uint32_t a = cell_active<St>((w >> (kBits * b)) & kMask, act, cs, k);
-    count += a;
-    keep |= (a ? kMask : 0u) << (kBits * b);
+__device__ __forceinline__ uint32_t word_keep(uint32_t w, Window8 win, uint32_t cs, uint32_t k, uint32_t& count) {
+  if constexpr (sizeof(St) == 1) {
+    const uint32_t a = active_hi8(w, win);
+    count += __popc(a);
+    return (a >> 7) * 0xFFu;
+  } else {
+    const uint32_t a0 = cell_active16(w & 0xFFFFu, cs, k), a1 = cell_active16(w >> 16, cs, k);
+    count += a0 + a1;
+    return (a0 ? 0xFFFFu : 0u) | (a1 ? 0xFFFF0000u : 0u);
   }
-  return keep;
 }
 
 // mode bit 0: write back expired cells; bit 1: write the hot bitmap. do_sre != 0: the
@@ -64,9 +52,8 @@ __global__ void __launch_bounds__(kCloseThreads) k_close(const __grid_constant__
   using SreWord = typename std::conditional<sizeof(St) == 1, uint2, uint4>::type;
   constexpr int kSreInts = sizeof(SreWord) / 4;
   const uint32_t cs = clock ? *clock : cs_value;
-  __shared__ uint8_t act[256];
+  const Window8 win = window8(cs, p.k);  // used by 8-bit cells only
   __shared__ uint32_t row_sum[kMaxRows];
-  if (sizeof(St) == 1) build_active_lut(act, cs, p.k);
   if (threadIdx.x < kMaxRows) row_sum[threadIdx.x] = 0;
   __syncthreads();
   const bool expire = (mode & 1u) != 0;
@@ -93,7 +80,7 @@ __global__ void __launch_bounds__(kCloseThreads) k_close(const __grid_constant__
         memcpy(x, &v[u], sizeof(SreWord));
 #pragma unroll
         for (int i = 0; i < kSreInts; ++i) {
-          keep[i] = word_keep<St>(x[i], act, cs, p.k, weight);
+          keep[i] = word_keep<St>(x[i], win, cs, p.k, weight);
           expired |= x[i] & ~keep[i];
         }
         const unsigned ballot = __ballot_sync(0xFFFFFFFFu, weight >= p.hot_min);
@@ -121,7 +108,7 @@ __global__ void __launch_bounds__(kCloseThreads) k_close(const __grid_constant__
       uint32_t keep[4], expired = 0;
 #pragma unroll
       for (int i = 0; i < 4; ++i) {
-        keep[i] = word_keep<St>(w[i], act, cs, p.k, count);
+        keep[i] = word_keep<St>(w[i], win, cs, p.k, count);
         expired |= w[i] & ~keep[i];
       }
       if (expire && expired) *cell = make_uint4(w[0] & keep[0], w[1] & keep[1], w[2] & keep[2], w[3] & keep[3]);
@@ -135,44 +122,59 @@ __global__ void __launch_bounds__(kCloseThreads) k_close(const __grid_constant__
 }
 
 // Hot lists HSE(0) and HSE(1) (column indices, any order) and |HSE(i)| for every row.
-// One thread per bitmap word; warp-aggregated appends.
-__global__ void __launch_bounds__(256) k_hot_lists(const uint32_t* __restrict__ hot_bits, uint32_t r, uint32_t q,
-                                                   uint32_t* __restrict__ hot_count, uint32_t* __restrict__ list0,
-                                                   uint32_t* __restrict__ list1, uint32_t* __restrict__ n_list) {
+// One thread per bitmap word; appends are aggregated per block (warp prefix sums, then one
+// atomicAdd per block, iteration and list). Run by blocks blk = 0..nblk-1 of a launch (the
+// whole block takes the same role; blockDim.x is a multiple of 32, at most 1024).
+__device__ __forceinline__ void hot_lists_part(const uint32_t* __restrict__ hot_bits, uint32_t r, uint32_t q,
+                                               uint32_t* __restrict__ hot_count, uint32_t* __restrict__ list0,
+                                               uint32_t* __restrict__ list1, uint32_t* __restrict__ n_list,
+                                               uint32_t blk, uint32_t nblk) {
   __shared__ uint32_t row_sum[kMaxRows];
+  __shared__ uint32_t warp_off[2][32];  // per list: this iteration's warp totals, then offsets
+  __shared__ uint32_t block_at[2];      // per list: the block's first entry this iteration
   if (threadIdx.x < kMaxRows) row_sum[threadIdx.x] = 0;
   __syncthreads();
   const uint32_t words_per_row = 1u << (q - 5);
   const uint64_t total = (uint64_t)r * words_per_row;
-  const uint32_t lane = threadIdx.x & 31;
-  for (uint64_t base = (uint64_t)blockIdx.x * blockDim.x; base < total; base += (uint64_t)gridDim.x * blockDim.x) {
+  const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5, n_warps = blockDim.x >> 5;
+  for (uint64_t base = (uint64_t)blk * blockDim.x; base < total; base += (uint64_t)nblk * blockDim.x) {
     const uint64_t wi = base + threadIdx.x;
     const uint32_t word = wi < total ? hot_bits[wi] : 0u;
     const uint32_t row = wi < total ? (uint32_t)(wi >> (q - 5)) : 0u;
     const uint32_t bits = __popc(word);
     if (bits) atomicAdd(&row_sum[row], bits);
-    // rows 0 and 1: append the column of every hot SRE
+    // rows 0 and 1: the column of every hot SRE goes to that row's list
+    uint32_t incl[2];
+#pragma unroll
     for (uint32_t rr = 0; rr < 2; ++rr) {
-      const uint32_t mine = (row == rr) ? bits : 0u;
-      uint32_t incl = mine;
+      incl[rr] = (row == rr) ? bits : 0u;
 #pragma unroll
       for (int off = 1; off < 32; off <<= 1) {
-        const uint32_t t = __shfl_up_sync(0xFFFFFFFFu, incl, off);
-        if (lane >= (uint32_t)off) incl += t;
+        const uint32_t t = __shfl_up_sync(0xFFFFFFFFu, incl[rr], off);
+        if (lane >= (uint32_t)off) incl[rr] += t;
       }
-      const uint32_t warp_total = __shfl_sync(0xFFFFFFFFu, incl, 31);
-      uint32_t start = 0;
-      if (lane == 31 && warp_total) start = atomicAdd(&n_list[rr], warp_total);
-      start = __shfl_sync(0xFFFFFFFFu, start, 31);
-      if (mine) {
-        uint32_t* list = rr == 0 ? list0 : list1;
-        uint32_t at = start + incl - mine;
-        const uint32_t col0 = (uint32_t)(wi & (words_per_row - 1)) << 5;
-        for (uint32_t m = word; m; m &= m - 1) list[at++] = col0 + (__ffs(m) - 1);
-      }
+      if (lane == 31) warp_off[rr][warp] = incl[rr];
     }
+    __syncthreads();
+    if (threadIdx.x < 2) {
+      const uint32_t rr = threadIdx.x;
+      uint32_t run = 0;
+      for (uint32_t w = 0; w < n_warps; ++w) {
+        const uint32_t t = warp_off[rr][w];
+        warp_off[rr][w] = run;
+        run += t;
+      }
+      block_at[rr] = run ? atomicAdd(&n_list[rr], run) : 0u;
+    }
+    __syncthreads();
+    if (row < 2 && bits) {
+      uint32_t* list = row == 0 ? list0 : list1;
+      uint32_t at = block_at[row] + warp_off[row][warp] + incl[row] - bits;
+      const uint32_t col0 = (uint32_t)(wi & (words_per_row - 1)) << 5;
+      for (uint32_t m = word; m; m &= m - 1) list[at++] = col0 + (__ffs(m) - 1);
+    }
+    __syncthreads();  // warp_off and block_at are rewritten by the next iteration
   }
-  __syncthreads();
   if (threadIdx.x < r && row_sum[threadIdx.x]) atomicAdd(&hot_count[threadIdx.x], row_sum[threadIdx.x]);
 }
 

@@ -15,6 +15,7 @@
 // round-to-nearest operations in a fixed order, so the super point decision is exact.
 #pragma once
 
+#include "k_close.cuh"
 #include "sse_internal.cuh"
 
 namespace sse {
@@ -87,22 +88,72 @@ __device__ __noinline__ void grow_deep(const KParams& p, const uint32_t* hot_bit
 // Hot bitmaps of rows 2..r-1 regrouped for the join: bit (c << delta) + t of table i-2 is
 // the hot flag of SRE c | (t << (q - delta)) of row i, so the 2^delta SREs that share their
 // low q-delta bits c (the part of B(i) fixed by B(i-1)) are adjacent bits.
-// One thread per output word; blockIdx.y = row - 2.
-__global__ void __launch_bounds__(256) k_row_regroup(const uint32_t* __restrict__ hot_bits, uint32_t q,
-                                                     uint32_t delta, uint32_t* __restrict__ tables) {
-  const uint32_t row = blockIdx.y + 2;
+// One thread per output word (rows flattened); blocks blk = 0..nblk-1 of a launch.
+// With delta <= 5 and q - delta >= 5, output word w = j * 2^delta + m holds c = 32j +
+// m * (32 >> delta) + b for b < 32 >> delta, and every t: bits m * (32 >> delta) + b of the
+// 2^delta input words j + t * 2^(q-delta-5), one load per t. Otherwise bit by bit.
+__device__ __forceinline__ void regroup_part(const uint32_t* __restrict__ hot_bits, uint32_t r, uint32_t q,
+                                             uint32_t delta, uint32_t* __restrict__ tables, uint32_t blk,
+                                             uint32_t nblk) {
   const uint64_t nwords = (1ull << q) >> 5;
-  uint32_t* out_row = tables + (uint64_t)blockIdx.y * nwords;
+  const uint64_t total = (uint64_t)(r - 2) * nwords;
   const uint32_t tmask = (1u << delta) - 1u;
-  for (uint64_t w = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; w < nwords; w += (uint64_t)gridDim.x * blockDim.x) {
+  const bool fast = delta <= 5 && q - delta >= 5;
+  for (uint64_t x = (uint64_t)blk * blockDim.x + threadIdx.x; x < total; x += (uint64_t)nblk * blockDim.x) {
+    const uint32_t row = 2 + (uint32_t)(x / nwords);
+    const uint64_t w = x % nwords;
+    const uint32_t* src = hot_bits + ((uint64_t)row << (q - 5));
     uint32_t out = 0;
-    for (uint32_t b = 0; b < 32; ++b) {
-      const uint64_t bit = (w << 5) + b;
-      const uint32_t c = (uint32_t)(bit >> delta), t = (uint32_t)bit & tmask;
-      out |= (hot_bit(hot_bits, q, row, c | (t << (q - delta))) ? 1u : 0u) << b;
+    if (fast) {
+      const uint32_t per = 32u >> delta;  // c values per output word
+      const uint64_t j = w >> delta;
+      const uint32_t m = (uint32_t)w & tmask;
+      const uint64_t tstride = 1ull << (q - delta - 5);
+      for (uint32_t t = 0; t <= tmask; ++t) {
+        const uint32_t v = src[j + t * tstride] >> (m * per);
+        for (uint32_t b = 0; b < per; ++b) out |= ((v >> b) & 1u) << ((b << delta) + t);
+      }
+    } else {
+      for (uint32_t b = 0; b < 32; ++b) {
+        const uint64_t bit = (w << 5) + b;
+        const uint32_t c = (uint32_t)(bit >> delta), t = (uint32_t)bit & tmask;
+        out |= (hot_bit(hot_bits, q, row, c | (t << (q - delta))) ? 1u : 0u) << b;
+      }
     }
-    out_row[w] = out;
+    tables[x] = out;
   }
+}
+
+// "Any hot" bitmap of row 3 (delta <= 5, q - delta >= 5): bit c is set when some of the
+// 2^delta SREs c | (t << (q - delta)) is hot, i.e. the OR over t of the row's bitmap words
+// j + t * 2^(q-delta-5) for the 32 c of output word j. Blocks blk = 0..nblk-1 of a launch.
+__device__ __forceinline__ void any_part(const uint32_t* __restrict__ hot_bits, uint32_t q, uint32_t delta,
+                                         uint32_t* __restrict__ any, uint32_t blk, uint32_t nblk) {
+  const uint32_t n_words = (1u << (q - delta)) >> 5;
+  const uint32_t* src = hot_bits + (3ull << (q - 5));
+  const uint32_t tstride = 1u << (q - delta - 5);
+  for (uint32_t j = blk * blockDim.x + threadIdx.x; j < n_words; j += nblk * blockDim.x) {
+    uint32_t out = 0;
+    for (uint32_t t = 0; t < (1u << delta); ++t) out |= src[j + t * tstride];
+    any[j] = out;
+  }
+}
+
+// Everything the join reads from the hot bitmap, in one launch: blocks [0, n_lists) build
+// the hot lists of rows 0-1 and the hot counts, the next n_regroup blocks the regrouped
+// tables of rows 2..r-1, the remaining blocks (when any != NULL) row 3's any-hot bitmap.
+__global__ void __launch_bounds__(256) k_hot_prep(const uint32_t* __restrict__ hot_bits, uint32_t r, uint32_t q,
+                                                  uint32_t delta, uint32_t* __restrict__ hot_count,
+                                                  uint32_t* __restrict__ list0, uint32_t* __restrict__ list1,
+                                                  uint32_t* __restrict__ n_list, uint32_t* __restrict__ tables,
+                                                  uint32_t* __restrict__ any, uint32_t n_lists, uint32_t n_regroup) {
+  const uint32_t b = blockIdx.x;
+  if (b < n_lists)
+    hot_lists_part(hot_bits, r, q, hot_count, list0, list1, n_list, b, n_lists);
+  else if (b < n_lists + n_regroup)
+    regroup_part(hot_bits, r, q, delta, tables, b - n_lists, n_regroup);
+  else if (any)
+    any_part(hot_bits, q, delta, any, b - n_lists - n_regroup, gridDim.x - n_lists - n_regroup);
 }
 
 // The 2^delta (<= 32) hot flags, indexed by the top delta bits of he_i, of the row whose
@@ -147,18 +198,6 @@ __device__ __noinline__ void grow_grouped(const KParams& p, const uint32_t* tabl
 }
 
 constexpr int kJoinThreads = 1024;
-
-// "Any hot" bitmap of a regrouped table: bit c is set when some of the 2^delta (<= 32) SREs
-// with low bits c is hot, i.e. when hot_group(table, c) != 0. One thread per output word.
-__global__ void __launch_bounds__(256) k_row_any(const uint32_t* __restrict__ table, uint32_t q, uint32_t delta,
-                                                 uint32_t* __restrict__ any) {
-  const uint32_t n_words = (1u << (q - delta)) >> 5;
-  for (uint32_t w = blockIdx.x * blockDim.x + threadIdx.x; w < n_words; w += gridDim.x * blockDim.x) {
-    uint32_t out = 0;
-    for (uint32_t b = 0; b < 32; ++b) out |= (hot_group(table, (w << 5) + b, delta) != 0 ? 1u : 0u) << b;
-    any[w] = out;
-  }
-}
 
 // Blocks stride over HSE(0), threads over HSE(1). For a pair (he_0, he_1), B(1) fixes the
 // low q-delta bits c of every admissible he_2 (he_2 = he_0 XOR B(2)); the regrouped row-2
@@ -240,11 +279,15 @@ __global__ void __launch_bounds__(kJoinThreads) k_join(const __grid_constant__ K
 // The close's report written straight into page-locked, device-mapped host memory (one
 // kernel instead of copy-engine transfers): the counters, then the first min(n_cand, cap,
 // n_stage) hosts, estimates and flags. Layout: CloseScratch | hosts[n_stage] |
-// est[n_stage] | flags[n_stage].
+// est[n_stage] | flags[n_stage]. When tick_clock is set, the last step of the close — the
+// clock moving to the next slice's stamp (1..tick_mod) — is done here too (nothing in this
+// kernel reads the clock).
 __global__ void __launch_bounds__(256) k_report(const CloseScratch* __restrict__ sc,
                                                 const uint32_t* __restrict__ hosts, const float* __restrict__ est,
                                                 const uint8_t* __restrict__ flags, uint32_t cap, uint32_t n_stage,
-                                                uint8_t* __restrict__ out) {
+                                                uint8_t* __restrict__ out, uint32_t* __restrict__ tick_clock,
+                                                uint32_t tick_mod) {
+  if (tick_clock && blockIdx.x == 0 && threadIdx.x == 0) *tick_clock = *tick_clock % tick_mod + 1u;
   const uint32_t n = min(min(sc->n_cand, cap), n_stage);
   const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x, stride = gridDim.x * blockDim.x;
   constexpr uint32_t kWords = sizeof(CloseScratch) / 4;
@@ -412,112 +455,136 @@ __global__ void __launch_bounds__(kJoinTiledThreads) k_join_tiled(
 }
 
 // ---------------------------------------------------------------- ordering
-// Ascending order of up to kSortChunk distinct keys (the usual report): each key is placed
-// at its rank, the number of smaller keys (ties, which a candidate set does not have, are
-// broken by index). kRankSplit neighbouring threads count one key's rank over interleaved
-// parts of the keys and add their counts with shuffles. Blocks split the keys; every block
-// reads them all into shared memory. Larger counts are left to k_sort_chunks and
-// k_merge_runs.
-constexpr int kRankThreads = 256;
+// The report lists the candidates in ascending order. One cooperative launch of kSortBlocks
+// blocks (all resident at once) sorts them:
+// * up to kSortChunk keys (the usual report): each key is placed at its rank, the number of
+//   smaller keys (ties, which a candidate set does not have, are broken by index); every
+//   block reads all keys into shared memory and kRankSplit neighbouring threads count one
+//   key's rank over interleaved parts of the keys, adding their counts with shuffles;
+// * more: every kSortChunk-key chunk is sorted in shared memory (bitonic network, tail
+//   padded with 0xFFFFFFFF, which sorts last), then sorted runs are merged pairwise (each key
+//   placed by a binary search in the partner run), pass after pass, with a grid-wide
+//   barrier between passes; the last pass writes `out`.
+constexpr int kSortThreads = 256;
 constexpr uint32_t kRankSplit = 8;
-__global__ void __launch_bounds__(kRankThreads) k_rank_sort(const uint32_t* __restrict__ keys,
-                                                            const uint32_t* __restrict__ n_ptr, uint32_t cap,
-                                                            uint32_t* __restrict__ out) {
-  __shared__ uint32_t s[kSortChunk];
-  const uint32_t n = min(*n_ptr, cap);
-  const uint32_t per_block = kRankThreads / kRankSplit;
-  if (n > kSortChunk || blockIdx.x * per_block >= n) return;
-  for (uint32_t x = threadIdx.x; x < n; x += blockDim.x) s[x] = keys[x];
+constexpr uint32_t kSortBlocks = kSortChunk / (kSortThreads / kRankSplit);  // 128
+constexpr uint32_t kBarrierSpins = 1u << 22;  // polls (64 ns apart) before a barrier gives up
+
+// Grid-wide barrier of a cooperative launch. bar[0] counts arrivals, bar[1] is the
+// generation; both are zero before the launch (the close's scratch is cleared). A wait that
+// outlasts kBarrierSpins polls sets *error and returns false; the caller then returns.
+__device__ __forceinline__ bool grid_barrier(uint32_t* bar, uint32_t* error) {
+  __shared__ uint32_t ok;
   __syncthreads();
-  const uint32_t i = blockIdx.x * per_block + threadIdx.x / kRankSplit;
-  const uint32_t part = threadIdx.x % kRankSplit;
-  const uint32_t v = i < n ? s[i] : 0u;
-  uint32_t rank = 0;
-  if (i < n)
-    for (uint32_t y = part; y < n; y += kRankSplit) rank += (s[y] < v || (s[y] == v && y < i)) ? 1u : 0u;
-#pragma unroll
-  for (uint32_t o = kRankSplit / 2; o > 0; o >>= 1) rank += __shfl_xor_sync(0xFFFFFFFFu, rank, o);
-  if (i < n && part == 0) out[rank] = v;
+  if (threadIdx.x == 0) {
+    volatile uint32_t* gen = bar + 1;
+    const uint32_t g = *gen;  // this barrier's generation: it cannot move before we arrive
+    ok = 1u;
+    __threadfence();
+    if (atomicAdd(bar, 1u) == gridDim.x - 1) {
+      atomicExch(bar, 0u);
+      __threadfence();
+      atomicAdd(bar + 1, 1u);
+    } else {
+      uint32_t spins = 0;
+      while (*gen == g) {
+        if (++spins > kBarrierSpins) {
+          atomicOr(error, 1u);
+          ok = 0u;
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  return ok != 0u;
 }
 
-// Sort of each kSortChunk-element chunk in shared memory, when there are more than
-// kSortChunk keys (fewer are sorted by k_rank_sort). Up to 1024 keys: rank sort (each
-// key's position is the number of keys before it in sorted order; ties by index). Larger
-// chunks: bitonic sort with the tail padded with 0xFFFFFFFF (which sorts last, so the first
-// entries are the real ones).
-__global__ void __launch_bounds__(1024) k_sort_chunks(uint32_t* __restrict__ keys, const uint32_t* __restrict__ n_ptr,
-                                                      uint32_t cap) {
+// keys: the n = min(*n_ptr, cap) unsorted candidates (reordered in place when n > kSortChunk);
+// alt: a second buffer of cap entries; out: the sorted candidates. bar: two zeroed words.
+__global__ void __launch_bounds__(kSortThreads) k_sort_candidates(uint32_t* __restrict__ keys,
+                                                                  uint32_t* __restrict__ alt,
+                                                                  uint32_t* __restrict__ out,
+                                                                  const uint32_t* __restrict__ n_ptr, uint32_t cap,
+                                                                  uint32_t* __restrict__ bar,
+                                                                  uint32_t* __restrict__ error) {
   __shared__ uint32_t s[kSortChunk];
   const uint32_t n = min(*n_ptr, cap);
-  if (n <= kSortChunk) return;
-  const uint32_t start = blockIdx.x * kSortChunk;
-  if (start >= n) return;
-  const uint32_t m = min(n - start, (uint32_t)kSortChunk);
-  if (m <= 1024) {
-    for (uint32_t x = threadIdx.x; x < m; x += blockDim.x) s[x] = keys[start + x];
+  if (n <= kSortChunk) {
+    const uint32_t per_block = kSortThreads / kRankSplit;
+    if (blockIdx.x * per_block >= n) return;
+    for (uint32_t x = threadIdx.x; x < n; x += blockDim.x) s[x] = keys[x];
     __syncthreads();
-    for (uint32_t x = threadIdx.x; x < m; x += blockDim.x) {
-      const uint32_t v = s[x];
-      uint32_t rank = 0;
-      for (uint32_t y = 0; y < m; ++y) {
-        const uint32_t u = s[y];
-        rank += (u < v || (u == v && y < x)) ? 1u : 0u;
-      }
-      keys[start + rank] = v;
-    }
+    const uint32_t i = blockIdx.x * per_block + threadIdx.x / kRankSplit;
+    const uint32_t part = threadIdx.x % kRankSplit;
+    const uint32_t v = i < n ? s[i] : 0u;
+    uint32_t rank = 0;
+    if (i < n)
+      for (uint32_t y = part; y < n; y += kRankSplit) rank += (s[y] < v || (s[y] == v && y < i)) ? 1u : 0u;
+#pragma unroll
+    for (uint32_t o = kRankSplit / 2; o > 0; o >>= 1) rank += __shfl_xor_sync(0xFFFFFFFFu, rank, o);
+    if (i < n && part == 0) out[rank] = v;
     return;
   }
-  for (uint32_t x = threadIdx.x; x < kSortChunk; x += blockDim.x) s[x] = (x < m) ? keys[start + x] : 0xFFFFFFFFu;
-  __syncthreads();
-  for (uint32_t size = 2; size <= kSortChunk; size <<= 1) {
-    for (uint32_t stride = size >> 1; stride > 0; stride >>= 1) {
-      for (uint32_t x = threadIdx.x; x < kSortChunk / 2; x += blockDim.x) {
-        const uint32_t lo = 2 * x - (x & (stride - 1));
-        const uint32_t hi = lo + stride;
-        const bool up = (lo & size) == 0;
-        const uint32_t a = s[lo], b = s[hi];
-        if ((a > b) == up) {
-          s[lo] = b;
-          s[hi] = a;
+  // chunk sorts (keys written back in place)
+  const uint32_t chunks = (n + kSortChunk - 1) / kSortChunk;
+  for (uint32_t c = blockIdx.x; c < chunks; c += gridDim.x) {
+    const uint32_t start = c * kSortChunk;
+    const uint32_t m = min(n - start, (uint32_t)kSortChunk);
+    for (uint32_t x = threadIdx.x; x < kSortChunk; x += blockDim.x) s[x] = x < m ? __ldcg(keys + start + x) : 0xFFFFFFFFu;
+    __syncthreads();
+    for (uint32_t size = 2; size <= kSortChunk; size <<= 1) {
+      for (uint32_t stride = size >> 1; stride > 0; stride >>= 1) {
+        for (uint32_t x = threadIdx.x; x < kSortChunk / 2; x += blockDim.x) {
+          const uint32_t lo = 2 * x - (x & (stride - 1));
+          const uint32_t hi = lo + stride;
+          const bool up = (lo & size) == 0;
+          const uint32_t a = s[lo], b = s[hi];
+          if ((a > b) == up) {
+            s[lo] = b;
+            s[hi] = a;
+          }
         }
+        __syncthreads();
       }
-      __syncthreads();
     }
+    for (uint32_t x = threadIdx.x; x < m; x += blockDim.x) keys[start + x] = s[x];
+    __syncthreads();  // s is refilled by the next chunk
   }
-  for (uint32_t x = threadIdx.x; x < m; x += blockDim.x) keys[start + x] = s[x];
-}
-
-// Merge sorted runs of length `width` pairwise from src into dst (stable; ranks by
-// binary search in the partner run).
-__global__ void __launch_bounds__(256) k_merge_runs(const uint32_t* __restrict__ src, uint32_t* __restrict__ dst,
-                                                    const uint32_t* __restrict__ n_ptr, uint32_t cap,
-                                                    uint32_t width) {
-  const uint32_t n = min(*n_ptr, cap);
-  if (n <= kSortChunk) return;  // k_rank_sort has sorted them
-  for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n; x += (uint64_t)gridDim.x * blockDim.x) {
-    const uint64_t pair_start = (x / (2ull * width)) * (2ull * width);
-    const uint64_t mid = pair_start + width < n ? pair_start + width : n;
-    const uint64_t end = pair_start + 2ull * width < n ? pair_start + 2ull * width : n;
-    const uint32_t v = src[x];
-    uint64_t lo, hi, pos;
-    if (x < mid) {  // left run: count right-run elements < v
-      lo = mid;
-      hi = end;
-      while (lo < hi) {
-        const uint64_t m = (lo + hi) >> 1;
-        if (src[m] < v) lo = m + 1; else hi = m;
+  // merge passes: runs of `width` pairwise, keys -> alt -> keys ... -> out (reads bypass L1,
+  // which other blocks' writes do not update)
+  const uint32_t* src = keys;
+  for (uint64_t width = kSortChunk; width < n; width *= 2) {
+    if (!grid_barrier(bar, error)) return;
+    uint32_t* dst = 2 * width >= n ? out : (src == keys ? alt : keys);
+    for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n; x += (uint64_t)gridDim.x * blockDim.x) {
+      const uint64_t pair_start = (x / (2 * width)) * (2 * width);
+      const uint64_t mid = pair_start + width < n ? pair_start + width : n;
+      const uint64_t end = pair_start + 2 * width < n ? pair_start + 2 * width : n;
+      const uint32_t v = __ldcg(src + x);
+      uint64_t lo, hi, pos;
+      if (x < mid) {  // left run: count right-run keys < v
+        lo = mid;
+        hi = end;
+        while (lo < hi) {
+          const uint64_t md = (lo + hi) >> 1;
+          if (__ldcg(src + md) < v) lo = md + 1; else hi = md;
+        }
+        pos = x + (lo - mid);
+      } else {  // right run: count left-run keys <= v
+        lo = pair_start;
+        hi = mid;
+        while (lo < hi) {
+          const uint64_t md = (lo + hi) >> 1;
+          if (__ldcg(src + md) <= v) lo = md + 1; else hi = md;
+        }
+        pos = pair_start + (x - mid) + (lo - pair_start);
       }
-      pos = pair_start + (x - pair_start) + (lo - mid);
-    } else {  // right run: count left-run elements <= v
-      lo = pair_start;
-      hi = mid;
-      while (lo < hi) {
-        const uint64_t m = (lo + hi) >> 1;
-        if (src[m] <= v) lo = m + 1; else hi = m;
-      }
-      pos = pair_start + (x - mid) + (lo - pair_start);
+      dst[pos] = v;
     }
-    dst[pos] = v;
+    src = dst;
   }
 }
 
@@ -557,14 +624,16 @@ __global__ void __launch_bounds__(kEstThreads) k_estimate(
   __shared__ uint32_t warp_u[kEstThreads / 32];
   __shared__ const St* row_base[kMaxRows];
   const St* sle = reinterpret_cast<const St*>(sle_bytes);
+  const uint32_t count = n_ptr ? min(*n_ptr, n) : n;
+  if (blockIdx.x >= count) return;  // the grid is sized for the capacity
   const uint32_t cs = clock ? *clock : cs_value;
-  if (sizeof(St) == 1)
+  const bool vec16 = (p.delta2 & 15u) == 0;
+  const bool u_only = sizeof(St) == 1 && vec16 && !hist;  // U from byte-wise activity masks
+  if (sizeof(St) == 1 && !u_only)
     for (uint32_t s = threadIdx.x; s < 256; s += blockDim.x) {
       const uint32_t a = stamp_age(s, cs);
       age_lut[s] = a < p.k ? (uint8_t)a : 255;
     }
-  const uint32_t count = n_ptr ? min(*n_ptr, n) : n;
-  const bool vec16 = (p.delta2 & 15u) == 0;
   const double eta2 = (double)p.eta2;
   for (uint32_t h = blockIdx.x; h < count; h += gridDim.x) {
     const uint32_t aip = hosts[h];
@@ -588,7 +657,29 @@ __global__ void __launch_bounds__(kEstThreads) k_estimate(
     constexpr int kVecCells = 16 / sizeof(St);  // cells per 16-byte load
     constexpr int kIntCells = 4 / sizeof(St);
     constexpr uint32_t kMask = sizeof(St) == 1 ? 0xFFu : 0xFFFFu;
-    if (vec16) {
+    if (u_only) {
+      // U only: a union cell counts when it is active in every row, so the rows' byte-wise
+      // activity masks (active_hi8) are ANDed; up to 8 rows' loads are in flight at once
+      const Window8 win = window8(cs, p.k);
+      for (uint32_t z = threadIdx.x * 16; z < p.eta2; z += blockDim.x * 16) {
+        uint32_t a0 = 0x80808080u, a1 = a0, a2 = a0, a3 = a0;
+        for (uint32_t i0 = 0; i0 < p.r2; i0 += 8) {
+          uint4 v[8];
+#pragma unroll
+          for (uint32_t j = 0; j < 8; ++j)
+            if (i0 + j < p.r2) v[j] = *reinterpret_cast<const uint4*>(row_base[i0 + j] + z);
+#pragma unroll
+          for (uint32_t j = 0; j < 8; ++j)
+            if (i0 + j < p.r2) {
+              a0 &= active_hi8(v[j].x, win);
+              a1 &= active_hi8(v[j].y, win);
+              a2 &= active_hi8(v[j].z, win);
+              a3 &= active_hi8(v[j].w, win);
+            }
+        }
+        u += __popc(a0) + __popc(a1) + __popc(a2) + __popc(a3);
+      }
+    } else if (vec16) {
       for (uint32_t z = threadIdx.x * kVecCells; z < p.eta2; z += blockDim.x * kVecCells) {
         uint32_t m[kVecCells];
 #pragma unroll

@@ -119,7 +119,6 @@ struct sse_handle {
   CloseScratch* scratch = nullptr;
   uint32_t* query_active2 = nullptr;
   uint32_t cand_cap = 0;  // max_candidates
-  int sort_passes = 0;    // merge passes after the chunk sort
   CloseScratch* host_scratch = nullptr;  // pinned
   sse_stats stats;
   // staging for sse_update_host
@@ -345,31 +344,23 @@ int advance_clock(sse_handle* h) {
   return SSE_OK;
 }
 
-// Sorts the first min(n_cand, cap) candidates into cand_out and returns it. Up to
-// kSortChunk keys (decided on the device): k_rank_sort; more: chunk sorts in place, then
-// merge passes alternating between cand and cand_alt, the last one into cand_out.
-uint32_t* launch_sort(sse_handle* h) {
-  const uint32_t cap = h->cand_cap;
-  const uint32_t* n_ptr = &h->scratch->n_cand;
-  const uint32_t small = std::min<uint32_t>(cap, kSortChunk);
-  const uint32_t per_block = kRankThreads / kRankSplit;
-  k_rank_sort<<<(small + per_block - 1) / per_block, kRankThreads, 0, h->stream>>>(h->cand, n_ptr, cap, h->cand_out);
-  h->launches += 1;
-  if (h->sort_passes == 0) return h->cand_out;
-  const unsigned chunks = (cap + kSortChunk - 1) / kSortChunk;
-  k_sort_chunks<<<chunks, 1024, 0, h->stream>>>(h->cand, n_ptr, cap);
-  h->launches += 1 + h->sort_passes;
-  uint32_t* src = h->cand;
-  uint32_t* dst = h->cand_alt;
-  uint32_t width = kSortChunk;
-  for (int pass = 0; pass < h->sort_passes; ++pass) {
-    if (pass + 1 == h->sort_passes) dst = h->cand_out;
-    const int grid = grid_for(h, cap, 256, 4);
-    k_merge_runs<<<grid, 256, 0, h->stream>>>(src, dst, n_ptr, cap, width);
-    std::swap(src, dst);
-    width *= 2;
-  }
-  return h->cand_out;
+// Sorts the first min(n_cand, cap) candidates into cand_out: one cooperative launch (its
+// blocks meet at grid barriers when there are more than kSortChunk candidates).
+int launch_sort(sse_handle* h) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(kSortBlocks);
+  cfg.blockDim = dim3(kSortThreads);
+  cfg.stream = h->stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  CloseScratch* sc = h->scratch;
+  SSE_CUDA(h, cudaLaunchKernelEx(&cfg, k_sort_candidates, h->cand, h->cand_alt, h->cand_out,
+                                 (const uint32_t*)&sc->n_cand, h->cand_cap, sc->barrier, &sc->error));
+  SSE_LAUNCHED(h);
+  return SSE_OK;
 }
 
 }  // namespace
@@ -481,11 +472,6 @@ int sse_init(const sse_params* p, void* cuda_stream, sse_handle** out) {
     return SSE_ERR_CUDA;
   }
   h->cand_cap = q.max_candidates;
-  uint64_t run = kSortChunk;
-  while (run < h->cand_cap) {
-    run *= 2;
-    h->sort_passes += 1;
-  }
   const uint64_t state_bytes = d.sre_bytes + d.sle_bytes;
   const uint64_t list_entries = 1ull << q.q;
   bool ok = cudaMalloc(&h->state, state_bytes) == cudaSuccess && cudaMalloc(&h->clock, 256) == cudaSuccess &&
@@ -521,6 +507,15 @@ int sse_init(const sse_params* p, void* cuda_stream, sse_handle** out) {
     h->kp.tab = h->rhfg_tab;
   }
   h->tiles = make_tiles(q, d, h->num_sms);
+  {  // the candidate sort's blocks must all be resident at once (cooperative launch)
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sort_candidates, kSortThreads, 0) != cudaSuccess ||
+        (uint64_t)per_sm * h->num_sms < kSortBlocks) {
+      cudaGetLastError();
+      sse_destroy(h);
+      return SSE_ERR_CUDA;
+    }
+  }
   for (int v = 0; v < 4 * kNumTiledVariants; ++v) {
     const TiledKernel fn = kTiledVariants[v / 4].fn[(v >> 1) & 1][v & 1];
     if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -540,7 +535,7 @@ int sse_init(const sse_params* p, void* cuda_stream, sse_handle** out) {
     h->join_smem_t2 = t2_bytes <= 128u * 1024u ? 1u : 0u;
     size_t used = h->join_smem_t2 ? t2_bytes : 0;
     const size_t any_bytes = ((size_t)1 << (q.q - d.delta)) / 8;
-    if (q.r > 3 && d.delta <= 5 && used + any_bytes <= 160u * 1024u) {
+    if (q.r > 3 && d.delta <= 5 && q.q - d.delta >= 5 && used + any_bytes <= 160u * 1024u) {
       if (cudaMalloc(&h->any3, any_bytes) != cudaSuccess) {
         cudaGetLastError();
         sse_destroy(h);
@@ -729,21 +724,14 @@ int close_enqueue(sse_handle* h, uint32_t** sorted, bool copy_counters = true) {
   int rc = launch_close_pass(h, sc->active2, 3u);
   if (rc) return rc;
   {
-    const uint64_t words = ((uint64_t)h->p.r << h->p.q) >> 5;
-    const int grid = grid_for(h, words, 256, 4);
-    k_hot_lists<<<grid, 256, 0, h->stream>>>(h->hot_bits, h->p.r, h->p.q, sc->hot, h->list0, h->list1, sc->n_list);
-    SSE_LAUNCHED(h);
-  }
-  {
     const uint64_t words = (1ull << h->p.q) >> 5;
-    const dim3 grid(grid_for(h, words, 256, 2), h->p.r - 2);
-    k_row_regroup<<<grid, 256, 0, h->stream>>>(h->hot_bits, h->p.q, h->p.delta, h->tables);
+    const uint32_t n_lists = grid_for(h, words * h->p.r, 256, 4);
+    const uint32_t n_regroup = grid_for(h, words * (h->p.r - 2), 256, 2);
+    const uint32_t n_any = h->any3 ? (uint32_t)((((1u << (h->p.q - h->kp.delta)) >> 5) + 255) / 256) : 0u;
+    k_hot_prep<<<n_lists + n_regroup + n_any, 256, 0, h->stream>>>(h->hot_bits, h->p.r, h->p.q, h->p.delta, sc->hot,
+                                                                  h->list0, h->list1, sc->n_list, h->tables, h->any3,
+                                                                  n_lists, n_regroup);
     SSE_LAUNCHED(h);
-    if (h->any3) {
-      const uint32_t any_words = (1u << (h->p.q - h->kp.delta)) >> 5;
-      k_row_any<<<(any_words + 255) / 256, 256, 0, h->stream>>>(h->tables + words, h->p.q, h->kp.delta, h->any3);
-      SSE_LAUNCHED(h);
-    }
     if (h->kp.delta <= 5)
       k_join_tiled<<<h->num_sms, kJoinTiledThreads, h->join_tiled_smem, h->stream>>>(
           h->kp, h->tables, h->any3, h->list0, h->list1, sc->n_list, h->cand, &sc->n_cand, h->cand_cap, &sc->overflow,
@@ -755,8 +743,9 @@ int close_enqueue(sse_handle* h, uint32_t** sorted, bool copy_counters = true) {
                                                                     h->join_list1_cap);
     SSE_LAUNCHED(h);
   }
-  *sorted = launch_sort(h);
-  SSE_CUDA(h, cudaGetLastError());
+  rc = launch_sort(h);
+  if (rc) return rc;
+  *sorted = h->cand_out;
   {
     const int grid = grid_for(h, h->cand_cap, 1, 16);
     const auto est_fn = h->wide ? k_estimate<uint16_t> : k_estimate<uint8_t>;
@@ -778,6 +767,7 @@ int close_collect(sse_handle* h, const uint32_t* sorted, sse_report* out) {
   const uint32_t n_kept = std::min(n_found, h->cand_cap);
   int status = SSE_OK;
   if (n_found > h->cand_cap) status = SSE_ERR_CAPACITY;
+  if (hs.error) status = SSE_ERR_TIMEOUT;
   h->stats.slice = h->slice;
   for (int i = 0; i < kMaxRows; ++i) {
     h->stats.hot[i] = i < (int)h->p.r ? hs.hot[i] : 0;
@@ -838,9 +828,7 @@ int close_graph_launch(sse_handle* h) {
       rc = close_enqueue(h, &h->close_sorted, false);
       if (rc == SSE_OK) {
         k_report<<<8, 256, 0, h->stream>>>(h->scratch, h->close_sorted, h->est, h->flags, h->cand_cap,
-                                           h->report_stage_n, h->report_stage_dev);
-        SSE_LAUNCHED(h);
-        k_tick<<<1, 32, 0, h->stream>>>(h->clock, 1, h->smod);
+                                           h->report_stage_n, h->report_stage_dev, h->clock, h->smod);
         SSE_LAUNCHED(h);
       }
       cudaGraph_t g = nullptr;
@@ -882,6 +870,7 @@ int collect_staged(sse_handle* h, const uint32_t* sorted, uint64_t slice, sse_re
   const uint32_t n_found = hs.n_cand;
   const uint32_t n_kept = std::min(n_found, h->cand_cap);
   int status = n_found > h->cand_cap ? SSE_ERR_CAPACITY : SSE_OK;
+  if (hs.error) status = SSE_ERR_TIMEOUT;
   h->stats.slice = slice;
   for (int i = 0; i < kMaxRows; ++i) {
     h->stats.hot[i] = i < (int)h->p.r ? hs.hot[i] : 0;
@@ -1254,7 +1243,7 @@ int batch_enqueue_step(sse_batch* b) {
     rc = close_enqueue(g, &b->sorted, false);
     if (rc) return rc;
     k_report<<<8, 256, 0, b->stream>>>(g->scratch, b->sorted, g->est, g->flags, g->cand_cap, g->report_stage_n,
-                                       g->report_stage_dev);
+                                       g->report_stage_dev, nullptr, 0u);
     SSE_LAUNCHED(g);
   }
   ClockList cl;

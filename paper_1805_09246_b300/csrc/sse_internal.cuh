@@ -64,6 +64,31 @@ __host__ __device__ __forceinline__ uint32_t stamp_of(uint64_t slice, uint32_t m
   return (uint32_t)(1 + slice % mod);
 }
 
+// Activity of four 8-bit stamps at once (SWAR on a 32-bit word). A stamp s is active for a
+// window of k slices at current stamp cs when s != 0 and (cs - s) mod 255 < k. The active
+// stamps form one cyclic interval, so with L = cs - k + 1, K = k when cs >= k, and
+// L = cs + 256 - k, K = k + 1 otherwise (the interval then wraps over 0, which s != 0
+// removes), s is active exactly when s != 0 and (s - L) mod 256 < K. The byte-wise
+// subtraction, addition and carry formulas are the standard ones (Hacker's Delight,
+// Section 2-18): no carry crosses a byte. Returns 0x80 in every active byte, 0 elsewhere.
+struct Window8 {
+  uint32_t L4;  // L in every byte
+  uint32_t C4;  // 256 - K in every byte (t < K exactly when t + (256 - K) does not carry)
+};
+__host__ __device__ __forceinline__ Window8 window8(uint32_t cs, uint32_t k) {
+  const uint32_t L = cs >= k ? cs - k + 1 : cs + 256 - k;
+  const uint32_t K = cs >= k ? k : k + 1;
+  return Window8{(L & 255u) * 0x01010101u, (256u - K) * 0x01010101u};
+}
+__host__ __device__ __forceinline__ uint32_t active_hi8(uint32_t w, Window8 win) {
+  constexpr uint32_t H = 0x80808080u, Lo = 0x7F7F7F7Fu;
+  const uint32_t t = ((w | H) - (win.L4 & Lo)) ^ ((w ^ ~win.L4) & H);  // (s - L) mod 256 per byte
+  const uint32_t sum = ((t & Lo) + (win.C4 & Lo)) ^ ((t ^ win.C4) & H);
+  const uint32_t carry = (t & win.C4) | ((t | win.C4) & ~sum);            // bit 7: t + C >= 256
+  const uint32_t nz = ((w & Lo) + Lo) | w;                                // bit 7: s != 0
+  return ~carry & nz & H;
+}
+
 // The estimator's device clock holds the current stamp; advancing a slice moves it along the
 // 1..mod cycle on the device, so launches read the right stamp even when replayed.
 __global__ void k_tick(uint32_t* clock, uint32_t n, uint32_t mod = 255u) {
@@ -79,8 +104,8 @@ struct CloseScratch {
   uint32_t n_cand;             // candidate hosts found (may exceed capacity)
   uint32_t n_super;            // candidates flagged super
   uint32_t overflow;           // nonzero when a buffer was too small
-  uint32_t error;              // nonzero when a device-side check failed
-  uint32_t pad[2];
+  uint32_t error;              // nonzero when a bounded device-side wait gave up
+  uint32_t barrier[2];         // grid barrier of the candidate sort (arrivals, generation)
 };
 
 }  // namespace sse

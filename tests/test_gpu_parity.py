@@ -366,6 +366,57 @@ def test_many_candidates_sorted_and_capacity():
     assert np.array_equal(small.hosts, want[:1000])
 
 
+def test_conditional_sort_node_follows_the_candidate_count():
+    """The close graph sorts more than 4096 candidates in a conditional node that the rank
+    sort switches on only when needed: slices alternating between thousands of candidates
+    (planted) and a handful give the reports of the kernels launched one by one, and the
+    planted slice's candidates are the oracle's (brute force)."""
+    S = sse()
+    p = S.Params(q=20, k=2, theta=64, max_candidates=1 << 14, seed=23)
+    orc = oracle.Oracle(oracle_params(p))
+    rng = np.random.default_rng(23)
+    hosts = np.unique(rng.integers(0, 2**32, 6000, dtype=np.uint64).astype(np.uint32))
+    sre, sle = _planted_state(p, orc, hosts, rng)
+    want = orc.candidates_brute()
+    assert len(want) > 4096
+    g, d = S.Estimator(p), S.Estimator(p)
+    d.close_use_graph(False)
+    blob = helpers.state_blob(g.export_state(), helpers.stamps_from_distances(sre, 0, p.k),
+                              helpers.stamps_from_distances(sle, 0, p.k), g.derived["row_pitch2"])
+    tr = synth.Traffic(synth.small_trace(seed=23))
+    counts = []
+    for t in range(6):
+        if t % 3 == 0:  # replant (a fresh slice-0 state)
+            g.import_state(blob)
+            d.import_state(blob)
+        else:
+            pairs = helpers.to_device(tr.slice(0, t))
+            g.update(pairs)
+            d.update(pairs)
+        rg, rd = g.close_slice(), d.close_slice()
+        assert np.array_equal(rg.hosts, rd.hosts) and np.array_equal(rg.flags, rd.flags)
+        assert np.array_equal(rg.est, rd.est) and rg.n_super == rd.n_super
+        if t % 3 == 0:
+            assert np.array_equal(rg.hosts, want)
+        counts.append(rg.n_candidates)
+    assert max(counts) > 4096 and min(counts) <= 4096
+
+
+def test_few_low_bits_per_row_without_any_hot_filter():
+    """q - delta < 5 (r = 8, q = 8, delta = 4): the join runs without row 3's any-hot bitmap;
+    state, hot SREs and reports still match the oracle."""
+    S = sse()
+    p = S.Params(r=8, q=8, delta=4, r2=5, q2=12, eta2=1024, delta2=16, k=3, theta=1024, seed=29)
+    rng = np.random.default_rng(29)
+    slices = []
+    for t in range(4):
+        src = rng.integers(0, 2**32, 6, dtype=np.uint64).astype(np.uint32)
+        heavy = np.stack([np.repeat(src, 3000), rng.integers(0, 2**32, 6 * 3000, dtype=np.uint64).astype(np.uint32)], 1)
+        noise = rng.integers(0, 2**32, (500, 2), dtype=np.uint64).astype(np.uint32)
+        slices.append(np.ascontiguousarray(np.concatenate([heavy, noise])[rng.permutation(6 * 3000 + 500)]))
+    run_both(p, slices)
+
+
 def test_candidate_overflow_is_reported():
     S = sse()
     p = S.Params(q=14, k=2, theta=64, max_candidates=64, seed=18)
