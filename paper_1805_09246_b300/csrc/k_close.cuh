@@ -25,11 +25,11 @@ __device__ __forceinline__ uint32_t cell_active16(uint32_t s, uint32_t cs, uint3
 
 // One 32-bit word of cells: adds its active cells to `count` and returns the mask that
 // keeps them (all ones over active cells, zero over the rest). 8-bit cells are tested four
-// at a time (active_hi8); 16-bit cells one by one.
-template <typename St>
+// at a time (active_hi8; WRAP = the window wraps over stamp 0); 16-bit cells one by one.
+template <typename St, bool WRAP>
 __device__ __forceinline__ uint32_t word_keep(uint32_t w, Window8 win, uint32_t cs, uint32_t k, uint32_t& count) {
   if constexpr (sizeof(St) == 1) {
-    const uint32_t a = active_hi8(w, win);
+    const uint32_t a = active_hi8<WRAP>(w, win);
     count += __popc(a);
     return (a >> 7) * 0xFFu;
   } else {
@@ -39,23 +39,13 @@ __device__ __forceinline__ uint32_t word_keep(uint32_t w, Window8 win, uint32_t 
   }
 }
 
-// mode bit 0: write back expired cells; bit 1: write the hot bitmap. do_sre != 0: the
-// RSRA is processed as well as the SLEA. Grid-stride over both arrays (any grid size).
-// Cells are St (8 or 16 bits); one SRE is 8 cells (a 64- or 128-bit word).
-template <typename St>
-__global__ void __launch_bounds__(kCloseThreads) k_close(const __grid_constant__ KParams p,
-                                                          uint8_t* __restrict__ sre, uint8_t* __restrict__ sle,
-                                                          uint32_t* __restrict__ hot_bits,
-                                                          uint32_t* __restrict__ active2, uint32_t cs_value,
-                                                          const uint32_t* __restrict__ clock, uint32_t do_sre,
-                                                          uint32_t mode) {
+// The pass of k_close for one window shape (WRAP: see word_keep).
+template <typename St, bool WRAP>
+__device__ __forceinline__ void close_body(const KParams& p, uint8_t* __restrict__ sre, uint8_t* __restrict__ sle,
+                                          uint32_t* __restrict__ hot_bits, uint32_t* row_sum, uint32_t cs,
+                                          Window8 win, uint32_t do_sre, uint32_t mode) {
   using SreWord = typename std::conditional<sizeof(St) == 1, uint2, uint4>::type;
   constexpr int kSreInts = sizeof(SreWord) / 4;
-  const uint32_t cs = clock ? *clock : cs_value;
-  const Window8 win = window8(cs, p.k);  // used by 8-bit cells only
-  __shared__ uint32_t row_sum[kMaxRows];
-  if (threadIdx.x < kMaxRows) row_sum[threadIdx.x] = 0;
-  __syncthreads();
   const bool expire = (mode & 1u) != 0;
   const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const uint64_t nthreads = (uint64_t)gridDim.x * blockDim.x;  // a multiple of 32
@@ -80,7 +70,7 @@ __global__ void __launch_bounds__(kCloseThreads) k_close(const __grid_constant__
         memcpy(x, &v[u], sizeof(SreWord));
 #pragma unroll
         for (int i = 0; i < kSreInts; ++i) {
-          keep[i] = word_keep<St>(x[i], win, cs, p.k, weight);
+          keep[i] = word_keep<St, WRAP>(x[i], win, cs, p.k, weight);
           expired |= x[i] & ~keep[i];
         }
         const unsigned ballot = __ballot_sync(0xFFFFFFFFu, weight >= p.hot_min);
@@ -108,7 +98,7 @@ __global__ void __launch_bounds__(kCloseThreads) k_close(const __grid_constant__
       uint32_t keep[4], expired = 0;
 #pragma unroll
       for (int i = 0; i < 4; ++i) {
-        keep[i] = word_keep<St>(w[i], win, cs, p.k, count);
+        keep[i] = word_keep<St, WRAP>(w[i], win, cs, p.k, count);
         expired |= w[i] & ~keep[i];
       }
       if (expire && expired) *cell = make_uint4(w[0] & keep[0], w[1] & keep[1], w[2] & keep[2], w[3] & keep[3]);
@@ -117,6 +107,27 @@ __global__ void __launch_bounds__(kCloseThreads) k_close(const __grid_constant__
     for (int off = 16; off > 0; off >>= 1) count += __shfl_xor_sync(0xFFFFFFFFu, count, off);
     if ((threadIdx.x & 31) == 0 && count) atomicAdd(&row_sum[(uint32_t)(x0 / vec_per_row)], count);
   }
+}
+
+// mode bit 0: write back expired cells; bit 1: write the hot bitmap. do_sre != 0: the
+// RSRA is processed as well as the SLEA. Grid-stride over both arrays (any grid size).
+// Cells are St (8 or 16 bits); one SRE is 8 cells (a 64- or 128-bit word).
+template <typename St>
+__global__ void __launch_bounds__(kCloseThreads) k_close(const __grid_constant__ KParams p,
+                                                          uint8_t* __restrict__ sre, uint8_t* __restrict__ sle,
+                                                          uint32_t* __restrict__ hot_bits,
+                                                          uint32_t* __restrict__ active2, uint32_t cs_value,
+                                                          const uint32_t* __restrict__ clock, uint32_t do_sre,
+                                                          uint32_t mode) {
+  const uint32_t cs = clock ? *clock : cs_value;
+  const Window8 win = window8(cs, p.k);  // used by 8-bit cells only
+  __shared__ uint32_t row_sum[kMaxRows];
+  if (threadIdx.x < kMaxRows) row_sum[threadIdx.x] = 0;
+  __syncthreads();
+  if (sizeof(St) == 1 && win.wrap)
+    close_body<St, true>(p, sre, sle, hot_bits, row_sum, cs, win, do_sre, mode);
+  else
+    close_body<St, false>(p, sre, sle, hot_bits, row_sum, cs, win, do_sre, mode);
   __syncthreads();
   if (threadIdx.x < p.r2 && row_sum[threadIdx.x]) atomicAdd(&active2[threadIdx.x], row_sum[threadIdx.x]);
 }

@@ -15,6 +15,8 @@
 // round-to-nearest operations in a fixed order, so the super point decision is exact.
 #pragma once
 
+#include <type_traits>
+
 #include "k_close.cuh"
 #include "sse_internal.cuh"
 
@@ -109,9 +111,16 @@ __device__ __forceinline__ void regroup_part(const uint32_t* __restrict__ hot_bi
       const uint64_t j = w >> delta;
       const uint32_t m = (uint32_t)w & tmask;
       const uint64_t tstride = 1ull << (q - delta - 5);
-      for (uint32_t t = 0; t <= tmask; ++t) {
-        const uint32_t v = src[j + t * tstride] >> (m * per);
-        for (uint32_t b = 0; b < per; ++b) out |= ((v >> b) & 1u) << ((b << delta) + t);
+      for (uint32_t t0 = 0; t0 <= tmask; t0 += 8) {  // 8 loads in flight (2^delta >= 2)
+        uint32_t v[8];
+#pragma unroll
+        for (uint32_t u = 0; u < 8; ++u) v[u] = t0 + u <= tmask ? src[j + (t0 + u) * tstride] : 0u;
+#pragma unroll
+        for (uint32_t u = 0; u < 8; ++u) {
+          if (t0 + u > tmask) break;
+          const uint32_t x = v[u] >> (m * per);
+          for (uint32_t b = 0; b < per; ++b) out |= ((x >> b) & 1u) << ((b << delta) + t0 + u);
+        }
       }
     } else {
       for (uint32_t b = 0; b < 32; ++b) {
@@ -124,36 +133,61 @@ __device__ __forceinline__ void regroup_part(const uint32_t* __restrict__ hot_bi
   }
 }
 
-// "Any hot" bitmap of row 3 (delta <= 5, q - delta >= 5): bit c is set when some of the
-// 2^delta SREs c | (t << (q - delta)) is hot, i.e. the OR over t of the row's bitmap words
-// j + t * 2^(q-delta-5) for the 32 c of output word j. Blocks blk = 0..nblk-1 of a launch.
-__device__ __forceinline__ void any_part(const uint32_t* __restrict__ hot_bits, uint32_t q, uint32_t delta,
-                                         uint32_t* __restrict__ any, uint32_t blk, uint32_t nblk) {
+// "Any hot" bitmap of one row (delta <= 5): bit c is set when some of the 2^delta SREs
+// c | (t << (q - delta)) is hot. With q - delta >= 5, output word j is the OR over t of the
+// row's bitmap words j + t * 2^(q-delta-5); otherwise the single word is built bit by bit.
+// Blocks blk = 0..nblk-1 of a launch.
+__device__ __forceinline__ void any_part(const uint32_t* __restrict__ hot_bits, uint32_t row, uint32_t q,
+                                         uint32_t delta, uint32_t* __restrict__ any, uint32_t blk, uint32_t nblk) {
+  const uint32_t* src = hot_bits + ((uint64_t)row << (q - 5));
+  if (q - delta < 5) {
+    if (blk == 0 && threadIdx.x == 0) {
+      uint32_t out = 0;
+      for (uint32_t c = 0; c < (1u << (q - delta)); ++c)
+        for (uint32_t t = 0; t < (1u << delta); ++t)
+          if (hot_bit(hot_bits, q, row, c | (t << (q - delta)))) out |= 1u << c;
+      any[0] = out;
+    }
+    return;
+  }
   const uint32_t n_words = (1u << (q - delta)) >> 5;
-  const uint32_t* src = hot_bits + (3ull << (q - 5));
   const uint32_t tstride = 1u << (q - delta - 5);
   for (uint32_t j = blk * blockDim.x + threadIdx.x; j < n_words; j += nblk * blockDim.x) {
     uint32_t out = 0;
-    for (uint32_t t = 0; t < (1u << delta); ++t) out |= src[j + t * tstride];
+    for (uint32_t t0 = 0; t0 < (1u << delta); t0 += 8) {  // 8 loads in flight
+      uint32_t v[8];
+#pragma unroll
+      for (uint32_t u = 0; u < 8; ++u) v[u] = t0 + u < (1u << delta) ? src[j + (t0 + u) * tstride] : 0u;
+#pragma unroll
+      for (uint32_t u = 0; u < 8; ++u) out |= v[u];
+    }
     any[j] = out;
   }
 }
 
 // Everything the join reads from the hot bitmap, in one launch: blocks [0, n_lists) build
 // the hot lists of rows 0-1 and the hot counts, the next n_regroup blocks the regrouped
-// tables of rows 2..r-1, the remaining blocks (when any != NULL) row 3's any-hot bitmap.
+// tables of rows 2..r-1, the rest (when any2 != NULL) the "any hot" bitmaps of rows 2 and 3
+// (any3 when r > 3), half of them each.
 __global__ void __launch_bounds__(256) k_hot_prep(const uint32_t* __restrict__ hot_bits, uint32_t r, uint32_t q,
                                                   uint32_t delta, uint32_t* __restrict__ hot_count,
                                                   uint32_t* __restrict__ list0, uint32_t* __restrict__ list1,
                                                   uint32_t* __restrict__ n_list, uint32_t* __restrict__ tables,
-                                                  uint32_t* __restrict__ any, uint32_t n_lists, uint32_t n_regroup) {
+                                                  uint32_t* __restrict__ any2, uint32_t* __restrict__ any3,
+                                                  uint32_t n_lists, uint32_t n_regroup) {
   const uint32_t b = blockIdx.x;
-  if (b < n_lists)
+  if (b < n_lists) {
     hot_lists_part(hot_bits, r, q, hot_count, list0, list1, n_list, b, n_lists);
-  else if (b < n_lists + n_regroup)
+  } else if (b < n_lists + n_regroup) {
     regroup_part(hot_bits, r, q, delta, tables, b - n_lists, n_regroup);
-  else if (any)
-    any_part(hot_bits, q, delta, any, b - n_lists - n_regroup, gridDim.x - n_lists - n_regroup);
+  } else if (any2) {
+    const uint32_t rest = gridDim.x - n_lists - n_regroup, x = b - n_lists - n_regroup;
+    const uint32_t half = (rest + 1) / 2;
+    if (x < half)
+      any_part(hot_bits, 2, q, delta, any2, x, half);
+    else if (any3)
+      any_part(hot_bits, 3, q, delta, any3, x - half, rest - half);
+  }
 }
 
 // The 2^delta (<= 32) hot flags, indexed by the top delta bits of he_i, of the row whose
@@ -166,7 +200,7 @@ __device__ __forceinline__ uint32_t hot_group(const uint32_t* table, uint32_t c,
 }
 
 // Rows 3..r-1 for delta <= 5: depth-first over the set bits of each row's hot group.
-__device__ __noinline__ void grow_grouped(const KParams& p, const uint32_t* tables, uint32_t he0, uint32_t b1,
+__device__ __forceinline__ void grow_grouped(const KParams& p, const uint32_t* tables, uint32_t he0, uint32_t b1,
                                           uint32_t b2, uint32_t* cand, uint32_t* n_cand, uint32_t cap,
                                           uint32_t* overflow) {
   const uint32_t delta = p.delta, q = p.q, shift_hi = q - delta;
@@ -307,25 +341,38 @@ __global__ void __launch_bounds__(256) k_report(const CloseScratch* __restrict__
 // and probes it against a chunk of HSE(0) staged in shared memory. With
 // g_1 = (he_1 >> delta) mod 2^(q-delta) and K(he_0) = (he_0 XOR (he_0 >> delta)) mod 2^(q-delta),
 // the low bits c of every admissible B(2) XOR he_0 are K(he_0) XOR g_1 (Eq. 7 and the overlap
-// of B(1) and B(2)), so a probe is one XOR and one lookup of the regrouped row-2 table.
-// Probes run 16 he_0 at a time; the (lane, he_0) pairs that found a hot row-2 group are
-// compacted into a per-warp list (warp prefix sum) and expanded by all 32 lanes together.
-// Chains that pass row 3's "any hot" test are queued in shared memory and grown by the whole
-// block at the end of the work unit; a full queue makes the thread grow the chain itself.
-constexpr int kJoinTiledThreads = 1024;
-constexpr uint32_t kJoinQueueCap = 2048;   // chains per block queue
-constexpr uint32_t kJoinChunkMax = 1024;   // he_0 per work unit
+// of B(1) and B(2)), so a probe is one XOR and one bit of row 2's "any hot" bitmap (some of
+// the 2^delta SREs with low bits c is hot). Probes run 16 he_0 at a time; the (lane, he_0)
+// pairs that hit are pushed on a per-warp stack (warp prefix sum), and whenever 32 wait, every
+// lane expands one: the hot SREs of the group come from the regrouped row-2 table, and each
+// chain must pass row 3's "any hot" bit before it is queued in shared memory; the block grows
+// the queued chains at the end of the work unit (a full queue makes the thread grow the chain
+// itself). The two "any hot" bitmaps are staged in shared memory when `stage` is set; the
+// blocks are small (kJoinTiledThreads) so that several share an SM.
+constexpr int kJoinTiledThreads = 256;
+constexpr uint32_t kJoinQueueCap = 512;    // chains per block queue
+constexpr uint32_t kJoinChunkMax = 256;    // he_0 per work unit
 constexpr uint32_t kJoinProbeBlock = 16;   // he_0 probed before a compaction
-constexpr uint32_t kJoinListWords = 32 * kJoinProbeBlock / 2;  // per warp: 16-bit entries
-// dynamic shared memory after the optional tables: queue, he_0 chunk, K chunk, he_1, lists
+constexpr uint32_t kJoinListWords = (32 + 32 * kJoinProbeBlock) / 2;  // per warp hit stack: 16-bit entries
+// dynamic shared memory after the optional bitmaps: queue, he_0 chunk, K chunk, he_1, lists
 constexpr size_t kJoinTiledFixedBytes =
     (3 * (size_t)kJoinQueueCap + 2 * kJoinChunkMax + kJoinTiledThreads + (kJoinTiledThreads / 32) * kJoinListWords) * 4;
 
+// Words of an "any hot" bitmap over the 2^(q-delta) values of c, and the shared-memory words
+// that hold one (a multiple of 4, so that what follows stays 16-byte aligned).
+__host__ __device__ __forceinline__ uint32_t any_words(uint32_t q, uint32_t delta) {
+  const uint32_t w = (1u << (q - delta)) >> 5;
+  return w ? w : 1u;
+}
+__host__ __device__ __forceinline__ uint32_t any_words_staged(uint32_t q, uint32_t delta) {
+  return (any_words(q, delta) + 3u) & ~3u;
+}
+
 __global__ void __launch_bounds__(kJoinTiledThreads) k_join_tiled(
-    const __grid_constant__ KParams p, const uint32_t* __restrict__ tables, const uint32_t* __restrict__ any3,
-    const uint32_t* __restrict__ list0, const uint32_t* __restrict__ list1, const uint32_t* __restrict__ n_list,
-    uint32_t* __restrict__ cand, uint32_t* __restrict__ n_cand, uint32_t cap, uint32_t* __restrict__ overflow,
-    uint32_t smem_t2) {
+    const __grid_constant__ KParams p, const uint32_t* __restrict__ tables, const uint32_t* __restrict__ any2,
+    const uint32_t* __restrict__ any3, const uint32_t* __restrict__ list0, const uint32_t* __restrict__ list1,
+    const uint32_t* __restrict__ n_list, uint32_t* __restrict__ cand, uint32_t* __restrict__ n_cand, uint32_t cap,
+    uint32_t* __restrict__ overflow, uint32_t stage) {
   extern __shared__ uint32_t sm[];
   __shared__ uint32_t s_qn;
   const uint32_t n0 = n_list[0], n1 = n_list[1];
@@ -335,22 +382,21 @@ __global__ void __launch_bounds__(kJoinTiledThreads) k_join_tiled(
   const uint32_t cmask = (1u << shift_hi) - 1u;
   const uint32_t span_mask = delta == 5 ? 0xFFFFFFFFu : (1u << (1u << delta)) - 1u;
   const bool row2_fits_all = 2 * delta + q <= 32;
-  const uint32_t nwords = (1u << q) >> 5;
   const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
-  // shared memory: [row-2 table] [any3] [queue: he0 | b1 | b2] [he_0 chunk] [K chunk] [he_1] [lists]
-  const uint32_t* t2 = tables;
+  // shared memory: [any2] [any3] [queue: he0 | b1 | b2] [he_0 chunk] [K chunk] [he_1] [lists]
+  const uint32_t aw = any_words(q, delta);
+  const uint32_t* a2 = any2;
+  const uint32_t* a3 = any3;
   uint32_t* next = sm;
-  if (smem_t2) {
-    for (uint32_t w = threadIdx.x; w < nwords; w += blockDim.x) sm[w] = tables[w];
-    t2 = sm;
-    next += nwords;
-  }
-  const uint32_t* a3 = nullptr;
-  if (any3) {
-    const uint32_t any_words = (1u << shift_hi) >> 5;
-    for (uint32_t w = threadIdx.x; w < any_words; w += blockDim.x) next[w] = any3[w];
-    a3 = next;
-    next += any_words;
+  if (stage) {
+    for (uint32_t w = threadIdx.x; w < aw; w += blockDim.x) next[w] = any2[w];
+    a2 = next;
+    next += any_words_staged(q, delta);
+    if (any3) {
+      for (uint32_t w = threadIdx.x; w < aw; w += blockDim.x) next[w] = any3[w];
+      a3 = next;
+    }
+    next += any_words_staged(q, delta);
   }
   uint32_t* qh = next;
   uint32_t* qb1 = qh + kJoinQueueCap;
@@ -359,6 +405,7 @@ __global__ void __launch_bounds__(kJoinTiledThreads) k_join_tiled(
   uint32_t* s_k = s_he0 + kJoinChunkMax;
   uint32_t* s_he1 = s_k + kJoinChunkMax;
   uint16_t* my_list = reinterpret_cast<uint16_t*>(s_he1 + kJoinTiledThreads) + warp * (2 * kJoinListWords);
+  static_assert(kJoinChunkMax <= 256, "hit entries hold 8-bit chunk indices");
   if (threadIdx.x == 0) s_qn = 0;
 
   // Work rows (tile of HSE(1), he_0), tile-major, split evenly over the blocks; a block's
@@ -368,10 +415,6 @@ __global__ void __launch_bounds__(kJoinTiledThreads) k_join_tiled(
   const uint64_t rows = (uint64_t)tiles1 * n0;
   const uint64_t r_begin = rows * blockIdx.x / gridDim.x, r_end = rows * (blockIdx.x + 1) / gridDim.x;
 
-  auto lookup = [&](uint32_t c) -> uint32_t {  // hot flags of row 2's group c
-    const uint32_t first = c << delta;
-    return (t2[first >> 5] >> (first & 31)) & span_mask;
-  };
   auto emit = [&](uint32_t he0, uint32_t b1, uint32_t b2) {
     const uint32_t at = atomicAdd(&s_qn, 1u);
     if (at < kJoinQueueCap) {
@@ -382,6 +425,29 @@ __global__ void __launch_bounds__(kJoinTiledThreads) k_join_tiled(
       grow_grouped(p, tables, he0, b1, b2, cand, n_cand, cap, overflow);
     }
   };
+  // One hit (he_0, he_1): every hot row-2 SRE of the group gives B(2); chains whose row-3
+  // group has a hot SRE are queued.
+  auto expand = [&](uint32_t e) {
+    const uint32_t he0 = s_he0[e & 255u];
+    const uint32_t b1 = he0 ^ s_he1[warp * 32 + (e >> 8)];
+    if (!fits32(1, delta, q, b1)) return;
+    const uint32_t low2 = b1 >> delta;
+    const uint32_t hi0 = he0 >> shift_hi;
+    const uint32_t first = ((he0 ^ low2) & cmask) << delta;  // row-2 group of c
+    uint32_t m = (tables[first >> 5] >> (first & 31)) & span_mask;
+    while (m) {
+      const uint32_t tp = __ffs(m) - 1;  // top bits of he_2
+      m &= m - 1;
+      const uint32_t b2 = low2 | ((tp ^ hi0) << shift_hi);
+      if (!row2_fits_all && !fits32(2, delta, q, b2)) continue;
+      if (a3) {
+        const uint32_t c3 = (he0 ^ (b2 >> delta)) & cmask;
+        if (!((a3[c3 >> 5] >> (c3 & 31)) & 1u)) continue;
+      }
+      emit(he0, b1, b2);
+    }
+  };
+  uint32_t hn = 0;  // entries on this warp's hit stack (the same in every lane)
 
   for (uint64_t r0 = r_begin; r0 < r_end;) {
     const uint32_t tile = (uint32_t)(r0 / n0), c0 = (uint32_t)(r0 % n0);
@@ -391,10 +457,14 @@ __global__ void __launch_bounds__(kJoinTiledThreads) k_join_tiled(
     const uint32_t m0 = (uint32_t)mm;
     r0 += m0;
     __syncthreads();  // previous unit's chunk and queue are done with
-    for (uint32_t j = threadIdx.x; j < m0; j += blockDim.x) {
-      const uint32_t he0 = list0[c0 + j];
-      s_he0[j] = he0;
-      s_k[j] = (he0 ^ (he0 >> delta)) & cmask;
+    for (uint32_t j = threadIdx.x; j < ((m0 + kJoinProbeBlock - 1) & ~(kJoinProbeBlock - 1)); j += blockDim.x) {
+      if (j < m0) {
+        const uint32_t he0 = list0[c0 + j];
+        s_he0[j] = he0;
+        s_k[j] = (he0 ^ (he0 >> delta)) & cmask;
+      } else {
+        s_k[j] = 0;  // the probe block's padding: an in-range c, masked off after the probes
+      }
     }
     const uint32_t b = tile * width1 + threadIdx.x;
     const bool valid = threadIdx.x < width1 && b < n1;
@@ -405,9 +475,21 @@ __global__ void __launch_bounds__(kJoinTiledThreads) k_join_tiled(
     for (uint32_t j0 = 0; j0 < m0; j0 += kJoinProbeBlock) {  // uniform over the block
       const uint32_t jn = min(kJoinProbeBlock, m0 - j0);
       uint32_t hits = 0;
-      if (valid)
-        for (uint32_t j = 0; j < jn; ++j) hits |= (lookup(s_k[j0 + j] ^ g1) != 0 ? 1u : 0u) << j;
-      // compact this warp's hits: exclusive prefix sum of the per-lane counts
+      if (valid) {
+        // 16 probes from four broadcast vector loads; entries past the chunk (inside the
+        // kJoinChunkMax-entry array, which is a multiple of 16) are masked off below
+        const uint4* k4 = reinterpret_cast<const uint4*>(s_k + j0);
+#pragma unroll
+        for (uint32_t v = 0; v < kJoinProbeBlock / 4; ++v) {
+          const uint4 kk = k4[v];
+          const uint32_t c[4] = {kk.x ^ g1, kk.y ^ g1, kk.z ^ g1, kk.w ^ g1};
+#pragma unroll
+          for (uint32_t u = 0; u < 4; ++u) hits |= (__funnelshift_r(a2[c[u] >> 5], 0u, c[u]) & 1u) << (4 * v + u);
+        }
+        if (jn < kJoinProbeBlock) hits &= (1u << jn) - 1u;
+      }
+      // append this warp's hits to its hit stack (exclusive prefix sum of the per-lane
+      // counts); each entry is (lane << 8) | index of he_0 in the chunk
       const uint32_t cnt = __popc(hits);
       uint32_t incl = cnt;
 #pragma unroll
@@ -416,35 +498,23 @@ __global__ void __launch_bounds__(kJoinTiledThreads) k_join_tiled(
         if (lane >= (uint32_t)o) incl += v;
       }
       const uint32_t total = __shfl_sync(0xFFFFFFFFu, incl, 31);
-      uint32_t at = incl - cnt;
+      uint32_t at = hn + incl - cnt;
       while (hits) {
         const uint32_t j = __ffs(hits) - 1;
         hits &= hits - 1;
-        my_list[at++] = (uint16_t)((lane << 4) | j);
+        my_list[at++] = (uint16_t)((lane << 8) | (j0 + j));
       }
+      hn += total;
       __syncwarp();
-      for (uint32_t i = lane; i < total; i += 32) {
-        const uint32_t e = my_list[i];
-        const uint32_t he0 = s_he0[j0 + (e & 15u)];
-        const uint32_t b1 = he0 ^ s_he1[warp * 32 + (e >> 4)];
-        if (!fits32(1, delta, q, b1)) continue;
-        const uint32_t low2 = b1 >> delta;
-        const uint32_t hi0 = he0 >> shift_hi;
-        uint32_t m = lookup((he0 ^ low2) & cmask);
-        while (m) {
-          const uint32_t tp = __ffs(m) - 1;  // top bits of he_2
-          m &= m - 1;
-          const uint32_t b2 = low2 | ((tp ^ hi0) << shift_hi);
-          if (!row2_fits_all && !fits32(2, delta, q, b2)) continue;
-          if (a3) {
-            const uint32_t c3 = (he0 ^ (b2 >> delta)) & cmask;
-            if (!((a3[c3 >> 5] >> (c3 & 31)) & 1u)) continue;
-          }
-          emit(he0, b1, b2);
-        }
+      while (hn >= 32) {  // every lane expands one hit, from the top of the stack
+        hn -= 32;
+        expand(my_list[hn + lane]);
+        __syncwarp();  // those entries are overwritten by the next append
       }
-      __syncwarp();  // the list is rewritten by the next probe block
     }
+    if (lane < hn) expand(my_list[lane]);  // the rest, before the chunk is replaced
+    hn = 0;
+    __syncwarp();
     __syncthreads();  // the queue is complete
     const uint32_t qn = min(s_qn, kJoinQueueCap);
     for (uint32_t i = threadIdx.x; i < qn; i += blockDim.x)
@@ -613,7 +683,7 @@ __device__ __forceinline__ uint32_t cell_age(uint32_t s, const uint8_t* age_lut,
 }
 
 template <typename St>
-__global__ void __launch_bounds__(kEstThreads) k_estimate(
+__global__ void __launch_bounds__(kEstThreads, 4) k_estimate(
     const __grid_constant__ KParams p, const uint8_t* __restrict__ sle_bytes, const uint32_t* __restrict__ hosts,
     const uint32_t* __restrict__ n_ptr, uint32_t n, const uint32_t* __restrict__ active2, double w_theta,
     uint32_t cs_value, const uint32_t* __restrict__ clock, float* __restrict__ est, uint8_t* __restrict__ flags,
@@ -661,24 +731,30 @@ __global__ void __launch_bounds__(kEstThreads) k_estimate(
       // U only: a union cell counts when it is active in every row, so the rows' byte-wise
       // activity masks (active_hi8) are ANDed; up to 8 rows' loads are in flight at once
       const Window8 win = window8(cs, p.k);
-      for (uint32_t z = threadIdx.x * 16; z < p.eta2; z += blockDim.x * 16) {
-        uint32_t a0 = 0x80808080u, a1 = a0, a2 = a0, a3 = a0;
-        for (uint32_t i0 = 0; i0 < p.r2; i0 += 8) {
-          uint4 v[8];
+      auto rows_and = [&](auto wrap) {  // wrap: std::true_type when the window wraps over 0
+        constexpr bool W = decltype(wrap)::value;
+        uint32_t c = 0;
+        for (uint32_t z = threadIdx.x * 16; z < p.eta2; z += blockDim.x * 16) {
+          uint32_t a0 = 0x80808080u, a1 = a0, a2 = a0, a3 = a0;
+          for (uint32_t i0 = 0; i0 < p.r2; i0 += 8) {
+            uint4 v[8];
 #pragma unroll
-          for (uint32_t j = 0; j < 8; ++j)
-            if (i0 + j < p.r2) v[j] = *reinterpret_cast<const uint4*>(row_base[i0 + j] + z);
+            for (uint32_t j = 0; j < 8; ++j)
+              if (i0 + j < p.r2) v[j] = *reinterpret_cast<const uint4*>(row_base[i0 + j] + z);
 #pragma unroll
-          for (uint32_t j = 0; j < 8; ++j)
-            if (i0 + j < p.r2) {
-              a0 &= active_hi8(v[j].x, win);
-              a1 &= active_hi8(v[j].y, win);
-              a2 &= active_hi8(v[j].z, win);
-              a3 &= active_hi8(v[j].w, win);
-            }
+            for (uint32_t j = 0; j < 8; ++j)
+              if (i0 + j < p.r2) {
+                a0 &= active_hi8<W>(v[j].x, win);
+                a1 &= active_hi8<W>(v[j].y, win);
+                a2 &= active_hi8<W>(v[j].z, win);
+                a3 &= active_hi8<W>(v[j].w, win);
+              }
+          }
+          c += __popc(a0) + __popc(a1) + __popc(a2) + __popc(a3);
         }
-        u += __popc(a0) + __popc(a1) + __popc(a2) + __popc(a3);
-      }
+        return c;
+      };
+      u = win.wrap ? rows_and(std::true_type{}) : rows_and(std::false_type{});
     } else if (vec16) {
       for (uint32_t z = threadIdx.x * kVecCells; z < p.eta2; z += blockDim.x * kVecCells) {
         uint32_t m[kVecCells];

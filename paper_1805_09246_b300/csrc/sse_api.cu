@@ -105,7 +105,10 @@ struct sse_handle {
   uint32_t* list0 = nullptr;
   uint32_t* list1 = nullptr;
   uint32_t* tables = nullptr;  // hot bitmaps of rows 2..r-1 regrouped for the join
+  uint32_t* any2 = nullptr;    // row 2's "any hot" bitmap over c (delta <= 5)
   uint32_t* any3 = nullptr;    // row 3's "any hot" bitmap over c (r > 3, delta <= 5)
+  uint32_t join_stage = 0;     // k_join_tiled stages any2 and any3 in shared memory
+  uint32_t join_grid = 0;      // k_join_tiled blocks (all resident)
   uint32_t* rhfg_tab = nullptr;  // RHFG[0] tabulation tables (rhfg_hash = 1)
   uint32_t join_smem_t2 = 0;   // stage the row-2 table in shared memory
   uint32_t join_list1_cap = 0; // HSE(1) entries staged in shared memory when it fits
@@ -436,6 +439,7 @@ void sse_destroy(sse_handle* h) {
   cudaFree(h->flags);
   cudaFree(h->scratch);
   cudaFree(h->query_active2);
+  cudaFree(h->any2);
   cudaFree(h->any3);
   cudaFree(h->rhfg_tab);
   cudaFree(h->swap_buf);
@@ -526,37 +530,43 @@ int sse_init(const sse_params* p, void* cuda_stream, sse_handle** out) {
       return SSE_ERR_CUDA;
     }
   }
-  // join shared memory: the regrouped row-2 table (2^q bits) up to q = 20, row 3's "any hot"
-  // bitmap (2^(q-delta) bits) when it fits, then as much of HSE(1) as fits in the rest of a
-  // 216 KiB budget
+  // k_join (delta > 5) shared memory: the regrouped row-2 table (2^q bits) up to q = 20, then
+  // as much of HSE(1) as fits in the rest of a 216 KiB budget
   {
     const size_t budget = 216u * 1024u;
     const size_t t2_bytes = (size_t)(list_entries / 8);
     h->join_smem_t2 = t2_bytes <= 128u * 1024u ? 1u : 0u;
-    size_t used = h->join_smem_t2 ? t2_bytes : 0;
-    const size_t any_bytes = ((size_t)1 << (q.q - d.delta)) / 8;
-    if (q.r > 3 && d.delta <= 5 && q.q - d.delta >= 5 && used + any_bytes <= 160u * 1024u) {
-      if (cudaMalloc(&h->any3, any_bytes) != cudaSuccess) {
-        cudaGetLastError();
-        sse_destroy(h);
-        return SSE_ERR_OOM;
-      }
-      used += any_bytes;
-    }
+    const size_t used = h->join_smem_t2 ? t2_bytes : 0;
     h->join_list1_cap = (uint32_t)std::min<uint64_t>(list_entries, (budget - used) / 4);
     h->join_smem = used + (size_t)h->join_list1_cap * 4;
-    h->join_tiled_smem = used + kJoinTiledFixedBytes;
-    if (d.delta <= 5 && cudaFuncSetAttribute(k_join_tiled, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)h->join_tiled_smem) != cudaSuccess) {
-      cudaGetLastError();
-      sse_destroy(h);
-      return SSE_ERR_CUDA;
-    }
     if (cudaFuncSetAttribute(k_join, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)h->join_smem) != cudaSuccess) {
       cudaGetLastError();
       sse_destroy(h);
       return SSE_ERR_CUDA;
     }
+  }
+  // k_join_tiled (delta <= 5): the "any hot" bitmaps of rows 2 and 3 (2^(q-delta) bits each),
+  // staged in shared memory when both fit in 64 KiB; as many blocks as fit on the SMs
+  if (d.delta <= 5) {
+    const size_t any_bytes = (size_t)any_words(q.q, d.delta) * 4;
+    if (cudaMalloc(&h->any2, any_bytes) != cudaSuccess || (q.r > 3 && cudaMalloc(&h->any3, any_bytes) != cudaSuccess)) {
+      cudaGetLastError();
+      sse_destroy(h);
+      return SSE_ERR_OOM;
+    }
+    h->join_stage = 2 * any_bytes <= 64u * 1024u ? 1u : 0u;
+    h->join_tiled_smem = (h->join_stage ? 2 * (size_t)any_words_staged(q.q, d.delta) * 4 : 0) + kJoinTiledFixedBytes;
+    int per_sm = 0;
+    if (cudaFuncSetAttribute(k_join_tiled, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)h->join_tiled_smem) !=
+            cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_join_tiled, kJoinTiledThreads, h->join_tiled_smem) !=
+            cudaSuccess ||
+        per_sm < 1) {
+      cudaGetLastError();
+      sse_destroy(h);
+      return SSE_ERR_CUDA;
+    }
+    h->join_grid = (uint32_t)(per_sm * h->num_sms);
   }
   const uint32_t first_stamp = stamp_of(0, h->smod);
   if (cudaMemcpyAsync(h->clock, &first_stamp, sizeof(first_stamp), cudaMemcpyHostToDevice, h->stream) != cudaSuccess ||
@@ -727,15 +737,16 @@ int close_enqueue(sse_handle* h, uint32_t** sorted, bool copy_counters = true) {
     const uint64_t words = (1ull << h->p.q) >> 5;
     const uint32_t n_lists = grid_for(h, words * h->p.r, 256, 4);
     const uint32_t n_regroup = grid_for(h, words * (h->p.r - 2), 256, 2);
-    const uint32_t n_any = h->any3 ? (uint32_t)((((1u << (h->p.q - h->kp.delta)) >> 5) + 255) / 256) : 0u;
+    const uint32_t any_each = (any_words(h->p.q, h->p.delta) + 255) / 256;
+    const uint32_t n_any = h->any2 ? (h->any3 ? 2 * any_each : any_each) : 0u;
     k_hot_prep<<<n_lists + n_regroup + n_any, 256, 0, h->stream>>>(h->hot_bits, h->p.r, h->p.q, h->p.delta, sc->hot,
-                                                                  h->list0, h->list1, sc->n_list, h->tables, h->any3,
-                                                                  n_lists, n_regroup);
+                                                                  h->list0, h->list1, sc->n_list, h->tables, h->any2,
+                                                                  h->any3, n_lists, n_regroup);
     SSE_LAUNCHED(h);
     if (h->kp.delta <= 5)
-      k_join_tiled<<<h->num_sms, kJoinTiledThreads, h->join_tiled_smem, h->stream>>>(
-          h->kp, h->tables, h->any3, h->list0, h->list1, sc->n_list, h->cand, &sc->n_cand, h->cand_cap, &sc->overflow,
-          h->join_smem_t2);
+      k_join_tiled<<<h->join_grid, kJoinTiledThreads, h->join_tiled_smem, h->stream>>>(
+          h->kp, h->tables, h->any2, h->any3, h->list0, h->list1, sc->n_list, h->cand, &sc->n_cand, h->cand_cap,
+          &sc->overflow, h->join_stage);
     else
       k_join<<<h->num_sms, kJoinThreads, h->join_smem, h->stream>>>(h->kp, h->hot_bits, h->tables, h->any3, h->list0,
                                                                     h->list1, sc->n_list, h->cand, &sc->n_cand,
@@ -747,7 +758,7 @@ int close_enqueue(sse_handle* h, uint32_t** sorted, bool copy_counters = true) {
   if (rc) return rc;
   *sorted = h->cand_out;
   {
-    const int grid = grid_for(h, h->cand_cap, 1, 16);
+    const int grid = grid_for(h, h->cand_cap, 1, 8);
     const auto est_fn = h->wide ? k_estimate<uint16_t> : k_estimate<uint8_t>;
     est_fn<<<grid, kEstThreads, 0, h->stream>>>(h->kp, h->sle, *sorted, &sc->n_cand, h->cand_cap, sc->active2,
                                                 h->d.w_theta, stamp_of(h->slice, h->smod), h->clock, h->est, h->flags,

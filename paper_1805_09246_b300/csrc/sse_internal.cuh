@@ -72,21 +72,29 @@ __host__ __device__ __forceinline__ uint32_t stamp_of(uint64_t slice, uint32_t m
 // subtraction, addition and carry formulas are the standard ones (Hacker's Delight,
 // Section 2-18): no carry crosses a byte. Returns 0x80 in every active byte, 0 elsewhere.
 struct Window8 {
-  uint32_t L4;  // L in every byte
-  uint32_t C4;  // 256 - K in every byte (t < K exactly when t + (256 - K) does not carry)
+  uint32_t L4;    // L in every byte
+  uint32_t C4;    // 256 - K in every byte (t < K exactly when t + (256 - K) does not carry)
+  uint32_t wrap;  // cs < k: the interval wraps over 0, so s != 0 must be tested too
 };
 __host__ __device__ __forceinline__ Window8 window8(uint32_t cs, uint32_t k) {
   const uint32_t L = cs >= k ? cs - k + 1 : cs + 256 - k;
   const uint32_t K = cs >= k ? k : k + 1;
-  return Window8{(L & 255u) * 0x01010101u, (256u - K) * 0x01010101u};
+  return Window8{(L & 255u) * 0x01010101u, (256u - K) * 0x01010101u, cs < k ? 1u : 0u};
 }
+// WRAP = win.wrap. Without the wrap, s = 0 gives (0 - L) mod 256 = 256 - L >= K, so the
+// interval test alone decides.
+template <bool WRAP>
 __host__ __device__ __forceinline__ uint32_t active_hi8(uint32_t w, Window8 win) {
   constexpr uint32_t H = 0x80808080u, Lo = 0x7F7F7F7Fu;
   const uint32_t t = ((w | H) - (win.L4 & Lo)) ^ ((w ^ ~win.L4) & H);  // (s - L) mod 256 per byte
-  const uint32_t sum = ((t & Lo) + (win.C4 & Lo)) ^ ((t ^ win.C4) & H);
-  const uint32_t carry = (t & win.C4) | ((t | win.C4) & ~sum);            // bit 7: t + C >= 256
-  const uint32_t nz = ((w & Lo) + Lo) | w;                                // bit 7: s != 0
+  const uint32_t low = (t & Lo) + (win.C4 & Lo);                       // carry into bit 7
+  const uint32_t carry = (t & win.C4) | ((t | win.C4) & low);           // bit 7: t + C >= 256
+  if (!WRAP) return ~carry & H;
+  const uint32_t nz = ((w & Lo) + Lo) | w;  // bit 7: s != 0
   return ~carry & nz & H;
+}
+__host__ __device__ __forceinline__ uint32_t active_hi8(uint32_t w, Window8 win) {
+  return win.wrap ? active_hi8<true>(w, win) : active_hi8<false>(w, win);
 }
 
 // The estimator's device clock holds the current stamp; advancing a slice moves it along the
