@@ -385,6 +385,23 @@ SSE_API int sse_batch_step(sse_batch* b, const uint64_t* h_counts, sse_report* o
 SSE_API int sse_batch_step_from(sse_batch* b, const uint32_t* const* d_pairs, const uint64_t* h_counts,
                                 sse_report* out);
 
+/* The step of sse_batch_step_from() split in two, so that the device runs steps back to
+ * back while the host reads reports. sse_batch_step_async() enqueues one step behind any
+ * earlier one on the batch's stream and returns at once; d_pairs: one device pointer per
+ * router (8-byte aligned; their pairs must stay unchanged until the step is collected) or
+ * NULL for the batch's input buffers. sse_batch_step_wait() blocks until the oldest
+ * enqueued step is done and fills out (may be NULL) with its report, as sse_batch_step()
+ * does. At most two steps may be enqueued and not yet collected: a third
+ * sse_batch_step_async(), a wait with none enqueued, and sse_batch_step, _load, _tune,
+ * _configure, _set_mode, _use_graph or _reset while any is, return SSE_ERR_STATE.
+ * Errors: INVALID_PARAM, CAPACITY, STATE, CUDA (step_async); CAPACITY, STATE, TIMEOUT, CUDA
+ * (step_wait). */
+SSE_API int sse_batch_step_async(sse_batch* b, const uint32_t* const* d_pairs, const uint64_t* h_counts);
+SSE_API int sse_batch_step_wait(sse_batch* b, sse_report* out);
+
+/* Steps enqueued by sse_batch_step_async() and not yet collected (0, 1 or 2). */
+SSE_API int sse_batch_pending(const sse_batch* b);
+
 /* Kernels executed by the batch's steps so far. */
 SSE_API uint64_t sse_batch_kernel_launches(const sse_batch* b);
 

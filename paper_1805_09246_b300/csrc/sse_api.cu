@@ -823,7 +823,8 @@ int ensure_report_stage(sse_handle* h) {
 
 // Report of a finished close from the stage (and, beyond report_stage_n entries, from the
 // device buffers): counters into the statistics, entries into out.
-int collect_staged(sse_handle* h, const uint32_t* sorted, uint64_t slice, sse_report* out);
+int collect_staged(sse_handle* h, const uint32_t* sorted, uint64_t slice, sse_report* out, const uint8_t* stage,
+                   uint32_t stage_n);
 
 int close_graph_launch(sse_handle* h) {
   if (!h->close_exec) {
@@ -872,12 +873,13 @@ int close_graph_launch(sse_handle* h) {
 int close_graph_collect(sse_handle* h, sse_report* out) {
   h->close_pending = 0;
   SSE_CUDA(h, cudaEventSynchronize(h->close_done));
-  return collect_staged(h, h->close_sorted, h->close_pending_slice, out);
+  return collect_staged(h, h->close_sorted, h->close_pending_slice, out, h->report_stage, h->report_stage_n);
 }
 
-int collect_staged(sse_handle* h, const uint32_t* sorted, uint64_t slice, sse_report* out) {
+int collect_staged(sse_handle* h, const uint32_t* sorted, uint64_t slice, sse_report* out, const uint8_t* stage,
+                   uint32_t stage_n) {
   CloseScratch hs;
-  memcpy(&hs, h->report_stage, sizeof(hs));  // written by k_report before the synchronisation
+  memcpy(&hs, stage, sizeof(hs));  // written by k_report before the synchronisation
   const uint32_t n_found = hs.n_cand;
   const uint32_t n_kept = std::min(n_found, h->cand_cap);
   int status = n_found > h->cand_cap ? SSE_ERR_CAPACITY : SSE_OK;
@@ -897,9 +899,9 @@ int collect_staged(sse_handle* h, const uint32_t* sorted, uint64_t slice, sse_re
     const uint32_t n_copy = std::min(n_kept, out->cap);
     out->truncated = (n_found > n_copy) ? 1u : 0u;
     if (n_kept > out->cap) status = SSE_ERR_CAPACITY;
-    const uint32_t staged = std::min(n_copy, h->report_stage_n);
-    const size_t n = h->report_stage_n;
-    const uint8_t* st = h->report_stage + sizeof(CloseScratch);
+    const uint32_t staged = std::min(n_copy, stage_n);
+    const size_t n = stage_n;
+    const uint8_t* st = stage + sizeof(CloseScratch);
     if (out->hosts) memcpy(out->hosts, st, (size_t)staged * 4);
     if (out->est) memcpy(out->est, st + n * 4, (size_t)staged * 4);
     if (out->flags) memcpy(out->flags, st + n * 8, staged);
@@ -1174,16 +1176,26 @@ struct sse_batch {
   sse_handle* global = nullptr;
   uint64_t capacity = 0;      // pairs per router input buffer
   uint32_t* inputs = nullptr; // n * capacity pairs
-  RouterInputs* d_in = nullptr;  // per-step input pointers and counts (device)
-  RouterInputs* h_in = nullptr;  // pinned copy, read by the step's copy node
+  RouterInputs* d_in = nullptr;      // per-step input pointers and counts (device)
+  RouterInputs* h_in[2] = {};        // pinned copies, one per step parity
+  uint8_t* stage[2] = {};            // page-locked, mapped report stages, one per step parity
+  uint8_t* stage_dev[2] = {};
+  uint32_t stage_n = 0;              // report entries per stage (the candidate capacity)
+  cudaEvent_t done[2] = {};          // recorded after each step, per parity
+  uint64_t issued = 0;               // steps launched
+  int pending = 0;                   // launched steps whose report is not collected (<= 2)
+  struct Pending {
+    uint64_t slice;
+    int mode;
+  } pend[2] = {};
   uint32_t* tile_next = nullptr;
   uint32_t item_pairs = 1u << 20;
   int unroll = 4;
   RouterTable rt;
   int use_graph = 1;
   int mode = SSE_BATCH_DETECT;
-  cudaGraph_t graph[6] = {};     // one captured step per (mode, routers expire)
-  cudaGraphExec_t exec[6] = {};
+  cudaGraph_t graph[12] = {};    // one captured step per (mode, routers expire, parity)
+  cudaGraphExec_t exec[12] = {};
   bool expire_now = false;       // this step expires the routers' old cells
   uint32_t since_expire = 0;     // steps since the routers were last expired
   uint32_t* sorted = nullptr;     // global's sorted candidates (fixed per configuration)
@@ -1197,7 +1209,7 @@ using RoutersKernel = void (*)(KParams, TileGeometry, RouterTable, int, uint64_t
                                uint32_t*, const uint32_t*, uint8_t*);
 
 void drop_graphs(sse_batch* b) {
-  for (int m = 0; m < 6; ++m) {
+  for (int m = 0; m < 12; ++m) {
     if (b->exec[m]) cudaGraphExecDestroy(b->exec[m]);
     if (b->graph[m]) cudaGraphDestroy(b->graph[m]);
     b->exec[m] = nullptr;
@@ -1216,7 +1228,6 @@ RoutersKernel routers_kernel(int unroll, bool whole) {
 // the routers (Algorithms 2 and 7) gives — without reading every router's state.
 int batch_enqueue_update(sse_batch* b) {
   sse_handle* g = b->global;
-  SSE_CUDA(g, cudaMemcpyAsync(b->d_in, b->h_in, sizeof(RouterInputs), cudaMemcpyHostToDevice, b->stream));
   const TileGeometry& tg = g->tiles;
   SSE_CUDA(g, cudaMemsetAsync(b->tile_next, 0, tg.tiles * sizeof(uint32_t), b->stream));
   const uint32_t per_tile = std::max<uint32_t>(1u, (uint32_t)g->num_sms / tg.tiles);
@@ -1240,7 +1251,7 @@ int batch_enqueue_update(sse_batch* b) {
 // One slice: update all routers, merge them (with their expiry) into the global estimator,
 // detect on it, and advance every clock (SSE_BATCH_DETECT); see sse_batch_set_mode for the
 // other modes.
-int batch_enqueue_step(sse_batch* b) {
+int batch_enqueue_step(sse_batch* b, int parity) {
   sse_handle* g = b->global;
   int rc = batch_enqueue_update(b);
   if (rc || b->mode == SSE_BATCH_SCAN) return rc;
@@ -1253,8 +1264,8 @@ int batch_enqueue_step(sse_batch* b) {
   if (detect) {
     rc = close_enqueue(g, &b->sorted, false);
     if (rc) return rc;
-    k_report<<<8, 256, 0, b->stream>>>(g->scratch, b->sorted, g->est, g->flags, g->cand_cap, g->report_stage_n,
-                                       g->report_stage_dev, nullptr, 0u);
+    k_report<<<8, 256, 0, b->stream>>>(g->scratch, b->sorted, g->est, g->flags, g->cand_cap, b->stage_n,
+                                       b->stage_dev[parity], nullptr, 0u);
     SSE_LAUNCHED(g);
   }
   ClockList cl;
@@ -1278,7 +1289,11 @@ void sse_batch_destroy(sse_batch* b) {
   cudaFree(b->inputs);
   cudaFree(b->d_in);
   cudaFree(b->tile_next);
-  if (b->h_in) cudaFreeHost(b->h_in);
+  for (int i = 0; i < 2; ++i) {
+    if (b->h_in[i]) cudaFreeHost(b->h_in[i]);
+    if (b->stage[i]) cudaFreeHost(b->stage[i]);
+    if (b->done[i]) cudaEventDestroy(b->done[i]);
+  }
   if (b->stream) cudaStreamDestroy(b->stream);
   delete b;
 }
@@ -1308,7 +1323,8 @@ int sse_batch_create(const sse_params* p, int n_routers, uint64_t capacity_pairs
     const bool ok = cudaMalloc(&b->inputs, (uint64_t)n_routers * capacity_pairs * 8) == cudaSuccess &&
                     cudaMalloc(&b->d_in, sizeof(RouterInputs)) == cudaSuccess &&
                     cudaMalloc(&b->tile_next, b->global->tiles.tiles * sizeof(uint32_t)) == cudaSuccess &&
-                    cudaMallocHost(&b->h_in, sizeof(RouterInputs)) == cudaSuccess;
+                    cudaMallocHost(&b->h_in[0], sizeof(RouterInputs)) == cudaSuccess &&
+                    cudaMallocHost(&b->h_in[1], sizeof(RouterInputs)) == cudaSuccess;
     if (!ok) {
       cudaGetLastError();
       rc = SSE_ERR_OOM;
@@ -1331,8 +1347,20 @@ int sse_batch_create(const sse_params* p, int n_routers, uint64_t capacity_pairs
     b->rt.state[r] = b->router[r]->state;
     b->rt.gbits[r] = b->router[r]->sle_bits;
   }
-  memset(b->h_in, 0, sizeof(RouterInputs));
-  rc = ensure_report_stage(b->global);  // the step's report kernel writes here
+  memset(b->h_in[0], 0, sizeof(RouterInputs));
+  memset(b->h_in[1], 0, sizeof(RouterInputs));
+  // the step's report kernel writes the whole report into the stage of the step's parity,
+  // so a step may run while the previous step's report is read
+  b->stage_n = b->global->cand_cap;
+  for (int i = 0; i < 2 && rc == SSE_OK; ++i) {
+    if (cudaHostAlloc(&b->stage[i], sizeof(CloseScratch) + (size_t)b->stage_n * 9, cudaHostAllocMapped) !=
+            cudaSuccess ||
+        cudaHostGetDevicePointer(reinterpret_cast<void**>(&b->stage_dev[i]), b->stage[i], 0) != cudaSuccess ||
+        cudaEventCreateWithFlags(&b->done[i], cudaEventDisableTiming) != cudaSuccess) {
+      cudaGetLastError();
+      rc = SSE_ERR_OOM;
+    }
+  }
   if (rc != SSE_OK) {
     sse_batch_destroy(b);
     return rc;
@@ -1350,6 +1378,7 @@ void* sse_batch_stream(sse_batch* b) { return b ? (void*)b->stream : nullptr; }
 
 int sse_batch_load(sse_batch* b, int router, const uint32_t* pairs, uint64_t n_pairs, int from_host) {
   if (!b || router < 0 || router >= b->n || (!pairs && n_pairs)) return SSE_ERR_INVALID_PARAM;
+  if (b->pending) return SSE_ERR_STATE;
   if (n_pairs > b->capacity) return SSE_ERR_CAPACITY;
   if (!n_pairs) return SSE_OK;
   SSE_CUDA(b->global, cudaMemcpyAsync(sse_batch_input(b, router), pairs, n_pairs * 8,
@@ -1372,18 +1401,21 @@ int sse_batch_global(sse_batch* b, sse_handle** out) {
 
 int sse_batch_use_graph(sse_batch* b, int enable) {
   if (!b) return SSE_ERR_INVALID_PARAM;
+  if (b->pending) return SSE_ERR_STATE;
   b->use_graph = enable ? 1 : 0;
   return SSE_OK;
 }
 
 int sse_batch_set_mode(sse_batch* b, int mode) {
   if (!b || mode < SSE_BATCH_DETECT || mode > SSE_BATCH_SCAN) return SSE_ERR_INVALID_PARAM;
+  if (b->pending) return SSE_ERR_STATE;
   b->mode = mode;
   return SSE_OK;
 }
 
 int sse_batch_reset(sse_batch* b) {
   if (!b) return SSE_ERR_INVALID_PARAM;
+  if (b->pending) return SSE_ERR_STATE;
   b->since_expire = 0;
   for (int r = 0; r < b->n; ++r) {
     const int rc = sse_reset(b->router[r]);
@@ -1395,6 +1427,7 @@ int sse_batch_reset(sse_batch* b) {
 int sse_batch_configure(sse_batch* b, uint32_t item_pairs, int unroll) {
   if (!b || item_pairs < 1024 || item_pairs > (1u << 30) || (unroll != 2 && unroll != 4 && unroll != 8))
     return SSE_ERR_INVALID_PARAM;
+  if (b->pending) return SSE_ERR_STATE;
   b->item_pairs = item_pairs;
   b->unroll = unroll;
   drop_graphs(b);  // the captured graphs hold the old launch configuration
@@ -1405,28 +1438,36 @@ int sse_batch_configure(sse_batch* b, uint32_t item_pairs, int unroll) {
 
 namespace {
 
-int batch_step(sse_batch* b, const uint32_t* const* d_pairs, const uint64_t* h_counts, sse_report* out) {
+// Launches one step (inputs from d_pairs) behind any earlier one on the batch's stream and
+// returns; batch_collect() waits for the oldest launched step and reads its report. The
+// slice bookkeeping is done at launch (it depends on nothing the step computes).
+int batch_launch(sse_batch* b, const uint32_t* const* d_pairs, const uint64_t* h_counts) {
   sse_handle* g = b->global;
   if (g->sticky) return g->sticky;
+  if (b->pending >= 2) return SSE_ERR_STATE;
   for (int r = 0; r < b->n; ++r) {
     if (b->router[r]->sticky) return b->router[r]->sticky;
     if (h_counts[r] && (!d_pairs[r] || (reinterpret_cast<uintptr_t>(d_pairs[r]) & 7u))) return SSE_ERR_INVALID_PARAM;
   }
-  for (int r = 0; r < b->n; ++r) {  // the step's copy node reads this pinned table
-    b->h_in->pairs[r] = reinterpret_cast<const uint2*>(d_pairs[r]);
-    b->h_in->counts[r] = h_counts[r];
+  const int parity = (int)(b->issued & 1);
+  RouterInputs* in = b->h_in[parity];  // free: the step that last used it has been collected
+  for (int r = 0; r < b->n; ++r) {
+    in->pairs[r] = reinterpret_cast<const uint2*>(d_pairs[r]);
+    in->counts[r] = h_counts[r];
   }
   // A router cell stamped at slice t leaves the window at t + k and would look active again
   // when its stamp comes round at t + 255; expiring the routers every 254 - k slices clears
   // every such cell in between (the global estimator expires its own cells at every close).
   const uint32_t every = g->p.k < 253 ? 254u - g->p.k : 1u;
   b->expire_now = b->mode != SSE_BATCH_SCAN && b->since_expire + 1 >= every;
+  SSE_CUDA(g, cudaMemcpyAsync(b->d_in, in, sizeof(RouterInputs), cudaMemcpyHostToDevice, b->stream));
+  const int kind = b->mode * 2 + (b->expire_now ? 1 : 0);
   const uint64_t launches0 = g->launches;
   if (b->use_graph) {
-    const int m = b->mode * 2 + (b->expire_now ? 1 : 0);
+    const int m = kind * 2 + parity;
     if (!b->exec[m]) {
       SSE_CUDA(g, cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
-      const int rc = batch_enqueue_step(b);
+      const int rc = batch_enqueue_step(b, parity);
       cudaGraph_t graph = nullptr;
       const cudaError_t e = cudaStreamEndCapture(b->stream, &graph);
       if (rc) {
@@ -1436,34 +1477,48 @@ int batch_step(sse_batch* b, const uint32_t* const* d_pairs, const uint64_t* h_c
       SSE_CUDA(g, e);
       b->graph[m] = graph;
       SSE_CUDA(g, cudaGraphInstantiate(&b->exec[m], b->graph[m], 0));
-      b->kernels_per_step[m] = g->launches - launches0;
+      b->kernels_per_step[kind] = g->launches - launches0;
       g->launches = launches0;
     }
     SSE_CUDA(g, cudaGraphLaunch(b->exec[m], b->stream));
   } else {
-    const int rc = batch_enqueue_step(b);
+    const int rc = batch_enqueue_step(b, parity);
     if (rc) return rc;
-    b->kernels_per_step[b->mode * 2 + (b->expire_now ? 1 : 0)] = g->launches - launches0;
+    b->kernels_per_step[kind] = g->launches - launches0;
     g->launches = launches0;
   }
-  b->launches += b->kernels_per_step[b->mode * 2 + (b->expire_now ? 1 : 0)];
-  int status = SSE_OK;
-  if (b->mode == SSE_BATCH_DETECT) {
-    SSE_CUDA(g, cudaStreamSynchronize(b->stream));
-    status = collect_staged(g, b->sorted, g->slice, out);
-  } else {
-    SSE_CUDA(g, cudaStreamSynchronize(b->stream));
-    if (out) {
-      out->slice = g->slice;
-      out->n_candidates = out->n_super = out->truncated = 0;
-    }
-    if (b->mode == SSE_BATCH_SCAN) return SSE_OK;  // the slice stays open
+  SSE_CUDA(g, cudaEventRecord(b->done[parity], b->stream));
+  b->launches += b->kernels_per_step[kind];
+  b->pend[parity] = sse_batch::Pending{g->slice, b->mode};
+  b->issued += 1;
+  b->pending += 1;
+  if (b->mode != SSE_BATCH_SCAN) {  // otherwise the slice stays open
+    b->since_expire = b->expire_now ? 0 : b->since_expire + 1;
+    for (int r = 0; r < b->n; ++r) b->router[r]->slice += 1;
+    g->slice += 1;
   }
-  if (status != SSE_OK && status != SSE_ERR_CAPACITY) return status;
-  b->since_expire = b->expire_now ? 0 : b->since_expire + 1;
-  for (int r = 0; r < b->n; ++r) b->router[r]->slice += 1;
-  g->slice += 1;
-  return status;
+  return SSE_OK;
+}
+
+int batch_collect(sse_batch* b, sse_report* out) {
+  sse_handle* g = b->global;
+  if (b->pending == 0) return SSE_ERR_STATE;
+  const int parity = (int)((b->issued - (uint64_t)b->pending) & 1);
+  b->pending -= 1;
+  SSE_CUDA(g, cudaEventSynchronize(b->done[parity]));
+  const sse_batch::Pending& st = b->pend[parity];
+  if (st.mode == SSE_BATCH_DETECT) return collect_staged(g, b->sorted, st.slice, out, b->stage[parity], b->stage_n);
+  if (out) {
+    out->slice = st.slice;
+    out->n_candidates = out->n_super = out->truncated = 0;
+  }
+  return SSE_OK;
+}
+
+int batch_step(sse_batch* b, const uint32_t* const* d_pairs, const uint64_t* h_counts, sse_report* out) {
+  if (b->pending) return SSE_ERR_STATE;
+  const int rc = batch_launch(b, d_pairs, h_counts);
+  return rc ? rc : batch_collect(b, out);
 }
 
 }  // namespace
@@ -1485,15 +1540,34 @@ int sse_batch_step_from(sse_batch* b, const uint32_t* const* d_pairs, const uint
   return batch_step(b, d_pairs, h_counts, out);
 }
 
+int sse_batch_step_async(sse_batch* b, const uint32_t* const* d_pairs, const uint64_t* h_counts) {
+  if (!b || !h_counts) return SSE_ERR_INVALID_PARAM;
+  const uint32_t* ptrs[kMaxRouters];
+  for (int r = 0; r < b->n; ++r) {
+    if (!d_pairs && h_counts[r] > b->capacity) return SSE_ERR_CAPACITY;
+    ptrs[r] = d_pairs ? d_pairs[r] : sse_batch_input(b, r);
+  }
+  return batch_launch(b, ptrs, h_counts);
+}
+
+int sse_batch_step_wait(sse_batch* b, sse_report* out) {
+  if (!b) return SSE_ERR_INVALID_PARAM;
+  return batch_collect(b, out);
+}
+
+int sse_batch_pending(const sse_batch* b) { return b ? b->pending : 0; }
+
 int sse_batch_tune(sse_batch* b, const uint32_t* const* d_pairs, const uint64_t* h_counts, int reps, float* times_ms,
                    int* chosen) {
   if (!b || !h_counts || reps < 1) return SSE_ERR_INVALID_PARAM;
+  if (b->pending) return SSE_ERR_STATE;
   sse_handle* g = b->global;
   for (int r = 0; r < b->n; ++r) {
     if (!d_pairs && h_counts[r] > b->capacity) return SSE_ERR_CAPACITY;
-    b->h_in->pairs[r] = reinterpret_cast<const uint2*>(d_pairs ? d_pairs[r] : sse_batch_input(b, r));
-    b->h_in->counts[r] = h_counts[r];
+    b->h_in[0]->pairs[r] = reinterpret_cast<const uint2*>(d_pairs ? d_pairs[r] : sse_batch_input(b, r));
+    b->h_in[0]->counts[r] = h_counts[r];
   }
+  SSE_CUDA(g, cudaMemcpyAsync(b->d_in, b->h_in[0], sizeof(RouterInputs), cudaMemcpyHostToDevice, b->stream));
   const uint32_t items[3] = {1u << 18, 1u << 20, 1u << 22};
   const int unrolls[3] = {2, 4, 8};
   cudaEvent_t e0, e1;

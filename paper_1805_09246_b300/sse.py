@@ -151,6 +151,9 @@ def lib() -> ctypes.CDLL:
             "sse_batch_tune": (i32, [vp, vp, vp, i32, vp, ctypes.POINTER(i32)]),
             "sse_batch_step": (i32, [vp, vp, vp]),
             "sse_batch_step_from": (i32, [vp, vp, vp, vp]),
+            "sse_batch_step_async": (i32, [vp, vp, vp]),
+            "sse_batch_step_wait": (i32, [vp, vp]),
+            "sse_batch_pending": (i32, [vp]),
             "sse_batch_kernel_launches": (u64, [vp]),
             "sse_server_config_default": (None, [vp]),
             "sse_server_create": (i32, [vp, vp, ctypes.POINTER(vp)]),
@@ -527,6 +530,24 @@ class Batch:
                                         ctypes.byref(chosen)), "sse_batch_tune")
         return chosen.value, [float(t) for t in times]
 
+    def _report_buffers(self, cap: int):
+        """(hosts, est, flags) arrays of `cap` entries, one set per step parity, reused."""
+        sets = getattr(self, "_report_bufs", None)
+        if sets is None or len(sets[0][0]) != cap:
+            sets = self._report_bufs = [(np.empty(cap, np.uint32), np.empty(cap, np.float32), np.empty(cap, np.uint8))
+                                        for _ in range(2)]
+        self._parity = getattr(self, "_parity", 0) ^ 1
+        return sets[self._parity]
+
+    def _report(self, rc: int, rep, bufs, cap: int, what: str) -> Report:
+        if rc != SSE_OK and rc != ERR_CAPACITY:
+            _check(rc, what)
+        hosts, est, flags = bufs
+        m = min(rep.n_candidates, cap, self.params.max_candidates)
+        return Report(slice=rep.slice, n_candidates=rep.n_candidates, n_super=rep.n_super,
+                      truncated=bool(rep.truncated), hosts=hosts[:m].copy(), est=est[:m].copy(),
+                      flags=flags[:m].copy(), status=rc)
+
     def step(self, counts=None, cap: int | None = None, inputs=None) -> Report:
         """One slice. Without `inputs`, router r scans counts[r] pairs of its loaded input
         buffer; with `inputs` (one CUDA tensor (n_r, 2) per router, already written), it scans
@@ -536,9 +557,7 @@ class Batch:
             _torch().cuda.current_stream().synchronize()  # producers finish before the batch stream reads
         c = np.ascontiguousarray(counts, dtype=np.uint64)
         cap = self.params.max_candidates if cap is None else cap
-        bufs = getattr(self, "_report_bufs", None)
-        if bufs is None or len(bufs[0]) != cap:  # reused across steps
-            bufs = self._report_bufs = (np.empty(cap, np.uint32), np.empty(cap, np.float32), np.empty(cap, np.uint8))
+        bufs = self._report_buffers(cap)
         hosts, est, flags = bufs
         rep = _Report(0, 0, 0, cap, 0, hosts.ctypes.data, est.ctypes.data, flags.ctypes.data)
         if inputs is not None:
@@ -546,12 +565,31 @@ class Batch:
                                                ctypes.byref(rep))
         else:
             rc = self._lib.sse_batch_step(self._b, ctypes.c_void_p(c.ctypes.data), ctypes.byref(rep))
-        if rc != SSE_OK and rc != ERR_CAPACITY:
-            _check(rc, "sse_batch_step")
-        m = min(rep.n_candidates, cap, self.params.max_candidates)
-        return Report(slice=rep.slice, n_candidates=rep.n_candidates, n_super=rep.n_super,
-                      truncated=bool(rep.truncated), hosts=hosts[:m].copy(), est=est[:m].copy(),
-                      flags=flags[:m].copy(), status=rc)
+        return self._report(rc, rep, bufs, cap, "sse_batch_step")
+
+    def step_async(self, inputs=None, counts=None) -> None:
+        """Enqueue one slice (see sse_batch_step_async) and return; `inputs`: one CUDA tensor
+        (n_r, 2) per router, unchanged until the step is collected, or None for the loaded
+        input buffers with `counts`. At most two steps may wait for step_wait()."""
+        if inputs is not None:
+            counts = [t.numel() // 2 for t in inputs]
+            _torch().cuda.current_stream().synchronize()  # producers finish before the batch stream reads
+        c = np.ascontiguousarray(counts, dtype=np.uint64)
+        _check(self._lib.sse_batch_step_async(self._b, self._ptrs(inputs), ctypes.c_void_p(c.ctypes.data)),
+               "sse_batch_step_async")
+
+    def step_wait(self, cap: int | None = None) -> Report:
+        """The report of the oldest enqueued slice (blocks until it is on the host)."""
+        cap = self.params.max_candidates if cap is None else cap
+        bufs = self._report_buffers(cap)
+        hosts, est, flags = bufs
+        rep = _Report(0, 0, 0, cap, 0, hosts.ctypes.data, est.ctypes.data, flags.ctypes.data)
+        rc = self._lib.sse_batch_step_wait(self._b, ctypes.byref(rep))
+        return self._report(rc, rep, bufs, cap, "sse_batch_step_wait")
+
+    @property
+    def pending(self) -> int:
+        return int(self._lib.sse_batch_pending(self._b))
 
     def router(self, r: int) -> Estimator:
         if r not in self._views:

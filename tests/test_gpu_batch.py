@@ -145,3 +145,44 @@ def test_batch_router_expiry_across_stamp_cycle():
             compare_state(batch.global_estimator(), og, p, t)
             for r in range(R):
                 compare_state(batch.router(r), orcs[r], p, t)
+
+
+@pytest.mark.parametrize("graph", [True, False])
+def test_batch_async_steps_equal_synchronous_steps(graph):
+    """Steps enqueued two ahead of their reports (sse_batch_step_async / _wait) give the
+    reports, slices and state of synchronous steps; calls that would race a pending step
+    are refused with STATE."""
+    S = sse()
+    p = S.Params(seed=35)
+    R, T = 4, 7
+    slices = router_traffic(R, T, seed=35)
+    dev = [[helpers.to_device(x) for x in per_router] for per_router in slices]
+    torch.cuda.synchronize()
+    cap = max(len(x) for s in slices for x in s)
+    a = S.Batch(p, R, cap, use_graph=graph)
+    b = S.Batch(p, R, cap, use_graph=graph)
+    sync = [a.step(inputs=dev[t]) for t in range(T)]
+    got = []
+    b.step_async(inputs=dev[0])
+    for t in range(1, T):
+        b.step_async(inputs=dev[t])
+        assert b.pending == 2
+        with pytest.raises(S.SSEError):
+            b.step_async(inputs=dev[t])  # a third pending step
+        with pytest.raises(S.SSEError):
+            b.set_mode(S.BATCH_ROUTERS)
+        got.append(b.step_wait())
+    got.append(b.step_wait())
+    assert b.pending == 0
+    with pytest.raises(S.SSEError):
+        b.step_wait()  # nothing pending
+    for x, y in zip(sync, got):
+        assert x.slice == y.slice and x.n_candidates == y.n_candidates and x.n_super == y.n_super
+        assert np.array_equal(x.hosts, y.hosts) and np.array_equal(x.est, y.est)
+        assert np.array_equal(x.flags, y.flags)
+    assert a.global_estimator().slice == b.global_estimator().slice == T
+    for x, y in zip(a.global_estimator().read_stamps(), b.global_estimator().read_stamps()):
+        assert np.array_equal(x, y)
+    for r in range(R):
+        for x, y in zip(a.router(r).read_stamps(), b.router(r).read_stamps()):
+            assert np.array_equal(x, y)
