@@ -46,7 +46,8 @@ def parse():
     ap.add_argument("--mode", type=int, default=0, help="update mode: 0 auto, 1 direct, 2 tiled")
     ap.add_argument("--prefill", type=int, default=PREFILL, help="slices scanned before warm-up")
     ap.add_argument("--distinct", type=int, default=DISTINCT, help="device-resident step inputs")
-    ap.add_argument("--workload", default="core_link", choices=["core_link", "edge_routers", "serving", "learned"])
+    ap.add_argument("--workload", default="core_link",
+                    choices=["core_link", "paper_params", "edge_routers", "serving", "learned"])
     ap.add_argument("--learn-train", type=int, default=1_000_000, help="training hosts (learned workload)")
     ap.add_argument("--learn-test", type=int, default=100_000, help="held-out hosts (learned workload)")
     ap.add_argument("--serve-seconds", type=float, default=0.5, help="virtual seconds of serving traffic")
@@ -449,7 +450,13 @@ def main():
         pg = dist
 
     tr = make_traffic(rank)
-    params = sse.core_link_params(k=8, seed=0)
+    # paper_params: the same core-link traffic through the estimator of the paper's
+    # experiments (q = q' = 17, eta' = 2^14, 16-bit stamps, window k = 300 slices)
+    paper = args.workload == "paper_params"
+    params = sse.paper_params(k=300) if paper else sse.core_link_params(k=8, seed=0)
+    # the paper's estimator is sized for its trace (1-second slices of an OC192 link, about
+    # 2^21 pairs): its slices are the first 2^21 pairs of each core-link slice
+    n_slice = (1 << 21) if paper else PAIRS_PER_SLICE
     stream = torch.cuda.Stream()  # the estimator's own (non-blocking) stream
     est = sse.Estimator(params, stream=stream)
     if args.mode:
@@ -459,7 +466,7 @@ def main():
 
     # inputs: PREFILL slices for the window, then DISTINCT slices the steps cycle through
     prefill, distinct = args.prefill, max(1, args.distinct)
-    host = [tr.slice(0, t) for t in range(prefill + distinct)]
+    host = [np.ascontiguousarray(tr.slice(0, t)[:n_slice]) for t in range(prefill + distinct)]
     dev_slices = [torch.from_numpy(h.view(np.int32)).to(dev) for h in host]
     torch.cuda.synchronize()
     for t in range(prefill):
@@ -541,7 +548,7 @@ def main():
         close_ms.append((time.perf_counter() - t0) * 1e3)
         close_dev.append((a, b))
     torch.cuda.synchronize()
-    total_pairs = args.steps * PAIRS_PER_SLICE * world
+    total_pairs = args.steps * n_slice * world
     value = total_pairs / elapsed_s / 1e9
 
     # ---- end to end through the public API: pinned host slices -> report on the host
@@ -572,37 +579,44 @@ def main():
             d2h += 64 + r.n_candidates * 9  # report header + hosts/est/flags
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0
-        e2e = {"value": round(k_e2e * PAIRS_PER_SLICE * world / dt / 1e9, 4), "unit": UNIT,
-               "h2d_bytes_per_step": PAIRS_PER_SLICE * PAIR_BYTES, "d2h_bytes_per_step": int(d2h / k_e2e),
+        e2e = {"value": round(k_e2e * n_slice * world / dt / 1e9, 4), "unit": UNIT,
+               "h2d_bytes_per_step": n_slice * PAIR_BYTES, "d2h_bytes_per_step": int(d2h / k_e2e),
                "steps": k_e2e}
         del e2e_est, pinned
 
     hbm_peak, peak_kind = peaks()
-    achieved = PAIRS_PER_SLICE * PAIR_BYTES / (upd_ms / 1e3) / 1e9
+    achieved = n_slice * PAIR_BYTES / (upd_ms / 1e3) / 1e9
     # DRAM bytes (read + write) of one k_update_tiled<8, 0, 1> launch on this slice, from an ncu
     # capture of this kernel version (dram__bytes_read.sum + dram__bytes_write.sum); only
     # reported when that variant is the one timed
-    traffic = TILED8_DRAM_BYTES if tuned == 3 else None
+    traffic = TILED8_DRAM_BYTES if tuned == 3 and not paper else None
     roofline = {"bound": "hbm", "kernel": "sse update (k_update_tiled + k_apply_bits)", "achieved": round(achieved, 2),
                 "peak": hbm_peak, "unit": "GB/s", "frac": round(achieved / hbm_peak, 4), "traffic": traffic,
                 "peak_source": f"{peak_kind} hbm_gbs",
-                "algorithmic_bytes_per_launch": PAIRS_PER_SLICE * PAIR_BYTES,
+                "algorithmic_bytes_per_launch": n_slice * PAIR_BYTES,
                 "binding_unit": "SM L1/shared-memory pipe (ncu l1tex throughput 88 % on k_update_tiled)"}
 
     if rank != 0:
         return
-    cpu = None if args.no_cpu else cpu_baseline([host[t] for t in range(8)])
+    cpu = None if args.no_cpu or paper else cpu_baseline([host[t] for t in range(8)])
     close_sorted = sorted(close_ms)
     out = {
         "metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(elapsed_s / args.steps * 1e3, 4), "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
-        "config": {"workload": "core_link: 2^25 pairs/slice, 16M-host Zipf(1.05), 200 planted super points; "
+        "scaling": "weak", "vs_baseline": None, "dtype": "u16" if paper else "u8", "data": "synthetic",
+        "config": {"workload": ("paper_params: core-link traffic cut to 2^21 pairs/slice (16M-host Zipf(1.05)); the paper's "
+                                "estimator q=17, r=5, delta=5, SLEA r'=5 x (2^17 SLEs, eta'=2^14, delta'=16), "
+                                "16-bit stamps, k=300, theta=1024")
+                               if paper else
+                               "core_link: 2^25 pairs/slice, 16M-host Zipf(1.05), 200 planted super points; "
                                "q=20, r=5, SLEA r'=5 x (2^16 SLEs, eta'=4096, delta'=16), k=8, theta=1024",
-                   "pairs_per_step": PAIRS_PER_SLICE, "l2": "inputs larger than L2 (256 MiB per step)",
+                   "pairs_per_step": n_slice,
+                   "l2": ("16 distinct 16 MiB slices cycled (256 MiB): a step's input was evicted since its last use"
+                          if paper else "inputs larger than L2 (256 MiB per step)"),
+                   "prefill_slices": prefill,
                    "update_mode": args.mode, "update_variant": tuned,
                    "variant_ms": [round(t, 4) for t in tune_ms]},
-        "update_gpkts": round(PAIRS_PER_SLICE / (upd_ms / 1e3) / 1e9, 3),
+        "update_gpkts": round(n_slice / (upd_ms / 1e3) / 1e9, 3),
         "update_ms": round(upd_ms, 4),
         "close_ms_p50": round(close_sorted[len(close_sorted) // 2], 4),
         "close_ms_p99": round(close_sorted[min(len(close_sorted) - 1, int(0.99 * len(close_sorted)))], 4),

@@ -44,16 +44,27 @@ __device__ __forceinline__ void emit_candidate(uint32_t aip, uint32_t* cand, uin
 }
 
 // Regain the hosts of a complete chain B[1..r-1] (bits [delta, 32) fixed).
+// With the multiply-add-shift RHFG[0], the top q bits of a*x + b (mod 2^64) equal he_0
+// exactly when a*x + b - (he_0 << (64 - q)) (mod 2^64) is below 2^(64-q); stepping x through
+// high | low, low = 0, 1, ..., adds a each time, so each low costs a compare and an add.
 __device__ __forceinline__ void regain(const KParams& p, uint32_t he0, const uint32_t* B, uint32_t* cand,
                                        uint32_t* n_cand, uint32_t cap, uint32_t* overflow) {
   uint64_t high = (uint64_t)B[1] << p.delta;
   for (uint32_t i = 2; i < p.r; ++i)
     high |= (uint64_t)(B[i] >> (p.q - p.delta)) << (i * p.delta + p.q - p.delta);
-  for (uint32_t low = 0; low < (1u << p.delta); ++low) {
-    const uint32_t aip = (uint32_t)(high | low);
-    if (rhfg0(p, aip) != he0) continue;
-    emit_candidate(aip, cand, n_cand, cap, overflow);
+  if (p.tab) {
+    for (uint32_t low = 0; low < (1u << p.delta); ++low) {
+      const uint32_t aip = (uint32_t)(high | low);
+      if (rhfg0(p, aip) != he0) continue;
+      emit_candidate(aip, cand, n_cand, cap, overflow);
+    }
+    return;
   }
+  const uint64_t a = p.key_a[kR0];
+  const uint64_t width = 1ull << (64 - p.q);
+  uint64_t v = a * (uint32_t)high + p.key_b[kR0] - ((uint64_t)he0 << (64 - p.q));
+  for (uint32_t low = 0; low < (1u << p.delta); ++low, v += a)
+    if (v < width) emit_candidate((uint32_t)high | low, cand, n_cand, cap, overflow);
 }
 
 // Rows 3..r-1 of a chain whose rows 0..2 are hot (rare: depth-first, explicit stack).
@@ -350,7 +361,7 @@ __global__ void __launch_bounds__(256) k_report(const CloseScratch* __restrict__
 // itself). The two "any hot" bitmaps are staged in shared memory when `stage` is set; the
 // blocks are small (kJoinTiledThreads) so that several share an SM.
 constexpr int kJoinTiledThreads = 256;
-constexpr uint32_t kJoinQueueCap = 512;    // chains per block queue
+constexpr uint32_t kJoinQueueCap = 2048;   // chains per block queue (grown by the block when half full)
 constexpr uint32_t kJoinChunkMax = 256;    // he_0 per work unit
 constexpr uint32_t kJoinProbeBlock = 16;   // he_0 probed before a compaction
 constexpr uint32_t kJoinListWords = (32 + 32 * kJoinProbeBlock) / 2;  // per warp hit stack: 16-bit entries
@@ -510,6 +521,20 @@ __global__ void __launch_bounds__(kJoinTiledThreads) k_join_tiled(
         hn -= 32;
         expand(my_list[hn + lane]);
         __syncwarp();  // those entries are overwritten by the next append
+      }
+      // every 4 probe blocks: a queue at least half full is grown by all threads, so that
+      // it rarely overflows into the divergent inline growth of emit()
+      if ((j0 / kJoinProbeBlock) % 4 == 3) {
+        __syncthreads();
+        const uint32_t qn = s_qn;  // no emit runs between the barriers
+        if (qn >= kJoinQueueCap / 2) {
+          const uint32_t n = min(qn, kJoinQueueCap);
+          for (uint32_t i = threadIdx.x; i < n; i += blockDim.x)
+            grow_grouped(p, tables, qh[i], qb1[i], qb2[i], cand, n_cand, cap, overflow);
+          __syncthreads();
+          if (threadIdx.x == 0) s_qn = 0;
+        }
+        __syncthreads();
       }
     }
     if (lane < hn) expand(my_list[lane]);  // the rest, before the chunk is replaced
