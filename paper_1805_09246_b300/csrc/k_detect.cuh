@@ -730,6 +730,14 @@ __global__ void __launch_bounds__(kEstThreads, 4) k_estimate(
       age_lut[s] = a < p.k ? (uint8_t)a : 255;
     }
   const double eta2 = (double)p.eta2;
+  // Eq. 12's P = prod_i SF(i,k), SF(i,k) = active2[i] / row_len2 (Definition 4), multiplied
+  // in row order; the same for every host, so it is computed while the first gathers run
+  __shared__ double s_P;
+  if (threadIdx.x == 0) {
+    double P = 1.0;
+    for (uint32_t i = 0; i < p.r2; ++i) P = __dmul_rn(P, __ddiv_rn((double)active2[i], (double)p.row_len2));
+    s_P = P;
+  }
   for (uint32_t h = blockIdx.x; h < count; h += gridDim.x) {
     const uint32_t aip = hosts[h];
     if (threadIdx.x < p.r2) {
@@ -819,9 +827,7 @@ __global__ void __launch_bounds__(kEstThreads, 4) k_estimate(
     if (threadIdx.x == 0) {
       uint32_t U = 0;
       for (int x = 0; x < kEstThreads / 32; ++x) U += warp_u[x];
-      // Eq. 12 with SF(i,k) = active2[i] / row_len2 (Definition 4), multiplied in row order.
-      double P = 1.0;
-      for (uint32_t i = 0; i < p.r2; ++i) P = __dmul_rn(P, __ddiv_rn((double)active2[i], (double)p.row_len2));
+      const double P = s_P;  // Eq. 12
       uint8_t f = 0;
       double w;
       if (P >= 1.0) {
