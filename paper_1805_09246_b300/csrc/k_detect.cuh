@@ -400,14 +400,40 @@ __global__ void __launch_bounds__(kJoinTiledThreads) k_join_tiled(
   const uint32_t* a3 = any3;
   uint32_t* next = sm;
   if (stage) {
-    for (uint32_t w = threadIdx.x; w < aw; w += blockDim.x) next[w] = any2[w];
-    a2 = next;
-    next += any_words_staged(q, delta);
-    if (any3) {
-      for (uint32_t w = threadIdx.x; w < aw; w += blockDim.x) next[w] = any3[w];
-      a3 = next;
+    // both bitmaps with 16-byte loads, all of a thread's loads issued before its stores
+    // (the word counts are multiples of 4 from 2^(q-delta) >= 128; smaller ones word by word)
+    uint32_t* d2 = next;
+    uint32_t* d3 = next + any_words_staged(q, delta);
+    if ((aw & 3u) == 0) {
+      const uint32_t n4 = aw >> 2;
+      for (uint32_t w0 = threadIdx.x; w0 < n4; w0 += 2 * blockDim.x) {
+        uint4 v2[2], v3[2];
+#pragma unroll
+        for (uint32_t u = 0; u < 2; ++u) {
+          const uint32_t w = w0 + u * blockDim.x;
+          if (w < n4) {
+            v2[u] = reinterpret_cast<const uint4*>(any2)[w];
+            if (any3) v3[u] = reinterpret_cast<const uint4*>(any3)[w];
+          }
+        }
+#pragma unroll
+        for (uint32_t u = 0; u < 2; ++u) {
+          const uint32_t w = w0 + u * blockDim.x;
+          if (w < n4) {
+            reinterpret_cast<uint4*>(d2)[w] = v2[u];
+            if (any3) reinterpret_cast<uint4*>(d3)[w] = v3[u];
+          }
+        }
+      }
+    } else {
+      for (uint32_t w = threadIdx.x; w < aw; w += blockDim.x) {
+        d2[w] = any2[w];
+        if (any3) d3[w] = any3[w];
+      }
     }
-    next += any_words_staged(q, delta);
+    a2 = d2;
+    if (any3) a3 = d3;
+    next = d3 + any_words_staged(q, delta);
   }
   uint32_t* qh = next;
   uint32_t* qb1 = qh + kJoinQueueCap;
