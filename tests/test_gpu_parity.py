@@ -366,11 +366,12 @@ def test_many_candidates_sorted_and_capacity():
     assert np.array_equal(small.hosts, want[:1000])
 
 
-def test_conditional_sort_node_follows_the_candidate_count():
-    """The close graph sorts more than 4096 candidates in a conditional node that the rank
-    sort switches on only when needed: slices alternating between thousands of candidates
-    (planted) and a handful give the reports of the kernels launched one by one, and the
-    planted slice's candidates are the oracle's (brute force)."""
+def test_sort_paths_alternate_in_the_close_graph():
+    """The one-launch candidate sort ranks up to 4096 candidates and chunk-sorts and merges
+    more (grid barriers between the merge passes): slices alternating between thousands of
+    candidates (planted) and a handful, closed from the CUDA graph, give the reports of the
+    kernels launched one by one, and the planted slice's candidates are the oracle's (brute
+    force)."""
     S = sse()
     p = S.Params(q=20, k=2, theta=64, max_candidates=1 << 14, seed=23)
     orc = oracle.Oracle(oracle_params(p))
