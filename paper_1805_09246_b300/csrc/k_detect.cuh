@@ -498,7 +498,7 @@ __global__ void __launch_bounds__(kJoinTiledThreads) k_join_tiled(
       if (j < m0) {
         const uint32_t he0 = list0[c0 + j];
         s_he0[j] = he0;
-        s_k[j] = (he0 ^ (he0 >> delta)) & cmask;
+        s_k[j] = ((he0 ^ (he0 >> delta)) & cmask) ^ 31u;  // K(he_0) with its 5 low bits flipped
       } else {
         s_k[j] = 0;  // the probe block's padding: an in-range c, masked off after the probes
       }
@@ -514,15 +514,21 @@ __global__ void __launch_bounds__(kJoinTiledThreads) k_join_tiled(
       uint32_t hits = 0;
       if (valid) {
         // 16 probes from four broadcast vector loads; entries past the chunk (inside the
-        // kJoinChunkMax-entry array, which is a multiple of 16) are masked off below
+        // kJoinChunkMax-entry array, which is a multiple of 16) are masked off below.
+        // With c' = c ^ 31 the word is c' >> 5 and rotating it left by c' (mod 32) brings bit
+        // c mod 32 to the top; the bits are gathered first probe highest, then reversed.
         const uint4* k4 = reinterpret_cast<const uint4*>(s_k + j0);
 #pragma unroll
         for (uint32_t v = 0; v < kJoinProbeBlock / 4; ++v) {
           const uint4 kk = k4[v];
           const uint32_t c[4] = {kk.x ^ g1, kk.y ^ g1, kk.z ^ g1, kk.w ^ g1};
 #pragma unroll
-          for (uint32_t u = 0; u < 4; ++u) hits |= (__funnelshift_r(a2[c[u] >> 5], 0u, c[u]) & 1u) << (4 * v + u);
+          for (uint32_t u = 0; u < 4; ++u) {
+            const uint32_t x = a2[c[u] >> 5];
+            hits = (hits << 1) | (__funnelshift_l(x, x, c[u]) >> 31);
+          }
         }
+        hits = __brev(hits) >> (32 - kJoinProbeBlock);
         if (jn < kJoinProbeBlock) hits &= (1u << jn) - 1u;
       }
       // append this warp's hits to its hit stack (exclusive prefix sum of the per-lane
