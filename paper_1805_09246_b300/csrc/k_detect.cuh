@@ -357,9 +357,10 @@ __global__ void __launch_bounds__(256) k_report(const CloseScratch* __restrict__
 // pairs that hit are pushed on a per-warp stack (warp prefix sum), and whenever 32 wait, every
 // lane expands one: the hot SREs of the group come from the regrouped row-2 table, and each
 // chain must pass row 3's "any hot" bit before it is queued in shared memory; the block grows
-// the queued chains at the end of the work unit (a full queue makes the thread grow the chain
-// itself). The two "any hot" bitmaps are staged in shared memory when `stage` is set; the
-// blocks are small (kJoinTiledThreads) so that several share an SM.
+// the queued chains every 4 probe blocks once the queue is half full, and at the end of the
+// work unit (a full queue makes the thread grow the chain itself). The two "any hot" bitmaps
+// are staged in shared memory when `stage` is set; the blocks are small (kJoinTiledThreads)
+// so that several share an SM.
 constexpr int kJoinTiledThreads = 256;
 constexpr uint32_t kJoinQueueCap = 2048;   // chains per block queue (grown by the block when half full)
 constexpr uint32_t kJoinChunkMax = 256;    // he_0 per work unit
