@@ -37,7 +37,7 @@ PAIR_BYTES = 8
 TILED8_DRAM_BYTES = 273_642_240 + 7_437_824
 
 
-def parse():
+def parse(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=None, help="timed steps (default 200; 27 epochs for learned)")
@@ -59,7 +59,7 @@ def parse():
     ap.add_argument("--no-graph", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    args = ap.parse_args()
+    args = ap.parse_args(argv)
     if args.steps is None:
         args.steps = 27 if args.workload == "learned" else 200
     return args
@@ -70,6 +70,41 @@ def dist_env():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return rank, world, local
+
+
+def init_ranks(world: int):
+    """The process group of a multi-rank run (NCCL with GPUs, gloo without), else None."""
+    if world <= 1:
+        return None
+    import torch
+    import torch.distributed as dist
+    dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    return dist
+
+
+def barrier(pg) -> None:
+    if pg is not None:
+        pg.barrier()
+
+
+def max_over_ranks(pg, value: float, device) -> float:
+    """The largest of every rank's value (the job's time is its slowest rank's)."""
+    if pg is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(pg, value: float, device) -> float:
+    """The sum of every rank's value (work done by the whole job)."""
+    if pg is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    pg.all_reduce(t, op=pg.ReduceOp.SUM)
+    return float(t.item())
 
 
 def peaks():
@@ -197,6 +232,7 @@ def main_edge_routers(args, rank, world, local):
 
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
+    pg = init_ranks(world)
     R = args.routers
     prefill, distinct = min(args.prefill, 4), max(1, min(args.distinct, 8))
     tr = synth.Traffic(synth.edge_routers(seed=rank, n_slices=prefill + distinct, n_routers=R))
@@ -229,6 +265,7 @@ def main_edge_routers(args, rank, world, local):
     stream = torch.cuda.ExternalStream(batch.stream_ptr)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     step_ms = []
+    barrier(pg)
     torch.cuda.synchronize()
     # each step is enqueued before the previous step's report is read, so the device runs
     # steps back to back (sse_batch_step_async / sse_batch_step_wait)
@@ -242,17 +279,21 @@ def main_edge_routers(args, rank, world, local):
         step_ms.append((time.perf_counter() - t0) * 1e3)
     e1.record(stream)
     torch.cuda.synchronize()
+    barrier(pg)
     clk = clocks.stop()
-    elapsed = e0.elapsed_time(e1) / 1e3
+    elapsed = max_over_ranks(pg, e0.elapsed_time(e1) / 1e3, dev)
     launches = batch.kernel_launches - launches0
     gstats = batch.global_estimator().stats()
+    total = sum(pairs_per_step)
+    total_all = sum_over_ranks(pg, float(total), dev)  # every rank scans its own routers' traces
+    if pg is not None:
+        pg.destroy_process_group()
     if rank != 0:
         return
     srt = sorted(step_ms)
-    total = sum(pairs_per_step)
     print(json.dumps({
         "metric": "Gpackets/s, 16-router batch step (persistent update + merge + global close)",
-        "value": round(total * world / elapsed / 1e9, 4), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "value": round(total_all / elapsed / 1e9, 4), "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(elapsed / args.steps * 1e3, 4), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
         "config": {"workload": f"edge_routers: {R} routers, loads log-uniform 2^20..2^25 pairs per router and "
@@ -279,6 +320,8 @@ def main_serving(args, rank, world, local):
     from paper_1805_09246_b300.requests import poisson_requests
 
     torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pg = init_ranks(world)
     R = 32
     offered = 2e9
     rs = poisson_requests(R, duration_s=args.serve_seconds, offered_pps=offered, batch_min=1 << 16,
@@ -304,20 +347,24 @@ def main_serving(args, rank, world, local):
     clocks = ClockSampler(local)
     clocks.start()
     time.sleep(0.3)
+    barrier(pg)
     t0 = time.perf_counter()
     for t, r, start, size in rs.requests[n_warm:]:
         srv.submit(r, t, batch(r, start, size))
     srv.flush()
-    wall = time.perf_counter() - t0
+    wall = max_over_ranks(pg, time.perf_counter() - t0, dev)
     clk = clocks.stop()
     reports = srv.poll()
     lat = sorted(l for _, l in reports)
     st = srv.stats()
+    total_all = sum_over_ranks(pg, float(total), dev)  # each rank serves its own request stream
+    if pg is not None:
+        pg.destroy_process_group()
     if rank != 0:
         return
     print(json.dumps({
         "metric": "Gpackets/s served (32 routers, Poisson batches) and slice-close-to-report p50/p99 ms",
-        "value": round(total * world / wall / 1e9, 4), "unit": UNIT, "n_gpus": world,
+        "value": round(total_all / wall / 1e9, 4), "unit": UNIT, "n_gpus": world,
         "steps": len(rs.requests) - n_warm, "warmup": n_warm, "ms_per_step": round(wall / max(1, len(rs.requests) - n_warm) * 1e3, 4),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
         "config": {"workload": f"serving: {R} routers, batches 64K-4M pairs log-uniform, Poisson arrivals "
@@ -328,7 +375,7 @@ def main_serving(args, rank, world, local):
         "close_ms_p50": round(lat[len(lat) // 2], 4) if lat else None,
         "close_ms_p99": round(lat[min(len(lat) - 1, int(0.99 * len(lat)))], 4) if lat else None,
         "slices_reported": len(reports), "slot_waits": st["slot_waits"],
-        "e2e": {"value": round(total * world / wall / 1e9, 4), "unit": UNIT,
+        "e2e": {"value": round(total_all / wall / 1e9, 4), "unit": UNIT,
                 "h2d_bytes_per_step": int(total * PAIR_BYTES / max(1, len(rs.requests) - n_warm)),
                 "d2h_bytes_per_step": 0},
         "clocks": clk,
@@ -347,6 +394,8 @@ def main_learned(args, rank, world, local):
     from paper_1805_09246_b300.synth import episodes as ep
 
     torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pg = init_ranks(world)
     cfg = ep.EpisodeConfig()
     params = learn.learned_params(cfg.k, seed=rank)
     t0 = time.perf_counter()
@@ -366,6 +415,7 @@ def main_learned(args, rank, world, local):
     clocks = ClockSampler(local)
     clocks.start()
     time.sleep(0.3)
+    barrier(pg)
     torch.cuda.synchronize()
     w0 = time.perf_counter()
     e0.record(stream)
@@ -373,10 +423,12 @@ def main_learned(args, rank, world, local):
                          first_epoch=args.warmup)
     e1.record(stream)
     torch.cuda.synchronize()
-    wall = time.perf_counter() - w0
+    barrier(pg)
+    wall = max_over_ranks(pg, time.perf_counter() - w0, dev)
     clk = clocks.stop()
     launches = mlp.kernel_launches - launches0
-    elapsed = e0.elapsed_time(e1) / 1e3
+    elapsed = max_over_ranks(pg, e0.elapsed_time(e1) / 1e3, dev)
+    samples_all = sum_over_ranks(pg, float(len(rows) * args.steps), dev)  # each rank trains its own network
     y = mlp.forward(tr.x).cpu().numpy()
     gate = learn.choose_gate(tr.lc.cpu().numpy(), y, tr.exact, act, params.eta2)
     mlp.set_gate(gate)
@@ -388,6 +440,8 @@ def main_learned(args, rank, world, local):
     gated = learn.active_cells(te.x, params.k) >= gate
     rel = lambda e, m: float(np.median(np.abs(e[m] - ex[m]) / ex[m])) if m.any() else None
     every = np.ones(len(ex), bool)
+    if pg is not None:
+        pg.destroy_process_group()
     if rank != 0:
         return
     samples = len(rows) * args.steps
@@ -395,7 +449,7 @@ def main_learned(args, rank, world, local):
     print(json.dumps({
         "metric": "learned correction: training samples/s (own forward/backward/Adam kernels); median relative "
                   "error learned vs linear counting on held-out hosts",
-        "value": round(samples * world / elapsed, 1), "unit": "samples/s", "n_gpus": world, "steps": args.steps,
+        "value": round(samples_all / elapsed, 1), "unit": "samples/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(elapsed / args.steps * 1e3, 3), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "bf16 weights, f32 accumulate", "data": "synthetic",
         "config": {"workload": f"learned: MLP 18->64->64->1, {args.learn_train} training hosts from GPU episodes "
@@ -417,7 +471,7 @@ def main_learned(args, rank, world, local):
                      "peak": round(148 * 128 * 2 * 2.032e9 / 1e12, 1), "unit": "TFLOP/s",
                      "frac": round(samples * flops_per_sample / elapsed / (148 * 128 * 2 * 2.032e9), 6),
                      "traffic": None, "peak_source": "FP32 FMA: 148 SMs x 128 lanes x 2 x 2.032 GHz (nominal)"},
-        "e2e": {"value": round(samples * world / wall, 1), "unit": "samples/s",
+        "e2e": {"value": round(samples_all / wall, 1), "unit": "samples/s",
                 "h2d_bytes_per_step": int(4 * len(rows)), "d2h_bytes_per_step": 4},
         "gpu_launches": int(launches), "clocks": clk,
     }), flush=True)
@@ -443,11 +497,7 @@ def main():
 
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    pg = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
-        pg = dist
+    pg = init_ranks(world)
 
     tr = make_traffic(rank)
     # paper_params: the same core-link traffic through the estimator of the paper's
@@ -499,8 +549,7 @@ def main():
     clocks = ClockSampler(local)
     clocks.start()
     time.sleep(0.3)
-    if pg:
-        pg.barrier()
+    barrier(pg)
     torch.cuda.synchronize()
     ev_start.record(stream)
     upd_ev[0][0].record(stream)
@@ -522,17 +571,12 @@ def main():
         n_cand += rep.n_candidates
     ev_end.record(stream)
     torch.cuda.synchronize()
-    if pg:
-        pg.barrier()
+    barrier(pg)
     clk = clocks.stop()
     launches = est.kernel_launches - launches0
     slice_stats = est.stats()
-    elapsed_s = ev_start.elapsed_time(ev_end) / 1e3
+    elapsed_s = max_over_ranks(pg, ev_start.elapsed_time(ev_end) / 1e3, dev)
     upd_ms = sum(a.elapsed_time(b) for a, b in upd_ev) / args.steps
-    if pg:
-        t = torch.tensor([elapsed_s], device=dev)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        elapsed_s = float(t.item())
 
     # ---- slice-close latency (after the timed region): the slice boundary is a synchronised
     # stream; latency = sse_close_slice until the report is in host memory
@@ -629,7 +673,7 @@ def main():
         "clocks": clk,
     }
     print(json.dumps(out), flush=True)
-    if pg:
+    if pg is not None:
         pg.destroy_process_group()
 
 

@@ -1,0 +1,64 @@
+"""The multi-rank plumbing of bench.py on the CPU: two gloo ranks (127.0.0.1) meet at the
+barrier, the job's time is the slowest rank's (MAX) and its work the sum over ranks; each
+rank scans its own router's trace; under a multi-rank launch only rank 0 runs and prints
+the reference arm. No GPU is used."""
+import contextlib
+import io
+import os
+import socket
+import sys
+
+import pytest
+
+from tests.conftest import ROOT
+
+torch = pytest.importorskip("torch")
+mp = pytest.importorskip("torch.multiprocessing")
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank_main(rank, world, port, out):
+    sys.path.insert(0, ROOT)
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world),
+                      LOCAL_RANK=str(rank))
+    import bench
+    r, w, _ = bench.dist_env()
+    pg = bench.init_ranks(w)
+    bench.barrier(pg)
+    slowest = bench.max_over_ranks(pg, 1.5 + r, "cpu")
+    work = bench.sum_over_ranks(pg, 10.0 * (r + 1), "cpu")
+    first_pair = bench.make_traffic(r).slice(0, 0)[:4].tolist()
+    args = bench.parse(["--impl", "reference", "--steps", "1", "--warmup", "0"])
+    buf = io.StringIO()
+    if r != 0:  # rank 0's oracle run is the single-rank path, timed elsewhere
+        with contextlib.redirect_stdout(buf):
+            bench.run_reference(args, r, w)
+    bench.barrier(pg)
+    pg.destroy_process_group()
+    out.put((r, w, slowest, work, first_pair, buf.getvalue()))
+
+
+def test_two_gloo_ranks_max_time_summed_work_and_rank_traces():
+    world = 2
+    ctx = mp.get_context("spawn")
+    out = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_rank_main, args=(r, world, port, out)) for r in range(world)]
+    for p in procs:
+        p.start()
+    results = [out.get(timeout=300) for _ in range(world)]
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    results.sort()
+    for r, w, slowest, work, _, printed in results:
+        assert w == world
+        assert slowest == 2.5  # the larger of 1.5 and 2.5
+        assert work == 30.0    # 10 + 20
+    assert results[0][4] != results[1][4]  # each rank scans its own trace
+    assert results[1][5] == ""             # rank 1 of the reference arm prints nothing
