@@ -135,9 +135,13 @@ __global__ void __launch_bounds__(128) k_mlp_forward(MlpShape s, const __nv_bflo
 constexpr uint32_t kTrainSamples = 4;
 constexpr int kTrainThreads = 256;
 
+// Shared memory of k_mlp_grad_partial: the weights, the samples' activations and deltas,
+// and W1 and W2 again with rows padded by one word (a warp reading one column of a padded
+// matrix hits 32 different banks).
 __host__ __device__ inline uint32_t train_smem_floats(const MlpShape& s) {
   const uint32_t wpad = (s.total + 3) & ~3u;
-  return wpad + kTrainSamples * (s.n_in + 4 * s.hidden) + 2 * kTrainSamples;
+  return wpad + kTrainSamples * (s.n_in + 4 * s.hidden) + 2 * kTrainSamples + s.hidden * (s.n_in + 1) +
+         s.hidden * (s.hidden + 1);
 }
 
 // HC, DC: the hidden width and input count when known at compile time (loops unroll), else 0.
@@ -159,6 +163,8 @@ __global__ void __launch_bounds__(kTrainThreads) k_mlp_grad_partial(MlpShape s, 
   float* d1 = d2 + S * H;                  // dz1
   float* dy = d1 + S * H;                  // [S]
   float* se = dy + S;                      // squared errors [S]
+  float* w1p = se + S;                     // W1 rows padded to D + 1
+  float* w2p = w1p + H * (D + 1);          // W2 rows padded to H + 1
   const float* W1 = w + s.off_w1;
   const float* B1 = w + s.off_b1;
   const float* W2 = w + s.off_w2;
@@ -187,11 +193,20 @@ __global__ void __launch_bounds__(kTrainThreads) k_mlp_grad_partial(MlpShape s, 
     xs[i] = q < ns ? x[(uint64_t)(rows ? rows[b0 + q] : b0 + q) * D + d] : 0.f;
   }
   __syncthreads();
+  for (uint32_t i = threadIdx.x; i < H * D; i += blockDim.x) {
+    const uint32_t o = i / D, d = i - o * D;
+    w1p[o * (D + 1) + d] = W1[i];
+  }
+  for (uint32_t i = threadIdx.x; i < H * H; i += blockDim.x) {
+    const uint32_t o = i / H, k = i - o * H;
+    w2p[o * (H + 1) + k] = W2[i];
+  }
+  __syncthreads();
   for (uint32_t i = threadIdx.x; i < S * H; i += blockDim.x) {  // layer 1
     const uint32_t q = i / H, o = i - q * H;
     float acc = B1[o];
 #pragma unroll
-    for (uint32_t d = 0; d < D; ++d) acc = fmaf(W1[o * D + d], xs[q * D + d], acc);
+    for (uint32_t d = 0; d < D; ++d) acc = fmaf(w1p[o * (D + 1) + d], xs[q * D + d], acc);
     h1[i] = fmaxf(acc, 0.f);
   }
   __syncthreads();
@@ -199,7 +214,7 @@ __global__ void __launch_bounds__(kTrainThreads) k_mlp_grad_partial(MlpShape s, 
     const uint32_t q = i / H, o = i - q * H;
     float acc = B2[o];
 #pragma unroll 16
-    for (uint32_t k = 0; k < H; ++k) acc = fmaf(W2[o * H + k], h1[q * H + k], acc);
+    for (uint32_t k = 0; k < H; ++k) acc = fmaf(w2p[o * (H + 1) + k], h1[q * H + k], acc);
     h2[i] = fmaxf(acc, 0.f);
   }
   __syncthreads();
@@ -227,7 +242,7 @@ __global__ void __launch_bounds__(kTrainThreads) k_mlp_grad_partial(MlpShape s, 
     float acc = 0.f;
     if (h1[i] > 0.f) {
 #pragma unroll 16
-      for (uint32_t o = 0; o < H; ++o) acc = fmaf(W2[o * H + k], d2[q * H + o], acc);
+      for (uint32_t o = 0; o < H; ++o) acc = fmaf(w2p[o * (H + 1) + k], d2[q * H + o], acc);
     }
     d1[i] = acc;
   }
@@ -271,61 +286,83 @@ __global__ void __launch_bounds__(kTrainThreads) k_mlp_grad_partial(MlpShape s, 
   }
 }
 
-// Sum over the CTAs' shares of parameter k: eight running sums over c = j mod 8, added
-// pairwise at the end (a fixed order, and eight loads in flight).
-__device__ __forceinline__ float sum_parts(const float* __restrict__ partial, uint32_t n_parts, uint32_t total,
-                                           uint32_t k) {
-  float a[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-  uint32_t c = 0;
-  for (; c + 8 <= n_parts; c += 8)
-#pragma unroll
-    for (int j = 0; j < 8; ++j) a[j] += partial[(uint64_t)(c + j) * total + k];
-  for (; c < n_parts; ++c) a[c & 7] += partial[(uint64_t)c * total + k];
-  return ((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7]));
+// Sum over the CTAs' shares of 32 parameters per block (kSumThreads = 256 threads, blockDim
+// fixed): warp j adds the shares c = j, j + 8, j + 16, ... of parameter k0 + lane (four loads
+// in flight, coalesced over the lanes), and the eight warps' sums are added in warp order in
+// shared memory — a fixed order. Returns the sum in warp 0 (other warps: 0).
+constexpr int kSumThreads = 256;
+constexpr uint32_t kSumParams = 32;  // parameters per block
+__device__ __forceinline__ float sum_parts_block(const float* __restrict__ partial, uint32_t n_parts, uint32_t total,
+                                                 uint32_t k) {
+  __shared__ float part_sum[kSumThreads / 32][32];
+  const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+  float acc = 0.f;
+  if (k < total) {
+    uint32_t c = warp;
+    for (; c + 24 < n_parts; c += 32) {  // four shares in flight
+      const float x0 = partial[(uint64_t)c * total + k], x1 = partial[(uint64_t)(c + 8) * total + k];
+      const float x2 = partial[(uint64_t)(c + 16) * total + k], x3 = partial[(uint64_t)(c + 24) * total + k];
+      acc += x0;
+      acc += x1;
+      acc += x2;
+      acc += x3;
+    }
+    for (; c < n_parts; c += 8) acc += partial[(uint64_t)c * total + k];
+  }
+  part_sum[warp][lane] = acc;
+  __syncthreads();
+  float sum = 0.f;
+  if (warp == 0)
+    for (uint32_t j = 0; j < kSumThreads / 32; ++j) sum += part_sum[j][lane];
+  return sum;
 }
 
-// Training step, part 2 (gradient only): g[k] = sum_parts; *loss = sum of loss_partial
-// (thread 0 of block 0).
-__global__ void k_mlp_reduce_grads(uint32_t total, uint32_t n_parts, const float* __restrict__ partial,
-                                   const float* __restrict__ loss_partial, float* __restrict__ g,
-                                   float* __restrict__ loss) {
-  const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k < total) g[k] = sum_parts(partial, n_parts, total, k);
-  if (k == 0) {
-    float l = 0.f;
-    for (uint32_t c = 0; c < n_parts; ++c) l += loss_partial[c];
-    *loss = l;
-  }
+// The loss of a step: the sum of the CTAs' loss shares, in share order (one thread).
+__device__ __forceinline__ float sum_loss(const float* __restrict__ loss_partial, uint32_t n_parts) {
+  float l = 0.f;
+  for (uint32_t c = 0; c < n_parts; ++c) l += loss_partial[c];
+  return l;
+}
+
+// Training step, part 2 (gradient only): g[k] = the summed shares (sum_parts_block, 32
+// parameters per block); *loss = sum_loss (thread 0 of the last block).
+__global__ void __launch_bounds__(kSumThreads) k_mlp_reduce_grads(uint32_t total, uint32_t n_parts,
+                                                                  const float* __restrict__ partial,
+                                                                  const float* __restrict__ loss_partial,
+                                                                  float* __restrict__ g, float* __restrict__ loss) {
+  const uint32_t k = blockIdx.x * kSumParams + (threadIdx.x & 31u);
+  const float gk = sum_parts_block(partial, n_parts, total, k);
+  if (threadIdx.x < 32 && k < total) g[k] = gk;
+  if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 32) *loss = sum_loss(loss_partial, n_parts);
 }
 
 // Adam (Kingma and Ba 2015) on the FP32 parameters; the BF16 copy is refreshed. The step
 // number is *step_base + step_off (the base lives on the device so that a captured epoch
 // replays correctly; k_mlp_step_add advances it), the learning rate *lr_dev when given,
 // else lr. With partial != NULL the gradient is first summed from the CTAs' shares
-// (sum_parts, as k_mlp_reduce_grads) and stored in g.
-__global__ void k_mlp_adam(uint32_t total, float* __restrict__ wf, __nv_bfloat16* __restrict__ wb,
-                           float* __restrict__ g, float* __restrict__ m, float* __restrict__ v,
-                           const float* __restrict__ lr_dev, float lr_val, const uint32_t* __restrict__ step_base,
-                           uint32_t step_off, float beta1, float beta2, float eps,
-                           const float* __restrict__ partial, uint32_t n_parts,
-                           const float* __restrict__ loss_partial, float* __restrict__ loss) {
-  const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+// (sum_parts_block, as k_mlp_reduce_grads) and stored in g. 32 parameters per block
+// (kSumThreads threads); warp 0 updates them.
+__global__ void __launch_bounds__(kSumThreads) k_mlp_adam(uint32_t total, float* __restrict__ wf,
+                                                          __nv_bfloat16* __restrict__ wb, float* __restrict__ g,
+                                                          float* __restrict__ m, float* __restrict__ v,
+                                                          const float* __restrict__ lr_dev, float lr_val,
+                                                          const uint32_t* __restrict__ step_base, uint32_t step_off,
+                                                          float beta1, float beta2, float eps,
+                                                          const float* __restrict__ partial, uint32_t n_parts,
+                                                          const float* __restrict__ loss_partial,
+                                                          float* __restrict__ loss) {
+  const uint32_t k = blockIdx.x * kSumParams + (threadIdx.x & 31u);
+  if (partial && loss && blockIdx.x == gridDim.x - 1 && threadIdx.x == 32) *loss = sum_loss(loss_partial, n_parts);
+  float gk = 0.f;
+  if (partial) gk = sum_parts_block(partial, n_parts, total, k);
+  if (threadIdx.x >= 32 || k >= total) return;
+  if (partial)
+    g[k] = gk;
+  else
+    gk = g[k];
   const float lr = lr_dev ? *lr_dev : lr_val;
   const float step = (float)(*step_base + step_off);
   const float bc1 = 1.f - powf(beta1, step), bc2 = 1.f - powf(beta2, step);
-  if (partial && k == 0 && loss) {
-    float l = 0.f;
-    for (uint32_t c = 0; c < n_parts; ++c) l += loss_partial[c];
-    *loss = l;
-  }
-  if (k >= total) return;
-  float gk;
-  if (partial) {
-    gk = sum_parts(partial, n_parts, total, k);
-    g[k] = gk;
-  } else {
-    gk = g[k];
-  }
   const float mk = beta1 * m[k] + (1.f - beta1) * gk;
   const float vk = beta2 * v[k] + (1.f - beta2) * gk * gk;
   m[k] = mk;

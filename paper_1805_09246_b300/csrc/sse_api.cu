@@ -2155,7 +2155,8 @@ int mlp_grad_partial(sse_mlp* m, const float* d_x, const float* d_t, const uint3
 // (parts == 0); the learning rate from *lr_dev when given, else lr.
 int mlp_adam(sse_mlp* m, const float* lr_dev, float lr, uint32_t step_off, cudaStream_t st, uint32_t parts,
              float* d_loss) {
-  k_mlp_adam<<<(m->s.total + 255) / 256, 256, 0, st>>>(m->s.total, m->wf, m->wb, m->g, m->m, m->v, lr_dev, lr,
+  k_mlp_adam<<<(m->s.total + kSumParams - 1) / kSumParams, kSumThreads, 0, st>>>(m->s.total, m->wf, m->wb, m->g,
+                                                                               m->m, m->v, lr_dev, lr,
                                                        m->d_step, step_off, 0.9f, 0.999f, 1e-8f,
                                                        parts ? m->partial : nullptr, parts, m->loss_partial, d_loss);
   m->launches += 1;
@@ -2179,7 +2180,8 @@ int sse_mlp_gradients(sse_mlp* m, const float* d_x, const float* d_t, const uint
   uint32_t parts = 0;
   int rc = mlp_grad_partial(m, d_x, d_t, d_rows, n, st, &parts);
   if (rc) return rc;
-  k_mlp_reduce_grads<<<(m->s.total + 255) / 256, 256, 0, st>>>(m->s.total, parts, m->partial, m->loss_partial, m->g,
+  k_mlp_reduce_grads<<<(m->s.total + kSumParams - 1) / kSumParams, kSumThreads, 0, st>>>(
+      m->s.total, parts, m->partial, m->loss_partial, m->g,
                                                                m->loss);
   m->launches += 1;
   if (cudaGetLastError() != cudaSuccess) return SSE_ERR_CUDA;
