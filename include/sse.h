@@ -187,8 +187,6 @@ SSE_API int sse_update(sse_handle* h, const uint32_t* d_pairs, uint64_t n_pairs)
  */
 SSE_API int sse_update_host(sse_handle* h, const uint32_t* h_pairs, uint64_t n_pairs);
 
-/* Selects how sse_update() writes cells (enum sse_update_mode). Results never depend on
- * it. Errors: INVALID_PARAM. */
 /*
  * Which end of a pair is the host aip whose opposite hosts are counted (Definition 1 lets a
  * host be either end): SSE_DIR_SRC (default) scans (src, dst) as (aip, bip), SSE_DIR_DST as
@@ -199,6 +197,8 @@ SSE_API int sse_update_host(sse_handle* h, const uint32_t* h_pairs, uint64_t n_p
 enum { SSE_DIR_SRC = 0, SSE_DIR_DST = 1, SSE_DIR_BOTH = 2 };
 SSE_API int sse_set_direction(sse_handle* h, int direction);
 
+/* Selects how sse_update() writes cells (enum sse_update_mode). Results never depend on
+ * it. Errors: INVALID_PARAM. */
 SSE_API int sse_set_update_mode(sse_handle* h, int mode);
 
 /* Number of update variants the autotuner chooses from (variant 0 is the direct update,
@@ -228,7 +228,9 @@ SSE_API int sse_autotune_update(sse_handle* h, const uint32_t* d_pairs, uint64_t
  * paper's "slice updating", Section 3.2). Blocks until the report is in host memory.
  * out may be NULL (statistics are still kept, see sse_get_stats()).
  * Errors: CAPACITY when candidates exceed max_candidates or out->cap (the report then
- * holds the first entries, truncated = 1, and the slice still advances); CUDA.
+ * holds the first entries, truncated = 1, and the slice still advances); TIMEOUT when the
+ * ordering of more than 4096 candidates, whose blocks meet at bounded device-side
+ * barriers, gave up waiting (the report's order is then not guaranteed); CUDA.
  */
 SSE_API int sse_close_slice(sse_handle* h, sse_report* out);
 
