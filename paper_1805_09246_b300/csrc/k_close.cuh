@@ -39,6 +39,65 @@ __device__ __forceinline__ uint32_t word_keep(uint32_t w, Window8 win, uint32_t 
   }
 }
 
+// Spreads the 16 low bits of x to the even bit positions (Morton interleave).
+__device__ __forceinline__ uint32_t spread16(uint32_t x) {
+  x &= 0xFFFFu;
+  x = (x | (x << 8)) & 0x00FF00FFu;
+  x = (x | (x << 4)) & 0x0F0F0F0Fu;
+  x = (x | (x << 2)) & 0x33333333u;
+  x = (x | (x << 1)) & 0x55555555u;
+  return x;
+}
+
+// RSRA part of the pass for 8-bit cells: two SREs (16 bytes) per load, four loads in flight,
+// 32-bit indices. Lane l of a warp holds SREs 2(b + l) and 2(b + l) + 1 of the warp's 64
+// consecutive SREs; their hot flags (two ballots) are interleaved into the two hot-bitmap
+// words, written by lanes 0 and 1.
+template <bool WRAP>
+__device__ __forceinline__ void close_rsra8(const KParams& p, uint8_t* __restrict__ sre,
+                                           uint32_t* __restrict__ hot_bits, Window8 win, uint32_t mode) {
+  const bool expire = (mode & 1u) != 0;
+  const uint32_t n_sre = p.r << p.q;  // a multiple of 32
+  const uint32_t n_vec = n_sre >> 1;
+  uint4* words = reinterpret_cast<uint4*>(sre);
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
+  const uint32_t nthreads = gridDim.x * blockDim.x;  // a multiple of 32
+  constexpr int kLoads = 4;
+  for (uint32_t g0 = tid; g0 - lane < n_vec; g0 += kLoads * nthreads) {
+    uint4 v[kLoads];
+#pragma unroll
+    for (int u = 0; u < kLoads; ++u) {
+      const uint32_t g = g0 + u * nthreads;
+      v[u] = g < n_vec ? words[g] : make_uint4(0u, 0u, 0u, 0u);
+    }
+#pragma unroll
+    for (int u = 0; u < kLoads; ++u) {
+      const uint32_t g = g0 + u * nthreads;
+      if (g - lane >= n_vec) break;  // warp-uniform: the whole warp is past the end
+      const uint32_t x[4] = {v[u].x, v[u].y, v[u].z, v[u].w};
+      uint32_t act[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) act[i] = active_hi8<WRAP>(x[i], win);
+      const uint32_t w0 = __popc(act[0]) + __popc(act[1]);  // SRE 2g
+      const uint32_t w1 = __popc(act[2]) + __popc(act[3]);  // SRE 2g + 1
+      const uint32_t b0 = __ballot_sync(0xFFFFFFFFu, w0 >= p.hot_min);
+      const uint32_t b1 = __ballot_sync(0xFFFFFFFFu, w1 >= p.hot_min);
+      if ((mode & 2u) && lane < 2) {
+        const uint32_t word = ((g - lane) >> 4) + lane;  // the warp's SREs start at 2(g - lane)
+        if (word < (n_sre >> 5)) hot_bits[word] = spread16(b0 >> (16 * lane)) | (spread16(b1 >> (16 * lane)) << 1);
+      }
+      if (expire && g < n_vec) {
+        // cells that are set (non-zero) but not active have left the window
+        const uint32_t e0 = x[0] & ~((act[0] >> 7) * 0xFFu), e1 = x[1] & ~((act[1] >> 7) * 0xFFu);
+        const uint32_t e2 = x[2] & ~((act[2] >> 7) * 0xFFu), e3 = x[3] & ~((act[3] >> 7) * 0xFFu);
+        if (e0 | e1 | e2 | e3)
+          words[g] = make_uint4(x[0] ^ e0, x[1] ^ e1, x[2] ^ e2, x[3] ^ e3);
+      }
+    }
+  }
+}
+
 // The pass of k_close for one window shape (WRAP: see word_keep).
 template <typename St, bool WRAP>
 __device__ __forceinline__ void close_body(const KParams& p, uint8_t* __restrict__ sre, uint8_t* __restrict__ sle,
@@ -49,7 +108,9 @@ __device__ __forceinline__ void close_body(const KParams& p, uint8_t* __restrict
   const bool expire = (mode & 1u) != 0;
   const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const uint64_t nthreads = (uint64_t)gridDim.x * blockDim.x;  // a multiple of 32
-  if (do_sre) {
+  if (do_sre && sizeof(St) == 1) {
+    close_rsra8<WRAP>(p, sre, hot_bits, win, mode);
+  } else if (do_sre) {
     // RSRA: SRE index g (row-major over [r][2^q]); r * 2^q is a multiple of 32, so every
     // iteration covers whole warps.
     const uint64_t n_sre = (uint64_t)p.r << p.q;
