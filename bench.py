@@ -544,6 +544,9 @@ def main():
     # so the device runs update, close, update, ... back to back.
     ev_start, ev_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     upd_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for a, b in [(ev_start, ev_end)] + upd_ev:  # created at their first record: outside the timed region
+        a.record(stream)
+        b.record(stream)
     launches0 = est.kernel_launches
     n_super = n_cand = 0
     clocks = ClockSampler(local)
@@ -581,10 +584,17 @@ def main():
     # ---- slice-close latency (after the timed region): the slice boundary is a synchronised
     # stream; latency = sse_close_slice until the report is in host memory
     close_ms, close_dev = [], []
-    for s in range(min(args.steps, 50)):
+    n_lat = min(args.steps, 50)
+    # the events are created (and first recorded) before the samples: a CUDA event is created
+    # lazily at its first record, which would otherwise fall inside the measured interval
+    lat_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n_lat)]
+    for a, b in lat_ev:
+        a.record(stream)
+        b.record(stream)
+    for s in range(n_lat):
         est.update(step_input(args.warmup + args.steps + s))
         stream.synchronize()
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a, b = lat_ev[s]
         t0 = time.perf_counter()
         a.record(stream)
         est.close_slice()

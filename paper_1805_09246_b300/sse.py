@@ -350,10 +350,14 @@ class Estimator:
     def _collect(self, fn, what: str, cap: int | None, raise_on_capacity: bool) -> Report:
         cap = self.params.max_candidates if cap is None else cap
         bufs = getattr(self, "_report_bufs", None)
-        if bufs is None or len(bufs[0]) != cap:  # reused across slices (allocating them costs more than the copy)
-            bufs = self._report_bufs = (np.empty(cap, np.uint32), np.empty(cap, np.float32), np.empty(cap, np.uint8))
-        hosts, est, flags = bufs
-        rep = _Report(0, 0, 0, cap, 0, hosts.ctypes.data, est.ctypes.data, flags.ctypes.data)
+        if bufs is None or len(bufs[0]) != cap:
+            # reused across slices, with their report struct: allocating the arrays, and even
+            # reading their addresses through numpy's ctypes attribute, costs more than the copy
+            h, e, f = np.empty(cap, np.uint32), np.empty(cap, np.float32), np.empty(cap, np.uint8)
+            bufs = self._report_bufs = (h, e, f, _Report(0, 0, 0, cap, 0, h.ctypes.data, e.ctypes.data, f.ctypes.data))
+        hosts, est, flags, rep = bufs
+        rep.slice = rep.n_candidates = rep.n_super = rep.truncated = 0
+        rep.cap = cap
         rc = fn(self._h, ctypes.byref(rep))
         if rc != SSE_OK and (rc != ERR_CAPACITY or raise_on_capacity):
             _check(rc, what, self._h)
@@ -534,15 +538,21 @@ class Batch:
         """(hosts, est, flags) arrays of `cap` entries, one set per step parity, reused."""
         sets = getattr(self, "_report_bufs", None)
         if sets is None or len(sets[0][0]) != cap:
-            sets = self._report_bufs = [(np.empty(cap, np.uint32), np.empty(cap, np.float32), np.empty(cap, np.uint8))
-                                        for _ in range(2)]
+            sets = []
+            for _ in range(2):  # with their report struct (numpy's ctypes attribute is slow)
+                h, e, f = np.empty(cap, np.uint32), np.empty(cap, np.float32), np.empty(cap, np.uint8)
+                sets.append((h, e, f, _Report(0, 0, 0, cap, 0, h.ctypes.data, e.ctypes.data, f.ctypes.data)))
+            self._report_bufs = sets
         self._parity = getattr(self, "_parity", 0) ^ 1
+        hosts, est, flags, rep = sets[self._parity]
+        rep.slice = rep.n_candidates = rep.n_super = rep.truncated = 0
+        rep.cap = cap
         return sets[self._parity]
 
     def _report(self, rc: int, rep, bufs, cap: int, what: str) -> Report:
         if rc != SSE_OK and rc != ERR_CAPACITY:
             _check(rc, what)
-        hosts, est, flags = bufs
+        hosts, est, flags, _ = bufs
         m = min(rep.n_candidates, cap, self.params.max_candidates)
         return Report(slice=rep.slice, n_candidates=rep.n_candidates, n_super=rep.n_super,
                       truncated=bool(rep.truncated), hosts=hosts[:m].copy(), est=est[:m].copy(),
@@ -558,8 +568,7 @@ class Batch:
         c = np.ascontiguousarray(counts, dtype=np.uint64)
         cap = self.params.max_candidates if cap is None else cap
         bufs = self._report_buffers(cap)
-        hosts, est, flags = bufs
-        rep = _Report(0, 0, 0, cap, 0, hosts.ctypes.data, est.ctypes.data, flags.ctypes.data)
+        rep = bufs[3]
         if inputs is not None:
             rc = self._lib.sse_batch_step_from(self._b, self._ptrs(inputs), ctypes.c_void_p(c.ctypes.data),
                                                ctypes.byref(rep))
@@ -582,8 +591,7 @@ class Batch:
         """The report of the oldest enqueued slice (blocks until it is on the host)."""
         cap = self.params.max_candidates if cap is None else cap
         bufs = self._report_buffers(cap)
-        hosts, est, flags = bufs
-        rep = _Report(0, 0, 0, cap, 0, hosts.ctypes.data, est.ctypes.data, flags.ctypes.data)
+        rep = bufs[3]
         rc = self._lib.sse_batch_step_wait(self._b, ctypes.byref(rep))
         return self._report(rc, rep, bufs, cap, "sse_batch_step_wait")
 
