@@ -15,6 +15,7 @@
 // round-to-nearest operations in a fixed order, so the super point decision is exact.
 #pragma once
 
+#include <cstddef>
 #include <type_traits>
 
 #include "k_close.cuh"
@@ -326,16 +327,17 @@ __global__ void __launch_bounds__(kJoinThreads) k_join(const __grid_constant__ K
 // n_stage) hosts, estimates and flags. Layout: CloseScratch | hosts[n_stage] |
 // est[n_stage] | flags[n_stage]. When tick_clock is set, the last step of the close — the
 // clock moving to the next slice's stamp (1..tick_mod) — is done here too (nothing in this
-// kernel reads the clock).
-__global__ void __launch_bounds__(256) k_report(const CloseScratch* __restrict__ sc,
-                                                const uint32_t* __restrict__ hosts, const float* __restrict__ est,
-                                                const uint8_t* __restrict__ flags, uint32_t cap, uint32_t n_stage,
-                                                uint8_t* __restrict__ out, uint32_t* __restrict__ tick_clock,
-                                                uint32_t tick_mod) {
+// kernel reads the clock). The last block to finish sets the stage's report_done after
+// every block's writes are visible to the host (system-scope fences), so the host can wait
+// on that word instead of on the stream.
+__global__ void __launch_bounds__(256) k_report(CloseScratch* __restrict__ sc, const uint32_t* __restrict__ hosts,
+                                                const float* __restrict__ est, const uint8_t* __restrict__ flags,
+                                                uint32_t cap, uint32_t n_stage, uint8_t* __restrict__ out,
+                                                uint32_t* __restrict__ tick_clock, uint32_t tick_mod) {
   if (tick_clock && blockIdx.x == 0 && threadIdx.x == 0) *tick_clock = *tick_clock % tick_mod + 1u;
   const uint32_t n = min(min(sc->n_cand, cap), n_stage);
   const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x, stride = gridDim.x * blockDim.x;
-  constexpr uint32_t kWords = sizeof(CloseScratch) / 4;
+  constexpr uint32_t kWords = offsetof(CloseScratch, report_blocks) / 4;  // the counters before the flags
   for (uint32_t i = tid; i < kWords; i += stride)
     reinterpret_cast<uint32_t*>(out)[i] = reinterpret_cast<const uint32_t*>(sc)[i];
   uint32_t* oh = reinterpret_cast<uint32_t*>(out + sizeof(CloseScratch));
@@ -345,6 +347,14 @@ __global__ void __launch_bounds__(256) k_report(const CloseScratch* __restrict__
     oh[i] = hosts[i];
     oe[i] = est[i];
     of[i] = flags[i];
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence_system();  // this block's writes (and, via the barrier, its threads') first
+    if (atomicAdd(&sc->report_blocks, 1u) == gridDim.x - 1) {
+      __threadfence_system();
+      *reinterpret_cast<volatile uint32_t*>(out + offsetof(CloseScratch, report_done)) = 1u;
+    }
   }
 }
 

@@ -5,6 +5,9 @@
 
 #include <algorithm>
 #include <cmath>
+#include <atomic>
+#include <chrono>
+#include <cstddef>
 #include <new>
 
 #include "k_batch.cuh"
@@ -860,6 +863,8 @@ int close_graph_launch(sse_handle* h) {
     SSE_CUDA(h, e);
   }
   if (!h->close_done) SSE_CUDA(h, cudaEventCreateWithFlags(&h->close_done, cudaEventDisableTiming));
+  // the report kernel sets this word last (no report is pending, so nothing writes it now)
+  *reinterpret_cast<volatile uint32_t*>(h->report_stage + offsetof(CloseScratch, report_done)) = 0u;
   SSE_CUDA(h, cudaGraphLaunch(h->close_exec, h->stream));
   SSE_CUDA(h, cudaEventRecord(h->close_done, h->stream));
   h->launches += h->close_kernels;
@@ -872,7 +877,26 @@ int close_graph_launch(sse_handle* h) {
 // Waits for the pending replay and fills `out` from the page-locked stage.
 int close_graph_collect(sse_handle* h, sse_report* out) {
   h->close_pending = 0;
-  SSE_CUDA(h, cudaEventSynchronize(h->close_done));
+  // The report is complete once the report kernel's last block has set report_done: poll
+  // that word for up to 5 ms (a close takes well under that), which wakes up sooner than a
+  // blocking wait; otherwise (a longer close, or a failed one) wait for the stream's event,
+  // which also reports errors.
+  const volatile uint32_t* done =
+      reinterpret_cast<const volatile uint32_t*>(h->report_stage + offsetof(CloseScratch, report_done));
+  bool flagged = false;
+  const auto t0 = std::chrono::steady_clock::now();
+  for (uint32_t i = 0;; ++i) {
+    if (*done) {
+      flagged = true;
+      break;
+    }
+    if ((i & 1023u) == 1023u && std::chrono::steady_clock::now() - t0 > std::chrono::milliseconds(5)) break;
+#if defined(__x86_64__)
+    __builtin_ia32_pause();
+#endif
+  }
+  if (!flagged) SSE_CUDA(h, cudaEventSynchronize(h->close_done));
+  std::atomic_thread_fence(std::memory_order_acquire);  // the report is read after the flag
   return collect_staged(h, h->close_sorted, h->close_pending_slice, out, h->report_stage, h->report_stage_n);
 }
 

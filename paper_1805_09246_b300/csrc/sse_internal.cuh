@@ -114,6 +114,8 @@ struct CloseScratch {
   uint32_t overflow;           // nonzero when a buffer was too small
   uint32_t error;              // nonzero when a bounded device-side wait gave up
   uint32_t barrier[2];         // grid barrier of the candidate sort (arrivals, generation)
+  uint32_t report_blocks;      // blocks of the report kernel that have written their part
+  uint32_t report_done;        // in the report stage: set last, once the whole report is there
 };
 
 }  // namespace sse
