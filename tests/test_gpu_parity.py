@@ -132,7 +132,7 @@ def test_autotune_keeps_state_and_picks_a_variant():
 
 @pytest.mark.parametrize("params", ["paper", "core_link", "many_rows"])
 def test_update_strategies_agree(params):
-    """Direct and tiled updates leave bit-identical stamps, including rows split into
+    """Direct and every tiled variant leave bit-identical stamps, including rows split into
     several shared-memory pieces (the paper's q'=17 rows) and misaligned group starts."""
     S = sse()
     p = {"paper": S.paper_params(k=8), "core_link": S.core_link_params(),
@@ -141,17 +141,24 @@ def test_update_strategies_agree(params):
     n = (1 << 22) + 3
     src = rng.integers(0, 2**32, 1 << 20, dtype=np.uint64).astype(np.uint32)
     pairs = np.stack([src[rng.integers(0, 1 << 20, n)], rng.integers(0, 2**32, n, dtype=np.uint64).astype(np.uint32)], 1)
-    a, b = S.Estimator(p), S.Estimator(p)
+    a = S.Estimator(p)
     a.set_update_mode(DIRECT)
-    b.set_update_mode(TILED)
+    tiled = []  # every tiled form the autotuner may pick
+    for v in range(1, S.update_variant_count()):
+        b = S.Estimator(p)
+        b.set_update_mode(TILED)
+        b.set_update_variant(v)
+        tiled.append(b)
     for t in range(2):
         buf = helpers.to_device(np.concatenate([np.zeros((1, 2), np.uint32), pairs]))
         a.update(buf[1:])
-        b.update(buf[1:])
-        for x, y in zip(a.read_stamps(), b.read_stamps()):
-            assert np.array_equal(x, y)
+        want = a.read_stamps()
+        for b in tiled:
+            b.update(buf[1:])
+            for x, y in zip(want, b.read_stamps()):
+                assert np.array_equal(x, y)
+            b.advance()
         a.advance()
-        b.advance()
         pairs = pairs[::-1].copy()
 
 
