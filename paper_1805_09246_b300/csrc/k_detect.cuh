@@ -390,11 +390,14 @@ __host__ __device__ __forceinline__ uint32_t any_words_staged(uint32_t q, uint32
   return (any_words(q, delta) + 3u) & ~3u;
 }
 
+// STAGE: both "any hot" bitmaps are copied to shared memory first, so that the probes are
+// shared-memory loads with 32-bit addresses (else they read the global bitmaps).
+template <bool STAGE>
 __global__ void __launch_bounds__(kJoinTiledThreads) k_join_tiled(
     const __grid_constant__ KParams p, const uint32_t* __restrict__ tables, const uint32_t* __restrict__ any2,
     const uint32_t* __restrict__ any3, const uint32_t* __restrict__ list0, const uint32_t* __restrict__ list1,
     const uint32_t* __restrict__ n_list, uint32_t* __restrict__ cand, uint32_t* __restrict__ n_cand, uint32_t cap,
-    uint32_t* __restrict__ overflow, uint32_t stage) {
+    uint32_t* __restrict__ overflow) {
   extern __shared__ uint32_t sm[];
   __shared__ uint32_t s_qn;
   const uint32_t n0 = n_list[0], n1 = n_list[1];
@@ -410,7 +413,7 @@ __global__ void __launch_bounds__(kJoinTiledThreads) k_join_tiled(
   const uint32_t* a2 = any2;
   const uint32_t* a3 = any3;
   uint32_t* next = sm;
-  if (stage) {
+  if constexpr (STAGE) {
     // both bitmaps with 16-byte loads, all of a thread's loads issued before its stores
     // (the word counts are multiples of 4 from 2^(q-delta) >= 128; smaller ones word by word)
     uint32_t* d2 = next;
@@ -536,7 +539,8 @@ __global__ void __launch_bounds__(kJoinTiledThreads) k_join_tiled(
 #pragma unroll
           for (uint32_t u = 0; u < 4; ++u) {
             const uint32_t x = a2[c[u] >> 5];
-            hits = (hits << 1) | (__funnelshift_l(x, x, c[u]) >> 31);
+            // (hits << 1) | top bit of the rotated word, as one funnel shift
+            hits = __funnelshift_l(__funnelshift_l(x, x, c[u]), hits, 1);
           }
         }
         hits = __brev(hits) >> (32 - kJoinProbeBlock);

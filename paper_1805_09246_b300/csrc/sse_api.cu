@@ -560,9 +560,10 @@ int sse_init(const sse_params* p, void* cuda_stream, sse_handle** out) {
     h->join_stage = 2 * any_bytes <= 64u * 1024u ? 1u : 0u;
     h->join_tiled_smem = (h->join_stage ? 2 * (size_t)any_words_staged(q.q, d.delta) * 4 : 0) + kJoinTiledFixedBytes;
     int per_sm = 0;
-    if (cudaFuncSetAttribute(k_join_tiled, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)h->join_tiled_smem) !=
+    const auto join_fn = h->join_stage ? k_join_tiled<true> : k_join_tiled<false>;
+    if (cudaFuncSetAttribute(join_fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)h->join_tiled_smem) !=
             cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_join_tiled, kJoinTiledThreads, h->join_tiled_smem) !=
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, join_fn, kJoinTiledThreads, h->join_tiled_smem) !=
             cudaSuccess ||
         per_sm < 1) {
       cudaGetLastError();
@@ -747,9 +748,10 @@ int close_enqueue(sse_handle* h, uint32_t** sorted, bool copy_counters = true) {
                                                                   h->any3, n_lists, n_regroup);
     SSE_LAUNCHED(h);
     if (h->kp.delta <= 5)
-      k_join_tiled<<<h->join_grid, kJoinTiledThreads, h->join_tiled_smem, h->stream>>>(
+      (h->join_stage ? k_join_tiled<true> : k_join_tiled<false>)<<<h->join_grid, kJoinTiledThreads,
+                                                                   h->join_tiled_smem, h->stream>>>(
           h->kp, h->tables, h->any2, h->any3, h->list0, h->list1, sc->n_list, h->cand, &sc->n_cand, h->cand_cap,
-          &sc->overflow, h->join_stage);
+          &sc->overflow);
     else
       k_join<<<h->num_sms, kJoinThreads, h->join_smem, h->stream>>>(h->kp, h->hot_bits, h->tables, h->any3, h->list0,
                                                                     h->list1, sc->n_list, h->cand, &sc->n_cand,

@@ -85,6 +85,30 @@ def test_small_trace_end_to_end(mode):
     assert sum(r.n_super for r in reports) > 100  # the planted super points are found
 
 
+def test_join_probes_global_any_hot_bitmaps():
+    """q - delta = 19: the "any hot" bitmaps of rows 2 and 3 (64 KiB each) are too large to
+    stage in shared memory, so the join probes them in global memory. Hot SREs, counts and
+    reports against the oracle."""
+    S = sse()
+    p = S.Params(r=5, q=23, delta=4, seed=23)
+    tr = synth.Traffic(synth.small_trace(seed=23))
+    est = S.Estimator(p)
+    orc = oracle.Oracle(oracle_params(p))
+    found = 0
+    for t in range(3):
+        if t:
+            orc.advance()
+        pairs = tr.slice(0, t)
+        est.update(helpers.to_device(pairs))
+        orc.scan(pairs)
+        rep = est.close_slice()
+        assert np.array_equal(est.hot_bitmap(), orc.hot())
+        assert est.stats()["active2"] == orc.row_counts().tolist()
+        compare_report(rep, orc.detect())
+        found += rep.n_candidates
+    assert found > 0
+
+
 @pytest.mark.parametrize("mode", [DIRECT, TILED])
 @pytest.mark.parametrize("n", [1, 2, 3, 31, 1000, 65537, 300001])
 def test_ragged_sizes_and_tiles(n, mode):
