@@ -177,6 +177,65 @@ __device__ __forceinline__ void any_part(const uint32_t* __restrict__ hot_bits, 
   }
 }
 
+// Eq. 12's P = prod_i SF(i,k), SF(i,k) = active2[i] / row_len2 (Definition 4), multiplied
+// in row order with round-to-nearest FP64 operations.
+__device__ __forceinline__ double setting_product(const uint32_t* active2, uint32_t r2, uint64_t row_len2) {
+  double P = 1.0;
+  for (uint32_t i = 0; i < r2; ++i) P = __dmul_rn(P, __ddiv_rn((double)active2[i], (double)row_len2));
+  return P;
+}
+
+struct LcResult {
+  double w;       // corrected weight (Eq. 12), clamped to [0, eta' - 1]
+  float est;      // Eq. 8 on w
+  uint8_t flags;  // SSE_FLAG_SUPER when w >= w_theta; SSE_FLAG_SATURATED when clamped at eta' - 1
+};
+
+// Algorithm 8's last steps for a host whose union SLE has U active cells: w from Eq. 12 in
+// FP64 with round-to-nearest operations in a fixed order (so the super point decision is
+// exact), and the estimate of Eq. 8.
+__device__ __forceinline__ LcResult lc_estimate(uint32_t U, double P, double eta2, double w_theta) {
+  LcResult res;
+  res.flags = 0;
+  double w;
+  if (P >= 1.0) {
+    w = eta2 - 1.0;
+    res.flags |= SSE_FLAG_SATURATED;
+  } else {
+    const double num = __dsub_rn((double)U, __dmul_rn(eta2, P));
+    const double den = __dsub_rn(1.0, P);
+    w = __ddiv_rn(num, den);
+    if (w < 0.0) w = 0.0;
+    if (!(w <= eta2 - 1.0)) {
+      w = eta2 - 1.0;
+      res.flags |= SSE_FLAG_SATURATED;
+    }
+  }
+  // est = -eta' ln(1 - x), x = w / eta' < 1 (eta' is a power of two, so x is exact). The
+  // flag is decided on w in FP64; the FP32 estimate is taken in FP32 from an argument that
+  // is exact in FP64: log1p(-x) below x = 1/2 (no cancellation), else log(1 - x), where
+  // 1 - x is exact (Sterbenz). Either way a few FP32 ulps from the FP64 value.
+  const double x = __dmul_rn(w, 1.0 / eta2);
+  const float lg = x < 0.5 ? log1pf((float)-x) : logf((float)__dsub_rn(1.0, x));
+  res.est = -(float)eta2 * lg;
+  if (w >= w_theta) res.flags |= SSE_FLAG_SUPER;
+  res.w = w;
+  return res;
+}
+
+// lc_estimate for every U = 0..eta' under one close's P (the same for all of its hosts),
+// built by `blocks` blocks of k_hot_prep; the estimates of that close then look U up. Unused
+// (est == nullptr) outside the slice close.
+struct EstTable {
+  double* w;
+  float* est;
+  uint8_t* flags;
+  const uint32_t* active2;  // SLEA row counts of the close (for P)
+  uint64_t row_len2;
+  double w_theta;
+  uint32_t r2, eta2, blocks;
+};
+
 // Everything the join reads from the hot bitmap, in one launch: blocks [0, n_lists) build
 // the hot lists of rows 0-1 and the hot counts, the next n_regroup blocks the regrouped
 // tables of rows 2..r-1, the rest (when any2 != NULL) the "any hot" bitmaps of rows 2 and 3
@@ -186,14 +245,31 @@ __global__ void __launch_bounds__(256) k_hot_prep(const uint32_t* __restrict__ h
                                                   uint32_t* __restrict__ list0, uint32_t* __restrict__ list1,
                                                   uint32_t* __restrict__ n_list, uint32_t* __restrict__ tables,
                                                   uint32_t* __restrict__ any2, uint32_t* __restrict__ any3,
-                                                  uint32_t n_lists, uint32_t n_regroup) {
+                                                  uint32_t n_lists, uint32_t n_regroup, EstTable tab) {
   const uint32_t b = blockIdx.x;
+  if (b >= gridDim.x - tab.blocks) {  // the last tab.blocks blocks: the estimate table
+    // Eq. 12's P as in setting_product (the same quotients, multiplied in row order), with the
+    // r' divisions done side by side
+    __shared__ double quot[kMaxRows];
+    if (threadIdx.x < tab.r2) quot[threadIdx.x] = __ddiv_rn((double)tab.active2[threadIdx.x], (double)tab.row_len2);
+    __syncthreads();
+    double P = 1.0;
+    for (uint32_t i = 0; i < tab.r2; ++i) P = __dmul_rn(P, quot[i]);
+    const uint32_t U = (b - (gridDim.x - tab.blocks)) * blockDim.x + threadIdx.x;
+    if (U <= tab.eta2) {
+      const LcResult res = lc_estimate(U, P, (double)tab.eta2, tab.w_theta);
+      tab.w[U] = res.w;
+      tab.est[U] = res.est;
+      tab.flags[U] = res.flags;
+    }
+    return;
+  }
   if (b < n_lists) {
     hot_lists_part(hot_bits, r, q, hot_count, list0, list1, n_list, b, n_lists);
   } else if (b < n_lists + n_regroup) {
     regroup_part(hot_bits, r, q, delta, tables, b - n_lists, n_regroup);
   } else if (any2) {
-    const uint32_t rest = gridDim.x - n_lists - n_regroup, x = b - n_lists - n_regroup;
+    const uint32_t rest = gridDim.x - n_lists - n_regroup - tab.blocks, x = b - n_lists - n_regroup;
     const uint32_t half = (rest + 1) / 2;
     if (x < half)
       any_part(hot_bits, 2, q, delta, any2, x, half);
@@ -757,7 +833,8 @@ __device__ __forceinline__ uint32_t cell_age(uint32_t s, const uint8_t* age_lut,
 template <typename St>
 __global__ void __launch_bounds__(kEstThreads, 4) k_estimate(
     const __grid_constant__ KParams p, const uint8_t* __restrict__ sle_bytes, const uint32_t* __restrict__ hosts,
-    const uint32_t* __restrict__ n_ptr, uint32_t n, const uint32_t* __restrict__ active2, double w_theta,
+    const uint32_t* __restrict__ n_ptr, uint32_t n, const uint32_t* __restrict__ active2, EstTable tab,
+    double w_theta,
     uint32_t cs_value, const uint32_t* __restrict__ clock, float* __restrict__ est, uint8_t* __restrict__ flags,
     double* __restrict__ w_out,
     uint32_t* __restrict__ u_out, uint32_t* __restrict__ hist, uint32_t* __restrict__ n_super) {
@@ -766,9 +843,12 @@ __global__ void __launch_bounds__(kEstThreads, 4) k_estimate(
   __shared__ uint32_t warp_u[kEstThreads / 32];
   __shared__ const St* row_base[kMaxRows];
   const St* sle = reinterpret_cast<const St*>(sle_bytes);
+  // the count, the stamp and the first host are loaded together (the grid is never larger
+  // than the host buffer, so hosts[blockIdx.x] is in bounds even past the count)
+  const uint32_t first_aip = hosts[blockIdx.x];
   const uint32_t count = n_ptr ? min(*n_ptr, n) : n;
-  if (blockIdx.x >= count) return;  // the grid is sized for the capacity
   const uint32_t cs = clock ? *clock : cs_value;
+  if (blockIdx.x >= count) return;  // the grid is sized for the capacity
   const bool vec16 = (p.delta2 & 15u) == 0;
   const bool u_only = sizeof(St) == 1 && vec16 && !hist;  // U from byte-wise activity masks
   if (sizeof(St) == 1 && !u_only)
@@ -777,16 +857,11 @@ __global__ void __launch_bounds__(kEstThreads, 4) k_estimate(
       age_lut[s] = a < p.k ? (uint8_t)a : 255;
     }
   const double eta2 = (double)p.eta2;
-  // Eq. 12's P = prod_i SF(i,k), SF(i,k) = active2[i] / row_len2 (Definition 4), multiplied
-  // in row order; the same for every host, so it is computed while the first gathers run
+  // Eq. 12's P: the same for every host (and already applied in the table when there is one)
   __shared__ double s_P;
-  if (threadIdx.x == 0) {
-    double P = 1.0;
-    for (uint32_t i = 0; i < p.r2; ++i) P = __dmul_rn(P, __ddiv_rn((double)active2[i], (double)p.row_len2));
-    s_P = P;
-  }
+  if (threadIdx.x == 0 && !tab.est) s_P = setting_product(active2, p.r2, p.row_len2);
   for (uint32_t h = blockIdx.x; h < count; h += gridDim.x) {
-    const uint32_t aip = hosts[h];
+    const uint32_t aip = h == blockIdx.x ? first_aip : hosts[h];
     if (threadIdx.x < p.r2) {
       const uint32_t j = mas_top(p.key_a[kLH + threadIdx.x], p.key_b[kLH + threadIdx.x], aip, p.q2);
       row_base[threadIdx.x] = sle + threadIdx.x * p.row_pitch2 + (uint64_t)j * p.delta2;
@@ -874,31 +949,18 @@ __global__ void __launch_bounds__(kEstThreads, 4) k_estimate(
     if (threadIdx.x == 0) {
       uint32_t U = 0;
       for (int x = 0; x < kEstThreads / 32; ++x) U += warp_u[x];
-      const double P = s_P;  // Eq. 12
-      uint8_t f = 0;
-      double w;
-      if (P >= 1.0) {
-        w = eta2 - 1.0;
-        f |= SSE_FLAG_SATURATED;
+      LcResult res;
+      if (tab.est) {  // this close's table
+        res.est = tab.est[U];
+        res.flags = tab.flags[U];
+        res.w = w_out ? tab.w[U] : 0.0;
       } else {
-        const double num = __dsub_rn((double)U, __dmul_rn(eta2, P));
-        const double den = __dsub_rn(1.0, P);
-        w = __ddiv_rn(num, den);
-        if (w < 0.0) w = 0.0;
-        if (!(w <= eta2 - 1.0)) {
-          w = eta2 - 1.0;
-          f |= SSE_FLAG_SATURATED;
-        }
+        res = lc_estimate(U, s_P, eta2, w_theta);
       }
-      // Eq. 8 on the corrected weight.
-      const double e = __dmul_rn(-eta2, log(__ddiv_rn(__dsub_rn(eta2, w), eta2)));
-      if (w >= w_theta) {
-        f |= SSE_FLAG_SUPER;
-        if (n_super) atomicAdd(n_super, 1u);
-      }
-      est[h] = (float)e;
-      if (flags) flags[h] = f;
-      if (w_out) w_out[h] = w;
+      if ((res.flags & SSE_FLAG_SUPER) && n_super) atomicAdd(n_super, 1u);
+      est[h] = res.est;
+      if (flags) flags[h] = res.flags;
+      if (w_out) w_out[h] = res.w;
       if (u_out) u_out[h] = U;
     }
     __syncthreads();

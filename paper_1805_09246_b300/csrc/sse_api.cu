@@ -124,6 +124,7 @@ struct sse_handle {
   uint8_t* flags = nullptr;
   CloseScratch* scratch = nullptr;
   uint32_t* query_active2 = nullptr;
+  uint8_t* est_table = nullptr;  // per-close estimate table (EstTable): w | est | flags over U = 0..eta'
   uint32_t cand_cap = 0;  // max_candidates
   CloseScratch* host_scratch = nullptr;  // pinned
   sse_stats stats;
@@ -442,6 +443,7 @@ void sse_destroy(sse_handle* h) {
   cudaFree(h->flags);
   cudaFree(h->scratch);
   cudaFree(h->query_active2);
+  cudaFree(h->est_table);
   cudaFree(h->any2);
   cudaFree(h->any3);
   cudaFree(h->rhfg_tab);
@@ -494,6 +496,7 @@ int sse_init(const sse_params* p, void* cuda_stream, sse_handle** out) {
             cudaMalloc(&h->flags, (uint64_t)h->cand_cap) == cudaSuccess &&
             cudaMalloc(&h->scratch, sizeof(CloseScratch)) == cudaSuccess &&
             cudaMalloc(&h->query_active2, kMaxRows * 4) == cudaSuccess &&
+            cudaMalloc(&h->est_table, (uint64_t)(q.eta2 + 1) * 13 + 16) == cudaSuccess &&
             cudaMallocHost(&h->host_scratch, sizeof(CloseScratch)) == cudaSuccess;
   if (!ok) {
     cudaGetLastError();
@@ -729,6 +732,23 @@ int sse_advance(sse_handle* h) {
 
 namespace {
 
+// The close's estimate table: (eta' + 1) entries of w (FP64), est (FP32) and flags in one
+// allocation, built by the last blocks of k_hot_prep from the close's row counts.
+EstTable est_table(sse_handle* h, const uint32_t* active2) {
+  const uint64_t n = (uint64_t)h->p.eta2 + 1;
+  EstTable t;
+  t.w = reinterpret_cast<double*>(h->est_table);
+  t.est = reinterpret_cast<float*>(h->est_table + n * 8);
+  t.flags = h->est_table + n * 12;
+  t.active2 = active2;
+  t.row_len2 = h->kp.row_len2;
+  t.w_theta = h->d.w_theta;
+  t.r2 = h->p.r2;
+  t.eta2 = h->p.eta2;
+  t.blocks = (uint32_t)((n + 255) / 256);
+  return t;
+}
+
 // Detection kernels of a close (no host synchronisation, so a CUDA graph can hold them):
 // the sorted candidates end in *sorted, estimates and flags in h->est / h->flags, and the
 // counters are copied to the pinned h->host_scratch.
@@ -743,9 +763,10 @@ int close_enqueue(sse_handle* h, uint32_t** sorted, bool copy_counters = true) {
     const uint32_t n_regroup = grid_for(h, words * (h->p.r - 2), 256, 2);
     const uint32_t any_each = (any_words(h->p.q, h->p.delta) + 255) / 256;
     const uint32_t n_any = h->any2 ? (h->any3 ? 2 * any_each : any_each) : 0u;
-    k_hot_prep<<<n_lists + n_regroup + n_any, 256, 0, h->stream>>>(h->hot_bits, h->p.r, h->p.q, h->p.delta, sc->hot,
-                                                                  h->list0, h->list1, sc->n_list, h->tables, h->any2,
-                                                                  h->any3, n_lists, n_regroup);
+    const EstTable tab = est_table(h, sc->active2);
+    k_hot_prep<<<n_lists + n_regroup + n_any + tab.blocks, 256, 0, h->stream>>>(
+        h->hot_bits, h->p.r, h->p.q, h->p.delta, sc->hot, h->list0, h->list1, sc->n_list, h->tables, h->any2,
+        h->any3, n_lists, n_regroup, tab);
     SSE_LAUNCHED(h);
     if (h->kp.delta <= 5)
       (h->join_stage ? k_join_tiled<true> : k_join_tiled<false>)<<<h->join_grid, kJoinTiledThreads,
@@ -766,7 +787,7 @@ int close_enqueue(sse_handle* h, uint32_t** sorted, bool copy_counters = true) {
     const int grid = grid_for(h, h->cand_cap, 1, 8);
     const auto est_fn = h->wide ? k_estimate<uint16_t> : k_estimate<uint8_t>;
     est_fn<<<grid, kEstThreads, 0, h->stream>>>(h->kp, h->sle, *sorted, &sc->n_cand, h->cand_cap, sc->active2,
-                                                h->d.w_theta, stamp_of(h->slice, h->smod), h->clock, h->est, h->flags,
+                                                est_table(h, sc->active2), h->d.w_theta, stamp_of(h->slice, h->smod), h->clock, h->est, h->flags,
                                                     nullptr, nullptr, nullptr, &sc->n_super);
     SSE_LAUNCHED(h);
   }
@@ -1024,7 +1045,7 @@ int sse_query(sse_handle* h, const uint32_t* d_hosts, uint32_t n, float* d_est, 
   if (rc) return rc;
   const int grid = grid_for(h, n, 1, 16);
   const auto est_fn = h->wide ? k_estimate<uint16_t> : k_estimate<uint8_t>;
-  est_fn<<<grid, kEstThreads, 0, h->stream>>>(h->kp, h->sle, d_hosts, nullptr, n, h->query_active2,
+  est_fn<<<grid, kEstThreads, 0, h->stream>>>(h->kp, h->sle, d_hosts, nullptr, n, h->query_active2, EstTable{},
                                                       h->d.w_theta, stamp_of(h->slice, h->smod), h->clock, d_est, d_flags, nullptr,
                                                       nullptr, d_hist, nullptr);
   SSE_LAUNCHED(h);
@@ -1184,7 +1205,8 @@ extern "C" int sse_query_noalloc(const sse_params* p, const uint8_t* d_sle, uint
       kp, nullptr, const_cast<uint8_t*>(d_sle), nullptr, counts, stamp_of(slice), nullptr, 0u, 0u);
   if (cudaGetLastError() != cudaSuccess) return SSE_ERR_CUDA;
   uint64_t grid = std::min<uint64_t>((uint64_t)n, (uint64_t)num_sms * 16);
-  k_estimate<uint8_t><<<(unsigned)grid, kEstThreads, 0, stream>>>(kp, d_sle, d_hosts, nullptr, n, counts, d.w_theta,
+  k_estimate<uint8_t><<<(unsigned)grid, kEstThreads, 0, stream>>>(kp, d_sle, d_hosts, nullptr, n, counts, EstTable{},
+                                                             d.w_theta,
                                                              stamp_of(slice), nullptr, d_est, d_flags, nullptr, nullptr,
                                                              nullptr, nullptr);
   if (cudaGetLastError() != cudaSuccess) return SSE_ERR_CUDA;
