@@ -39,60 +39,51 @@ __device__ __forceinline__ uint32_t word_keep(uint32_t w, Window8 win, uint32_t 
   }
 }
 
-// Spreads the 16 low bits of x to the even bit positions (Morton interleave).
-__device__ __forceinline__ uint32_t spread16(uint32_t x) {
-  x &= 0xFFFFu;
-  x = (x | (x << 8)) & 0x00FF00FFu;
-  x = (x | (x << 4)) & 0x0F0F0F0Fu;
-  x = (x | (x << 2)) & 0x33333333u;
-  x = (x | (x << 1)) & 0x55555555u;
-  return x;
-}
-
-// RSRA part of the pass for 8-bit cells: two SREs (16 bytes) per load, four loads in flight,
-// 32-bit indices. Lane l of a warp holds SREs 2(b + l) and 2(b + l) + 1 of the warp's 64
-// consecutive SREs; their hot flags (two ballots) are interleaved into the two hot-bitmap
-// words, written by lanes 0 and 1.
+// RSRA part of the pass for 8-bit cells: one SRE (8 bytes) per load, eight loads in flight,
+// 32-bit indices. A warp covers 64 consecutive SREs 64j .. 64j + 63 per step: lane l holds
+// SREs 64j + l and 64j + 32 + l, so its two ballots are the two hot-bitmap words of those
+// SREs as they are (lane 0 writes both).
 template <bool WRAP>
 __device__ __forceinline__ void close_rsra8(const KParams& p, uint8_t* __restrict__ sre,
                                            uint32_t* __restrict__ hot_bits, Window8 win, uint32_t mode) {
   const bool expire = (mode & 1u) != 0;
-  const uint32_t n_sre = p.r << p.q;  // a multiple of 32
-  const uint32_t n_vec = n_sre >> 1;
-  uint4* words = reinterpret_cast<uint4*>(sre);
+  const uint32_t n_sre = p.r << p.q;         // a multiple of 32 (q >= 5)
+  const uint32_t n_pair = (n_sre + 63) >> 6;  // warp steps: 64 SREs each, the last maybe 32
+  uint2* words = reinterpret_cast<uint2*>(sre);
   const uint32_t lane = threadIdx.x & 31u;
-  const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
-  const uint32_t nthreads = gridDim.x * blockDim.x;  // a multiple of 32
-  constexpr int kLoads = 4;
-  for (uint32_t g0 = tid; g0 - lane < n_vec; g0 += kLoads * nthreads) {
-    uint4 v[kLoads];
+  const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;  // blockDim.x is a multiple of 32
+  constexpr int kSteps = 4;                               // warp steps in flight (8 loads per lane)
+  for (uint32_t j0 = warp; j0 < n_pair; j0 += kSteps * nwarps) {
+    uint2 v[kSteps][2];
 #pragma unroll
-    for (int u = 0; u < kLoads; ++u) {
-      const uint32_t g = g0 + u * nthreads;
-      v[u] = g < n_vec ? words[g] : make_uint4(0u, 0u, 0u, 0u);
+    for (int u = 0; u < kSteps; ++u) {
+      const uint32_t j = j0 + u * nwarps;  // warp-uniform
+      if (j < n_pair) {
+        v[u][0] = words[64 * j + lane];
+        v[u][1] = 64 * j + 32 < n_sre ? words[64 * j + 32 + lane] : make_uint2(0u, 0u);
+      }
     }
 #pragma unroll
-    for (int u = 0; u < kLoads; ++u) {
-      const uint32_t g = g0 + u * nthreads;
-      if (g - lane >= n_vec) break;  // warp-uniform: the whole warp is past the end
-      const uint32_t x[4] = {v[u].x, v[u].y, v[u].z, v[u].w};
-      uint32_t act[4];
+    for (int u = 0; u < kSteps; ++u) {
+      const uint32_t j = j0 + u * nwarps;
+      if (j >= n_pair) break;  // warp-uniform
+      uint32_t bal[2];
 #pragma unroll
-      for (int i = 0; i < 4; ++i) act[i] = active_hi8<WRAP>(x[i], win);
-      const uint32_t w0 = __popc(act[0]) + __popc(act[1]);  // SRE 2g
-      const uint32_t w1 = __popc(act[2]) + __popc(act[3]);  // SRE 2g + 1
-      const uint32_t b0 = __ballot_sync(0xFFFFFFFFu, w0 >= p.hot_min);
-      const uint32_t b1 = __ballot_sync(0xFFFFFFFFu, w1 >= p.hot_min);
-      if ((mode & 2u) && lane < 2) {
-        const uint32_t word = ((g - lane) >> 4) + lane;  // the warp's SREs start at 2(g - lane)
-        if (word < (n_sre >> 5)) hot_bits[word] = spread16(b0 >> (16 * lane)) | (spread16(b1 >> (16 * lane)) << 1);
+      for (int h = 0; h < 2; ++h) {
+        const uint32_t a0 = active_hi8<WRAP>(v[u][h].x, win), a1 = active_hi8<WRAP>(v[u][h].y, win);
+        bal[h] = __ballot_sync(0xFFFFFFFFu, __popc(a0) + __popc(a1) >= p.hot_min);
+        if (expire && 64 * j + 32 * h < n_sre) {
+          // cells that are set (non-zero) but not active have left the window
+          const uint32_t e0 = v[u][h].x & ~((a0 >> 7) * 0xFFu), e1 = v[u][h].y & ~((a1 >> 7) * 0xFFu);
+          if (e0 | e1) words[64 * j + 32 * h + lane] = make_uint2(v[u][h].x ^ e0, v[u][h].y ^ e1);
+        }
       }
-      if (expire && g < n_vec) {
-        // cells that are set (non-zero) but not active have left the window
-        const uint32_t e0 = x[0] & ~((act[0] >> 7) * 0xFFu), e1 = x[1] & ~((act[1] >> 7) * 0xFFu);
-        const uint32_t e2 = x[2] & ~((act[2] >> 7) * 0xFFu), e3 = x[3] & ~((act[3] >> 7) * 0xFFu);
-        if (e0 | e1 | e2 | e3)
-          words[g] = make_uint4(x[0] ^ e0, x[1] ^ e1, x[2] ^ e2, x[3] ^ e3);
+      if ((mode & 2u) && lane == 0) {
+        if (64 * j + 32 < n_sre)
+          reinterpret_cast<uint2*>(hot_bits)[j] = make_uint2(bal[0], bal[1]);
+        else
+          hot_bits[2 * j] = bal[0];  // the ragged last step: SREs 64j .. 64j + 31 only
       }
     }
   }

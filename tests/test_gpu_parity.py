@@ -85,6 +85,20 @@ def test_small_trace_end_to_end(mode):
     assert sum(r.n_super for r in reports) > 100  # the planted super points are found
 
 
+def test_close_pass_with_a_ragged_last_warp_step():
+    """r * 2^q = 288 SREs (r=9, q=5): the close pass covers 64 SREs per warp step, so its
+    last step holds only 32. State (expiry), hot bitmap, counts and reports."""
+    S = sse()
+    p = S.Params(r=9, q=5, delta=4, q2=6, eta2=64, delta2=8, k=3, theta=8, seed=31)
+    rng = np.random.default_rng(31)
+    slices = []
+    for _ in range(5):
+        pairs = rng.integers(0, 2**32, (3000, 2), dtype=np.uint64).astype(np.uint32)
+        pairs[:, 0] %= 5
+        slices.append(pairs)
+    run_both(p, slices)
+
+
 def test_join_probes_global_any_hot_bitmaps():
     """q - delta = 19: the "any hot" bitmaps of rows 2 and 3 (64 KiB each) are too large to
     stage in shared memory, so the join probes them in global memory. Hot SREs, counts and
