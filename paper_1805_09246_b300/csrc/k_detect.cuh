@@ -678,7 +678,9 @@ __global__ void __launch_bounds__(kJoinTiledThreads) k_join_tiled(
 // * up to kSortChunk keys (the usual report): each key is placed at its rank, the number of
 //   smaller keys (ties, which a candidate set does not have, are broken by index); every
 //   block reads all keys into shared memory and kRankSplit neighbouring threads count one
-//   key's rank over interleaved parts of the keys, adding their counts with shuffles;
+//   key's rank over interleaved parts of the keys, adding their counts with shuffles. With
+//   small_by_estimate set the launch leaves these to k_estimate, whose block for a host
+//   counts that host's rank while it gathers the SLEs, and returns at once;
 // * more: every kSortChunk-key chunk is sorted in shared memory (bitonic network, tail
 //   padded with 0xFFFFFFFF, which sorts last), then sorted runs are merged pairwise (each key
 //   placed by a binary search in the partner run), pass after pass, with a grid-wide
@@ -727,10 +729,12 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_candidates(uint32_t* __re
                                                                   uint32_t* __restrict__ out,
                                                                   const uint32_t* __restrict__ n_ptr, uint32_t cap,
                                                                   uint32_t* __restrict__ bar,
-                                                                  uint32_t* __restrict__ error) {
+                                                                  uint32_t* __restrict__ error,
+                                                                  uint32_t small_by_estimate) {
   __shared__ uint32_t s[kSortChunk];
   const uint32_t n = min(*n_ptr, cap);
   if (n <= kSortChunk) {
+    if (small_by_estimate) return;
     const uint32_t per_block = kSortThreads / kRankSplit;
     if (blockIdx.x * per_block >= n) return;
     for (uint32_t x = threadIdx.x; x < n; x += blockDim.x) s[x] = keys[x];
@@ -834,7 +838,7 @@ template <typename St>
 __global__ void __launch_bounds__(kEstThreads, 4) k_estimate(
     const __grid_constant__ KParams p, const uint8_t* __restrict__ sle_bytes, const uint32_t* __restrict__ hosts,
     const uint32_t* __restrict__ n_ptr, uint32_t n, const uint32_t* __restrict__ active2, EstTable tab,
-    double w_theta,
+    const uint32_t* __restrict__ unsorted, uint32_t* __restrict__ hosts_out, double w_theta,
     uint32_t cs_value, const uint32_t* __restrict__ clock, float* __restrict__ est, uint8_t* __restrict__ flags,
     double* __restrict__ w_out,
     uint32_t* __restrict__ u_out, uint32_t* __restrict__ hist, uint32_t* __restrict__ n_super) {
@@ -844,11 +848,16 @@ __global__ void __launch_bounds__(kEstThreads, 4) k_estimate(
   __shared__ const St* row_base[kMaxRows];
   const St* sle = reinterpret_cast<const St*>(sle_bytes);
   // the count, the stamp and the first host are loaded together (the grid is never larger
-  // than the host buffer, so hosts[blockIdx.x] is in bounds even past the count)
-  const uint32_t first_aip = hosts[blockIdx.x];
+  // than the host buffers, so index blockIdx.x is in bounds even past the count)
+  const uint32_t first_aip = (unsorted ? unsorted : hosts)[blockIdx.x];
   const uint32_t count = n_ptr ? min(*n_ptr, n) : n;
   const uint32_t cs = clock ? *clock : cs_value;
   if (blockIdx.x >= count) return;  // the grid is sized for the capacity
+  // rank mode (unsorted given, at most kSortChunk hosts): the hosts come unsorted, and the
+  // outputs of each go to its rank in ascending order (the number of smaller hosts; ties,
+  // which a candidate set does not have, broken by index), hosts_out included; otherwise
+  // `hosts` is already sorted and the outputs go to the host's own index
+  const bool rank_mode = unsorted != nullptr && count <= kSortChunk && hist == nullptr;
   const bool vec16 = (p.delta2 & 15u) == 0;
   const bool u_only = sizeof(St) == 1 && vec16 && !hist;  // U from byte-wise activity masks
   if (sizeof(St) == 1 && !u_only)
@@ -860,8 +869,33 @@ __global__ void __launch_bounds__(kEstThreads, 4) k_estimate(
   // Eq. 12's P: the same for every host (and already applied in the table when there is one)
   __shared__ double s_P;
   if (threadIdx.x == 0 && !tab.est) s_P = setting_product(active2, p.r2, p.row_len2);
+  __shared__ uint32_t warp_rank[kEstThreads / 32];
   for (uint32_t h = blockIdx.x; h < count; h += gridDim.x) {
-    const uint32_t aip = h == blockIdx.x ? first_aip : hosts[h];
+    const uint32_t aip = rank_mode ? (h == blockIdx.x ? first_aip : unsorted[h])
+                                   : (h == blockIdx.x && !unsorted ? first_aip : hosts[h]);
+    // rank mode: this thread's share of the host's rank, over keys y = threadIdx.x + i *
+    // blockDim.x; the first eight are loaded here and compared after the SLE gathers, so that
+    // both sets of loads are in flight together
+    uint32_t rank = 0;
+    uint32_t kk[8];
+    auto rank_batch = [&](uint32_t y0, bool load) {
+#pragma unroll
+      for (uint32_t u = 0; u < 8; ++u) {
+        const uint32_t y = y0 + u * blockDim.x + threadIdx.x;
+        if (load) kk[u] = y < count ? unsorted[y] : 0u;
+      }
+#pragma unroll
+      for (uint32_t u = 0; u < 8; ++u) {
+        const uint32_t y = y0 + u * blockDim.x + threadIdx.x;
+        rank += (y < count && (kk[u] < aip || (kk[u] == aip && y < h))) ? 1u : 0u;
+      }
+    };
+    if (rank_mode)
+#pragma unroll
+      for (uint32_t u = 0; u < 8; ++u) {
+        const uint32_t y = u * blockDim.x + threadIdx.x;
+        kk[u] = y < count ? unsorted[y] : 0u;
+      }
     if (threadIdx.x < p.r2) {
       const uint32_t j = mas_top(p.key_a[kLH + threadIdx.x], p.key_b[kLH + threadIdx.x], aip, p.q2);
       row_base[threadIdx.x] = sle + threadIdx.x * p.row_pitch2 + (uint64_t)j * p.delta2;
@@ -940,15 +974,29 @@ __global__ void __launch_bounds__(kEstThreads, 4) k_estimate(
         }
       }
     }
+    if (rank_mode) {
+      rank_batch(0, false);  // the keys loaded before the gathers
+      for (uint32_t y0 = 8 * blockDim.x; y0 < count; y0 += 8 * blockDim.x) rank_batch(y0, true);
+    }
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) u += __shfl_xor_sync(0xFFFFFFFFu, u, off);
-    if ((threadIdx.x & 31) == 0) warp_u[threadIdx.x >> 5] = u;
+    for (int off = 16; off > 0; off >>= 1) {
+      u += __shfl_xor_sync(0xFFFFFFFFu, u, off);
+      rank += __shfl_xor_sync(0xFFFFFFFFu, rank, off);
+    }
+    if ((threadIdx.x & 31) == 0) {
+      warp_u[threadIdx.x >> 5] = u;
+      warp_rank[threadIdx.x >> 5] = rank;
+    }
     __syncthreads();
     if (hist && hist_smem)
       for (uint32_t a = threadIdx.x; a < p.k; a += blockDim.x) hist_row[a] = sh_hist[a];
     if (threadIdx.x == 0) {
-      uint32_t U = 0;
-      for (int x = 0; x < kEstThreads / 32; ++x) U += warp_u[x];
+      uint32_t U = 0, at = 0;
+      for (int x = 0; x < kEstThreads / 32; ++x) {
+        U += warp_u[x];
+        at += warp_rank[x];
+      }
+      const uint32_t slot = rank_mode ? at : h;  // where this host's outputs go
       LcResult res;
       if (tab.est) {  // this close's table
         res.est = tab.est[U];
@@ -958,10 +1006,11 @@ __global__ void __launch_bounds__(kEstThreads, 4) k_estimate(
         res = lc_estimate(U, s_P, eta2, w_theta);
       }
       if ((res.flags & SSE_FLAG_SUPER) && n_super) atomicAdd(n_super, 1u);
-      est[h] = res.est;
-      if (flags) flags[h] = res.flags;
-      if (w_out) w_out[h] = res.w;
-      if (u_out) u_out[h] = U;
+      est[slot] = res.est;
+      if (flags) flags[slot] = res.flags;
+      if (w_out) w_out[slot] = res.w;
+      if (u_out) u_out[slot] = U;
+      if (rank_mode) hosts_out[slot] = aip;
     }
     __syncthreads();
   }

@@ -364,8 +364,9 @@ int launch_sort(sse_handle* h) {
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   CloseScratch* sc = h->scratch;
+  // up to kSortChunk candidates are placed by the estimate kernel (rank mode)
   SSE_CUDA(h, cudaLaunchKernelEx(&cfg, k_sort_candidates, h->cand, h->cand_alt, h->cand_out,
-                                 (const uint32_t*)&sc->n_cand, h->cand_cap, sc->barrier, &sc->error));
+                                 (const uint32_t*)&sc->n_cand, h->cand_cap, sc->barrier, &sc->error, 1u));
   SSE_LAUNCHED(h);
   return SSE_OK;
 }
@@ -786,9 +787,11 @@ int close_enqueue(sse_handle* h, uint32_t** sorted, bool copy_counters = true) {
   {
     const int grid = grid_for(h, h->cand_cap, 1, 8);
     const auto est_fn = h->wide ? k_estimate<uint16_t> : k_estimate<uint8_t>;
+    // up to kSortChunk candidates: rank mode (h->cand unsorted in, h->cand_out written here)
     est_fn<<<grid, kEstThreads, 0, h->stream>>>(h->kp, h->sle, *sorted, &sc->n_cand, h->cand_cap, sc->active2,
-                                                est_table(h, sc->active2), h->d.w_theta, stamp_of(h->slice, h->smod), h->clock, h->est, h->flags,
-                                                    nullptr, nullptr, nullptr, &sc->n_super);
+                                                est_table(h, sc->active2), h->cand, h->cand_out, h->d.w_theta,
+                                                stamp_of(h->slice, h->smod), h->clock, h->est, h->flags, nullptr,
+                                                nullptr, nullptr, &sc->n_super);
     SSE_LAUNCHED(h);
   }
   if (copy_counters)
@@ -1046,7 +1049,7 @@ int sse_query(sse_handle* h, const uint32_t* d_hosts, uint32_t n, float* d_est, 
   const int grid = grid_for(h, n, 1, 16);
   const auto est_fn = h->wide ? k_estimate<uint16_t> : k_estimate<uint8_t>;
   est_fn<<<grid, kEstThreads, 0, h->stream>>>(h->kp, h->sle, d_hosts, nullptr, n, h->query_active2, EstTable{},
-                                                      h->d.w_theta, stamp_of(h->slice, h->smod), h->clock, d_est, d_flags, nullptr,
+                                                      nullptr, nullptr, h->d.w_theta, stamp_of(h->slice, h->smod), h->clock, d_est, d_flags, nullptr,
                                                       nullptr, d_hist, nullptr);
   SSE_LAUNCHED(h);
   return SSE_OK;
@@ -1206,7 +1209,7 @@ extern "C" int sse_query_noalloc(const sse_params* p, const uint8_t* d_sle, uint
   if (cudaGetLastError() != cudaSuccess) return SSE_ERR_CUDA;
   uint64_t grid = std::min<uint64_t>((uint64_t)n, (uint64_t)num_sms * 16);
   k_estimate<uint8_t><<<(unsigned)grid, kEstThreads, 0, stream>>>(kp, d_sle, d_hosts, nullptr, n, counts, EstTable{},
-                                                             d.w_theta,
+                                                             nullptr, nullptr, d.w_theta,
                                                              stamp_of(slice), nullptr, d_est, d_flags, nullptr, nullptr,
                                                              nullptr, nullptr);
   if (cudaGetLastError() != cudaSuccess) return SSE_ERR_CUDA;
