@@ -75,7 +75,7 @@ __global__ void __launch_bounds__(kTiledThreads, 1) k_update_tiled(const __grid_
                                                                    const uint32_t* __restrict__ clock) {
   const St stamp = (St)(clock ? *clock : stamp_value);
   St* sre = reinterpret_cast<St*>(sre_bytes);
-  extern __shared__ uint32_t bm[];
+  extern __shared__ __align__(16) uint32_t bm[];
   const uint32_t tile = blockIdx.x % g.tiles;
   const uint32_t group = blockIdx.x / g.tiles;
   const uint32_t row = tile / g.pieces;
@@ -150,12 +150,31 @@ __global__ void __launch_bounds__(kTiledThreads, 1) k_update_tiled(const __grid_
     touch(v.x, v.y);
     if (tile == 0) stamp_rsra(p, v.x, v.y, sre, stamp);
   }
+  // flush: OR the piece's bitmap into the global SLEA bitmap with bulk reductions done in L2
+  // by the Tensor Memory Accelerator (cp.reduce.async.bulk .or.b32), not one atomic per
+  // word from the SM. Both ends are 16-byte aligned and the size is a multiple of 16: the
+  // row pitch is a multiple of 4096 cells, a piece and its start multiples of 1024
+  // (bytes = cells / 8).
+  // The threads' shared-memory writes are made visible to the async proxy before thread 0
+  // issues the reductions, and thread 0 waits until they are complete before it exits.
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   __syncthreads();
-  // flush: OR the piece's non-zero words into the global SLEA bitmap
-  uint32_t* dst = gbits + (((uint64_t)row * p.row_pitch2 + lo) >> 5);
-  for (uint32_t w = threadIdx.x; w < words; w += blockDim.x) {
-    const uint32_t v = bm[w];
-    if (v) atomicOr(&dst[w], v);
+  if (threadIdx.x == 0) {
+    uint8_t* dst = reinterpret_cast<uint8_t*>(gbits) + (((uint64_t)row * p.row_pitch2 + lo) >> 3);
+    const uint32_t src = (uint32_t)__cvta_generic_to_shared(bm);
+    // the last piece of a row may reach past the row pitch (pieces are rounded up to 1024
+    // cells): only the cells of the row are reduced (those beyond are never set)
+    const uint64_t row_cells_left = p.row_pitch2 - lo;
+    const uint32_t bytes = (uint32_t)((row_cells_left < g.piece_bytes ? row_cells_left : g.piece_bytes) >> 3);
+    constexpr uint32_t kChunk = 32768u;
+    for (uint32_t off = 0; off < bytes; off += kChunk) {
+      const uint32_t n = bytes - off < kChunk ? bytes - off : kChunk;
+      asm volatile("cp.reduce.async.bulk.global.shared::cta.bulk_group.or.b32 [%0], [%1], %2;" ::"l"(dst + off),
+                   "r"(src + off), "r"(n)
+                   : "memory");
+    }
+    asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+    asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");  // the reductions are done
   }
 }
 
