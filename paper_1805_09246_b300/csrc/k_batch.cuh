@@ -38,7 +38,7 @@ __global__ void __launch_bounds__(kTiledThreads, 1)
                      uint32_t* __restrict__ tile_next, const uint32_t* __restrict__ clock,
                      uint8_t* __restrict__ g_sre) {
   const uint64_t* counts = in->counts;
-  extern __shared__ uint32_t bm[];
+  extern __shared__ __align__(16) uint32_t bm[];
   __shared__ uint64_t first_item[kMaxRouters + 1];
   __shared__ uint32_t sh_item;
   const uint8_t stamp = (uint8_t)*clock;
@@ -57,14 +57,17 @@ __global__ void __launch_bounds__(kTiledThreads, 1)
   const uint64_t total = first_item[n_routers];
   const SleTile st(p, row, lo, g.piece_bytes);
   auto touch = [&](uint32_t aip, uint32_t bip) { st.touch<WHOLE, false>(bm, aip, bip); };
-  auto flush = [&](int r) {
-    uint32_t* dst = rt.gbits[r] + (((uint64_t)row * p.row_pitch2 + lo) >> 5);
-    for (uint32_t w = threadIdx.x; w < words; w += blockDim.x) {
-      const uint32_t v = bm[w];
-      if (v) {
-        atomicOr(&dst[w], v);
-        bm[w] = 0;
-      }
+  // the bitmap of router r into its global SLEA bitmap (bitmap_or_bulk); with `zero`, the
+  // bitmap is cleared for the next router once the reductions have read it
+  auto flush = [&](int r, bool zero) {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    if (threadIdx.x == 0)
+      bitmap_or_bulk(bm, reinterpret_cast<uint8_t*>(rt.gbits[r]) + (((uint64_t)row * p.row_pitch2 + lo) >> 3),
+                     tile_flush_bytes(p.row_pitch2, lo, g.piece_bytes), !zero);
+    if (zero) {
+      __syncthreads();
+      for (uint32_t w = threadIdx.x; w < words; w += blockDim.x) bm[w] = 0;
     }
   };
   for (uint32_t w = threadIdx.x; w < words; w += blockDim.x) bm[w] = 0;
@@ -79,7 +82,7 @@ __global__ void __launch_bounds__(kTiledThreads, 1)
     int r = 0;
     while (r + 1 < n_routers && first_item[r + 1] <= it) ++r;
     if (r != cur) {
-      if (cur >= 0) flush(cur);  // flush also re-zeroes the words it empties
+      if (cur >= 0) flush(cur, true);
       __syncthreads();
       cur = r;
     }
@@ -156,7 +159,7 @@ __global__ void __launch_bounds__(kTiledThreads, 1)
       if (rsra) stamp_rsra(p, v.x, v.y, sre, stamp, g_sre);
     }
   }
-  if (cur >= 0) flush(cur);
+  if (cur >= 0) flush(cur, false);
   (void)sre_bytes;
 }
 

@@ -57,6 +57,35 @@ struct SleTile {
   }
 };
 
+// ORs `bytes` of a shared-memory bitmap into global memory with bulk reductions done in L2 by
+// the Tensor Memory Accelerator (cp.reduce.async.bulk .or.b32), not one atomic per word from
+// the SM. Called by one thread, after every thread's writes to the bitmap were followed by
+// fence.proxy.async.shared::cta and a barrier. Both addresses are 16-byte aligned and bytes
+// is a multiple of 16. Returns once the bitmap has been read (it may then be rewritten) or,
+// with `done`, once the reductions are complete.
+__device__ __forceinline__ void bitmap_or_bulk(const uint32_t* bm, uint8_t* dst, uint32_t bytes, bool done) {
+  const uint32_t src = (uint32_t)__cvta_generic_to_shared(bm);
+  constexpr uint32_t kChunk = 32768u;
+  for (uint32_t off = 0; off < bytes; off += kChunk) {
+    const uint32_t n = bytes - off < kChunk ? bytes - off : kChunk;
+    asm volatile("cp.reduce.async.bulk.global.shared::cta.bulk_group.or.b32 [%0], [%1], %2;" ::"l"(dst + off),
+                 "r"(src + off), "r"(n)
+                 : "memory");
+  }
+  asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+  if (done)
+    asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+  else
+    asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+}
+
+// Bytes of a tile's bitmap to reduce into the row: the last piece of a row may reach past
+// the row pitch (pieces are rounded up to 1024 cells), and cells beyond it are never set.
+__device__ __forceinline__ uint32_t tile_flush_bytes(uint64_t row_pitch2, uint32_t lo, uint32_t piece_bytes) {
+  const uint64_t left = row_pitch2 - lo;
+  return (uint32_t)((left < piece_bytes ? left : piece_bytes) >> 3);
+}
+
 struct TileGeometry {
   uint32_t tiles;         // tiles per group (r' * pieces)
   uint32_t pieces;        // pieces per SLEA row
@@ -150,32 +179,14 @@ __global__ void __launch_bounds__(kTiledThreads, 1) k_update_tiled(const __grid_
     touch(v.x, v.y);
     if (tile == 0) stamp_rsra(p, v.x, v.y, sre, stamp);
   }
-  // flush: OR the piece's bitmap into the global SLEA bitmap with bulk reductions done in L2
-  // by the Tensor Memory Accelerator (cp.reduce.async.bulk .or.b32), not one atomic per
-  // word from the SM. Both ends are 16-byte aligned and the size is a multiple of 16: the
-  // row pitch is a multiple of 4096 cells, a piece and its start multiples of 1024
-  // (bytes = cells / 8).
-  // The threads' shared-memory writes are made visible to the async proxy before thread 0
-  // issues the reductions, and thread 0 waits until they are complete before it exits.
+  // flush: OR the piece's bitmap into the global SLEA bitmap (bitmap_or_bulk). Byte offsets
+  // are cells / 8: the row pitch is a multiple of 4096 cells, a piece and its start
+  // multiples of 1024, so both ends are 16-byte aligned.
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   __syncthreads();
-  if (threadIdx.x == 0) {
-    uint8_t* dst = reinterpret_cast<uint8_t*>(gbits) + (((uint64_t)row * p.row_pitch2 + lo) >> 3);
-    const uint32_t src = (uint32_t)__cvta_generic_to_shared(bm);
-    // the last piece of a row may reach past the row pitch (pieces are rounded up to 1024
-    // cells): only the cells of the row are reduced (those beyond are never set)
-    const uint64_t row_cells_left = p.row_pitch2 - lo;
-    const uint32_t bytes = (uint32_t)((row_cells_left < g.piece_bytes ? row_cells_left : g.piece_bytes) >> 3);
-    constexpr uint32_t kChunk = 32768u;
-    for (uint32_t off = 0; off < bytes; off += kChunk) {
-      const uint32_t n = bytes - off < kChunk ? bytes - off : kChunk;
-      asm volatile("cp.reduce.async.bulk.global.shared::cta.bulk_group.or.b32 [%0], [%1], %2;" ::"l"(dst + off),
-                   "r"(src + off), "r"(n)
-                   : "memory");
-    }
-    asm volatile("cp.async.bulk.commit_group;" ::: "memory");
-    asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");  // the reductions are done
-  }
+  if (threadIdx.x == 0)
+    bitmap_or_bulk(bm, reinterpret_cast<uint8_t*>(gbits) + (((uint64_t)row * p.row_pitch2 + lo) >> 3),
+                   tile_flush_bytes(p.row_pitch2, lo, g.piece_bytes), true);
 }
 
 // Stamp every SLEA cell whose bit is set and clear the bitmap. One thread per bitmap word
