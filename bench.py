@@ -658,7 +658,7 @@ def main():
 
     if rank != 0:
         return
-    cpu = None if args.no_cpu or paper else cpu_baseline([host[t] for t in range(8)])
+    cpu = None if args.no_cpu or paper else cpu_baseline(host)
     close_sorted = sorted(close_ms)
     out = {
         "metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": world, "steps": args.steps,
