@@ -168,13 +168,15 @@ def test_autotune_keeps_state_and_picks_a_variant():
         assert np.array_equal(x, y)
 
 
-@pytest.mark.parametrize("params", ["paper", "core_link", "many_rows"])
+@pytest.mark.parametrize("params", ["paper", "core_link", "many_rows", "ragged_pieces"])
 def test_update_strategies_agree(params):
     """Direct and every tiled variant leave bit-identical stamps, including rows split into
-    several shared-memory pieces (the paper's q'=17 rows) and misaligned group starts."""
+    several shared-memory pieces (the paper's q'=17 rows; three pieces whose last one, rounded
+    up to 1024 cells, reaches 1024 cells past the row pitch) and misaligned group starts."""
     S = sse()
     p = {"paper": S.paper_params(k=8), "core_link": S.core_link_params(),
-         "many_rows": S.Params(r2=16, q2=14, eta2=2048, seed=4)}[params]
+         "many_rows": S.Params(r2=16, q2=14, eta2=2048, seed=4),
+         "ragged_pieces": S.Params(q2=17, delta2=32, eta2=4096, seed=6)}[params]
     rng = np.random.default_rng(7)
     n = (1 << 22) + 3
     src = rng.integers(0, 2**32, 1 << 20, dtype=np.uint64).astype(np.uint32)
