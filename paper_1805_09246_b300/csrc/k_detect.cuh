@@ -448,7 +448,7 @@ __global__ void __launch_bounds__(256) k_report(CloseScratch* __restrict__ sc, c
 // are staged in shared memory when `stage` is set; the blocks are small (kJoinTiledThreads)
 // so that several share an SM.
 constexpr int kJoinTiledThreads = 256;
-constexpr uint32_t kJoinQueueCap = 2048;   // chains per block queue (grown by the block when half full)
+constexpr uint32_t kJoinQueueCap = 1024;   // chains per block queue (grown by the block when half full)
 constexpr uint32_t kJoinChunkMax = 256;    // he_0 per work unit
 constexpr uint32_t kJoinProbeBlock = 16;   // he_0 probed before a compaction
 constexpr uint32_t kJoinListWords = (32 + 32 * kJoinProbeBlock) / 2;  // per warp hit stack: 16-bit entries
