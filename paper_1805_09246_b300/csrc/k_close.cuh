@@ -39,7 +39,7 @@ __device__ __forceinline__ uint32_t word_keep(uint32_t w, Window8 win, uint32_t 
   }
 }
 
-// RSRA part of the pass for 8-bit cells: one SRE (8 bytes) per load, eight loads in flight,
+// RSRA part of the pass for 8-bit cells: one SRE (8 bytes) per load, four loads in flight,
 // 32-bit indices. A warp covers 64 consecutive SREs 64j .. 64j + 63 per step: lane l holds
 // SREs 64j + l and 64j + 32 + l, so its two ballots are the two hot-bitmap words of those
 // SREs as they are (lane 0 writes both).
@@ -53,7 +53,7 @@ __device__ __forceinline__ void close_rsra8(const KParams& p, uint8_t* __restric
   const uint32_t lane = threadIdx.x & 31u;
   const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;  // blockDim.x is a multiple of 32
-  constexpr int kSteps = 4;                               // warp steps in flight (8 loads per lane)
+  constexpr int kSteps = 2;                               // warp steps in flight (4 loads per lane)
   for (uint32_t j0 = warp; j0 < n_pair; j0 += kSteps * nwarps) {
     uint2 v[kSteps][2];
 #pragma unroll
