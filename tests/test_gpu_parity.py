@@ -275,6 +275,41 @@ def test_k1_discrete_window():
     run_both(p, [tr.slice(0, t) for t in range(3)])
 
 
+def test_estimates_across_the_whole_range_of_U():
+    """Hosts with 1 .. 2000 distinct destinations on 64-cell SLEs (eta' = 64): union counts
+    from a few cells to every cell, so w / eta' falls in both halves of [0, 1) and at the
+    saturation clamp. The per-host query path (Eq. 12 and Eq. 8 for each host) and the close's
+    table over U (its reported candidates) against the oracle: flags exact, estimates within
+    the FP32 tolerance."""
+    S = sse()
+    p = S.Params(q2=6, eta2=64, delta2=8, k=2, theta=16, seed=41)
+    rng = np.random.default_rng(41)
+    counts = [1, 2, 4, 8, 12, 16, 24, 32, 40, 48, 56, 64, 96, 128, 256, 512, 2000]
+    hosts = np.unique(rng.integers(0, 2**32, 4 * len(counts), dtype=np.uint64).astype(np.uint32))
+    hosts = rng.permutation(hosts)[: len(counts)]
+    pairs = np.concatenate([np.stack([np.full(c, h, np.uint32),
+                                      rng.integers(0, 2**32, c, dtype=np.uint64).astype(np.uint32)], 1)
+                            for h, c in zip(hosts, counts)])
+    pairs = pairs[rng.permutation(len(pairs))]
+    est = S.Estimator(p)
+    orc = oracle.Oracle(oracle_params(p))
+    est.update(helpers.to_device(pairs))
+    orc.scan(pairs)
+    e, f = est.query(helpers.to_device(hosts))
+    ref = orc.estimate(hosts)
+    assert close_enough(e.cpu().numpy(), ref["est"])
+    assert np.array_equal(f.cpu().numpy(), ref["flags"])
+    x = ref["w"] / p.eta2
+    assert (x > 0).any() and (x < 0.5).any() and (x >= 0.5).any()
+    assert (ref["flags"] & oracle.SATURATED).any()
+    rep = est.close_slice()
+    det = orc.detect()
+    compare_report(rep, det)
+    assert rep.n_candidates >= 8
+    big = det["est"] >= p.eta2 * np.log(2.0)  # est >= eta' ln 2 exactly when w / eta' >= 1/2
+    assert big.any() and (~big).any()  # the table path sees both halves too
+
+
 def test_query_matches_oracle_estimates():
     S = sse()
     p = S.Params(k=4, seed=12)
