@@ -949,13 +949,23 @@ __global__ void __launch_bounds__(kEstThreads, 4) k_estimate(
         uint32_t m[kVecCells];
 #pragma unroll
         for (int b = 0; b < kVecCells; ++b) m[b] = 0;
-        for (uint32_t i = 0; i < p.r2; ++i) {
-          const uint4 v = *reinterpret_cast<const uint4*>(row_base[i] + z);
-          const uint32_t x[4] = {v.x, v.y, v.z, v.w};
+        // several rows' loads in flight at once (8 for 16-bit cells, 4 for 8-bit, whose 16
+        // per-cell maxima take the registers), then their distances
+        constexpr uint32_t kRowBatch = sizeof(St) == 1 ? 4 : 8;
+        for (uint32_t i0 = 0; i0 < p.r2; i0 += kRowBatch) {
+          uint4 v[kRowBatch];
 #pragma unroll
-          for (int b = 0; b < kVecCells; ++b)
-            m[b] = max(m[b], cell_age<St>((x[b / kIntCells] >> (8 * sizeof(St) * (b % kIntCells))) & kMask, age_lut,
-                                          cs, p.k));
+          for (uint32_t j = 0; j < kRowBatch; ++j)
+            if (i0 + j < p.r2) v[j] = *reinterpret_cast<const uint4*>(row_base[i0 + j] + z);
+#pragma unroll
+          for (uint32_t j = 0; j < kRowBatch; ++j) {
+            if (i0 + j >= p.r2) break;
+            const uint32_t x[4] = {v[j].x, v[j].y, v[j].z, v[j].w};
+#pragma unroll
+            for (int b = 0; b < kVecCells; ++b)
+              m[b] = max(m[b], cell_age<St>((x[b / kIntCells] >> (8 * sizeof(St) * (b % kIntCells))) & kMask,
+                                            age_lut, cs, p.k));
+          }
         }
 #pragma unroll
         for (int b = 0; b < kVecCells; ++b)
