@@ -44,12 +44,36 @@ __device__ __forceinline__ void emit_candidate(uint32_t aip, uint32_t* cand, uin
     atomicOr(overflow, 1u);
 }
 
+// The 2^delta (<= 32) values a * low (mod 2^64), low < 2^delta, of the multiply-add-shift
+// RHFG[0]'s multiplier a, in ascending order with their low bits (a is odd, so they are
+// distinct). Built in shared memory by the threads below 2^delta of a block (the caller
+// synchronises before use).
+struct RegainTable {
+  uint64_t d[32];
+  uint32_t low[32];
+};
+__device__ __forceinline__ void build_regain_table(const KParams& p, RegainTable* t) {
+  const uint32_t n = 1u << p.delta;
+  if (threadIdx.x < n) {
+    const uint64_t a = p.key_a[kR0];
+    const uint64_t d = a * threadIdx.x;
+    uint32_t rank = 0;
+    for (uint32_t j = 0; j < n; ++j) rank += (a * j < d) ? 1u : 0u;
+    t->d[rank] = d;
+    t->low[rank] = threadIdx.x;
+  }
+}
+
 // Regain the hosts of a complete chain B[1..r-1] (bits [delta, 32) fixed).
 // With the multiply-add-shift RHFG[0], the top q bits of a*x + b (mod 2^64) equal he_0
-// exactly when a*x + b - (he_0 << (64 - q)) (mod 2^64) is below 2^(64-q); stepping x through
-// high | low, low = 0, 1, ..., adds a each time, so each low costs a compare and an add.
+// exactly when v = a*x + b - (he_0 << (64 - q)) (mod 2^64) is below W = 2^(64-q); with
+// x = high | low, v = v0 + a*low, i.e. a*low (mod 2^64) lies in the circular interval
+// [-v0, -v0 + W). Given the sorted table of a*low (rt), the lows are found by a binary
+// search for -v0 and a walk while (a*low + v0) mod 2^64 < W, usually a single test;
+// otherwise each low costs a compare and an add (stepping x adds a each time).
 __device__ __forceinline__ void regain(const KParams& p, uint32_t he0, const uint32_t* B, uint32_t* cand,
-                                       uint32_t* n_cand, uint32_t cap, uint32_t* overflow) {
+                                       uint32_t* n_cand, uint32_t cap, uint32_t* overflow,
+                                       const RegainTable* rt = nullptr) {
   uint64_t high = (uint64_t)B[1] << p.delta;
   for (uint32_t i = 2; i < p.r; ++i)
     high |= (uint64_t)(B[i] >> (p.q - p.delta)) << (i * p.delta + p.q - p.delta);
@@ -64,6 +88,20 @@ __device__ __forceinline__ void regain(const KParams& p, uint32_t he0, const uin
   const uint64_t a = p.key_a[kR0];
   const uint64_t width = 1ull << (64 - p.q);
   uint64_t v = a * (uint32_t)high + p.key_b[kR0] - ((uint64_t)he0 << (64 - p.q));
+  if (rt) {
+    const uint32_t n = 1u << p.delta;
+    const uint64_t s = 0ull - v;  // the interval's start
+    uint32_t at = 0;              // entries of the table below s
+    for (uint32_t step = n >> 1; step > 0; step >>= 1)
+      if (rt->d[at + step - 1] < s) at += step;
+    if (rt->d[at] < s) at += 1;
+    for (uint32_t k = 0; k < n; ++k) {
+      const uint32_t i = (at + k) & (n - 1u);
+      if (rt->d[i] + v >= width) break;  // (a*low + v0) mod 2^64 ascends from here
+      emit_candidate((uint32_t)high | rt->low[i], cand, n_cand, cap, overflow);
+    }
+    return;
+  }
   for (uint32_t low = 0; low < (1u << p.delta); ++low, v += a)
     if (v < width) emit_candidate((uint32_t)high | low, cand, n_cand, cap, overflow);
 }
@@ -290,7 +328,7 @@ __device__ __forceinline__ uint32_t hot_group(const uint32_t* table, uint32_t c,
 // Rows 3..r-1 for delta <= 5: depth-first over the set bits of each row's hot group.
 __device__ __forceinline__ void grow_grouped(const KParams& p, const uint32_t* tables, uint32_t he0, uint32_t b1,
                                           uint32_t b2, uint32_t* cand, uint32_t* n_cand, uint32_t cap,
-                                          uint32_t* overflow) {
+                                          uint32_t* overflow, const RegainTable* rt = nullptr) {
   const uint32_t delta = p.delta, q = p.q, shift_hi = q - delta;
   const uint32_t cmask = (1u << shift_hi) - 1u, hi0 = he0 >> shift_hi;
   const uint64_t nwords = (1ull << q) >> 5;
@@ -301,7 +339,7 @@ __device__ __forceinline__ void grow_grouped(const KParams& p, const uint32_t* t
   if (i < (int)p.r) M[i] = hot_group(tables + (uint64_t)(i - 2) * nwords, (he0 ^ (b2 >> delta)) & cmask, delta);
   while (i >= 3) {
     if (i == (int)p.r) {  // chain complete
-      regain(p, he0, B, cand, n_cand, cap, overflow);
+      regain(p, he0, B, cand, n_cand, cap, overflow, rt);
       i -= 1;
       continue;
     }
@@ -534,6 +572,11 @@ __global__ void __launch_bounds__(kJoinTiledThreads) k_join_tiled(
   uint16_t* my_list = reinterpret_cast<uint16_t*>(s_he1 + kJoinTiledThreads) + warp * (2 * kJoinListWords);
   static_assert(kJoinChunkMax <= 256, "hit entries hold 8-bit chunk indices");
   if (threadIdx.x == 0) s_qn = 0;
+  // the sorted a*low table of regain (multiply-add-shift RHFG[0]; first used after the
+  // barrier that opens every work unit)
+  __shared__ RegainTable s_rt;
+  if (!p.tab) build_regain_table(p, &s_rt);
+  const RegainTable* rt = p.tab ? nullptr : &s_rt;
 
   // Work rows (tile of HSE(1), he_0), tile-major, split evenly over the blocks; a block's
   // range is cut into units of at most kJoinChunkMax he_0 of one tile.
@@ -549,7 +592,7 @@ __global__ void __launch_bounds__(kJoinTiledThreads) k_join_tiled(
       qb1[at] = b1;
       qb2[at] = b2;
     } else {
-      grow_grouped(p, tables, he0, b1, b2, cand, n_cand, cap, overflow);
+      grow_grouped(p, tables, he0, b1, b2, cand, n_cand, cap, overflow, rt);
     }
   };
   // One hit (he_0, he_1): every hot row-2 SRE of the group gives B(2); chains whose row-3
@@ -653,7 +696,7 @@ __global__ void __launch_bounds__(kJoinTiledThreads) k_join_tiled(
         if (qn >= kJoinQueueCap / 2) {
           const uint32_t n = min(qn, kJoinQueueCap);
           for (uint32_t i = threadIdx.x; i < n; i += blockDim.x)
-            grow_grouped(p, tables, qh[i], qb1[i], qb2[i], cand, n_cand, cap, overflow);
+            grow_grouped(p, tables, qh[i], qb1[i], qb2[i], cand, n_cand, cap, overflow, rt);
           __syncthreads();
           if (threadIdx.x == 0) s_qn = 0;
         }
@@ -666,7 +709,7 @@ __global__ void __launch_bounds__(kJoinTiledThreads) k_join_tiled(
     __syncthreads();  // the queue is complete
     const uint32_t qn = min(s_qn, kJoinQueueCap);
     for (uint32_t i = threadIdx.x; i < qn; i += blockDim.x)
-      grow_grouped(p, tables, qh[i], qb1[i], qb2[i], cand, n_cand, cap, overflow);
+      grow_grouped(p, tables, qh[i], qb1[i], qb2[i], cand, n_cand, cap, overflow, rt);
     __syncthreads();
     if (threadIdx.x == 0) s_qn = 0;
   }
