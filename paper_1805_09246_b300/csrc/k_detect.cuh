@@ -71,12 +71,10 @@ __device__ __forceinline__ void build_regain_table(const KParams& p, RegainTable
 // [-v0, -v0 + W). Given the sorted table of a*low (rt), the lows are found by a binary
 // search for -v0 and a walk while (a*low + v0) mod 2^64 < W, usually a single test;
 // otherwise each low costs a compare and an add (stepping x adds a each time).
-__device__ __forceinline__ void regain(const KParams& p, uint32_t he0, const uint32_t* B, uint32_t* cand,
-                                       uint32_t* n_cand, uint32_t cap, uint32_t* overflow,
-                                       const RegainTable* rt = nullptr) {
-  uint64_t high = (uint64_t)B[1] << p.delta;
-  for (uint32_t i = 2; i < p.r; ++i)
-    high |= (uint64_t)(B[i] >> (p.q - p.delta)) << (i * p.delta + p.q - p.delta);
+// `high`: address bits [delta, 32) of the chain (Eq. 7).
+__device__ __forceinline__ void regain_high(const KParams& p, uint32_t he0, uint64_t high, uint32_t* cand,
+                                            uint32_t* n_cand, uint32_t cap, uint32_t* overflow,
+                                            const RegainTable* rt) {
   if (p.tab) {
     for (uint32_t low = 0; low < (1u << p.delta); ++low) {
       const uint32_t aip = (uint32_t)(high | low);
@@ -104,6 +102,17 @@ __device__ __forceinline__ void regain(const KParams& p, uint32_t he0, const uin
   }
   for (uint32_t low = 0; low < (1u << p.delta); ++low, v += a)
     if (v < width) emit_candidate((uint32_t)high | low, cand, n_cand, cap, overflow);
+}
+
+// The chain B[1..r-1]: B(1) gives address bits [delta, delta + q), each further B(i) its top
+// delta bits at [i*delta + q - delta, (i+1)*delta + q - delta) (Eq. 7).
+__device__ __forceinline__ void regain(const KParams& p, uint32_t he0, const uint32_t* B, uint32_t* cand,
+                                       uint32_t* n_cand, uint32_t cap, uint32_t* overflow,
+                                       const RegainTable* rt = nullptr) {
+  uint64_t high = (uint64_t)B[1] << p.delta;
+  for (uint32_t i = 2; i < p.r; ++i)
+    high |= (uint64_t)(B[i] >> (p.q - p.delta)) << (i * p.delta + p.q - p.delta);
+  regain_high(p, he0, high, cand, n_cand, cap, overflow, rt);
 }
 
 // Rows 3..r-1 of a chain whose rows 0..2 are hot (rare: depth-first, explicit stack).
@@ -357,6 +366,42 @@ __device__ __forceinline__ void grow_grouped(const KParams& p, const uint32_t* t
   }
 }
 
+// grow_grouped for r = 5: rows 3 and 4 as two nested loops over their hot groups, the chain
+// in registers.
+__device__ __forceinline__ void grow_grouped5(const KParams& p, const uint32_t* tables, uint32_t he0, uint32_t b1,
+                                           uint32_t b2, uint32_t* cand, uint32_t* n_cand, uint32_t cap,
+                                           uint32_t* overflow, const RegainTable* rt) {
+  const uint32_t delta = p.delta, q = p.q, shift_hi = q - delta;
+  const uint32_t cmask = (1u << shift_hi) - 1u, hi0 = he0 >> shift_hi;
+  const uint64_t nwords = (1ull << q) >> 5;
+  const uint64_t high12 = ((uint64_t)b1 << delta) | ((uint64_t)(b2 >> shift_hi) << (2 * delta + shift_hi));
+  uint32_t m3 = hot_group(tables + nwords, (he0 ^ (b2 >> delta)) & cmask, delta);
+  while (m3) {
+    const uint32_t b3 = (b2 >> delta) | (((uint32_t)(__ffs(m3) - 1) ^ hi0) << shift_hi);
+    m3 &= m3 - 1u;
+    if (!fits32(3, delta, q, b3)) continue;
+    const uint64_t high123 = high12 | ((uint64_t)(b3 >> shift_hi) << (3 * delta + shift_hi));
+    uint32_t m4 = hot_group(tables + 2 * nwords, (he0 ^ (b3 >> delta)) & cmask, delta);
+    while (m4) {
+      const uint32_t b4 = (b3 >> delta) | (((uint32_t)(__ffs(m4) - 1) ^ hi0) << shift_hi);
+      m4 &= m4 - 1u;
+      if (!fits32(4, delta, q, b4)) continue;
+      regain_high(p, he0, high123 | ((uint64_t)(b4 >> shift_hi) << (4 * delta + shift_hi)), cand, n_cand, cap,
+                  overflow, rt);
+    }
+  }
+}
+
+// Rows 3..r-1 of one queued chain: the r = 5 loops, else the general depth-first walk.
+__device__ __forceinline__ void grow_chain(const KParams& p, const uint32_t* tables, uint32_t he0, uint32_t b1,
+                                        uint32_t b2, uint32_t* cand, uint32_t* n_cand, uint32_t cap,
+                                        uint32_t* overflow, const RegainTable* rt) {
+  if (p.r == 5)
+    grow_grouped5(p, tables, he0, b1, b2, cand, n_cand, cap, overflow, rt);
+  else
+    grow_grouped(p, tables, he0, b1, b2, cand, n_cand, cap, overflow, rt);
+}
+
 constexpr int kJoinThreads = 1024;
 
 // Blocks stride over HSE(0), threads over HSE(1). For a pair (he_0, he_1), B(1) fixes the
@@ -592,7 +637,7 @@ __global__ void __launch_bounds__(kJoinTiledThreads) k_join_tiled(
       qb1[at] = b1;
       qb2[at] = b2;
     } else {
-      grow_grouped(p, tables, he0, b1, b2, cand, n_cand, cap, overflow, rt);
+      grow_chain(p, tables, he0, b1, b2, cand, n_cand, cap, overflow, rt);
     }
   };
   // One hit (he_0, he_1): every hot row-2 SRE of the group gives B(2); chains whose row-3
@@ -696,7 +741,7 @@ __global__ void __launch_bounds__(kJoinTiledThreads) k_join_tiled(
         if (qn >= kJoinQueueCap / 2) {
           const uint32_t n = min(qn, kJoinQueueCap);
           for (uint32_t i = threadIdx.x; i < n; i += blockDim.x)
-            grow_grouped(p, tables, qh[i], qb1[i], qb2[i], cand, n_cand, cap, overflow, rt);
+            grow_chain(p, tables, qh[i], qb1[i], qb2[i], cand, n_cand, cap, overflow, rt);
           __syncthreads();
           if (threadIdx.x == 0) s_qn = 0;
         }
@@ -709,7 +754,7 @@ __global__ void __launch_bounds__(kJoinTiledThreads) k_join_tiled(
     __syncthreads();  // the queue is complete
     const uint32_t qn = min(s_qn, kJoinQueueCap);
     for (uint32_t i = threadIdx.x; i < qn; i += blockDim.x)
-      grow_grouped(p, tables, qh[i], qb1[i], qb2[i], cand, n_cand, cap, overflow, rt);
+      grow_chain(p, tables, qh[i], qb1[i], qb2[i], cand, n_cand, cap, overflow, rt);
     __syncthreads();
     if (threadIdx.x == 0) s_qn = 0;
   }
