@@ -87,17 +87,8 @@ __device__ __forceinline__ void regain_high(const KParams& p, uint32_t he0, uint
   const uint64_t width = 1ull << (64 - p.q);
   uint64_t v = a * (uint32_t)high + p.key_b[kR0] - ((uint64_t)he0 << (64 - p.q));
   if (rt) {
-    const uint32_t n = 1u << p.delta;
-    const uint64_t s = 0ull - v;  // the interval's start
-    uint32_t at = 0;              // entries of the table below s
-    for (uint32_t step = n >> 1; step > 0; step >>= 1)
-      if (rt->d[at + step - 1] < s) at += step;
-    if (rt->d[at] < s) at += 1;
-    for (uint32_t k = 0; k < n; ++k) {
-      const uint32_t i = (at + k) & (n - 1u);
-      if (rt->d[i] + v >= width) break;  // (a*low + v0) mod 2^64 ascends from here
-      emit_candidate((uint32_t)high | rt->low[i], cand, n_cand, cap, overflow);
-    }
+    regain_search(rt->d, rt->low, 1u << p.delta, v, width,
+                  [&](uint32_t low) { emit_candidate((uint32_t)high | low, cand, n_cand, cap, overflow); });
     return;
   }
   for (uint32_t low = 0; low < (1u << p.delta); ++low, v += a)

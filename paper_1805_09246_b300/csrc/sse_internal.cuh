@@ -49,6 +49,26 @@ __device__ __forceinline__ uint32_t rhfg0(const KParams& p, uint32_t aip) {
   return mas_top(p.key_a[kR0], p.key_b[kR0], aip, p.q);
 }
 
+// The lows of regain's interval test by search: emit(low) for every entry of the table d
+// (n values a*low mod 2^64, ascending, a power of two of them, with their lows) whose
+// (d + v) mod 2^64 is below width. A binary search finds the first entry at or above -v;
+// from there (d + v) mod 2^64 ascends around the table, so the walk stops at the first
+// miss.
+template <typename Emit>
+__host__ __device__ __forceinline__ void regain_search(const uint64_t* d, const uint32_t* low, uint32_t n, uint64_t v,
+                                                       uint64_t width, Emit emit) {
+  const uint64_t s = 0ull - v;  // the interval's start
+  uint32_t at = 0;              // entries of the table below s
+  for (uint32_t step = n >> 1; step > 0; step >>= 1)
+    if (d[at + step - 1] < s) at += step;
+  if (d[at] < s) at += 1;
+  for (uint32_t k = 0; k < n; ++k) {
+    const uint32_t i = (at + k) & (n - 1u);
+    if (d[i] + v >= width) break;
+    emit(low[i]);
+  }
+}
+
 // Cyclic stamp arithmetic: slice t has stamp 1 + (t mod 255); 0 marks an unset cell.
 __host__ __device__ __forceinline__ uint8_t stamp_of(uint64_t slice) { return (uint8_t)(1 + slice % 255); }
 
