@@ -62,3 +62,18 @@ def test_two_gloo_ranks_max_time_summed_work_and_rank_traces():
         assert work == 30.0    # 10 + 20
     assert results[0][4] != results[1][4]  # each rank scans its own trace
     assert results[1][5] == ""             # rank 1 of the reference arm prints nothing
+
+
+def test_cpu_baseline_runs_until_its_time_and_slice_minimums():
+    """The CPU baseline scans slices in turn (from the first again when the given ones run
+    out) until both the minimum time and the minimum slice count are reached."""
+    import numpy as np
+    sys.path.insert(0, ROOT)
+    import bench
+    rng = np.random.default_rng(3)
+    slices = [rng.integers(0, 2**32, (4096, 2), dtype=np.uint64).astype(np.uint32) for _ in range(2)]
+    r = bench.cpu_baseline(slices, min_seconds=0.0, min_slices=5, max_slices=64)
+    assert "over 5 full core-link slices" in r["sample"] and r["cores"] == 1 and r["value"] > 0
+    r = bench.cpu_baseline(slices, min_seconds=0.3, min_slices=1, max_slices=64)
+    n = int(r["sample"].split(" over ")[1].split()[0])
+    assert n >= 1 and float(r["sample"].split("pairs, ")[1].split(" s)")[0]) >= 0.3 or n == 64
