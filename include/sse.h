@@ -230,7 +230,8 @@ SSE_API int sse_autotune_update(sse_handle* h, const uint32_t* d_pairs, uint64_t
  * Errors: CAPACITY when candidates exceed max_candidates or out->cap (the report then
  * holds the first entries, truncated = 1, and the slice still advances); TIMEOUT when the
  * ordering of more than 4096 candidates, whose blocks meet at bounded device-side
- * barriers, gave up waiting (the report's order is then not guaranteed); CUDA.
+ * barriers, gave up waiting (the report's hosts and order are then not valid; the slice
+ * still advances and the handle stays usable); CUDA.
  */
 SSE_API int sse_close_slice(sse_handle* h, sse_report* out);
 
@@ -238,6 +239,19 @@ SSE_API int sse_close_slice(sse_handle* h, sse_report* out);
  * copies, clock tick) from a CUDA graph captured at the first call; 0: launches the same
  * kernels one by one. Results are identical. Errors: INVALID_PARAM. */
 SSE_API int sse_close_use_graph(sse_handle* h, int enable);
+
+/*
+ * Failure-detection hook (the paper has no counterpart; for tests of the bounded device-side
+ * waits). When a close finds more than 4096 candidates, their ordering runs as one
+ * cooperative launch whose blocks meet at grid-wide barriers; each wait polls at most
+ * spin_limit times (0 restores the default of 2^22 polls, about a quarter of a second)
+ * and then gives up. extra_arrivals = 1 makes every barrier wait for one block that does
+ * not exist, so every wait runs out: that close returns SSE_ERR_TIMEOUT, its report order
+ * is not valid, and the handle stays usable (no sticky error); set 0 again and the next
+ * close is correct. Applies to closes enqueued after the call (stream-ordered); blocks
+ * until the setting is on the device. Errors: INVALID_PARAM (extra_arrivals > 1), CUDA.
+ */
+SSE_API int sse_debug_sort_barrier(sse_handle* h, uint32_t spin_limit, uint32_t extra_arrivals);
 
 /* sse_close_slice in two halves, so that the next slice's updates can be enqueued while the
  * report is produced: _async enqueues the close (graph mode only) and moves the handle to
@@ -284,12 +298,14 @@ SSE_API int sse_query(sse_handle* h, const uint32_t* d_hosts, uint32_t n, float*
  * slice (the index t of the slice being scanned), d_hosts [n], d_est [n], d_flags [n] or
  * NULL; results equal sse_query() on an estimator holding those stamps. The only scratch,
  * one active-cell counter per SLEA row, is a 64-byte array inside the library that every
- * GPU which loads the library keeps until the process exits; r' above 16 is rejected with
- * SSE_ERR_INVALID_PARAM. The first call on a device looks up that array's device address
- * (make it before any stream capture); each call clears the counters and then runs
- * asynchronously on cuda_stream. All calls share the one array, so calls whose GPU work
- * overlaps (different streams or threads) race and must be serialised by the caller.
- * Allocates nothing. Errors: INVALID_PARAM, CUDA.
+ * GPU which loads the library keeps until the process exits; it holds a counter for every
+ * r' that parameter validation accepts (at most 16). Only 8-bit stamps are served:
+ * p->stamp_bits = 16 is rejected with SSE_ERR_INVALID_PARAM. The first call on a device
+ * looks up that array's device address for the device current on the calling thread (make
+ * it before any stream capture); cuda_stream must belong to that same device. Each call
+ * clears the counters and then runs asynchronously on cuda_stream. All calls share the one
+ * array, so calls whose GPU work overlaps (different streams or threads) race and must be
+ * serialised by the caller. Allocates nothing. Errors: INVALID_PARAM, CUDA.
  */
 SSE_API int sse_query_noalloc(const sse_params* p, const uint8_t* d_sle, uint64_t slice, const uint32_t* d_hosts,
                               uint32_t n, float* d_est, uint8_t* d_flags, void* cuda_stream);

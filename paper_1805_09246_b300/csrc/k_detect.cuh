@@ -770,9 +770,10 @@ constexpr uint32_t kSortBlocks = kSortChunk / (kSortThreads / kRankSplit);  // 1
 constexpr uint32_t kBarrierSpins = 1u << 22;  // polls (64 ns apart) before a barrier gives up
 
 // Grid-wide barrier of a cooperative launch. bar[0] counts arrivals, bar[1] is the
-// generation; both are zero before the launch (the close's scratch is cleared). A wait that
-// outlasts kBarrierSpins polls sets *error and returns false; the caller then returns.
-__device__ __forceinline__ bool grid_barrier(uint32_t* bar, uint32_t* error) {
+// generation; both are zero before the launch (the close's scratch is cleared). The block
+// whose arrival is number `last` (gridDim.x - 1 normally) releases the others. A wait that
+// outlasts `spins` polls sets *error and returns false; the caller then returns.
+__device__ __forceinline__ bool grid_barrier(uint32_t* bar, uint32_t* error, uint32_t spins_max, uint32_t last) {
   __shared__ uint32_t ok;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -780,14 +781,14 @@ __device__ __forceinline__ bool grid_barrier(uint32_t* bar, uint32_t* error) {
     const uint32_t g = *gen;  // this barrier's generation: it cannot move before we arrive
     ok = 1u;
     __threadfence();
-    if (atomicAdd(bar, 1u) == gridDim.x - 1) {
+    if (atomicAdd(bar, 1u) == last) {
       atomicExch(bar, 0u);
       __threadfence();
       atomicAdd(bar + 1, 1u);
     } else {
       uint32_t spins = 0;
       while (*gen == g) {
-        if (++spins > kBarrierSpins) {
+        if (++spins > spins_max) {
           atomicOr(error, 1u);
           ok = 0u;
           break;
@@ -803,13 +804,17 @@ __device__ __forceinline__ bool grid_barrier(uint32_t* bar, uint32_t* error) {
 
 // keys: the n = min(*n_ptr, cap) unsorted candidates (reordered in place when n > kSortChunk);
 // alt: a second buffer of cap entries; out: the sorted candidates. bar: two zeroed words.
+// ctl (may be NULL): ctl[0] the barrier's poll limit (0: kBarrierSpins), ctl[1] arrivals the
+// barrier waits for beyond the grid's blocks (0; a failure-detection test sets 1, so that
+// every barrier wait runs out and the launch reports the timeout in *error).
 __global__ void __launch_bounds__(kSortThreads) k_sort_candidates(uint32_t* __restrict__ keys,
                                                                   uint32_t* __restrict__ alt,
                                                                   uint32_t* __restrict__ out,
                                                                   const uint32_t* __restrict__ n_ptr, uint32_t cap,
                                                                   uint32_t* __restrict__ bar,
                                                                   uint32_t* __restrict__ error,
-                                                                  uint32_t small_by_estimate) {
+                                                                  uint32_t small_by_estimate,
+                                                                  const uint32_t* __restrict__ ctl) {
   __shared__ uint32_t s[kSortChunk];
   const uint32_t n = min(*n_ptr, cap);
   if (n <= kSortChunk) {
@@ -856,9 +861,11 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_candidates(uint32_t* __re
   }
   // merge passes: runs of `width` pairwise, keys -> alt -> keys ... -> out (reads bypass L1,
   // which other blocks' writes do not update)
+  const uint32_t spins = ctl && ctl[0] ? ctl[0] : kBarrierSpins;
+  const uint32_t last = gridDim.x - 1 + (ctl ? ctl[1] : 0u);
   const uint32_t* src = keys;
   for (uint64_t width = kSortChunk; width < n; width *= 2) {
-    if (!grid_barrier(bar, error)) return;
+    if (!grid_barrier(bar, error, spins, last)) return;
     uint32_t* dst = 2 * width >= n ? out : (src == keys ? alt : keys);
     for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n; x += (uint64_t)gridDim.x * blockDim.x) {
       const uint64_t pair_start = (x / (2 * width)) * (2 * width);

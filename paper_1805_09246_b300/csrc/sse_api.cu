@@ -100,6 +100,7 @@ struct sse_handle {
   // device memory
   uint8_t* state = nullptr;  // RSRA then SLEA
   uint32_t* clock = nullptr; // device copy of the current stamp, 1 + (slice mod 255)
+  uint32_t* sort_ctl = nullptr;  // in the clock's allocation: the sort barrier's controls (k_sort_candidates)
   uint8_t* sre = nullptr;
   uint8_t* sle = nullptr;
   uint32_t* hot_bits = nullptr;
@@ -366,7 +367,8 @@ int launch_sort(sse_handle* h) {
   CloseScratch* sc = h->scratch;
   // up to kSortChunk candidates are placed by the estimate kernel (rank mode)
   SSE_CUDA(h, cudaLaunchKernelEx(&cfg, k_sort_candidates, h->cand, h->cand_alt, h->cand_out,
-                                 (const uint32_t*)&sc->n_cand, h->cand_cap, sc->barrier, &sc->error, 1u));
+                                 (const uint32_t*)&sc->n_cand, h->cand_cap, sc->barrier, &sc->error, 1u,
+                                 (const uint32_t*)h->sort_ctl));
   SSE_LAUNCHED(h);
   return SSE_OK;
 }
@@ -506,6 +508,7 @@ int sse_init(const sse_params* p, void* cuda_stream, sse_handle** out) {
   }
   h->sre = h->state;
   h->sle = h->state + d.sre_bytes;
+  h->sort_ctl = h->clock + 16;  // bytes 64..71 of the clock's 256
   if (q.rhfg_hash == 1) {
     uint32_t tab[1024];
     make_rhfg_tables(q, tab);
@@ -577,7 +580,8 @@ int sse_init(const sse_params* p, void* cuda_stream, sse_handle** out) {
     h->join_grid = (uint32_t)(per_sm * h->num_sms);
   }
   const uint32_t first_stamp = stamp_of(0, h->smod);
-  if (cudaMemcpyAsync(h->clock, &first_stamp, sizeof(first_stamp), cudaMemcpyHostToDevice, h->stream) != cudaSuccess ||
+  if (cudaMemsetAsync(h->clock, 0, 256, h->stream) != cudaSuccess ||
+      cudaMemcpyAsync(h->clock, &first_stamp, sizeof(first_stamp), cudaMemcpyHostToDevice, h->stream) != cudaSuccess ||
       cudaMemsetAsync(h->state, 0, state_bytes, h->stream) != cudaSuccess ||
       cudaMemsetAsync(h->hot_bits, 0, ((uint64_t)q.r << q.q) / 8, h->stream) != cudaSuccess ||
       cudaMemsetAsync(h->sle_bits, 0, h->sle_cells / 8, h->stream) != cudaSuccess ||
@@ -989,7 +993,8 @@ int sse_close_slice(sse_handle* h, sse_report* out) {
   int rc = close_enqueue(h, &sorted);
   if (rc) return rc;
   const int status = close_collect(h, sorted, out);
-  if (status != SSE_OK && status != SSE_ERR_CAPACITY) return status;
+  // a full or out-of-order report still closes the slice (as the graph path does)
+  if (status != SSE_OK && status != SSE_ERR_CAPACITY && status != SSE_ERR_TIMEOUT) return status;
   const int rc_tick = advance_clock(h);
   return rc_tick ? rc_tick : status;
 }
@@ -997,6 +1002,16 @@ int sse_close_slice(sse_handle* h, sse_report* out) {
 int sse_close_use_graph(sse_handle* h, int enable) {
   if (!h || h->close_pending) return SSE_ERR_INVALID_PARAM;
   h->close_graph = enable ? 1 : 0;
+  return SSE_OK;
+}
+
+int sse_debug_sort_barrier(sse_handle* h, uint32_t spin_limit, uint32_t extra_arrivals) {
+  if (!h || extra_arrivals > 1u) return SSE_ERR_INVALID_PARAM;
+  if (h->sticky) return h->sticky;
+  const uint32_t ctl[2] = {spin_limit, extra_arrivals};
+  // stream-ordered with the closes, read by the sort kernel at each replay of the close graph
+  SSE_CUDA(h, cudaMemcpyAsync(h->sort_ctl, ctl, sizeof(ctl), cudaMemcpyHostToDevice, h->stream));
+  SSE_CUDA(h, cudaStreamSynchronize(h->stream));  // ctl is a stack array
   return SSE_OK;
 }
 
@@ -1152,9 +1167,13 @@ namespace {
 
 constexpr int kNoAllocMaxRows = 16;  // scratch capacity: one counter per SLEA row
 static __device__ __align__(256) uint32_t g_noalloc_row_counts[kNoAllocMaxRows];
+// Parameter validation already caps r' at kMaxRows, so every valid estimator fits.
+static_assert(kNoAllocMaxRows >= kMaxRows, "the scratch array must hold a counter for every SLEA row");
 
 constexpr int kNoAllocMaxDevices = 64;
-uint32_t* g_noalloc_ptr[kNoAllocMaxDevices];  // device address of the array, per device
+// Device address of the array, per device. Atomic: two host threads may make their first
+// call on a device at the same time; both look up the same address, either store wins.
+std::atomic<uint32_t*> g_noalloc_ptr[kNoAllocMaxDevices];
 
 // First call on a device: look up the array's device address with that device current.
 // The host-side name of the array is only a stand-in and must never reach a kernel.
@@ -1164,15 +1183,17 @@ int noalloc_scratch(uint32_t** out) {
     cudaGetLastError();
     return SSE_ERR_CUDA;
   }
-  if (!g_noalloc_ptr[dev]) {
+  uint32_t* cached = g_noalloc_ptr[dev].load(std::memory_order_acquire);
+  if (!cached) {
     void* ptr = nullptr;
     if (cudaGetSymbolAddress(&ptr, g_noalloc_row_counts) != cudaSuccess || !ptr) {
       cudaGetLastError();
       return SSE_ERR_CUDA;
     }
-    g_noalloc_ptr[dev] = static_cast<uint32_t*>(ptr);
+    cached = static_cast<uint32_t*>(ptr);
+    g_noalloc_ptr[dev].store(cached, std::memory_order_release);
   }
-  *out = g_noalloc_ptr[dev];
+  *out = cached;
   return SSE_OK;
 }
 
@@ -1185,7 +1206,7 @@ extern "C" int sse_query_noalloc(const sse_params* p, const uint8_t* d_sle, uint
   sse_derived d;
   const int rc = derive_params(*p, q, d);
   if (rc != SSE_OK) return rc;
-  if (q.r2 > (uint32_t)kNoAllocMaxRows) return SSE_ERR_INVALID_PARAM;  // beyond the scratch array
+  if (q.r2 > (uint32_t)kNoAllocMaxRows) return SSE_ERR_INVALID_PARAM;  // beyond the scratch array (see static_assert)
   if (q.stamp_bits != 8) return SSE_ERR_INVALID_PARAM;                // 8-bit stamps only
   if (n == 0) return SSE_OK;
   if (!d_sle || !d_hosts || !d_est || (reinterpret_cast<uintptr_t>(d_sle) & 15u)) return SSE_ERR_INVALID_PARAM;

@@ -20,6 +20,7 @@ SSE_OK = 0
 FLAG_SUPER = 1
 FLAG_SATURATED = 2
 ERR_CAPACITY = -3
+ERR_TIMEOUT = -6
 UPDATE_AUTO, UPDATE_DIRECT, UPDATE_TILED = 0, 1, 2
 BATCH_DETECT, BATCH_ROUTERS, BATCH_SCAN = 0, 1, 2
 DIR_SRC, DIR_DST, DIR_BOTH = 0, 1, 2
@@ -148,6 +149,8 @@ def lib() -> ctypes.CDLL:
             "sse_batch_global": (i32, [vp, ctypes.POINTER(vp)]),
             "sse_batch_use_graph": (i32, [vp, i32]),
             "sse_batch_configure": (i32, [vp, u32, i32]),
+            "sse_debug_sort_barrier": (i32, [vp, u32, u32]),
+            "sse_microbench": (i32, [vp, u64, vp, vp]),
             "sse_batch_tune": (i32, [vp, vp, vp, i32, vp, ctypes.POINTER(i32)]),
             "sse_batch_step": (i32, [vp, vp, vp]),
             "sse_batch_step_from": (i32, [vp, vp, vp, vp]),
@@ -192,6 +195,29 @@ def lib() -> ctypes.CDLL:
             fn.argtypes = args
         _lib = L
     return _lib
+
+
+class _MicrobenchResult(ctypes.Structure):
+    _fields_ = [("l2_random_byte_stores_per_s", ctypes.c_double), ("smem_random_atomics_per_s", ctypes.c_double),
+                ("l2_stream_load_bytes_per_s", ctypes.c_double), ("hbm_stream_load_bytes_per_s", ctypes.c_double),
+                ("sms", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+
+
+MICROBENCH_MIN_BYTES = (1 << 30) + 4096
+
+
+def microbench(stream=None) -> dict:
+    """Peak rates of the update's memory units on the current device (sse_microbench): random
+    one-byte L2 stores/s, random shared-memory atomic ORs/s, streaming 128-bit load bytes/s
+    from L2 and from HBM."""
+    torch = _torch()
+    buf = torch.empty(MICROBENCH_MIN_BYTES, dtype=torch.uint8, device="cuda")
+    st = stream if stream is not None else torch.cuda.current_stream()
+    out = _MicrobenchResult()
+    _check(lib().sse_microbench(ctypes.c_void_p(buf.data_ptr()), buf.numel(), ctypes.c_void_p(st.cuda_stream),
+                                ctypes.byref(out)), "sse_microbench")
+    del buf
+    return {name: getattr(out, name) for name, _ in _MicrobenchResult._fields_ if name != "reserved"}
 
 
 def update_variant_count() -> int:
@@ -432,6 +458,12 @@ class Estimator:
 
     def sync(self) -> None:
         _check(self._lib.sse_sync(self._h), "sse_sync")
+
+    def debug_sort_barrier(self, spin_limit: int, extra_arrivals: int) -> None:
+        """Failure-detection hook: bound the candidate sort's barrier waits to spin_limit polls
+        (0: default); extra_arrivals = 1 makes every wait run out (sse_debug_sort_barrier)."""
+        _check(self._lib.sse_debug_sort_barrier(self._h, spin_limit, extra_arrivals), "sse_debug_sort_barrier",
+               self._h)
 
     def close_use_graph(self, enable: bool) -> None:
         """Replay sse_close_slice from a CUDA graph (default) or launch its kernels one by one."""

@@ -18,9 +18,9 @@ def sse():
     return mod
 
 
-def router_traffic(n_routers, n_slices, seed):
-    cfg = synth.TrafficConfig(seed=seed, n_slices=n_slices, n_routers=n_routers, load_min=1 << 12,
-                              load_max=1 << 17, n_sources=20_000, n_planted=12, planted_min=1500,
+def router_traffic(n_routers, n_slices, seed, load_min=1 << 12, load_max=1 << 17):
+    cfg = synth.TrafficConfig(seed=seed, n_slices=n_slices, n_routers=n_routers, load_min=load_min,
+                              load_max=load_max, n_sources=20_000, n_planted=12, planted_min=1500,
                               planted_max=6000, group_min=1, group_max=min(3, n_routers))
     tr = synth.Traffic(cfg)
     return [[tr.slice(r, t) for r in range(n_routers)] for t in range(n_slices)]
@@ -75,6 +75,64 @@ def test_batch_matches_single_router_api_and_oracle(graph):
         compare_state(batch.router(r), orcs[r], p, T - 1)
     assert batch.router(0).slice == T and batch.global_estimator().slice == T
     assert batch.kernel_launches > 0
+
+
+def batch_against_oracle(batch, p, slices):
+    """Steps `batch` through `slices`; after every step the report equals the detection of
+    the oracle's routers merged into a global oracle (Algorithms 2 and 7, then 4, 5 and 8);
+    at the end the global and every router state equal the oracle's."""
+    R, T = len(slices[0]), len(slices)
+    orcs = [oracle.Oracle(oracle_params(p)) for _ in range(R)]
+    og = oracle.Oracle(oracle_params(p))
+    found = 0
+    for t, per_router in enumerate(slices):
+        rep = batch.step(inputs=[helpers.to_device(x) for x in per_router])
+        for o, pairs in zip(orcs, per_router):
+            if t:
+                o.advance()
+            o.scan(pairs)
+        if t:
+            og.advance()
+        og.merge(orcs)
+        compare_report(rep, og.detect())
+        found += rep.n_super
+    compare_state(batch.global_estimator(), og, p, T - 1)
+    for r in range(R):
+        compare_state(batch.router(r), orcs[r], p, T - 1)
+    return found
+
+
+@pytest.mark.parametrize("item_pairs,unroll", [(1024, 2), (1024, 4), (1024, 8), (1025, 2)])
+def test_batch_chunked_items_match_oracle(item_pairs, unroll):
+    """Every router's slice spans 3-40 work items of the persistent update: items resume in
+    the middle of a router's pairs (with item_pairs = 1025, at odd pairs, so the 16-byte peel
+    runs), the last item of a router is partial, the RSRA owner of an item is chunk mod
+    tiles, and a CTA flushes its bitmap whenever its next item belongs to another router.
+    Reports and states against oracle routers and their merge."""
+    S = sse()
+    p = S.Params(seed=36)
+    R, T = 5, 4
+    slices = router_traffic(R, T, seed=36 + item_pairs + unroll, load_min=3 * item_pairs + 1,
+                            load_max=40 * item_pairs)
+    counts = [len(x) for s in slices for x in s]
+    assert min(counts) > 2 * item_pairs and any(c % item_pairs for c in counts)
+    batch = S.Batch(p, R, max(counts))
+    batch.configure(item_pairs, unroll)
+    assert batch_against_oracle(batch, p, slices) > 0
+
+
+def test_batch_tuner_item_size_with_routers_over_several_items():
+    """The tuner's smallest item size, 2^18 pairs, with every router above it (loads up to
+    three items, none a multiple of the item): state and reports against the oracle."""
+    S = sse()
+    p = S.Params(seed=37)
+    R, T = 3, 3
+    slices = router_traffic(R, T, seed=37, load_min=(1 << 18) + 3, load_max=3 << 18)
+    counts = [len(x) for s in slices for x in s]
+    assert min(counts) > 1 << 18 and all(c % (1 << 18) for c in counts)
+    batch = S.Batch(p, R, max(counts), use_graph=False)
+    batch.configure(1 << 18, 4)
+    batch_against_oracle(batch, p, slices)
 
 
 def test_batch_graph_replay_equals_direct_launches_and_tuning_keeps_results():

@@ -67,6 +67,80 @@ def test_window_of_300_slices(mode):
     assert close_enough(est_q.cpu().numpy(), ref["est"])
 
 
+def _paper_close_checks(est, orc, p, t, brute=False, extra_hosts=None):
+    """State, hot SREs, row counts and report at slice t; with `brute`, the candidate set
+    also against every 32-bit address whose r SREs are hot, and a query of the candidates
+    (plus `extra_hosts`) with per-distance counts against the oracle's Algorithm 8."""
+    det = orc.detect()
+    if brute:  # the query evaluates the window ending at the current slice: before the close
+        hosts = det["hosts"] if extra_hosts is None else np.union1d(det["hosts"], extra_hosts)
+        e, f, h = est.query(helpers.to_device(hosts), hist=True)
+        ref = orc.estimate(hosts, hist=True)
+        assert close_enough(e.cpu().numpy(), ref["est"])
+        assert np.array_equal(f.cpu().numpy(), ref["flags"])
+        assert np.array_equal(h.cpu().numpy().view(np.uint32), ref["hist"])
+        assert ref["hist"][:, 256:].any()  # distances above 255 occur
+    rep = est.close_slice()
+    compare_state(est, orc, p, t)
+    assert np.array_equal(est.hot_bitmap(), orc.hot())
+    assert est.stats()["active2"] == orc.row_counts().tolist()
+    compare_report(rep, det)
+    if brute:
+        assert np.array_equal(rep.hosts, orc.candidates_brute())
+    return rep
+
+
+@pytest.mark.parametrize("mode", [DIRECT, TILED])
+def test_paper_parameters_match_oracle(mode):
+    """The paper's own estimator (Section 5): r = r' = 5, q = q' = 17, delta = 5, delta' = 16,
+    eta' = 2^14, 16-bit cells, sliding window k = 300. Traffic: 20 slices of 2^17 pairs, 260
+    slices without traffic, 20 more slices of 2^17 pairs, then 6 empty slices (20 planted
+    hosts of 2k-20k destinations over a Zipf(1.1) background). A row of 2.1 M cells takes two
+    bitmap pieces in the tiled update; the estimate gathers 16-bit cells of 2^14-cell SLEs,
+    looks U up in the 16,385-entry table of the close, and the query's per-distance counts
+    (k > 256) hold distances above 255. Every check of the close against the oracle at
+    slices 0, 19, 290, 299 and 305; at 299 the candidates also against brute force over all
+    2^32 addresses and the query with histograms against Algorithm 8."""
+    sse = S()
+    p = sse.paper_params()
+    assert (p.q, p.q2, p.delta, p.eta2, p.k, p.stamp_bits) == (17, 17, 5, 1 << 14, 300, 16)
+    tr = synth.Traffic(synth.TrafficConfig(seed=25, n_slices=40))
+    est = sse.Estimator(p)
+    est.set_update_mode(mode)
+    orc = oracle.Oracle(oracle_params(p))
+    rng = np.random.default_rng(25)
+    t = 0
+    reports = []
+    for phase in range(2):
+        for j in range(20):
+            if t:
+                orc.advance()
+            pairs = tr.slice(0, 20 * phase + j)
+            est.update(helpers.to_device(pairs))
+            orc.scan(pairs)
+            if t in (0, 19, 290):
+                reports.append(_paper_close_checks(est, orc, p, t))
+            elif t == 299:
+                extra = rng.integers(0, 2**32, 200, dtype=np.uint64).astype(np.uint32)
+                reports.append(_paper_close_checks(est, orc, p, t, brute=True, extra_hosts=extra))
+            else:
+                est.advance()
+            t += 1
+        if phase == 0:
+            for _ in range(260):  # slices 20..279 carry no traffic
+                orc.advance()
+                est.advance()
+                t += 1
+    for _ in range(6):  # slices 300..305: the first slices leave the window
+        orc.advance()
+        if t < 305:
+            est.advance()
+        t += 1
+    reports.append(_paper_close_checks(est, orc, p, 305))
+    assert reports[3].n_super >= 10  # planted hosts of both phases are inside the window at 299
+    assert reports[3].n_super >= reports[1].n_super
+
+
 def test_16bit_stamp_cycle_wraps():
     """65,540 slice advances wrap the 16-bit stamp cycle: every old cell has expired, and the
     slices after the wrap give the state of a fresh oracle that saw only them."""

@@ -459,6 +459,62 @@ def test_decision_in_weight_domain_matches_estimate_threshold():
         assert np.array_equal((est >= theta)[far], (w >= w_theta)[far])
 
 
+@pytest.mark.parametrize("counts,U,case", [((60, 80, 100), 30, "P < 1/2"),
+                                           ((170, 180, 185), 60, "P > 1/2"),
+                                           ((150, 150, 150), 20, "w < 0")])
+def test_corrected_weight_and_estimate_closed_form(counts, U, case):
+    """Eq. 11-12 and Eq. 8 worked by hand on a hand-set SLEA: r' = 3 rows of
+    L' = 2^q' * delta' + eta' - delta' = 188 cells; row i holds exactly counts[i] active cells
+    (distance < k), U of the host's eta' = 64 union cells are active in all three rows and a
+    few more in one row only, inactive cells hold distances >= k. Then
+    P = (c_0/L') (c_1/L') (c_2/L'), multiplied in row order; w = (U - eta' P) / (1 - P),
+    clamped at 0; est = -eta' ln(1 - w/eta'); super iff w >= eta'(1 - e^(-theta/eta')).
+    The oracle's w must be the same double, so a wrong L', a wrong product, a dropped
+    term or a sign error fails."""
+    import math
+    p = small_params(r2=3, q2=5, delta2=4, eta2=64, k=4, theta=32, seed=46)
+    o = Oracle(p)
+    L = o.row_len2
+    assert L == 32 * 4 + 64 - 4 == 188
+    aip = 0x5EED1234
+    rng = np.random.default_rng(46)
+    sle = np.full((p.r2, L), INF, dtype=np.uint16)
+    sle[:, ::7] = p.k  # inactive: distance exactly k
+    sle[:, 3::11] = p.k + 3
+    zs = rng.permutation(p.eta2)
+    common, extra = zs[:U], np.array_split(zs[U:], p.r2)  # extra[i]: active in row i only
+    for i in range(p.r2):
+        base = o.lh(i, aip) * p.delta2
+        inside = np.concatenate([common, extra[i]]) + base
+        outside = np.setdiff1d(np.arange(L), np.arange(base, base + p.eta2))
+        m = counts[i] - len(inside)
+        assert 0 <= m <= len(outside)
+        active = np.concatenate([inside, rng.choice(outside, m, replace=False)])
+        sle[i, active] = rng.integers(0, p.k, len(active))
+    o.set_raw(None, sle)
+    assert o.row_counts().tolist() == list(counts)
+    e = o.estimate([aip])
+    assert e["U"][0] == U
+    eta2 = float(p.eta2)
+    P = 1.0
+    for c in counts:
+        P = P * (c / L)
+    w = (U - eta2 * P) / (1.0 - P)
+    if case == "w < 0":
+        assert w < 0
+        w = 0.0
+    else:
+        assert 0 < w < eta2 - 1 and (P < 0.5) == (case == "P < 1/2")
+    est = -eta2 * math.log((eta2 - w) / eta2)
+    assert e["w"][0] == w
+    assert abs(e["est"][0] - est) <= 1e-12 * max(est, 1e-300)
+    w_theta = eta2 * (1.0 - math.exp(-p.theta / eta2))
+    assert bool(e["flags"][0] & oracle.SUPER) == (w >= w_theta)
+    assert not e["flags"][0] & oracle.SATURATED
+    if case != "w < 0":
+        assert e["flags"][0] & oracle.SUPER  # both positive cases are above theta = 32
+
+
 def test_saturation_and_clamping():
     p = small_params(q2=4, delta2=4, eta2=64, k=2, seed=44)
     o = Oracle(p)

@@ -10,8 +10,10 @@ import ctypes
 import numpy as np
 import pytest
 
+import oracle
 from paper_1805_09246_b300 import synth
 from tests import helpers
+from tests.test_gpu_parity import oracle_params
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -34,6 +36,7 @@ def test_noalloc_query_matches_query_on_two_calls():
     p = sse.Params(seed=21)
     tr = synth.Traffic(synth.small_trace(seed=21))
     est = sse.Estimator(p)
+    orc = oracle.Oracle(oracle_params(p))
     stream = torch.cuda.current_stream()
     ip, _ = tr.planted()
     rng = np.random.default_rng(21)
@@ -41,8 +44,10 @@ def test_noalloc_query_matches_query_on_two_calls():
         # a different window for each call: the scratch must not keep the first call's counts
         for t in range(3 * call, 3 * call + 3):
             est.update(helpers.to_device(tr.slice(0, t)))
+            orc.scan(tr.slice(0, t))
             if t < 3 * call + 2:
                 est.advance()
+                orc.advance()
         _, sle = est.read_stamps()
         sle_padded = np.zeros((p.r2, est.derived["row_pitch2"]), np.uint8)
         sle_padded[:, : sle.shape[1]] = sle
@@ -62,9 +67,19 @@ def test_noalloc_query_matches_query_on_two_calls():
         assert np.all(np.abs(got - ref) <= EST_RTOL * np.maximum(np.abs(ref), 1e-30))
         assert np.array_equal(d_flags.cpu().numpy(), ref_flags.cpu().numpy())
         assert (ref_flags.cpu().numpy() & sse.FLAG_SUPER).any()
+        # and directly against the oracle's Algorithm 8 on the same window
+        want = orc.estimate(hosts)
+        assert np.all(np.abs(got - want["est"]) <= EST_RTOL * np.maximum(want["est"], 1e-30))
+        assert np.array_equal(d_flags.cpu().numpy(), want["flags"])
 
 
-def test_noalloc_query_rejects_too_many_rows():
+def test_noalloc_query_rejects_rows_beyond_the_validator_limit_and_16bit_stamps():
+    """r' = 17 fails parameter validation (the scratch array holds a counter for every r'
+    that validation accepts); 16-bit stamps are refused with INVALID_PARAM."""
     from paper_1805_09246_b300 import sse
-    p = sse.Params(r2=17)
-    assert noalloc_fn()(ctypes.byref(p.to_c()), None, 0, None, 1, None, None, None) == -1
+    fn = noalloc_fn()
+    assert fn(ctypes.byref(sse.Params(r2=17).to_c()), None, 0, None, 1, None, None, None) == -1
+    p16 = sse.Params(stamp_bits=16)
+    dummy = torch.zeros(16, dtype=torch.int32, device="cuda")
+    assert fn(ctypes.byref(p16.to_c()), dummy.data_ptr(), 0, dummy.data_ptr(), 1, dummy.data_ptr(),
+              None, None) == -1
