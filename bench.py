@@ -59,6 +59,11 @@ def parse(argv=None):
     ap.add_argument("--no-graph", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--latency-samples", type=int, default=200, help="synchronised slice closes timed after the run")
+    ap.add_argument("--paced", action="store_true",
+                    help="serving: submit each request at its arrival time (wall clock) instead of at once")
+    ap.add_argument("--serve-slices", type=int, default=200,
+                    help="slice closes of the paced serving leg of the core-link run (0: no serving leg)")
     args = ap.parse_args(argv)
     if args.steps is None:
         args.steps = 27 if args.workload == "learned" else 200
@@ -316,26 +321,30 @@ def main_edge_routers(args, rank, world, local):
     }), flush=True)
 
 
-def main_serving(args, rank, world, local):
-    """32 routers send batches of 64K-4M pairs (log-uniform) with Poisson arrivals offering
-    2e9 pairs/s in aggregate; a slice boundary every 2^26 offered pairs (33.6 ms of virtual
-    time), window k = 16, estimator memory budget 40 GB. The request loop admits batches as
-    staging slots free up; reports slice-close-to-report latency and throughput."""
-    import torch
+SERVE_ROUTERS = 32
+SERVE_OFFERED = 2e9  # pairs/s offered by all routers together
+SERVE_SLICE_PAIRS = 1 << 26  # a slice boundary every 2^26 offered pairs
+
+
+def serve(rank: int, seconds: float, paced: bool, pool_pairs: int | None = None, warm: int = 200) -> dict:
+    """The serving configuration: 32 routers send batches of 64K-4M pairs (log-uniform) with
+    Poisson arrivals offering 2e9 pairs/s in aggregate; a slice boundary every 2^26 offered
+    pairs (33.6 ms of virtual time), window k = 16, estimator memory budget 40 GB; requests
+    are page-locked host memory. The first `warm` requests are submitted at once (untimed);
+    the rest at once too, or with `paced`, each at its arrival time on the wall clock (the
+    offered load). Returns the pairs and wall time of the timed requests and the
+    slice-close-to-report latencies of the slices they closed."""
     from paper_1805_09246_b300 import sse
     from paper_1805_09246_b300.requests import poisson_requests
 
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-    pg = init_ranks(world)
-    R = 32
-    offered = 2e9
-    rs = poisson_requests(R, duration_s=args.serve_seconds, offered_pps=offered, batch_min=1 << 16,
-                          batch_max=1 << 22, seed=rank)
+    R = SERVE_ROUTERS
+    rs = poisson_requests(R, duration_s=seconds, offered_pps=SERVE_OFFERED, batch_min=1 << 16,
+                          batch_max=1 << 22, pool_pairs=pool_pairs, seed=rank, wrap=pool_pairs is None)
+    import torch
     pools = [torch.from_numpy(p.view(np.int32)).pin_memory() for p in rs.pools]  # DMA sources
     pinned = [p.numpy().view(np.uint32) for p in pools]
     params = sse.Params(q=22, q2=16, eta2=4096, k=16, seed=0)
-    slice_s = (1 << 26) / offered
+    slice_s = SERVE_SLICE_PAIRS / SERVE_OFFERED
     srv = sse.Server(params, n_routers=R, slots=16, slot_pairs=1 << 22, memory_budget=40 << 30,
                      slice_seconds=slice_s)
 
@@ -345,46 +354,81 @@ def main_serving(args, rank, world, local):
             return pool[start:start + size]
         return np.take(pool, np.arange(start, start + size), axis=0, mode="wrap")
 
-    n_warm = min(len(rs.requests) // 10, 200)
+    n_warm = min(len(rs.requests) // 10, warm)
     for t, r, start, size in rs.requests[:n_warm]:
         srv.submit(r, t, batch(r, start, size))
+    timed = rs.requests[n_warm:]
+    first_slice = int(timed[0][0] / slice_s) if timed else 0
+    total = sum(size for _, _, _, size in timed)
     torch.cuda.synchronize()
-    total = sum(size for _, _, _, size in rs.requests[n_warm:])
-    clocks = ClockSampler(local)
+    clocks = ClockSampler(torch.cuda.current_device())
     clocks.start()
     time.sleep(0.3)
-    barrier(pg)
     t0 = time.perf_counter()
-    for t, r, start, size in rs.requests[n_warm:]:
+    v0 = timed[0][0] if timed else 0.0
+    for t, r, start, size in timed:
+        if paced:  # wait for the request's arrival time
+            while True:
+                ahead = (t - v0) - (time.perf_counter() - t0)
+                if ahead <= 0:
+                    break
+                if ahead > 2e-3:
+                    time.sleep(ahead - 1e-3)
         srv.submit(r, t, batch(r, start, size))
     srv.flush()
-    wall = max_over_ranks(pg, time.perf_counter() - t0, dev)
+    wall = time.perf_counter() - t0
     clk = clocks.stop()
     reports = srv.poll()
-    lat = sorted(l for _, l in reports)
+    # slices closed by the timed requests: every slice after the one the first timed request fell in
+    lat = sorted(l for rep, l in reports if rep.slice >= first_slice)
     st = srv.stats()
-    total_all = sum_over_ranks(pg, float(total), dev)  # each rank serves its own request stream
+    srv.close()
+    del pools
+    return {"requests": len(rs.requests), "timed_requests": len(timed), "warm_requests": n_warm,
+            "pairs_timed": total, "wall": wall, "virtual": (timed[-1][0] - v0) if timed else 0.0,
+            "latencies": lat, "slices_reported": len(reports), "slot_waits": st["slot_waits"], "clocks": clk,
+            "slice_s": slice_s}
+
+
+def pctl(xs, q):
+    return round(xs[min(len(xs) - 1, int(q * len(xs)))], 4) if xs else None
+
+
+def main_serving(args, rank, world, local):
+    """Serving (see serve()): throughput and slice-close-to-report p50/p99; with --paced the
+    requests arrive at the offered rate, otherwise as fast as the host submits them."""
+    import torch
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pg = init_ranks(world)
+    barrier(pg)
+    res = serve(rank, args.serve_seconds, args.paced, pool_pairs=(1 << 22) if args.paced else None)
+    wall = max_over_ranks(pg, res["wall"], dev)
+    total_all = sum_over_ranks(pg, float(res["pairs_timed"]), dev)  # each rank serves its own request stream
     if pg is not None:
         pg.destroy_process_group()
     if rank != 0:
         return
+    n, lat = res["timed_requests"], res["latencies"]
     print(json.dumps({
         "metric": "Gpackets/s served (32 routers, Poisson batches) and slice-close-to-report p50/p99 ms",
         "value": round(total_all / wall / 1e9, 4), "unit": UNIT, "n_gpus": world,
-        "steps": len(rs.requests) - n_warm, "warmup": n_warm, "ms_per_step": round(wall / max(1, len(rs.requests) - n_warm) * 1e3, 4),
+        "steps": n, "warmup": res["warm_requests"], "ms_per_step": round(wall / max(1, n) * 1e3, 4),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
-        "config": {"workload": f"serving: {R} routers, batches 64K-4M pairs log-uniform, Poisson arrivals "
-                               f"offering {offered:.0e} pairs/s, slice every 2^26 offered pairs ({slice_s*1e3:.1f} ms "
-                               "virtual), k=16, q=22, SLEA 5 x 2^16 x 4096, budget 40 GB, 16 staging slots of 2^22",
-                   "virtual_seconds": args.serve_seconds, "requests": len(rs.requests), "pairs_timed": total,
-                   "step": "one admitted request"},
-        "close_ms_p50": round(lat[len(lat) // 2], 4) if lat else None,
-        "close_ms_p99": round(lat[min(len(lat) - 1, int(0.99 * len(lat)))], 4) if lat else None,
-        "slices_reported": len(reports), "slot_waits": st["slot_waits"],
+        "config": {"workload": f"serving: {SERVE_ROUTERS} routers, batches 64K-4M pairs log-uniform, Poisson arrivals "
+                               f"offering {SERVE_OFFERED:.0e} pairs/s, slice every 2^26 offered pairs "
+                               f"({res['slice_s']*1e3:.1f} ms virtual), k=16, q=22, SLEA 5 x 2^16 x 4096, budget 40 GB, "
+                               "16 staging slots of 2^22",
+                   "virtual_seconds": args.serve_seconds, "requests": res["requests"], "pairs_timed": res["pairs_timed"],
+                   "paced": args.paced, "step": "one admitted request"},
+        "close_ms_p50": pctl(lat, 0.5), "close_ms_p99": pctl(lat, 0.99), "close_samples": len(lat),
+        "offered_gpkts": SERVE_OFFERED / 1e9,
+        "slices_reported": res["slices_reported"], "slot_waits": res["slot_waits"],
         "e2e": {"value": round(total_all / wall / 1e9, 4), "unit": UNIT,
-                "h2d_bytes_per_step": int(total * PAIR_BYTES / max(1, len(rs.requests) - n_warm)),
+                "h2d_bytes_per_step": int(res["pairs_timed"] * PAIR_BYTES / max(1, n)),
                 "d2h_bytes_per_step": 0},
-        "clocks": clk,
+        "clocks": res["clocks"],
     }), flush=True)
 
 
@@ -590,7 +634,7 @@ def main():
     # ---- slice-close latency (after the timed region): the slice boundary is a synchronised
     # stream; latency = sse_close_slice until the report is in host memory
     close_ms, close_dev = [], []
-    n_lat = min(args.steps, 50)
+    n_lat = args.latency_samples
     # the events are created (and first recorded) before the samples: a CUDA event is created
     # lazily at its first record, which would otherwise fall inside the measured interval
     lat_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n_lat)]
@@ -644,6 +688,16 @@ def main():
                "steps": k_e2e}
         del e2e_est, pinned
 
+    # ---- roofs of the update's other units, measured on this device (sse_microbench)
+    mb = sse.microbench(stream)
+    torch.cuda.synchronize()
+    upd_pps = n_slice / (upd_ms / 1e3)
+    stamps_per_pair = params.r2 + params.r * 2.0 ** -est.derived["tau"]  # r' + r 2^-tau cells per pair
+    l2_roof_pps = mb["l2_random_byte_stores_per_s"] / stamps_per_pair
+    # the tiled design per pair: one shared-memory atomic per SLEA row, and every row's CTA
+    # reads the 8-byte pair through the SM's load pipe (from L2 after the first)
+    lsu_s_per_pair = params.r2 / mb["smem_random_atomics_per_s"] + params.r2 * PAIR_BYTES / mb["l2_stream_load_bytes_per_s"]
+
     hbm_peak, peak_kind = peaks()
     achieved = n_slice * PAIR_BYTES / (upd_ms / 1e3) / 1e9
     # DRAM bytes (read + write) of one k_update_tiled<8, 0, 1> launch on this slice, from an ncu
@@ -654,7 +708,38 @@ def main():
                 "peak": hbm_peak, "unit": "GB/s", "frac": round(achieved / hbm_peak, 4), "traffic": traffic,
                 "peak_source": f"{peak_kind} hbm_gbs",
                 "algorithmic_bytes_per_launch": n_slice * PAIR_BYTES,
-                "binding_unit": "SM L1/shared-memory pipe (ncu l1tex throughput 88 % on k_update_tiled)"}
+                "binding_unit": "SM L1/shared-memory pipe (ncu l1tex throughput on k_update_tiled)",
+                "l2_stamp_roof_gpkts": round(l2_roof_pps / 1e9, 3),
+                "l2_sector_frac": round(upd_pps / l2_roof_pps, 4),
+                "l2_sector_note": (f"update rate / (measured random one-byte L2 stores/s / {stamps_per_pair:.3f} stamps "
+                                   "per pair): the roof of stamping every cell in L2; above 1 the tiled design beats it"),
+                "l1tex_roof_gpkts": round(1.0 / lsu_s_per_pair / 1e9, 3),
+                "l1tex_frac": round(upd_pps * lsu_s_per_pair, 4),
+                "l1tex_note": (f"update rate x ({params.r2} / measured random shared-memory atomics/s + "
+                               f"{params.r2} x 8 B / measured L2 streaming-load B/s): share of the SM load pipe's "
+                               "time the tiled design's algorithmic work takes"),
+                "microbench": {k: (round(v / 1e9, 2) if isinstance(v, float) else v) for k, v in mb.items()},
+                "microbench_unit": "G per second (stores, atomics) and GB/s (loads)"}
+
+    # ---- paced serving leg: the serving configuration at its offered load, for the
+    # slice-close-to-report latency of config E (each rank serves its own request stream)
+    serving = None
+    if args.serve_slices > 0 and not paper:
+        del dev_slices
+        torch.cuda.empty_cache()
+        secs = (args.serve_slices + 2) * SERVE_SLICE_PAIRS / SERVE_OFFERED
+        res = serve(rank, secs, paced=True, pool_pairs=1 << 22, warm=50)
+        lat = res["latencies"]
+        serving = {"serving_close_ms_p50": pctl(lat, 0.5), "serving_close_ms_p99": pctl(lat, 0.99),
+                   "serving_close_samples": len(lat),
+                   "serving_served_gpkts": round(res["pairs_timed"] / res["wall"] / 1e9, 4),
+                   "serving_offered_gpkts": SERVE_OFFERED / 1e9,
+                   "serving_config": {"routers": SERVE_ROUTERS, "paced": True, "virtual_s": round(res["virtual"], 3),
+                                      "wall_s": round(res["wall"], 3), "requests": res["timed_requests"],
+                                      "slot_waits": res["slot_waits"], "clocks": res["clocks"],
+                                      "workload": "serving: 32 routers, batches 64K-4M pairs, Poisson arrivals paced at "
+                                                  "2e9 pairs/s, slice every 2^26 offered pairs, k=16, q=22, "
+                                                  "SLEA 5 x 2^16 x 4096; latency = slice boundary to report on the host"}}
 
     if rank != 0:
         return
@@ -688,6 +773,8 @@ def main():
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
         "clocks": clk,
     }
+    if serving:
+        out.update(serving)
     print(json.dumps(out), flush=True)
     if pg is not None:
         pg.destroy_process_group()

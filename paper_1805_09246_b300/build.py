@@ -19,17 +19,21 @@ FLAGS = [
 ]
 
 
+# translation units: the API with every estimator kernel, and the roof microbenchmarks
+UNITS = ["sse_api.cu", "microbench.cu"]
+
+
 def sources() -> list[str]:
     return sorted(glob.glob(os.path.join(CSRC, "*.cu")) + glob.glob(os.path.join(CSRC, "*.cuh"))
-                  + [os.path.join(INCLUDE, "sse.h")])
+                  + glob.glob(os.path.join(INCLUDE, "*.h")))
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
-    """Compile csrc/sse_api.cu (which includes the kernels) into libsse.so if stale."""
+    """Compile the translation units (sse_api.cu includes the kernels) into libsse.so if stale."""
     newest = max(os.path.getmtime(s) for s in sources())
     if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= newest:
         return LIB
-    cmd = [NVCC, *FLAGS, "-I", INCLUDE, "-o", LIB + ".tmp", os.path.join(CSRC, "sse_api.cu")]
+    cmd = [NVCC, *FLAGS, "-I", INCLUDE, "-o", LIB + ".tmp", *[os.path.join(CSRC, u) for u in UNITS]]
     if verbose:
         cmd.insert(1, "-Xptxas=-v")
     subprocess.run(cmd, check=True)

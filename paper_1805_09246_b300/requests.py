@@ -27,9 +27,12 @@ class RequestStream:
 
 
 def poisson_requests(n_routers: int, duration_s: float, offered_pps: float, batch_min: int, batch_max: int,
-                     pool_pairs: int | None = None, seed: int = 0) -> RequestStream:
+                     pool_pairs: int | None = None, seed: int = 0, wrap: bool = True) -> RequestStream:
     """pool_pairs=None sizes every router's pool to its whole request stream, so no batch
-    wraps around and every batch is a contiguous view of the pool."""
+    wraps around and every batch is a contiguous view of the pool. With wrap=False a batch
+    that would run past the end of its pool starts at the pool's beginning instead, so
+    every batch is a contiguous view of the pool whatever its size (pool_pairs must be at
+    least batch_max)."""
     rng = np.random.default_rng(seed)
     mean_batch = (batch_max - batch_min) / np.log(batch_max / batch_min)
     rate = offered_pps / n_routers / mean_batch  # batches per second per router
@@ -50,8 +53,12 @@ def poisson_requests(n_routers: int, duration_s: float, offered_pps: float, batc
                               planted_max=20000, group_min=1, group_max=min(8, n_routers))
     tr = synth.Traffic(cfg)
     pools = [tr.slice(r, 0) for r in range(n_routers)]
+    if not wrap and pool < batch_max:
+        raise ValueError("pool_pairs below batch_max with wrap=False")
     reqs, pos = [], np.zeros(n_routers, np.int64)
     for t, r, size in plan:
+        if not wrap and pos[r] + size > pool:
+            pos[r] = 0
         reqs.append((t, r, int(pos[r]), size))
         pos[r] = (pos[r] + size) % pool
     reqs.sort(key=lambda x: (x[0], x[1]))
