@@ -26,19 +26,23 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "sse_oracle.cpp")
-_LIB = os.path.join(_HERE, "liborc.so")
+# SSE_ORACLE_LIB: load another build of the same source (the sanitizer build of the tests)
+_LIB = os.environ.get("SSE_ORACLE_LIB") or os.path.join(_HERE, "liborc.so")
 
 SUPER = 1
 SATURATED = 2
 
 
-def build(force: bool = False) -> str:
-    """Compile ``liborc.so`` (plain C++17, no FMA contraction)."""
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
-        cmd = ["g++", "-O2", "-std=c++17", "-fPIC", "-shared", "-pthread", "-ffp-contract=off",
-               "-o", _LIB, _SRC]
-        subprocess.run(cmd, check=True)
-    return _LIB
+def build(force: bool = False, sanitize: bool = False, out: str | None = None) -> str:
+    """Compile ``liborc.so`` (plain C++17, no FMA contraction). ``sanitize`` builds with
+    AddressSanitizer and UndefinedBehaviorSanitizer (any report aborts) into ``out``."""
+    lib = out or _LIB
+    if sanitize or force or not os.path.exists(lib) or os.path.getmtime(lib) < os.path.getmtime(_SRC):
+        cmd = ["g++", "-O2", "-std=c++17", "-fPIC", "-shared", "-pthread", "-ffp-contract=off"]
+        if sanitize:
+            cmd += ["-g", "-fsanitize=address,undefined", "-fno-sanitize-recover=all", "-fno-omit-frame-pointer"]
+        subprocess.run(cmd + ["-o", lib, _SRC], check=True)
+    return lib
 
 
 class _Params(ctypes.Structure):

@@ -28,17 +28,24 @@ def sources() -> list[str]:
                   + glob.glob(os.path.join(INCLUDE, "*.h")))
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    """Compile the translation units (sse_api.cu includes the kernels) into libsse.so if stale."""
+def build(force: bool = False, verbose: bool = False, nvtx: bool | None = None, out: str | None = None) -> str:
+    """Compile the translation units (sse_api.cu includes the kernels) into libsse.so if stale.
+    nvtx (default: the SSE_NVTX environment variable) compiles in NVTX ranges around the
+    entry points; out builds into another path (always rebuilt)."""
+    if nvtx is None:
+        nvtx = os.environ.get("SSE_NVTX", "0") not in ("", "0")
+    lib = out or LIB
     newest = max(os.path.getmtime(s) for s in sources())
-    if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= newest:
-        return LIB
-    cmd = [NVCC, *FLAGS, "-I", INCLUDE, "-o", LIB + ".tmp", *[os.path.join(CSRC, u) for u in UNITS]]
+    if out is None and not force and not nvtx and os.path.exists(lib) and os.path.getmtime(lib) >= newest:
+        return lib
+    cmd = [NVCC, *FLAGS, "-I", INCLUDE, "-o", lib + ".tmp", *[os.path.join(CSRC, u) for u in UNITS]]
+    if nvtx:
+        cmd.insert(1, "-DSSE_NVTX")
     if verbose:
         cmd.insert(1, "-Xptxas=-v")
     subprocess.run(cmd, check=True)
-    os.replace(LIB + ".tmp", LIB)
-    return LIB
+    os.replace(lib + ".tmp", lib)
+    return lib
 
 
 if __name__ == "__main__":

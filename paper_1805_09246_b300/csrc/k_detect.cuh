@@ -516,19 +516,24 @@ __global__ void __launch_bounds__(256) k_report(CloseScratch* __restrict__ sc, c
 // the 2^delta SREs with low bits c is hot). Probes run 16 he_0 at a time; the (lane, he_0)
 // pairs that hit are pushed on a per-warp stack (warp prefix sum), and whenever 32 wait, every
 // lane expands one: the hot SREs of the group come from the regrouped row-2 table, and each
-// chain must pass row 3's "any hot" bit before it is queued in shared memory; the block grows
-// the queued chains every 4 probe blocks once the queue is half full, and at the end of the
-// work unit (a full queue makes the thread grow the chain itself). The two "any hot" bitmaps
-// are staged in shared memory when `stage` is set; the blocks are small (kJoinTiledThreads)
-// so that several share an SM.
+// chain must pass row 3's "any hot" bit before it is queued. Each warp works as a pipeline of
+// stages, all 32 lanes in every stage: expanded chains go to the warp's partial-chain queue;
+// whenever 32 wait, each lane grows one through rows 3 and 4 (warp-uniform loops over their
+// hot SREs) into the warp's complete-chain queue; whenever 32 of those wait, each lane
+// regains the hosts of one. So the divergent depth-first walk of a lone lane never runs, and
+// the regain search, the bulk of the work when hot SREs are common, runs on full warps. The
+// two "any hot" bitmaps are staged in shared memory when `stage` is set; the blocks are small
+// (kJoinTiledThreads) so that several share an SM.
 constexpr int kJoinTiledThreads = 256;
-constexpr uint32_t kJoinQueueCap = 1024;   // chains per block queue (grown by the block when half full)
+constexpr uint32_t kJoinWarpQueue = 64;    // entries of each per-warp chain queue (< 32 waiting + 32 pushed)
 constexpr uint32_t kJoinChunkMax = 256;    // he_0 per work unit
 constexpr uint32_t kJoinProbeBlock = 16;   // he_0 probed before a compaction
 constexpr uint32_t kJoinListWords = (32 + 32 * kJoinProbeBlock) / 2;  // per warp hit stack: 16-bit entries
-// dynamic shared memory after the optional bitmaps: queue, he_0 chunk, K chunk, he_1, lists
+// dynamic shared memory after the optional bitmaps: per-warp chain queues (partial: 3 words,
+// complete: 2 words per entry), he_0 chunk, K chunk, he_1, hit stacks
 constexpr size_t kJoinTiledFixedBytes =
-    (3 * (size_t)kJoinQueueCap + 2 * kJoinChunkMax + kJoinTiledThreads + (kJoinTiledThreads / 32) * kJoinListWords) * 4;
+    ((kJoinTiledThreads / 32) * 5 * (size_t)kJoinWarpQueue + 2 * kJoinChunkMax + kJoinTiledThreads +
+     (kJoinTiledThreads / 32) * kJoinListWords) * 4;
 
 // Words of an "any hot" bitmap over the 2^(q-delta) values of c, and the shared-memory words
 // that hold one (a multiple of 4, so that what follows stays 16-byte aligned).
@@ -549,7 +554,6 @@ __global__ void __launch_bounds__(kJoinTiledThreads) k_join_tiled(
     const uint32_t* __restrict__ n_list, uint32_t* __restrict__ cand, uint32_t* __restrict__ n_cand, uint32_t cap,
     uint32_t* __restrict__ overflow) {
   extern __shared__ uint32_t sm[];
-  __shared__ uint32_t s_qn;
   const uint32_t n0 = n_list[0], n1 = n_list[1];
   if (n0 == 0 || n1 == 0) return;
   const uint32_t delta = p.delta, q = p.q;
@@ -599,15 +603,18 @@ __global__ void __launch_bounds__(kJoinTiledThreads) k_join_tiled(
     if (any3) a3 = d3;
     next = d3 + any_words_staged(q, delta);
   }
-  uint32_t* qh = next;
-  uint32_t* qb1 = qh + kJoinQueueCap;
-  uint32_t* qb2 = qb1 + kJoinQueueCap;
-  uint32_t* s_he0 = qb2 + kJoinQueueCap;
+  // per-warp queues: partial chains (he_0, B(1), B(2)) and complete chains (he_0, address
+  // bits [delta, 32)), kJoinWarpQueue entries each
+  uint32_t* wq_he0 = next + warp * (5 * kJoinWarpQueue);
+  uint32_t* wq_b1 = wq_he0 + kJoinWarpQueue;
+  uint32_t* wq_b2 = wq_b1 + kJoinWarpQueue;
+  uint32_t* wc_he0 = wq_b2 + kJoinWarpQueue;
+  uint32_t* wc_high = wc_he0 + kJoinWarpQueue;
+  uint32_t* s_he0 = next + (kJoinTiledThreads / 32) * (5 * kJoinWarpQueue);
   uint32_t* s_k = s_he0 + kJoinChunkMax;
   uint32_t* s_he1 = s_k + kJoinChunkMax;
   uint16_t* my_list = reinterpret_cast<uint16_t*>(s_he1 + kJoinTiledThreads) + warp * (2 * kJoinListWords);
   static_assert(kJoinChunkMax <= 256, "hit entries hold 8-bit chunk indices");
-  if (threadIdx.x == 0) s_qn = 0;
   // the sorted a*low table of regain (multiply-add-shift RHFG[0]; first used after the
   // barrier that opens every work unit)
   __shared__ RegainTable s_rt;
@@ -620,37 +627,109 @@ __global__ void __launch_bounds__(kJoinTiledThreads) k_join_tiled(
   const uint32_t width1 = (n1 + tiles1 - 1) / tiles1;
   const uint64_t rows = (uint64_t)tiles1 * n0;
   const uint64_t r_begin = rows * blockIdx.x / gridDim.x, r_end = rows * (blockIdx.x + 1) / gridDim.x;
+  const uint32_t lt_mask = (1u << lane) - 1u;
+  const uint64_t nwords = (1ull << q) >> 5;
 
-  auto emit = [&](uint32_t he0, uint32_t b1, uint32_t b2) {
-    const uint32_t at = atomicAdd(&s_qn, 1u);
-    if (at < kJoinQueueCap) {
-      qh[at] = he0;
-      qb1[at] = b1;
-      qb2[at] = b2;
-    } else {
-      grow_chain(p, tables, he0, b1, b2, cand, n_cand, cap, overflow, rt);
+  // Every stage below is entered by all 32 lanes of the warp together, each lane holding
+  // one item or none (`ok`), and loops while any lane has work; items flow to the next stage
+  // through the warp's queues, which hand the next stage 32 at a time.
+  uint32_t cn = 0;  // complete chains queued (the same in every lane)
+  // Regain (Eq. 7 plus the delta low bits): one complete chain per lane.
+  auto push_complete = [&](bool ok, uint32_t he0, uint32_t high) {
+    const uint32_t b = __ballot_sync(0xFFFFFFFFu, ok);
+    if (ok) {
+      const uint32_t at = cn + __popc(b & lt_mask);
+      wc_he0[at] = he0;
+      wc_high[at] = high;
+    }
+    cn += __popc(b);
+    if (cn >= 32) {
+      cn -= 32;
+      __syncwarp();
+      const uint32_t e0 = wc_he0[cn + lane], eh = wc_high[cn + lane];
+      __syncwarp();
+      regain_high(p, e0, eh, cand, n_cand, cap, overflow, rt);
     }
   };
-  // One hit (he_0, he_1): every hot row-2 SRE of the group gives B(2); chains whose row-3
-  // group has a hot SRE are queued.
-  auto expand = [&](uint32_t e) {
-    const uint32_t he0 = s_he0[e & 255u];
-    const uint32_t b1 = he0 ^ s_he1[warp * 32 + (e >> 8)];
-    if (!fits32(1, delta, q, b1)) return;
+  // Rows 3 .. r-1 of a chain (Algorithm 5). For r = 5 the hot SREs of rows 3 and 4 are
+  // walked by warp-uniform loops and the complete chains queued for regain; other r grow
+  // their chains lane by lane (depth first, regaining inline).
+  auto grow = [&](bool ok, uint32_t he0, uint32_t b1, uint32_t b2) {
+    if (p.r != 5) {
+      if (ok) grow_chain(p, tables, he0, b1, b2, cand, n_cand, cap, overflow, rt);
+      return;
+    }
+    const uint32_t hi0 = he0 >> shift_hi;
+    const uint64_t high12 = ((uint64_t)b1 << delta) | ((uint64_t)(b2 >> shift_hi) << (2 * delta + shift_hi));
+    uint32_t m3 = ok ? hot_group(tables + nwords, (he0 ^ (b2 >> delta)) & cmask, delta) : 0u;
+    while (__any_sync(0xFFFFFFFFu, m3 != 0u)) {
+      uint32_t m4 = 0, b3 = 0;
+      if (m3) {
+        b3 = (b2 >> delta) | (((uint32_t)(__ffs(m3) - 1) ^ hi0) << shift_hi);
+        m3 &= m3 - 1u;
+        if (fits32(3, delta, q, b3)) m4 = hot_group(tables + 2 * nwords, (he0 ^ (b3 >> delta)) & cmask, delta);
+      }
+      const uint64_t high123 = high12 | ((uint64_t)(b3 >> shift_hi) << (3 * delta + shift_hi));
+      while (__any_sync(0xFFFFFFFFu, m4 != 0u)) {
+        bool done = false;
+        uint32_t high = 0;
+        if (m4) {
+          const uint32_t b4 = (b3 >> delta) | (((uint32_t)(__ffs(m4) - 1) ^ hi0) << shift_hi);
+          m4 &= m4 - 1u;
+          // with B(4) inside 32 address bits (fits32), bits [delta, 32) hold the whole chain
+          done = fits32(4, delta, q, b4);
+          high = (uint32_t)(high123 | ((uint64_t)(b4 >> shift_hi) << (4 * delta + shift_hi)));
+        }
+        push_complete(done, he0, high);
+      }
+    }
+  };
+  uint32_t pn = 0;  // partial chains queued (the same in every lane)
+  auto push_partial = [&](bool ok, uint32_t he0, uint32_t b1, uint32_t b2) {
+    const uint32_t b = __ballot_sync(0xFFFFFFFFu, ok);
+    if (ok) {
+      const uint32_t at = pn + __popc(b & lt_mask);
+      wq_he0[at] = he0;
+      wq_b1[at] = b1;
+      wq_b2[at] = b2;
+    }
+    pn += __popc(b);
+    if (pn >= 32) {
+      pn -= 32;
+      __syncwarp();
+      const uint32_t e0 = wq_he0[pn + lane], e1 = wq_b1[pn + lane], e2 = wq_b2[pn + lane];
+      __syncwarp();
+      grow(true, e0, e1, e2);
+    }
+  };
+  // One hit (he_0, he_1) per lane: every hot row-2 SRE of the group gives B(2); chains whose
+  // row-3 group has a hot SRE are queued.
+  auto expand = [&](bool ok, uint32_t e) {
+    uint32_t he0 = 0, b1 = 0, m = 0;
+    if (ok) {
+      he0 = s_he0[e & 255u];
+      b1 = he0 ^ s_he1[warp * 32 + (e >> 8)];
+    }
     const uint32_t low2 = b1 >> delta;
     const uint32_t hi0 = he0 >> shift_hi;
-    const uint32_t first = ((he0 ^ low2) & cmask) << delta;  // row-2 group of c
-    uint32_t m = (tables[first >> 5] >> (first & 31)) & span_mask;
-    while (m) {
-      const uint32_t tp = __ffs(m) - 1;  // top bits of he_2
-      m &= m - 1;
-      const uint32_t b2 = low2 | ((tp ^ hi0) << shift_hi);
-      if (!row2_fits_all && !fits32(2, delta, q, b2)) continue;
-      if (a3) {
-        const uint32_t c3 = (he0 ^ (b2 >> delta)) & cmask;
-        if (!((a3[c3 >> 5] >> (c3 & 31)) & 1u)) continue;
+    if (ok && fits32(1, delta, q, b1)) {
+      const uint32_t first = ((he0 ^ low2) & cmask) << delta;  // row-2 group of c
+      m = (tables[first >> 5] >> (first & 31)) & span_mask;
+    }
+    while (__any_sync(0xFFFFFFFFu, m != 0u)) {
+      bool keep = false;
+      uint32_t b2 = 0;
+      if (m) {
+        const uint32_t tp = __ffs(m) - 1;  // top bits of he_2
+        m &= m - 1;
+        b2 = low2 | ((tp ^ hi0) << shift_hi);
+        keep = row2_fits_all || fits32(2, delta, q, b2);
+        if (keep && a3) {
+          const uint32_t c3 = (he0 ^ (b2 >> delta)) & cmask;
+          keep = (a3[c3 >> 5] >> (c3 & 31)) & 1u;
+        }
       }
-      emit(he0, b1, b2);
+      push_partial(keep, he0, b1, b2);
     }
   };
   uint32_t hn = 0;  // entries on this warp's hit stack (the same in every lane)
@@ -662,7 +741,7 @@ __global__ void __launch_bounds__(kJoinTiledThreads) k_join_tiled(
     if (mm > r_end - r0) mm = r_end - r0;
     const uint32_t m0 = (uint32_t)mm;
     r0 += m0;
-    __syncthreads();  // previous unit's chunk and queue are done with
+    __syncthreads();  // previous unit's chunk is done with
     for (uint32_t j = threadIdx.x; j < ((m0 + kJoinProbeBlock - 1) & ~(kJoinProbeBlock - 1)); j += blockDim.x) {
       if (j < m0) {
         const uint32_t he0 = list0[c0 + j];
@@ -721,34 +800,20 @@ __global__ void __launch_bounds__(kJoinTiledThreads) k_join_tiled(
       __syncwarp();
       while (hn >= 32) {  // every lane expands one hit, from the top of the stack
         hn -= 32;
-        expand(my_list[hn + lane]);
+        expand(true, my_list[hn + lane]);
         __syncwarp();  // those entries are overwritten by the next append
       }
-      // every 4 probe blocks: a queue at least half full is grown by all threads, so that
-      // it rarely overflows into the divergent inline growth of emit()
-      if ((j0 / kJoinProbeBlock) % 4 == 3) {
-        __syncthreads();
-        const uint32_t qn = s_qn;  // no emit runs between the barriers
-        if (qn >= kJoinQueueCap / 2) {
-          const uint32_t n = min(qn, kJoinQueueCap);
-          for (uint32_t i = threadIdx.x; i < n; i += blockDim.x)
-            grow_chain(p, tables, qh[i], qb1[i], qb2[i], cand, n_cand, cap, overflow, rt);
-          __syncthreads();
-          if (threadIdx.x == 0) s_qn = 0;
-        }
-        __syncthreads();
-      }
     }
-    if (lane < hn) expand(my_list[lane]);  // the rest, before the chunk is replaced
+    // the rest of the hits, before the chunk is replaced (the chain queues carry over)
+    expand(lane < hn, lane < hn ? my_list[lane] : 0u);
     hn = 0;
     __syncwarp();
-    __syncthreads();  // the queue is complete
-    const uint32_t qn = min(s_qn, kJoinQueueCap);
-    for (uint32_t i = threadIdx.x; i < qn; i += blockDim.x)
-      grow_chain(p, tables, qh[i], qb1[i], qb2[i], cand, n_cand, cap, overflow, rt);
-    __syncthreads();
-    if (threadIdx.x == 0) s_qn = 0;
   }
+  // the chains still queued: partial ones grown, then complete ones regained
+  grow(lane < pn, wq_he0[lane], wq_b1[lane], wq_b2[lane]);
+  pn = 0;
+  __syncwarp();
+  if (lane < cn) regain_high(p, wc_he0[lane], wc_high[lane], cand, n_cand, cap, overflow, rt);
 }
 
 // ---------------------------------------------------------------- ordering

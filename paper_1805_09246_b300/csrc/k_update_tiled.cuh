@@ -95,8 +95,10 @@ struct TileGeometry {
 
 // grid = groups * tiles CTAs; dynamic shared memory = piece_bytes / 8 + kRsraQueueBytes. UNROLL 128-bit loads
 // are in flight per thread; CHECK reads the bitmap word first and skips the atomic when the
-// bit is already set (repeated pairs are common in real traffic).
-template <typename St, int UNROLL, bool CHECK, bool WHOLE>
+// bit is already set (repeated pairs are common in real traffic). PIPE issues the next block
+// iteration's loads before the current iteration's pairs are hashed (two register buffers),
+// so each thread's loads overlap its own atomics.
+template <typename St, int UNROLL, bool CHECK, bool WHOLE, bool PIPE = false>
 __global__ void __launch_bounds__(kTiledThreads, 1) k_update_tiled(const __grid_constant__ KParams p, TileGeometry g,
                                                                    const uint2* __restrict__ pairs, uint64_t n,
                                                                    uint8_t* __restrict__ sre_bytes,
@@ -115,21 +117,23 @@ __global__ void __launch_bounds__(kTiledThreads, 1) k_update_tiled(const __grid_
   RsraQueue rq{reinterpret_cast<uint2*>(bm + words) + (threadIdx.x >> 5) * kRsraQueueEntries, 0u, threadIdx.x & 31u};
   __syncthreads();
 
-  // this group's pairs: [begin, end)
-  const uint64_t begin = n * group / g.groups, end = n * (group + 1) / g.groups;
+  // this group's pairs: [begin, end). The pairs before the first 128-byte boundary (the
+  // head, at most 15) belong to group 0; the rest is cut at multiples of 16 pairs, so every
+  // group starts on a 128-byte line and a warp's 512-byte load covers four whole lines (an
+  // unaligned one spans five, and the load pipe moves one line per wavefront). The head's
+  // and the odd last pair's RSRA work belongs to tile 0.
+  const uint64_t head = min((uint64_t)(((128u - (reinterpret_cast<uintptr_t>(pairs) & 127u)) & 127u) >> 3), n);
+  const uint64_t lines = (n - head) >> 4;
+  const uint64_t begin = head + 16 * (lines * group / g.groups);
+  const uint64_t end = group + 1 == g.groups ? n : head + 16 * (lines * (group + 1) / g.groups);
   const SleTile st(p, row, lo, g.piece_bytes);
   auto touch = [&](uint32_t aip, uint32_t bip) { st.touch<WHOLE, CHECK>(bm, aip, bip); };
-  // peel to a 16-byte boundary, then two pairs per 128-bit load; the peeled and the odd
-  // last pair's RSRA work belongs to tile 0
-  uint64_t j0 = begin;
-  if (j0 < end && (reinterpret_cast<uintptr_t>(pairs + j0) & 15u)) {
-    if (threadIdx.x == 0) {
-      const uint2 v = pairs[j0];
-      touch(v.x, v.y);
-      if (tile == 0) stamp_rsra(p, v.x, v.y, sre, stamp);
-    }
-    j0 += 1;
+  if (group == 0 && threadIdx.x < head) {
+    const uint2 v = pairs[threadIdx.x];
+    touch(v.x, v.y);
+    if (tile == 0) stamp_rsra(p, v.x, v.y, sre, stamp);
   }
+  const uint64_t j0 = begin;
   const uint4* vec = reinterpret_cast<const uint4*>(pairs + j0);
   const uint32_t nvec = (uint32_t)((end - j0) >> 1);
   const uint32_t stride = blockDim.x;
@@ -140,11 +144,7 @@ __global__ void __launch_bounds__(kTiledThreads, 1) k_update_tiled(const __grid_
   // ownership let the compiler predicate the hashing of H1 into every tile).
   const uint32_t full = nvec / (stride * UNROLL);
   uint32_t owner = 0;
-  for (uint32_t k = 0; k < full; ++k) {
-    const uint32_t base = k * stride * UNROLL + threadIdx.x;
-    uint4 buf[UNROLL];
-#pragma unroll
-    for (int u = 0; u < UNROLL; ++u) buf[u] = load_stream(vec + base + u * stride, policy);
+  auto block_iteration = [&](const uint4 (&buf)[UNROLL]) {
 #pragma unroll
     for (int u = 0; u < UNROLL; ++u) {
       touch(buf[u].x, buf[u].y);
@@ -158,6 +158,35 @@ __global__ void __launch_bounds__(kTiledThreads, 1) k_update_tiled(const __grid_
       }
     }
     owner = owner + 1 == g.tiles ? 0 : owner + 1;
+  };
+  if (PIPE) {
+    uint4 cur[UNROLL];
+    if (full > 0) {
+#pragma unroll
+      for (int u = 0; u < UNROLL; ++u) cur[u] = load_stream(vec + threadIdx.x + u * stride, policy);
+    }
+    for (uint32_t k = 0; k < full; ++k) {
+      uint4 nxt[UNROLL];
+      if (k + 1 < full) {  // uniform
+        const uint32_t base = (k + 1) * stride * UNROLL + threadIdx.x;
+#pragma unroll
+        for (int u = 0; u < UNROLL; ++u) nxt[u] = load_stream(vec + base + u * stride, policy);
+      } else {
+#pragma unroll
+        for (int u = 0; u < UNROLL; ++u) nxt[u] = make_uint4(0, 0, 0, 0);
+      }
+      block_iteration(cur);
+#pragma unroll
+      for (int u = 0; u < UNROLL; ++u) cur[u] = nxt[u];
+    }
+  } else {
+    for (uint32_t k = 0; k < full; ++k) {
+      const uint32_t base = k * stride * UNROLL + threadIdx.x;
+      uint4 buf[UNROLL];
+#pragma unroll
+      for (int u = 0; u < UNROLL; ++u) buf[u] = load_stream(vec + base + u * stride, policy);
+      block_iteration(buf);
+    }
   }
   const bool mine = owner == tile && p.sre_on;  // remainder: the last, partial iteration
   for (uint32_t u = 0; u < UNROLL; ++u) {

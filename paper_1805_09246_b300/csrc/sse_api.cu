@@ -10,6 +10,24 @@
 #include <cstddef>
 #include <new>
 
+// NVTX ranges around the entry points' host work (update, close, merge, query, batch
+// steps), for timeline tools; compiled in only with -DSSE_NVTX (header-only NVTX v3, no
+// library to link; a range costs nothing when no tool is attached).
+#ifdef SSE_NVTX
+#include <nvtx3/nvToolsExt.h>
+namespace {
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
+}  // namespace
+#define SSE_NVTX_RANGE(name) NvtxRange sse_nvtx_range_(name)
+#else
+#define SSE_NVTX_RANGE(name) ((void)0)
+#endif
+
 #include "k_batch.cuh"
 #include "k_close.cuh"
 #include "k_detect.cuh"
@@ -259,13 +277,14 @@ struct TiledVariant {
   int unroll;
   bool check;
 };
-#define SSE_TILED(U, C)                                                           \
-  {{{k_update_tiled<uint8_t, U, C, false>, k_update_tiled<uint8_t, U, C, true>},   \
-    {k_update_tiled<uint16_t, U, C, false>, k_update_tiled<uint16_t, U, C, true>}}, \
+#define SSE_TILED(U, C, P)                                                                  \
+  {{{k_update_tiled<uint8_t, U, C, false, P>, k_update_tiled<uint8_t, U, C, true, P>},       \
+    {k_update_tiled<uint16_t, U, C, false, P>, k_update_tiled<uint16_t, U, C, true, P>}}, \
    U, C}
 const TiledVariant kTiledVariants[] = {
-    SSE_TILED(4, false), SSE_TILED(2, false), SSE_TILED(8, false),
-    SSE_TILED(4, true),  SSE_TILED(2, true),  SSE_TILED(8, true),
+    SSE_TILED(4, false, false), SSE_TILED(2, false, false), SSE_TILED(8, false, false),
+    SSE_TILED(4, true, false),  SSE_TILED(2, true, false),  SSE_TILED(8, true, false),
+    SSE_TILED(4, false, true),  SSE_TILED(5, false, true),  SSE_TILED(3, false, true),
 };
 #undef SSE_TILED
 constexpr int kNumTiledVariants = sizeof(kTiledVariants) / sizeof(kTiledVariants[0]);
@@ -662,6 +681,7 @@ int sse_autotune_update(sse_handle* h, const uint32_t* d_pairs, uint64_t n_pairs
 }
 
 int sse_update(sse_handle* h, const uint32_t* d_pairs, uint64_t n_pairs) {
+  SSE_NVTX_RANGE("sse_update");
   if (!h) return SSE_ERR_INVALID_PARAM;
   if (h->sticky) return h->sticky;
   if (n_pairs == 0) return SSE_OK;
@@ -670,6 +690,7 @@ int sse_update(sse_handle* h, const uint32_t* d_pairs, uint64_t n_pairs) {
 }
 
 int sse_update_host(sse_handle* h, const uint32_t* h_pairs, uint64_t n_pairs) {
+  SSE_NVTX_RANGE("sse_update_host");
   if (!h) return SSE_ERR_INVALID_PARAM;
   if (h->sticky) return h->sticky;
   if (n_pairs == 0) return SSE_OK;
@@ -724,6 +745,7 @@ int sse_update_host(sse_handle* h, const uint32_t* h_pairs, uint64_t n_pairs) {
 }
 
 int sse_advance(sse_handle* h) {
+  SSE_NVTX_RANGE("sse_advance");
   if (!h) return SSE_ERR_INVALID_PARAM;
   if (h->sticky) return h->sticky;
   SSE_CUDA(h, cudaMemsetAsync(h->scratch, 0, sizeof(CloseScratch), h->stream));
@@ -985,6 +1007,7 @@ int close_slice_graph(sse_handle* h, sse_report* out) {
 extern "C" {
 
 int sse_close_slice(sse_handle* h, sse_report* out) {
+  SSE_NVTX_RANGE("sse_close_slice");
   if (!h) return SSE_ERR_INVALID_PARAM;
   if (h->sticky) return h->sticky;
   if (h->close_pending) return SSE_ERR_STATE;
@@ -1016,6 +1039,7 @@ int sse_debug_sort_barrier(sse_handle* h, uint32_t spin_limit, uint32_t extra_ar
 }
 
 int sse_close_slice_async(sse_handle* h) {
+  SSE_NVTX_RANGE("sse_close_slice_async");
   if (!h) return SSE_ERR_INVALID_PARAM;
   if (h->sticky) return h->sticky;
   if (!h->close_graph || h->close_pending) return SSE_ERR_STATE;
@@ -1023,6 +1047,7 @@ int sse_close_slice_async(sse_handle* h) {
 }
 
 int sse_close_slice_wait(sse_handle* h, sse_report* out) {
+  SSE_NVTX_RANGE("sse_close_slice_wait");
   if (!h) return SSE_ERR_INVALID_PARAM;
   if (h->sticky) return h->sticky;
   if (!h->close_pending) return SSE_ERR_STATE;
@@ -1030,6 +1055,7 @@ int sse_close_slice_wait(sse_handle* h, sse_report* out) {
 }
 
 int sse_merge(sse_handle* dst, const sse_handle* const* srcs, int n) {
+  SSE_NVTX_RANGE("sse_merge");
   if (!dst || !srcs || n < 1 || n > kMaxMergeSources) return SSE_ERR_INVALID_PARAM;
   if (dst->sticky) return dst->sticky;
   MergeSources sre_src, sle_src;
@@ -1054,6 +1080,7 @@ int sse_merge(sse_handle* dst, const sse_handle* const* srcs, int n) {
 }
 
 int sse_query(sse_handle* h, const uint32_t* d_hosts, uint32_t n, float* d_est, uint8_t* d_flags, uint32_t* d_hist) {
+  SSE_NVTX_RANGE("sse_query");
   if (!h) return SSE_ERR_INVALID_PARAM;
   if (h->sticky) return h->sticky;
   if (n == 0) return SSE_OK;
@@ -1598,6 +1625,7 @@ int batch_step(sse_batch* b, const uint32_t* const* d_pairs, const uint64_t* h_c
 extern "C" {
 
 int sse_batch_step(sse_batch* b, const uint64_t* h_counts, sse_report* out) {
+  SSE_NVTX_RANGE("sse_batch_step");
   if (!b || !h_counts) return SSE_ERR_INVALID_PARAM;
   const uint32_t* ptrs[kMaxRouters];
   for (int r = 0; r < b->n; ++r) {
@@ -1613,6 +1641,7 @@ int sse_batch_step_from(sse_batch* b, const uint32_t* const* d_pairs, const uint
 }
 
 int sse_batch_step_async(sse_batch* b, const uint32_t* const* d_pairs, const uint64_t* h_counts) {
+  SSE_NVTX_RANGE("sse_batch_step_async");
   if (!b || !h_counts) return SSE_ERR_INVALID_PARAM;
   const uint32_t* ptrs[kMaxRouters];
   for (int r = 0; r < b->n; ++r) {

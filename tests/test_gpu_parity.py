@@ -202,16 +202,22 @@ def test_update_strategies_agree(params):
         pairs = pairs[::-1].copy()
 
 
-def test_misaligned_device_pointer():
-    """Pairs starting 8 bytes past a 16-byte boundary (a peeled first pair)."""
+@pytest.mark.parametrize("mode", [DIRECT, TILED])
+@pytest.mark.parametrize("offset,n", [(1, 10001), (5, 70001), (15, 70000), (16, 70001), (9, 3), (3, 12)])
+def test_misaligned_device_pointer(offset, n, mode):
+    """Pairs starting `offset` pairs past a 128-byte boundary: the tiled update's head (the
+    pairs before the first 128-byte line, up to 15, all of them when n is smaller) and the
+    direct update's 16-byte peel, against the oracle."""
     S = sse()
-    p = S.Params(seed=3)
-    rng = np.random.default_rng(3)
-    pairs = rng.integers(0, 2**32, (10001, 2), dtype=np.uint64).astype(np.uint32)
+    p = S.Params(seed=3 + offset)
+    rng = np.random.default_rng(3 + offset)
+    pairs = rng.integers(0, 2**32, (n, 2), dtype=np.uint64).astype(np.uint32)
     pairs[:, 0] = pairs[:, 0] % 50
-    buf = helpers.to_device(np.concatenate([np.zeros((1, 2), np.uint32), pairs]))
+    buf = helpers.to_device(np.concatenate([np.zeros((offset, 2), np.uint32), pairs]))
+    assert buf.data_ptr() % 128 == 0
     est = S.Estimator(p)
-    est.update(buf[1:])
+    est.set_update_mode(mode)
+    est.update(buf[offset:])
     orc = oracle.Oracle(oracle_params(p))
     orc.scan(pairs)
     compare_state(est, orc, p, 0)

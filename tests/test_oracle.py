@@ -666,3 +666,53 @@ def test_tabulation_rhfg0_structure_and_tables():
         he0 = o.rhfg0(int(x))
         for i in range(1, p.r):
             assert o.rhfg(i, int(x)) ^ he0 == (int(x) >> (i * o.delta)) & ((1 << p.q) - 1)
+
+
+# ---------------------------------------------------------------- sanitizer build
+
+SANITIZED_RUN = r"""
+import numpy as np
+import oracle
+from paper_1805_09246_b300 import synth
+tr = synth.Traffic(synth.small_trace(seed=3))
+p = oracle.Params(k=3, seed=3)
+a, b = oracle.Oracle(p, track_exact=True), oracle.Oracle(p)
+for t in range(4):
+    if t:
+        a.advance(); b.advance()
+    s = tr.slice(0, t)
+    a.scan(s[::2]); b.scan(s[1::2])
+a.merge([b])
+det = a.detect()
+assert len(det["hosts"]) > 0
+e = a.estimate(det["hosts"], hist=True)
+a.features(det["hosts"][:8]); a.sre_weights(det["hosts"][:8])
+a.exact_counts(det["hosts"]); a.exact_super()
+sre, sle = a.raw(); a.set_raw(sre, sle); a.canonical(); a.hot(); a.row_counts()
+t = oracle.Oracle(oracle.Params(q=10, delta=8, q2=6, eta2=64, delta2=8, k=2, theta=8, seed=4, rhfg_hash=1))
+few = tr.slice(0, 0)[:600].copy()
+few[:, 0] %= 11  # eleven hosts: a handful of hot SREs per row
+t.scan(few)
+assert len(t.detect()["hosts"]) > 0
+print("sanitized oracle ok", len(det["hosts"]))
+"""
+
+
+@pytest.mark.slow
+def test_oracle_under_address_and_undefined_behavior_sanitizers(tmp_path):
+    """The oracle built with -fsanitize=address,undefined (every report aborts) runs scan,
+    advance, merge, detection, estimation with histograms, exact counts, raw state and the
+    tabulation hash on a small trace in a child process."""
+    import os
+    import subprocess
+    import sys
+    lib = oracle.build(sanitize=True, out=str(tmp_path / "liborc_asan.so"))
+    asan = subprocess.run(["g++", "-print-file-name=libasan.so"], capture_output=True, text=True).stdout.strip()
+    ubsan = subprocess.run(["g++", "-print-file-name=libubsan.so"], capture_output=True, text=True).stdout.strip()
+    env = dict(os.environ, SSE_ORACLE_LIB=lib, LD_PRELOAD=f"{asan}:{ubsan}",
+               ASAN_OPTIONS="detect_leaks=0:abort_on_error=1", UBSAN_OPTIONS="print_stacktrace=1")
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run([sys.executable, "-c", SANITIZED_RUN], cwd=root, env=env, capture_output=True, text=True,
+                       timeout=600)
+    assert r.returncode == 0, r.stdout[-2000:] + r.stderr[-4000:]
+    assert "sanitized oracle ok" in r.stdout
