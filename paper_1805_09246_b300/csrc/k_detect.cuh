@@ -518,21 +518,25 @@ __global__ void __launch_bounds__(256) k_report(CloseScratch* __restrict__ sc, c
 // lane expands one: the hot SREs of the group come from the regrouped row-2 table, and each
 // chain must pass row 3's "any hot" bit before it is queued. Each warp works as a pipeline of
 // stages, all 32 lanes in every stage: expanded chains go to the warp's partial-chain queue;
-// whenever 32 wait, each lane grows one through rows 3 and 4 (warp-uniform loops over their
-// hot SREs) into the warp's complete-chain queue; whenever 32 of those wait, each lane
-// regains the hosts of one. So the divergent depth-first walk of a lone lane never runs, and
-// the regain search, the bulk of the work when hot SREs are common, runs on full warps. The
+// whenever 32 wait, each lane walks one chain's row-3 hot SREs (a warp-uniform loop) and
+// queues every B(3) whose row-4 group holds a hot SRE; whenever 32 of those wait, each lane
+// walks one's row-4 hot SREs into the warp's complete-chain queue; whenever 32 complete
+// chains wait, each lane regains the hosts of one. So the divergent depth-first walk of a lone
+// lane never runs, a loop waits only for the lane with the most hot SREs of one row, and
+// the regain search, a large part of the work when hot SREs are common, runs on full warps. The
 // two "any hot" bitmaps are staged in shared memory when `stage` is set; the blocks are small
 // (kJoinTiledThreads) so that several share an SM.
 constexpr int kJoinTiledThreads = 256;
 constexpr uint32_t kJoinWarpQueue = 64;    // entries of each per-warp chain queue (< 32 waiting + 32 pushed)
+constexpr uint32_t kJoinQueueWords = 9;    // words per entry over a warp's three queues (3 + 4 + 2)
 constexpr uint32_t kJoinChunkMax = 256;    // he_0 per work unit
 constexpr uint32_t kJoinProbeBlock = 16;   // he_0 probed before a compaction
 constexpr uint32_t kJoinListWords = (32 + 32 * kJoinProbeBlock) / 2;  // per warp hit stack: 16-bit entries
 // dynamic shared memory after the optional bitmaps: per-warp chain queues (partial: 3 words,
-// complete: 2 words per entry), he_0 chunk, K chunk, he_1, hit stacks
+// waiting for row 4: 4 words, complete: 2 words per entry), he_0 chunk, K chunk, he_1, hit
+// stacks
 constexpr size_t kJoinTiledFixedBytes =
-    ((kJoinTiledThreads / 32) * 5 * (size_t)kJoinWarpQueue + 2 * kJoinChunkMax + kJoinTiledThreads +
+    ((kJoinTiledThreads / 32) * kJoinQueueWords * (size_t)kJoinWarpQueue + 2 * kJoinChunkMax + kJoinTiledThreads +
      (kJoinTiledThreads / 32) * kJoinListWords) * 4;
 
 // Words of an "any hot" bitmap over the 2^(q-delta) values of c, and the shared-memory words
@@ -603,14 +607,19 @@ __global__ void __launch_bounds__(kJoinTiledThreads) k_join_tiled(
     if (any3) a3 = d3;
     next = d3 + any_words_staged(q, delta);
   }
-  // per-warp queues: partial chains (he_0, B(1), B(2)) and complete chains (he_0, address
-  // bits [delta, 32)), kJoinWarpQueue entries each
-  uint32_t* wq_he0 = next + warp * (5 * kJoinWarpQueue);
+  // per-warp queues of kJoinWarpQueue entries: partial chains (he_0, B(1), B(2)), chains
+  // waiting for row 4 (he_0, address bits so far, B(3), row 4's hot SREs) and complete
+  // chains (he_0, address bits [delta, 32))
+  uint32_t* wq_he0 = next + warp * (kJoinQueueWords * kJoinWarpQueue);
   uint32_t* wq_b1 = wq_he0 + kJoinWarpQueue;
   uint32_t* wq_b2 = wq_b1 + kJoinWarpQueue;
-  uint32_t* wc_he0 = wq_b2 + kJoinWarpQueue;
+  uint32_t* wf_he0 = wq_b2 + kJoinWarpQueue;
+  uint32_t* wf_high = wf_he0 + kJoinWarpQueue;
+  uint32_t* wf_b3 = wf_high + kJoinWarpQueue;
+  uint32_t* wf_m4 = wf_b3 + kJoinWarpQueue;
+  uint32_t* wc_he0 = wf_m4 + kJoinWarpQueue;
   uint32_t* wc_high = wc_he0 + kJoinWarpQueue;
-  uint32_t* s_he0 = next + (kJoinTiledThreads / 32) * (5 * kJoinWarpQueue);
+  uint32_t* s_he0 = next + (kJoinTiledThreads / 32) * (kJoinQueueWords * kJoinWarpQueue);
   uint32_t* s_k = s_he0 + kJoinChunkMax;
   uint32_t* s_he1 = s_k + kJoinChunkMax;
   uint16_t* my_list = reinterpret_cast<uint16_t*>(s_he1 + kJoinTiledThreads) + warp * (2 * kJoinListWords);
@@ -651,9 +660,48 @@ __global__ void __launch_bounds__(kJoinTiledThreads) k_join_tiled(
       regain_high(p, e0, eh, cand, n_cand, cap, overflow, rt);
     }
   };
-  // Rows 3 .. r-1 of a chain (Algorithm 5). For r = 5 the hot SREs of rows 3 and 4 are
-  // walked by warp-uniform loops and the complete chains queued for regain; other r grow
-  // their chains lane by lane (depth first, regaining inline).
+  // Row 4 (Algorithm 5, r = 5): one chain (he_0, address bits so far, B(3), row 4's hot
+  // SREs of its group) per lane; every hot SRE that keeps B(4) inside 32 address bits
+  // completes the chain.
+  auto grow4 = [&](bool ok, uint32_t he0, uint32_t high123, uint32_t b3, uint32_t m4) {
+    const uint32_t hi0 = he0 >> shift_hi;
+    if (!ok) m4 = 0;
+    while (__any_sync(0xFFFFFFFFu, m4 != 0u)) {
+      bool done = false;
+      uint32_t high = 0;
+      if (m4) {
+        const uint32_t b4 = (b3 >> delta) | (((uint32_t)(__ffs(m4) - 1) ^ hi0) << shift_hi);
+        m4 &= m4 - 1u;
+        // with B(4) inside 32 address bits (fits32), bits [delta, 32) hold the whole chain
+        done = fits32(4, delta, q, b4);
+        high = (uint32_t)((uint64_t)high123 | ((uint64_t)(b4 >> shift_hi) << (4 * delta + shift_hi)));
+      }
+      push_complete(done, he0, high);
+    }
+  };
+  uint32_t fn = 0;  // chains waiting for row 4 (the same in every lane)
+  auto push_four = [&](bool ok, uint32_t he0, uint32_t high123, uint32_t b3, uint32_t m4) {
+    const uint32_t b = __ballot_sync(0xFFFFFFFFu, ok);
+    if (ok) {
+      const uint32_t at = fn + __popc(b & lt_mask);
+      wf_he0[at] = he0;
+      wf_high[at] = high123;
+      wf_b3[at] = b3;
+      wf_m4[at] = m4;
+    }
+    fn += __popc(b);
+    if (fn >= 32) {
+      fn -= 32;
+      __syncwarp();
+      const uint32_t e0 = wf_he0[fn + lane], eh = wf_high[fn + lane], e3 = wf_b3[fn + lane], em = wf_m4[fn + lane];
+      __syncwarp();
+      grow4(true, e0, eh, e3, em);
+    }
+  };
+  // Rows 3 .. r-1 of a chain (Algorithm 5). For r = 5, row 3's hot SREs are walked one per
+  // lane and every B(3) whose row-4 group holds a hot SRE is queued for row 4, so that each
+  // stage loops over one row's hot SREs only; other r grow their chains lane by lane (depth
+  // first, regaining inline).
   auto grow = [&](bool ok, uint32_t he0, uint32_t b1, uint32_t b2) {
     if (p.r != 5) {
       if (ok) grow_chain(p, tables, he0, b1, b2, cand, n_cand, cap, overflow, rt);
@@ -669,19 +717,9 @@ __global__ void __launch_bounds__(kJoinTiledThreads) k_join_tiled(
         m3 &= m3 - 1u;
         if (fits32(3, delta, q, b3)) m4 = hot_group(tables + 2 * nwords, (he0 ^ (b3 >> delta)) & cmask, delta);
       }
-      const uint64_t high123 = high12 | ((uint64_t)(b3 >> shift_hi) << (3 * delta + shift_hi));
-      while (__any_sync(0xFFFFFFFFu, m4 != 0u)) {
-        bool done = false;
-        uint32_t high = 0;
-        if (m4) {
-          const uint32_t b4 = (b3 >> delta) | (((uint32_t)(__ffs(m4) - 1) ^ hi0) << shift_hi);
-          m4 &= m4 - 1u;
-          // with B(4) inside 32 address bits (fits32), bits [delta, 32) hold the whole chain
-          done = fits32(4, delta, q, b4);
-          high = (uint32_t)(high123 | ((uint64_t)(b4 >> shift_hi) << (4 * delta + shift_hi)));
-        }
-        push_complete(done, he0, high);
-      }
+      // with B(3) inside 32 address bits, so are the bits fixed so far
+      const uint32_t high123 = (uint32_t)(high12 | ((uint64_t)(b3 >> shift_hi) << (3 * delta + shift_hi)));
+      push_four(m4 != 0u, he0, high123, b3, m4);
     }
   };
   uint32_t pn = 0;  // partial chains queued (the same in every lane)
@@ -809,9 +847,13 @@ __global__ void __launch_bounds__(kJoinTiledThreads) k_join_tiled(
     hn = 0;
     __syncwarp();
   }
-  // the chains still queued: partial ones grown, then complete ones regained
+  // the chains still queued: partial ones grown, then those waiting for row 4, then the
+  // complete ones regained
   grow(lane < pn, wq_he0[lane], wq_b1[lane], wq_b2[lane]);
   pn = 0;
+  __syncwarp();
+  grow4(lane < fn, wf_he0[lane], wf_high[lane], wf_b3[lane], wf_m4[lane]);
+  fn = 0;
   __syncwarp();
   if (lane < cn) regain_high(p, wc_he0[lane], wc_high[lane], cand, n_cand, cap, overflow, rt);
 }
