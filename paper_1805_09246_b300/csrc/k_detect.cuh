@@ -35,6 +35,20 @@ __device__ __forceinline__ bool fits32(uint32_t i, uint32_t delta, uint32_t q, u
   return true;
 }
 
+// The top bits t of he_i (i >= 2) that keep B(i) inside 32 address bits, as a mask over
+// the 2^delta SREs of a row-i group: B(i)'s top delta bits, (t XOR hi0) with hi0 the top
+// delta bits of he_0, sit at address bits [i*delta + q - delta, i*delta + q), so only the
+// w = 32 - (i*delta + q - delta) low ones (0 <= w <= delta) may be set: t must agree with hi0
+// above bit w, 2^w consecutive values. (Its low q - delta bits come from B(i-1), which fits.)
+__device__ __forceinline__ uint32_t fits32_tops(uint32_t i, uint32_t delta, uint32_t q, uint32_t hi0) {
+  const int top = (int)(i * delta + q - delta);
+  const int w = 32 - top;
+  if (w >= (int)delta) return delta == 5 ? 0xFFFFFFFFu : (1u << (1u << delta)) - 1u;
+  if (w <= 0) return 1u << hi0;
+  const uint32_t base = (hi0 >> w) << w;
+  return ((1u << (1u << w)) - 1u) << base;
+}
+
 __device__ __forceinline__ void emit_candidate(uint32_t aip, uint32_t* cand, uint32_t* n_cand, uint32_t cap,
                                                uint32_t* overflow) {
   const uint32_t at = atomicAdd(n_cand, 1u);
@@ -51,16 +65,22 @@ __device__ __forceinline__ void emit_candidate(uint32_t aip, uint32_t* cand, uin
 struct RegainTable {
   uint64_t d[32];
   uint32_t low[32];
+  uint8_t first[65];  // entries below j * 2^58, j = 0..64 (regain_search_bucketed)
 };
 __device__ __forceinline__ void build_regain_table(const KParams& p, RegainTable* t) {
   const uint32_t n = 1u << p.delta;
+  const uint64_t a = p.key_a[kR0];
   if (threadIdx.x < n) {
-    const uint64_t a = p.key_a[kR0];
     const uint64_t d = a * threadIdx.x;
     uint32_t rank = 0;
     for (uint32_t j = 0; j < n; ++j) rank += (a * j < d) ? 1u : 0u;
     t->d[rank] = d;
     t->low[rank] = threadIdx.x;
+  }
+  if (threadIdx.x <= 64) {
+    uint32_t below = 0;
+    for (uint32_t j = 0; j < n; ++j) below += ((a * j) >> 58) < threadIdx.x ? 1u : 0u;
+    t->first[threadIdx.x] = (uint8_t)below;
   }
 }
 
@@ -87,8 +107,8 @@ __device__ __forceinline__ void regain_high(const KParams& p, uint32_t he0, uint
   const uint64_t width = 1ull << (64 - p.q);
   uint64_t v = a * (uint32_t)high + p.key_b[kR0] - ((uint64_t)he0 << (64 - p.q));
   if (rt) {
-    regain_search(rt->d, rt->low, 1u << p.delta, v, width,
-                  [&](uint32_t low) { emit_candidate((uint32_t)high | low, cand, n_cand, cap, overflow); });
+    regain_search_bucketed(rt->d, rt->low, rt->first, 1u << p.delta, v, width,
+                           [&](uint32_t low) { emit_candidate((uint32_t)high | low, cand, n_cand, cap, overflow); });
     return;
   }
   for (uint32_t low = 0; low < (1u << p.delta); ++low, v += a)
@@ -709,13 +729,16 @@ __global__ void __launch_bounds__(kJoinTiledThreads) k_join_tiled(
     }
     const uint32_t hi0 = he0 >> shift_hi;
     const uint64_t high12 = ((uint64_t)b1 << delta) | ((uint64_t)(b2 >> shift_hi) << (2 * delta + shift_hi));
-    uint32_t m3 = ok ? hot_group(tables + nwords, (he0 ^ (b2 >> delta)) & cmask, delta) : 0u;
+    uint32_t m3 = ok ? hot_group(tables + nwords, (he0 ^ (b2 >> delta)) & cmask, delta) & fits32_tops(3, delta, q, hi0)
+                     : 0u;
+    const uint32_t tops4 = fits32_tops(4, delta, q, hi0);
     while (__any_sync(0xFFFFFFFFu, m3 != 0u)) {
       uint32_t m4 = 0, b3 = 0;
       if (m3) {
         b3 = (b2 >> delta) | (((uint32_t)(__ffs(m3) - 1) ^ hi0) << shift_hi);
         m3 &= m3 - 1u;
-        if (fits32(3, delta, q, b3)) m4 = hot_group(tables + 2 * nwords, (he0 ^ (b3 >> delta)) & cmask, delta);
+        if (fits32(3, delta, q, b3))
+          m4 = hot_group(tables + 2 * nwords, (he0 ^ (b3 >> delta)) & cmask, delta) & tops4;
       }
       // with B(3) inside 32 address bits, so are the bits fixed so far
       const uint32_t high123 = (uint32_t)(high12 | ((uint64_t)(b3 >> shift_hi) << (3 * delta + shift_hi)));
@@ -752,7 +775,7 @@ __global__ void __launch_bounds__(kJoinTiledThreads) k_join_tiled(
     const uint32_t hi0 = he0 >> shift_hi;
     if (ok && fits32(1, delta, q, b1)) {
       const uint32_t first = ((he0 ^ low2) & cmask) << delta;  // row-2 group of c
-      m = (tables[first >> 5] >> (first & 31)) & span_mask;
+      m = (tables[first >> 5] >> (first & 31)) & span_mask & fits32_tops(2, delta, q, hi0);
     }
     while (__any_sync(0xFFFFFFFFu, m != 0u)) {
       bool keep = false;
@@ -1052,7 +1075,7 @@ __global__ void __launch_bounds__(kEstThreads, 4) k_estimate(
   // `hosts` is already sorted and the outputs go to the host's own index
   const bool rank_mode = unsorted != nullptr && count <= kSortChunk && hist == nullptr;
   const bool vec16 = (p.delta2 & 15u) == 0;
-  const bool u_only = sizeof(St) == 1 && vec16 && !hist;  // U from byte-wise activity masks
+  const bool u_only = vec16 && !hist;  // U from byte-wise or half-word-wise activity masks
   if (sizeof(St) == 1 && !u_only)
     for (uint32_t s = threadIdx.x; s < 256; s += blockDim.x) {
       const uint32_t a = stamp_age(s, cs);
@@ -1110,14 +1133,21 @@ __global__ void __launch_bounds__(kEstThreads, 4) k_estimate(
     constexpr int kIntCells = 4 / sizeof(St);
     constexpr uint32_t kMask = sizeof(St) == 1 ? 0xFFu : 0xFFFFu;
     if (u_only) {
-      // U only: a union cell counts when it is active in every row, so the rows' byte-wise
-      // activity masks (active_hi8) are ANDed; up to 8 rows' loads are in flight at once
-      const Window8 win = window8(cs, p.k);
-      auto rows_and = [&](auto wrap) {  // wrap: std::true_type when the window wraps over 0
+      // U only: a union cell counts when it is active in every row, so the rows' activity
+      // masks (active_hi8 for 8-bit cells, active_hi16 for 16-bit ones: the top bit of every
+      // active cell) are ANDed; up to 8 rows' loads are in flight at once
+      constexpr uint32_t kAll = sizeof(St) == 1 ? 0x80808080u : 0x80008000u;
+      auto rows_and = [&](auto wrap, auto win) {  // wrap: std::true_type when the window wraps over 0
         constexpr bool W = decltype(wrap)::value;
+        auto active = [&](uint32_t x) {
+          if constexpr (sizeof(St) == 1)
+            return active_hi8<W>(x, win);
+          else
+            return active_hi16<W>(x, win);
+        };
         uint32_t c = 0;
-        for (uint32_t z = threadIdx.x * 16; z < p.eta2; z += blockDim.x * 16) {
-          uint32_t a0 = 0x80808080u, a1 = a0, a2 = a0, a3 = a0;
+        for (uint32_t z = threadIdx.x * kVecCells; z < p.eta2; z += blockDim.x * kVecCells) {
+          uint32_t a0 = kAll, a1 = a0, a2 = a0, a3 = a0;
           for (uint32_t i0 = 0; i0 < p.r2; i0 += 8) {
             uint4 v[8];
 #pragma unroll
@@ -1126,17 +1156,23 @@ __global__ void __launch_bounds__(kEstThreads, 4) k_estimate(
 #pragma unroll
             for (uint32_t j = 0; j < 8; ++j)
               if (i0 + j < p.r2) {
-                a0 &= active_hi8<W>(v[j].x, win);
-                a1 &= active_hi8<W>(v[j].y, win);
-                a2 &= active_hi8<W>(v[j].z, win);
-                a3 &= active_hi8<W>(v[j].w, win);
+                a0 &= active(v[j].x);
+                a1 &= active(v[j].y);
+                a2 &= active(v[j].z);
+                a3 &= active(v[j].w);
               }
           }
           c += __popc(a0) + __popc(a1) + __popc(a2) + __popc(a3);
         }
         return c;
       };
-      u = win.wrap ? rows_and(std::true_type{}) : rows_and(std::false_type{});
+      if constexpr (sizeof(St) == 1) {
+        const Window8 win = window8(cs, p.k);
+        u = win.wrap ? rows_and(std::true_type{}, win) : rows_and(std::false_type{}, win);
+      } else {
+        const Window16 win = window16(cs, p.k);
+        u = win.wrap ? rows_and(std::true_type{}, win) : rows_and(std::false_type{}, win);
+      }
     } else if (vec16) {
       for (uint32_t z = threadIdx.x * kVecCells; z < p.eta2; z += blockDim.x * kVecCells) {
         uint32_t m[kVecCells];

@@ -69,6 +69,23 @@ __host__ __device__ __forceinline__ void regain_search(const uint64_t* d, const 
   }
 }
 
+// regain_search with the binary search replaced by a bucket lookup: first[j] (j = 0..64) is
+// the number of table entries below j * 2^58, so the entries below the interval's start s are
+// first[s >> 58] plus those of s's bucket below s (about n / 64 of them: a few at most).
+template <typename Emit>
+__host__ __device__ __forceinline__ void regain_search_bucketed(const uint64_t* d, const uint32_t* low,
+                                                                const uint8_t* first, uint32_t n, uint64_t v,
+                                                                uint64_t width, Emit emit) {
+  const uint64_t s = 0ull - v;  // the interval's start
+  uint32_t at = first[s >> 58];
+  while (at < n && d[at] < s) ++at;
+  for (uint32_t k = 0; k < n; ++k) {
+    const uint32_t i = (at + k) & (n - 1u);
+    if (d[i] + v >= width) break;
+    emit(low[i]);
+  }
+}
+
 // Cyclic stamp arithmetic: slice t has stamp 1 + (t mod 255); 0 marks an unset cell.
 __host__ __device__ __forceinline__ uint8_t stamp_of(uint64_t slice) { return (uint8_t)(1 + slice % 255); }
 
@@ -115,6 +132,35 @@ __host__ __device__ __forceinline__ uint32_t active_hi8(uint32_t w, Window8 win)
 }
 __host__ __device__ __forceinline__ uint32_t active_hi8(uint32_t w, Window8 win) {
   return win.wrap ? active_hi8<true>(w, win) : active_hi8<false>(w, win);
+}
+
+// The same test for two 16-bit stamps in a 32-bit word (cycle 1..65535, windows k <= 65534):
+// the active stamps form the cyclic interval from L = cs - k + 1 (mod 65535, in 1..65535) to
+// cs; with K = k when cs >= k and L = cs + 65536 - k, K = k + 1 otherwise (the interval then
+// wraps over 0, which s != 0 removes), s is active exactly when s != 0 and
+// (s - L) mod 65536 < K. Returns 0x8000 in every active half, 0 elsewhere.
+struct Window16 {
+  uint32_t L2;    // L in both halves
+  uint32_t C2;    // 65536 - K in both halves
+  uint32_t wrap;  // cs < k
+};
+__host__ __device__ __forceinline__ Window16 window16(uint32_t cs, uint32_t k) {
+  const uint32_t L = cs >= k ? cs - k + 1 : cs + 65536 - k;
+  const uint32_t K = cs >= k ? k : k + 1;
+  return Window16{(L & 0xFFFFu) * 0x00010001u, (65536u - K) * 0x00010001u, cs < k ? 1u : 0u};
+}
+template <bool WRAP>
+__host__ __device__ __forceinline__ uint32_t active_hi16(uint32_t w, Window16 win) {
+  constexpr uint32_t H = 0x80008000u, Lo = 0x7FFF7FFFu;
+  const uint32_t t = ((w | H) - (win.L2 & Lo)) ^ ((w ^ ~win.L2) & H);  // (s - L) mod 65536 per half
+  const uint32_t low = (t & Lo) + (win.C2 & Lo);                       // carry into bit 15
+  const uint32_t carry = (t & win.C2) | ((t | win.C2) & low);           // bit 15: t + C >= 65536
+  if (!WRAP) return ~carry & H;
+  const uint32_t nz = ((w & Lo) + Lo) | w;  // bit 15: s != 0
+  return ~carry & nz & H;
+}
+__host__ __device__ __forceinline__ uint32_t active_hi16(uint32_t w, Window16 win) {
+  return win.wrap ? active_hi16<true>(w, win) : active_hi16<false>(w, win);
 }
 
 // The estimator's device clock holds the current stamp; advancing a slice moves it along the

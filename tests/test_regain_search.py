@@ -1,5 +1,5 @@
-"""Host-side check of the search that regain uses in the join (regain_search in
-csrc/sse_internal.cuh): for a complete chain, the low address bits whose multiply-add-shift
+"""Host-side check of the searches that regain uses in the join (regain_search and
+regain_search_bucketed in csrc/sse_internal.cuh): for a complete chain, the low address bits whose multiply-add-shift
 RHFG[0] value lands on he_0 are those low < 2^delta with (v + a*low) mod 2^64 below
 2^(64-q). The search over the sorted a*low table is compared, case by case, with the plain
 loop over every low: random multipliers and offsets, offsets placed just inside and just
@@ -54,8 +54,20 @@ int main() {
             if (got & (1u << low)) ++bad;  // each low once
             got |= 1u << low;
           });
+          // the bucketed search: entries below each 2^58-wide bucket
+          uint8_t first[65];
+          for (uint32_t j = 0; j <= 64; ++j) {
+            uint32_t below = 0;
+            for (uint32_t i = 0; i < n; ++i) below += (d[i] >> 58) < j ? 1u : 0u;
+            first[j] = (uint8_t)below;
+          }
+          uint32_t got2 = 0;
+          regain_search_bucketed(d, lows, first, n, v, width, [&](uint32_t low) {
+            if (got2 & (1u << low)) ++bad;
+            got2 |= 1u << low;
+          });
           ++checked;
-          if (got != want) ++bad;
+          if (got != want || got2 != want) ++bad;
           if (want) ++hits;
         }
       }
