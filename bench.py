@@ -34,6 +34,8 @@ PAIRS_PER_SLICE = 1 << 25
 PREFILL = 8          # slices scanned before warm-up so that the window is full
 DISTINCT = 16        # device-resident slices the warm-up and timed steps cycle through
 PAIR_BYTES = 8
+CORE_LINK_WORKLOAD = ("core_link: 2^25 pairs/slice, 16M-host Zipf(1.05), 200 planted super points; "
+                      "q=20, r=5, SLEA r'=5 x (2^16 SLEs, eta'=4096, delta'=16), k=8, theta=1024")
 TILED8_DRAM_BYTES = 273_630_720 + 7_365_632
 
 
@@ -204,8 +206,9 @@ def run_reference(args, rank, world):
         "impl": "reference", "metric": METRIC, "value": round(value, 6), "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt / args.steps * 1e3, 3),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
-        "config": {"workload": "core_link: 2^25 pairs/slice, q=20, SLEA 2^16x2^12, k=8, theta=1024",
-                   "sample_pairs_per_step": sample},
+        "config": {"workload": CORE_LINK_WORKLOAD, "pairs_per_step": PAIRS_PER_SLICE,
+                   "l2": "inputs larger than L2 (256 MiB per step)"},
+        "sample_pairs_per_step": sample,
         "cpu_baseline": {"value": round(value, 6), "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc},
         "e2e": {"value": round(value, 6), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
@@ -756,9 +759,7 @@ def main():
         "config": {"workload": ("paper_params: core-link traffic cut to 2^21 pairs/slice (16M-host Zipf(1.05)); the paper's "
                                 "estimator q=17, r=5, delta=5, SLEA r'=5 x (2^17 SLEs, eta'=2^14, delta'=16), "
                                 "16-bit stamps, k=300, theta=1024")
-                               if paper else
-                               "core_link: 2^25 pairs/slice, 16M-host Zipf(1.05), 200 planted super points; "
-                               "q=20, r=5, SLEA r'=5 x (2^16 SLEs, eta'=4096, delta'=16), k=8, theta=1024",
+                               if paper else CORE_LINK_WORKLOAD,
                    "pairs_per_step": n_slice,
                    "l2": ("16 distinct 16 MiB slices cycled (256 MiB): a step's input was evicted since its last use"
                           if paper else "inputs larger than L2 (256 MiB per step)"),
