@@ -36,7 +36,7 @@ DISTINCT = 16        # device-resident slices the warm-up and timed steps cycle 
 PAIR_BYTES = 8
 CORE_LINK_WORKLOAD = ("core_link: 2^25 pairs/slice, 16M-host Zipf(1.05), 200 planted super points; "
                       "q=20, r=5, SLEA r'=5 x (2^16 SLEs, eta'=4096, delta'=16), k=8, theta=1024")
-TILED8_DRAM_BYTES = 273_630_720 + 7_365_632
+TILED8_DRAM_BYTES = 273_558_784 + 7_141_376
 
 
 def parse(argv=None):
@@ -630,6 +630,7 @@ def main():
         n_super += rep.n_super
         n_cand += rep.n_candidates
     ev_end.record(stream)
+    last_rep = rep
     torch.cuda.synchronize()
     barrier(pg)
     clk = clocks.stop()
@@ -707,7 +708,7 @@ def main():
 
     hbm_peak, peak_kind = peaks()
     achieved = n_slice * PAIR_BYTES / (upd_ms / 1e3) / 1e9
-    # DRAM bytes (read + write) of one k_update_tiled<8, 0, 1> launch on this slice, from an ncu
+    # DRAM bytes (read + write) of one k_update_tiled<8, 0, 1, 0> launch on this slice, from an ncu
     # capture of this kernel version (dram__bytes_read.sum + dram__bytes_write.sum); only
     # reported when that variant is the one timed
     traffic = TILED8_DRAM_BYTES if tuned == 3 and not paper else None
@@ -774,7 +775,10 @@ def main():
         "close_samples": len(close_ms),
         "candidates_per_slice": round(n_cand / args.steps, 1), "super_per_slice": round(n_super / args.steps, 1),
         "last_slice": {"hot_sre_per_row": slice_stats["hot"], "join_pairs": slice_stats["join_pairs"],
-                       "sf": [round(c / est.derived["row_len2"], 4) for c in slice_stats["active2"]]},
+                       "sf": [round(c / est.derived["row_len2"], 4) for c in slice_stats["active2"]],
+                       # candidates whose corrected weight hit Eq. 12's saturation clamp
+                       "saturated": int(np.count_nonzero(last_rep.flags & sse.FLAG_SATURATED)),
+                       "candidates": int(last_rep.n_candidates)},
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
         "clocks": clk,
     }
