@@ -726,6 +726,10 @@ def main():
                 "l1tex_note": (f"update rate x ({params.r2} / measured random shared-memory atomics/s + "
                                f"{params.r2} x 8 B / measured L2 streaming-load B/s): share of the SM load pipe's "
                                "time the tiled design's algorithmic work takes"),
+                "update_vs_skeleton": round(upd_pps / mb["tiled_skeleton_pairs_per_s"], 4),
+                "skeleton_note": ("update rate / the rate of the tiled update's skeleton (same grid, loads and "
+                                  "one shared atomic per pair and row, no hashing or sampling): the share of "
+                                  "this design's measured floor that the update reaches"),
                 "microbench": {k: (round(v / 1e9, 2) if isinstance(v, float) else v) for k, v in mb.items()},
                 "microbench_unit": "G per second (stores, atomics) and GB/s (loads)"}
 

@@ -36,12 +36,17 @@ typedef struct sse_microbench_result {
   double l2_stream_load_bytes_per_s;
   /* the same loads over the whole buffer (>= 1 GiB, from HBM), bytes per second */
   double hbm_stream_load_bytes_per_s;
+  /* the tiled update's skeleton, pairs per second: 2^25 pairs streamed from HBM by groups of
+   * 5 CTAs (one per SLEA row, a 128.5 KiB bitmap each, one CTA per SM), each CTA loading
+   * every pair of its group and setting one pseudo-random bit per pair with a shared atomic
+   * OR; the method's hashing and sampling left out. The floor of the update's design. */
+  double tiled_skeleton_pairs_per_s;
   uint32_t sms;  /* streaming multiprocessors of the device */
   uint32_t reserved;
 } sse_microbench_result;
 
 /*
- * Runs the four measurements on cuda_stream (each the best of three timed launches after
+ * Runs the five measurements on cuda_stream (each the best of three timed launches after
  * one untimed launch; about 0.1 s in all) and fills *out. d_buf: caller-owned device
  * scratch of buf_bytes >= kSseMicrobenchMinBytes, 256-byte aligned; its contents are
  * overwritten. Blocks until done. Errors: INVALID_PARAM, CUDA.

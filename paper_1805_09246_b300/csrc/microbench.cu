@@ -104,6 +104,62 @@ __global__ void __launch_bounds__(1024) k_mb_stream_loads(const uint4* __restric
   if (acc == 0x9E3779B9u) sink[0] = acc;  // keeps the loads; practically never taken
 }
 
+// Pseudo-random 32-bit words over n_vec 16-byte vectors (the skeleton's pairs).
+__global__ void __launch_bounds__(256) k_mb_fill(uint4* __restrict__ dst, uint32_t n_vec) {
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n_vec; i += gridDim.x * blockDim.x)
+    dst[i] = make_uint4(mb_mix(4 * i), mb_mix(4 * i + 1), mb_mix(4 * i + 2), mb_mix(4 * i + 3));
+}
+
+constexpr int kSkelThreads = 1024;
+constexpr int kSkelUnroll = 8;
+constexpr uint32_t kSkelRows = 5;
+
+// The tiled update's skeleton: the same grid (groups of kSkelRows CTAs, one bitmap of
+// `words` 32-bit words per CTA, one CTA per SM), the same aligned 128-bit pair loads and one
+// shared atomic OR per pair and CTA at a pseudo-random cell; no hashing of the method, no
+// sampling, no flush. Its rate is the floor of the update's design on this device.
+__global__ void __launch_bounds__(kSkelThreads, 1) k_mb_tiled_skeleton(const uint4* __restrict__ vec, uint32_t nvec,
+                                                                       uint32_t words, uint32_t groups,
+                                                                       uint32_t* __restrict__ sink) {
+  extern __shared__ uint32_t bm[];
+  for (uint32_t w = threadIdx.x; w < words; w += blockDim.x) bm[w] = 0;
+  __syncthreads();
+  const uint32_t row = blockIdx.x % kSkelRows, group = blockIdx.x / kSkelRows;
+  const uint32_t cells = words * 32u;
+  const uint32_t key = 0x9E3779B9u * (row + 1u);
+  // this group's vectors, in whole 8-vector (128-byte) lines
+  const uint32_t lines = nvec >> 3;
+  const uint32_t begin = 8u * (uint32_t)((uint64_t)lines * group / groups);
+  const uint32_t end = 8u * (uint32_t)((uint64_t)lines * (group + 1) / groups);
+  uint64_t policy;
+  asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(policy));
+  auto touch = [&](uint32_t a, uint32_t b) {
+    const uint32_t cell = __umulhi((a * key) ^ (b + key), cells);
+    atomicOr(&bm[cell >> 5], 1u << (cell & 31u));
+  };
+  const uint32_t stride = blockDim.x;
+  uint32_t i = begin + threadIdx.x;
+  for (; i + (kSkelUnroll - 1) * stride < end; i += kSkelUnroll * stride) {
+    uint4 v[kSkelUnroll];
+#pragma unroll
+    for (int u = 0; u < kSkelUnroll; ++u) v[u] = mb_load_stream(vec + i + u * stride, policy);
+#pragma unroll
+    for (int u = 0; u < kSkelUnroll; ++u) {
+      touch(v[u].x, v[u].y);
+      touch(v[u].z, v[u].w);
+    }
+  }
+  for (; i < end; i += stride) {
+    const uint4 v = mb_load_stream(vec + i, policy);
+    touch(v.x, v.y);
+    touch(v.z, v.w);
+  }
+  __syncthreads();
+  uint32_t acc = 0;
+  for (uint32_t w = threadIdx.x; w < words; w += blockDim.x) acc |= bm[w];
+  if (acc == 0x12345678u) sink[blockIdx.x] = acc;  // keeps the atomics; practically never taken
+}
+
 struct EventPair {
   cudaEvent_t a = nullptr, b = nullptr;
   bool ok = false;
@@ -190,5 +246,22 @@ extern "C" int sse_microbench(void* d_buf, uint64_t buf_bytes, void* cuda_stream
   });
   if (ms_hbm <= 0.0f) return SSE_ERR_CUDA;
   out->hbm_stream_load_bytes_per_s = (double)hbm_vec * 16 / (ms_hbm * 1e-3);
+
+  // 4. the tiled update's skeleton over 2^25 pseudo-random pairs (the first 256 MiB of the
+  // buffer, written first; more than L2 holds, so each launch streams them from HBM)
+  const uint32_t skel_vec = (1u << 25) / 2;
+  const uint32_t skel_groups = (uint32_t)sms / kSkelRows;
+  if (cudaFuncSetAttribute(k_mb_tiled_skeleton, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(words * 4u)) !=
+      cudaSuccess) {
+    cudaGetLastError();
+    return SSE_ERR_CUDA;
+  }
+  k_mb_fill<<<(unsigned)sms * 8, 256, 0, stream>>>(reinterpret_cast<uint4*>(buf), skel_vec);
+  const float ms_sk = best_ms(stream, 3, [&] {
+    k_mb_tiled_skeleton<<<skel_groups * kSkelRows, kSkelThreads, words * 4u, stream>>>(
+        reinterpret_cast<const uint4*>(buf), skel_vec, words, skel_groups, sink);
+  });
+  if (ms_sk <= 0.0f) return SSE_ERR_CUDA;
+  out->tiled_skeleton_pairs_per_s = (double)skel_vec * 2 / (ms_sk * 1e-3);
   return SSE_OK;
 }

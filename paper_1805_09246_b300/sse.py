@@ -200,7 +200,8 @@ def lib() -> ctypes.CDLL:
 class _MicrobenchResult(ctypes.Structure):
     _fields_ = [("l2_random_byte_stores_per_s", ctypes.c_double), ("smem_random_atomics_per_s", ctypes.c_double),
                 ("l2_stream_load_bytes_per_s", ctypes.c_double), ("hbm_stream_load_bytes_per_s", ctypes.c_double),
-                ("sms", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+                ("tiled_skeleton_pairs_per_s", ctypes.c_double), ("sms", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32)]
 
 
 MICROBENCH_MIN_BYTES = (1 << 30) + 4096
@@ -209,7 +210,7 @@ MICROBENCH_MIN_BYTES = (1 << 30) + 4096
 def microbench(stream=None) -> dict:
     """Peak rates of the update's memory units on the current device (sse_microbench): random
     one-byte L2 stores/s, random shared-memory atomic ORs/s, streaming 128-bit load bytes/s
-    from L2 and from HBM."""
+    from L2 and from HBM, and the tiled update's skeleton in pairs/s."""
     torch = _torch()
     buf = torch.empty(MICROBENCH_MIN_BYTES, dtype=torch.uint8, device="cuda")
     st = stream if stream is not None else torch.cuda.current_stream()
