@@ -38,16 +38,20 @@ __global__ void k_swap_pairs(const uint2* __restrict__ in, uint2* __restrict__ o
 // Stamps are cells of type St (uint8_t or uint16_t); kernels take byte pointers to the
 // estimator and address it in cells.
 
-// Algorithm 6 for one pair: in every row i of SLEA, cell H3(bip) of SLE LH_i(aip).
+// Algorithm 6 for one pair: in every row i of SLEA, cell H3(bip) of SLE LH_i(aip); into a
+// second SLEA as well when sle2 is set (a serving router's global estimator).
 template <typename St, int R2>
-__device__ __forceinline__ void stamp_slea(const KParams& p, uint32_t aip, uint32_t bip, St* sle, St stamp) {
+__device__ __forceinline__ void stamp_slea(const KParams& p, uint32_t aip, uint32_t bip, St* sle, St stamp,
+                                           St* sle2 = nullptr) {
   const uint32_t h3 = mas_top(p.key_a[kH3], p.key_b[kH3], bip, p.lg_eta2);
   const uint32_t rows = R2 > 0 ? (uint32_t)R2 : p.r2;
 #pragma unroll
   for (uint32_t i = 0; i < (R2 > 0 ? (uint32_t)R2 : (uint32_t)kMaxRows); ++i) {
     if (R2 == 0 && i >= rows) break;
     const uint32_t j = mas_top(p.key_a[kLH + i], p.key_b[kLH + i], aip, p.q2);
-    sle[i * p.row_pitch2 + (uint64_t)j * p.delta2 + h3] = stamp;
+    const uint64_t at = i * p.row_pitch2 + (uint64_t)j * p.delta2 + h3;
+    sle[at] = stamp;
+    if (sle2) sle2[at] = stamp;
   }
 }
 
@@ -128,22 +132,26 @@ struct RsraQueue {
 
 template <typename St, int R2>
 __device__ __forceinline__ void apply_pair(const KParams& p, uint32_t aip, uint32_t bip, St* sre, St* sle,
-                                           St stamp) {
-  stamp_slea<St, R2>(p, aip, bip, sle, stamp);
-  stamp_rsra(p, aip, bip, sre, stamp);
+                                           St stamp, St* sre2, St* sle2) {
+  stamp_slea<St, R2>(p, aip, bip, sle, stamp, sle2);
+  stamp_rsra(p, aip, bip, sre, stamp, sre2);
 }
 
 // pairs: 8-byte aligned {src, dst} pairs. UNROLL 128-bit loads are in flight per thread.
 // The stamp is read from the estimator's device clock when `clock` is set, so a captured
-// CUDA graph replays correctly in later slices.
+// CUDA graph replays correctly in later slices. sre2_bytes / sle2_bytes (may be NULL): a
+// second estimator that receives the same stamps (a serving router's global estimator).
 template <typename St, int R2, int UNROLL>
 __global__ void __launch_bounds__(256) k_update_direct(const __grid_constant__ KParams p,
                                                        const uint2* __restrict__ pairs, uint64_t n,
                                                        uint8_t* __restrict__ sre_bytes, uint8_t* __restrict__ sle_bytes,
-                                                       uint32_t stamp_value, const uint32_t* __restrict__ clock) {
+                                                       uint32_t stamp_value, const uint32_t* __restrict__ clock,
+                                                       uint8_t* __restrict__ sre2_bytes, uint8_t* __restrict__ sle2_bytes) {
   const St stamp = (St)(clock ? *clock : stamp_value);
   St* sre = reinterpret_cast<St*>(sre_bytes);
   St* sle = reinterpret_cast<St*>(sle_bytes);
+  St* sre2 = reinterpret_cast<St*>(sre2_bytes);
+  St* sle2 = reinterpret_cast<St*>(sle2_bytes);
   const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   const uint2* base = pairs;
@@ -151,7 +159,7 @@ __global__ void __launch_bounds__(256) k_update_direct(const __grid_constant__ K
   if ((reinterpret_cast<uintptr_t>(base) & 15u) != 0 && cnt > 0) {  // peel one pair to reach 16 B
     if (tid == 0) {
       uint2 v = base[0];
-      apply_pair<St, R2>(p, v.x, v.y, sre, sle, stamp);
+      apply_pair<St, R2>(p, v.x, v.y, sre, sle, stamp, sre2, sle2);
     }
     base += 1;
     cnt -= 1;
@@ -169,14 +177,14 @@ __global__ void __launch_bounds__(256) k_update_direct(const __grid_constant__ K
     for (int u = 0; u < UNROLL; ++u) {
       const uint64_t i = i0 + (uint64_t)u * stride;
       if (i < nvec) {
-        apply_pair<St, R2>(p, buf[u].x, buf[u].y, sre, sle, stamp);
-        apply_pair<St, R2>(p, buf[u].z, buf[u].w, sre, sle, stamp);
+        apply_pair<St, R2>(p, buf[u].x, buf[u].y, sre, sle, stamp, sre2, sle2);
+        apply_pair<St, R2>(p, buf[u].z, buf[u].w, sre, sle, stamp, sre2, sle2);
       }
     }
   }
   if ((cnt & 1) && tid == 0) {
     uint2 v = base[cnt - 1];
-    apply_pair<St, R2>(p, v.x, v.y, sre, sle, stamp);
+    apply_pair<St, R2>(p, v.x, v.y, sre, sle, stamp, sre2, sle2);
   }
 }
 

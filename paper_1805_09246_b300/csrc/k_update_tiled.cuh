@@ -103,9 +103,12 @@ __global__ void __launch_bounds__(kTiledThreads, 1) k_update_tiled(const __grid_
                                                                    const uint2* __restrict__ pairs, uint64_t n,
                                                                    uint8_t* __restrict__ sre_bytes,
                                                                    uint32_t* __restrict__ gbits, uint32_t stamp_value,
-                                                                   const uint32_t* __restrict__ clock) {
+                                                                   const uint32_t* __restrict__ clock,
+                                                                   uint8_t* __restrict__ sre2_bytes,
+                                                                   uint32_t* __restrict__ gbits2) {
   const St stamp = (St)(clock ? *clock : stamp_value);
   St* sre = reinterpret_cast<St*>(sre_bytes);
+  St* sre2 = reinterpret_cast<St*>(sre2_bytes);  // may be NULL: see the flush
   extern __shared__ __align__(16) uint32_t bm[];
   const uint32_t tile = blockIdx.x % g.tiles;
   const uint32_t group = blockIdx.x / g.tiles;
@@ -131,7 +134,7 @@ __global__ void __launch_bounds__(kTiledThreads, 1) k_update_tiled(const __grid_
   if (group == 0 && threadIdx.x < head) {
     const uint2 v = pairs[threadIdx.x];
     touch(v.x, v.y);
-    if (tile == 0) stamp_rsra(p, v.x, v.y, sre, stamp);
+    if (tile == 0) stamp_rsra(p, v.x, v.y, sre, stamp, sre2);
   }
   const uint64_t j0 = begin;
   const uint4* vec = reinterpret_cast<const uint4*>(pairs + j0);
@@ -153,8 +156,8 @@ __global__ void __launch_bounds__(kTiledThreads, 1) k_update_tiled(const __grid_
     if (owner == tile && p.sre_on) {
 #pragma unroll
       for (int u = 0; u < UNROLL; ++u) {
-        rq.push(p, true, buf[u].x, buf[u].y, sre, stamp);
-        rq.push(p, true, buf[u].z, buf[u].w, sre, stamp);
+        rq.push(p, true, buf[u].x, buf[u].y, sre, stamp, sre2);
+        rq.push(p, true, buf[u].z, buf[u].w, sre, stamp, sre2);
       }
     }
     owner = owner + 1 == g.tiles ? 0 : owner + 1;
@@ -198,24 +201,29 @@ __global__ void __launch_bounds__(kTiledThreads, 1) k_update_tiled(const __grid_
       touch(v.z, v.w);
     }
     if (mine) {
-      rq.push(p, ok, v.x, v.y, sre, stamp);
-      rq.push(p, ok, v.z, v.w, sre, stamp);
+      rq.push(p, ok, v.x, v.y, sre, stamp, sre2);
+      rq.push(p, ok, v.z, v.w, sre, stamp, sre2);
     }
   }
-  if (p.sre_on) rq.drain(p, sre, stamp);
+  if (p.sre_on) rq.drain(p, sre, stamp, sre2);
   if (((end - j0) & 1) && threadIdx.x == 0) {
     const uint2 v = pairs[end - 1];
     touch(v.x, v.y);
-    if (tile == 0) stamp_rsra(p, v.x, v.y, sre, stamp);
+    if (tile == 0) stamp_rsra(p, v.x, v.y, sre, stamp, sre2);
   }
   // flush: OR the piece's bitmap into the global SLEA bitmap (bitmap_or_bulk). Byte offsets
   // are cells / 8: the row pitch is a multiple of 4096 cells, a piece and its start
   // multiples of 1024, so both ends are 16-byte aligned.
+  // With gbits2 (a second estimator's SLEA bitmap, e.g. a serving router's global
+  // estimator: sre2 above received the RSRA stamps) the piece is ORed into both.
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   __syncthreads();
-  if (threadIdx.x == 0)
-    bitmap_or_bulk(bm, reinterpret_cast<uint8_t*>(gbits) + (((uint64_t)row * p.row_pitch2 + lo) >> 3),
-                   tile_flush_bytes(p.row_pitch2, lo, g.piece_bytes), true);
+  if (threadIdx.x == 0) {
+    const uint64_t at = ((uint64_t)row * p.row_pitch2 + lo) >> 3;
+    const uint32_t bytes = tile_flush_bytes(p.row_pitch2, lo, g.piece_bytes);
+    if (gbits2) bitmap_or_bulk(bm, reinterpret_cast<uint8_t*>(gbits2) + at, bytes, false);
+    bitmap_or_bulk(bm, reinterpret_cast<uint8_t*>(gbits) + at, bytes, true);
+  }
 }
 
 // Stamp every SLEA cell whose bit is set and clear the bitmap. One thread per bitmap word

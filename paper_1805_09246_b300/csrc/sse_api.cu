@@ -119,6 +119,12 @@ struct sse_handle {
   uint8_t* state = nullptr;  // RSRA then SLEA
   uint32_t* clock = nullptr; // device copy of the current stamp, 1 + (slice mod 255)
   uint32_t* sort_ctl = nullptr;  // in the clock's allocation: the sort barrier's controls (k_sort_candidates)
+  // A second estimator that receives every write of this one's updates (a serving router's
+  // global estimator, not owned): its RSRA and SLEA get the same stamps, directly or through
+  // its SLEA bitmap (applied when it closes the slice).
+  uint8_t* mirror_sre = nullptr;
+  uint8_t* mirror_sle = nullptr;
+  uint32_t* mirror_bits = nullptr;
   uint8_t* sre = nullptr;
   uint8_t* sle = nullptr;
   uint32_t* hot_bits = nullptr;
@@ -251,7 +257,7 @@ int launch_update_direct(sse_handle* h, const uint32_t* d_pairs, uint64_t n) {
   const uint2* pairs = reinterpret_cast<const uint2*>(d_pairs);
   const auto fn = h->wide ? (h->p.r2 == 5 ? k_update_direct<uint16_t, 5, kUnroll> : k_update_direct<uint16_t, 0, kUnroll>)
                           : (h->p.r2 == 5 ? k_update_direct<uint8_t, 5, kUnroll> : k_update_direct<uint8_t, 0, kUnroll>);
-  fn<<<grid, 256, 0, h->stream>>>(h->kp, pairs, n, h->sre, h->sle, stamp, h->clock);
+  fn<<<grid, 256, 0, h->stream>>>(h->kp, pairs, n, h->sre, h->sle, stamp, h->clock, h->mirror_sre, h->mirror_sle);
   SSE_LAUNCHED(h);
   return SSE_OK;
 }
@@ -271,7 +277,7 @@ TileGeometry make_tiles(const sse_params& p, const sse_derived& d, int num_sms) 
 
 // Tiled update variants: loads in flight per thread and test-before-set atomics.
 using TiledKernel = void (*)(KParams, TileGeometry, const uint2*, uint64_t, uint8_t*, uint32_t*, uint32_t,
-                            const uint32_t*);
+                            const uint32_t*, uint8_t*, uint32_t*);
 struct TiledVariant {
   TiledKernel fn[2][2];  // [16-bit cells][one tile per row (no range test)]
   int unroll;
@@ -299,8 +305,10 @@ int launch_update_tiled(sse_handle* h, const uint32_t* d_pairs, uint64_t n, int 
   constexpr uint64_t kMaxPairsPerLaunch = 1ull << 30;  // keeps per-group indices in 32 bits
   for (uint64_t done = 0; done < n; done += kMaxPairsPerLaunch) {
     const uint64_t m = std::min(kMaxPairsPerLaunch, n - done);
-    fn<<<g.groups * g.tiles, kTiledThreads, smem, h->stream>>>(
-        h->kp, g, reinterpret_cast<const uint2*>(d_pairs + 2 * done), m, h->sre, h->sle_bits, stamp, h->clock);
+    fn<<<g.groups * g.tiles, kTiledThreads, smem, h->stream>>>(h->kp, g,
+                                                               reinterpret_cast<const uint2*>(d_pairs + 2 * done), m,
+                                                               h->sre, h->sle_bits, stamp, h->clock, h->mirror_sre,
+                                                               h->mirror_bits);
     SSE_LAUNCHED(h);
   }
   const uint64_t words = h->sle_cells / 32;
@@ -1758,7 +1766,9 @@ struct sse_server {
   cudaEvent_t ev_router[kMaxRouters] = {};
   sse_handle* global = nullptr;
   cudaStream_t gstream = nullptr;
-  cudaEvent_t ev_merged = nullptr;
+  cudaStream_t xstream = nullptr;  // the routers' expiry pass, after each close
+  cudaEvent_t ev_closed = nullptr;  // the global estimator's close kernels are done
+  cudaEvent_t ev_merged = nullptr;  // the routers' expiry pass is done
   RouterTable rt;
   std::vector<ServerSlot> slots;
   size_t next_slot = 0;
@@ -1821,9 +1831,14 @@ void reporter_loop(sse_server* s) {
   }
 }
 
-// Closes the current slice: routers -> global merge (expiring the routers' old cells),
-// detection on the global stream, router clocks advance; the report is collected by the
-// reporter thread. At most one close is in flight.
+// Closes the current slice. Every router's update also wrote the global estimator (its RSRA
+// directly, its SLEA through the global's bitmap), so the global estimator already holds the
+// merge of the routers (Algorithms 2 and 7: the most recent stamp per cell) and the close
+// needs no pass over the routers' state: the global's bitmap is applied and the slice closed
+// on the global stream. Then, on a stream of its own so that it does not delay the report,
+// one pass resets the routers' cells that left the window (their next updates wait for it),
+// and the router clocks advance; the report is collected by the reporter thread. At most one
+// close is in flight.
 int server_close_slice(sse_server* s) {
   {
     std::unique_lock<std::mutex> lk(s->mu);
@@ -1836,10 +1851,22 @@ int server_close_slice(sse_server* s) {
     SSE_CUDA(g, cudaEventRecord(s->ev_router[r], s->rstream[r]));
     SSE_CUDA(g, cudaStreamWaitEvent(s->gstream, s->ev_router[r], 0));
   }
-  const uint64_t n16 = (g->d.sre_bytes + g->d.sle_bytes) / 16;
-  k_merge_routers<<<grid_for(g, n16, 256, 8), 256, 0, s->gstream>>>(g->state, s->rt, s->n, n16, g->p.k, g->clock);
+  const uint64_t words = g->sle_cells / 32;
+  k_apply_bits<uint8_t><<<grid_for(g, words, 256, 8), 256, 0, s->gstream>>>(g->sle_bits, g->sle, words, 0u, g->clock);
   SSE_LAUNCHED(g);
-  SSE_CUDA(g, cudaEventRecord(s->ev_merged, s->gstream));
+  uint32_t* sorted = nullptr;
+  int rc = close_enqueue(g, &sorted);
+  if (rc) return rc;
+  SSE_CUDA(g, cudaEventRecord(s->ev_closed, s->gstream));
+  k_tick<<<1, 32, 0, s->gstream>>>(g->clock, 1);
+  SSE_LAUNCHED(g);
+  // the routers' expiry at this slice's stamp (router clocks tick only after it)
+  const uint64_t n16 = (g->d.sre_bytes + g->d.sle_bytes) / 16;
+  SSE_CUDA(g, cudaStreamWaitEvent(s->xstream, s->ev_closed, 0));
+  k_merge_routers<<<grid_for(g, n16, 256, 8), 256, 0, s->xstream>>>(nullptr, s->rt, s->n, n16, g->p.k,
+                                                                     s->router[0]->clock);
+  SSE_LAUNCHED(g);
+  SSE_CUDA(g, cudaEventRecord(s->ev_merged, s->xstream));
   for (int r = 0; r < s->n; ++r) {
     sse_handle* h = s->router[r];
     SSE_CUDA(h, cudaStreamWaitEvent(s->rstream[r], s->ev_merged, 0));
@@ -1847,11 +1874,6 @@ int server_close_slice(sse_server* s) {
     SSE_LAUNCHED(h);
     h->slice += 1;
   }
-  uint32_t* sorted = nullptr;
-  int rc = close_enqueue(g, &sorted);
-  if (rc) return rc;
-  k_tick<<<1, 32, 0, s->gstream>>>(g->clock, 1);
-  SSE_LAUNCHED(g);
   {
     std::lock_guard<std::mutex> lk(s->mu);
     s->pending.push_back(PendingClose{s->cur_slice, boundary, sorted});
@@ -1891,6 +1913,7 @@ void sse_server_destroy(sse_server* s) {
     if (s->ev_router[r]) cudaEventDestroy(s->ev_router[r]);
   }
   if (s->gstream) cudaStreamSynchronize(s->gstream);
+  if (s->xstream) cudaStreamSynchronize(s->xstream);
   sse_destroy(s->global);
   for (ServerSlot& sl : s->slots) {
     if (sl.done) cudaEventDestroy(sl.done);
@@ -1899,9 +1922,11 @@ void sse_server_destroy(sse_server* s) {
     if (sl.h_pin) cudaFreeHost(sl.h_pin);
   }
   if (s->ev_merged) cudaEventDestroy(s->ev_merged);
+  if (s->ev_closed) cudaEventDestroy(s->ev_closed);
   for (int r = 0; r < s->n; ++r)
     if (s->rstream[r]) cudaStreamDestroy(s->rstream[r]);
   if (s->gstream) cudaStreamDestroy(s->gstream);
+  if (s->xstream) cudaStreamDestroy(s->xstream);
   delete s;
 }
 
@@ -1925,6 +1950,8 @@ int sse_server_create(const sse_params* p, const sse_server_config* cfg, sse_ser
   s->cfg = *cfg;
   s->n = (int)cfg->n_routers;
   bool ok = cudaStreamCreateWithFlags(&s->gstream, cudaStreamNonBlocking) == cudaSuccess &&
+            cudaStreamCreateWithFlags(&s->xstream, cudaStreamNonBlocking) == cudaSuccess &&
+            cudaEventCreateWithFlags(&s->ev_closed, cudaEventDisableTiming) == cudaSuccess &&
             cudaEventCreateWithFlags(&s->ev_merged, cudaEventDisableTiming) == cudaSuccess;
   for (int r = 0; r < s->n && ok; ++r)
     ok = cudaStreamCreateWithFlags(&s->rstream[r], cudaStreamNonBlocking) == cudaSuccess &&
@@ -1957,6 +1984,10 @@ int sse_server_create(const sse_params* p, const sse_server_config* cfg, sse_ser
   for (int r = 0; r < s->n; ++r) {
     s->rt.state[r] = s->router[r]->state;
     s->rt.gbits[r] = s->router[r]->sle_bits;
+    // every write of a router's updates goes to the global estimator as well
+    s->router[r]->mirror_sre = s->global->sre;
+    s->router[r]->mirror_sle = s->global->sle;
+    s->router[r]->mirror_bits = s->global->sle_bits;
   }
   s->rep_hosts.resize(q.max_candidates);
   s->rep_est.resize(q.max_candidates);

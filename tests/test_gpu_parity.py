@@ -246,18 +246,19 @@ def test_window_wraps_stamp_cycle():
     assert est.slice == 300
 
 
-@pytest.mark.parametrize("sle_rows", ["core_link", "four_times_longer"])
+@pytest.mark.parametrize("sle_rows", ["core_link", "sixteen_times_longer"])
 def test_core_link_full_size_parity(sle_rows):
     """Three 2^25-pair slices of the core-link trace in the benchmark's configuration
     (automatic update strategy): state, hot SREs, row counts, candidates (against the
     definitional brute force over all 2^32 addresses) and estimates. The benchmark's SLEA
     rows (2^16 SLEs) are saturated at this load, so most estimates take Eq. 12's clamp; with
-    rows of 2^18 SLEs (q' = 18) they are not, and the estimates are compared in the regime
-    where Eq. 12 corrects a partly filled union SLE."""
+    rows of 2^20 SLEs (q' = 20, ten bitmap pieces per row in the tiled update) they are not,
+    and the estimates are compared in the regime where Eq. 12 corrects a partly filled union
+    SLE."""
     S = sse()
     p = S.core_link_params()
-    if sle_rows == "four_times_longer":
-        p = S.Params(q=20, q2=18, eta2=4096, k=8, seed=0)
+    if sle_rows == "sixteen_times_longer":
+        p = S.Params(q=20, q2=20, eta2=4096, k=8, seed=0)
     tr = synth.Traffic(synth.core_link())
     est = S.Estimator(p)
     orc = oracle.Oracle(oracle_params(p))
@@ -278,7 +279,7 @@ def test_core_link_full_size_parity(sle_rows):
     assert close_enough(rep.est, ref["est"])
     ip, _ = tr.planted()
     assert len(np.intersect1d(ip, rep.super_points)) > 20
-    if sle_rows == "four_times_longer":
+    if sle_rows == "sixteen_times_longer":
         sf = np.array(orc.row_counts()) / orc.row_len2
         assert sf.max() < 0.9  # rows far from full
         assert np.count_nonzero((ref["flags"] & oracle.SATURATED) == 0) > len(want) // 4
