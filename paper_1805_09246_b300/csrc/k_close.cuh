@@ -17,25 +17,26 @@ namespace sse {
 constexpr int kCloseThreads = 256;
 constexpr uint32_t kSleBytesPerBlock = kCloseThreads * 16;  // == kPitchAlign
 
-// Activity of one 16-bit cell: set and younger than the window (cyclic age mod 65535).
-__device__ __forceinline__ uint32_t cell_active16(uint32_t s, uint32_t cs, uint32_t k) {
-  const uint32_t age = cs >= s ? cs - s : cs + 65535u - s;
-  return (s != 0 && age < k) ? 1u : 0u;
-}
+// The window tests of one pass: four 8-bit or two 16-bit cells at a time.
+struct CloseWindow {
+  Window8 w8;
+  Window16 w16;
+};
 
 // One 32-bit word of cells: adds its active cells to `count` and returns the mask that
 // keeps them (all ones over active cells, zero over the rest). 8-bit cells are tested four
-// at a time (active_hi8; WRAP = the window wraps over stamp 0); 16-bit cells one by one.
+// at a time (active_hi8), 16-bit cells two at a time (active_hi16); WRAP = the window wraps
+// over stamp 0.
 template <typename St, bool WRAP>
-__device__ __forceinline__ uint32_t word_keep(uint32_t w, Window8 win, uint32_t cs, uint32_t k, uint32_t& count) {
+__device__ __forceinline__ uint32_t word_keep(uint32_t w, const CloseWindow& win, uint32_t& count) {
   if constexpr (sizeof(St) == 1) {
-    const uint32_t a = active_hi8<WRAP>(w, win);
+    const uint32_t a = active_hi8<WRAP>(w, win.w8);
     count += __popc(a);
     return (a >> 7) * 0xFFu;
   } else {
-    const uint32_t a0 = cell_active16(w & 0xFFFFu, cs, k), a1 = cell_active16(w >> 16, cs, k);
-    count += a0 + a1;
-    return (a0 ? 0xFFFFu : 0u) | (a1 ? 0xFFFF0000u : 0u);
+    const uint32_t a = active_hi16<WRAP>(w, win.w16);
+    count += __popc(a);
+    return (a >> 15) * 0xFFFFu;
   }
 }
 
@@ -92,15 +93,15 @@ __device__ __forceinline__ void close_rsra8(const KParams& p, uint8_t* __restric
 // The pass of k_close for one window shape (WRAP: see word_keep).
 template <typename St, bool WRAP>
 __device__ __forceinline__ void close_body(const KParams& p, uint8_t* __restrict__ sre, uint8_t* __restrict__ sle,
-                                          uint32_t* __restrict__ hot_bits, uint32_t* row_sum, uint32_t cs,
-                                          Window8 win, uint32_t do_sre, uint32_t mode) {
+                                          uint32_t* __restrict__ hot_bits, uint32_t* row_sum,
+                                          const CloseWindow& win, uint32_t do_sre, uint32_t mode) {
   using SreWord = typename std::conditional<sizeof(St) == 1, uint2, uint4>::type;
   constexpr int kSreInts = sizeof(SreWord) / 4;
   const bool expire = (mode & 1u) != 0;
   const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const uint64_t nthreads = (uint64_t)gridDim.x * blockDim.x;  // a multiple of 32
   if (do_sre && sizeof(St) == 1) {
-    close_rsra8<WRAP>(p, sre, hot_bits, win, mode);
+    close_rsra8<WRAP>(p, sre, hot_bits, win.w8, mode);
   } else if (do_sre) {
     // RSRA: SRE index g (row-major over [r][2^q]); r * 2^q is a multiple of 32, so every
     // iteration covers whole warps.
@@ -122,7 +123,7 @@ __device__ __forceinline__ void close_body(const KParams& p, uint8_t* __restrict
         memcpy(x, &v[u], sizeof(SreWord));
 #pragma unroll
         for (int i = 0; i < kSreInts; ++i) {
-          keep[i] = word_keep<St, WRAP>(x[i], win, cs, p.k, weight);
+          keep[i] = word_keep<St, WRAP>(x[i], win, weight);
           expired |= x[i] & ~keep[i];
         }
         const unsigned ballot = __ballot_sync(0xFFFFFFFFu, weight >= p.hot_min);
@@ -150,7 +151,7 @@ __device__ __forceinline__ void close_body(const KParams& p, uint8_t* __restrict
       uint32_t keep[4], expired = 0;
 #pragma unroll
       for (int i = 0; i < 4; ++i) {
-        keep[i] = word_keep<St, WRAP>(w[i], win, cs, p.k, count);
+        keep[i] = word_keep<St, WRAP>(w[i], win, count);
         expired |= w[i] & ~keep[i];
       }
       if (expire && expired) *cell = make_uint4(w[0] & keep[0], w[1] & keep[1], w[2] & keep[2], w[3] & keep[3]);
@@ -172,14 +173,17 @@ __global__ void __launch_bounds__(kCloseThreads) k_close(const __grid_constant__
                                                           const uint32_t* __restrict__ clock, uint32_t do_sre,
                                                           uint32_t mode) {
   const uint32_t cs = clock ? *clock : cs_value;
-  const Window8 win = window8(cs, p.k);  // used by 8-bit cells only
+  CloseWindow win;
+  win.w8 = window8(cs, p.k);    // 8-bit cells
+  win.w16 = window16(cs, p.k);  // 16-bit cells
   __shared__ uint32_t row_sum[kMaxRows];
   if (threadIdx.x < kMaxRows) row_sum[threadIdx.x] = 0;
   __syncthreads();
-  if (sizeof(St) == 1 && win.wrap)
-    close_body<St, true>(p, sre, sle, hot_bits, row_sum, cs, win, do_sre, mode);
+  const bool wrap = sizeof(St) == 1 ? win.w8.wrap != 0 : win.w16.wrap != 0;
+  if (wrap)
+    close_body<St, true>(p, sre, sle, hot_bits, row_sum, win, do_sre, mode);
   else
-    close_body<St, false>(p, sre, sle, hot_bits, row_sum, cs, win, do_sre, mode);
+    close_body<St, false>(p, sre, sle, hot_bits, row_sum, win, do_sre, mode);
   __syncthreads();
   if (threadIdx.x < p.r2 && row_sum[threadIdx.x]) atomicAdd(&active2[threadIdx.x], row_sum[threadIdx.x]);
 }
