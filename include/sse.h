@@ -444,11 +444,14 @@ SSE_API int sse_batch_reset(sse_batch* b);
  * estimator and stream: requests of different routers run concurrently, those of one router
  * in order. A request is copied into one of `slots` pinned staging buffers and scanned from
  * its device twin; when every slot is busy, admission waits for the oldest one (the only
- * backpressure). A request in a later slice first closes the current slice: the routers are
- * merged into the global estimator (Algorithm 7; routers' old cells expire on the way),
- * detection runs on the global estimator while the next slice's requests proceed, and a
- * reporter thread collects the report; its latency runs from the slice boundary to the
- * report being on the host. Arrival times must not decrease. One thread submits.
+ * backpressure). Every update of a router writes the global estimator as well (its RSRA
+ * and SLEA stamps, or its SLEA bitmap), so the global estimator always holds the merge of the
+ * routers (Algorithm 7: the most recent stamp per cell). A request in a later slice first
+ * closes the current slice: detection runs on the global estimator while the next slice's
+ * requests proceed, then one pass resets the routers' cells that left the window (the
+ * routers' next updates wait for it), and a reporter thread collects the report; its
+ * latency runs from the slice boundary to the report being on the host. Arrival times must
+ * not decrease. One thread submits.
  */
 typedef struct sse_server sse_server;
 
@@ -489,7 +492,8 @@ SSE_API int sse_server_poll(sse_server* s, sse_report* out, double* latency_ms);
 
 SSE_API int sse_server_get_stats(sse_server* s, sse_server_stats* out);
 
-/* The estimators (owned by the server; read-only use after sse_server_flush). */
+/* The estimators (owned by the server; read-only use after sse_server_flush: an update
+ * through a router's handle would also write the global estimator). */
 SSE_API int sse_server_router(sse_server* s, uint32_t router, sse_handle** out);
 SSE_API int sse_server_global(sse_server* s, sse_handle** out);
 
