@@ -11,6 +11,13 @@ delta'=16, window k=8, theta=1024, 8-bit stamps.
 Prints one JSON line. Under torchrun (N > 1) every rank runs its own router's trace
 (independent estimators: weak scaling, no data-path collective); the time is the max
 over ranks. --impl reference times the CPU oracle (tests' checker) on a bounded sample.
+
+After the timed core-link steps the same line also carries, measured on the same GPU: the
+roofs of the update's units (sse_microbench), a paced serving leg (32 routers at the offered
+2e9 pairs/s: slice-close-to-report p50/p99), and, from child processes running the other
+workloads, the 16-edge-router batch step and the learned correction (training samples/s,
+median relative error against linear counting); --no-legs and --serve-slices 0 leave those
+out. --workload selects one of the other workloads alone.
 """
 from __future__ import annotations
 
@@ -66,6 +73,8 @@ def parse(argv=None):
                     help="serving: submit each request at its arrival time (wall clock) instead of at once")
     ap.add_argument("--serve-slices", type=int, default=200,
                     help="slice closes of the paced serving leg of the core-link run (0: no serving leg)")
+    ap.add_argument("--no-legs", action="store_true",
+                    help="core-link run without the edge-router and learned-correction legs")
     args = ap.parse_args(argv)
     if args.steps is None:
         args.steps = 27 if args.workload == "learned" else 200
@@ -391,6 +400,23 @@ def serve(rank: int, seconds: float, paced: bool, pool_pairs: int | None = None,
             "pairs_timed": total, "wall": wall, "virtual": (timed[-1][0] - v0) if timed else 0.0,
             "latencies": lat, "slices_reported": len(reports), "slot_waits": st["slot_waits"], "clocks": clk,
             "slice_s": slice_s}
+
+
+def run_leg(argv: list[str], timeout: float = 900.0) -> dict:
+    """Another workload of this benchmark in a child process on this rank's GPU (the
+    distributed environment removed, so that it runs alone); its JSON line, or the error."""
+    drop = ("RANK", "WORLD_SIZE", "LOCAL_RANK", "LOCAL_WORLD_SIZE", "GROUP_RANK", "ROLE_RANK", "MASTER_ADDR",
+            "MASTER_PORT", "TORCHELASTIC_RUN_ID", "GROUP_WORLD_SIZE", "ROLE_WORLD_SIZE")
+    env = {k: v for k, v in os.environ.items() if k not in drop}
+    try:
+        r = subprocess.run([sys.executable, os.path.abspath(__file__), *argv], capture_output=True, text=True,
+                           timeout=timeout, env=env, cwd=ROOT)
+    except subprocess.TimeoutExpired:
+        return {"error": f"timed out after {timeout:.0f} s"}
+    lines = [x for x in r.stdout.splitlines() if x.startswith("{")]
+    if r.returncode != 0 or not lines:
+        return {"error": f"exit {r.returncode}: {r.stderr.strip().splitlines()[-1] if r.stderr.strip() else ''}"}
+    return json.loads(lines[-1])
 
 
 def pctl(xs, q):
@@ -755,6 +781,25 @@ def main():
 
     if rank != 0:
         return
+    # ---- the other workloads of the configuration, each in a child process on this GPU once
+    # the timed work above is done: 16 batched edge routers, and the learned correction
+    legs = {}
+    if not args.no_legs and not paper:
+        torch.cuda.synchronize()
+        e = run_leg(["--workload", "edge_routers", "--steps", "30", "--warmup", "3"])
+        legs["edge_routers"] = e if "error" in e else {
+            "value": e["value"], "unit": e["unit"], "ms_per_step": e["ms_per_step"], "step_ms_p50": e["step_ms_p50"],
+            "step_ms_p99": e["step_ms_p99"], "gpu_launches": e["gpu_launches"], "clocks": e["clocks"],
+            "workload": e["config"]["workload"], "pairs_per_step_mean": e["config"]["pairs_per_step_mean"]}
+        l = run_leg(["--workload", "learned", "--steps", "27", "--warmup", "3"])
+        legs["learned"] = l if "error" in l else {
+            "train_samples_per_s": l["value"], "median_rel_err_learned": l["median_rel_err_learned"],
+            "median_rel_err_lc": l["median_rel_err_lc"],
+            "median_rel_err_learned_above_gate": l["median_rel_err_learned_above_gate"],
+            "median_rel_err_lc_above_gate": l["median_rel_err_lc_above_gate"],
+            "hosts_above_gate": l["hosts_above_gate"], "p90_rel_err_learned": l["p90_rel_err_learned"],
+            "p90_rel_err_lc": l["p90_rel_err_lc"], "gpu_launches": l["gpu_launches"], "clocks": l["clocks"],
+            "workload": l["config"]["workload"]}
     cpu = None if args.no_cpu or paper else cpu_baseline(host)
     close_sorted = sorted(close_ms)
     out = {
@@ -788,6 +833,7 @@ def main():
     }
     if serving:
         out.update(serving)
+    out.update(legs)
     print(json.dumps(out), flush=True)
     if pg is not None:
         pg.destroy_process_group()
