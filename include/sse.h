@@ -67,6 +67,13 @@ enum sse_update_mode {
   SSE_UPDATE_TILED = 2   /* SLEA writes collect in on-chip bitmaps, then merge into it */
 };
 
+/* Joins of a slice close (sse_set_join): both find the same candidate hosts. */
+enum sse_join_mode {
+  SSE_JOIN_AUTO = 0,     /* from the top row down where it applies, else from row 0 up */
+  SSE_JOIN_FORWARD = 1,  /* from rows 0, 1, 2 up (Algorithms 4-5) */
+  SSE_JOIN_BACKWARD = 2  /* from rows 0 and r-1 down (see sse_set_join) */
+};
+
 /*
  * Parameters (symbols of the paper). sse_params_default() fills the values of the
  * paper's experiment (Section 5): r=r'=5, q=q'=17, delta=5, eta=8, delta'=16,
@@ -239,6 +246,22 @@ SSE_API int sse_close_slice(sse_handle* h, sse_report* out);
  * copies, clock tick) from a CUDA graph captured at the first call; 0: launches the same
  * kernels one by one. Results are identical. Errors: INVALID_PARAM. */
 SSE_API int sse_close_use_graph(sse_handle* h, int enable);
+
+/*
+ * Chooses how a close grows candidate tuples (Section 3.3, Algorithms 4-5; Eq. 7). Both ways
+ * list every chain of hot SREs, one per row, that one 32-bit address maps to, and regain the
+ * hosts of each from RHFG[0]; the candidate sets are identical. SSE_JOIN_FORWARD grows the
+ * chains from HSE(0) x HSE(1) upwards, as the paper does. SSE_JOIN_BACKWARD starts from
+ * HSE(0) and HSE(r-1): B(r-1) = aip >> (r-1)*delta keeps only s = 32 - (r-1)*delta bits of
+ * an address, so he_{r-1} agrees with he_0 above bit s and only pairs inside one of the
+ * 2^(q-s) column blocks can meet; rows r-2 .. 1 then each add delta address bits. It applies
+ * when delta <= 5, 4 <= r <= 6 and q - s <= 12 (the paper's q = 17,
+ * delta = 5, r = 5 has s = 12: 32 blocks). SSE_JOIN_AUTO (the default) takes it wherever it
+ * applies. Takes effect at the next close (a captured close graph is dropped and captured
+ * again). Errors: INVALID_PARAM (unknown mode, or BACKWARD where it does not apply), STATE
+ * (a close is pending).
+ */
+SSE_API int sse_set_join(sse_handle* h, int mode);
 
 /*
  * Failure-detection hook (the paper has no counterpart; for tests of the bounded device-side

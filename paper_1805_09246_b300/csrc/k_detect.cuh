@@ -294,16 +294,58 @@ struct EstTable {
   uint32_t r2, eta2, blocks;
 };
 
+// The hot SREs of one row grouped by column block: block b (columns [b * 2^s, (b+1) * 2^s),
+// 5 <= s < q) lists its hot columns at blist[b * 2^s ...] (any order) and their number in
+// bcount[b]. One block of the launch per column block (b = blk, blk + nblk, ...), which
+// reads the block's 2^(s-5) bitmap words 8 per thread at a time.
+__device__ __forceinline__ void block_list_part(const uint32_t* __restrict__ hot_bits, uint32_t row, uint32_t q,
+                                                uint32_t s, uint32_t* __restrict__ blist,
+                                                uint32_t* __restrict__ bcount, uint32_t blk, uint32_t nblk) {
+  __shared__ uint32_t s_n;
+  const uint32_t nb = 1u << (q - s), wpb = 1u << (s - 5);
+  const uint32_t* src = hot_bits + ((uint64_t)row << (q - 5));
+  for (uint32_t b = blk; b < nb; b += nblk) {
+    if (threadIdx.x == 0) s_n = 0;
+    __syncthreads();
+    uint32_t* out = blist + ((uint64_t)b << s);
+    for (uint32_t w0 = 0; w0 < wpb; w0 += 8 * blockDim.x) {
+      uint32_t v[8];
+#pragma unroll
+      for (uint32_t u = 0; u < 8; ++u) {
+        const uint32_t w = w0 + u * blockDim.x + threadIdx.x;
+        v[u] = w < wpb ? src[b * wpb + w] : 0u;
+      }
+#pragma unroll
+      for (uint32_t u = 0; u < 8; ++u) {
+        uint32_t x = v[u];
+        if (!x) continue;
+        uint32_t at = atomicAdd(&s_n, (uint32_t)__popc(x));
+        const uint32_t col0 = (b * wpb + w0 + u * blockDim.x + threadIdx.x) << 5;
+        while (x) {
+          out[at++] = col0 + (uint32_t)(__ffs(x) - 1);
+          x &= x - 1u;
+        }
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) bcount[b] = s_n;
+    __syncthreads();  // s_n is reset for the next column block
+  }
+}
+
 // Everything the join reads from the hot bitmap, in one launch: blocks [0, n_lists) build
 // the hot lists of rows 0-1 and the hot counts, the next n_regroup blocks the regrouped
-// tables of rows 2..r-1, the rest (when any2 != NULL) the "any hot" bitmaps of rows 2 and 3
-// (any3 when r > 3), half of them each.
+// tables of rows 2..r-1, the next n_block blocks row r-1's hot SREs by column block of 2^s
+// (the join from the top row down), the rest (when any2 != NULL) the "any hot" bitmaps of
+// rows 2 and 3 (any3 when r > 3), half of them each.
 __global__ void __launch_bounds__(256) k_hot_prep(const uint32_t* __restrict__ hot_bits, uint32_t r, uint32_t q,
                                                   uint32_t delta, uint32_t* __restrict__ hot_count,
                                                   uint32_t* __restrict__ list0, uint32_t* __restrict__ list1,
                                                   uint32_t* __restrict__ n_list, uint32_t* __restrict__ tables,
                                                   uint32_t* __restrict__ any2, uint32_t* __restrict__ any3,
-                                                  uint32_t n_lists, uint32_t n_regroup, EstTable tab) {
+                                                  uint32_t n_lists, uint32_t n_regroup, EstTable tab,
+                                                  uint32_t* __restrict__ blist, uint32_t* __restrict__ bcount,
+                                                  uint32_t n_block, uint32_t s) {
   const uint32_t b = blockIdx.x;
   if (b >= gridDim.x - tab.blocks) {  // the last tab.blocks blocks: the estimate table
     // Eq. 12's P as in setting_product (the same quotients, multiplied in row order), with the
@@ -326,8 +368,11 @@ __global__ void __launch_bounds__(256) k_hot_prep(const uint32_t* __restrict__ h
     hot_lists_part(hot_bits, r, q, hot_count, list0, list1, n_list, b, n_lists);
   } else if (b < n_lists + n_regroup) {
     regroup_part(hot_bits, r, q, delta, tables, b - n_lists, n_regroup);
+  } else if (b < n_lists + n_regroup + n_block) {
+    block_list_part(hot_bits, r - 1, q, s, blist, bcount, b - n_lists - n_regroup, n_block);
   } else if (any2) {
-    const uint32_t rest = gridDim.x - n_lists - n_regroup - tab.blocks, x = b - n_lists - n_regroup;
+    const uint32_t first_any = n_lists + n_regroup + n_block;
+    const uint32_t rest = gridDim.x - first_any - tab.blocks, x = b - first_any;
     const uint32_t half = (rest + 1) / 2;
     if (x < half)
       any_part(hot_bits, 2, q, delta, any2, x, half);
@@ -879,6 +924,153 @@ __global__ void __launch_bounds__(kJoinTiledThreads) k_join_tiled(
   fn = 0;
   __syncwarp();
   if (lane < cn) regain_high(p, wc_he0[lane], wc_high[lane], cand, n_cand, cap, overflow, rt);
+}
+
+// Join from the top row down, for r = R (4..6), delta <= 5 and s = 32 - (R-1)*delta with
+// 5 <= s < q. B(R-1) = aip >> (R-1)*delta has only s bits inside a 32-bit address, so
+// he_{R-1} = he_0 XOR B(R-1) agrees with he_0 above bit s: the hot SREs of row R-1 that can
+// share a host with he_0 are those of he_0's column block of 2^s (listed by k_hot_prep).
+// Each such pair fixes address bits [(R-1)*delta, 32). Then every row L = R-2 .. 1 adds bits
+// [L*delta, (L+1)*delta): B(L)'s upper q-delta bits repeat B(L+1)'s lower ones (the overlap
+// of Algorithm 5), so he_L's upper q-delta bits are known, and its delta low bits are the
+// set bits of one 2^delta-bit group of row L's hot bitmap. A chain through row 1 fixes bits
+// [delta, 32) and is regained as in the join from row 0 up (Eq. 7). The chains are those of
+// Algorithms 4-5 that stay inside 32 address bits, found from the other end: the top row's
+// 2^(q-s) blocks cut the pairs to start from by that factor against HSE(0) x HSE(1).
+// Every stage runs on whole warps: each lane holds one chain, and the children of a row
+// wait in the warp's queue for that row until 32 are there.
+constexpr int kJoinDownThreads = 256;
+constexpr uint32_t kJoinDownQueue = 64;   // entries per queue (< 32 waiting + 32 pushed)
+constexpr uint32_t kJoinDownUnroll = 4;   // row R-1 entries per lane in flight
+
+template <int R>
+struct DownWalk {
+  const KParams& p;
+  const uint32_t* hot;   // hot bitmaps of all rows
+  uint32_t* qs;          // this warp's queues: level L holds he_0 [kJoinDownQueue], then bits
+  uint32_t cnt[R - 2];   // entries waiting at level L (the same in every lane); level 0: complete
+  uint32_t delta, qbits, gmask, span_mask, lane, lt_mask;
+  uint32_t* cand;
+  uint32_t* n_cand;
+  uint32_t cap;
+  uint32_t* overflow;
+  const RegainTable* rt;
+
+  __device__ __forceinline__ DownWalk(const KParams& p_, const uint32_t* hot_, uint32_t* qs_, uint32_t lane_,
+                                      uint32_t* cand_, uint32_t* n_cand_, uint32_t cap_, uint32_t* overflow_,
+                                      const RegainTable* rt_)
+      : p(p_), hot(hot_), qs(qs_), delta(p_.delta), qbits(p_.q), gmask((1u << (p_.q - p_.delta)) - 1u),
+        span_mask(p_.delta == 5 ? 0xFFFFFFFFu : (1u << (1u << p_.delta)) - 1u), lane(lane_),
+        lt_mask((1u << lane_) - 1u), cand(cand_), n_cand(n_cand_), cap(cap_), overflow(overflow_), rt(rt_) {
+#pragma unroll
+    for (int L = 0; L < R - 2; ++L) cnt[L] = 0;
+  }
+
+  // Row L's hot flags for the chain (he_0, bits [(L+1)*delta, 32) of the address): the
+  // 2^delta SREs whose upper q-delta bits are those of he_0 XOR B(L), adjacent in the bitmap.
+  template <int L>
+  __device__ __forceinline__ uint32_t group(uint32_t he0, uint32_t a) const {
+    const uint32_t first = (((he0 >> delta) ^ (a >> ((L + 1) * delta))) & gmask) << delta;
+    return (__ldg(hot + ((uint64_t)L << (qbits - 5)) + (first >> 5)) >> (first & 31)) & span_mask;
+  }
+
+  // Every hot SRE t of row L's group (m) extends the chain by bits [L*delta, (L+1)*delta):
+  // the low delta bits of B(L) = he_0 XOR he_L are t XOR the low delta bits of he_0.
+  template <int L>
+  __device__ __forceinline__ void walk(uint32_t m, uint32_t he0, uint32_t a) {
+    const uint32_t xl = he0 & ((1u << delta) - 1u);
+    while (__any_sync(0xFFFFFFFFu, m != 0u)) {
+      const bool has = m != 0u;
+      uint32_t child = 0;
+      if (has) {
+        const uint32_t t = (uint32_t)(__ffs(m) - 1);
+        m &= m - 1u;
+        child = a | ((t ^ xl) << (L * delta));
+      }
+      push<L - 1>(has, he0, child);
+    }
+  }
+
+  // Queue a chain for row L (L >= 1) or, at L = 0, a complete chain for regain; whenever
+  // 32 wait, every lane takes one.
+  template <int L>
+  __device__ __forceinline__ void push(bool ok, uint32_t he0, uint32_t a) {
+    uint32_t* qh = qs + L * 2 * kJoinDownQueue;
+    uint32_t* qa = qh + kJoinDownQueue;
+    const uint32_t b = __ballot_sync(0xFFFFFFFFu, ok);
+    if (ok) {
+      const uint32_t at = cnt[L] + __popc(b & lt_mask);
+      qh[at] = he0;
+      qa[at] = a;
+    }
+    cnt[L] += __popc(b);
+    if (cnt[L] >= 32) {
+      cnt[L] -= 32;
+      __syncwarp();
+      const uint32_t e0 = qh[cnt[L] + lane], ea = qa[cnt[L] + lane];
+      __syncwarp();  // those entries are overwritten by the next push
+      if constexpr (L == 0)
+        regain_high(p, e0, ea, cand, n_cand, cap, overflow, rt);
+      else
+        walk<L>(group<L>(e0, ea), e0, ea);
+    }
+  }
+
+  // The chains still queued at level L and below, the highest level first.
+  template <int L>
+  __device__ __forceinline__ void flush() {
+    uint32_t* qh = qs + L * 2 * kJoinDownQueue;
+    const bool ok = lane < cnt[L];
+    const uint32_t e0 = ok ? qh[lane] : 0u, ea = ok ? qh[kJoinDownQueue + lane] : 0u;
+    cnt[L] = 0;
+    __syncwarp();
+    if constexpr (L == 0) {
+      if (ok) regain_high(p, e0, ea, cand, n_cand, cap, overflow, rt);
+    } else {
+      walk<L>(ok ? group<L>(e0, ea) : 0u, e0, ea);
+      flush<L - 1>();
+    }
+  }
+};
+
+// One warp per he_0 of HSE(0) (list0, striding over the grid's warps); its lanes take the
+// row R-1 hot SREs of he_0's block, kJoinDownUnroll each at a time.
+template <int R>
+__global__ void __launch_bounds__(kJoinDownThreads) k_join_down(
+    const __grid_constant__ KParams p, const uint32_t* __restrict__ hot_bits, const uint32_t* __restrict__ list0,
+    const uint32_t* __restrict__ n_list, const uint32_t* __restrict__ blist, const uint32_t* __restrict__ bcount,
+    uint32_t* __restrict__ cand, uint32_t* __restrict__ n_cand, uint32_t cap, uint32_t* __restrict__ overflow) {
+  static_assert(R >= 4 && R <= 6, "rows");
+  __shared__ uint32_t s_queue[kJoinDownThreads / 32][(R - 2) * 2 * kJoinDownQueue];
+  __shared__ RegainTable s_rt;
+  if (!p.tab) build_regain_table(p, &s_rt);
+  __syncthreads();
+  const uint32_t n0 = n_list[0];
+  const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+  DownWalk<R> w(p, hot_bits, s_queue[warp], lane, cand, n_cand, cap, overflow, p.tab ? nullptr : &s_rt);
+  const uint32_t top = (R - 1) * p.delta;  // B(R-1) is address bits [top, 32)
+  const uint32_t s = 32u - top;
+  const uint32_t warps = gridDim.x * (blockDim.x >> 5);
+  for (uint32_t i = blockIdx.x * (blockDim.x >> 5) + warp; i < n0; i += warps) {
+    const uint32_t he0 = list0[i];
+    const uint32_t b = he0 >> s;
+    const uint32_t n4 = bcount[b];
+    const uint32_t* l4 = blist + ((uint64_t)b << s);
+    for (uint32_t k0 = 0; k0 < n4; k0 += 32 * kJoinDownUnroll) {  // uniform over the warp
+      uint32_t a[kJoinDownUnroll], m[kJoinDownUnroll];
+#pragma unroll
+      for (uint32_t u = 0; u < kJoinDownUnroll; ++u) {
+        const uint32_t k = k0 + u * 32 + lane;
+        a[u] = k < n4 ? (he0 ^ l4[k]) << top : 0u;
+      }
+#pragma unroll
+      for (uint32_t u = 0; u < kJoinDownUnroll; ++u)
+        m[u] = k0 + u * 32 + lane < n4 ? w.template group<R - 2>(he0, a[u]) : 0u;
+#pragma unroll
+      for (uint32_t u = 0; u < kJoinDownUnroll; ++u) w.template walk<R - 2>(m[u], he0, a[u]);
+    }
+  }
+  w.template flush<R - 3>();
 }
 
 // ---------------------------------------------------------------- ordering

@@ -142,6 +142,12 @@ struct sse_handle {
   uint32_t join_list1_cap = 0; // HSE(1) entries staged in shared memory when it fits
   size_t join_smem = 0;
   size_t join_tiled_smem = 0;  // k_join_tiled (delta <= 5)
+  // the join from the top row down (k_join_down), where the parameters admit it
+  int join_mode = SSE_JOIN_AUTO;
+  uint32_t join_down_s = 0;       // columns per block of row r-1: 2^s, s = 32 - (r-1)*delta (0: not admitted)
+  uint32_t join_down_grid = 0;
+  uint32_t* blist = nullptr;      // row r-1's hot SREs by column block (2^q entries)
+  uint32_t* bcount = nullptr;     // their number per block (2^(q-s) entries)
   uint32_t* cand = nullptr;  // two buffers of cand_cap entries
   uint32_t* cand_alt = nullptr;
   uint32_t* cand_out = nullptr;  // the sorted candidates
@@ -240,6 +246,25 @@ KParams make_kparams(const sse_params& p, const sse_derived& d) {
   k.row_len2 = d.row_len2;
   return k;
 }
+
+// The join from the top row down (k_join_down) applies when B(r-1) keeps only
+// s = 32 - (r-1)*delta < q bits inside a 32-bit address (so row r-1's hot SREs fall into
+// 2^(q-s) column blocks, at most 4096), with delta <= 5, 4 <= r <= 6 and s >= 5 (valid
+// parameters have (r-2)*delta + q >= 32, so s < q always, and r = 3 would need q >= 27).
+// Returns s, or 0 when it does not apply.
+uint32_t join_down_bits(const sse_params& p, const sse_derived& d) {
+  if (d.delta > 5 || p.r < 4 || p.r > 6) return 0;
+  const int s = 32 - (int)((p.r - 1) * d.delta);
+  if (s < 5 || s >= (int)p.q || (int)p.q - s > 12) return 0;
+  return (uint32_t)s;
+}
+
+using JoinDownKernel = void (*)(KParams, const uint32_t*, const uint32_t*, const uint32_t*, const uint32_t*,
+                                const uint32_t*, uint32_t*, uint32_t*, uint32_t, uint32_t*);
+const JoinDownKernel kJoinDownFns[3] = {k_join_down<4>, k_join_down<5>, k_join_down<6>};
+
+// The close's join: from the top row down where it applies, unless SSE_JOIN_FORWARD is set.
+bool join_down(const sse_handle* h) { return h->join_down_s != 0 && h->join_mode != SSE_JOIN_FORWARD; }
 
 int grid_for(const sse_handle* h, uint64_t work, int block, int per_sm) {
   uint64_t g = (work + block - 1) / block;
@@ -476,6 +501,8 @@ void sse_destroy(sse_handle* h) {
   cudaFree(h->est_table);
   cudaFree(h->any2);
   cudaFree(h->any3);
+  cudaFree(h->blist);
+  cudaFree(h->bcount);
   cudaFree(h->rhfg_tab);
   cudaFree(h->swap_buf);
   if (h->host_scratch) cudaFreeHost(h->host_scratch);
@@ -605,6 +632,23 @@ int sse_init(const sse_params* p, void* cuda_stream, sse_handle** out) {
       return SSE_ERR_CUDA;
     }
     h->join_grid = (uint32_t)(per_sm * h->num_sms);
+  }
+  if (const uint32_t s = join_down_bits(q, d)) {
+    int per_sm = 0;
+    const auto fn = kJoinDownFns[q.r - 4];
+    if (cudaMalloc(&h->blist, list_entries * 4) != cudaSuccess ||
+        cudaMalloc(&h->bcount, ((size_t)1 << (q.q - s)) * 4) != cudaSuccess) {
+      cudaGetLastError();
+      sse_destroy(h);
+      return SSE_ERR_OOM;
+    }
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kJoinDownThreads, 0) != cudaSuccess || per_sm < 1) {
+      cudaGetLastError();
+      sse_destroy(h);
+      return SSE_ERR_CUDA;
+    }
+    h->join_down_s = s;
+    h->join_down_grid = (uint32_t)(per_sm * h->num_sms);
   }
   const uint32_t first_stamp = stamp_of(0, h->smod);
   if (cudaMemsetAsync(h->clock, 0, 256, h->stream) != cudaSuccess ||
@@ -794,16 +838,25 @@ int close_enqueue(sse_handle* h, uint32_t** sorted, bool copy_counters = true) {
   if (rc) return rc;
   {
     const uint64_t words = (1ull << h->p.q) >> 5;
+    const bool down = join_down(h);
+    const uint32_t s = h->join_down_s;
     const uint32_t n_lists = grid_for(h, words * h->p.r, 256, 4);
-    const uint32_t n_regroup = grid_for(h, words * (h->p.r - 2), 256, 2);
+    // the join from the top row down reads the plain hot bitmaps and row r-1 by column block;
+    // the join from row 0 up reads the regrouped tables and the "any hot" bitmaps
+    const uint32_t n_regroup = down ? 0u : grid_for(h, words * (h->p.r - 2), 256, 2);
+    const uint32_t n_block = down ? std::min(1u << (h->p.q - s), 1024u) : 0u;
     const uint32_t any_each = (any_words(h->p.q, h->p.delta) + 255) / 256;
-    const uint32_t n_any = h->any2 ? (h->any3 ? 2 * any_each : any_each) : 0u;
+    const uint32_t n_any = !down && h->any2 ? (h->any3 ? 2 * any_each : any_each) : 0u;
     const EstTable tab = est_table(h, sc->active2);
-    k_hot_prep<<<n_lists + n_regroup + n_any + tab.blocks, 256, 0, h->stream>>>(
-        h->hot_bits, h->p.r, h->p.q, h->p.delta, sc->hot, h->list0, h->list1, sc->n_list, h->tables, h->any2,
-        h->any3, n_lists, n_regroup, tab);
+    k_hot_prep<<<n_lists + n_regroup + n_block + n_any + tab.blocks, 256, 0, h->stream>>>(
+        h->hot_bits, h->p.r, h->p.q, h->p.delta, sc->hot, h->list0, h->list1, sc->n_list, h->tables,
+        down ? nullptr : h->any2, h->any3, n_lists, n_regroup, tab, h->blist, h->bcount, n_block, s);
     SSE_LAUNCHED(h);
-    if (h->kp.delta <= 5)
+    if (down)
+      kJoinDownFns[h->p.r - 4]<<<h->join_down_grid, kJoinDownThreads, 0, h->stream>>>(
+          h->kp, h->hot_bits, h->list0, sc->n_list, h->blist, h->bcount, h->cand, &sc->n_cand, h->cand_cap,
+          &sc->overflow);
+    else if (h->kp.delta <= 5)
       (h->join_stage ? k_join_tiled<true> : k_join_tiled<false>)<<<h->join_grid, kJoinTiledThreads,
                                                                    h->join_tiled_smem, h->stream>>>(
           h->kp, h->tables, h->any2, h->any3, h->list0, h->list1, sc->n_list, h->cand, &sc->n_cand, h->cand_cap,
@@ -1033,6 +1086,23 @@ int sse_close_slice(sse_handle* h, sse_report* out) {
 int sse_close_use_graph(sse_handle* h, int enable) {
   if (!h || h->close_pending) return SSE_ERR_INVALID_PARAM;
   h->close_graph = enable ? 1 : 0;
+  return SSE_OK;
+}
+
+int sse_set_join(sse_handle* h, int mode) {
+  if (!h || mode < SSE_JOIN_AUTO || mode > SSE_JOIN_BACKWARD) return SSE_ERR_INVALID_PARAM;
+  if (mode == SSE_JOIN_BACKWARD && !h->join_down_s) return SSE_ERR_INVALID_PARAM;
+  if (h->close_pending) return SSE_ERR_STATE;
+  if (mode == h->join_mode) return SSE_OK;
+  h->join_mode = mode;
+  if (h->close_exec) {  // captured with the other join
+    cudaGraphExecDestroy(h->close_exec);
+    h->close_exec = nullptr;
+  }
+  if (h->close_g) {
+    cudaGraphDestroy(h->close_g);
+    h->close_g = nullptr;
+  }
   return SSE_OK;
 }
 

@@ -22,6 +22,7 @@ FLAG_SATURATED = 2
 ERR_CAPACITY = -3
 ERR_TIMEOUT = -6
 UPDATE_AUTO, UPDATE_DIRECT, UPDATE_TILED = 0, 1, 2
+JOIN_AUTO, JOIN_FORWARD, JOIN_BACKWARD = 0, 1, 2
 BATCH_DETECT, BATCH_ROUTERS, BATCH_SCAN = 0, 1, 2
 DIR_SRC, DIR_DST, DIR_BOTH = 0, 1, 2
 
@@ -150,6 +151,7 @@ def lib() -> ctypes.CDLL:
             "sse_batch_use_graph": (i32, [vp, i32]),
             "sse_batch_configure": (i32, [vp, u32, i32]),
             "sse_debug_sort_barrier": (i32, [vp, u32, u32]),
+            "sse_set_join": (i32, [vp, i32]),
             "sse_microbench": (i32, [vp, u64, vp, vp]),
             "sse_batch_tune": (i32, [vp, vp, vp, i32, vp, ctypes.POINTER(i32)]),
             "sse_batch_step": (i32, [vp, vp, vp]),
@@ -334,6 +336,11 @@ class Estimator:
 
     def set_update_mode(self, mode: int) -> None:
         _check(self._lib.sse_set_update_mode(self._h, mode), "sse_set_update_mode")
+
+    def set_join(self, mode: int) -> None:
+        """JOIN_AUTO, JOIN_FORWARD (rows 0, 1, 2 up) or JOIN_BACKWARD (rows 0 and r-1 down);
+        identical candidates (sse_set_join)."""
+        _check(self._lib.sse_set_join(self._h, mode), "sse_set_join")
 
     def set_direction(self, direction: int) -> None:
         """DIR_SRC (aip = source, default), DIR_DST (aip = destination) or DIR_BOTH (Definition 1)."""

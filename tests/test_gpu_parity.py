@@ -101,12 +101,13 @@ def test_close_pass_with_a_ragged_last_warp_step():
 
 def test_join_probes_global_any_hot_bitmaps():
     """q - delta = 19: the "any hot" bitmaps of rows 2 and 3 (64 KiB each) are too large to
-    stage in shared memory, so the join probes them in global memory. Hot SREs, counts and
-    reports against the oracle."""
+    stage in shared memory, so the join from row 0 up probes them in global memory. Hot SREs,
+    counts and reports against the oracle."""
     S = sse()
     p = S.Params(r=5, q=23, delta=4, seed=23)
     tr = synth.Traffic(synth.small_trace(seed=23))
     est = S.Estimator(p)
+    est.set_join(S.JOIN_FORWARD)
     orc = oracle.Oracle(oracle_params(p))
     found = 0
     for t in range(3):
