@@ -151,7 +151,8 @@ typedef struct sse_stats {
   uint64_t slice;          /* index of the slice that was closed */
   uint32_t hot[16];        /* |HSE(i)|: hot SREs of RSRA row i (Section 3.3) */
   uint32_t active2[16];    /* active cells of SLEA row i; SF(i,k) = active2[i] / row_len2 (Definition 4) */
-  uint64_t join_pairs;     /* (he_0, he_1) pairs examined to grow candidate tuples */
+  uint64_t join_pairs;     /* pairs the last close's join grew tuples from: (he_0, he_1) from
+                              row 0 up, (he_0, he_{r-1}) of one column block from the top down */
   uint32_t n_candidates;
   uint32_t n_super;
 } sse_stats;

@@ -1039,7 +1039,8 @@ template <int R>
 __global__ void __launch_bounds__(kJoinDownThreads) k_join_down(
     const __grid_constant__ KParams p, const uint32_t* __restrict__ hot_bits, const uint32_t* __restrict__ list0,
     const uint32_t* __restrict__ n_list, const uint32_t* __restrict__ blist, const uint32_t* __restrict__ bcount,
-    uint32_t* __restrict__ cand, uint32_t* __restrict__ n_cand, uint32_t cap, uint32_t* __restrict__ overflow) {
+    uint32_t* __restrict__ cand, uint32_t* __restrict__ n_cand, uint32_t cap, uint32_t* __restrict__ overflow,
+    unsigned long long* __restrict__ n_pairs) {
   static_assert(R >= 4 && R <= 6, "rows");
   __shared__ uint32_t s_queue[kJoinDownThreads / 32][(R - 2) * 2 * kJoinDownQueue];
   __shared__ RegainTable s_rt;
@@ -1051,11 +1052,13 @@ __global__ void __launch_bounds__(kJoinDownThreads) k_join_down(
   const uint32_t top = (R - 1) * p.delta;  // B(R-1) is address bits [top, 32)
   const uint32_t s = 32u - top;
   const uint32_t warps = gridDim.x * (blockDim.x >> 5);
+  uint64_t pairs = 0;
   for (uint32_t i = blockIdx.x * (blockDim.x >> 5) + warp; i < n0; i += warps) {
     const uint32_t he0 = list0[i];
     const uint32_t b = he0 >> s;
     const uint32_t n4 = bcount[b];
     const uint32_t* l4 = blist + ((uint64_t)b << s);
+    pairs += n4;
     for (uint32_t k0 = 0; k0 < n4; k0 += 32 * kJoinDownUnroll) {  // uniform over the warp
       uint32_t a[kJoinDownUnroll], m[kJoinDownUnroll];
 #pragma unroll
@@ -1071,6 +1074,7 @@ __global__ void __launch_bounds__(kJoinDownThreads) k_join_down(
     }
   }
   w.template flush<R - 3>();
+  if (lane == 0 && pairs) atomicAdd(n_pairs, (unsigned long long)pairs);
 }
 
 // ---------------------------------------------------------------- ordering

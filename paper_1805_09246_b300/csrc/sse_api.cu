@@ -260,7 +260,7 @@ uint32_t join_down_bits(const sse_params& p, const sse_derived& d) {
 }
 
 using JoinDownKernel = void (*)(KParams, const uint32_t*, const uint32_t*, const uint32_t*, const uint32_t*,
-                                const uint32_t*, uint32_t*, uint32_t*, uint32_t, uint32_t*);
+                                const uint32_t*, uint32_t*, uint32_t*, uint32_t, uint32_t*, unsigned long long*);
 const JoinDownKernel kJoinDownFns[3] = {k_join_down<4>, k_join_down<5>, k_join_down<6>};
 
 // The close's join: from the top row down where it applies, unless SSE_JOIN_FORWARD is set.
@@ -855,7 +855,7 @@ int close_enqueue(sse_handle* h, uint32_t** sorted, bool copy_counters = true) {
     if (down)
       kJoinDownFns[h->p.r - 4]<<<h->join_down_grid, kJoinDownThreads, 0, h->stream>>>(
           h->kp, h->hot_bits, h->list0, sc->n_list, h->blist, h->bcount, h->cand, &sc->n_cand, h->cand_cap,
-          &sc->overflow);
+          &sc->overflow, &sc->down_pairs);
     else if (h->kp.delta <= 5)
       (h->join_stage ? k_join_tiled<true> : k_join_tiled<false>)<<<h->join_grid, kJoinTiledThreads,
                                                                    h->join_tiled_smem, h->stream>>>(
@@ -900,7 +900,7 @@ int close_collect(sse_handle* h, const uint32_t* sorted, sse_report* out) {
     h->stats.hot[i] = i < (int)h->p.r ? hs.hot[i] : 0;
     h->stats.active2[i] = i < (int)h->p.r2 ? hs.active2[i] : 0;
   }
-  h->stats.join_pairs = (uint64_t)hs.n_list[0] * hs.n_list[1];
+  h->stats.join_pairs = join_down(h) ? hs.down_pairs : (uint64_t)hs.n_list[0] * hs.n_list[1];
   h->stats.n_candidates = n_found;
   h->stats.n_super = hs.n_super;
   if (out) {
@@ -1026,7 +1026,7 @@ int collect_staged(sse_handle* h, const uint32_t* sorted, uint64_t slice, sse_re
     h->stats.hot[i] = i < (int)h->p.r ? hs.hot[i] : 0;
     h->stats.active2[i] = i < (int)h->p.r2 ? hs.active2[i] : 0;
   }
-  h->stats.join_pairs = (uint64_t)hs.n_list[0] * hs.n_list[1];
+  h->stats.join_pairs = join_down(h) ? hs.down_pairs : (uint64_t)hs.n_list[0] * hs.n_list[1];
   h->stats.n_candidates = n_found;
   h->stats.n_super = hs.n_super;
   if (out) {

@@ -175,6 +175,7 @@ struct CloseScratch {
   uint32_t active2[kMaxRows];  // active cells of each SLEA row
   uint32_t hot[kMaxRows];      // hot SREs of each RSRA row
   uint32_t n_list[2];          // entries of the hot lists of rows 0 and 1
+  unsigned long long down_pairs;  // (he_0, he_{r-1}) pairs the join from the top row down started from
   uint32_t n_cand;             // candidate hosts found (may exceed capacity)
   uint32_t n_super;            // candidates flagged super
   uint32_t overflow;           // nonzero when a buffer was too small

@@ -75,6 +75,13 @@ def test_joins_match_brute_force_on_dense_hot_rows(r, q, delta, n_hosts, noise):
     for rep in (rf, rb):
         assert np.array_equal(rep.flags, ref["flags"])
         assert close_enough(rep.est, ref["est"])
+    # the pairs each join started from: HSE(0) x HSE(1), or HSE(0) x HSE(r-1) by column block
+    hot = orc.hot()
+    h0, h1, hl = (np.flatnonzero(hot[i]) for i in (0, 1, r - 1))
+    s, nb = 32 - (r - 1) * delta, 1 << (q - (32 - (r - 1) * delta))
+    by_block = np.dot(np.bincount(h0 >> s, minlength=nb), np.bincount(hl >> s, minlength=nb))
+    assert fwd.stats()["join_pairs"] == len(h0) * len(h1)
+    assert bwd.stats()["join_pairs"] == by_block < len(h0) * len(h1)
 
 
 def test_join_overflow_reports_the_same_count():
