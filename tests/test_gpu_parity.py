@@ -608,6 +608,57 @@ def test_async_close_pipelined_with_next_update():
         assert np.array_equal(x, y)
 
 
+def test_async_reports_interleaved_with_other_closes():
+    """An asynchronous close writes its report on a second stream while the next work runs;
+    synchronous closes (report inside the close graph), closes launched kernel by kernel,
+    slice advances and a reset that follow it must wait for that report. Every report, and
+    the state, equal those of a handle that only closes synchronously; the last reports
+    against the oracle."""
+    S = sse()
+    p = S.Params(q=17, seed=43)
+    tr = synth.Traffic(synth.small_trace(seed=43))
+    pairs = [tr.slice(0, t) for t in range(8)]
+    slices = [helpers.to_device(x) for x in pairs]
+    plan = ["async", "sync", "async", "advance", "async", "direct", "async", "sync"]
+    a, b = S.Estimator(p), S.Estimator(p)
+    orc = oracle.Oracle(oracle_params(p))
+    for t, (x, how) in enumerate(zip(slices, plan)):
+        if t:
+            orc.advance()
+        orc.scan(pairs[t])
+        a.update(x)
+        b.update(x)
+        if how == "advance":
+            a.advance()
+            b.advance()
+            continue
+        ra = a.close_slice()
+        if how == "async":
+            b.close_slice_async()
+            rb = b.close_slice_wait()
+        elif how == "direct":
+            b.close_use_graph(False)
+            rb = b.close_slice()
+            b.close_use_graph(True)
+        else:
+            rb = b.close_slice()
+        assert ra.slice == rb.slice == t
+        assert np.array_equal(ra.hosts, rb.hosts) and np.array_equal(ra.est, rb.est)
+        assert np.array_equal(ra.flags, rb.flags) and ra.n_super == rb.n_super
+        compare_report(rb, orc.detect())
+    for x, y in zip(a.read_stamps(), b.read_stamps()):
+        assert np.array_equal(x, y)
+    b.update(slices[0])
+    b.close_slice_async()
+    b.close_slice_wait()
+    b.reset()  # after an asynchronous report
+    b.update(slices[0])
+    fresh = S.Estimator(p)
+    fresh.update(slices[0])
+    rf, rb = fresh.close_slice(), b.close_slice()
+    assert np.array_equal(rf.hosts, rb.hosts) and np.array_equal(rf.est, rb.est)
+
+
 @pytest.mark.parametrize("rhfg_hash", [0, 1])
 def test_directions_and_tabulation_rhfg0(rhfg_hash):
     """Definition 1 either way: SSE_DIR_DST equals scanning the exchanged pairs, SSE_DIR_BOTH
