@@ -23,21 +23,33 @@ struct CloseWindow {
   Window16 w16;
 };
 
-// One 32-bit word of cells: adds its active cells to `count` and returns the mask that
-// keeps them (all ones over active cells, zero over the rest). 8-bit cells are tested four
-// at a time (active_hi8), 16-bit cells two at a time (active_hi16); WRAP = the window wraps
+// One 32-bit word of cells: the top bit of every active cell (8-bit cells tested four at a
+// time by active_hi8, 16-bit cells two at a time by active_hi16); WRAP = the window wraps
 // over stamp 0.
 template <typename St, bool WRAP>
-__device__ __forceinline__ uint32_t word_keep(uint32_t w, const CloseWindow& win, uint32_t& count) {
-  if constexpr (sizeof(St) == 1) {
-    const uint32_t a = active_hi8<WRAP>(w, win.w8);
-    count += __popc(a);
-    return (a >> 7) * 0xFFu;
-  } else {
-    const uint32_t a = active_hi16<WRAP>(w, win.w16);
-    count += __popc(a);
-    return (a >> 15) * 0xFFFFu;
-  }
+__device__ __forceinline__ uint32_t word_active(uint32_t w, const CloseWindow& win) {
+  if constexpr (sizeof(St) == 1)
+    return active_hi8<WRAP>(w, win.w8);
+  else
+    return active_hi16<WRAP>(w, win.w16);
+}
+
+// The mask that keeps a word's active cells (all ones over them, zero elsewhere) from its
+// top bits: one byte permute (PTX prmt.b32, whose selector nibbles with bit 3 set replicate
+// the selected byte's top bit over the result byte) that copies each cell's top bit over
+// the cell: selectors 8, 9, 10, 11 (byte i from byte i) for 8-bit cells, 9, 9, 11, 11 (both
+// bytes of a cell from its upper byte) for 16-bit cells.
+template <typename St>
+__device__ __forceinline__ uint32_t keep_mask(uint32_t a) {
+  uint32_t r;
+  asm("prmt.b32 %0, %1, 0, %2;" : "=r"(r) : "r"(a), "n"(sizeof(St) == 1 ? 0xBA98 : 0xBB99));
+  return r;
+}
+
+// Active cells of four words' top-bit masks with one population count: shifted by 0..3 the
+// masks' bits (7, 15, 23, 31, or 15, 31) no longer overlap.
+__device__ __forceinline__ uint32_t count4(uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3) {
+  return __popc(a0 | (a1 >> 1) | (a2 >> 2) | (a3 >> 3));
 }
 
 // RSRA part of the pass for 8-bit cells: one SRE (8 bytes) per load, four loads in flight,
@@ -73,10 +85,10 @@ __device__ __forceinline__ void close_rsra8(const KParams& p, uint8_t* __restric
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
         const uint32_t a0 = active_hi8<WRAP>(v[u][h].x, win), a1 = active_hi8<WRAP>(v[u][h].y, win);
-        bal[h] = __ballot_sync(0xFFFFFFFFu, __popc(a0) + __popc(a1) >= p.hot_min);
+        bal[h] = __ballot_sync(0xFFFFFFFFu, (uint32_t)__popc(a0 | (a1 >> 1)) >= p.hot_min);
         if (expire && 64 * j + 32 * h < n_sre) {
           // cells that are set (non-zero) but not active have left the window
-          const uint32_t e0 = v[u][h].x & ~((a0 >> 7) * 0xFFu), e1 = v[u][h].y & ~((a1 >> 7) * 0xFFu);
+          const uint32_t e0 = v[u][h].x & ~keep_mask<uint8_t>(a0), e1 = v[u][h].y & ~keep_mask<uint8_t>(a1);
           if (e0 | e1) words[64 * j + 32 * h + lane] = make_uint2(v[u][h].x ^ e0, v[u][h].y ^ e1);
         }
       }
@@ -90,7 +102,7 @@ __device__ __forceinline__ void close_rsra8(const KParams& p, uint8_t* __restric
   }
 }
 
-// The pass of k_close for one window shape (WRAP: see word_keep).
+// The pass of k_close for one window shape (WRAP: see word_active).
 template <typename St, bool WRAP>
 __device__ __forceinline__ void close_body(const KParams& p, uint8_t* __restrict__ sre, uint8_t* __restrict__ sle,
                                           uint32_t* __restrict__ hot_bits, uint32_t* row_sum,
@@ -119,13 +131,19 @@ __device__ __forceinline__ void close_body(const KParams& p, uint8_t* __restrict
       for (int u = 0; u < kLoads; ++u) {
         const uint64_t g = g0 + u * nthreads;
         if (g >= n_sre) break;  // whole warps (g0 and nthreads are multiples of 32 apart)
-        uint32_t x[kSreInts], keep[kSreInts], weight = 0, expired = 0;
+        uint32_t x[kSreInts], keep[kSreInts], a[kSreInts], expired = 0;
         memcpy(x, &v[u], sizeof(SreWord));
 #pragma unroll
         for (int i = 0; i < kSreInts; ++i) {
-          keep[i] = word_keep<St, WRAP>(x[i], win, weight);
+          a[i] = word_active<St, WRAP>(x[i], win);
+          keep[i] = keep_mask<St>(a[i]);
           expired |= x[i] & ~keep[i];
         }
+        uint32_t weight;
+        if constexpr (kSreInts == 4)
+          weight = count4(a[0], a[1], a[2], a[3]);
+        else
+          weight = __popc(a[0] | (a[1] >> 1));
         const unsigned ballot = __ballot_sync(0xFFFFFFFFu, weight >= p.hot_min);
         if ((mode & 2u) && (threadIdx.x & 31) == 0) hot_bits[g >> 5] = ballot;
         if (expire && expired) {
@@ -148,12 +166,14 @@ __device__ __forceinline__ void close_body(const KParams& p, uint8_t* __restrict
       uint4* cell = reinterpret_cast<uint4*>(sle) + x;
       const uint4 v = *cell;
       uint32_t w[4] = {v.x, v.y, v.z, v.w};
-      uint32_t keep[4], expired = 0;
+      uint32_t a[4], keep[4], expired = 0;
 #pragma unroll
       for (int i = 0; i < 4; ++i) {
-        keep[i] = word_keep<St, WRAP>(w[i], win, count);
+        a[i] = word_active<St, WRAP>(w[i], win);
+        keep[i] = keep_mask<St>(a[i]);
         expired |= w[i] & ~keep[i];
       }
+      count += count4(a[0], a[1], a[2], a[3]);
       if (expire && expired) *cell = make_uint4(w[0] & keep[0], w[1] & keep[1], w[2] & keep[2], w[3] & keep[3]);
     }
 #pragma unroll

@@ -1223,7 +1223,15 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_candidates(uint32_t* __re
 }
 
 // ---------------------------------------------------------------- estimation
-constexpr int kEstThreads = 128;
+constexpr int kEstThreads = 128;      // threads per host, for SLE rows below 16 KiB
+constexpr int kEstThreadsWide = 512;  // for rows of 16 KiB and more (the launch bound below)
+
+// Threads per host of k_estimate: a host's r' rows are gathered in rounds of one 16-byte
+// vector per thread and row, so wide rows (eta' cells of 2 bytes at the paper's
+// eta' = 2^14: 32 KiB) take 4 rounds at 512 threads where they would take 16 at 128.
+__host__ __device__ __forceinline__ int est_threads(uint32_t eta2, uint32_t cell_bytes) {
+  return (uint64_t)eta2 * cell_bytes >= 16384u ? kEstThreadsWide : kEstThreads;
+}
 
 // One CTA per host (grid-stride). hosts: n_ptr ? min(*n_ptr, n) hosts : n hosts. active2:
 // active cells per SLEA row. Outputs (any may be NULL except est): est, flags, w (FP64
@@ -1247,7 +1255,7 @@ __device__ __forceinline__ uint32_t cell_age(uint32_t s, const uint8_t* age_lut,
 }
 
 template <typename St>
-__global__ void __launch_bounds__(kEstThreads, 4) k_estimate(
+__global__ void __launch_bounds__(kEstThreadsWide, 1) k_estimate(
     const __grid_constant__ KParams p, const uint8_t* __restrict__ sle_bytes, const uint32_t* __restrict__ hosts,
     const uint32_t* __restrict__ n_ptr, uint32_t n, const uint32_t* __restrict__ active2, EstTable tab,
     const uint32_t* __restrict__ unsorted, uint32_t* __restrict__ hosts_out, double w_theta,
@@ -1256,7 +1264,7 @@ __global__ void __launch_bounds__(kEstThreads, 4) k_estimate(
     uint32_t* __restrict__ u_out, uint32_t* __restrict__ hist, uint32_t* __restrict__ n_super) {
   __shared__ uint8_t age_lut[256];
   __shared__ uint32_t sh_hist[256];
-  __shared__ uint32_t warp_u[kEstThreads / 32];
+  __shared__ uint32_t warp_u[kEstThreadsWide / 32];
   __shared__ const St* row_base[kMaxRows];
   const St* sle = reinterpret_cast<const St*>(sle_bytes);
   // the count, the stamp and the first host are loaded together (the grid is never larger
@@ -1281,7 +1289,7 @@ __global__ void __launch_bounds__(kEstThreads, 4) k_estimate(
   // Eq. 12's P: the same for every host (and already applied in the table when there is one)
   __shared__ double s_P;
   if (threadIdx.x == 0 && !tab.est) s_P = setting_product(active2, p.r2, p.row_len2);
-  __shared__ uint32_t warp_rank[kEstThreads / 32];
+  __shared__ uint32_t warp_rank[kEstThreadsWide / 32];
   for (uint32_t h = blockIdx.x; h < count; h += gridDim.x) {
     const uint32_t aip = rank_mode ? (h == blockIdx.x ? first_aip : unsorted[h])
                                    : (h == blockIdx.x && !unsorted ? first_aip : hosts[h]);
@@ -1358,7 +1366,7 @@ __global__ void __launch_bounds__(kEstThreads, 4) k_estimate(
                 a3 &= active(v[j].w);
               }
           }
-          c += __popc(a0) + __popc(a1) + __popc(a2) + __popc(a3);
+          c += count4(a0, a1, a2, a3);
         }
         return c;
       };
@@ -1427,10 +1435,12 @@ __global__ void __launch_bounds__(kEstThreads, 4) k_estimate(
       for (uint32_t a = threadIdx.x; a < p.k; a += blockDim.x) hist_row[a] = sh_hist[a];
     if (threadIdx.x == 0) {
       uint32_t U = 0, at = 0;
-      for (int x = 0; x < kEstThreads / 32; ++x) {
-        U += warp_u[x];
-        at += warp_rank[x];
-      }
+#pragma unroll
+      for (uint32_t x = 0; x < kEstThreadsWide / 32; ++x)
+        if (x < (blockDim.x >> 5)) {
+          U += warp_u[x];
+          at += warp_rank[x];
+        }
       const uint32_t slot = rank_mode ? at : h;  // where this host's outputs go
       LcResult res;
       if (tab.est) {  // this close's table

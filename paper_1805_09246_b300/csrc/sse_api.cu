@@ -875,7 +875,9 @@ int close_enqueue(sse_handle* h, uint32_t** sorted, bool copy_counters = true) {
     const int grid = grid_for(h, h->cand_cap, 1, 8);
     const auto est_fn = h->wide ? k_estimate<uint16_t> : k_estimate<uint8_t>;
     // up to kSortChunk candidates: rank mode (h->cand unsorted in, h->cand_out written here)
-    est_fn<<<grid, kEstThreads, 0, h->stream>>>(h->kp, h->sle, *sorted, &sc->n_cand, h->cand_cap, sc->active2,
+    const int threads = est_threads(h->p.eta2, h->wide ? 2 : 1);
+    est_fn<<<threads == kEstThreads ? grid : grid_for(h, h->cand_cap, 1, 2), threads, 0, h->stream>>>(
+        h->kp, h->sle, *sorted, &sc->n_cand, h->cand_cap, sc->active2,
                                                 est_table(h, sc->active2), h->cand, h->cand_out, h->d.w_theta,
                                                 stamp_of(h->slice, h->smod), h->clock, h->est, h->flags, nullptr,
                                                 nullptr, nullptr, &sc->n_super);
@@ -1168,7 +1170,8 @@ int sse_query(sse_handle* h, const uint32_t* d_hosts, uint32_t n, float* d_est, 
   if (rc) return rc;
   const int grid = grid_for(h, n, 1, 16);
   const auto est_fn = h->wide ? k_estimate<uint16_t> : k_estimate<uint8_t>;
-  est_fn<<<grid, kEstThreads, 0, h->stream>>>(h->kp, h->sle, d_hosts, nullptr, n, h->query_active2, EstTable{},
+  est_fn<<<grid, est_threads(h->p.eta2, h->wide ? 2 : 1), 0, h->stream>>>(h->kp, h->sle, d_hosts, nullptr, n,
+                                                                         h->query_active2, EstTable{},
                                                       nullptr, nullptr, h->d.w_theta, stamp_of(h->slice, h->smod), h->clock, d_est, d_flags, nullptr,
                                                       nullptr, d_hist, nullptr);
   SSE_LAUNCHED(h);
@@ -1334,10 +1337,9 @@ extern "C" int sse_query_noalloc(const sse_params* p, const uint8_t* d_sle, uint
       kp, nullptr, const_cast<uint8_t*>(d_sle), nullptr, counts, stamp_of(slice), nullptr, 0u, 0u);
   if (cudaGetLastError() != cudaSuccess) return SSE_ERR_CUDA;
   uint64_t grid = std::min<uint64_t>((uint64_t)n, (uint64_t)num_sms * 16);
-  k_estimate<uint8_t><<<(unsigned)grid, kEstThreads, 0, stream>>>(kp, d_sle, d_hosts, nullptr, n, counts, EstTable{},
-                                                             nullptr, nullptr, d.w_theta,
-                                                             stamp_of(slice), nullptr, d_est, d_flags, nullptr, nullptr,
-                                                             nullptr, nullptr);
+  k_estimate<uint8_t><<<(unsigned)grid, est_threads(q.eta2, 1), 0, stream>>>(
+      kp, d_sle, d_hosts, nullptr, n, counts, EstTable{}, nullptr, nullptr, d.w_theta, stamp_of(slice), nullptr, d_est,
+      d_flags, nullptr, nullptr, nullptr, nullptr);
   if (cudaGetLastError() != cudaSuccess) return SSE_ERR_CUDA;
   return SSE_OK;
 }
