@@ -55,6 +55,7 @@ PLANTED = [
     (5, 20, 4, 5000, 0.004),  # the core link's: s = 16, 16 blocks
     (6, 12, 5, 150, 0.05),    # s = 7, 32 blocks of 128 columns; groups of 32 often hot
     (6, 16, 4, 1000, 0.03),   # s = 12, 16 blocks
+    (6, 19, 5, 800, 0.012),   # s = 7: 4096 blocks, more than the 1024 block-list CTAs (4 each)
 ]
 
 
