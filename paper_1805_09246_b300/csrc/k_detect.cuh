@@ -7,9 +7,11 @@
 // so only its top delta bits are free: the 2^delta choices are looked up in row i's hot
 // bitmap (the paper's overlap test, applied to all of HSE(i) at once). A complete chain
 // fixes bits [delta, 32); the delta low bits are enumerated and a host is kept when
-// RHFG[0] maps it back to he_0, which makes all of its r SREs exactly the chain's.
+// RHFG[0] maps it back to he_0, which makes all of its r SREs exactly the chain's. Where a
+// 32-bit address leaves B(r-1) fewer than q bits, k_join_down finds the same chains from
+// rows 0 and r-1 down (see there); k_join_tiled and k_join grow them from rows 0, 1, 2 up.
 //
-// Estimation (Algorithm 8, Eq. 11-12): one warp per host gathers its r' SLEs; a cell of
+// Estimation (Algorithm 8, Eq. 11-12): one block per host gathers its r' SLEs; a cell of
 // the union SLE counts when it is active in every row, with the largest distance over the
 // rows; the corrected weight and the estimate are computed in FP64 with explicit
 // round-to-nearest operations in a fixed order, so the super point decision is exact.
