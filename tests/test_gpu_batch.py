@@ -44,9 +44,10 @@ def run_reference(p, slices):
 
 
 @pytest.mark.parametrize("graph", [True, False])
-def test_batch_matches_single_router_api_and_oracle(graph):
+@pytest.mark.parametrize("q", [14, 17])  # q = 17, delta = 5: the global close joins from the top row down
+def test_batch_matches_single_router_api_and_oracle(graph, q):
     S = sse()
-    p = S.Params(seed=31)
+    p = S.Params(q=q, seed=31)
     R, T = 5, 6
     slices = router_traffic(R, T, seed=31)
     cap = max(len(x) for s in slices for x in s)

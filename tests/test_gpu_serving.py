@@ -77,11 +77,12 @@ def oracle_reports(p, rs, n_routers, keep=lambda t, r: True):
     return dets, routers
 
 
-def test_server_reports_match_oracle():
+@pytest.mark.parametrize("q", [14, 17])  # q = 17, delta = 5: the global close joins from the top row down
+def test_server_reports_match_oracle(q):
     """Every report of the serving loop (hosts and flags exact, estimates within 1e-6
     relative) against the merged oracle routers fed the same admitted batches."""
     S = sse()
-    p = S.Params(seed=44)
+    p = S.Params(q=q, seed=44)
     rs = stream(seed=44)
     srv = S.Server(p, n_routers=6, slots=3, slot_pairs=8192, memory_budget=1 << 32, slice_seconds=SLICE_S)
     for t, r, start, size in rs.requests:
