@@ -158,3 +158,29 @@ def test_set_join_switches_between_closes():
     small.set_join(S.JOIN_FORWARD)
     with pytest.raises(S.SSEError):
         small.set_join(S.JOIN_BACKWARD)
+
+
+def test_join_edge_cases():
+    """No hot SRE at all; hot SREs in every row but the top one (no pair to start from, and no
+    chain from row 0 up either); a single planted host. Both joins against the brute force."""
+    S = sse()
+    p = S.Params(r=5, q=17, delta=5, k=2, theta=64, seed=81)
+    rng = np.random.default_rng(81)
+    cases = []
+    orc = oracle.Oracle(oracle_params(p))
+    cases.append(("empty", orc, *orc.raw()))
+    orc = oracle.Oracle(oracle_params(p))
+    sre, sle = planted_state(p, orc, rng, 0, 0.03)
+    sre[p.r - 1] = helpers.INF  # the top row holds no hot SRE
+    orc.set_raw(sre, sle)
+    cases.append(("no top row", orc, sre, sle))
+    orc = oracle.Oracle(oracle_params(p))
+    cases.append(("one host", orc, *planted_state(p, orc, rng, 1, 0.0)))
+    for name, orc, sre, sle in cases:
+        want = orc.candidates_brute()
+        assert len(want) == {"empty": 0, "no top row": 0, "one host": 1}[name], name
+        fwd, bwd = estimators(p, sre, sle, [S.JOIN_FORWARD, S.JOIN_BACKWARD])
+        rf, rb = fwd.close_slice(), bwd.close_slice()
+        assert np.array_equal(rf.hosts, want) and np.array_equal(rb.hosts, want), name
+        if name != "one host":
+            assert bwd.stats()["join_pairs"] == 0, name
