@@ -192,6 +192,8 @@ __global__ void __launch_bounds__(kCloseThreads) k_close(const __grid_constant__
                                                           uint32_t* __restrict__ active2, uint32_t cs_value,
                                                           const uint32_t* __restrict__ clock, uint32_t do_sre,
                                                           uint32_t mode) {
+  pdl_wait();
+  pdl_trigger();
   const uint32_t cs = clock ? *clock : cs_value;
   CloseWindow win;
   win.w8 = window8(cs, p.k);    // 8-bit cells

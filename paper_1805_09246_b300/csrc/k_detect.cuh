@@ -348,6 +348,8 @@ __global__ void __launch_bounds__(256) k_hot_prep(const uint32_t* __restrict__ h
                                                   uint32_t n_lists, uint32_t n_regroup, EstTable tab,
                                                   uint32_t* __restrict__ blist, uint32_t* __restrict__ bcount,
                                                   uint32_t n_block, uint32_t s) {
+  pdl_wait();
+  pdl_trigger();
   const uint32_t b = blockIdx.x;
   if (b >= gridDim.x - tab.blocks) {  // the last tab.blocks blocks: the estimate table
     // Eq. 12's P as in setting_product (the same quotients, multiplied in row order), with the
@@ -479,6 +481,8 @@ __global__ void __launch_bounds__(kJoinThreads) k_join(const __grid_constant__ K
                                                        uint32_t* __restrict__ n_cand, uint32_t cap,
                                                        uint32_t* __restrict__ overflow, uint32_t smem_t2,
                                                        uint32_t list1_cap) {
+  pdl_wait();
+  pdl_trigger();
   extern __shared__ uint32_t sm[];
   const uint32_t n0 = n_list[0], n1 = n_list[1];
   if (n0 == 0 || n1 == 0) return;
@@ -551,6 +555,8 @@ __global__ void __launch_bounds__(256) k_report(CloseScratch* __restrict__ sc, c
                                                 const float* __restrict__ est, const uint8_t* __restrict__ flags,
                                                 uint32_t cap, uint32_t n_stage, uint8_t* __restrict__ out,
                                                 uint32_t* __restrict__ tick_clock, uint32_t tick_mod) {
+  pdl_wait();
+  pdl_trigger();
   if (tick_clock && blockIdx.x == 0 && threadIdx.x == 0) *tick_clock = *tick_clock % tick_mod + 1u;
   const uint32_t n = min(min(sc->n_cand, cap), n_stage);
   const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x, stride = gridDim.x * blockDim.x;
@@ -624,6 +630,8 @@ __global__ void __launch_bounds__(kJoinTiledThreads) k_join_tiled(
     const uint32_t* __restrict__ any3, const uint32_t* __restrict__ list0, const uint32_t* __restrict__ list1,
     const uint32_t* __restrict__ n_list, uint32_t* __restrict__ cand, uint32_t* __restrict__ n_cand, uint32_t cap,
     uint32_t* __restrict__ overflow) {
+  pdl_wait();
+  pdl_trigger();
   extern __shared__ uint32_t sm[];
   const uint32_t n0 = n_list[0], n1 = n_list[1];
   if (n0 == 0 || n1 == 0) return;
@@ -1043,6 +1051,8 @@ __global__ void __launch_bounds__(kJoinDownThreads) k_join_down(
     const uint32_t* __restrict__ n_list, const uint32_t* __restrict__ blist, const uint32_t* __restrict__ bcount,
     uint32_t* __restrict__ cand, uint32_t* __restrict__ n_cand, uint32_t cap, uint32_t* __restrict__ overflow,
     unsigned long long* __restrict__ n_pairs) {
+  pdl_wait();
+  pdl_trigger();
   static_assert(R >= 4 && R <= 6, "rows");
   __shared__ uint32_t s_queue[kJoinDownThreads / 32][(R - 2) * 2 * kJoinDownQueue];
   __shared__ RegainTable s_rt;
@@ -1143,6 +1153,8 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_candidates(uint32_t* __re
                                                                   uint32_t* __restrict__ error,
                                                                   uint32_t small_by_estimate,
                                                                   const uint32_t* __restrict__ ctl) {
+  pdl_wait();
+  pdl_trigger();
   __shared__ uint32_t s[kSortChunk];
   const uint32_t n = min(*n_ptr, cap);
   if (n <= kSortChunk) {
@@ -1264,6 +1276,8 @@ __global__ void __launch_bounds__(kEstThreadsWide, 1) k_estimate(
     uint32_t cs_value, const uint32_t* __restrict__ clock, float* __restrict__ est, uint8_t* __restrict__ flags,
     double* __restrict__ w_out,
     uint32_t* __restrict__ u_out, uint32_t* __restrict__ hist, uint32_t* __restrict__ n_super) {
+  pdl_wait();
+  pdl_trigger();
   __shared__ uint8_t age_lut[256];
   __shared__ uint32_t sh_hist[256];
   __shared__ uint32_t warp_u[kEstThreadsWide / 32];

@@ -106,6 +106,8 @@ __global__ void __launch_bounds__(kTiledThreads, 1) k_update_tiled(const __grid_
                                                                    const uint32_t* __restrict__ clock,
                                                                    uint8_t* __restrict__ sre2_bytes,
                                                                    uint32_t* __restrict__ gbits2) {
+  pdl_wait();
+  pdl_trigger();
   const St stamp = (St)(clock ? *clock : stamp_value);
   St* sre = reinterpret_cast<St*>(sre_bytes);
   St* sre2 = reinterpret_cast<St*>(sre2_bytes);  // may be NULL: see the flush
@@ -233,6 +235,8 @@ template <typename St>
 __global__ void __launch_bounds__(256) k_apply_bits(uint32_t* __restrict__ gbits, uint8_t* __restrict__ sle,
                                                     uint64_t n_words, uint32_t stamp_value,
                                                     const uint32_t* __restrict__ clock) {
+  pdl_wait();
+  pdl_trigger();
   constexpr int kCellsPerVec = 16 / sizeof(St);  // 16 or 8
   constexpr int kVecs = 32 / kCellsPerVec;       // 2 or 4
   constexpr int kCellsPerInt = 4 / sizeof(St);   // 4 or 2

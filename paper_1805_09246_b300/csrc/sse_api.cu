@@ -266,6 +266,26 @@ const JoinDownKernel kJoinDownFns[3] = {k_join_down<4>, k_join_down<5>, k_join_d
 // The close's join: from the top row down where it applies, unless SSE_JOIN_FORWARD is set.
 bool join_down(const sse_handle* h) { return h->join_down_s != 0 && h->join_mode != SSE_JOIN_FORWARD; }
 
+// Launches `kernel` after the previous kernel on `stream` with programmatic stream
+// serialization: its blocks may be scheduled once every block of the previous kernel has
+// called pdl_trigger(), and each waits in pdl_wait() for that kernel's completion before it
+// touches memory, so the launch latency overlaps the previous kernel instead of following it.
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t stream,
+                       Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
+
 int grid_for(const sse_handle* h, uint64_t work, int block, int per_sm) {
   uint64_t g = (work + block - 1) / block;
   uint64_t cap = (uint64_t)h->num_sms * per_sm;
@@ -338,7 +358,8 @@ int launch_update_tiled(sse_handle* h, const uint32_t* d_pairs, uint64_t n, int 
   }
   const uint64_t words = h->sle_cells / 32;
   const auto apply = h->wide ? k_apply_bits<uint16_t> : k_apply_bits<uint8_t>;
-  apply<<<grid_for(h, words, 256, 8), 256, 0, h->stream>>>(h->sle_bits, h->sle, words, stamp, h->clock);
+  SSE_CUDA(h, launch_pdl(apply, dim3(grid_for(h, words, 256, 8)), dim3(256), 0, h->stream, h->sle_bits, h->sle,
+                         words, stamp, (const uint32_t*)h->clock));
   SSE_LAUNCHED(h);
   return SSE_OK;
 }
@@ -848,24 +869,28 @@ int close_enqueue(sse_handle* h, uint32_t** sorted, bool copy_counters = true) {
     const uint32_t any_each = (any_words(h->p.q, h->p.delta) + 255) / 256;
     const uint32_t n_any = !down && h->any2 ? (h->any3 ? 2 * any_each : any_each) : 0u;
     const EstTable tab = est_table(h, sc->active2);
-    k_hot_prep<<<n_lists + n_regroup + n_block + n_any + tab.blocks, 256, 0, h->stream>>>(
-        h->hot_bits, h->p.r, h->p.q, h->p.delta, sc->hot, h->list0, h->list1, sc->n_list, h->tables,
-        down ? nullptr : h->any2, h->any3, n_lists, n_regroup, tab, h->blist, h->bcount, n_block, s);
+    SSE_CUDA(h, launch_pdl(k_hot_prep, dim3(n_lists + n_regroup + n_block + n_any + tab.blocks), dim3(256), 0,
+                           h->stream, (const uint32_t*)h->hot_bits, h->p.r, h->p.q, h->p.delta, sc->hot, h->list0,
+                           h->list1, sc->n_list, h->tables, down ? nullptr : h->any2, h->any3, n_lists, n_regroup,
+                           tab, h->blist, h->bcount, n_block, s));
     SSE_LAUNCHED(h);
     if (down)
-      kJoinDownFns[h->p.r - 4]<<<h->join_down_grid, kJoinDownThreads, 0, h->stream>>>(
-          h->kp, h->hot_bits, h->list0, sc->n_list, h->blist, h->bcount, h->cand, &sc->n_cand, h->cand_cap,
-          &sc->overflow, &sc->down_pairs);
+      SSE_CUDA(h, launch_pdl(kJoinDownFns[h->p.r - 4], dim3(h->join_down_grid), dim3(kJoinDownThreads), 0, h->stream,
+                             h->kp, (const uint32_t*)h->hot_bits, (const uint32_t*)h->list0,
+                             (const uint32_t*)sc->n_list, (const uint32_t*)h->blist, (const uint32_t*)h->bcount,
+                             h->cand, &sc->n_cand, h->cand_cap, &sc->overflow, &sc->down_pairs));
     else if (h->kp.delta <= 5)
-      (h->join_stage ? k_join_tiled<true> : k_join_tiled<false>)<<<h->join_grid, kJoinTiledThreads,
-                                                                   h->join_tiled_smem, h->stream>>>(
-          h->kp, h->tables, h->any2, h->any3, h->list0, h->list1, sc->n_list, h->cand, &sc->n_cand, h->cand_cap,
-          &sc->overflow);
+      SSE_CUDA(h, launch_pdl(h->join_stage ? k_join_tiled<true> : k_join_tiled<false>, dim3(h->join_grid),
+                             dim3(kJoinTiledThreads), h->join_tiled_smem, h->stream, h->kp,
+                             (const uint32_t*)h->tables, (const uint32_t*)h->any2, (const uint32_t*)h->any3,
+                             (const uint32_t*)h->list0, (const uint32_t*)h->list1, (const uint32_t*)sc->n_list,
+                             h->cand, &sc->n_cand, h->cand_cap, &sc->overflow));
     else
-      k_join<<<h->num_sms, kJoinThreads, h->join_smem, h->stream>>>(h->kp, h->hot_bits, h->tables, h->any3, h->list0,
-                                                                    h->list1, sc->n_list, h->cand, &sc->n_cand,
-                                                                    h->cand_cap, &sc->overflow, h->join_smem_t2,
-                                                                    h->join_list1_cap);
+      SSE_CUDA(h, launch_pdl(k_join, dim3(h->num_sms), dim3(kJoinThreads), h->join_smem, h->stream, h->kp,
+                             (const uint32_t*)h->hot_bits, (const uint32_t*)h->tables, (const uint32_t*)h->any3,
+                             (const uint32_t*)h->list0, (const uint32_t*)h->list1, (const uint32_t*)sc->n_list,
+                             h->cand, &sc->n_cand, h->cand_cap, &sc->overflow, h->join_smem_t2,
+                             h->join_list1_cap));
     SSE_LAUNCHED(h);
   }
   rc = launch_sort(h);
@@ -876,11 +901,12 @@ int close_enqueue(sse_handle* h, uint32_t** sorted, bool copy_counters = true) {
     const auto est_fn = h->wide ? k_estimate<uint16_t> : k_estimate<uint8_t>;
     // up to kSortChunk candidates: rank mode (h->cand unsorted in, h->cand_out written here)
     const int threads = est_threads(h->p.eta2, h->wide ? 2 : 1);
-    est_fn<<<threads == kEstThreads ? grid : grid_for(h, h->cand_cap, 1, 2), threads, 0, h->stream>>>(
-        h->kp, h->sle, *sorted, &sc->n_cand, h->cand_cap, sc->active2,
-                                                est_table(h, sc->active2), h->cand, h->cand_out, h->d.w_theta,
-                                                stamp_of(h->slice, h->smod), h->clock, h->est, h->flags, nullptr,
-                                                nullptr, nullptr, &sc->n_super);
+    SSE_CUDA(h, launch_pdl(est_fn, dim3(threads == kEstThreads ? grid : grid_for(h, h->cand_cap, 1, 2)),
+                           dim3(threads), 0, h->stream, h->kp, (const uint8_t*)h->sle, (const uint32_t*)*sorted,
+                           (const uint32_t*)&sc->n_cand, h->cand_cap, (const uint32_t*)sc->active2,
+                           est_table(h, sc->active2), (const uint32_t*)h->cand, h->cand_out, h->d.w_theta,
+                           stamp_of(h->slice, h->smod), (const uint32_t*)h->clock, h->est, h->flags,
+                           (double*)nullptr, (uint32_t*)nullptr, (uint32_t*)nullptr, &sc->n_super));
     SSE_LAUNCHED(h);
   }
   if (copy_counters)
@@ -957,8 +983,9 @@ int close_graph_launch(sse_handle* h) {
     if (e == cudaSuccess) {
       rc = close_enqueue(h, &h->close_sorted, false);
       if (rc == SSE_OK) {
-        k_report<<<8, 256, 0, h->stream>>>(h->scratch, h->close_sorted, h->est, h->flags, h->cand_cap,
-                                           h->report_stage_n, h->report_stage_dev, h->clock, h->smod);
+        SSE_CUDA(h, launch_pdl(k_report, dim3(8), dim3(256), 0, h->stream, h->scratch,
+                               (const uint32_t*)h->close_sorted, (const float*)h->est, (const uint8_t*)h->flags,
+                               h->cand_cap, h->report_stage_n, h->report_stage_dev, h->clock, h->smod));
         SSE_LAUNCHED(h);
       }
       cudaGraph_t g = nullptr;

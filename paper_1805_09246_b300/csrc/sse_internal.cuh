@@ -163,6 +163,15 @@ __host__ __device__ __forceinline__ uint32_t active_hi16(uint32_t w, Window16 wi
   return win.wrap ? active_hi16<true>(w, win) : active_hi16<false>(w, win);
 }
 
+// Programmatic dependent launch. A kernel launched with programmatic stream serialization
+// may be scheduled before the previous kernel on its stream has finished; pdl_wait(), called
+// before the kernel touches memory, returns once that kernel has completed and its writes
+// are visible (for an ordinary launch it returns at once). pdl_trigger() lets the next
+// kernel be scheduled once every block of this one has called it (so no block of this
+// kernel can be kept waiting for room by the next one's blocks).
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 // The estimator's device clock holds the current stamp; advancing a slice moves it along the
 // 1..mod cycle on the device, so launches read the right stamp even when replayed.
 __global__ void k_tick(uint32_t* clock, uint32_t n, uint32_t mod = 255u) {
