@@ -228,9 +228,10 @@ __global__ void __launch_bounds__(kTiledThreads, 1) k_update_tiled(const __grid_
   }
 }
 
-// Stamp every SLEA cell whose bit is set and clear the bitmap. One thread per bitmap word
-// (32 cells: two 16-byte vectors of 8-bit stamps or four of 16-bit stamps); each word has a
-// single owner.
+// Stamp every SLEA cell whose bit is set and clear the bitmap. One thread per 16-byte vector
+// of cells (16 8-bit or 8 16-bit stamps), so a warp reads and writes 512 contiguous bytes;
+// the 2 or 4 lanes that share a bitmap word read it together, and the first of them clears
+// it after the warp has read it.
 template <typename St>
 __global__ void __launch_bounds__(256) k_apply_bits(uint32_t* __restrict__ gbits, uint8_t* __restrict__ sle,
                                                     uint64_t n_words, uint32_t stamp_value,
@@ -238,33 +239,34 @@ __global__ void __launch_bounds__(256) k_apply_bits(uint32_t* __restrict__ gbits
   pdl_wait();
   pdl_trigger();
   constexpr int kCellsPerVec = 16 / sizeof(St);  // 16 or 8
-  constexpr int kVecs = 32 / kCellsPerVec;       // 2 or 4
+  constexpr int kVecs = 32 / kCellsPerVec;       // vectors per bitmap word: 2 or 4
   constexpr int kCellsPerInt = 4 / sizeof(St);   // 4 or 2
   constexpr uint32_t kCellMask = sizeof(St) == 1 ? 0xFFu : 0xFFFFu;
   const uint32_t stamp = clock ? *clock : stamp_value;
   const uint32_t fill = sizeof(St) == 1 ? stamp * 0x01010101u : stamp * 0x00010001u;
-  for (uint64_t w = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; w < n_words;
-       w += (uint64_t)gridDim.x * blockDim.x) {
-    const uint32_t bits = gbits[w];
-    if (!bits) continue;
-    uint4* cells = reinterpret_cast<uint4*>(sle + (w << 5) * sizeof(St));
+  const uint64_t n_vecs = n_words * kVecs;
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;  // a multiple of 32
+  // warp-uniform loop: every lane of a warp takes the same number of steps
+  for (uint64_t v0 = (uint64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); v0 < n_vecs; v0 += stride) {
+    const uint64_t v = v0 + (threadIdx.x & 31u);
+    const bool ok = v < n_vecs;
+    const uint32_t bits = ok ? gbits[v / kVecs] : 0u;
+    __syncwarp();  // every lane sharing the word has read it
+    if (ok && bits && v % kVecs == 0) gbits[v / kVecs] = 0;
+    const uint32_t hb = (bits >> (kCellsPerVec * (uint32_t)(v % kVecs))) & ((1u << kCellsPerVec) - 1u);
+    if (!hb) continue;
+    uint4* cells = reinterpret_cast<uint4*>(sle) + v;
+    const uint4 c = *cells;
+    uint32_t x[4] = {c.x, c.y, c.z, c.w};
 #pragma unroll
-    for (int h = 0; h < kVecs; ++h) {
-      const uint32_t hb = (bits >> (kCellsPerVec * h)) & ((1u << kCellsPerVec) - 1u);
-      if (!hb) continue;
-      uint4 v = cells[h];
-      uint32_t x[4] = {v.x, v.y, v.z, v.w};
+    for (int q = 0; q < 4; ++q) {
+      const uint32_t nib = (hb >> (kCellsPerInt * q)) & ((1u << kCellsPerInt) - 1u);
+      uint32_t mask = 0;  // all ones in the cells whose bit is set
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const uint32_t nib = (hb >> (kCellsPerInt * q)) & ((1u << kCellsPerInt) - 1u);
-        uint32_t mask = 0;  // all ones in the cells whose bit is set
-#pragma unroll
-        for (int b = 0; b < kCellsPerInt; ++b) mask |= ((nib >> b) & 1u) ? kCellMask << (8 * sizeof(St) * b) : 0u;
-        x[q] = (x[q] & ~mask) | (fill & mask);
-      }
-      cells[h] = make_uint4(x[0], x[1], x[2], x[3]);
+      for (int b = 0; b < kCellsPerInt; ++b) mask |= ((nib >> b) & 1u) ? kCellMask << (8 * sizeof(St) * b) : 0u;
+      x[q] = (x[q] & ~mask) | (fill & mask);
     }
-    gbits[w] = 0;
+    *cells = make_uint4(x[0], x[1], x[2], x[3]);
   }
 }
 
