@@ -52,6 +52,18 @@ __device__ __forceinline__ uint32_t count4(uint32_t a0, uint32_t a1, uint32_t a2
   return __popc(a0 | (a1 >> 1) | (a2 >> 2) | (a3 >> 3));
 }
 
+// A word's top-bit mask packed into one bit per cell, in cell order: for 8-bit cells the
+// bits at 0, 8, 16, 24 of a >> 7, multiplied by 1 + 2^7 + 2^14 + 2^21, land on bits 21..24
+// without carries (every other term of the product falls below bit 21 on a bit of its own,
+// or above bit 24); for 16-bit cells bits 0 and 16, times 1 + 2^15, land on bits 15, 16.
+template <typename St>
+__device__ __forceinline__ uint32_t pack_active(uint32_t a) {
+  if constexpr (sizeof(St) == 1)
+    return (((a >> 7) * 0x204081u) >> 21) & 0xFu;
+  else
+    return (((a >> 15) * 0x8001u) >> 15) & 0x3u;
+}
+
 // RSRA part of the pass for 8-bit cells: one SRE (8 bytes) per load, four loads in flight,
 // 32-bit indices. A warp covers 64 consecutive SREs 64j .. 64j + 63 per step: lane l holds
 // SREs 64j + l and 64j + 32 + l, so its two ballots are the two hot-bitmap words of those
@@ -106,7 +118,8 @@ __device__ __forceinline__ void close_rsra8(const KParams& p, uint8_t* __restric
 template <typename St, bool WRAP>
 __device__ __forceinline__ void close_body(const KParams& p, uint8_t* __restrict__ sre, uint8_t* __restrict__ sle,
                                           uint32_t* __restrict__ hot_bits, uint32_t* row_sum,
-                                          const CloseWindow& win, uint32_t do_sre, uint32_t mode) {
+                                          const CloseWindow& win, uint32_t do_sre, uint32_t mode,
+                                          uint32_t* __restrict__ sle_act) {
   using SreWord = typename std::conditional<sizeof(St) == 1, uint2, uint4>::type;
   constexpr int kSreInts = sizeof(SreWord) / 4;
   const bool expire = (mode & 1u) != 0;
@@ -156,12 +169,14 @@ __device__ __forceinline__ void close_body(const KParams& p, uint8_t* __restrict
     }
   }
   // SLEA: 16 bytes per thread; a row pitch is a multiple of 4096 cells, so a warp's
-  // 512 bytes lie in one row
+  // 512 bytes lie in one row. With sle_act, the cells' activity also goes to a bitmap (bit c
+  // for cell c of the SLEA): a lane's 16 or 8 bits, two or four lanes to a word.
   const uint64_t n_vec = (uint64_t)p.r2 * p.row_pitch2 * sizeof(St) / 16;
   const uint64_t vec_per_row = p.row_pitch2 * sizeof(St) / 16;
+  constexpr uint32_t kVecCells = 16 / sizeof(St);  // cells per lane: 16 or 8
   for (uint64_t x0 = tid - (threadIdx.x & 31); x0 < n_vec; x0 += nthreads) {
     const uint64_t x = x0 + (threadIdx.x & 31);
-    uint32_t count = 0;
+    uint32_t count = 0, act = 0;
     if (x < n_vec) {
       uint4* cell = reinterpret_cast<uint4*>(sle) + x;
       const uint4 v = *cell;
@@ -175,6 +190,14 @@ __device__ __forceinline__ void close_body(const KParams& p, uint8_t* __restrict
       }
       count += count4(a[0], a[1], a[2], a[3]);
       if (expire && expired) *cell = make_uint4(w[0] & keep[0], w[1] & keep[1], w[2] & keep[2], w[3] & keep[3]);
+      constexpr uint32_t kIntCells = kVecCells / 4;
+#pragma unroll
+      for (int i = 0; i < 4; ++i) act |= pack_active<St>(a[i]) << (kIntCells * i);
+    }
+    if (sle_act) {  // warp-uniform
+      act |= __shfl_down_sync(0xFFFFFFFFu, act, 1) << kVecCells;
+      if constexpr (kVecCells == 8) act |= __shfl_down_sync(0xFFFFFFFFu, act, 2) << 16;
+      if ((threadIdx.x & (32 / kVecCells - 1)) == 0 && x < n_vec) sle_act[x * kVecCells / 32] = act;
     }
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) count += __shfl_xor_sync(0xFFFFFFFFu, count, off);
@@ -183,7 +206,8 @@ __device__ __forceinline__ void close_body(const KParams& p, uint8_t* __restrict
 }
 
 // mode bit 0: write back expired cells; bit 1: write the hot bitmap. do_sre != 0: the
-// RSRA is processed as well as the SLEA. Grid-stride over both arrays (any grid size).
+// RSRA is processed as well as the SLEA. sle_act (may be NULL): the SLEA cells' activity
+// bitmap, for the close's estimate. Grid-stride over both arrays (any grid size).
 // Cells are St (8 or 16 bits); one SRE is 8 cells (a 64- or 128-bit word).
 template <typename St>
 __global__ void __launch_bounds__(kCloseThreads) k_close(const __grid_constant__ KParams p,
@@ -191,7 +215,7 @@ __global__ void __launch_bounds__(kCloseThreads) k_close(const __grid_constant__
                                                           uint32_t* __restrict__ hot_bits,
                                                           uint32_t* __restrict__ active2, uint32_t cs_value,
                                                           const uint32_t* __restrict__ clock, uint32_t do_sre,
-                                                          uint32_t mode) {
+                                                          uint32_t mode, uint32_t* __restrict__ sle_act) {
   pdl_wait();
   pdl_trigger();
   const uint32_t cs = clock ? *clock : cs_value;
@@ -203,9 +227,9 @@ __global__ void __launch_bounds__(kCloseThreads) k_close(const __grid_constant__
   __syncthreads();
   const bool wrap = sizeof(St) == 1 ? win.w8.wrap != 0 : win.w16.wrap != 0;
   if (wrap)
-    close_body<St, true>(p, sre, sle, hot_bits, row_sum, win, do_sre, mode);
+    close_body<St, true>(p, sre, sle, hot_bits, row_sum, win, do_sre, mode, sle_act);
   else
-    close_body<St, false>(p, sre, sle, hot_bits, row_sum, win, do_sre, mode);
+    close_body<St, false>(p, sre, sle, hot_bits, row_sum, win, do_sre, mode, sle_act);
   __syncthreads();
   if (threadIdx.x < p.r2 && row_sum[threadIdx.x]) atomicAdd(&active2[threadIdx.x], row_sum[threadIdx.x]);
 }

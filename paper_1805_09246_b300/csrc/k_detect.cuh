@@ -1268,20 +1268,24 @@ __device__ __forceinline__ uint32_t cell_age(uint32_t s, const uint8_t* age_lut,
   }
 }
 
-template <typename St>
+// ACT: U from the close pass's activity bitmap (sle_act), the close's own estimate;
+// otherwise from the stamps (queries, features, histograms).
+template <typename St, bool ACT = false>
 __global__ void __launch_bounds__(kEstThreadsWide, 1) k_estimate(
     const __grid_constant__ KParams p, const uint8_t* __restrict__ sle_bytes, const uint32_t* __restrict__ hosts,
     const uint32_t* __restrict__ n_ptr, uint32_t n, const uint32_t* __restrict__ active2, EstTable tab,
     const uint32_t* __restrict__ unsorted, uint32_t* __restrict__ hosts_out, double w_theta,
     uint32_t cs_value, const uint32_t* __restrict__ clock, float* __restrict__ est, uint8_t* __restrict__ flags,
     double* __restrict__ w_out,
-    uint32_t* __restrict__ u_out, uint32_t* __restrict__ hist, uint32_t* __restrict__ n_super) {
+    uint32_t* __restrict__ u_out, uint32_t* __restrict__ hist, uint32_t* __restrict__ n_super,
+    const uint32_t* __restrict__ sle_act) {
   pdl_wait();
   pdl_trigger();
   __shared__ uint8_t age_lut[256];
   __shared__ uint32_t sh_hist[256];
   __shared__ uint32_t warp_u[kEstThreadsWide / 32];
   __shared__ const St* row_base[kMaxRows];
+  __shared__ uint64_t row_cell[kMaxRows];  // the host's SLE start in each row, as an SLEA cell index
   const St* sle = reinterpret_cast<const St*>(sle_bytes);
   // the count, the stamp and the first host are loaded together (the grid is never larger
   // than the host buffers, so index blockIdx.x is in bounds even past the count)
@@ -1295,7 +1299,9 @@ __global__ void __launch_bounds__(kEstThreadsWide, 1) k_estimate(
   // `hosts` is already sorted and the outputs go to the host's own index
   const bool rank_mode = unsorted != nullptr && count <= kSortChunk && hist == nullptr;
   const bool vec16 = (p.delta2 & 15u) == 0;
-  const bool u_only = vec16 && !hist;  // U from byte-wise or half-word-wise activity masks
+  // U alone: from the close pass's activity bitmap when given, else from byte-wise or
+  // half-word-wise activity masks of the stamps
+  const bool u_only = ACT || (vec16 && !hist);
   if (sizeof(St) == 1 && !u_only)
     for (uint32_t s = threadIdx.x; s < 256; s += blockDim.x) {
       const uint32_t a = stamp_age(s, cs);
@@ -1334,7 +1340,8 @@ __global__ void __launch_bounds__(kEstThreadsWide, 1) k_estimate(
       }
     if (threadIdx.x < p.r2) {
       const uint32_t j = mas_top(p.key_a[kLH + threadIdx.x], p.key_b[kLH + threadIdx.x], aip, p.q2);
-      row_base[threadIdx.x] = sle + threadIdx.x * p.row_pitch2 + (uint64_t)j * p.delta2;
+      row_cell[threadIdx.x] = threadIdx.x * p.row_pitch2 + (uint64_t)j * p.delta2;
+      row_base[threadIdx.x] = sle + row_cell[threadIdx.x];
     }
     // per-distance counts: in shared memory for windows up to 256 slices, else straight
     // into this host's output row (zeroed first)
@@ -1352,6 +1359,31 @@ __global__ void __launch_bounds__(kEstThreadsWide, 1) k_estimate(
     constexpr int kVecCells = 16 / sizeof(St);  // cells per 16-byte load
     constexpr int kIntCells = 4 / sizeof(St);
     constexpr uint32_t kMask = sizeof(St) == 1 ? 0xFFu : 0xFFFFu;
+    if constexpr (ACT) {
+      // U only, from the activity bitmap of this close (bit c: SLEA cell c is active): a union
+      // cell counts when it is active in every row, so the rows' bits are ANDed. Row i's eta'
+      // bits start at bit row_cell[i], at any alignment: each 32-bit piece is a funnel shift
+      // of two words (the bitmap has a word of padding after the last row)
+      const uint32_t n_words = p.eta2 >> 5;
+      for (uint32_t k = threadIdx.x; k < n_words; k += blockDim.x) {
+        uint32_t m = 0xFFFFFFFFu;
+        for (uint32_t i0 = 0; i0 < p.r2; i0 += 4) {  // 4 rows' loads in flight
+          uint32_t lo[4], hi[4], sh[4];
+#pragma unroll
+          for (uint32_t j = 0; j < 4; ++j)
+            if (i0 + j < p.r2) {
+              const uint64_t b = row_cell[i0 + j] + ((uint64_t)k << 5);
+              sh[j] = (uint32_t)b & 31u;
+              lo[j] = sle_act[b >> 5];
+              hi[j] = sle_act[(b >> 5) + 1];
+            }
+#pragma unroll
+          for (uint32_t j = 0; j < 4; ++j)
+            if (i0 + j < p.r2) m &= __funnelshift_r(lo[j], hi[j], sh[j]);
+        }
+        u += __popc(m);
+      }
+    } else {  // from the stamps
     if (u_only) {
       // U only: a union cell counts when it is active in every row, so the rows' activity
       // masks (active_hi8 for 8-bit cells, active_hi16 for 16-bit ones: the top bit of every
@@ -1432,6 +1464,7 @@ __global__ void __launch_bounds__(kEstThreadsWide, 1) k_estimate(
           if (hist) atomicAdd(hist_smem ? &sh_hist[m] : &hist_row[m], 1u);
         }
       }
+    }
     }
     if (rank_mode) {
       rank_batch(0, false);  // the keys loaded before the gathers

@@ -129,6 +129,7 @@ struct sse_handle {
   uint8_t* sle = nullptr;
   uint32_t* hot_bits = nullptr;
   uint32_t* sle_bits = nullptr;  // touched-cell bitmap of SLEA for the tiled update (kept zero)
+  uint32_t* sle_act = nullptr;   // activity bitmap of SLEA cells, written by a close's pass for its estimate
   TileGeometry tiles;
   uint32_t* list0 = nullptr;
   uint32_t* list1 = nullptr;
@@ -412,7 +413,8 @@ int launch_close_pass(sse_handle* h, uint32_t* active2, uint32_t mode) {
   const auto fn = h->wide ? k_close<uint16_t> : k_close<uint8_t>;
   fn<<<(unsigned)(h->num_sms * 8), kCloseThreads, 0, h->stream>>>(h->kp, h->sre, h->sle, h->hot_bits, active2,
                                                                   stamp_of(h->slice, h->smod), h->clock,
-                                                                  mode ? 1u : 0u, mode);
+                                                                  mode ? 1u : 0u, mode,
+                                                                  (mode & 2u) ? h->sle_act : nullptr);
   SSE_LAUNCHED(h);
   return SSE_OK;
 }
@@ -509,6 +511,7 @@ void sse_destroy(sse_handle* h) {
   cudaFree(h->clock);
   cudaFree(h->hot_bits);
   cudaFree(h->sle_bits);
+  cudaFree(h->sle_act);
   cudaFree(h->list0);
   cudaFree(h->list1);
   cudaFree(h->tables);
@@ -564,6 +567,7 @@ int sse_init(const sse_params* p, void* cuda_stream, sse_handle** out) {
   bool ok = cudaMalloc(&h->state, state_bytes) == cudaSuccess && cudaMalloc(&h->clock, 256) == cudaSuccess &&
             cudaMalloc(&h->hot_bits, ((uint64_t)q.r << q.q) / 8) == cudaSuccess &&
             cudaMalloc(&h->sle_bits, h->sle_cells / 8) == cudaSuccess &&
+            cudaMalloc(&h->sle_act, h->sle_cells / 8 + 8) == cudaSuccess &&  // + a word read past the last row
             cudaMalloc(&h->list0, list_entries * 4) == cudaSuccess &&
             cudaMalloc(&h->list1, list_entries * 4) == cudaSuccess &&
             cudaMalloc(&h->tables, (q.r - 2) * (list_entries / 8)) == cudaSuccess &&
@@ -898,7 +902,7 @@ int close_enqueue(sse_handle* h, uint32_t** sorted, bool copy_counters = true) {
   *sorted = h->cand_out;
   {
     const int grid = grid_for(h, h->cand_cap, 1, 8);
-    const auto est_fn = h->wide ? k_estimate<uint16_t> : k_estimate<uint8_t>;
+    const auto est_fn = h->wide ? k_estimate<uint16_t, true> : k_estimate<uint8_t, true>;
     // up to kSortChunk candidates: rank mode (h->cand unsorted in, h->cand_out written here)
     const int threads = est_threads(h->p.eta2, h->wide ? 2 : 1);
     SSE_CUDA(h, launch_pdl(est_fn, dim3(threads == kEstThreads ? grid : grid_for(h, h->cand_cap, 1, 2)),
@@ -906,7 +910,8 @@ int close_enqueue(sse_handle* h, uint32_t** sorted, bool copy_counters = true) {
                            (const uint32_t*)&sc->n_cand, h->cand_cap, (const uint32_t*)sc->active2,
                            est_table(h, sc->active2), (const uint32_t*)h->cand, h->cand_out, h->d.w_theta,
                            stamp_of(h->slice, h->smod), (const uint32_t*)h->clock, h->est, h->flags,
-                           (double*)nullptr, (uint32_t*)nullptr, (uint32_t*)nullptr, &sc->n_super));
+                           (double*)nullptr, (uint32_t*)nullptr, (uint32_t*)nullptr, &sc->n_super,
+                           (const uint32_t*)h->sle_act));
     SSE_LAUNCHED(h);
   }
   if (copy_counters)
@@ -1200,7 +1205,7 @@ int sse_query(sse_handle* h, const uint32_t* d_hosts, uint32_t n, float* d_est, 
   est_fn<<<grid, est_threads(h->p.eta2, h->wide ? 2 : 1), 0, h->stream>>>(h->kp, h->sle, d_hosts, nullptr, n,
                                                                          h->query_active2, EstTable{},
                                                       nullptr, nullptr, h->d.w_theta, stamp_of(h->slice, h->smod), h->clock, d_est, d_flags, nullptr,
-                                                      nullptr, d_hist, nullptr);
+                                                      nullptr, d_hist, nullptr, nullptr);
   SSE_LAUNCHED(h);
   return SSE_OK;
 }
@@ -1361,12 +1366,12 @@ extern "C" int sse_query_noalloc(const sse_params* p, const uint8_t* d_sle, uint
     return SSE_ERR_CUDA;
   }
   k_close<uint8_t><<<(unsigned)(num_sms * 8), kCloseThreads, 0, stream>>>(
-      kp, nullptr, const_cast<uint8_t*>(d_sle), nullptr, counts, stamp_of(slice), nullptr, 0u, 0u);
+      kp, nullptr, const_cast<uint8_t*>(d_sle), nullptr, counts, stamp_of(slice), nullptr, 0u, 0u, nullptr);
   if (cudaGetLastError() != cudaSuccess) return SSE_ERR_CUDA;
   uint64_t grid = std::min<uint64_t>((uint64_t)n, (uint64_t)num_sms * 16);
   k_estimate<uint8_t><<<(unsigned)grid, est_threads(q.eta2, 1), 0, stream>>>(
       kp, d_sle, d_hosts, nullptr, n, counts, EstTable{}, nullptr, nullptr, d.w_theta, stamp_of(slice), nullptr, d_est,
-      d_flags, nullptr, nullptr, nullptr, nullptr);
+      d_flags, nullptr, nullptr, nullptr, nullptr, nullptr);
   if (cudaGetLastError() != cudaSuccess) return SSE_ERR_CUDA;
   return SSE_OK;
 }
