@@ -209,8 +209,9 @@ __device__ __forceinline__ void close_body(const KParams& p, uint8_t* __restrict
 // RSRA is processed as well as the SLEA. sle_act (may be NULL): the SLEA cells' activity
 // bitmap, for the close's estimate. Grid-stride over both arrays (any grid size).
 // Cells are St (8 or 16 bits); one SRE is 8 cells (a 64- or 128-bit word).
+// 8-bit cells: eight blocks per SM (32 registers), the occupancy of the launch's grid.
 template <typename St>
-__global__ void __launch_bounds__(kCloseThreads) k_close(const __grid_constant__ KParams p,
+__global__ void __launch_bounds__(kCloseThreads, sizeof(St) == 1 ? 8 : 1) k_close(const __grid_constant__ KParams p,
                                                           uint8_t* __restrict__ sre, uint8_t* __restrict__ sle,
                                                           uint32_t* __restrict__ hot_bits,
                                                           uint32_t* __restrict__ active2, uint32_t cs_value,
