@@ -1271,7 +1271,7 @@ __device__ __forceinline__ uint32_t cell_age(uint32_t s, const uint8_t* age_lut,
 // ACT: U from the close pass's activity bitmap (sle_act), the close's own estimate;
 // otherwise from the stamps (queries, features, histograms).
 template <typename St, bool ACT = false>
-__global__ void __launch_bounds__(kEstThreadsWide, 1) k_estimate(
+__global__ void __launch_bounds__(kEstThreadsWide, ACT ? 2 : 1) k_estimate(
     const __grid_constant__ KParams p, const uint8_t* __restrict__ sle_bytes, const uint32_t* __restrict__ hosts,
     const uint32_t* __restrict__ n_ptr, uint32_t n, const uint32_t* __restrict__ active2, EstTable tab,
     const uint32_t* __restrict__ unsorted, uint32_t* __restrict__ hosts_out, double w_theta,
