@@ -152,6 +152,8 @@ __global__ void __launch_bounds__(kTrainThreads) k_mlp_grad_partial(MlpShape s, 
                                                                      const uint32_t* __restrict__ rows, uint32_t n,
                                                                      float* __restrict__ partial,
                                                                      float* __restrict__ loss_partial) {
+  pdl_wait();
+  pdl_trigger();
   extern __shared__ __align__(16) float train_sm[];
   const uint32_t H = HC ? (uint32_t)HC : s.hidden, D = DC ? (uint32_t)DC : s.n_in;
   constexpr uint32_t S = kTrainSamples;
@@ -330,6 +332,8 @@ __global__ void __launch_bounds__(kSumThreads) k_mlp_reduce_grads(uint32_t total
                                                                   const float* __restrict__ partial,
                                                                   const float* __restrict__ loss_partial,
                                                                   float* __restrict__ g, float* __restrict__ loss) {
+  pdl_wait();
+  pdl_trigger();
   const uint32_t k = blockIdx.x * kSumParams + (threadIdx.x & 31u);
   const float gk = sum_parts_block(partial, n_parts, total, k);
   if (threadIdx.x < 32 && k < total) g[k] = gk;
@@ -351,6 +355,8 @@ __global__ void __launch_bounds__(kSumThreads) k_mlp_adam(uint32_t total, float*
                                                           const float* __restrict__ partial, uint32_t n_parts,
                                                           const float* __restrict__ loss_partial,
                                                           float* __restrict__ loss) {
+  pdl_wait();
+  pdl_trigger();
   const uint32_t k = blockIdx.x * kSumParams + (threadIdx.x & 31u);
   if (partial && loss && blockIdx.x == gridDim.x - 1 && threadIdx.x == 32) *loss = sum_loss(loss_partial, n_parts);
   float gk = 0.f;
@@ -372,7 +378,10 @@ __global__ void __launch_bounds__(kSumThreads) k_mlp_adam(uint32_t total, float*
   wb[k] = __float2bfloat16_rn(w);
 }
 
-__global__ void k_mlp_step_add(uint32_t* step_base, uint32_t n) { *step_base += n; }
+__global__ void k_mlp_step_add(uint32_t* step_base, uint32_t n) {
+  pdl_wait();
+  *step_base += n;
+}
 
 __global__ void k_mlp_to_bf16(uint32_t total, const float* __restrict__ wf, __nv_bfloat16* __restrict__ wb) {
   const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;

@@ -2381,22 +2381,22 @@ int mlp_grad_partial(sse_mlp* m, const float* d_x, const float* d_t, const uint3
                      cudaStream_t st, uint32_t* parts) {
   *parts = (n + kTrainSamples - 1) / kTrainSamples;
   const auto fn = (m->s.hidden == 64 && m->s.n_in == 18) ? k_mlp_grad_partial<64, 18> : k_mlp_grad_partial<0, 0>;
-  fn<<<*parts, kTrainThreads, train_smem_floats(m->s) * 4, st>>>(m->s, m->wb, d_x, d_t, d_rows, n, m->partial,
-                                                                  m->loss_partial);
+  const cudaError_t e = launch_pdl(fn, dim3(*parts), dim3(kTrainThreads), train_smem_floats(m->s) * 4, st, m->s,
+                                   (const __nv_bfloat16*)m->wb, d_x, d_t, d_rows, n, m->partial, m->loss_partial);
   m->launches += 1;
-  return cudaGetLastError() == cudaSuccess ? SSE_OK : SSE_ERR_CUDA;
+  return e == cudaSuccess ? SSE_OK : SSE_ERR_CUDA;
 }
 
 // Part 2: Adam step number *d_step + step_off on the summed shares (parts > 0) or on m->g
 // (parts == 0); the learning rate from *lr_dev when given, else lr.
 int mlp_adam(sse_mlp* m, const float* lr_dev, float lr, uint32_t step_off, cudaStream_t st, uint32_t parts,
              float* d_loss) {
-  k_mlp_adam<<<(m->s.total + kSumParams - 1) / kSumParams, kSumThreads, 0, st>>>(m->s.total, m->wf, m->wb, m->g,
-                                                                               m->m, m->v, lr_dev, lr,
-                                                       m->d_step, step_off, 0.9f, 0.999f, 1e-8f,
-                                                       parts ? m->partial : nullptr, parts, m->loss_partial, d_loss);
+  const cudaError_t e =
+      launch_pdl(k_mlp_adam, dim3((m->s.total + kSumParams - 1) / kSumParams), dim3(kSumThreads), 0, st, m->s.total,
+                 m->wf, m->wb, m->g, m->m, m->v, lr_dev, lr, (const uint32_t*)m->d_step, step_off, 0.9f, 0.999f,
+                 1e-8f, parts ? (const float*)m->partial : nullptr, parts, (const float*)m->loss_partial, d_loss);
   m->launches += 1;
-  return cudaGetLastError() == cudaSuccess ? SSE_OK : SSE_ERR_CUDA;
+  return e == cudaSuccess ? SSE_OK : SSE_ERR_CUDA;
 }
 
 int mlp_step_add(sse_mlp* m, uint32_t n, cudaStream_t st) {
