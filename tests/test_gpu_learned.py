@@ -136,6 +136,33 @@ def test_adam_step_follows_update_rule():
     assert np.array_equal(bits.astype(np.uint32) << 16, omlp.bf16(f).astype(np.float32).view(np.uint32))
 
 
+def test_epoch_replay_equals_the_steps():
+    """sse_mlp_train_epoch replays an epoch from one CUDA graph (each minibatch's gradient
+    shares, then Adam summing them, with programmatic dependent launch between the kernels):
+    parameters, gradients and loss equal, bit for bit, the same minibatches taken one step at a
+    time through sse_mlp_gradients and sse_mlp_adam. Two epochs, the last minibatch of each
+    partial."""
+    sse = S()
+    n, batch, lr = 3000, 512, 2e-3
+    rng = np.random.default_rng(8)
+    x = torch.from_numpy(rng.uniform(0, 8, (n, 18)).astype(np.float32)).cuda()
+    t = torch.from_numpy(rng.normal(0, 1, n).astype(np.float32)).cuda()
+    w32 = random_net(18, 64, 9)
+    a = sse.MLP(18, hidden=64, max_batch=batch, seed=4)
+    b = sse.MLP(18, hidden=64, max_batch=batch, seed=4)
+    a.set_params(w32)
+    b.set_params(w32)
+    for _ in range(2):
+        perm = torch.from_numpy(rng.permutation(n).astype(np.int32)).cuda()
+        la = a.train_epoch(x, t, perm, batch, lr)
+        for b0 in range(0, n, batch):
+            lb = b.gradients(x, t, rows=perm[b0:b0 + batch])
+            b.adam(lr)
+        assert la == lb
+        for pa, pb in zip(a.params(), b.params()):
+            assert np.array_equal(pa, pb)
+
+
 def test_training_lowers_loss_and_learned_beats_linear_counting():
     """A network trained on GPU episodes (the library's own kernels) has a lower median
     relative error on held-out episodes than plain linear counting, and a much lower one on
