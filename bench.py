@@ -10,7 +10,8 @@ delta'=16, window k=8, theta=1024, 8-bit stamps.
 
 Prints one JSON line. Under torchrun (N > 1) every rank runs its own router's trace
 (independent estimators: weak scaling, no data-path collective); the time is the max
-over ranks. --impl reference times the CPU oracle (tests' checker) on a bounded sample.
+over ranks. --impl reference times the CPU oracle (tests' checker) on the host's cores,
+one oracle estimator per thread, on a bounded sample.
 
 After the timed core-link steps the same line also carries, measured on the same GPU: the
 roofs of the update's units (sse_microbench), a paced serving leg (32 routers at the offered
@@ -190,60 +191,128 @@ def make_traffic(rank: int):
     return synth.Traffic(synth.core_link(seed=rank))
 
 
-def run_reference(args, rank, world):
-    """The CPU oracle as it stands, single-threaded, on a bounded sample of each slice."""
+CPU_THREADS_MAX = 64  # host threads for the oracle timings (one oracle estimator each, ~90 MiB)
+
+
+def host_cores() -> int:
+    """The host cores this process may run on."""
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def oracle_threads(threads: int | None) -> int:
+    return max(1, min(threads or host_cores(), CPU_THREADS_MAX))
+
+
+def core_link_oracle_params():
+    import oracle
+    return oracle.Params(q=20, q2=16, eta2=4096, k=8, theta=1024, seed=0)
+
+
+def run_reference(args, rank, world, threads: int | None = None):
+    """The CPU oracle as it stands on the host's cores, on a bounded sample of each slice:
+    one oracle estimator per thread (the data-parallel use of the unchanged oracle, one
+    router per core; its C scan loop runs without Python's interpreter lock). In every step
+    each thread scans the first 2^21 pairs of a core-link slice (thread i starts i slices
+    further on) and advances its slice."""
     if rank != 0:
         return
+    import threading
+
     import oracle
     tr = make_traffic(0)
     sample = 1 << 21
-    o = oracle.Oracle(oracle.Params(q=20, q2=16, eta2=4096, k=8, theta=1024, seed=0))
-    data = [tr.slice(0, t)[:sample].copy() for t in range(min(args.warmup + args.steps, 16))]
-    for w in range(args.warmup):
-        o.scan(data[w % len(data)])
-        o.advance()
+    n_thr = oracle_threads(threads)
+    data = [tr.slice(0, t)[:sample].copy() for t in range(16)]
+    orcs = [oracle.Oracle(core_link_oracle_params()) for _ in range(n_thr)]
+    start, done = threading.Barrier(n_thr + 1), threading.Barrier(n_thr + 1)
+
+    def work(i):
+        o = orcs[i]
+        for w in range(args.warmup):
+            o.scan(data[(i + w) % len(data)])
+            o.advance()
+        start.wait()
+        for s in range(args.steps):
+            o.scan(data[(i + args.warmup + s) % len(data)])
+            o.advance()
+        done.wait()
+
+    pool = [threading.Thread(target=work, args=(i,)) for i in range(n_thr)]
+    for t in pool:
+        t.start()
+    start.wait()
     t0 = time.perf_counter()
-    for s in range(args.steps):
-        o.scan(data[(args.warmup + s) % len(data)])
-        o.advance()
+    done.wait()
     dt = time.perf_counter() - t0
-    value = args.steps * sample / dt / 1e9
-    desc = (f"oracle scan (Alg. 3 + Alg. 6) of the first {sample} pairs of each core-link slice plus the "
-            "per-slice distance increment; detection is not timed: the oracle's tuple growth is "
-            "O(|HSE|^3) at this size")
+    for t in pool:
+        t.join()
+    value = n_thr * args.steps * sample / dt / 1e9
+    desc = (f"{n_thr} oracle estimator{'s' if n_thr > 1 else ''}, one per host thread, each scanning (Alg. 3 + Alg. 6) the first {sample} "
+            "pairs of a core-link slice per step plus the per-slice distance increment; detection is not "
+            "timed: the oracle's tuple growth is O(|HSE|^3) at this size")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": round(value, 6), "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt / args.steps * 1e3, 3),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
         "config": {"workload": CORE_LINK_WORKLOAD, "pairs_per_step": PAIRS_PER_SLICE,
                    "l2": "inputs larger than L2 (256 MiB per step)"},
-        "sample_pairs_per_step": sample,
-        "cpu_baseline": {"value": round(value, 6), "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc},
+        "sample_pairs_per_step": n_thr * sample,
+        "cpu_baseline": {"value": round(value, 6), "unit": UNIT, "cores": n_thr, "kind": "oracle", "sample": desc},
         "e2e": {"value": round(value, 6), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
 
 
-def cpu_baseline(tr_slices, min_seconds=12.0, min_slices=8, max_slices=64):
-    """The oracle's update loop, single-threaded, over full slices of the workload (the
-    generated slices in turn, again from the first when they run out) until at least
-    min_seconds of CPU work and min_slices slices are done."""
+def cpu_baseline(tr_slices, min_seconds=12.0, min_slices=8, max_slices=64, threads: int | None = None):
+    """The oracle's update loop on the host's cores over full slices of the workload: one
+    oracle estimator per thread, each scanning the generated slices in turn (thread i
+    starts i slices further on, again from the first when they run out) and advancing its
+    slice after each, until min_seconds have passed and min_slices slices are done in all
+    (at most max_slices per thread). The rate is all threads' pairs over the wall time from
+    the common start until the last thread ends."""
+    import threading
+
     import oracle
-    o = oracle.Oracle(oracle.Params(q=20, q2=16, eta2=4096, k=8, theta=1024, seed=0))
-    n = 0
-    t = 0
-    t0 = time.perf_counter()
-    while t < max_slices and (t < min_slices or time.perf_counter() - t0 < min_seconds):
-        if t:
-            o.advance()
-        s = tr_slices[t % len(tr_slices)]
-        o.scan(s)
-        n += len(s)
-        t += 1
-    dt = time.perf_counter() - t0
-    return {"value": round(n / dt / 1e9, 6), "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"oracle scan + slice increment over {t} full core-link slices "
-                      f"(the {len(tr_slices)} generated ones in turn; {n} pairs, {dt:.1f} s); "
-                      f"detection excluded (tuple growth is O(|HSE|^3) here)"}
+    n_thr = oracle_threads(threads)
+    orcs = [oracle.Oracle(core_link_oracle_params()) for _ in range(n_thr)]
+    pairs, slices = [0] * n_thr, [0] * n_thr
+    lock = threading.Lock()
+    total = [0]
+    start = threading.Barrier(n_thr + 1)
+    t0 = [0.0]
+
+    def work(i):
+        o = orcs[i]
+        start.wait()
+        t = 0
+        while t < max_slices:
+            with lock:
+                if total[0] >= min_slices and time.perf_counter() - t0[0] >= min_seconds:
+                    break
+                total[0] += 1
+            if t:
+                o.advance()
+            s = tr_slices[(i + t) % len(tr_slices)]
+            o.scan(s)
+            pairs[i] += len(s)
+            t += 1
+        slices[i] = t
+
+    pool = [threading.Thread(target=work, args=(i,)) for i in range(n_thr)]
+    for t in pool:
+        t.start()
+    t0[0] = time.perf_counter()
+    start.wait()
+    for t in pool:
+        t.join()
+    dt = time.perf_counter() - t0[0]
+    n, n_slices = sum(pairs), sum(slices)
+    return {"value": round(n / dt / 1e9, 6), "unit": UNIT, "cores": n_thr, "kind": "oracle",
+            "sample": f"{n_thr} oracle estimator{'s' if n_thr > 1 else ''}, one per host thread, oracle scan + slice increment over "
+                      f"{n_slices} full core-link slices in all (the {len(tr_slices)} generated ones in turn; "
+                      f"{n} pairs, {dt:.1f} s); detection excluded (tuple growth is O(|HSE|^3) here)"}
 
 
 def main_edge_routers(args, rank, world, local):

@@ -65,15 +65,26 @@ def test_two_gloo_ranks_max_time_summed_work_and_rank_traces():
 
 
 def test_cpu_baseline_runs_until_its_time_and_slice_minimums():
-    """The CPU baseline scans slices in turn (from the first again when the given ones run
-    out) until both the minimum time and the minimum slice count are reached."""
+    """The CPU baseline's threads scan slices in turn (from the first again when the given
+    ones run out) until both the minimum time and the minimum slice count (over all
+    threads) are reached; `cores` is the number of threads that ran."""
     import numpy as np
     sys.path.insert(0, ROOT)
     import bench
     rng = np.random.default_rng(3)
     slices = [rng.integers(0, 2**32, (4096, 2), dtype=np.uint64).astype(np.uint32) for _ in range(2)]
-    r = bench.cpu_baseline(slices, min_seconds=0.0, min_slices=5, max_slices=64)
-    assert "over 5 full core-link slices" in r["sample"] and r["cores"] == 1 and r["value"] > 0
-    r = bench.cpu_baseline(slices, min_seconds=0.3, min_slices=1, max_slices=64)
+    r = bench.cpu_baseline(slices, min_seconds=0.0, min_slices=5, max_slices=64, threads=1)
+    assert "over 5 full core-link slices in all" in r["sample"] and r["cores"] == 1 and r["value"] > 0
+    r = bench.cpu_baseline(slices, min_seconds=0.3, min_slices=1, max_slices=64, threads=2)
+    assert r["cores"] == 2 and r["sample"].startswith("2 oracle estimators")
     n = int(r["sample"].split(" over ")[1].split()[0])
-    assert n >= 1 and float(r["sample"].split("pairs, ")[1].split(" s)")[0]) >= 0.3 or n == 64
+    assert n >= 1 and float(r["sample"].split("pairs, ")[1].split(" s)")[0]) >= 0.3 or n == 2 * 64
+    r = bench.cpu_baseline(slices, min_seconds=0.0, min_slices=7, max_slices=2, threads=3)
+    assert r["cores"] == 3 and int(r["sample"].split(" over ")[1].split()[0]) == 6  # 3 threads x at most 2
+
+
+def test_oracle_threads_bounded_by_host_cores_and_cap():
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench.oracle_threads(None) == min(bench.host_cores(), bench.CPU_THREADS_MAX)
+    assert bench.oracle_threads(3) == 3 and bench.oracle_threads(10**6) == bench.CPU_THREADS_MAX
