@@ -180,11 +180,6 @@ SSE_API void sse_destroy(sse_handle* h);
  * the r SREs RSRA[i, RHFG[i](aip)], cell H2(bip), only if LSB(H1(bip)) >= tau;
  * Algorithm 6 for SLEA: cell H3(bip) of SLE LH_i(aip) in every row i). Every touched cell
  * is stamped with the current slice; repeated and concurrent writes are idempotent.
- * The tiled update (SSE_UPDATE_TILED, and AUTO on large batches) first collects a slice's
- * SLEA cells as bits and writes their stamps later: in the slice close's pass, which reads
- * the SLEA anyway, or at the start of any other call that reads the SLEA (query, merge,
- * features, export, read_stamps), so every result is the same as with immediate stamps.
- * Estimators of a batch or a server stamp at each update as before.
  * d_pairs: device memory, 2*n_pairs uint32 {src, dst, src, dst, ...}, 8-byte aligned.
  * Asynchronous on the handle's stream. n_pairs == 0 is a no-op.
  * Errors: INVALID_PARAM (NULL with n_pairs > 0, misaligned), CUDA.

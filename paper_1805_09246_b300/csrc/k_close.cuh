@@ -64,18 +64,6 @@ __device__ __forceinline__ uint32_t pack_active(uint32_t a) {
     return (((a >> 15) * 0x8001u) >> 15) & 0x3u;
 }
 
-// All ones over the cells of a 32-bit word whose bit is set in `bits` (bit i for cell i):
-// for 8-bit cells bits 0..3, multiplied by 1 + 2^7 + 2^14 + 2^21, land on bits 0, 8, 16, 24
-// without carries (the sixteen partial products sit on distinct bits), and times 0xFF fill
-// their bytes; for 16-bit cells bits 0, 1 times 1 + 2^15 land on bits 0 and 16.
-template <typename St>
-__device__ __forceinline__ uint32_t cell_mask(uint32_t bits) {
-  if constexpr (sizeof(St) == 1)
-    return ((bits * 0x204081u) & 0x01010101u) * 0xFFu;
-  else
-    return ((bits * 0x8001u) & 0x00010001u) * 0xFFFFu;
-}
-
 // RSRA part of the pass for 8-bit cells: one SRE (8 bytes) per load, four loads in flight,
 // 32-bit indices. A warp covers 64 consecutive SREs 64j .. 64j + 63 per step: lane l holds
 // SREs 64j + l and 64j + 32 + l, so its two ballots are the two hot-bitmap words of those
@@ -131,8 +119,7 @@ template <typename St, bool WRAP>
 __device__ __forceinline__ void close_body(const KParams& p, uint8_t* __restrict__ sre, uint8_t* __restrict__ sle,
                                           uint32_t* __restrict__ hot_bits, uint32_t* row_sum,
                                           const CloseWindow& win, uint32_t do_sre, uint32_t mode,
-                                          uint32_t* __restrict__ sle_act, uint32_t* __restrict__ pend,
-                                          uint32_t fill) {
+                                          uint32_t* __restrict__ sle_act) {
   using SreWord = typename std::conditional<sizeof(St) == 1, uint2, uint4>::type;
   constexpr int kSreInts = sizeof(SreWord) / 4;
   const bool expire = (mode & 1u) != 0;
@@ -187,29 +174,13 @@ __device__ __forceinline__ void close_body(const KParams& p, uint8_t* __restrict
   const uint64_t n_vec = (uint64_t)p.r2 * p.row_pitch2 * sizeof(St) / 16;
   const uint64_t vec_per_row = p.row_pitch2 * sizeof(St) / 16;
   constexpr uint32_t kVecCells = 16 / sizeof(St);  // cells per lane: 16 or 8
-  constexpr uint32_t kIntCells = kVecCells / 4;   // cells per 32-bit word: 4 or 2
-  constexpr uint32_t kLanesPerWord = 32 / kVecCells;  // lanes whose cells share a bitmap word: 2 or 4
   for (uint64_t x0 = tid - (threadIdx.x & 31); x0 < n_vec; x0 += nthreads) {
     const uint64_t x = x0 + (threadIdx.x & 31);
     uint32_t count = 0, act = 0;
-    uint32_t pbits = 0;  // this lane's cells touched by tiled updates of this slice, not yet stamped
-    if (pend) {          // warp-uniform: the lanes sharing a word read it, then the first clears it
-      const uint32_t word = x < n_vec ? pend[x / kLanesPerWord] : 0u;
-      __syncwarp();
-      if (word && x % kLanesPerWord == 0) pend[x / kLanesPerWord] = 0u;
-      pbits = (word >> (kVecCells * (uint32_t)(x % kLanesPerWord))) & ((1u << kVecCells) - 1u);
-    }
     if (x < n_vec) {
       uint4* cell = reinterpret_cast<uint4*>(sle) + x;
       const uint4 v = *cell;
       uint32_t w[4] = {v.x, v.y, v.z, v.w};
-      if (pbits) {  // the stamps of the pending cells first (the current stamp: active below)
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-          const uint32_t m = cell_mask<St>((pbits >> (kIntCells * i)) & ((1u << kIntCells) - 1u));
-          w[i] = (w[i] & ~m) | (fill & m);
-        }
-      }
       uint32_t a[4], keep[4], expired = 0;
 #pragma unroll
       for (int i = 0; i < 4; ++i) {
@@ -218,10 +189,8 @@ __device__ __forceinline__ void close_body(const KParams& p, uint8_t* __restrict
         expired |= w[i] & ~keep[i];
       }
       count += count4(a[0], a[1], a[2], a[3]);
-      if (expire && expired)
-        *cell = make_uint4(w[0] & keep[0], w[1] & keep[1], w[2] & keep[2], w[3] & keep[3]);
-      else if (pbits)
-        *cell = make_uint4(w[0], w[1], w[2], w[3]);
+      if (expire && expired) *cell = make_uint4(w[0] & keep[0], w[1] & keep[1], w[2] & keep[2], w[3] & keep[3]);
+      constexpr uint32_t kIntCells = kVecCells / 4;
 #pragma unroll
       for (int i = 0; i < 4; ++i) act |= pack_active<St>(a[i]) << (kIntCells * i);
     }
@@ -238,10 +207,7 @@ __device__ __forceinline__ void close_body(const KParams& p, uint8_t* __restrict
 
 // mode bit 0: write back expired cells; bit 1: write the hot bitmap. do_sre != 0: the
 // RSRA is processed as well as the SLEA. sle_act (may be NULL): the SLEA cells' activity
-// bitmap, for the close's estimate. pend (may be NULL; only with mode bit 0): the tiled
-// update's touched-cell bitmap of this slice; its cells are stamped with the current stamp
-// before they are tested (what k_apply_bits would have written) and the bitmap is cleared.
-// Grid-stride over both arrays (any grid size).
+// bitmap, for the close's estimate. Grid-stride over both arrays (any grid size).
 // Cells are St (8 or 16 bits); one SRE is 8 cells (a 64- or 128-bit word).
 // 8-bit cells: eight blocks per SM (32 registers), the occupancy of the launch's grid.
 template <typename St>
@@ -250,8 +216,7 @@ __global__ void __launch_bounds__(kCloseThreads, sizeof(St) == 1 ? 8 : 1) k_clos
                                                           uint32_t* __restrict__ hot_bits,
                                                           uint32_t* __restrict__ active2, uint32_t cs_value,
                                                           const uint32_t* __restrict__ clock, uint32_t do_sre,
-                                                          uint32_t mode, uint32_t* __restrict__ sle_act,
-                                                          uint32_t* __restrict__ pend) {
+                                                          uint32_t mode, uint32_t* __restrict__ sle_act) {
   pdl_wait();
   pdl_trigger();
   const uint32_t cs = clock ? *clock : cs_value;
@@ -262,11 +227,10 @@ __global__ void __launch_bounds__(kCloseThreads, sizeof(St) == 1 ? 8 : 1) k_clos
   if (threadIdx.x < kMaxRows) row_sum[threadIdx.x] = 0;
   __syncthreads();
   const bool wrap = sizeof(St) == 1 ? win.w8.wrap != 0 : win.w16.wrap != 0;
-  const uint32_t fill = sizeof(St) == 1 ? (cs & 0xFFu) * 0x01010101u : (cs & 0xFFFFu) * 0x00010001u;
   if (wrap)
-    close_body<St, true>(p, sre, sle, hot_bits, row_sum, win, do_sre, mode, sle_act, pend, fill);
+    close_body<St, true>(p, sre, sle, hot_bits, row_sum, win, do_sre, mode, sle_act);
   else
-    close_body<St, false>(p, sre, sle, hot_bits, row_sum, win, do_sre, mode, sle_act, pend, fill);
+    close_body<St, false>(p, sre, sle, hot_bits, row_sum, win, do_sre, mode, sle_act);
   __syncthreads();
   if (threadIdx.x < p.r2 && row_sum[threadIdx.x]) atomicAdd(&active2[threadIdx.x], row_sum[threadIdx.x]);
 }

@@ -129,13 +129,6 @@ struct sse_handle {
   uint8_t* sle = nullptr;
   uint32_t* hot_bits = nullptr;
   uint32_t* sle_bits = nullptr;  // touched-cell bitmap of SLEA for the tiled update (kept zero)
-  // Deferred stamping: a tiled update leaves its touched cells in sle_bits (bits_pending)
-  // and the next close pass stamps them while it reads the SLEA anyway; every other call
-  // that reads the SLEA stamps them first (flush_bits). Off for the batch's and the
-  // server's estimators, which apply their bitmaps themselves.
-  bool defer_apply = true;
-  bool bits_pending = false;
-  cudaEvent_t ev_flushed = nullptr;  // a merge source's deferred stamps are written
   uint32_t* sle_act = nullptr;   // activity bitmap of SLEA cells, written by a close's pass for its estimate
   TileGeometry tiles;
   uint32_t* list0 = nullptr;
@@ -350,22 +343,6 @@ constexpr int kNumTiledVariants = sizeof(kTiledVariants) / sizeof(kTiledVariants
 // Update variants seen by the autotuner: 0 = direct, 1 + v = tiled variant v.
 constexpr int kNumUpdateVariants = 1 + kNumTiledVariants;
 
-// Stamps every SLEA cell whose bit is set in the tiled update's bitmap with the current
-// stamp, and clears the bitmap.
-int launch_apply(sse_handle* h) {
-  const uint64_t words = h->sle_cells / 32;
-  const auto apply = h->wide ? k_apply_bits<uint16_t> : k_apply_bits<uint8_t>;
-  SSE_CUDA(h, launch_pdl(apply, dim3(grid_for(h, words, 256, 8)), dim3(256), 0, h->stream, h->sle_bits, h->sle,
-                         words, stamp_of(h->slice, h->smod), (const uint32_t*)h->clock));
-  SSE_LAUNCHED(h);
-  h->bits_pending = false;
-  return SSE_OK;
-}
-
-// Before a call that reads the SLEA stamps (or replaces them): the deferred stamps of this
-// slice's tiled updates.
-int flush_bits(sse_handle* h) { return h->bits_pending ? launch_apply(h) : SSE_OK; }
-
 int launch_update_tiled(sse_handle* h, const uint32_t* d_pairs, uint64_t n, int variant) {
   const uint32_t stamp = stamp_of(h->slice, h->smod);
   const TileGeometry& g = h->tiles;
@@ -380,11 +357,12 @@ int launch_update_tiled(sse_handle* h, const uint32_t* d_pairs, uint64_t n, int 
                                                                h->mirror_bits);
     SSE_LAUNCHED(h);
   }
-  if (h->defer_apply) {  // stamped by the next close pass, or by flush_bits before a read
-    h->bits_pending = true;
-    return SSE_OK;
-  }
-  return launch_apply(h);
+  const uint64_t words = h->sle_cells / 32;
+  const auto apply = h->wide ? k_apply_bits<uint16_t> : k_apply_bits<uint8_t>;
+  SSE_CUDA(h, launch_pdl(apply, dim3(grid_for(h, words, 256, 8)), dim3(256), 0, h->stream, h->sle_bits, h->sle,
+                         words, stamp, (const uint32_t*)h->clock));
+  SSE_LAUNCHED(h);
+  return SSE_OK;
 }
 
 // Batches of at least this many pairs use the tiled update in SSE_UPDATE_AUTO mode unless
@@ -433,20 +411,11 @@ int launch_update(sse_handle* h, const uint32_t* d_pairs, uint64_t n) {
 // bit only the SLEA counts are needed and RSRA is skipped.
 int launch_close_pass(sse_handle* h, uint32_t* active2, uint32_t mode) {
   const auto fn = h->wide ? k_close<uint16_t> : k_close<uint8_t>;
-  // an expiring pass also stamps the cells left pending by tiled updates (deferred handles
-  // always pass the bitmap, so a captured close stamps whatever its replay finds there)
-  const bool fuse = (mode & 1u) && h->defer_apply;
-  if (!fuse) {
-    const int rc = flush_bits(h);
-    if (rc) return rc;
-  }
   fn<<<(unsigned)(h->num_sms * 8), kCloseThreads, 0, h->stream>>>(h->kp, h->sre, h->sle, h->hot_bits, active2,
                                                                   stamp_of(h->slice, h->smod), h->clock,
                                                                   mode ? 1u : 0u, mode,
-                                                                  (mode & 2u) ? h->sle_act : nullptr,
-                                                                  fuse ? h->sle_bits : nullptr);
+                                                                  (mode & 2u) ? h->sle_act : nullptr);
   SSE_LAUNCHED(h);
-  if (fuse) h->bits_pending = false;
   return SSE_OK;
 }
 
@@ -566,7 +535,6 @@ void sse_destroy(sse_handle* h) {
   if (h->capture_stream) cudaStreamDestroy(h->capture_stream);
   if (h->report_stage) cudaFreeHost(h->report_stage);
   if (h->close_done) cudaEventDestroy(h->close_done);
-  if (h->ev_flushed) cudaEventDestroy(h->ev_flushed);
   delete h;
 }
 
@@ -766,14 +734,9 @@ int sse_autotune_update(sse_handle* h, const uint32_t* d_pairs, uint64_t n_pairs
   float best_ms = 0.f;
   for (int v = 0; v < kNumUpdateVariants && rc == SSE_OK; ++v) {
     // the pairs belong to the current slice, so repeating their update changes nothing
-    // each timed run includes the stamping of its cells (a tiled run defers it)
     rc = launch_variant(h, d_pairs, n_pairs, v);
-    if (rc == SSE_OK) rc = flush_bits(h);
     if (rc == SSE_OK && cudaEventRecord(e0, h->stream) != cudaSuccess) rc = fail(h, cudaGetLastError());
-    for (int r = 0; r < reps && rc == SSE_OK; ++r) {
-      rc = launch_variant(h, d_pairs, n_pairs, v);
-      if (rc == SSE_OK) rc = flush_bits(h);
-    }
+    for (int r = 0; r < reps && rc == SSE_OK; ++r) rc = launch_variant(h, d_pairs, n_pairs, v);
     if (rc == SSE_OK && (cudaEventRecord(e1, h->stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess))
       rc = fail(h, cudaGetLastError());
     if (rc != SSE_OK) break;
@@ -1050,7 +1013,6 @@ int close_graph_launch(sse_handle* h) {
   // the report kernel sets this word last (no report is pending, so nothing writes it now)
   *reinterpret_cast<volatile uint32_t*>(h->report_stage + offsetof(CloseScratch, report_done)) = 0u;
   SSE_CUDA(h, cudaGraphLaunch(h->close_exec, h->stream));
-  h->bits_pending = false;  // the replay's close pass stamped them
   SSE_CUDA(h, cudaEventRecord(h->close_done, h->stream));
   h->launches += h->close_kernels;
   h->close_pending = 1;
@@ -1219,20 +1181,6 @@ int sse_merge(sse_handle* dst, const sse_handle* const* srcs, int n) {
     sre_src.ptr[j] = s->sre;
     sle_src.ptr[j] = s->sle;
   }
-  int rc = flush_bits(dst);
-  for (int j = 0; j < n && rc == SSE_OK; ++j) {
-    // a source's deferred stamps, on its own stream, before dst's stream reads its SLEA
-    sse_handle* s = const_cast<sse_handle*>(srcs[j]);
-    if (!s->bits_pending) continue;
-    rc = flush_bits(s);
-    if (rc == SSE_OK && !s->ev_flushed &&
-        cudaEventCreateWithFlags(&s->ev_flushed, cudaEventDisableTiming) != cudaSuccess)
-      rc = fail(s, cudaGetLastError());
-    if (rc == SSE_OK && (cudaEventRecord(s->ev_flushed, s->stream) != cudaSuccess ||
-                         cudaStreamWaitEvent(dst->stream, s->ev_flushed, 0) != cudaSuccess))
-      rc = fail(dst, cudaGetLastError());
-  }
-  if (rc) return rc;
   const uint32_t cs = stamp_of(dst->slice, dst->smod);
   const auto merge_fn = dst->wide ? k_merge<uint16_t> : k_merge<uint8_t>;
   const uint64_t n16_sre = dst->d.sre_bytes / 16, n16_sle = dst->d.sle_bytes / 16;
@@ -1281,8 +1229,6 @@ int sse_get_hot_bitmap(sse_handle* h, uint32_t* h_bits, size_t cap_bytes) {
 int sse_read_stamps(sse_handle* h, uint8_t* h_sre, size_t sre_cap, uint8_t* h_sle, size_t sle_cap) {
   if (!h) return SSE_ERR_INVALID_PARAM;
   if ((h_sre && sre_cap < h->d.sre_bytes) || (h_sle && sle_cap < h->d.sle_bytes)) return SSE_ERR_CAPACITY;
-  const int rc = flush_bits(h);
-  if (rc) return rc;
   if (h_sre) SSE_CUDA(h, cudaMemcpyAsync(h_sre, h->sre, h->d.sre_bytes, cudaMemcpyDeviceToHost, h->stream));
   if (h_sle) SSE_CUDA(h, cudaMemcpyAsync(h_sle, h->sle, h->d.sle_bytes, cudaMemcpyDeviceToHost, h->stream));
   SSE_CUDA(h, cudaStreamSynchronize(h->stream));
@@ -1306,8 +1252,6 @@ int sse_export_state(sse_handle* h, void* h_buf, size_t cap, size_t* used) {
   *used = total;
   if (!h_buf) return SSE_OK;
   if (cap < total) return SSE_ERR_CAPACITY;
-  const int rc = flush_bits(h);
-  if (rc) return rc;
   StateHeader hd;
   memset(&hd, 0, sizeof(hd));
   hd.magic = kMagic;
@@ -1334,8 +1278,6 @@ int sse_import_state(sse_handle* h, const void* h_buf, size_t n) {
   if (n < sizeof(hd) + hd.sre_bytes + hd.sle_bytes) return SSE_ERR_INVALID_PARAM;
   const uint8_t* body = static_cast<const uint8_t*>(h_buf) + sizeof(hd);
   const uint32_t stamp = stamp_of(hd.slice, h->smod);
-  const int rc = flush_bits(h);  // clears the bitmap; the stamps are then replaced
-  if (rc) return rc;
   SSE_CUDA(h, cudaMemcpyAsync(h->state, body, hd.sre_bytes + hd.sle_bytes, cudaMemcpyHostToDevice, h->stream));
   SSE_CUDA(h, cudaMemcpyAsync(h->clock, &stamp, sizeof(stamp), cudaMemcpyHostToDevice, h->stream));
   SSE_CUDA(h, cudaStreamSynchronize(h->stream));
@@ -1424,7 +1366,7 @@ extern "C" int sse_query_noalloc(const sse_params* p, const uint8_t* d_sle, uint
     return SSE_ERR_CUDA;
   }
   k_close<uint8_t><<<(unsigned)(num_sms * 8), kCloseThreads, 0, stream>>>(
-      kp, nullptr, const_cast<uint8_t*>(d_sle), nullptr, counts, stamp_of(slice), nullptr, 0u, 0u, nullptr, nullptr);
+      kp, nullptr, const_cast<uint8_t*>(d_sle), nullptr, counts, stamp_of(slice), nullptr, 0u, 0u, nullptr);
   if (cudaGetLastError() != cudaSuccess) return SSE_ERR_CUDA;
   uint64_t grid = std::min<uint64_t>((uint64_t)n, (uint64_t)num_sms * 16);
   k_estimate<uint8_t><<<(unsigned)grid, est_threads(q.eta2, 1), 0, stream>>>(
@@ -1588,9 +1530,6 @@ int sse_batch_create(const sse_params* p, int n_routers, uint64_t capacity_pairs
   }
   for (int r = 0; r < n_routers && rc == SSE_OK; ++r) rc = sse_init(p, b->stream, &b->router[r]);
   if (rc == SSE_OK) rc = sse_init(p, b->stream, &b->global);
-  // the batch applies its estimators' bitmaps itself (k_apply_routers, k_apply_bits)
-  for (int r = 0; r < n_routers && rc == SSE_OK; ++r) b->router[r]->defer_apply = false;
-  if (rc == SSE_OK) b->global->defer_apply = false;
   if (rc == SSE_OK) {
     const bool ok = cudaMalloc(&b->inputs, (uint64_t)n_routers * capacity_pairs * 8) == cudaSuccess &&
                     cudaMalloc(&b->d_in, sizeof(RouterInputs)) == cudaSuccess &&
@@ -2128,9 +2067,6 @@ int sse_server_create(const sse_params* p, const sse_server_config* cfg, sse_ser
   }
   for (int r = 0; r < s->n && rc == SSE_OK; ++r) rc = sse_init(p, s->rstream[r], &s->router[r]);
   if (rc == SSE_OK) rc = sse_init(p, s->gstream, &s->global);
-  // the server applies its estimators' bitmaps itself at each boundary
-  for (int r = 0; r < s->n && rc == SSE_OK; ++r) s->router[r]->defer_apply = false;
-  if (rc == SSE_OK) s->global->defer_apply = false;
   if (rc == SSE_OK) {
     s->slots.resize(cfg->slots);
     for (ServerSlot& sl : s->slots) {
@@ -2576,8 +2512,6 @@ int sse_features(sse_handle* h, const uint32_t* d_hosts, uint32_t n, float* d_x)
   if (!h || (!d_hosts && n) || (!d_x && n) || h->wide) return SSE_ERR_INVALID_PARAM;
   if (h->sticky) return h->sticky;
   if (!n) return SSE_OK;
-  const int rc = flush_bits(h);
-  if (rc) return rc;
   k_features<<<grid_for(h, n, 1, 16), kFeatThreads, 0, h->stream>>>(h->kp, h->sre, h->sle, d_hosts, n, h->clock, d_x);
   SSE_LAUNCHED(h);
   return SSE_OK;
@@ -2608,7 +2542,6 @@ int sse_reset(sse_handle* h) {
   const uint32_t first = stamp_of(0, h->smod);
   SSE_CUDA(h, cudaMemsetAsync(h->state, 0, h->d.sre_bytes + h->d.sle_bytes, h->stream));
   SSE_CUDA(h, cudaMemsetAsync(h->sle_bits, 0, h->sle_cells / 8, h->stream));
-  h->bits_pending = false;
   SSE_CUDA(h, cudaMemsetAsync(h->hot_bits, 0, ((uint64_t)h->p.r << h->p.q) / 8, h->stream));
   SSE_CUDA(h, cudaMemsetAsync(h->scratch, 0, sizeof(CloseScratch), h->stream));
   SSE_CUDA(h, cudaMemcpyAsync(h->clock, &first, 4, cudaMemcpyHostToDevice, h->stream));

@@ -1,10 +1,10 @@
-"""Deferred stamping of the tiled update, through the C ABI.
+"""Calls interleaved with a slice's updates, through the C ABI.
 
-A tiled update keeps a slice's SLEA cells as bits; the slice close's pass stamps them while
-it reads the SLEA, and every other call that reads the SLEA (query, features, read_stamps,
-export, merge, advance) stamps them first. Whatever the calls in between, each observation
-must equal that of the direct update, which stamps every cell at once, and the oracle's
-(Algorithms 3 and 6, then 8 at the close).
+The tiled update collects a slice's SLEA cells as bits and stamps them afterwards. Whatever
+the calls between updates (query, features, read_stamps, export, merge of estimators on
+other streams, advance, an asynchronous close with the next slice's update behind it), each
+observation must equal that of the direct update, which stamps every cell at once, and the
+oracle's (Algorithms 3 and 6, then 8 at the close).
 """
 import numpy as np
 import pytest
@@ -77,10 +77,10 @@ def test_calls_between_updates_see_the_tiled_cells(stamp_bits):
         compare_state(tiled, orc, p, t)
 
 
-def test_merge_of_sources_with_pending_cells_on_other_streams():
-    """Two routers on streams of their own, each with pending tiled cells, merged into a
-    third estimator that has pending cells of its own: the merged state and the next close
-    equal the oracle's merge."""
+def test_merge_of_tiled_sources_on_other_streams():
+    """Two routers on streams of their own, each updated by the tiled kernel, merged into a
+    third estimator updated the same way: the merged state and the next close equal the
+    oracle's merge."""
     S = sse()
     p = S.Params(seed=9)
     tr = synth.Traffic(synth.TrafficConfig(seed=9, n_routers=3, n_slices=4))
@@ -107,8 +107,8 @@ def test_merge_of_sources_with_pending_cells_on_other_streams():
 
 def test_pipelined_closes_and_advance():
     """The benchmark's order (the next slice's update enqueued behind an asynchronous
-    close, before its report is read) and sse_advance (a close pass without detection)
-    stamp the pending cells of the right slice."""
+    close, before its report is read) and sse_advance (a close pass without detection):
+    every tiled cell carries the stamp of its own slice."""
     S = sse()
     p = S.Params(seed=13, k=3)
     tr = synth.Traffic(synth.small_trace(seed=13))
