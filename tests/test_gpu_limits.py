@@ -64,3 +64,16 @@ def test_largest_dimensions_match_oracle(shape, mode):
     del g_sre, o_sre
     for row in range(p.r2):
         same_cells(g_sle[row], o_sle[row], lut)
+
+
+@pytest.mark.parametrize("mode", [DIRECT, TILED])
+def test_most_rows_match_oracle(mode):
+    """r = r' = 16, the most rows validation accepts (delta = 2 at q = 14: a chain's 16 rows
+    each add two address bits), over four slices of the small trace: state, hot SREs, row
+    counts and reports every slice."""
+    from paper_1805_09246_b300 import sse as S
+    from tests.test_gpu_parity import run_both
+    p = S.Params(r=16, q=14, r2=16, seed=43)
+    tr = synth.Traffic(synth.small_trace(seed=43))
+    _, _, reports = run_both(p, [tr.slice(0, t) for t in range(4)], mode=mode)
+    assert reports[-1].n_super >= 15
