@@ -975,7 +975,8 @@ int ensure_report_stage(sse_handle* h) {
 int collect_staged(sse_handle* h, const uint32_t* sorted, uint64_t slice, sse_report* out, const uint8_t* stage,
                    uint32_t stage_n);
 
-int close_graph_launch(sse_handle* h) {
+// Captures the close's kernels into a CUDA graph and instantiates it, once per handle.
+int close_graph_build(sse_handle* h) {
   if (!h->close_exec) {
     if (!h->capture_stream) SSE_CUDA(h, cudaStreamCreateWithFlags(&h->capture_stream, cudaStreamNonBlocking));
     const int rc_stage = ensure_report_stage(h);
@@ -1009,6 +1010,12 @@ int close_graph_launch(sse_handle* h) {
     if (rc) return rc;
     SSE_CUDA(h, e);
   }
+  return SSE_OK;
+}
+
+int close_graph_launch(sse_handle* h) {
+  const int rc_build = close_graph_build(h);
+  if (rc_build) return rc_build;
   if (!h->close_done) SSE_CUDA(h, cudaEventCreateWithFlags(&h->close_done, cudaEventDisableTiming));
   // the report kernel sets this word last (no report is pending, so nothing writes it now)
   *reinterpret_cast<volatile uint32_t*>(h->report_stage + offsetof(CloseScratch, report_done)) = 0u;
@@ -1845,7 +1852,6 @@ struct ServerSlot {
 struct PendingClose {
   uint64_t slice;
   std::chrono::steady_clock::time_point boundary;
-  uint32_t* sorted;
 };
 
 struct ReadyReport {
@@ -1910,7 +1916,8 @@ void reporter_loop(sse_server* s) {
     rep.hosts = s->rep_hosts.data();
     rep.est = s->rep_est.data();
     rep.flags = s->rep_flags.data();
-    const int status = close_collect(s->global, pc.sorted, &rep);
+    // the report kernel's page-locked stage (close_graph_collect polls its completion word)
+    const int status = close_graph_collect(s->global, &rep);
     const double ms =
         std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - pc.boundary).count();
     ReadyReport rr;
@@ -1926,7 +1933,6 @@ void reporter_loop(sse_server* s) {
     rr.flags.assign(rep.flags, rep.flags + m);
     lk.lock();
     if (status != SSE_OK && status != SSE_ERR_CAPACITY && s->error == SSE_OK) s->error = status;
-    s->global->slice += 1;
     s->latencies.push_back(ms);
     s->ready.push_back(std::move(rr));
     s->pending.pop_front();
@@ -1938,11 +1944,13 @@ void reporter_loop(sse_server* s) {
 // Closes the current slice. Every router's update also wrote the global estimator (its RSRA
 // directly, its SLEA through the global's bitmap), so the global estimator already holds the
 // merge of the routers (Algorithms 2 and 7: the most recent stamp per cell) and the close
-// needs no pass over the routers' state: the global's bitmap is applied and the slice closed
-// on the global stream. Then, on a stream of its own so that it does not delay the report,
-// one pass resets the routers' cells that left the window (their next updates wait for it),
-// and the router clocks advance; the report is collected by the reporter thread. At most one
-// close is in flight.
+// needs no pass over the routers' state: once the routers' updates are done (each request
+// makes the global stream wait for its own), the global's bitmap is applied and the close's graph replayed
+// on the global stream (expiry and counts, detection, the report written into page-locked
+// host memory, the clock tick). Then, on a stream of its own so that it does not delay the
+// report, one pass resets the routers' cells that left the window (their next updates wait
+// for it), and the router clocks advance; the report is collected by the reporter thread. At
+// most one close is in flight.
 int server_close_slice(sse_server* s) {
   {
     std::unique_lock<std::mutex> lk(s->mu);
@@ -1951,19 +1959,12 @@ int server_close_slice(sse_server* s) {
   }
   sse_handle* g = s->global;
   const auto boundary = std::chrono::steady_clock::now();
-  for (int r = 0; r < s->n; ++r) {
-    SSE_CUDA(g, cudaEventRecord(s->ev_router[r], s->rstream[r]));
-    SSE_CUDA(g, cudaStreamWaitEvent(s->gstream, s->ev_router[r], 0));
-  }
   const uint64_t words = g->sle_cells / 32;
   k_apply_bits<uint8_t><<<grid_for(g, words, 256, 8), 256, 0, s->gstream>>>(g->sle_bits, g->sle, words, 0u, g->clock);
   SSE_LAUNCHED(g);
-  uint32_t* sorted = nullptr;
-  int rc = close_enqueue(g, &sorted);
+  const int rc = close_graph_launch(g);  // advances g->slice; the graph ticks the global clock
   if (rc) return rc;
   SSE_CUDA(g, cudaEventRecord(s->ev_closed, s->gstream));
-  k_tick<<<1, 32, 0, s->gstream>>>(g->clock, 1);
-  SSE_LAUNCHED(g);
   // the routers' expiry at this slice's stamp (router clocks tick only after it)
   const uint64_t n16 = (g->d.sre_bytes + g->d.sle_bytes) / 16;
   SSE_CUDA(g, cudaStreamWaitEvent(s->xstream, s->ev_closed, 0));
@@ -1980,7 +1981,7 @@ int server_close_slice(sse_server* s) {
   }
   {
     std::lock_guard<std::mutex> lk(s->mu);
-    s->pending.push_back(PendingClose{s->cur_slice, boundary, sorted});
+    s->pending.push_back(PendingClose{s->cur_slice, boundary});
   }
   s->cv.notify_all();
   s->cur_slice += 1;
@@ -2096,6 +2097,12 @@ int sse_server_create(const sse_params* p, const sse_server_config* cfg, sse_ser
   s->rep_hosts.resize(q.max_candidates);
   s->rep_est.resize(q.max_candidates);
   s->rep_flags.resize(q.max_candidates);
+  // the global estimator's close graph, captured now rather than at the first boundary
+  rc = close_graph_build(s->global);
+  if (rc != SSE_OK) {
+    sse_server_destroy(s);
+    return rc;
+  }
   s->reporter = std::thread(reporter_loop, s);
   *out = s;
   return SSE_OK;
@@ -2141,6 +2148,12 @@ int sse_server_submit(sse_server* s, uint32_t router, double t_arrival, const ui
     SSE_CUDA(h, cudaEventRecord(sl.done, s->rstream[router]));
     sl.used = true;
     done += m;
+  }
+  // the next slice close (on the global stream) waits for this request's updates; the wait is
+  // enqueued now, so the boundary itself only launches the close
+  if (n_pairs) {
+    SSE_CUDA(h, cudaEventRecord(s->ev_router[router], s->rstream[router]));
+    SSE_CUDA(h, cudaStreamWaitEvent(s->gstream, s->ev_router[router], 0));
   }
   if (pinned && n_pairs)  // copies on one stream finish in order: the last one covers all
     SSE_CUDA(h, cudaEventSynchronize(s->slots[(s->next_slot + s->slots.size() - 1) % s->slots.size()].copied));
