@@ -1965,6 +1965,11 @@ int server_close_slice(sse_server* s) {
   const int rc = close_graph_launch(g);  // advances g->slice; the graph ticks the global clock
   if (rc) return rc;
   SSE_CUDA(g, cudaEventRecord(s->ev_closed, s->gstream));
+  {  // the reporter starts waiting for the report now, while the routers' work is enqueued
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->pending.push_back(PendingClose{s->cur_slice, boundary});
+  }
+  s->cv.notify_all();
   // the routers' expiry at this slice's stamp (router clocks tick only after it)
   const uint64_t n16 = (g->d.sre_bytes + g->d.sle_bytes) / 16;
   SSE_CUDA(g, cudaStreamWaitEvent(s->xstream, s->ev_closed, 0));
@@ -1979,11 +1984,6 @@ int server_close_slice(sse_server* s) {
     SSE_LAUNCHED(h);
     h->slice += 1;
   }
-  {
-    std::lock_guard<std::mutex> lk(s->mu);
-    s->pending.push_back(PendingClose{s->cur_slice, boundary});
-  }
-  s->cv.notify_all();
   s->cur_slice += 1;
   return SSE_OK;
 }
