@@ -894,7 +894,8 @@ def main():
             "hosts_above_gate": l["hosts_above_gate"], "p90_rel_err_learned": l["p90_rel_err_learned"],
             "p90_rel_err_lc": l["p90_rel_err_lc"], "gpu_launches": l["gpu_launches"], "clocks": l["clocks"],
             "workload": l["config"]["workload"]}
-    cpu = None if args.no_cpu or paper else cpu_baseline(host)
+    # the oracle on the host's cores: at one rank only (with more ranks the host runs their work)
+    cpu = None if args.no_cpu or paper or world > 1 else cpu_baseline(host)
     close_sorted = sorted(close_ms)
     out = {
         "metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": world, "steps": args.steps,
