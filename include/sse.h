@@ -473,8 +473,9 @@ SSE_API int sse_batch_reset(sse_batch* b);
  * routers (Algorithm 7: the most recent stamp per cell). A request in a later slice first
  * closes the current slice: detection runs on the global estimator while the next slice's
  * requests proceed, then one pass resets the routers' cells that left the window (the
- * routers' next updates wait for it), and a reporter thread collects the report; its
- * latency runs from the slice boundary to the report being on the host. Arrival times must
+ * routers' next updates wait for it), and a reporter thread collects the report (the
+ * close's last kernel writes it into page-locked host memory); its latency runs from the
+ * slice boundary to the report being on the host. Arrival times must
  * not decrease. One thread submits.
  */
 typedef struct sse_server sse_server;
