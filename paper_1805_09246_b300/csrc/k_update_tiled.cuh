@@ -118,7 +118,7 @@ __global__ void __launch_bounds__(kTiledThreads, 1) k_update_tiled(const __grid_
   const uint32_t piece = tile % g.pieces;
   const uint32_t lo = piece * g.piece_bytes;  // cell range [lo, lo + piece_bytes) of the row
   const uint32_t words = g.piece_bytes >> 5;
-  for (uint32_t w = threadIdx.x; w < words; w += blockDim.x) bm[w] = 0;
+  for (uint32_t w = threadIdx.x; w < words; w += kTiledThreads) bm[w] = 0;
   RsraQueue rq{reinterpret_cast<uint2*>(bm + words) + (threadIdx.x >> 5) * kRsraQueueEntries, 0u, threadIdx.x & 31u};
   __syncthreads();
 
@@ -141,7 +141,7 @@ __global__ void __launch_bounds__(kTiledThreads, 1) k_update_tiled(const __grid_
   const uint64_t j0 = begin;
   const uint4* vec = reinterpret_cast<const uint4*>(pairs + j0);
   const uint32_t nvec = (uint32_t)((end - j0) >> 1);
-  const uint32_t stride = blockDim.x;
+  constexpr uint32_t stride = kTiledThreads;  // the launch's block size: load offsets fold into immediates
   const uint64_t policy = stream_policy();
   // Block iteration k covers vectors [k*stride*UNROLL, (k+1)*stride*UNROLL); its RSRA work
   // belongs to tile k mod tiles. The test is uniform across the block and taken once per
