@@ -67,10 +67,10 @@ __global__ void __launch_bounds__(kTiledThreads, 1)
                      tile_flush_bytes(p.row_pitch2, lo, g.piece_bytes), !zero);
     if (zero) {
       __syncthreads();
-      for (uint32_t w = threadIdx.x; w < words; w += blockDim.x) bm[w] = 0;
+      for (uint32_t w = threadIdx.x; w < words; w += kTiledThreads) bm[w] = 0;
     }
   };
-  for (uint32_t w = threadIdx.x; w < words; w += blockDim.x) bm[w] = 0;
+  for (uint32_t w = threadIdx.x; w < words; w += kTiledThreads) bm[w] = 0;
   RsraQueue rq{reinterpret_cast<uint2*>(bm + words) + (threadIdx.x >> 5) * kRsraQueueEntries, 0u, threadIdx.x & 31u};
   int cur = -1;
   while (true) {
@@ -109,12 +109,12 @@ __global__ void __launch_bounds__(kTiledThreads, 1)
     const uint64_t policy = stream_policy();
     auto scan = [&](auto with_rsra) {
       constexpr bool kRsra = decltype(with_rsra)::value;
-      for (uint32_t b0 = threadIdx.x - lane; b0 < nvec; b0 += blockDim.x * UNROLL) {
+      for (uint32_t b0 = threadIdx.x - lane; b0 < nvec; b0 += kTiledThreads * UNROLL) {
         const uint32_t i0 = b0 + lane;
         uint4 buf[UNROLL];
-        if (b0 + (UNROLL - 1) * blockDim.x + 31 < nvec) {  // every load of the warp in range
+        if (b0 + (UNROLL - 1) * kTiledThreads + 31 < nvec) {  // every load of the warp in range
 #pragma unroll
-          for (int u = 0; u < UNROLL; ++u) buf[u] = load_stream(vec + i0 + u * blockDim.x, policy);
+          for (int u = 0; u < UNROLL; ++u) buf[u] = load_stream(vec + i0 + u * kTiledThreads, policy);
 #pragma unroll
           for (int u = 0; u < UNROLL; ++u) {
             touch(buf[u].x, buf[u].y);
@@ -131,12 +131,12 @@ __global__ void __launch_bounds__(kTiledThreads, 1)
         }
 #pragma unroll
         for (int u = 0; u < UNROLL; ++u) {
-          const uint32_t i = i0 + u * blockDim.x;
+          const uint32_t i = i0 + u * kTiledThreads;
           buf[u] = i < nvec ? load_stream(vec + i, policy) : make_uint4(0, 0, 0, 0);
         }
 #pragma unroll
         for (int u = 0; u < UNROLL; ++u) {
-          const bool ok = i0 + u * blockDim.x < nvec;
+          const bool ok = i0 + u * kTiledThreads < nvec;
           if (ok) {
             touch(buf[u].x, buf[u].y);
             touch(buf[u].z, buf[u].w);
