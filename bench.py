@@ -44,7 +44,7 @@ DISTINCT = 16        # device-resident slices the warm-up and timed steps cycle 
 PAIR_BYTES = 8
 CORE_LINK_WORKLOAD = ("core_link: 2^25 pairs/slice, 16M-host Zipf(1.05), 200 planted super points; "
                       "q=20, r=5, SLEA r'=5 x (2^16 SLEs, eta'=4096, delta'=16), k=8, theta=1024")
-TILED8_DRAM_BYTES = 273_638_144 + 7_103_744
+TILED8_DRAM_BYTES = 273_648_896 + 7_201_024
 
 
 def parse(argv=None):
