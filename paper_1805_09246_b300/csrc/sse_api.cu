@@ -1945,12 +1945,13 @@ void reporter_loop(sse_server* s) {
 // directly, its SLEA through the global's bitmap), so the global estimator already holds the
 // merge of the routers (Algorithms 2 and 7: the most recent stamp per cell) and the close
 // needs no pass over the routers' state: once the routers' updates are done (each request
-// makes the global stream wait for its own), the global's bitmap is applied and the close's graph replayed
-// on the global stream (expiry and counts, detection, the report written into page-locked
-// host memory, the clock tick). Then, on a stream of its own so that it does not delay the
-// report, one pass resets the routers' cells that left the window (their next updates wait
-// for it), and the router clocks advance; the report is collected by the reporter thread. At
-// most one close is in flight.
+// makes the global stream wait for its own), the global's bitmap is applied and the close's
+// graph replayed on the global stream (expiry and counts, detection, the report written into
+// page-locked host memory, the clock tick). The reporter thread is woken at once. Then, on a
+// stream of its own so that it does not delay the report, one pass resets the routers' cells
+// that left the window (their next updates wait for it), and the router clocks advance. At
+// most one close is in flight; the reporter owns the global estimator's report fields until
+// it has collected the report.
 int server_close_slice(sse_server* s) {
   {
     std::unique_lock<std::mutex> lk(s->mu);
