@@ -294,6 +294,8 @@ struct EstTable {
   uint64_t row_len2;
   double w_theta;
   uint32_t r2, eta2, blocks;
+  uint32_t per_block;  // entries per block (a multiple of 32, at most the block size): the
+                       // FP64 work spread over many SMs
 };
 
 // The hot SREs of one row grouped by column block: block b (columns [b * 2^s, (b+1) * 2^s),
@@ -359,8 +361,8 @@ __global__ void __launch_bounds__(256) k_hot_prep(const uint32_t* __restrict__ h
     __syncthreads();
     double P = 1.0;
     for (uint32_t i = 0; i < tab.r2; ++i) P = __dmul_rn(P, quot[i]);
-    const uint32_t U = (b - (gridDim.x - tab.blocks)) * blockDim.x + threadIdx.x;
-    if (U <= tab.eta2) {
+    const uint32_t U = (b - (gridDim.x - tab.blocks)) * tab.per_block + threadIdx.x;
+    if (threadIdx.x < tab.per_block && U <= tab.eta2) {
       const LcResult res = lc_estimate(U, P, (double)tab.eta2, tab.w_theta);
       tab.w[U] = res.w;
       tab.est[U] = res.est;

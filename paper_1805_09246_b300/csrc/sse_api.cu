@@ -849,7 +849,11 @@ EstTable est_table(sse_handle* h, const uint32_t* active2) {
   t.w_theta = h->d.w_theta;
   t.r2 = h->p.r2;
   t.eta2 = h->p.eta2;
-  t.blocks = (uint32_t)((n + 255) / 256);
+  // about two blocks per SM, whole warps each: the table's FP64 divisions and logarithms
+  // then run on every SM instead of on n / 256 of them
+  const uint64_t per = (n + 2 * (uint64_t)h->num_sms - 1) / (2 * (uint64_t)h->num_sms);
+  t.per_block = (uint32_t)std::min<uint64_t>(256, (per + 31) / 32 * 32);
+  t.blocks = (uint32_t)((n + t.per_block - 1) / t.per_block);
   return t;
 }
 
