@@ -359,7 +359,9 @@ int launch_update_tiled(sse_handle* h, const uint32_t* d_pairs, uint64_t n, int 
   }
   const uint64_t words = h->sle_cells / 32;
   const auto apply = h->wide ? k_apply_bits<uint16_t> : k_apply_bits<uint8_t>;
-  SSE_CUDA(h, launch_pdl(apply, dim3(grid_for(h, words, 256, 8)), dim3(256), 0, h->stream, h->sle_bits, h->sle,
+  // one thread per 16-byte vector of cells (2 or 4 per bitmap word), up to 8 blocks per SM
+  const uint64_t vecs = words * (h->wide ? 4 : 2);
+  SSE_CUDA(h, launch_pdl(apply, dim3(grid_for(h, vecs, 256, 8)), dim3(256), 0, h->stream, h->sle_bits, h->sle,
                          words, stamp, (const uint32_t*)h->clock));
   SSE_LAUNCHED(h);
   return SSE_OK;
@@ -1464,7 +1466,7 @@ int batch_enqueue_update(sse_batch* b) {
   k_apply_routers<<<grid, 256, 0, b->stream>>>(b->rt, g->d.sre_bytes, words, g->clock, global ? g->sle_bits : nullptr);
   SSE_LAUNCHED(g);
   if (global) {
-    k_apply_bits<uint8_t><<<grid_for(g, words, 256, 8), 256, 0, b->stream>>>(g->sle_bits, g->sle, words, 0u, g->clock);
+    k_apply_bits<uint8_t><<<grid_for(g, 2 * words, 256, 8), 256, 0, b->stream>>>(g->sle_bits, g->sle, words, 0u, g->clock);
     SSE_LAUNCHED(g);
   }
   return SSE_OK;
@@ -1965,7 +1967,7 @@ int server_close_slice(sse_server* s) {
   sse_handle* g = s->global;
   const auto boundary = std::chrono::steady_clock::now();
   const uint64_t words = g->sle_cells / 32;
-  k_apply_bits<uint8_t><<<grid_for(g, words, 256, 8), 256, 0, s->gstream>>>(g->sle_bits, g->sle, words, 0u, g->clock);
+  k_apply_bits<uint8_t><<<grid_for(g, 2 * words, 256, 8), 256, 0, s->gstream>>>(g->sle_bits, g->sle, words, 0u, g->clock);
   SSE_LAUNCHED(g);
   const int rc = close_graph_launch(g);  // advances g->slice; the graph ticks the global clock
   if (rc) return rc;
