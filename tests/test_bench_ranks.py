@@ -88,3 +88,27 @@ def test_oracle_threads_bounded_by_host_cores_and_cap():
     import bench
     assert bench.oracle_threads(None) == min(bench.host_cores(), bench.CPU_THREADS_MAX)
     assert bench.oracle_threads(3) == 3 and bench.oracle_threads(10**6) == bench.CPU_THREADS_MAX
+
+
+def test_reference_arm_line_carries_the_contract_keys(monkeypatch, capsys):
+    """The reference arm (the oracle on host threads) prints one JSON line with the keys the
+    benchmark contract asks of it; a small trace stands in for the core-link slices."""
+    import json
+    sys.path.insert(0, ROOT)
+    import bench
+    from paper_1805_09246_b300 import synth
+    monkeypatch.setattr(bench, "make_traffic",
+                        lambda rank: synth.Traffic(synth.TrafficConfig(seed=rank, n_slices=16)))
+    args = bench.parse(["--impl", "reference", "--steps", "2", "--warmup", "1"])
+    bench.run_reference(args, 0, 1, threads=2)
+    lines = [x for x in capsys.readouterr().out.splitlines() if x.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    for key in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+                "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert key in d, key
+    assert d["impl"] == "reference" and d["steps"] == 2 and d["warmup"] == 1 and d["value"] > 0
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] == 2
+    assert d["cpu_baseline"]["value"] == d["value"] and d["e2e"]["value"] == d["value"]
+    assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
+    assert d["config"]["workload"] == bench.CORE_LINK_WORKLOAD
