@@ -232,15 +232,20 @@ def run_reference(args, rank, world, threads: int | None = None):
     start, done = threading.Barrier(n_thr + 1), threading.Barrier(n_thr + 1)
 
     def work(i):
-        o = orcs[i]
-        for w in range(args.warmup):
-            o.scan(data[(i + w) % len(data)])
-            o.advance()
-        start.wait()
-        for s in range(args.steps):
-            o.scan(data[(i + args.warmup + s) % len(data)])
-            o.advance()
-        done.wait()
+        try:
+            o = orcs[i]
+            for w in range(args.warmup):
+                o.scan(data[(i + w) % len(data)])
+                o.advance()
+            start.wait()
+            for s in range(args.steps):
+                o.scan(data[(i + args.warmup + s) % len(data)])
+                o.advance()
+            done.wait()
+        except BaseException:  # a failed thread breaks the barriers, so the run fails instead of waiting
+            start.abort()
+            done.abort()
+            raise
 
     pool = [threading.Thread(target=work, args=(i,)) for i in range(n_thr)]
     for t in pool:
@@ -287,7 +292,10 @@ def cpu_baseline(tr_slices, min_seconds=12.0, min_slices=8, max_slices=64, threa
 
     def work(i):
         o = orcs[i]
-        start.wait()
+        try:
+            start.wait()
+        except threading.BrokenBarrierError:
+            return
         t = 0
         while t < max_slices:
             with lock:
